@@ -1,0 +1,527 @@
+"""Pins for the FP64 oracle: each check compares it with something other than itself
+(closed forms, invariants, an independent derivation, brute force, the paper's values).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+
+import synth
+from oracle import gf_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- K0 --------
+def _k0_tensor_product(h=1.0, E=1.0, nu=0.3):
+    """Exact K_e from 1D integrals of linear hats (no quadrature, no B matrix).
+
+    S_ab[i,j] = int d_a N_i d_b N_j factorises over the axes into the 1D integrals
+    m = int phi phi, k = int phi' phi', c = int phi' phi; then
+    K[3i+al, 3j+be] = lam S_{al be} + mu S_{be al} + mu delta_{al be} sum_g S_gg.
+    """
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    m1 = h / 6.0 * np.array([[2.0, 1.0], [1.0, 2.0]])
+    k1 = 1.0 / h * np.array([[1.0, -1.0], [-1.0, 1.0]])
+    c1 = np.array([[-0.5, -0.5], [0.5, 0.5]])  # c1[p,q] = int phi_p' phi_q
+    nodes = O.LOCAL_NODES
+
+    def S(a, b):
+        out = np.zeros((8, 8))
+        for i, ni in enumerate(nodes):
+            for j, nj in enumerate(nodes):
+                v = 1.0
+                for d in range(3):
+                    p, q = ni[d], nj[d]
+                    if d == a and d == b:
+                        v *= k1[p, q]
+                    elif d == a:
+                        v *= c1[p, q]
+                    elif d == b:
+                        v *= c1[q, p]
+                    else:
+                        v *= m1[p, q]
+                out[i, j] = v
+        return out
+
+    Ss = {(a, b): S(a, b) for a in range(3) for b in range(3)}
+    trace = Ss[0, 0] + Ss[1, 1] + Ss[2, 2]
+    K = np.zeros((24, 24))
+    for al in range(3):
+        for be in range(3):
+            blk = lam * Ss[al, be] + mu * Ss[be, al] + (mu * trace if al == be else 0.0)
+            K[al::3, be::3] = blk
+    return K
+
+
+def _rigid_modes(x, y, z):
+    n = x.size
+    R = np.zeros((3 * n, 6))
+    R[0::3, 0] = 1
+    R[1::3, 1] = 1
+    R[2::3, 2] = 1
+    R[0::3, 3], R[1::3, 3] = -y, x
+    R[1::3, 4], R[2::3, 4] = -z, y
+    R[0::3, 5], R[2::3, 5] = z, -x
+    return R
+
+
+def test_k0_equals_exact_tensor_product_integration():
+    for h in (1.0, 2.0, 0.5):
+        assert np.allclose(O.element_stiffness(h), _k0_tensor_product(h), rtol=0, atol=1e-15)
+
+
+def test_k0_symmetric_and_gauss_exact():
+    K = O.element_stiffness()
+    assert np.array_equal(K, K.T) or np.abs(K - K.T).max() < 1e-16
+    assert np.abs(O.element_stiffness(gauss=4) - K).max() < 1e-15
+
+
+def test_k0_spectrum_and_rigid_null_space():
+    K = O.element_stiffness()
+    ev = np.linalg.eigvalsh(K)
+    assert np.sum(np.abs(ev) < 1e-13) == 6 and np.sum(ev > 1e-3) == 18
+    pts = np.array(O.LOCAL_NODES, dtype=float)
+    R = _rigid_modes(pts[:, 0], pts[:, 1], pts[:, 2])
+    assert np.abs(K @ R).max() < 1e-14
+    assert np.linalg.matrix_rank(R) == 6
+
+
+def test_k0_integer_structure_and_scaling():
+    nu = 0.3
+    K = O.element_stiffness(1.0, 1.0, nu)
+    M = K * (1 + nu) * (1 - 2 * nu) * 720
+    assert np.abs(M - np.round(M)).max() < 1e-12
+    assert np.abs(np.round(M)).max() == 88
+    assert np.abs(O.element_stiffness(2.0) - 2.0 * K).max() < 1e-15
+    assert np.abs(O.element_stiffness(1.0, 3.0) - 3.0 * K).max() < 1e-15
+
+
+def test_uniform_strain_energy_closed_form():
+    """u = A x on an unconstrained solid block: u^T K u = V * eps:C:eps."""
+    m = O.Mesh(3, 2, 2, h=0.5)
+    K0 = O.element_stiffness(m.h)
+    Kfull = O.assemble_sparse(m, np.ones(m.n_elem), K0, constrained=False)
+    x, y, z = m.node_coords()
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((3, 3))
+    u = np.zeros(m.n_dof)
+    for c in range(3):
+        u[c::3] = A[c, 0] * x + A[c, 1] * y + A[c, 2] * z
+    eps = 0.5 * (A + A.T)
+    nu, E = 0.3, 1.0
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    density = lam * np.trace(eps) ** 2 + 2 * mu * np.sum(eps * eps)
+    vol = m.n_elem * m.h ** 3
+    assert abs(u @ (Kfull @ u) - vol * density) < 1e-12 * vol * density
+    # patch test: interior nodes feel no force under a linear field
+    f = Kfull @ u
+    i = np.arange(m.n_nodes) % (m.nx + 1)
+    j = (np.arange(m.n_nodes) // (m.nx + 1)) % (m.ny + 1)
+    k = np.arange(m.n_nodes) // ((m.nx + 1) * (m.ny + 1))
+    interior = (i > 0) & (i < m.nx) & (j > 0) & (j < m.ny) & (k > 0) & (k < m.nz)
+    assert interior.any()
+    assert np.abs(f.reshape(-1, 3)[interior]).max() < 1e-13
+
+
+# ---------------------------------------------------------------- mesh ------
+def test_mesh_counts_and_load():
+    for (nx, ny, nz), ndof in (((16, 8, 8), 4131), ((96, 48, 48), 698691), ((192, 96, 96), 5447811)):
+        assert 3 * (nx + 1) * (ny + 1) * (nz + 1) == ndof
+    m = O.Mesh(16, 8, 8)
+    assert m.n_dof == 4131 and m.fixed.sum() == 3 * 9 * 9
+    f = O.cantilever_load(m)
+    assert np.linalg.norm(f) == 1.0
+    n = int(np.nonzero(f)[0][0]) // 3
+    x, y, z = m.node_coords()
+    assert (x[n], y[n], z[n]) == (16.0, 4.0, 4.0) and f[3 * n + 2] == -1.0
+    # element connectivity: element 0 nodes are the unit cube corners in local order
+    pts = np.stack(m.node_coords(), axis=1)[m.conn[0]]
+    assert np.array_equal(pts, np.array(O.LOCAL_NODES, dtype=float))
+    e = 1 + 16 * (2 + 8 * 3)
+    assert np.array_equal(np.stack(m.node_coords(), axis=1)[m.conn[e, 0]], [1, 2, 3])
+    with pytest.raises(ValueError):
+        O.cantilever_load(O.Mesh(4, 3, 2))
+
+
+# ---------------------------------------------------------------- operator --
+def test_apply_matches_dense_brute_force_and_sparse():
+    m = O.Mesh(4, 2, 2)
+    rho = synth.uniform_density(4, 2, 2, 3)
+    E = O.young_modulus(rho, 1e-3, 3)
+    K0 = O.element_stiffness()
+    u = synth.random_vector(m.n_dof, 7)
+    Kd = O.assemble_dense_free(m, E, K0)
+    y_ref = np.zeros(m.n_dof)
+    y_ref[m.free] = Kd @ u[m.free]
+    y = O.apply_K(m, E, K0, u)
+    assert np.abs(y - y_ref).max() < 1e-13 * np.abs(y_ref).max()
+    Ks = O.assemble_sparse(m, E, K0)
+    assert np.abs(Ks @ u - y).max() < 1e-13 * np.abs(y).max()
+    nodes = [0, 5, 13, m.n_nodes - 1, m.node(4, 1, 1)]
+    yn = O.apply_K_at_nodes(m, E, K0, u, nodes)
+    assert np.abs(yn - y.reshape(-1, 3)[nodes]).max() < 1e-13 * np.abs(y).max()
+
+
+def test_operator_symmetric_spd_and_rigid_modes():
+    m = O.Mesh(3, 2, 2)
+    E = O.young_modulus(synth.uniform_density(3, 2, 2, 1), 1e-3, 3)
+    K0 = O.element_stiffness()
+    u, v = synth.random_vector(m.n_dof, 1), synth.random_vector(m.n_dof, 2)
+    assert abs(u @ O.apply_K(m, E, K0, v) - v @ O.apply_K(m, E, K0, u)) < 1e-13
+    Kd = O.assemble_dense_free(m, E, K0)
+    assert np.linalg.eigvalsh(Kd).min() > 0
+    Kfull = O.assemble_sparse(m, E, K0, constrained=False)
+    R = _rigid_modes(*m.node_coords())
+    assert np.abs(Kfull @ R).max() < 1e-13
+
+
+def test_floor_monotonicity_identity():
+    """Eq. (floor_monotonicity): K(rb) - K(ra) = (rb - ra) sum_e (1 - rho_e^p) K_e  (PSD)."""
+    m = O.Mesh(4, 2, 2)
+    rho = synth.uniform_density(4, 2, 2, 9)
+    K0 = O.element_stiffness()
+    u = synth.random_vector(m.n_dof, 3)
+    ra, rb, p = 1e-6, 1e-3, 3
+    lhs = O.apply_K(m, O.young_modulus(rho, rb, p), K0, u) - O.apply_K(m, O.young_modulus(rho, ra, p), K0, u)
+    rhs = (rb - ra) * O.apply_K(m, 1.0 - rho ** 3, K0, u)
+    assert np.abs(lhs - rhs).max() < 1e-13 * np.abs(rhs).max() + 1e-16
+    assert u @ lhs >= 0
+    # K(rho_min) >= rho_min K_solid
+    Kmin = O.assemble_dense_free(m, O.young_modulus(rho, rb, p), K0)
+    Ks = O.assemble_dense_free(m, np.ones(m.n_elem), K0)
+    assert np.linalg.eigvalsh(Kmin - rb * Ks).min() > -1e-12
+
+
+def test_young_modulus_values_and_void_derivative():
+    assert np.array_equal(O.young_modulus(np.array([0.0, 1.0]), 1e-3, 3), [1e-3, 1.0])
+    r = np.array([0.3, 0.77])
+    assert np.allclose(O.young_modulus(r, 1e-4, 4.5), 1e-4 + (1 - 1e-4) * r ** 4.5, rtol=1e-15)
+    assert np.array_equal(O.young_modulus(r, 1e-4, 3), 1e-4 + (1 - 1e-4) * (r * r * r))
+    # Remark after Prop. 1: d/drho_min [rho + (1-rho) rho^p] = 1 - rho^p + p (1-rho) rho^(p-1) >= 0
+    for p in (3.0, 4.5):
+        for rm in (1e-6, 1e-3, 0.3):
+            h = rm * 1e-5
+            num = (O.young_modulus(np.array([rm + h]), rm + h, p)[0]
+                   - O.young_modulus(np.array([rm - h]), rm - h, p)[0]) / (2 * h)
+            exact = 1 - rm ** p + p * (1 - rm) * rm ** (p - 1)
+            assert exact >= 0 and abs(num - exact) < 1e-6 * exact
+
+
+# ---------------------------------------------------------------- hierarchy -
+def test_prolongation_interpolates_linears_and_galerkin_equals_rediscretisation():
+    fine = O.Mesh(4, 2, 4, h=1.0)
+    coarse = O.Mesh(2, 1, 2, h=2.0)
+    P = O.prolongation(fine)
+    assert P.shape == (fine.n_dof, coarse.n_dof)
+    xc, yc, zc = coarse.node_coords()
+    xf, yf, zf = fine.node_coords()
+    for c in range(3):
+        uc = np.zeros(coarse.n_dof)
+        uc[c::3] = 1.0 + 2 * xc - 3 * yc + 0.5 * zc
+        uf = P @ uc
+        assert np.abs(uf[c::3] - (1.0 + 2 * xf - 3 * yf + 0.5 * zf)).max() < 1e-14
+    # at constant modulus, P^T K_h P = K_2h, masked on both sides
+    K0f, K0c = O.element_stiffness(1.0), O.element_stiffness(2.0)
+    Kf = O.assemble_sparse(fine, np.full(fine.n_elem, 0.7), K0f)
+    Kc = O.assemble_sparse(coarse, np.full(coarse.n_elem, 0.7), K0c)
+    Pm = sp.diags(fine.free * 1.0) @ P @ sp.diags(coarse.free * 1.0)
+    G = (Pm.T @ Kf @ Pm).toarray()
+    assert np.abs(G - Kc.toarray()).max() < 1e-13
+
+
+def test_coarsen_modulus_mean():
+    m = O.Mesh(4, 2, 2)
+    E = np.arange(m.n_elem, dtype=float)
+    Ec = O.coarsen_modulus(m, E)
+    # coarse element 0 = mean of fine elements with ex<2, ey<2, ez<2
+    idx = [ex + 4 * (ey + 2 * ez) for ez in (0, 1) for ey in (0, 1) for ex in (0, 1)]
+    assert Ec[0] == np.mean(E[idx]) and Ec.size == 2
+    assert np.all(O.coarsen_modulus(m, np.full(m.n_elem, 0.25)) == 0.25)
+
+
+def test_block_diagonal_matches_assembled():
+    m = O.Mesh(3, 2, 2)
+    E = O.young_modulus(synth.uniform_density(3, 2, 2, 4), 1e-3, 3)
+    K0 = O.element_stiffness()
+    Kd = O.assemble_sparse(m, E, K0, constrained=False).toarray()
+    Db = O.node_block_diagonal(m, E, K0)
+    fixed_node = m.fixed[0::3]
+    for n in range(m.n_nodes):
+        ref = np.eye(3) if fixed_node[n] else Kd[3 * n:3 * n + 3, 3 * n:3 * n + 3]
+        assert np.abs(Db[n] - ref).max() < 1e-14
+    d = O.operator_diagonal(m, E, K0)
+    assert np.abs(d - np.einsum("nii->ni", Db).ravel()).max() < 1e-14
+
+
+def _hier(nx=8, ny=4, nz=4, seed=0, levels=3, rho_min=1e-3):
+    m = O.Mesh(nx, ny, nz)
+    E = O.young_modulus(synth.uniform_density(nx, ny, nz, seed), rho_min, 3)
+    return m, E, O.build_hierarchy(m, E, levels)
+
+
+def test_vcycle_symmetric_linear_and_exact_on_one_level():
+    m, E, H = _hier()
+    a, b = synth.random_vector(m.n_dof, 1), synth.random_vector(m.n_dof, 2)
+    a[m.fixed] = 0
+    b[m.fixed] = 0
+    Va, Vb = O.vcycle(H, a), O.vcycle(H, b)
+    assert abs(b @ Va - a @ Vb) < 1e-12 * np.linalg.norm(Va) * np.linalg.norm(b)
+    assert np.abs(O.vcycle(H, 2 * a - b) - (2 * Va - Vb)).max() < 1e-12 * np.abs(Va).max()
+    H1 = O.build_hierarchy(m, E, 1)
+    x = O.vcycle(H1, a)
+    assert np.abs(O.apply_K(m, E, H1.levels[0].K0, x) - a).max() < 1e-10 * np.abs(a).max()
+
+
+def test_vcycle_contracts_error_in_energy_norm():
+    """As a stationary iteration, x <- x + B(f - K x) reduces the K-norm of the error."""
+    m, E, H = _hier(seed=3)
+    K0 = H.levels[0].K0
+    x_true = synth.random_vector(m.n_dof, 4)
+    x_true[m.fixed] = 0
+    f = O.apply_K(m, E, K0, x_true)
+    x = np.zeros(m.n_dof)
+    err0 = None
+    for it in range(6):
+        e = x_true - x
+        en = math.sqrt(e @ O.apply_K(m, E, K0, e))
+        if err0 is None:
+            err0 = en
+        x = x + O.vcycle(H, f - O.apply_K(m, E, K0, x))
+    e = x_true - x
+    assert math.sqrt(e @ O.apply_K(m, E, K0, e)) < 0.5 * err0
+
+
+# ---------------------------------------------------------------- FGMRES ----
+def test_fgmres_diagonal_distinct_eigenvalues():
+    d = np.array([1.0, 2.0, 2.0, 3.0, 3.0, 3.0, 5.0])
+    f = np.ones(7)
+    res = O.fgmres(lambda v: d * v, lambda v: v, f, restart=30, kmax=50, tol=1e-12)
+    assert res.iters <= 4 and res.flag == O.CONVERGED
+    assert np.abs(res.x - f / d).max() < 1e-12
+    assert res.history[0] == 1.0
+
+
+def test_fgmres_projected_estimate_equals_true_residual_each_step():
+    m, E, H = _hier(seed=2)
+    K0 = H.levels[0].K0
+    f = O.cantilever_load(m)
+    A = lambda v: O.apply_K(m, E, K0, v)
+    B = lambda v: O.vcycle(H, v)
+    full = O.fgmres(A, B, f, restart=6, kmax=14, tol=1e-14)
+    for k in range(1, 15):
+        r = O.fgmres(A, B, f, restart=6, kmax=k, tol=1e-14)
+        assert r.iters == k and np.array_equal(r.history[:k], full.history[:k])
+        true = np.linalg.norm(f - A(r.x)) / np.linalg.norm(f)
+        assert abs(r.history[k] - true) <= 1e-9 * true + 1e-15
+        if k % 6 == 0:
+            # a restart boundary holds the cycle-start true residual of the same iterate
+            assert full.history[k] == true
+        else:
+            assert full.history[k] == r.history[k]
+    assert full.history[0] == 1.0
+
+
+def test_fgmres_equals_independent_right_preconditioned_gmres():
+    """With a fixed linear preconditioner FGMRES coincides with right-preconditioned GMRES
+    (Sec. 4.5.3): residual = min over the Krylov space K_k(K B, f), computed here from an
+    orthonormalised power basis and a dense least-squares solve."""
+    m, E, H = _hier(seed=5)
+    K0 = H.levels[0].K0
+    f = O.cantilever_load(m)
+    A = lambda v: O.apply_K(m, E, K0, v)
+    B = lambda v: O.vcycle(H, v)
+    res = O.fgmres(A, B, f, restart=30, kmax=8, tol=1e-14)
+    basis = [f / np.linalg.norm(f)]
+    for k in range(1, 9):
+        Q, _ = np.linalg.qr(np.stack(basis, axis=1))
+        W = np.stack([A(B(Q[:, i])) for i in range(k)], axis=1)
+        c, *_ = np.linalg.lstsq(W, f, rcond=None)
+        rmin = np.linalg.norm(f - W @ c) / np.linalg.norm(f)
+        assert abs(res.history[k] - rmin) <= 1e-7 * rmin
+        nxt = A(B(basis[-1]))
+        basis.append(nxt / np.linalg.norm(nxt))
+
+
+def test_fgmres_converges_to_direct_solution():
+    m, E, H = _hier(seed=1)
+    K0 = H.levels[0].K0
+    f = O.cantilever_load(m)
+    res = O.fgmres(lambda v: O.apply_K(m, E, K0, v), lambda v: O.vcycle(H, v), f,
+                   restart=30, kmax=200, tol=1e-10)
+    Kd = O.assemble_dense_free(m, E, K0)
+    x = np.zeros(m.n_dof)
+    x[m.free] = np.linalg.solve(Kd, f[m.free])
+    assert res.flag == O.CONVERGED
+    assert np.linalg.norm(res.x - x) <= 1e-6 * np.linalg.norm(x)
+    assert O.true_residual(m, E, K0, f, res.x) < 1e-9
+
+
+def test_fgmres_restart_records_true_residual_and_breakdown():
+    m, E, H = _hier(seed=7)
+    K0 = H.levels[0].K0
+    f = O.cantilever_load(m)
+    A = lambda v: O.apply_K(m, E, K0, v)
+    r = O.fgmres(A, lambda v: v, f, restart=5, kmax=5, tol=1e-14)   # one full cycle
+    r2 = O.fgmres(A, lambda v: v, f, restart=5, kmax=7, tol=1e-14)
+    true5 = np.linalg.norm(f - A(r.x)) / np.linalg.norm(f)
+    assert r2.history[5] == true5
+    # singular preconditioner: both directions map to the same z -> degenerate column
+    n = 6
+    f2 = np.zeros(n)
+    f2[0] = f2[-1] = 1.0
+    proj = lambda v: np.eye(n)[0] * (v[0] + v[-1]) / 2.0   # rank one: second z is 0
+    rb = O.fgmres(lambda v: v, proj, f2, restart=10, kmax=10, tol=1e-12)
+    assert rb.flag == O.BREAKDOWN and rb.iters == 1 and np.allclose(rb.x, np.eye(n)[0])
+    assert abs(rb.history[1] - 1 / math.sqrt(2)) < 1e-15
+    # f an eigenvector with identity preconditioner: happy breakdown = converged in 1 step
+    rc = O.fgmres(lambda v: 4.0 * v, lambda v: v, f2, restart=10, kmax=10, tol=1e-12)
+    assert rc.flag == O.CONVERGED and rc.iters == 1 and np.allclose(rc.x, f2 / 4)
+
+
+# ---------------------------------------------------------------- guard -----
+def test_true_residual_definition():
+    m, E, H = _hier(seed=1)
+    K0 = H.levels[0].K0
+    f = O.cantilever_load(m)
+    assert O.true_residual(m, E, K0, f, np.zeros(m.n_dof)) == 1.0
+    Kd = O.assemble_dense_free(m, E, K0)
+    x = np.zeros(m.n_dof)
+    x[m.free] = np.linalg.solve(Kd, f[m.free])
+    assert O.true_residual(m, E, K0, f, x) < 1e-12
+    assert O.true_residual(m, E, K0, 3.0 * f, 3.0 * x) < 1e-12
+
+
+# ---------------------------------------------------------------- policy ----
+def _read_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def test_trigger_rule_on_paper_false_keep_rows():
+    rows = _read_rows("false_keep_rows.txt")
+    assert len(rows) == 4
+    for seed, q, r50, r100, outcome in rows:
+        assert O.trigger_rule(float(r50), float(r100)) == (outcome == "escalate")
+
+
+def test_trigger_rule_boundaries():
+    for r50, r100, outcome in _read_rows("trigger_boundaries.txt"):
+        assert O.trigger_rule(float(r50), float(r100)) == (outcome == "escalate"), (r50, r100)
+
+
+def test_probe_features_early_convergence_gives_ratio_one():
+    hist = np.linspace(1.0, 1e-7, 31)
+    r50, r100 = O.probe_features(hist, 30)
+    assert r50 == r100 == hist[30]
+    hist = np.geomspace(1.0, 1e-3, 101)
+    r50, r100 = O.probe_features(hist, 100)
+    assert r50 == hist[50] and r100 == hist[100]
+
+
+class _Fake:
+    def __init__(self, etas, probe_hist):
+        self.etas, self.probe_hist, self.calls = etas, probe_hist, []
+
+    def probe(self, rm, iters):
+        h = np.asarray(self.probe_hist)
+        return O.SolveResult(np.zeros(1), h, len(h) - 1, O.MAX_ITERS, float(h[-1]))
+
+    def attempt(self, rm, kmax):
+        self.calls.append(rm)
+        return O.SolveResult(np.full(1, rm), np.ones(2), 1, O.CONVERGED, 1e-7), self.etas[rm]
+
+
+def test_guarded_policy_algorithm_1():
+    ladder = [1e-5, 1e-4, 1e-3]
+    # preserve: probe plateau low -> try rho0 first; guard rejects rho0 -> next floor
+    hist = np.geomspace(1.0, 1e-6, 101)
+    fk = _Fake({1e-6: 2e-6, 1e-5: 5e-7, 1e-4: 1e-8, 1e-3: 1e-9}, hist)
+    r = O.guarded_policy(fk.probe, fk.attempt, 1e-6, ladder)
+    assert not r.escalated and fk.calls == [1e-6, 1e-5] and r.floor_index == 1 and r.status == O.ACCEPTED
+    # escalate on r50 >= 1e-2: rho0 is skipped
+    fk = _Fake({1e-6: 1e-9, 1e-5: 2e-6, 1e-4: 1e-6, 1e-3: 1e-9}, np.full(101, 0.5))
+    r = O.guarded_policy(fk.probe, fk.attempt, 1e-6, ladder)
+    assert r.escalated and fk.calls == [1e-5, 1e-4] and r.floor_index == 2  # eta == tau accepts
+    # nothing admissible
+    fk = _Fake({1e-6: 1.0, 1e-5: 1.0, 1e-4: 1.0, 1e-3: 1.0}, np.full(101, 0.5))
+    r = O.guarded_policy(fk.probe, fk.attempt, 1e-6, ladder)
+    assert r.status == O.NO_ADMISSIBLE_FLOOR and r.floor_index == -1 and len(r.attempts) == 3
+    # full ladder and given start
+    fk = _Fake({1e-6: 1.0, 1e-5: 1e-7, 1e-4: 1e-7, 1e-3: 1e-7}, hist)
+    r = O.guarded_policy(fk.probe, fk.attempt, 1e-6, ladder, selector="full")
+    assert fk.calls == [1e-6, 1e-5] and r.floor_index == 1
+    fk = _Fake({1e-6: 1.0, 1e-5: 1.0, 1e-4: 1e-7, 1e-3: 1e-7}, hist)
+    r = O.guarded_policy(fk.probe, fk.attempt, 1e-6, ladder, selector="given", first_index=2)
+    assert fk.calls == [1e-4] and r.floor_index == 2
+
+
+def test_select_floor_end_to_end_and_compliance_decreases_with_floor():
+    m = O.Mesh(8, 4, 4)
+    rho = synth.bernoulli_density(8, 4, 4, 43, 0.35)
+    setup = O.SolverSetup(m, rho, p=3, n_levels=2)
+    f = O.cantilever_load(m)
+    r = O.select_floor(setup, f, 1e-6, [1e-5, 1e-4, 1e-3])
+    assert r.status == O.ACCEPTED and r.eta <= 1e-6
+    E = O.young_modulus(rho, r.rho_min, 3)
+    assert O.true_residual(m, E, O.element_stiffness(), f, r.u) == r.eta
+    comps = []
+    for rm in (1e-6, 1e-5, 1e-4, 1e-3):
+        Kd = O.assemble_dense_free(m, O.young_modulus(rho, rm, 3), O.element_stiffness())
+        comps.append(f[m.free] @ np.linalg.solve(Kd, f[m.free]))
+    assert all(a > b for a, b in zip(comps, comps[1:]))
+
+
+# ---------------------------------------------------------------- a12 -------
+def test_sensitivity_matches_central_differences():
+    m = O.Mesh(4, 2, 2)
+    rho = 0.2 + 0.7 * synth.uniform_density(4, 2, 2, 11)
+    f = O.cantilever_load(m)
+    K0 = O.element_stiffness()
+    rm, p = 1e-3, 3.0
+
+    def C(r):
+        Kd = O.assemble_dense_free(m, O.young_modulus(r, rm, p), K0)
+        u = np.zeros(m.n_dof)
+        u[m.free] = np.linalg.solve(Kd, f[m.free])
+        return f @ u, u
+
+    c0, u0 = C(rho)
+    assert O.compliance(f, u0) == c0
+    dc = O.sensitivity(m, rho, rm, p, K0, u0)
+    for e in (0, 5, 11):
+        h = 1e-6
+        rp, rmn = rho.copy(), rho.copy()
+        rp[e] += h
+        rmn[e] -= h
+        fd = (C(rp)[0] - C(rmn)[0]) / (2 * h)
+        assert abs(fd - dc[e]) < 1e-5 * abs(dc[e])
+
+
+def test_filter_and_oc_update():
+    m = O.Mesh(6, 4, 3)
+    Hf = O.filter_weights(m, 1.5)
+    assert abs(Hf - Hf.T).max() < 1e-15
+    assert np.allclose(O.density_filter(Hf, np.full(m.n_elem, 0.4)), 0.4)
+    # r_min = 1.5: the 3x3x3 neighbourhood minus the 8 corners (dist sqrt(3) > 1.5)
+    centre = 2 + 6 * (1 + 4 * 1)
+    assert Hf[centre].nnz == 19
+    x = np.full(m.n_elem, 0.3)
+    dc = -synth.uniform_density(6, 4, 3, 1) - 0.1
+    xn = O.oc_update(x, dc, np.ones(m.n_elem), 0.3, move=0.2)
+    assert abs(xn.mean() - 0.3) < 1e-3 and np.all(np.abs(xn - x) <= 0.2 + 1e-15)
+    g = synth.random_vector(m.n_elem, 2)
+    y = synth.random_vector(m.n_elem, 3)
+    # adjoint of the filter: <H y, g> = <y, H^T g>
+    assert abs(O.density_filter(Hf, y) @ g - y @ O.density_filter_adjoint(Hf, g)) < 1e-12
