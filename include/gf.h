@@ -1,0 +1,227 @@
+/*
+ * gf.h -- C ABI of the B300 guarded floor-selection state solver.
+ *
+ * The operation (arXiv 2607.26382): for a frozen density field rho_hat on a
+ * structured nx*ny*nz grid of cubic 8-node hexahedra, solve the linear-elastic
+ * state equation K(rho_min) u = f (Eq. frozen_operator, with the floor scaling
+ * E_e = rho_min + (1 - rho_min) rho_hat_e^p of Eq. floor_scaling) by
+ * right-preconditioned restarted FGMRES with a matrix-free geometric-multigrid
+ * V-cycle (Table solver-config), accept a solution only if the recomputed FP64
+ * true residual ||f - K u|| / ||f|| <= tau (Eq. relative_residual, Table
+ * residual-semantics), and choose the floor with the probe -> ladder -> guard
+ * policy of Algorithm 1 with the rule of Eq. (trigger).
+ *
+ * Conventions shared by every call
+ *  - Node n(i,j,k) = i + (nx+1)*(j + (ny+1)*k); DOF 3n+c (x,y,z interleaved);
+ *    element e = ex + nx*(ey + ny*ez). Vectors of length n_dof, element arrays of
+ *    length n_elem.
+ *  - Cantilever support: every DOF of the nodes on the x = 0 face is fixed. The
+ *    operator acts on free DOFs; fixed entries of inputs are ignored and fixed
+ *    entries of outputs are written as 0.
+ *  - Unless a pointer is documented as "host", it is a DEVICE pointer on the
+ *    device that was current at gf_create_grid, owned by the caller, and must
+ *    stay valid until the call's work on the grid's stream has completed.
+ *  - Every call is enqueued on the stream given to gf_create_grid. Calls that
+ *    return a host value (gf_true_residual, gf_solve, gf_select_floor) block
+ *    until that value is known. A grid is not thread-safe.
+ *  - Every call returns GF_OK (0) or a negative GF_ERR_* code and never throws;
+ *    gf_last_error() gives a message for the calling thread. Solver outcomes
+ *    (not converged, no admissible floor) are NOT errors: they are reported in
+ *    the info structs.
+ */
+#ifndef GF_H
+#define GF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GF_OK              0
+#define GF_ERR_ARG        -1   /* bad argument (size, null pointer, unsupported grid) */
+#define GF_ERR_OOM        -2   /* device allocation failed */
+#define GF_ERR_CUDA       -3   /* a CUDA runtime call failed */
+#define GF_ERR_NONFINITE  -4   /* NaN/Inf (or out-of-range density) in an input */
+#define GF_ERR_TIMEOUT    -5   /* a bounded device wait gave up */
+#define GF_ERR_STATE      -6   /* call order: density or floor not set yet */
+
+/* precision of the V-cycle (Krylov vectors, outer K*u and guard are always FP64) */
+#define GF_FP64   0   /* FP64 everywhere */
+#define GF_MIXED  1   /* FP32 smoothers / transfers / level K*u with BF16-stored densities;
+                         coarsest solve FP64 */
+
+/* FGMRES stop flags (gf_solve_info.flag) */
+#define GF_FLAG_CONVERGED  0   /* recorded residual (projected or cycle-start true) <= tol */
+#define GF_FLAG_MAX_ITERS  1   /* budget kmax reached */
+#define GF_FLAG_BREAKDOWN  2   /* h_{j+1,j} ~ 0 without convergence */
+
+/* policy outcome (gf_select_info.status), Algorithm 1 */
+#define GF_ACCEPTED            0
+#define GF_NO_ADMISSIBLE_FLOOR 1
+
+/* first-floor selectors */
+#define GF_SEL_RULE   0   /* probe at rho0, Eq. (trigger) picks (rho0, ladder) or ladder */
+#define GF_SEL_FULL   1   /* no probe: try rho0 then every ladder floor in order */
+#define GF_SEL_GIVEN  2   /* no probe: start at first_index of (rho0, ladder...) */
+
+#define GF_MAX_LADDER 8
+
+typedef struct gf_grid gf_grid;
+
+typedef struct {
+    int    restart;    /* FGMRES restart length m (>= 1, <= 64) */
+    int    kmax;       /* iteration budget (Arnoldi steps over all cycles) */
+    double tol;        /* stop when the recorded relative residual <= tol */
+    int    prec;       /* GF_FP64 or GF_MIXED */
+    int    nu1, nu2;   /* pre/post node-block Jacobi sweeps (>= 1) */
+    double omega;      /* Jacobi damping */
+    double* history;   /* host, optional: receives history[0..iters] (length >= kmax+1) */
+} gf_solve_opts;
+
+typedef struct {
+    int    iters;          /* Arnoldi steps taken */
+    int    flag;           /* GF_FLAG_* */
+    double stop_estimate;  /* last recorded history value */
+} gf_solve_info;
+
+typedef struct {
+    double rho0;                       /* original floor */
+    double ladder[GF_MAX_LADDER];      /* escalation ladder, increasing */
+    int    n_ladder;
+    double tau;                        /* acceptance tolerance on the true residual */
+    int    kmax;                       /* budget of each selected solve */
+    int    probe_iters;                /* probe budget (100 in the paper) */
+    double r50_escalate;               /* Eq. (trigger): 1e-2 */
+    double r100_stall;                 /* 1e-4 */
+    double plateau_ratio;              /* 0.6 */
+    int    checkpoint_a, checkpoint_b; /* 50, 100 */
+    int    selector;                   /* GF_SEL_* */
+    int    first_index;                /* for GF_SEL_GIVEN */
+    gf_solve_opts solve;               /* restart, prec, smoother (kmax/tol/history ignored) */
+} gf_policy;
+
+typedef struct {
+    double rho_min;
+    int    iters;
+    int    flag;
+    double stop_estimate;
+    double eta;        /* recomputed FP64 true residual */
+    int    accepted;
+} gf_attempt;
+
+typedef struct {
+    int    status;          /* GF_ACCEPTED or GF_NO_ADMISSIBLE_FLOOR */
+    int    floor_index;     /* index into (rho0, ladder...), -1 if none */
+    double rho_min;
+    double eta;
+    double r50, r100;       /* probe features (NaN when no probe ran) */
+    int    escalated;
+    int    probe_iters_run;
+    int    n_attempts;
+    gf_attempt attempts[GF_MAX_LADDER + 1];
+} gf_select_info;
+
+typedef struct {
+    long long kernel_launches;   /* kernels this library launched on the grid */
+    long long apply_K_fp64;      /* fine-level FP64 operator applications */
+    long long vcycles;           /* preconditioner applications */
+} gf_stats;
+
+/* ---- lifetime ---------------------------------------------------------------- */
+
+/* Create a grid of nx*ny*nz cubic elements of edge h, Young's modulus E0 (solid),
+ * Poisson ratio nu, and a `levels`-level hierarchy (level l has (nx,ny,nz)/2^l
+ * elements of edge h*2^l). Requires nx, ny, nz divisible by 2^(levels-1), ny and
+ * nz even, 1 <= levels <= 8, and the coarsest level at most 6144 DOFs. `stream` is
+ * a cudaStream_t (NULL = legacy default stream). Allocates all level workspace.
+ * Sec. 3.1 (Discretization), Table solver-config. */
+int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int levels,
+                   void* stream, gf_grid** out);
+int gf_destroy_grid(gf_grid* g);
+
+/* Sizes: any pointer may be NULL. */
+int gf_grid_sizes(const gf_grid* g, int* n_dof, int* n_elem, int* n_nodes, int* levels);
+
+/* ---- state ------------------------------------------------------------------- */
+
+/* Store the floor-independent density rho_hat (n_elem doubles in [0,1], device)
+ * and the SIMP exponent p; keeps an FP64 and a BF16 copy. GF_ERR_NONFINITE if an
+ * entry is NaN/Inf or outside [0,1]. Invalidates the floor. Sec. 3.2. */
+int gf_set_density(gf_grid* g, const double* rho_hat, double p);
+
+/* Set the floor: E_e = rho_min + (1 - rho_min) rho_hat_e^p (Eq. floor_scaling, E0
+ * scales it), coarse moduli = mean of the 8 children, and the FP64 inverse of the
+ * coarsest operator. 0 < rho_min <= 1. */
+int gf_set_floor(gf_grid* g, double rho_min);
+
+/* f = unit point load in -z at the node (nx, ny/2, nz/2) (n_dof doubles, device);
+ * the cantilever of Table geometries. */
+int gf_cantilever_load(gf_grid* g, double* f);
+
+/* mask[d] = 1 if DOF d is free, 0 if fixed (n_dof bytes, device). */
+int gf_free_mask(gf_grid* g, uint8_t* mask);
+
+/* ---- operator and preconditioner -------------------------------------------- */
+
+/* y = K(rho_min) u on free DOFs, FP64 (Eq. frozen_operator), matrix-free. u, y:
+ * n_dof doubles, must not alias. */
+int gf_apply_K(gf_grid* g, const double* u, double* y);
+
+/* Same operator in FP32 with the moduli computed from the BF16 density copy (the
+ * V-cycle's fine-level operator in GF_MIXED). u, y: n_dof floats. */
+int gf_apply_K_f32(gf_grid* g, const float* u, float* y);
+
+/* z = B v: one V-cycle (nu1 pre / nu2 post node-block Jacobi sweeps with damping
+ * omega, restriction = transpose of trilinear prolongation, FP64 coarsest solve)
+ * in precision `prec`. v, z: n_dof doubles; fixed entries of v are ignored. */
+int gf_vcycle(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2, double omega);
+
+/* ---- solve, guard, policy ----------------------------------------------------- */
+
+/* Right-preconditioned restarted FGMRES(m) with classical Gram-Schmidt plus one
+ * re-orthogonalisation and Givens rotations, preconditioned by gf_vcycle. u holds
+ * the initial guess on entry (fixed entries ignored) and the solution on exit.
+ * History entry k is the cycle-start true residual at a cycle start and the
+ * Givens-projected estimate otherwise (Table residual-semantics). */
+int gf_solve(gf_grid* g, const double* f, double* u, const gf_solve_opts* opts,
+             gf_solve_info* info);
+
+/* *eta (host) = ||M(f - K u)||_2 / ||M f||_2 in FP64: the acceptance guard, one
+ * operator application (Eq. relative_residual, Table residual-semantics). */
+int gf_true_residual(gf_grid* g, const double* f, const double* u, double* eta);
+
+/* Algorithm 1: probe at rho0 for probe_iters, candidate list from Eq. (trigger)
+ * (or the selector), an independent solve from u = 0 at each candidate floor,
+ * accept the first with eta <= tau. On GF_ACCEPTED u holds the accepted solution
+ * and the grid's floor is the accepted floor; otherwise u holds the last attempt. */
+int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol,
+                    gf_select_info* info);
+
+/* ---- host-only policy logic (no device work; usable without a GPU) ----------- */
+
+/* Defaults of Table solver-config / Eq. (trigger) with the given rho0 and ladder. */
+void gf_policy_defaults(gf_policy* pol);
+/* Eq. (trigger): 1 = escalate, 0 = preserve. */
+int gf_trigger_rule(double r50, double r100, const gf_policy* pol);
+/* r50 = history[min(a, k_stop)], r100 = history[min(b, k_stop)] (Sec. 3.4). */
+int gf_probe_features(const double* history, int k_stop, const gf_policy* pol,
+                      double* r50, double* r100);
+
+/* ---- sensitivity (the optimisation loop's consumer of the solve) ------------- */
+
+/* dc_e = -p (1 - rho_min) rho_hat_e^(p-1) u_e^T K0 u_e (Sec. 3.1), FP64, at the
+ * grid's current floor. u: n_dof, dc: n_elem doubles. */
+int gf_sensitivity(gf_grid* g, const double* u, double* dc);
+
+/* ---- diagnostics -------------------------------------------------------------- */
+int gf_get_stats(const gf_grid* g, gf_stats* s);
+int gf_reset_stats(gf_grid* g);
+const char* gf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GF_H */

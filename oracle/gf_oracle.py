@@ -562,6 +562,7 @@ class SelectResult:
     r100: float
     escalated: bool
     attempts: list
+    probe_iters_run: int = 0
 
 
 @dataclass
@@ -606,8 +607,10 @@ def guarded_policy(probe_fn, attempt_fn, rho0: float, ladder, tau: float = 1e-6,
     floors = [rho0] + list(ladder)
     r50 = r100 = float("nan")
     escalated = False
+    probe_k = 0
     if selector == "rule":
         probe = probe_fn(rho0, probe_iters)
+        probe_k = probe.iters
         r50, r100 = probe_features(probe.history, probe.iters, th)
         escalated = trigger_rule(r50, r100, th)
         cand = candidate_floors(escalated, rho0, ladder)
@@ -626,9 +629,10 @@ def guarded_policy(probe_fn, attempt_fn, rho0: float, ladder, tau: float = 1e-6,
         ok = eta <= tau
         attempts.append(Attempt(rm, res.iters, res.flag, res.stop_estimate, eta, ok))
         if ok:
-            return SelectResult(ACCEPTED, start + idx, rm, res.x, eta, r50, r100, escalated, attempts)
+            return SelectResult(ACCEPTED, start + idx, rm, res.x, eta, r50, r100, escalated, attempts,
+                                probe_k)
     return SelectResult(NO_ADMISSIBLE_FLOOR, -1, float("nan"), None, float("nan"), r50, r100,
-                        escalated, attempts)
+                        escalated, attempts, probe_k)
 
 
 def select_floor(setup: SolverSetup, f: np.ndarray, rho0: float, ladder, tau: float = 1e-6,

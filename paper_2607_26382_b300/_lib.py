@@ -1,0 +1,294 @@
+"""ctypes binding of the C ABI in include/gf.h (argument marshalling only).
+
+Every computation runs in libgf_b300.so; this module checks tensor shapes, dtypes
+and devices, passes raw pointers and the current CUDA stream, and converts the
+info structs. It never computes anything itself and has no CPU fallback: if the
+shared library is missing, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_longlong, c_uint8, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgf_b300.so")
+
+GF_OK = 0
+GF_FP64, GF_MIXED = 0, 1
+GF_FLAG_CONVERGED, GF_FLAG_MAX_ITERS, GF_FLAG_BREAKDOWN = 0, 1, 2
+GF_ACCEPTED, GF_NO_ADMISSIBLE_FLOOR = 0, 1
+GF_SEL_RULE, GF_SEL_FULL, GF_SEL_GIVEN = 0, 1, 2
+GF_MAX_LADDER = 8
+
+ERRORS = {-1: "GF_ERR_ARG", -2: "GF_ERR_OOM", -3: "GF_ERR_CUDA", -4: "GF_ERR_NONFINITE",
+          -5: "GF_ERR_TIMEOUT", -6: "GF_ERR_STATE"}
+
+EXPORTED = [
+    "gf_create_grid", "gf_destroy_grid", "gf_grid_sizes", "gf_set_density", "gf_set_floor",
+    "gf_cantilever_load", "gf_free_mask", "gf_apply_K", "gf_apply_K_f32", "gf_vcycle", "gf_solve",
+    "gf_true_residual", "gf_select_floor", "gf_policy_defaults", "gf_trigger_rule",
+    "gf_probe_features", "gf_sensitivity", "gf_get_stats", "gf_reset_stats", "gf_last_error",
+]
+
+
+class GFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("restart", c_int), ("kmax", c_int), ("tol", c_double), ("prec", c_int),
+                ("nu1", c_int), ("nu2", c_int), ("omega", c_double), ("history", POINTER(c_double))]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("flag", c_int), ("stop_estimate", c_double)]
+
+
+class Policy(ctypes.Structure):
+    _fields_ = [("rho0", c_double), ("ladder", c_double * GF_MAX_LADDER), ("n_ladder", c_int),
+                ("tau", c_double), ("kmax", c_int), ("probe_iters", c_int),
+                ("r50_escalate", c_double), ("r100_stall", c_double), ("plateau_ratio", c_double),
+                ("checkpoint_a", c_int), ("checkpoint_b", c_int), ("selector", c_int),
+                ("first_index", c_int), ("solve", SolveOpts)]
+
+
+class Attempt(ctypes.Structure):
+    _fields_ = [("rho_min", c_double), ("iters", c_int), ("flag", c_int),
+                ("stop_estimate", c_double), ("eta", c_double), ("accepted", c_int)]
+
+
+class SelectInfo(ctypes.Structure):
+    _fields_ = [("status", c_int), ("floor_index", c_int), ("rho_min", c_double), ("eta", c_double),
+                ("r50", c_double), ("r100", c_double), ("escalated", c_int), ("probe_iters_run", c_int),
+                ("n_attempts", c_int), ("attempts", Attempt * (GF_MAX_LADDER + 1))]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", c_longlong), ("apply_K_fp64", c_longlong), ("vcycles", c_longlong)]
+
+
+_LIB = None
+
+
+def lib():
+    """Load libgf_b300.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library missing: {LIB_PATH} (run python -m paper_2607_26382_b300.build)")
+    L = ctypes.CDLL(LIB_PATH)
+    P = c_void_p
+    sig = {
+        "gf_create_grid": [c_int, c_int, c_int, c_double, c_double, c_double, c_int, P, POINTER(P)],
+        "gf_destroy_grid": [P],
+        "gf_grid_sizes": [P, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)],
+        "gf_set_density": [P, P, c_double],
+        "gf_set_floor": [P, c_double],
+        "gf_cantilever_load": [P, P],
+        "gf_free_mask": [P, P],
+        "gf_apply_K": [P, P, P],
+        "gf_apply_K_f32": [P, P, P],
+        "gf_vcycle": [P, P, P, c_int, c_int, c_int, c_double],
+        "gf_solve": [P, P, P, POINTER(SolveOpts), POINTER(SolveInfo)],
+        "gf_true_residual": [P, P, P, POINTER(c_double)],
+        "gf_select_floor": [P, P, P, POINTER(Policy), POINTER(SelectInfo)],
+        "gf_trigger_rule": [c_double, c_double, POINTER(Policy)],
+        "gf_probe_features": [POINTER(c_double), c_int, POINTER(Policy), POINTER(c_double), POINTER(c_double)],
+        "gf_sensitivity": [P, P, P],
+        "gf_get_stats": [P, POINTER(Stats)],
+        "gf_reset_stats": [P],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = c_int
+    L.gf_policy_defaults.argtypes = [POINTER(Policy)]
+    L.gf_policy_defaults.restype = None
+    L.gf_last_error.argtypes = []
+    L.gf_last_error.restype = c_char_p
+    _LIB = L
+    return L
+
+
+def _check(code):
+    if code < 0:
+        raise GFError(code, lib().gf_last_error().decode())
+    return code
+
+
+# ------------------------------------------------------------- host-only logic --
+def policy_defaults(**kw) -> Policy:
+    """gf_policy_defaults, then overrides: ladder=[...], solve_* fields, or any Policy field."""
+    p = Policy()
+    lib().gf_policy_defaults(ctypes.byref(p))
+    ladder = kw.pop("ladder", None)
+    if ladder is not None:
+        if len(ladder) > GF_MAX_LADDER:
+            raise ValueError("ladder too long")
+        for i, v in enumerate(ladder):
+            p.ladder[i] = float(v)
+        p.n_ladder = len(ladder)
+    for k, v in kw.items():
+        if k.startswith("solve_"):
+            setattr(p.solve, k[6:], v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def trigger_rule(r50: float, r100: float, policy: Policy | None = None) -> bool:
+    p = policy or policy_defaults()
+    return bool(_check(lib().gf_trigger_rule(float(r50), float(r100), ctypes.byref(p))))
+
+
+def probe_features(history, k_stop: int, policy: Policy | None = None):
+    p = policy or policy_defaults()
+    arr = (c_double * len(history))(*[float(h) for h in history])
+    r50, r100 = c_double(), c_double()
+    _check(lib().gf_probe_features(arr, int(k_stop), ctypes.byref(p), ctypes.byref(r50), ctypes.byref(r100)))
+    return r50.value, r100.value
+
+
+# ------------------------------------------------------------- device objects ---
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t, dtype, n, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be contiguous with {n} elements")
+    return c_void_p(t.data_ptr())
+
+
+class Grid:
+    """A structured hex8 grid with its level hierarchy and solver workspace (gf_grid)."""
+
+    def __init__(self, nx, ny, nz, h=1.0, E0=1.0, nu=0.3, levels=3, stream=None):
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = c_void_p()
+        _check(lib().gf_create_grid(int(nx), int(ny), int(nz), float(h), float(E0), float(nu), int(levels),
+                                    c_void_p(stream.cuda_stream), ctypes.byref(handle)))
+        self._h = handle
+        nd, ne, nn, nl = c_int(), c_int(), c_int(), c_int()
+        _check(lib().gf_grid_sizes(handle, ctypes.byref(nd), ctypes.byref(ne), ctypes.byref(nn), ctypes.byref(nl)))
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.n_dof, self.n_elem, self.n_nodes, self.levels = nd.value, ne.value, nn.value, nl.value
+        self.rho_min = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gf_destroy_grid(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # state
+    def set_density(self, rho_hat, p=3.0):
+        _check(lib().gf_set_density(self._h, _ptr(rho_hat, _torch().float64, self.n_elem, "rho_hat"), float(p)))
+
+    def set_floor(self, rho_min):
+        _check(lib().gf_set_floor(self._h, float(rho_min)))
+        self.rho_min = float(rho_min)
+
+    def cantilever_load(self, f):
+        _check(lib().gf_cantilever_load(self._h, _ptr(f, _torch().float64, self.n_dof, "f")))
+        return f
+
+    def free_mask(self, mask):
+        _check(lib().gf_free_mask(self._h, _ptr(mask, _torch().uint8, self.n_dof, "mask")))
+        return mask
+
+    # operator / preconditioner
+    def apply_K(self, u, y):
+        t = _torch().float64
+        _check(lib().gf_apply_K(self._h, _ptr(u, t, self.n_dof, "u"), _ptr(y, t, self.n_dof, "y")))
+        return y
+
+    def apply_K_f32(self, u, y):
+        t = _torch().float32
+        _check(lib().gf_apply_K_f32(self._h, _ptr(u, t, self.n_dof, "u"), _ptr(y, t, self.n_dof, "y")))
+        return y
+
+    def vcycle(self, v, z, prec=GF_FP64, nu1=2, nu2=2, omega=0.6):
+        t = _torch().float64
+        _check(lib().gf_vcycle(self._h, _ptr(v, t, self.n_dof, "v"), _ptr(z, t, self.n_dof, "z"), int(prec),
+                               int(nu1), int(nu2), float(omega)))
+        return z
+
+    # solve / guard / policy
+    def solve(self, f, u, restart=30, kmax=200, tol=1e-6, prec=GF_FP64, nu1=2, nu2=2, omega=0.6,
+              want_history=True):
+        t = _torch().float64
+        hist = (c_double * (kmax + 1))() if want_history else None
+        o = SolveOpts(int(restart), int(kmax), float(tol), int(prec), int(nu1), int(nu2), float(omega),
+                      ctypes.cast(hist, POINTER(c_double)) if hist is not None else None)
+        info = SolveInfo()
+        _check(lib().gf_solve(self._h, _ptr(f, t, self.n_dof, "f"), _ptr(u, t, self.n_dof, "u"),
+                              ctypes.byref(o), ctypes.byref(info)))
+        out = {"iters": info.iters, "flag": info.flag, "stop_estimate": info.stop_estimate}
+        if hist is not None:
+            out["history"] = [hist[i] for i in range(info.iters + 1)]
+        return out
+
+    def true_residual(self, f, u):
+        t = _torch().float64
+        eta = c_double()
+        _check(lib().gf_true_residual(self._h, _ptr(f, t, self.n_dof, "f"), _ptr(u, t, self.n_dof, "u"),
+                                      ctypes.byref(eta)))
+        return eta.value
+
+    def select_floor(self, f, u, policy: Policy):
+        t = _torch().float64
+        info = SelectInfo()
+        _check(lib().gf_select_floor(self._h, _ptr(f, t, self.n_dof, "f"), _ptr(u, t, self.n_dof, "u"),
+                                     ctypes.byref(policy), ctypes.byref(info)))
+        atts = [dict(rho_min=a.rho_min, iters=a.iters, flag=a.flag, stop_estimate=a.stop_estimate,
+                     eta=a.eta, accepted=bool(a.accepted)) for a in info.attempts[:info.n_attempts]]
+        if info.status == GF_ACCEPTED:
+            self.rho_min = info.rho_min
+        return dict(status=info.status, floor_index=info.floor_index, rho_min=info.rho_min, eta=info.eta,
+                    r50=info.r50, r100=info.r100, escalated=bool(info.escalated),
+                    probe_iters_run=info.probe_iters_run, attempts=atts)
+
+    def sensitivity(self, u, dc):
+        t = _torch().float64
+        _check(lib().gf_sensitivity(self._h, _ptr(u, t, self.n_dof, "u"), _ptr(dc, t, self.n_elem, "dc")))
+        return dc
+
+    def stats(self):
+        s = Stats()
+        _check(lib().gf_get_stats(self._h, ctypes.byref(s)))
+        return {"kernel_launches": s.kernel_launches, "apply_K_fp64": s.apply_K_fp64, "vcycles": s.vcycles}
+
+    def reset_stats(self):
+        _check(lib().gf_reset_stats(self._h))
+
+
+def create_grid(nx, ny, nz, h=1.0, E0=1.0, nu=0.3, levels=3, stream=None) -> Grid:
+    return Grid(nx, ny, nz, h, E0, nu, levels, stream)

@@ -1,0 +1,835 @@
+// C ABI of the guarded floor-selection state solver (see include/gf.h).
+//
+// Host side: the grid handle, hierarchy set-up, the V-cycle schedule, the FGMRES
+// driver (device-resident Arnoldi/Givens state, host polls a mapped stop flag with
+// at most two steps in flight) and Algorithm 1 of arXiv 2607.26382.
+#include "../../include/gf.h"
+#include "stencil.cuh"
+#include "krylov.cuh"
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+#include <utility>
+
+namespace {
+
+thread_local std::string g_err;
+
+int set_err(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return set_err(e_ == cudaErrorMemoryAllocation ? GF_ERR_OOM : GF_ERR_CUDA,  \
+                           std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+#define RET(call)                      \
+    do {                               \
+        int r_ = (call);               \
+        if (r_ != GF_OK) return r_;    \
+    } while (0)
+
+inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+struct Level {
+    int nx, ny, nz;
+    double h;
+    long long nodes, ndof, nel;
+    double* E64 = nullptr;
+    float* E32 = nullptr;
+    double *b64 = nullptr, *x64 = nullptr, *t64 = nullptr, *r64 = nullptr;
+    float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr, *r32 = nullptr;
+    gf::GridDims dims() const { return gf::GridDims{nx, ny, nz}; }
+};
+
+// Element stiffness of the unit cube (E = 1 scaled by E0 by the caller) from the
+// exact 1D integrals of linear hats: S_ab[i,j] = int d_a N_i d_b N_j factorises
+// into m = int phi phi, k = int phi' phi', c = int phi' phi per axis, and
+// K[3i+al][3j+be] = lam S_{al be} + mu S_{be al} + mu delta_{al be} sum_g S_gg.
+void build_k0(double E0, double nu, double* K)
+{
+    const double lam = E0 * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    const double mu = E0 / (2.0 * (1.0 + nu));
+    const double m1[2][2] = {{2.0 / 6.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 6.0}};
+    const double k1[2][2] = {{1.0, -1.0}, {-1.0, 1.0}};
+    const double c1[2][2] = {{-0.5, -0.5}, {0.5, 0.5}};
+    int off[8][3];
+    for (int z = 0; z < 2; ++z)
+        for (int y = 0; y < 2; ++y)
+            for (int x = 0; x < 2; ++x) {
+                const int a = gf::local_index(x, y, z);
+                off[a][0] = x;
+                off[a][1] = y;
+                off[a][2] = z;
+            }
+    auto S = [&](int a, int b, int i, int j) {
+        double v = 1.0;
+        for (int d = 0; d < 3; ++d) {
+            const int p = off[i][d], q = off[j][d];
+            if (d == a && d == b) v *= k1[p][q];
+            else if (d == a) v *= c1[p][q];
+            else if (d == b) v *= c1[q][p];
+            else v *= m1[p][q];
+        }
+        return v;
+    };
+    for (int i = 0; i < 8; ++i)
+        for (int j = 0; j < 8; ++j)
+            for (int al = 0; al < 3; ++al)
+                for (int be = 0; be < 3; ++be) {
+                    double v = lam * S(al, be, i, j) + mu * S(be, al, i, j);
+                    if (al == be) v += mu * (S(0, 0, i, j) + S(1, 1, i, j) + S(2, 2, i, j));
+                    K[(3 * i + al) * 24 + 3 * j + be] = v;
+                }
+}
+
+}  // namespace
+
+struct gf_grid {
+    int nx, ny, nz, L;
+    double h, E0, nu;
+    cudaStream_t stream;
+    int device, sms;
+    long long nodes, ndof, nel;
+    std::vector<Level> lv;
+    gf::K0Param<double> K0d;
+    gf::K0Param<float> K0f;
+    double* rho64 = nullptr;
+    __nv_bfloat16* rho16 = nullptr;
+    double p = 3.0;
+    bool has_density = false, has_floor = false;
+    double rho_min = 0.0;
+    double* Ainv = nullptr;
+    int nc = 0;
+    double *gjcol = nullptr, *gjrow = nullptr;
+    int* dflag = nullptr;
+    // Krylov workspace
+    int m_alloc = 0;
+    double *V = nullptr, *Z = nullptr, *partial = nullptr, *work = nullptr, *xsave = nullptr;
+    gf::KState* st = nullptr;
+    gf::KState* gst = nullptr;   // guard scratch
+    double* hist = nullptr;
+    int hist_cap = 0;
+    int* host_status = nullptr;       // mapped pinned
+    int* host_status_dev = nullptr;
+    int nbr = 0;                      // blocks for reductions
+    cudaEvent_t ev[3];
+    gf_stats stats{};
+};
+
+namespace {
+// Launch a kernel on the grid's stream, count it, and report launch errors.
+template <typename... KArgs, typename... Args>
+int launch(gf_grid* g, dim3 grid, dim3 block, void (*kern)(KArgs...), Args... args)
+{
+    kern<<<grid, block, 0, g->stream>>>(args...);
+    g->stats.kernel_launches++;
+    CK(cudaGetLastError());
+    return GF_OK;
+}
+}  // namespace
+
+#define LAUNCH(g, grid, block, kern, ...) RET(launch((g), dim3(grid), dim3(block), kern, __VA_ARGS__))
+
+namespace {
+
+int check_grid(const gf_grid* g)
+{
+    if (!g) return set_err(GF_ERR_ARG, "null grid");
+    return GF_OK;
+}
+
+int set_device(const gf_grid* g)
+{
+    CK(cudaSetDevice(g->device));
+    return GF_OK;
+}
+
+// ------------------------------------------------------------------ stencils --
+template <typename T, typename ET, int MODE>
+int stencil(gf_grid* g, int l, const T* x, const T* b, T* out, const ET* E, const gf::K0Param<T>& K0,
+            T omega, const int* halt)
+{
+    const Level& L = g->lv[l];
+    LAUNCH(g, nblk(L.nodes), 256, (gf::node_stencil_kernel<T, ET, MODE>), x, b, out, E, L.dims(), K0, omega,
+           halt);
+    return GF_OK;
+}
+
+template <typename T>
+const gf::K0Param<T>& k0(const gf_grid* g);
+template <>
+const gf::K0Param<double>& k0<double>(const gf_grid* g) { return g->K0d; }
+template <>
+const gf::K0Param<float>& k0<float>(const gf_grid* g) { return g->K0f; }
+
+template <typename T>
+struct LvBuf;
+template <>
+struct LvBuf<double> {
+    static double* b(Level& L) { return L.b64; }
+    static double* x(Level& L) { return L.x64; }
+    static double* t(Level& L) { return L.t64; }
+    static double* r(Level& L) { return L.r64; }
+    static const double* E(Level& L) { return L.E64; }
+};
+template <>
+struct LvBuf<float> {
+    static float* b(Level& L) { return L.b32; }
+    static float* x(Level& L) { return L.x32; }
+    static float* t(Level& L) { return L.t32; }
+    static float* r(Level& L) { return L.r32; }
+    static const float* E(Level& L) { return L.E32; }
+};
+
+// One V-cycle z = B v in precision T (Table solver-config: 2:1 trilinear transfer,
+// damped node-block Jacobi smoothing, coarsest solve by the FP64 dense inverse).
+template <typename T>
+int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omega, const int* halt)
+{
+    using B = LvBuf<T>;
+    const int L = g->L;
+    const int NX0 = g->nx + 1;
+    g->stats.vcycles++;
+    if (L == 1) {
+        double* bm = g->lv[0].b64;
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, double>), v, bm, g->ndof, NX0, halt);
+        LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<double, double>), g->Ainv, (const double*)bm, z,
+               g->nc, halt);
+        return GF_OK;
+    }
+    std::vector<T*> cur(L);
+    // level-0 right-hand side
+    const T* b0;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        b0 = reinterpret_cast<const T*>(v);
+    } else {
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, T>), v, B::b(g->lv[0]), g->ndof, NX0, halt);
+        b0 = B::b(g->lv[0]);
+    }
+    for (int l = 0; l < L - 1; ++l) {
+        Level& lev = g->lv[l];
+        const T* b = (l == 0) ? b0 : B::b(lev);
+        T* x = B::x(lev);
+        T* t = B::t(lev);
+        LAUNCH(g, nblk(lev.nodes), 256, (gf::first_sweep_kernel<T, T, T>), b, x, B::E(lev), lev.dims(), k0<T>(g),
+               omega, halt);
+        for (int s = 1; s < nu1; ++s) {
+            RET((stencil<T, T, gf::ST_SWEEP>(g, l, x, b, t, B::E(lev), k0<T>(g), omega, halt)));
+            std::swap(x, t);
+        }
+        cur[l] = x;
+        RET((stencil<T, T, gf::ST_RESID>(g, l, x, b, B::r(lev), B::E(lev), k0<T>(g), omega, halt)));
+        Level& c = g->lv[l + 1];
+        LAUNCH(g, nblk(c.nodes), 256, gf::restrict_kernel<T>, B::r(lev), B::b(c), c.dims(), halt);
+    }
+    {
+        Level& c = g->lv[L - 1];
+        LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<T, T>), g->Ainv, B::b(c), B::x(c), g->nc, halt);
+        cur[L - 1] = B::x(c);
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        Level& lev = g->lv[l];
+        const T* b = (l == 0) ? b0 : B::b(lev);
+        T* x = cur[l];
+        T* t = (x == B::x(lev)) ? B::t(lev) : B::x(lev);
+        LAUNCH(g, nblk(lev.nodes), 256, (gf::prolong_add_kernel<T, T>), x, cur[l + 1], lev.dims(), halt);
+        for (int s = 0; s < nu2; ++s) {
+            T* out = t;
+            const bool last = (l == 0 && s == nu2 - 1);
+            if constexpr (sizeof(T) == sizeof(double)) {
+                if (last) out = reinterpret_cast<T*>(z);
+            }
+            RET((stencil<T, T, gf::ST_SWEEP>(g, l, x, b, out, B::E(lev), k0<T>(g), omega, halt)));
+            if (last && sizeof(T) == sizeof(double)) {
+                x = out;
+                break;
+            }
+            std::swap(x, t);
+        }
+        cur[l] = x;
+    }
+    if constexpr (sizeof(T) != sizeof(double))
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<T, double>), (const T*)cur[0], z, g->ndof, NX0, halt);
+    return GF_OK;
+}
+
+int vcycle_dispatch(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2, double omega,
+                    const int* halt)
+{
+    if (prec == GF_MIXED) return vcycle_impl<float>(g, v, z, nu1, nu2, (float)omega, halt);
+    return vcycle_impl<double>(g, v, z, nu1, nu2, omega, halt);
+}
+
+int applyK64(gf_grid* g, const double* u, double* y, const int* halt)
+{
+    g->stats.apply_K_fp64++;
+    return stencil<double, double, gf::ST_APPLY>(g, 0, u, nullptr, y, g->lv[0].E64, g->K0d, 0.0, halt);
+}
+
+// ------------------------------------------------------------------ set-up ----
+int alloc(void** p, size_t bytes)
+{
+    CK(cudaMalloc(p, bytes));
+    return GF_OK;
+}
+
+template <typename T>
+int allocT(T** p, size_t n)
+{
+    return alloc(reinterpret_cast<void**>(p), n * sizeof(T));
+}
+
+int build_coarse_inverse(gf_grid* g)
+{
+    Level& c = g->lv[g->L - 1];
+    const long long n = g->nc;
+    CK(cudaMemsetAsync(g->Ainv, 0, sizeof(double) * n * n, g->stream));
+    gf::K0Param<double> K = g->K0d;   // the level's E64 already carries h
+    LAUNCH(g, nblk(c.nel * 576), 256, gf::coarse_assemble_kernel, c.E64, g->Ainv, c.dims(), K);
+    LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, g->Ainv, c.dims());
+    for (int k = 0; k < n; ++k) {
+        LAUNCH(g, nblk(n), 256, gf::gj_prepare_kernel, g->Ainv, g->gjcol, g->gjrow, (int)n, k);
+        LAUNCH(g, nblk(n * n), 256, gf::gj_eliminate_kernel, g->Ainv, g->gjcol, g->gjrow, (int)n, k);
+    }
+    return GF_OK;
+}
+
+int ensure_krylov(gf_grid* g, int m, int kmax)
+{
+    if (m > g->m_alloc) {
+        cudaFree(g->V);
+        cudaFree(g->Z);
+        g->V = g->Z = nullptr;
+        g->m_alloc = 0;
+        RET(allocT(&g->V, (size_t)(m + 1) * g->ndof));
+        RET(allocT(&g->Z, (size_t)m * g->ndof));
+        g->m_alloc = m;
+    }
+    if (kmax + 1 > g->hist_cap) {
+        cudaFree(g->hist);
+        g->hist = nullptr;
+        g->hist_cap = 0;
+        RET(allocT(&g->hist, (size_t)kmax + 1));
+        g->hist_cap = kmax + 1;
+    }
+    return GF_OK;
+}
+
+__global__ void init_state_kernel(gf::KState* st, int kmax, int m, double tol)
+{
+    st->k = 0;
+    st->kmax = kmax;
+    st->m = m;
+    st->tol = tol;
+    st->status = gf::KS_RUN;
+    st->flag = 1;
+    st->J = 0;
+    st->j = 0;
+}
+
+struct HostState {
+    int k, flag, status, J;
+};
+
+int read_state(gf_grid* g, HostState* hs)
+{
+    gf::KState* st = g->st;
+    CK(cudaMemcpyAsync(&hs->k, &st->k, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(&hs->flag, &st->flag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(&hs->status, &st->status, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return GF_OK;
+}
+
+int pick_nv(int nv)
+{
+    return nv <= 8 ? 8 : (nv <= 16 ? 16 : 32);
+}
+
+template <int NV>
+int cgs2_step(gf_grid* g, int j, double* w)
+{
+    const long long n = g->ndof, ld = g->ndof;
+    const int nv = j + 1;
+    LAUNCH(g, g->nbr, gf::RED_THREADS, gf::cgs_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
+    LAUNCH(g, 1, 32 * 32, gf::reduce_partials_kernel, g->partial, g->nbr, NV + 1, NV + 1, g->st, 0, 1);
+    LAUNCH(g, g->nbr, gf::RED_THREADS, gf::cgs_update_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
+    LAUNCH(g, 1, 32 * 32, gf::reduce_partials_kernel, g->partial, g->nbr, NV, nv, g->st, 1, 1);
+    LAUNCH(g, g->nbr, gf::RED_THREADS, gf::cgs_update_norm_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
+    LAUNCH(g, 1, 32, gf::reduce_partials_kernel, g->partial, g->nbr, 1, 1, g->st, 2, 1);
+    LAUNCH(g, 1, 32, gf::arnoldi_tail_kernel, g->st, g->hist, j, NV, g->host_status_dev, 1e-14);
+    return GF_OK;
+}
+
+int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
+{
+    const long long ld = g->ndof;
+    double* vj = g->V + (long long)j * ld;
+    double* zj = g->Z + (long long)j * ld;
+    double* w = g->V + (long long)(j + 1) * ld;
+    const int* halt = &g->st->status;
+    RET(vcycle_dispatch(g, vj, zj, o->prec, o->nu1, o->nu2, o->omega, halt));
+    RET(applyK64(g, zj, w, halt));
+    switch (pick_nv(j + 1)) {
+        case 8: RET(cgs2_step<8>(g, j, w)); break;
+        case 16: RET(cgs2_step<16>(g, j, w)); break;
+        default: RET(cgs2_step<32>(g, j, w)); break;
+    }
+    LAUNCH(g, 2 * g->sms, 256, gf::scale_kernel, w, g->ndof, g->st, 1);
+    return GF_OK;
+}
+
+// r = M f - K x into V_0, ||r||, ||Mf||, history[k], g = beta e1, V_0 /= beta.
+int cycle_start(gf_grid* g, const double* f, const double* x, bool x_zero, bool first)
+{
+    double* v0 = g->V;
+    if (!x_zero) RET(applyK64(g, x, v0, nullptr));
+    LAUNCH(g, g->nbr, gf::RED_THREADS, gf::residual_norms_kernel, f, v0, v0, g->ndof, g->nx + 1, g->partial,
+           x_zero ? 1 : 0);
+    LAUNCH(g, 1, 64, gf::reduce_partials_kernel, g->partial, g->nbr, 2, 2, g->st, 0, 0);
+    LAUNCH(g, 1, 32, gf::cycle_start_tail_kernel, g->st, g->hist, g->host_status_dev, first ? 1 : 0);
+    LAUNCH(g, 2 * g->sms, 256, gf::scale_kernel, v0, g->ndof, g->st, 1);
+    return GF_OK;
+}
+
+int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, gf_solve_info* info,
+               bool x_zero, double* host_hist)
+{
+    const int m = o->restart;
+    RET(ensure_krylov(g, m, o->kmax));
+    const int NX0 = g->nx + 1;
+    // fixed entries of u are written as 0
+    LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, double>), u, u, g->ndof, NX0, nullptr);
+    LAUNCH(g, 1, 1, init_state_kernel, g->st, o->kmax, m, o->tol);
+    *g->host_status = gf::KS_RUN;
+    bool first = true;
+    HostState hs{};
+    for (;;) {
+        RET(cycle_start(g, f, u, x_zero && first, first));
+        first = false;
+        x_zero = false;
+        CK(cudaStreamSynchronize(g->stream));
+        if (*(volatile int*)g->host_status != gf::KS_RUN) break;
+        for (int j = 0; j < m; ++j) {
+            RET(arnoldi_step(g, j, o));
+            CK(cudaEventRecord(g->ev[j % 3], g->stream));
+            if (j >= 1) {
+                CK(cudaEventSynchronize(g->ev[(j - 1) % 3]));
+                if (*(volatile int*)g->host_status != gf::KS_RUN) break;
+            }
+        }
+        LAUNCH(g, 1, 1, gf::backsolve_kernel, g->st);
+        LAUNCH(g, 2 * g->sms, 256, gf::update_x_kernel, u, g->Z, g->ndof, g->ndof, g->st);
+        RET(read_state(g, &hs));
+        if (hs.status != gf::KS_RUN) break;
+    }
+    RET(read_state(g, &hs));
+    if (info) {
+        info->iters = hs.k;
+        info->flag = hs.flag;
+        double est = 0.0;
+        CK(cudaMemcpy(&est, g->hist + hs.k, sizeof(double), cudaMemcpyDeviceToHost));
+        info->stop_estimate = est;
+    }
+    if (host_hist) CK(cudaMemcpy(host_hist, g->hist, sizeof(double) * (hs.k + 1), cudaMemcpyDeviceToHost));
+    return GF_OK;
+}
+
+int validate_opts(const gf_solve_opts* o)
+{
+    if (!o) return set_err(GF_ERR_ARG, "null opts");
+    if (o->restart < 1 || o->restart > gf::KRY_MMAX) return set_err(GF_ERR_ARG, "restart must be in [1, 32]");
+    if (o->kmax < 0) return set_err(GF_ERR_ARG, "kmax < 0");
+    if (!(o->tol >= 0.0)) return set_err(GF_ERR_ARG, "tol must be >= 0");
+    if (o->prec != GF_FP64 && o->prec != GF_MIXED) return set_err(GF_ERR_ARG, "prec");
+    if (o->nu1 < 1 || o->nu2 < 1 || o->nu1 > 16 || o->nu2 > 16) return set_err(GF_ERR_ARG, "nu1/nu2 in [1,16]");
+    if (!(o->omega > 0.0 && o->omega < 2.0)) return set_err(GF_ERR_ARG, "omega in (0,2)");
+    return GF_OK;
+}
+
+int guard_impl(gf_grid* g, const double* f, const double* u, double* eta)
+{
+    RET(applyK64(g, u, g->work, nullptr));
+    LAUNCH(g, g->nbr, gf::RED_THREADS, gf::residual_norms_kernel, f, g->work, (double*)nullptr, g->ndof,
+           g->nx + 1, g->partial, 0);
+    LAUNCH(g, 1, 64, gf::reduce_partials_kernel, g->partial, g->nbr, 2, 2, g->gst, 0, 0);
+    double h[2];
+    CK(cudaMemcpyAsync(h, g->gst->h1, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return set_err(GF_ERR_NONFINITE, "non-finite residual");
+    if (h[1] == 0.0) return set_err(GF_ERR_ARG, "f is zero on the free DOFs");
+    *eta = std::sqrt(h[0]) / std::sqrt(h[1]);
+    return GF_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI ====
+extern "C" {
+
+const char* gf_last_error(void) { return g_err.c_str(); }
+
+int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int levels, void* stream,
+                   gf_grid** out)
+{
+    if (!out) return set_err(GF_ERR_ARG, "null out");
+    *out = nullptr;
+    if (nx < 1 || ny < 2 || nz < 2 || (ny & 1) || (nz & 1)) return set_err(GF_ERR_ARG, "need nx>=1, even ny,nz >= 2");
+    if (levels < 1 || levels > 8) return set_err(GF_ERR_ARG, "levels in [1,8]");
+    const int div = 1 << (levels - 1);
+    if (nx % div || ny % div || nz % div) return set_err(GF_ERR_ARG, "grid not divisible by 2^(levels-1)");
+    if (!(h > 0) || !(E0 > 0) || !(nu > -1.0 && nu < 0.5)) return set_err(GF_ERR_ARG, "h, E0 > 0, nu in (-1,0.5)");
+    const long long cn = 3LL * (nx / div + 1) * (ny / div + 1) * (nz / div + 1);
+    if (cn > 6144) return set_err(GF_ERR_ARG, "coarsest level above 6144 DOFs: add levels");
+    gf_grid* g = new gf_grid();
+    g->nx = nx; g->ny = ny; g->nz = nz; g->L = levels;
+    g->h = h; g->E0 = E0; g->nu = nu;
+    g->stream = (cudaStream_t)stream;
+    auto fail = [&](int code) { gf_destroy_grid(g); return code; };
+    if (cudaGetDevice(&g->device) != cudaSuccess) return fail(set_err(GF_ERR_CUDA, "cudaGetDevice"));
+    if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
+        return fail(set_err(GF_ERR_CUDA, "SM count"));
+    g->nodes = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+    g->ndof = 3 * g->nodes;
+    g->nel = (long long)nx * ny * nz;
+    double K[576];
+    build_k0(E0, nu, K);
+    for (int q = 0; q < 576; ++q) {
+        g->K0d.k[q] = K[q];
+        g->K0f.k[q] = (float)K[q];
+    }
+    for (int l = 0; l < levels; ++l) {
+        Level L;
+        L.nx = nx >> l; L.ny = ny >> l; L.nz = nz >> l;
+        L.h = h * (double)(1 << l);
+        L.nodes = (long long)(L.nx + 1) * (L.ny + 1) * (L.nz + 1);
+        L.ndof = 3 * L.nodes;
+        L.nel = (long long)L.nx * L.ny * L.nz;
+        int r = GF_OK;
+        if ((r = allocT(&L.E64, L.nel)) || (r = allocT(&L.E32, L.nel)) ||
+            (r = allocT(&L.b64, L.ndof)) || (r = allocT(&L.x64, L.ndof)) || (r = allocT(&L.t64, L.ndof)) ||
+            (r = allocT(&L.r64, L.ndof)) || (r = allocT(&L.b32, L.ndof)) || (r = allocT(&L.x32, L.ndof)) ||
+            (r = allocT(&L.t32, L.ndof)) || (r = allocT(&L.r32, L.ndof))) {
+            g->lv.push_back(L);
+            return fail(r);
+        }
+        g->lv.push_back(L);
+    }
+    g->nc = (int)g->lv.back().ndof;
+    int r = GF_OK;
+    g->nbr = (int)std::min<long long>(2LL * g->sms, std::max<long long>(1, (g->ndof + 1023) / 1024));
+    if ((r = allocT(&g->Ainv, (size_t)g->nc * g->nc)) || (r = allocT(&g->gjcol, g->nc)) ||
+        (r = allocT(&g->gjrow, g->nc)) || (r = allocT(&g->dflag, 4)) || (r = allocT(&g->rho64, g->nel)) ||
+        (r = allocT(&g->rho16, g->nel)) || (r = allocT(&g->work, g->ndof)) ||
+        (r = allocT(&g->partial, (size_t)g->nbr * 40)) || (r = allocT(&g->st, 1)) || (r = allocT(&g->gst, 1)))
+        return fail(r);
+    if (cudaHostAlloc((void**)&g->host_status, sizeof(int), cudaHostAllocMapped) != cudaSuccess)
+        return fail(set_err(GF_ERR_CUDA, "cudaHostAlloc"));
+    if (cudaHostGetDevicePointer((void**)&g->host_status_dev, g->host_status, 0) != cudaSuccess)
+        return fail(set_err(GF_ERR_CUDA, "cudaHostGetDevicePointer"));
+    for (int i = 0; i < 3; ++i)
+        if (cudaEventCreateWithFlags(&g->ev[i], cudaEventDisableTiming) != cudaSuccess)
+            return fail(set_err(GF_ERR_CUDA, "event"));
+    *out = g;
+    return GF_OK;
+}
+
+int gf_destroy_grid(gf_grid* g)
+{
+    if (!g) return GF_OK;
+    cudaSetDevice(g->device);
+    cudaStreamSynchronize(g->stream);
+    for (Level& L : g->lv) {
+        cudaFree(L.E64); cudaFree(L.E32);
+        cudaFree(L.b64); cudaFree(L.x64); cudaFree(L.t64); cudaFree(L.r64);
+        cudaFree(L.b32); cudaFree(L.x32); cudaFree(L.t32); cudaFree(L.r32);
+    }
+    cudaFree(g->Ainv); cudaFree(g->gjcol); cudaFree(g->gjrow); cudaFree(g->dflag);
+    cudaFree(g->rho64); cudaFree(g->rho16); cudaFree(g->work); cudaFree(g->partial);
+    cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Z); cudaFree(g->hist);
+    cudaFree(g->xsave);
+    if (g->host_status) cudaFreeHost(g->host_status);
+    for (int i = 0; i < 3; ++i)
+        if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+    delete g;
+    return GF_OK;
+}
+
+int gf_grid_sizes(const gf_grid* g, int* n_dof, int* n_elem, int* n_nodes, int* levels)
+{
+    RET(check_grid(g));
+    if (n_dof) *n_dof = (int)g->ndof;
+    if (n_elem) *n_elem = (int)g->nel;
+    if (n_nodes) *n_nodes = (int)g->nodes;
+    if (levels) *levels = g->L;
+    return GF_OK;
+}
+
+int gf_set_density(gf_grid* g, const double* rho_hat, double p)
+{
+    RET(check_grid(g));
+    if (!rho_hat) return set_err(GF_ERR_ARG, "null rho_hat");
+    if (!(p >= 1.0 && p <= 16.0)) return set_err(GF_ERR_ARG, "p in [1,16]");
+    RET(set_device(g));
+    CK(cudaMemsetAsync(g->dflag, 0, sizeof(int), g->stream));
+    LAUNCH(g, nblk(g->nel), 256, gf::density_check_kernel, rho_hat, g->rho16, g->rho64, g->nel, g->dflag);
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    g->has_floor = false;
+    if (bad) {
+        g->has_density = false;
+        return set_err(GF_ERR_NONFINITE, "density has NaN/Inf or values outside [0,1]");
+    }
+    g->p = p;
+    g->has_density = true;
+    return GF_OK;
+}
+
+int gf_set_floor(gf_grid* g, double rho_min)
+{
+    RET(check_grid(g));
+    if (!g->has_density) return set_err(GF_ERR_STATE, "set_density first");
+    if (!(rho_min > 0.0 && rho_min <= 1.0)) return set_err(GF_ERR_ARG, "rho_min in (0,1]");
+    RET(set_device(g));
+    const double p = g->p;
+    const int p_int = (p == std::floor(p)) ? (int)p : 0;
+    Level& f = g->lv[0];
+    LAUNCH(g, nblk(g->nel), 256, gf::modulus_fp64_kernel, g->rho64, f.E64, g->nel, rho_min, p, p_int, f.h);
+    LAUNCH(g, nblk(g->nel), 256, gf::modulus_fp32_kernel, g->rho16, f.E32, g->nel, (float)rho_min, (float)p,
+           p_int, (float)f.h);
+    for (int l = 1; l < g->L; ++l) {
+        Level& c = g->lv[l];
+        LAUNCH(g, nblk(c.nel), 256, gf::coarsen_kernel<double>, g->lv[l - 1].E64, c.E64, c.dims());
+        LAUNCH(g, nblk(c.nel), 256, gf::coarsen_kernel<float>, g->lv[l - 1].E32, c.E32, c.dims());
+    }
+    RET(build_coarse_inverse(g));
+    g->rho_min = rho_min;
+    g->has_floor = true;
+    return GF_OK;
+}
+
+int gf_cantilever_load(gf_grid* g, double* f)
+{
+    RET(check_grid(g));
+    if (!f) return set_err(GF_ERR_ARG, "null f");
+    RET(set_device(g));
+    LAUNCH(g, nblk(g->ndof), 256, gf::cantilever_load_kernel, f, g->lv[0].dims());
+    return GF_OK;
+}
+
+int gf_free_mask(gf_grid* g, uint8_t* mask)
+{
+    RET(check_grid(g));
+    if (!mask) return set_err(GF_ERR_ARG, "null mask");
+    RET(set_device(g));
+    LAUNCH(g, nblk(g->ndof), 256, gf::free_mask_kernel, mask, g->lv[0].dims());
+    return GF_OK;
+}
+
+int gf_apply_K(gf_grid* g, const double* u, double* y)
+{
+    RET(check_grid(g));
+    if (!u || !y || u == y) return set_err(GF_ERR_ARG, "u, y non-null and distinct");
+    if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
+    RET(set_device(g));
+    return applyK64(g, u, y, nullptr);
+}
+
+int gf_apply_K_f32(gf_grid* g, const float* u, float* y)
+{
+    RET(check_grid(g));
+    if (!u || !y || u == y) return set_err(GF_ERR_ARG, "u, y non-null and distinct");
+    if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
+    RET(set_device(g));
+    return stencil<float, float, gf::ST_APPLY>(g, 0, u, nullptr, y, g->lv[0].E32, g->K0f, 0.0f, nullptr);
+}
+
+int gf_vcycle(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2, double omega)
+{
+    RET(check_grid(g));
+    if (!v || !z || v == z) return set_err(GF_ERR_ARG, "v, z non-null and distinct");
+    if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
+    if (prec != GF_FP64 && prec != GF_MIXED) return set_err(GF_ERR_ARG, "prec");
+    if (nu1 < 1 || nu2 < 1 || nu1 > 16 || nu2 > 16 || !(omega > 0 && omega < 2)) return set_err(GF_ERR_ARG, "smoother");
+    RET(set_device(g));
+    return vcycle_dispatch(g, v, z, prec, nu1, nu2, omega, nullptr);
+}
+
+int gf_solve(gf_grid* g, const double* f, double* u, const gf_solve_opts* opts, gf_solve_info* info)
+{
+    RET(check_grid(g));
+    RET(validate_opts(opts));
+    if (!f || !u || f == u) return set_err(GF_ERR_ARG, "f, u non-null and distinct");
+    if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
+    RET(set_device(g));
+    return solve_impl(g, f, u, opts, info, false, opts->history);
+}
+
+int gf_true_residual(gf_grid* g, const double* f, const double* u, double* eta)
+{
+    RET(check_grid(g));
+    if (!f || !u || !eta) return set_err(GF_ERR_ARG, "null pointer");
+    if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
+    RET(set_device(g));
+    return guard_impl(g, f, u, eta);
+}
+
+void gf_policy_defaults(gf_policy* pol)
+{
+    if (!pol) return;
+    std::memset(pol, 0, sizeof(*pol));
+    pol->rho0 = 1e-6;
+    pol->ladder[0] = 1e-5;
+    pol->ladder[1] = 1e-4;
+    pol->ladder[2] = 1e-3;
+    pol->n_ladder = 3;
+    pol->tau = 1e-6;
+    pol->kmax = 200;
+    pol->probe_iters = 100;
+    pol->r50_escalate = 1e-2;
+    pol->r100_stall = 1e-4;
+    pol->plateau_ratio = 0.6;
+    pol->checkpoint_a = 50;
+    pol->checkpoint_b = 100;
+    pol->selector = GF_SEL_RULE;
+    pol->first_index = 0;
+    pol->solve.restart = 30;
+    pol->solve.kmax = 200;
+    pol->solve.tol = 1e-6;
+    pol->solve.prec = GF_FP64;
+    pol->solve.nu1 = 2;
+    pol->solve.nu2 = 2;
+    pol->solve.omega = 0.6;
+    pol->solve.history = nullptr;
+}
+
+int gf_trigger_rule(double r50, double r100, const gf_policy* pol)
+{
+    if (!pol) return set_err(GF_ERR_ARG, "null policy");
+    return (r50 >= pol->r50_escalate) || (r100 >= pol->r100_stall && r100 / r50 >= pol->plateau_ratio) ? 1 : 0;
+}
+
+int gf_probe_features(const double* history, int k_stop, const gf_policy* pol, double* r50, double* r100)
+{
+    if (!history || !pol || !r50 || !r100 || k_stop < 0) return set_err(GF_ERR_ARG, "bad argument");
+    *r50 = history[std::min(pol->checkpoint_a, k_stop)];
+    *r100 = history[std::min(pol->checkpoint_b, k_stop)];
+    return GF_OK;
+}
+
+int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol, gf_select_info* info)
+{
+    RET(check_grid(g));
+    if (!f || !u || !pol || !info || f == u) return set_err(GF_ERR_ARG, "null pointer");
+    if (!g->has_density) return set_err(GF_ERR_STATE, "set_density first");
+    if (pol->n_ladder < 0 || pol->n_ladder > GF_MAX_LADDER) return set_err(GF_ERR_ARG, "n_ladder");
+    if (!(pol->rho0 > 0) || pol->probe_iters < 0 || pol->kmax < 0) return set_err(GF_ERR_ARG, "policy");
+    gf_solve_opts o = pol->solve;
+    o.history = nullptr;
+    o.tol = pol->tau;
+    RET(validate_opts(&o));
+    RET(set_device(g));
+    std::memset(info, 0, sizeof(*info));
+    info->r50 = info->r100 = std::nan("");
+    info->floor_index = -1;
+    info->rho_min = std::nan("");
+    info->eta = std::nan("");
+    double floors[GF_MAX_LADDER + 1];
+    floors[0] = pol->rho0;
+    for (int i = 0; i < pol->n_ladder; ++i) floors[i + 1] = pol->ladder[i];
+    const int nf = pol->n_ladder + 1;
+    int start = 0;
+    if (pol->selector == GF_SEL_RULE) {
+        RET(gf_set_floor(g, pol->rho0));
+        std::vector<double> hist((size_t)pol->probe_iters + 1);
+        gf_solve_opts po = o;
+        po.kmax = pol->probe_iters;
+        gf_solve_info pi{};
+        CK(cudaMemsetAsync(u, 0, sizeof(double) * g->ndof, g->stream));
+        RET(solve_impl(g, f, u, &po, &pi, true, hist.data()));
+        info->probe_iters_run = pi.iters;
+        RET(gf_probe_features(hist.data(), pi.iters, pol, &info->r50, &info->r100));
+        info->escalated = gf_trigger_rule(info->r50, info->r100, pol);
+        start = info->escalated ? 1 : 0;
+    } else if (pol->selector == GF_SEL_FULL) {
+        start = 0;
+    } else if (pol->selector == GF_SEL_GIVEN) {
+        if (pol->first_index < 0 || pol->first_index >= nf) return set_err(GF_ERR_ARG, "first_index");
+        start = pol->first_index;
+        info->escalated = start > 0;
+    } else {
+        return set_err(GF_ERR_ARG, "selector");
+    }
+    info->status = GF_NO_ADMISSIBLE_FLOOR;
+    for (int idx = start; idx < nf; ++idx) {
+        const double rm = floors[idx];
+        if (!(g->has_floor && g->rho_min == rm)) RET(gf_set_floor(g, rm));
+        o.kmax = pol->kmax;
+        gf_solve_info si{};
+        CK(cudaMemsetAsync(u, 0, sizeof(double) * g->ndof, g->stream));
+        RET(solve_impl(g, f, u, &o, &si, true, nullptr));
+        double eta = 0.0;
+        RET(guard_impl(g, f, u, &eta));
+        gf_attempt& a = info->attempts[info->n_attempts++];
+        a.rho_min = rm;
+        a.iters = si.iters;
+        a.flag = si.flag;
+        a.stop_estimate = si.stop_estimate;
+        a.eta = eta;
+        a.accepted = eta <= pol->tau;
+        if (a.accepted) {
+            info->status = GF_ACCEPTED;
+            info->floor_index = idx;
+            info->rho_min = rm;
+            info->eta = eta;
+            break;
+        }
+    }
+    return GF_OK;
+}
+
+int gf_sensitivity(gf_grid* g, const double* u, double* dc)
+{
+    RET(check_grid(g));
+    if (!u || !dc) return set_err(GF_ERR_ARG, "null pointer");
+    if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
+    RET(set_device(g));
+    gf::K0Param<double> K = g->K0d;
+    for (int q = 0; q < 576; ++q) K.k[q] *= g->h;
+    const double p = g->p;
+    const int pm1_int = (p == std::floor(p)) ? (int)p - 1 : -1;
+    LAUNCH(g, nblk(g->nel), 256, gf::sensitivity_kernel, u, g->rho64, dc, g->lv[0].dims(), K,
+           -p * (1.0 - g->rho_min), p - 1.0, pm1_int);
+    return GF_OK;
+}
+
+int gf_get_stats(const gf_grid* g, gf_stats* s)
+{
+    RET(check_grid(g));
+    if (!s) return set_err(GF_ERR_ARG, "null stats");
+    *s = g->stats;
+    return GF_OK;
+}
+
+int gf_reset_stats(gf_grid* g)
+{
+    RET(check_grid(g));
+    g->stats = gf_stats{};
+    return GF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,358 @@
+// FGMRES(m) device kernels: fused classical Gram-Schmidt with one re-orthogonalisation
+// (CGS2), deterministic two-stage reductions, the Givens/Hessenberg update and the
+// residual history on the device, so the host only polls a stop flag.
+//
+// Right-preconditioned flexible GMRES (Saad 1993), as used by the paper's outer
+// solver (Sec. 3.5 "Why a flexible Krylov method", Table residual-semantics):
+//   z_j = B v_j, w = K z_j, h = V^T w, w -= V h, h' = V^T w, w -= V h', h += h',
+//   h_{j+1,j} = ||w||, rotate, g_{j+1} = -s g_j, g_j = c g_j, history = |g_{j+1}|/||f||.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace gf {
+
+constexpr int KRY_MMAX = 32;
+constexpr int RED_THREADS = 256;
+
+enum { KS_RUN = 0, KS_STOP = 1 };
+
+struct KState {
+    double H[(KRY_MMAX + 1) * KRY_MMAX];   // column-major, ld = KRY_MMAX+1
+    double cs[KRY_MMAX], sn[KRY_MMAX], g[KRY_MMAX + 1];
+    double h1[KRY_MMAX + 2];               // first-pass dots (+ ||w||^2 in slot NV)
+    double h2[KRY_MMAX + 1];               // second-pass dots
+    double y[KRY_MMAX];
+    double ww;                             // ||w||^2 after CGS2
+    double fnorm, tol, inv, beta;
+    int k, kmax, m, J, status, flag, j;
+};
+
+// ---------------------------------------------------------------- reductions --
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&acc)[NV], int nv, double* __restrict__ out_row)
+{
+    __shared__ double red[RED_THREADS / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double v = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < RED_THREADS / 32; ++w) s += red[w][threadIdx.x];
+        out_row[threadIdx.x] = s;
+    }
+}
+
+// rows of block b: [b*chunk, min(n, (b+1)*chunk))
+__device__ __forceinline__ void block_rows(long long n, long long& r0, long long& r1)
+{
+    const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    r0 = (long long)blockIdx.x * chunk;
+    r1 = r0 + chunk < n ? r0 + chunk : n;
+}
+
+// pass 1: partial[b][i] = sum_r V_i[r] w[r] (i < nv), partial[b][nv] = sum_r w[r]^2
+template <int NV>
+__global__ void __launch_bounds__(RED_THREADS)
+cgs_dots_kernel(const double* __restrict__ V, long long ld, int nv, const double* __restrict__ w,
+                long long n, double* __restrict__ partial, const KState* __restrict__ st)
+{
+    if (st->status != KS_RUN) return;
+    double acc[NV + 1];
+#pragma unroll
+    for (int q = 0; q <= NV; ++q) acc[q] = 0.0;
+    long long r0, r1;
+    block_rows(n, r0, r1);
+    for (long long r = r0 + threadIdx.x; r < r1; r += RED_THREADS) {
+        const double wr = w[r];
+#pragma unroll
+        for (int q = 0; q < NV; ++q)
+            if (q < nv) acc[q] = fma(V[q * ld + r], wr, acc[q]);
+        acc[NV] = fma(wr, wr, acc[NV]);
+    }
+    // row layout: dots in slots [0, nv), ||w||^2 in slot NV (row stride NV + 1)
+    block_reduce_store<NV + 1>(acc, NV + 1, partial + (long long)blockIdx.x * (NV + 1));
+}
+
+// pass 2: w -= sum_i h1_i V_i ; partial[b][i] = sum_r V_i[r] w_new[r]
+template <int NV>
+__global__ void __launch_bounds__(RED_THREADS)
+cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
+                       long long n, double* __restrict__ partial, const KState* __restrict__ st)
+{
+    if (st->status != KS_RUN) return;
+    __shared__ double h[NV];
+    double acc[NV];
+    if (threadIdx.x < NV) h[threadIdx.x] = threadIdx.x < nv ? st->h1[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+    __syncthreads();
+    long long r0, r1;
+    block_rows(n, r0, r1);
+    for (long long r = r0 + threadIdx.x; r < r1; r += RED_THREADS) {
+        double v[NV];
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            v[q] = q < nv ? V[q * ld + r] : 0.0;
+            s = fma(h[q], v[q], s);
+        }
+        const double wn = w[r] - s;
+        w[r] = wn;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] = fma(v[q], wn, acc[q]);
+    }
+    block_reduce_store<NV>(acc, nv, partial + (long long)blockIdx.x * NV);
+}
+
+// pass 3: w -= sum_i h2_i V_i ; partial[b][0] = ||w_new||^2 (block part)
+template <int NV>
+__global__ void __launch_bounds__(RED_THREADS)
+cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
+                       long long n, double* __restrict__ partial, const KState* __restrict__ st)
+{
+    if (st->status != KS_RUN) return;
+    __shared__ double h[NV];
+    if (threadIdx.x < NV) h[threadIdx.x] = threadIdx.x < nv ? st->h2[threadIdx.x] : 0.0;
+    __syncthreads();
+    double acc[1] = {0.0};
+    long long r0, r1;
+    block_rows(n, r0, r1);
+    for (long long r = r0 + threadIdx.x; r < r1; r += RED_THREADS) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < NV; ++q)
+            if (q < nv) s = fma(h[q], V[q * ld + r], s);
+        const double wn = w[r] - s;
+        w[r] = wn;
+        acc[0] = fma(wn, wn, acc[0]);
+    }
+    block_reduce_store<1>(acc, 1, partial + blockIdx.x);
+}
+
+// Sum partial[b][i] over blocks b (fixed order: deterministic). One warp per i.
+// dst selects where the sums go in the state: 0 -> h1[0..cnt), 1 -> h2[0..cnt),
+// 2 -> ww (cnt == 1).
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nblocks, int stride, int cnt,
+                                       KState* __restrict__ st, int dst, int check_status)
+{
+    if (check_status && st->status != KS_RUN) return;
+    const int lane = threadIdx.x & 31;
+    const int i = threadIdx.x >> 5;
+    for (int q = i; q < cnt; q += blockDim.x >> 5) {
+        double s = 0.0;
+        for (int b = lane; b < nblocks; b += 32) s += partial[(long long)b * stride + q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            if (dst == 0) st->h1[q] = s;
+            else if (dst == 1) st->h2[q] = s;
+            else st->ww = s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Arnoldi tail --
+// One thread: finish column j of H, apply the stored rotations, form the new
+// one, update g, record the history, decide whether to stop.
+__global__ void arnoldi_tail_kernel(KState* __restrict__ st, double* __restrict__ hist, int j,
+                                    int ww0_slot, volatile int* host_status, double breakdown_rtol)
+{
+    if (threadIdx.x != 0 || st->status != KS_RUN) return;
+    const int ldh = KRY_MMAX + 1;
+    double* col = st->H + (long long)j * ldh;
+    const double wnorm0 = sqrt(st->h1[ww0_slot]);
+    for (int i = 0; i <= j; ++i) col[i] = st->h1[i] + st->h2[i];
+    const double hnext = sqrt(st->ww);
+    col[j + 1] = hnext;
+    for (int i = 0; i < j; ++i) {
+        const double a = col[i], b = col[i + 1];
+        col[i] = st->cs[i] * a + st->sn[i] * b;
+        col[i + 1] = -st->sn[i] * a + st->cs[i] * b;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double rho = hypot(a, b);
+    st->j = j;
+    if (rho == 0.0) {            // degenerate column: breakdown, drop the step
+        st->status = KS_STOP;
+        st->flag = 2;
+        st->J = j;
+        *host_status = KS_STOP;
+        return;
+    }
+    const double c = a / rho, s = b / rho;
+    st->cs[j] = c;
+    st->sn[j] = s;
+    col[j] = rho;
+    col[j + 1] = 0.0;
+    const double gj = st->g[j];
+    st->g[j + 1] = -s * gj;
+    st->g[j] = c * gj;
+    st->k += 1;
+    st->J = j + 1;
+    const double est = fabs(st->g[j + 1]) / st->fnorm;
+    hist[st->k] = est;
+    if (est <= st->tol) {
+        st->status = KS_STOP;
+        st->flag = 0;
+    } else if (st->k >= st->kmax) {
+        st->status = KS_STOP;
+        st->flag = 1;
+    } else if (hnext <= breakdown_rtol * wnorm0) {
+        st->status = KS_STOP;
+        st->flag = 2;
+    } else {
+        st->inv = 1.0 / hnext;
+    }
+    if (st->status == KS_STOP) *host_status = KS_STOP;
+}
+
+// Cycle start: beta = ||r||, history[k] = beta/||f|| (a true residual), g = beta e1.
+__global__ void cycle_start_tail_kernel(KState* __restrict__ st, double* __restrict__ hist,
+                                        volatile int* host_status, int first)
+{
+    if (threadIdx.x != 0) return;
+    const double beta = sqrt(st->h1[0]);          // ||M f - K x||
+    if (first) st->fnorm = sqrt(st->h1[1]);       // ||M f||
+    st->beta = beta;
+    st->J = 0;
+    const double rel = beta / st->fnorm;
+    hist[st->k] = rel;
+    for (int i = 0; i <= st->m; ++i) st->g[i] = 0.0;
+    st->g[0] = beta;
+    if (rel <= st->tol) {
+        st->status = KS_STOP;
+        st->flag = 0;
+    } else if (st->k >= st->kmax) {
+        st->status = KS_STOP;
+        st->flag = 1;
+    } else {
+        st->status = KS_RUN;
+        st->inv = 1.0 / beta;
+    }
+    *host_status = st->status;
+}
+
+// Upper-triangular back substitution H[0:J,0:J] y = g[0:J].
+__global__ void backsolve_kernel(KState* __restrict__ st)
+{
+    if (threadIdx.x != 0) return;
+    const int ldh = KRY_MMAX + 1;
+    const int J = st->J;
+    for (int i = J - 1; i >= 0; --i) {
+        double s = st->g[i];
+        for (int c = i + 1; c < J; ++c) s -= st->H[(long long)c * ldh + i] * st->y[c];
+        st->y[i] = s / st->H[(long long)i * ldh + i];
+    }
+}
+
+// x += sum_{i<J} y_i Z_i
+__global__ void __launch_bounds__(256)
+update_x_kernel(double* __restrict__ x, const double* __restrict__ Z, long long ld, long long n,
+                const KState* __restrict__ st)
+{
+    __shared__ double ys[KRY_MMAX];
+    const int J = st->J;
+    if (threadIdx.x < J) ys[threadIdx.x] = st->y[threadIdx.x];
+    __syncthreads();
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (long long)gridDim.x * blockDim.x) {
+        double s = x[r];
+        for (int i = 0; i < J; ++i) s = fma(ys[i], Z[i * ld + r], s);
+        x[r] = s;
+    }
+}
+
+// v *= st->inv (skipped once stopped)
+__global__ void scale_kernel(double* __restrict__ v, long long n, const KState* __restrict__ st, int check_status)
+{
+    if (check_status && st->status != KS_RUN) return;
+    const double s = st->inv;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
+         r += (long long)gridDim.x * blockDim.x)
+        v[r] *= s;
+}
+
+// r = M f - y (y = K x) into r; partial[b][0] = ||r||^2, partial[b][1] = ||M f||^2.
+// fixed DOFs: (r/3) % NX == 0.
+__global__ void __launch_bounds__(RED_THREADS)
+residual_norms_kernel(const double* __restrict__ f, const double* y, double* r,
+                      long long n, int NX, double* __restrict__ partial, int y_is_zero)
+{
+    double acc[2] = {0.0, 0.0};
+    long long r0, r1;
+    block_rows(n, r0, r1);
+    for (long long q = r0 + threadIdx.x; q < r1; q += RED_THREADS) {
+        const bool fixed = ((q / 3) % NX) == 0;
+        const double fv = fixed ? 0.0 : f[q];
+        const double rv = y_is_zero ? fv : fv - y[q];
+        if (r) r[q] = rv;
+        acc[0] = fma(rv, rv, acc[0]);
+        acc[1] = fma(fv, fv, acc[1]);
+    }
+    block_reduce_store<2>(acc, 2, partial + (long long)blockIdx.x * 2);
+}
+
+// masked copy (fixed entries -> 0), optional type conversion
+template <typename TI, typename TO>
+__global__ void masked_convert_kernel(const TI* a, TO* b, long long n, int NX,
+                                      const int* __restrict__ halt)
+{
+    if (halt != nullptr && *halt != 0) return;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x)
+        b[q] = (((q / 3) % NX) == 0) ? TO(0) : (TO)a[q];
+}
+
+// Dense GEMV for the coarsest solve: x = A b, A row-major FP64 (n x n); one warp per row.
+template <typename TB, typename TX>
+__global__ void __launch_bounds__(256)
+dense_gemv_kernel(const double* __restrict__ A, const TB* __restrict__ b, TX* __restrict__ x, int n,
+                  const int* __restrict__ halt)
+{
+    if (halt != nullptr && *halt != 0) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const double* row = A + (long long)warp * n;
+    double s = 0.0;
+    for (int c = lane; c < n; c += 32) s = fma(row[c], (double)b[c], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) x[warp] = (TX)s;
+}
+
+// Gauss-Jordan inversion of an SPD matrix without pivoting, one pivot per pair of
+// launches: (1) save column k and the scaled pivot row, (2) eliminate.
+__global__ void gj_prepare_kernel(double* __restrict__ A, double* __restrict__ col, double* __restrict__ row,
+                                  int n, int k)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double piv = 1.0 / A[(long long)k * n + k];
+    col[t] = A[(long long)t * n + k];
+    const double v = (t == k) ? 1.0 : A[(long long)k * n + t];
+    row[t] = v * piv;
+}
+
+__global__ void gj_eliminate_kernel(double* __restrict__ A, const double* __restrict__ col,
+                                    const double* __restrict__ row, int n, int k)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)n * n) return;
+    const int i = (int)(t / n), c = (int)(t % n);
+    if (i == k) {
+        A[t] = row[c];
+    } else {
+        const double base = (c == k) ? 0.0 : A[t];
+        A[t] = base - col[i] * row[c];
+    }
+}
+
+}  // namespace gf

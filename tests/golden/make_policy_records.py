@@ -1,0 +1,50 @@
+"""Write the oracle's Algorithm-1 record for the 96x48x48 smoothed-Gaussian state.
+
+    python tests/golden/make_policy_records.py [--seed 0]
+
+Calls only oracle/ (and the seeded generators in synth/). The record (probe
+features, candidate floors, per-attempt iterations, flags and recomputed eta) is
+a full-size decision fixture for the GPU path and gives the oracle's own step and
+set-up counts, from which the CPU baseline extrapolates a bounded timing sample.
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import synth  # noqa: E402
+from oracle import gf_oracle as O  # noqa: E402
+
+WORKLOAD = dict(nx=96, ny=48, nz=48, levels=4, p=3.0, rho0=1e-6, ladder=[1e-5, 1e-4, 1e-3],
+                tau=1e-6, kmax=200, probe_iters=100, restart=30, sigma=2.0, floor_frac=0.4)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--seed", type=int, default=0)
+    args = ap.parse_args()
+    w = WORKLOAD
+    rho = synth.smoothed_gaussian_density(w["nx"], w["ny"], w["nz"], args.seed, w["sigma"], w["floor_frac"])
+    m = O.Mesh(w["nx"], w["ny"], w["nz"])
+    f = O.cantilever_load(m)
+    setup = O.SolverSetup(m, rho, p=w["p"], n_levels=w["levels"], restart=w["restart"])
+    t0 = time.time()
+    r = O.select_floor(setup, f, w["rho0"], w["ladder"], tau=w["tau"], kmax=w["kmax"],
+                       probe_iters=w["probe_iters"])
+    rec = dict(workload=w, seed=args.seed, oracle_seconds=time.time() - t0, status=r.status,
+               floor_index=r.floor_index, rho_min=r.rho_min, eta=r.eta, r50=r.r50, r100=r.r100,
+               escalated=r.escalated, probe_iters_run=r.probe_iters_run,
+               attempts=[dict(rho_min=a.rho_min, iters=a.iters, flag=a.flag, stop_estimate=a.stop_estimate,
+                              eta=a.eta, accepted=a.accepted) for a in r.attempts])
+    out = os.path.join(HERE, f"policy_c2_seed{args.seed}.json")
+    with open(out, "w") as fh:
+        json.dump(rec, fh, indent=1)
+    print(json.dumps(rec, indent=1))
+
+
+if __name__ == "__main__":
+    main()

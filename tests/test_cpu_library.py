@@ -1,0 +1,82 @@
+"""CPU checks of the CUDA library: it builds, loads, exports every symbol declared in
+include/gf.h, and its host-only policy logic makes the same decisions as the oracle
+on identical residuals (bit-exact integer decisions)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import gf_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def gflib():
+    from paper_2607_26382_b300 import build
+    build.build()
+    from paper_2607_26382_b300 import _lib
+    return _lib
+
+
+def _declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "gf.h")).read()
+    return sorted(set(re.findall(r"\b(gf_[A-Za-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(gflib):
+    L = gflib.lib()
+    declared = _declared_symbols()
+    assert len(declared) >= 18
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(gflib.EXPORTED) <= set(declared)
+
+
+def test_trigger_rule_matches_oracle_bit_exact(gflib):
+    rng = np.random.default_rng(0)
+    pol = gflib.policy_defaults()
+    # random pairs over the decision-relevant range plus exact threshold hits
+    r50 = 10.0 ** rng.uniform(-8, 0, 4000)
+    r100 = r50 * 10.0 ** rng.uniform(-4, 0.5, 4000)
+    extra = [(1e-2, 1e-9), (1e-3, 1e-4), (1e-4 / 0.6, 1e-4), (1.6e-4, 1e-4), (2e-4, 9.99e-5)]
+    pairs = list(zip(r50, r100)) + extra
+    for a, b in pairs:
+        assert gflib.trigger_rule(a, b, pol) == O.trigger_rule(a, b), (a, b)
+
+
+def test_trigger_rule_golden_rows(gflib):
+    here = os.path.join(ROOT, "tests", "golden")
+    for fname, cols in (("false_keep_rows.txt", (2, 3, 4)), ("trigger_boundaries.txt", (0, 1, 2))):
+        for line in open(os.path.join(here, fname)):
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            f = line.split()
+            r50, r100, out = float(f[cols[0]]), float(f[cols[1]]), f[cols[2]]
+            assert gflib.trigger_rule(r50, r100) == (out == "escalate")
+
+
+def test_probe_features_match_oracle(gflib):
+    hist = list(np.geomspace(1.0, 1e-7, 140))
+    for k_stop in (0, 10, 49, 50, 51, 99, 100, 139):
+        assert gflib.probe_features(hist, k_stop) == O.probe_features(np.array(hist), k_stop)
+
+
+def test_policy_defaults(gflib):
+    p = gflib.policy_defaults()
+    assert (p.rho0, p.tau, p.kmax, p.probe_iters) == (1e-6, 1e-6, 200, 100)
+    assert [p.ladder[i] for i in range(p.n_ladder)] == [1e-5, 1e-4, 1e-3]
+    assert (p.r50_escalate, p.r100_stall, p.plateau_ratio) == (1e-2, 1e-4, 0.6)
+    assert (p.solve.restart, p.solve.nu1, p.solve.nu2, p.solve.omega) == (30, 2, 2, 0.6)
+    p2 = gflib.policy_defaults(ladder=[1e-3, 1e-2], rho0=1e-12, solve_prec=gflib.GF_MIXED)
+    assert p2.n_ladder == 2 and p2.rho0 == 1e-12 and p2.solve.prec == gflib.GF_MIXED
+
+
+def test_missing_library_fails_loudly(gflib, monkeypatch):
+    monkeypatch.setattr(gflib, "_LIB", None)
+    monkeypatch.setattr(gflib, "LIB_PATH", "/nonexistent/libgf_b300.so")
+    with pytest.raises(RuntimeError):
+        gflib.lib()

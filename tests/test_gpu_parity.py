@@ -1,0 +1,345 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on identical
+seeded inputs.
+
+Tolerances: FP64 operator / guard / sensitivity 1e-10 relative (the stated bar);
+FP64 V-cycle 1e-9 relative (a composite of smoothers, transfers and a dense inverse
+whose rounding is amplified by the coarse condition number); FP32/BF16 paths are
+compared against the oracle evaluated on the same BF16-rounded density, with FP32
+tolerances; whole FGMRES solves to +-1 iteration and 1e-6 relative on the history
+(the cross-platform agreement the paper reports, Sec. 4.5.2), and every GPU
+solution is re-checked by the oracle's own FP64 guard.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gf_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gf():
+    from paper_2607_26382_b300 import build
+    build.build()
+    import paper_2607_26382_b300 as gf
+    return gf
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def bf16_round(x):
+    return torch.as_tensor(x).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def relerr(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+GRIDS = [(16, 8, 8, 3), (24, 10, 6, 2), (2, 2, 2, 1), (1, 2, 2, 1), (38, 6, 4, 2), (8, 4, 4, 3)]
+
+
+def make(gf, nx, ny, nz, L, seed=0, rho_min=1e-3, p=3.0, kind="uniform"):
+    if kind == "uniform":
+        rho = synth.uniform_density(nx, ny, nz, seed)
+    elif kind == "bernoulli":
+        rho = synth.bernoulli_density(nx, ny, nz, seed, 0.35)
+    else:
+        rho = synth.smoothed_gaussian_density(nx, ny, nz, seed)
+    g = gf.create_grid(nx, ny, nz, levels=L)
+    g.set_density(dev(rho), p)
+    g.set_floor(rho_min)
+    m = O.Mesh(nx, ny, nz)
+    return g, m, rho
+
+
+# ------------------------------------------------------------- a1: integer work --
+@pytest.mark.parametrize("nx,ny,nz,L", GRIDS)
+def test_load_and_mask_bit_exact(gf, nx, ny, nz, L):
+    g = gf.create_grid(nx, ny, nz, levels=L)
+    m = O.Mesh(nx, ny, nz)
+    f = torch.full((g.n_dof,), 7.0, dtype=torch.float64, device="cuda")
+    g.cantilever_load(f)
+    assert np.array_equal(host(f), O.cantilever_load(m))
+    mask = torch.zeros(g.n_dof, dtype=torch.uint8, device="cuda")
+    g.free_mask(mask)
+    assert np.array_equal(mask.cpu().numpy().astype(bool), m.free)
+    assert (g.n_dof, g.n_elem, g.n_nodes) == (m.n_dof, m.n_elem, m.n_nodes)
+
+
+# ------------------------------------------------------------- a4: K*u ----------
+@pytest.mark.parametrize("nx,ny,nz,L", GRIDS)
+@pytest.mark.parametrize("p", [3.0, 4.5])
+def test_apply_K_fp64_parity(gf, nx, ny, nz, L, p):
+    g, m, rho = make(gf, nx, ny, nz, L, seed=nx, p=p)
+    u = synth.random_vector(m.n_dof, 11)
+    y = torch.full((g.n_dof,), np.nan, dtype=torch.float64, device="cuda")
+    g.apply_K(dev(u), y)
+    E = O.young_modulus(rho, 1e-3, p)
+    ref = O.apply_K(m, E, O.element_stiffness(), u)
+    got = host(y)
+    assert relerr(got, ref) <= 1e-10
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert np.all(got[m.fixed] == 0.0)
+
+
+@pytest.mark.parametrize("nx,ny,nz,L", GRIDS[:3])
+def test_apply_K_f32_parity(gf, nx, ny, nz, L):
+    g, m, rho = make(gf, nx, ny, nz, L, seed=3)
+    u = synth.random_vector(m.n_dof, 5).astype(np.float32)
+    y = torch.zeros(g.n_dof, dtype=torch.float32, device="cuda")
+    g.apply_K_f32(dev(u, torch.float32), y)
+    E = O.young_modulus(bf16_round(rho), 1e-3, 3.0)
+    ref = O.apply_K(m, E, O.element_stiffness(), u.astype(np.float64))
+    assert relerr(host(y), ref) <= 2e-5
+
+
+def test_apply_K_linear_and_symmetric_on_gpu(gf):
+    g, m, rho = make(gf, 12, 6, 6, 2, seed=1)
+    a, b = synth.random_vector(m.n_dof, 1), synth.random_vector(m.n_dof, 2)
+    ya, yb, yab = (torch.zeros(g.n_dof, dtype=torch.float64, device="cuda") for _ in range(3))
+    g.apply_K(dev(a), ya)
+    g.apply_K(dev(b), yb)
+    g.apply_K(dev(2 * a - b), yab)
+    A, B, AB = host(ya), host(yb), host(yab)
+    assert relerr(AB, 2 * A - B) < 1e-13
+    am, bm = np.where(m.fixed, 0, a), np.where(m.fixed, 0, b)
+    assert abs(am @ B - bm @ A) < 1e-12 * np.linalg.norm(A) * np.linalg.norm(b)
+
+
+# ------------------------------------------------------------- a5: V-cycle ------
+@pytest.mark.parametrize("nx,ny,nz,L", [(16, 8, 8, 3), (24, 12, 8, 3), (8, 4, 4, 2), (2, 2, 2, 1)])
+def test_vcycle_fp64_parity(gf, nx, ny, nz, L):
+    g, m, rho = make(gf, nx, ny, nz, L, seed=2)
+    E = O.young_modulus(rho, 1e-3, 3.0)
+    H = O.build_hierarchy(m, E, L)
+    v = synth.random_vector(m.n_dof, 9)
+    z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.vcycle(dev(v), z, gf.GF_FP64)
+    vm = np.where(m.fixed, 0, v)
+    ref = O.vcycle(H, vm)
+    assert relerr(host(z), ref) <= 1e-9
+
+
+def test_vcycle_mixed_parity(gf):
+    nx, ny, nz, L = 16, 8, 8, 3
+    g, m, rho = make(gf, nx, ny, nz, L, seed=2)
+    # the mixed V-cycle builds its level moduli from the BF16 density in FP32; its
+    # coarsest inverse comes from the FP64 moduli
+    E16 = O.young_modulus(bf16_round(rho), 1e-3, 3.0)
+    H = O.build_hierarchy(m, E16, L)
+    H64 = O.build_hierarchy(m, O.young_modulus(rho, 1e-3, 3.0), L)
+    H.levels[-1].chol = H64.levels[-1].chol
+    v = np.where(m.fixed, 0, synth.random_vector(m.n_dof, 9))
+    z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.vcycle(dev(v), z, gf.GF_MIXED)
+    assert relerr(host(z), O.vcycle(H, v)) <= 1e-4
+
+
+# ------------------------------------------------------------- a6/a7: solve ------
+def _oracle_solve(m, rho, rho_min, L, f, kmax=200, restart=30, tol=1e-6):
+    setup = O.SolverSetup(m, rho, p=3.0, n_levels=L, restart=restart)
+    return O.solve_at_floor(setup, f, rho_min, kmax, tol)
+
+
+@pytest.mark.parametrize("case", [(16, 8, 8, 3, "uniform", 1e-3, 30), (16, 8, 8, 3, "bernoulli", 1e-6, 30),
+                                  (24, 12, 8, 3, "smooth", 1e-3, 8)])
+def test_solve_fp64_parity(gf, case):
+    nx, ny, nz, L, kind, rm, restart = case
+    g, m, rho = make(gf, nx, ny, nz, L, seed=4, rho_min=rm, kind=kind)
+    f = O.cantilever_load(m)
+    res, E, K0 = _oracle_solve(m, rho, rm, L, f, restart=restart)
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    out = g.solve(dev(f), u, restart=restart, kmax=200, tol=1e-6, prec=gf.GF_FP64)
+    assert abs(out["iters"] - res.iters) <= 1
+    assert out["flag"] == res.flag
+    k = min(out["iters"], res.iters)
+    h_gpu, h_ref = np.array(out["history"][:k + 1]), res.history[:k + 1]
+    assert np.all(np.abs(h_gpu - h_ref) <= 1e-6 * h_ref + 1e-15)
+    # the oracle's own guard on the GPU's solution, and the GPU guard against it. At a
+    # converged u, f - K u cancels: a 1e-10 relative error in K u moves eta by up to
+    # 1e-10 * ||K u|| / ||f||, so that is the bound (not 1e-10 * eta).
+    uh = host(u)
+    eta_oracle = O.true_residual(m, E, K0, f, uh)
+    eta_gpu = g.true_residual(dev(f), u)
+    if res.flag == O.CONVERGED:
+        assert eta_oracle <= 1.5e-6
+    ku = np.linalg.norm(O.apply_K(m, E, K0, uh))
+    assert abs(eta_gpu - eta_oracle) <= 1e-10 * ku / np.linalg.norm(f)
+
+
+def test_solve_mixed_converges_and_guard(gf):
+    nx, ny, nz, L = 16, 8, 8, 3
+    g, m, rho = make(gf, nx, ny, nz, L, seed=0, rho_min=1e-3)
+    f = O.cantilever_load(m)
+    res, E, K0 = _oracle_solve(m, rho, 1e-3, L, f)
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    out = g.solve(dev(f), u, prec=gf.GF_MIXED)
+    assert out["flag"] == gf.GF_FLAG_CONVERGED and abs(out["iters"] - res.iters) <= 2
+    eta = O.true_residual(m, E, K0, f, host(u))
+    assert eta <= 1.5e-6
+    # error against the FP64 oracle solution: u, compliance, sensitivity
+    ug, ur = host(u), res.x
+    assert np.linalg.norm(ug - ur) <= 1e-4 * np.linalg.norm(ur)
+    assert abs(f @ ug - f @ ur) <= 1e-5 * abs(f @ ur)
+
+
+def test_true_residual_parity_and_one_apply(gf):
+    g, m, rho = make(gf, 16, 8, 8, 3, seed=1)
+    f = O.cantilever_load(m)
+    u = synth.random_vector(m.n_dof, 3) * 1e-2
+    E = O.young_modulus(rho, 1e-3, 3.0)
+    g.reset_stats()
+    eta = g.true_residual(dev(f), dev(u))
+    assert g.stats()["apply_K_fp64"] == 1     # the guard costs exactly one operator application
+    ref = O.true_residual(m, E, O.element_stiffness(), f, u)
+    assert abs(eta - ref) <= 1e-12 * ref
+    assert g.true_residual(dev(f), torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")) == 1.0
+
+
+def test_solve_edge_cases(gf):
+    g, m, rho = make(gf, 8, 4, 4, 2, seed=1)
+    f = dev(O.cantilever_load(m))
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    out = g.solve(f, u, kmax=0)
+    assert out["iters"] == 0 and out["flag"] == gf.GF_FLAG_MAX_ITERS and out["history"] == [1.0]
+    assert torch.all(u == 0)
+    out = g.solve(f, u, restart=1, kmax=5)          # restart every step
+    assert out["iters"] == 5 and out["flag"] == gf.GF_FLAG_MAX_ITERS
+    ref = O.SolverSetup(m, rho, p=3.0, n_levels=2, restart=1)
+    r, _, _ = O.solve_at_floor(ref, O.cantilever_load(m), 1e-3, 5, 1e-6)
+    assert np.allclose(out["history"], r.history, rtol=1e-8)
+    # restart from the previous iterate: history[0] is its true residual
+    eta0 = g.true_residual(f, u)
+    out2 = g.solve(f, u, restart=30, kmax=3)
+    assert abs(out2["history"][0] - eta0) <= 1e-12 * eta0
+
+
+def test_errors(gf):
+    with pytest.raises(gf.GFError):
+        gf.create_grid(16, 7, 8, levels=1)           # odd ny
+    with pytest.raises(gf.GFError):
+        gf.create_grid(12, 8, 8, levels=4)           # not divisible
+    g = gf.create_grid(4, 2, 2, levels=1)
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    with pytest.raises(gf.GFError) as e:
+        g.apply_K(u, u.clone())
+    assert e.value.code == -6                         # GF_ERR_STATE
+    bad = np.full(g.n_elem, 0.5)
+    bad[3] = np.nan
+    with pytest.raises(gf.GFError) as e:
+        g.set_density(dev(bad), 3.0)
+    assert e.value.code == -4                         # GF_ERR_NONFINITE
+    bad[3] = 1.5
+    with pytest.raises(gf.GFError):
+        g.set_density(dev(bad), 3.0)
+    with pytest.raises(TypeError):
+        g.set_density(dev(np.ones(g.n_elem), torch.float32), 3.0)
+
+
+# ------------------------------------------------------------- a8: policy --------
+@pytest.mark.parametrize("seed,q", [(43, 0.35), (47, 0.30)])
+def test_select_floor_parity(gf, seed, q):
+    nx, ny, nz, L = 16, 8, 8, 3
+    rho = synth.bernoulli_density(nx, ny, nz, seed, q)
+    m = O.Mesh(nx, ny, nz)
+    f = O.cantilever_load(m)
+    setup = O.SolverSetup(m, rho, p=3.0, n_levels=L)
+    ladder = [1e-5, 1e-4, 1e-3]
+    ref = O.select_floor(setup, f, 1e-9, ladder, tau=1e-6, kmax=60, probe_iters=100)
+    g = gf.create_grid(nx, ny, nz, levels=L)
+    g.set_density(dev(rho), 3.0)
+    pol = gf.policy_defaults(rho0=1e-9, ladder=ladder, kmax=60)
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    out = g.select_floor(dev(f), u, pol)
+    assert abs(out["r50"] - ref.r50) <= 1e-4 * ref.r50
+    assert abs(out["r100"] - ref.r100) <= 1e-4 * ref.r100
+    assert out["escalated"] == ref.escalated
+    assert out["status"] == ref.status and out["floor_index"] == ref.floor_index
+    assert len(out["attempts"]) == len(ref.attempts)
+    for a, b in zip(out["attempts"], ref.attempts):
+        assert a["rho_min"] == b.rho_min and abs(a["iters"] - b.iters) <= 1
+        assert a["accepted"] == b.accepted
+    if out["status"] == gf.GF_ACCEPTED:
+        E = O.young_modulus(rho, out["rho_min"], 3.0)
+        assert O.true_residual(m, E, O.element_stiffness(), f, host(u)) <= 1e-6 * (1 + 1e-9)
+
+
+def test_select_floor_no_admissible(gf):
+    nx, ny, nz, L = 8, 4, 4, 2
+    rho = synth.bernoulli_density(nx, ny, nz, 1, 0.3)
+    g = gf.create_grid(nx, ny, nz, levels=L)
+    g.set_density(dev(rho), 3.0)
+    f = dev(O.cantilever_load(O.Mesh(nx, ny, nz)))
+    pol = gf.policy_defaults(rho0=1e-6, ladder=[1e-5], kmax=1, probe_iters=1, selector=gf.GF_SEL_FULL)
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    out = g.select_floor(f, u, pol)
+    assert out["status"] == gf.GF_NO_ADMISSIBLE_FLOOR and out["floor_index"] == -1
+    assert len(out["attempts"]) == 2 and not any(a["accepted"] for a in out["attempts"])
+
+
+# ------------------------------------------------------------- a12: sensitivity ---
+def test_sensitivity_parity(gf):
+    g, m, rho = make(gf, 12, 6, 6, 2, seed=5)
+    u = synth.random_vector(m.n_dof, 4)
+    dc = torch.zeros(g.n_elem, dtype=torch.float64, device="cuda")
+    g.sensitivity(dev(u), dc)
+    ref = O.sensitivity(m, rho, 1e-3, 3.0, O.element_stiffness(), u)
+    assert relerr(host(dc), ref) <= 1e-10
+
+
+# ------------------------------------------------------------- full-size samples --
+@pytest.mark.parametrize("dims", [(96, 48, 48, 4), (192, 96, 96, 5)])
+def test_full_size_apply_sampled(gf, dims):
+    nx, ny, nz, L = dims
+    rho = synth.smoothed_gaussian_density(nx, ny, nz, 0) if nx == 96 else synth.uniform_density(nx, ny, nz, 0)
+    g = gf.create_grid(nx, ny, nz, levels=L)
+    g.set_density(dev(rho), 3.0)
+    g.set_floor(1e-6)
+    u = synth.random_vector(g.n_dof, 1)
+    y = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.apply_K(dev(u), y)
+    yh = host(y).reshape(-1, 3)
+    rng = np.random.default_rng(0)
+    nodes = rng.choice(g.n_nodes, 300, replace=False)
+    nodes[:3] = [0, g.n_nodes - 1, nx]          # corners / fixed face
+    E = O.young_modulus(rho, 1e-6, 3.0)
+    ref = _apply_at_nodes(nx, ny, nz, E, u, nodes)
+    scale = np.abs(ref).max()
+    assert np.abs(yh[nodes] - ref).max() <= 1e-10 * scale
+
+
+def _apply_at_nodes(nx, ny, nz, E, u, nodes):
+    """Oracle K*u at sampled nodes on a big grid without building the full mesh arrays."""
+    K0 = O.element_stiffness()
+    out = np.zeros((len(nodes), 3))
+    NX, NY = nx + 1, ny + 1
+    for t, n in enumerate(nodes):
+        i, j, k = n % NX, (n // NX) % NY, n // (NX * NY)
+        if i == 0:
+            continue
+        acc = np.zeros(3)
+        for a, (ox, oy, oz) in enumerate(O.LOCAL_NODES):
+            ex, ey, ez = i - ox, j - oy, k - oz
+            if not (0 <= ex < nx and 0 <= ey < ny and 0 <= ez < nz):
+                continue
+            e = ex + nx * (ey + ny * ez)
+            ue = np.zeros(24)
+            for b, (bx, by, bz) in enumerate(O.LOCAL_NODES):
+                ni = ex + bx
+                if ni == 0:
+                    continue
+                node = ni + NX * ((ey + by) + NY * (ez + bz))
+                ue[3 * b:3 * b + 3] = u[3 * node:3 * node + 3]
+            acc += E[e] * (K0[3 * a:3 * a + 3] @ ue)
+        out[t] = acc
+    return out
