@@ -100,6 +100,10 @@ typedef struct {
     int    checkpoint_a, checkpoint_b; /* 50, 100 */
     int    selector;                   /* GF_SEL_* */
     int    first_index;                /* for GF_SEL_GIVEN */
+    int    fuse_probe;                 /* 1: read the probe features off the running solve at
+                                          rho0 (bit-identical to a separate probe followed by an
+                                          independent solve, because the solver is deterministic);
+                                          0: run the probe and the rho0 solve separately */
     gf_solve_opts solve;               /* restart, prec, smoother (kmax/tol/history ignored) */
 } gf_policy;
 

@@ -53,7 +53,7 @@ class Policy(ctypes.Structure):
                 ("tau", c_double), ("kmax", c_int), ("probe_iters", c_int),
                 ("r50_escalate", c_double), ("r100_stall", c_double), ("plateau_ratio", c_double),
                 ("checkpoint_a", c_int), ("checkpoint_b", c_int), ("selector", c_int),
-                ("first_index", c_int), ("solve", SolveOpts)]
+                ("first_index", c_int), ("fuse_probe", c_int), ("solve", SolveOpts)]
 
 
 class Attempt(ctypes.Structure):

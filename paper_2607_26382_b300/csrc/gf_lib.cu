@@ -12,6 +12,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <string>
 #include <vector>
 #include <algorithm>
@@ -127,6 +128,14 @@ struct gf_grid {
     int nbr = 0;                      // blocks for reductions
     cudaEvent_t ev[3];
     gf_stats stats{};
+    // CUDA graphs of the Arnoldi steps (one per j), captured on cap_stream
+    cudaStream_t cur_stream = nullptr;   // where launch() enqueues (cap_stream while capturing)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t step_exec[gf::KRY_MMAX] = {};
+    long long step_nodes[gf::KRY_MMAX] = {};
+    int gkey_prec = -1, gkey_nu1 = -1, gkey_nu2 = -1;
+    double gkey_omega = -1.0;
+    bool use_graphs = true;
 };
 
 namespace {
@@ -134,7 +143,7 @@ namespace {
 template <typename... KArgs, typename... Args>
 int launch(gf_grid* g, dim3 grid, dim3 block, void (*kern)(KArgs...), Args... args)
 {
-    kern<<<grid, block, 0, g->stream>>>(args...);
+    kern<<<grid, block, 0, g->cur_stream>>>(args...);
     g->stats.kernel_launches++;
     CK(cudaGetLastError());
     return GF_OK;
@@ -296,9 +305,8 @@ int build_coarse_inverse(gf_grid* g)
 {
     Level& c = g->lv[g->L - 1];
     const long long n = g->nc;
-    CK(cudaMemsetAsync(g->Ainv, 0, sizeof(double) * n * n, g->stream));
     gf::K0Param<double> K = g->K0d;   // the level's E64 already carries h
-    LAUNCH(g, nblk(c.nel * 576), 256, gf::coarse_assemble_kernel, c.E64, g->Ainv, c.dims(), K);
+    LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, c.E64, g->Ainv, c.dims(), K);
     LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, g->Ainv, c.dims());
     for (int k = 0; k < n; ++k) {
         LAUNCH(g, nblk(n), 256, gf::gj_prepare_kernel, g->Ainv, g->gjcol, g->gjrow, (int)n, k);
@@ -307,8 +315,18 @@ int build_coarse_inverse(gf_grid* g)
     return GF_OK;
 }
 
+void drop_graphs(gf_grid* g)
+{
+    for (int j = 0; j < gf::KRY_MMAX; ++j) {
+        if (g->step_exec[j]) cudaGraphExecDestroy(g->step_exec[j]);
+        g->step_exec[j] = nullptr;
+        g->step_nodes[j] = 0;
+    }
+}
+
 int ensure_krylov(gf_grid* g, int m, int kmax)
 {
+    if (m > g->m_alloc || kmax + 1 > g->hist_cap) drop_graphs(g);
     if (m > g->m_alloc) {
         cudaFree(g->V);
         cudaFree(g->Z);
@@ -405,8 +423,55 @@ int cycle_start(gf_grid* g, const double* f, const double* x, bool x_zero, bool 
     return GF_OK;
 }
 
+// Replay the captured graph of Arnoldi step j (capturing it on first use).
+int run_step(gf_grid* g, int j, const gf_solve_opts* o)
+{
+    if (!g->use_graphs) return arnoldi_step(g, j, o);
+    if (g->gkey_prec != o->prec || g->gkey_nu1 != o->nu1 || g->gkey_nu2 != o->nu2 || g->gkey_omega != o->omega) {
+        drop_graphs(g);
+        g->gkey_prec = o->prec;
+        g->gkey_nu1 = o->nu1;
+        g->gkey_nu2 = o->nu2;
+        g->gkey_omega = o->omega;
+    }
+    if (!g->step_exec[j]) {
+        const gf_stats before = g->stats;
+        CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+        g->cur_stream = g->cap_stream;
+        const int r = arnoldi_step(g, j, o);
+        g->cur_stream = g->stream;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+        if (r != GF_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        CK(e);
+        const cudaError_t ei = cudaGraphInstantiate(&g->step_exec[j], graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ei);
+        g->step_nodes[j] = g->stats.kernel_launches - before.kernel_launches;
+        g->stats = before;
+    }
+    CK(cudaGraphLaunch(g->step_exec[j], g->stream));
+    g->stats.kernel_launches += g->step_nodes[j];
+    g->stats.apply_K_fp64 += 1;
+    g->stats.vcycles += 1;
+    return GF_OK;
+}
+
+// Optional pause after `at` Arnoldi steps: the probe of Algorithm 1 read off the
+// running solve. Because the solver is deterministic, the first `at` steps of the
+// selected solve at rho0 are the probe's steps, bit for bit.
+struct ProbeHook {
+    int at = -1;
+    const gf_policy* pol = nullptr;
+    bool decided = false, escalate = false;
+    double r50 = 0.0, r100 = 0.0;
+};
+
 int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, gf_solve_info* info,
-               bool x_zero, double* host_hist)
+               bool x_zero, double* host_hist, ProbeHook* hook = nullptr)
 {
     const int m = o->restart;
     RET(ensure_krylov(g, m, o->kmax));
@@ -415,7 +480,8 @@ int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, g
     LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, double>), u, u, g->ndof, NX0, nullptr);
     LAUNCH(g, 1, 1, init_state_kernel, g->st, o->kmax, m, o->tol);
     *g->host_status = gf::KS_RUN;
-    bool first = true;
+    bool first = true, aborted = false;
+    long long launched = 0;
     HostState hs{};
     for (;;) {
         RET(cycle_start(g, f, u, x_zero && first, first));
@@ -424,13 +490,32 @@ int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, g
         CK(cudaStreamSynchronize(g->stream));
         if (*(volatile int*)g->host_status != gf::KS_RUN) break;
         for (int j = 0; j < m; ++j) {
-            RET(arnoldi_step(g, j, o));
+            RET(run_step(g, j, o));
+            ++launched;
             CK(cudaEventRecord(g->ev[j % 3], g->stream));
+            if (hook && !hook->decided && launched == hook->at) {
+                RET(read_state(g, &hs));
+                if (hs.status == gf::KS_RUN) {
+                    double h2[2];
+                    const int ia = std::min(hook->pol->checkpoint_a, hs.k), ib = std::min(hook->pol->checkpoint_b, hs.k);
+                    CK(cudaMemcpy(&h2[0], g->hist + ia, sizeof(double), cudaMemcpyDeviceToHost));
+                    CK(cudaMemcpy(&h2[1], g->hist + ib, sizeof(double), cudaMemcpyDeviceToHost));
+                    hook->decided = true;
+                    hook->r50 = h2[0];
+                    hook->r100 = h2[1];
+                    hook->escalate = gf_trigger_rule(h2[0], h2[1], hook->pol) == 1;
+                    if (hook->escalate) {
+                        aborted = true;
+                        break;
+                    }
+                }
+            }
             if (j >= 1) {
                 CK(cudaEventSynchronize(g->ev[(j - 1) % 3]));
                 if (*(volatile int*)g->host_status != gf::KS_RUN) break;
             }
         }
+        if (aborted) break;
         LAUNCH(g, 1, 1, gf::backsolve_kernel, g->st);
         LAUNCH(g, 2 * g->sms, 256, gf::update_x_kernel, u, g->Z, g->ndof, g->ndof, g->st);
         RET(read_state(g, &hs));
@@ -498,6 +583,7 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     g->nx = nx; g->ny = ny; g->nz = nz; g->L = levels;
     g->h = h; g->E0 = E0; g->nu = nu;
     g->stream = (cudaStream_t)stream;
+    g->cur_stream = g->stream;
     auto fail = [&](int code) { gf_destroy_grid(g); return code; };
     if (cudaGetDevice(&g->device) != cudaSuccess) return fail(set_err(GF_ERR_CUDA, "cudaGetDevice"));
     if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
@@ -543,6 +629,13 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     for (int i = 0; i < 3; ++i)
         if (cudaEventCreateWithFlags(&g->ev[i], cudaEventDisableTiming) != cudaSuccess)
             return fail(set_err(GF_ERR_CUDA, "event"));
+    if (cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(set_err(GF_ERR_CUDA, "capture stream"));
+    g->cur_stream = g->stream;
+    {
+        const char* e = getenv("GF_GRAPHS");
+        g->use_graphs = !(e && e[0] == '0');
+    }
     *out = g;
     return GF_OK;
 }
@@ -562,6 +655,8 @@ int gf_destroy_grid(gf_grid* g)
     cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Z); cudaFree(g->hist);
     cudaFree(g->xsave);
     if (g->host_status) cudaFreeHost(g->host_status);
+    drop_graphs(g);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     for (int i = 0; i < 3; ++i)
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
     delete g;
@@ -707,6 +802,7 @@ void gf_policy_defaults(gf_policy* pol)
     pol->checkpoint_b = 100;
     pol->selector = GF_SEL_RULE;
     pol->first_index = 0;
+    pol->fuse_probe = 1;
     pol->solve.restart = 30;
     pol->solve.kmax = 200;
     pol->solve.tol = 1e-6;
@@ -753,7 +849,54 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
     for (int i = 0; i < pol->n_ladder; ++i) floors[i + 1] = pol->ladder[i];
     const int nf = pol->n_ladder + 1;
     int start = 0;
-    if (pol->selector == GF_SEL_RULE) {
+    if (pol->selector == GF_SEL_RULE && pol->fuse_probe) {
+        // Probe fused with the rho0 solve: run the rho0 solve with budget kmax and read
+        // r50/r100 off its history after probe_iters steps (or at its stop).
+        RET(gf_set_floor(g, pol->rho0));
+        gf_solve_opts so = o;
+        so.kmax = std::max(pol->kmax, pol->probe_iters);
+        const bool cap = pol->probe_iters > pol->kmax;   // the probe may run past kmax
+        gf_solve_opts so2 = o;
+        so2.kmax = pol->kmax;
+        ProbeHook hook;
+        hook.at = pol->probe_iters;
+        hook.pol = pol;
+        std::vector<double> hist((size_t)so.kmax + 1);
+        gf_solve_info si{};
+        CK(cudaMemsetAsync(u, 0, sizeof(double) * g->ndof, g->stream));
+        RET(solve_impl(g, f, u, cap ? &so : &so2, &si, true, hist.data(), &hook));
+        if (hook.decided) {
+            info->r50 = hook.r50;
+            info->r100 = hook.r100;
+            info->escalated = hook.escalate;
+            info->probe_iters_run = pol->probe_iters;
+        } else {
+            info->probe_iters_run = std::min(si.iters, pol->probe_iters);
+            RET(gf_probe_features(hist.data(), si.iters, pol, &info->r50, &info->r100));
+            info->escalated = gf_trigger_rule(info->r50, info->r100, pol);
+        }
+        start = info->escalated ? 1 : 0;
+        if (!info->escalated && !cap) {
+            // the rho0 solve is the first candidate's selected solve
+            double eta = 0.0;
+            RET(guard_impl(g, f, u, &eta));
+            gf_attempt& a = info->attempts[info->n_attempts++];
+            a.rho_min = pol->rho0;
+            a.iters = si.iters;
+            a.flag = si.flag;
+            a.stop_estimate = si.stop_estimate;
+            a.eta = eta;
+            a.accepted = eta <= pol->tau;
+            if (a.accepted) {
+                info->status = GF_ACCEPTED;
+                info->floor_index = 0;
+                info->rho_min = pol->rho0;
+                info->eta = eta;
+                return GF_OK;
+            }
+            start = 1;
+        }
+    } else if (pol->selector == GF_SEL_RULE) {
         RET(gf_set_floor(g, pol->rho0));
         std::vector<double> hist((size_t)pol->probe_iters + 1);
         gf_solve_opts po = o;
@@ -776,6 +919,7 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
     }
     info->status = GF_NO_ADMISSIBLE_FLOOR;
     for (int idx = start; idx < nf; ++idx) {
+        if (idx == 0 && info->n_attempts > 0) continue;   // rho0 already attempted (fused probe)
         const double rm = floors[idx];
         if (!(g->has_floor && g->rho_min == rm)) RET(gf_set_floor(g, rm));
         o.kmax = pol->kmax;

@@ -352,29 +352,37 @@ __global__ void density_check_kernel(const double* __restrict__ rho, __nv_bfloat
     r16[e] = __double2bfloat16(r);
 }
 
-// Dense coarsest operator (all DOFs of the coarsest level, row-major n x n):
-// A += E_e h K0 element by element.
+// Dense coarsest operator (all DOFs of the coarsest level, row-major n x n), one
+// thread per entry: A[r][c] = sum over the elements e containing both nodes of
+// E_e h K0[3 a_r + c_r][3 a_c + c_c], summed in a fixed element order so that the
+// matrix (and its inverse) is bit-reproducible.
 __global__ void coarse_assemble_kernel(const double* __restrict__ E, double* __restrict__ A, GridDims d,
                                        const __grid_constant__ K0Param<double> K0)
 {
-    const long long ne = (long long)d.nx * d.ny * d.nz;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ne * 576) return;
-    const long long e = t / 576;
-    const int pq = (int)(t % 576), p = pq / 24, q = pq % 24;
-    const int ex = (int)(e % d.nx);
-    const long long tt = e / d.nx;
-    const int ey = (int)(tt % d.ny), ez = (int)(tt / d.ny);
-    const int NX = d.nx + 1, NY = d.ny + 1;
-    const int NZ = d.nz + 1;
+    const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
     const long long ndof = 3LL * NX * NY * NZ;
-    const int ap = p / 3, cp = p % 3, aq = q / 3, cq = q % 3;
-    // local index -> offsets
-    const int oxp = (ap == 1 || ap == 2 || ap == 5 || ap == 6), oyp = (ap == 2 || ap == 3 || ap == 6 || ap == 7), ozp = ap >= 4;
-    const int oxq = (aq == 1 || aq == 2 || aq == 5 || aq == 6), oyq = (aq == 2 || aq == 3 || aq == 6 || aq == 7), ozq = aq >= 4;
-    const long long np_ = (ex + oxp) + (long long)NX * ((ey + oyp) + (long long)NY * (ez + ozp));
-    const long long nq_ = (ex + oxq) + (long long)NX * ((ey + oyq) + (long long)NY * (ez + ozq));
-    atomicAdd(&A[(3 * np_ + cp) * ndof + 3 * nq_ + cq], E[e] * K0.k[pq]);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ndof * ndof) return;
+    const long long r = t / ndof, c = t % ndof;
+    const long long nr = r / 3, nc = c / 3;
+    const int cr = (int)(r % 3), cc = (int)(c % 3);
+    const int ir = (int)(nr % NX), jr = (int)((nr / NX) % NY), kr = (int)(nr / ((long long)NX * NY));
+    const int ic = (int)(nc % NX), jc = (int)((nc / NX) % NY), kc = (int)(nc / ((long long)NX * NY));
+    double s = 0.0;
+    if (abs(ir - ic) <= 1 && abs(jr - jc) <= 1 && abs(kr - kc) <= 1) {
+        const int x0 = max(max(ir, ic) - 1, 0), x1 = min(min(ir, ic), d.nx - 1);
+        const int y0 = max(max(jr, jc) - 1, 0), y1 = min(min(jr, jc), d.ny - 1);
+        const int z0 = max(max(kr, kc) - 1, 0), z1 = min(min(kr, kc), d.nz - 1);
+        for (int ez = z0; ez <= z1; ++ez)
+            for (int ey = y0; ey <= y1; ++ey)
+                for (int ex = x0; ex <= x1; ++ex) {
+                    const int ar = local_index(ir - ex, jr - ey, kr - ez);
+                    const int ac = local_index(ic - ex, jc - ey, kc - ez);
+                    s = fma(E[ex + (long long)d.nx * (ey + (long long)d.ny * ez)],
+                            K0.k[(3 * ar + cr) * 24 + 3 * ac + cc], s);
+                }
+    }
+    A[t] = s;
 }
 
 // Fixed DOFs (nodes with i == 0): zero row and column, unit diagonal.

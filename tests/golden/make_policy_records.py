@@ -19,7 +19,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import synth  # noqa: E402
 from oracle import gf_oracle as O  # noqa: E402
 
-WORKLOAD = dict(nx=96, ny=48, nz=48, levels=4, p=3.0, rho0=1e-6, ladder=[1e-5, 1e-4, 1e-3],
+WORKLOAD = dict(nx=96, ny=48, nz=48, levels=5, p=3.0, rho0=1e-6, ladder=[1e-5, 1e-4, 1e-3],
                 tau=1e-6, kmax=200, probe_iters=100, restart=30, sigma=2.0, floor_frac=0.4)
 
 

@@ -343,3 +343,44 @@ def _apply_at_nodes(nx, ny, nz, E, u, nodes):
             acc += E[e] * (K0[3 * a:3 * a + 3] @ ue)
         out[t] = acc
     return out
+
+
+# ------------------------------------------------------------- fused probe, graphs --
+@pytest.mark.parametrize("seed,q,rho0,kmax", [(43, 0.35, 1e-9, 60), (47, 0.30, 1e-9, 60), (1, 0.30, 1e-6, 200),
+                                              (5, 0.20, 1e-9, 40)])
+def test_fused_probe_bit_identical(gf, seed, q, rho0, kmax):
+    """Reading r50/r100 off the running rho0 solve gives exactly the separate probe's
+    decisions and the independent rho0 solve's iterate (Algorithm 1 unchanged)."""
+    nx, ny, nz, L = 16, 8, 8, 3
+    rho = dev(synth.bernoulli_density(nx, ny, nz, seed, q))
+    f = dev(O.cantilever_load(O.Mesh(nx, ny, nz)))
+    outs, us = [], []
+    for fuse in (1, 0):
+        g = gf.create_grid(nx, ny, nz, levels=L)
+        g.set_density(rho, 3.0)
+        pol = gf.policy_defaults(rho0=rho0, ladder=[1e-5, 1e-4, 1e-3], kmax=kmax, fuse_probe=fuse)
+        u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        outs.append(g.select_floor(f, u, pol))
+        us.append(u.clone())
+    a, b = outs
+    for key in ("status", "floor_index", "escalated", "r50", "r100", "eta"):
+        assert a[key] == b[key] or (np.isnan(a[key]) and np.isnan(b[key])), key
+    assert a["attempts"] == b["attempts"]
+    assert torch.equal(us[0], us[1])
+
+
+def test_graph_replay_bit_identical(gf, monkeypatch):
+    nx, ny, nz, L = 16, 8, 8, 3
+    rho = dev(synth.uniform_density(nx, ny, nz, 2))
+    f = dev(O.cantilever_load(O.Mesh(nx, ny, nz)))
+    res = []
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("GF_GRAPHS", graphs)
+        g = gf.create_grid(nx, ny, nz, levels=L)
+        g.set_density(rho, 3.0)
+        g.set_floor(1e-3)
+        u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        out = g.solve(f, u, restart=7, prec=gf.GF_MIXED)
+        res.append((out, u.clone(), g.stats()))
+    assert res[0][0] == res[1][0] and torch.equal(res[0][1], res[1][1])
+    assert res[0][2]["kernel_launches"] == res[1][2]["kernel_launches"]
