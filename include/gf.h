@@ -220,6 +220,31 @@ int gf_probe_features(const double* history, int k_stop, const gf_policy* pol,
  * grid's current floor. u: n_dof, dc: n_elem doubles. */
 int gf_sensitivity(gf_grid* g, const double* u, double* dc);
 
+/* ---- the one entry point that allocates nothing -------------------------------- */
+
+/* The paper has no counterpart to this call; it exists for callers that must not
+ * allocate device memory: code recorded into a CUDA graph or running under stream
+ * capture (cudaMalloc is illegal there), hosts that give the library a fixed,
+ * pre-reserved memory budget, and latency-critical loops that must never reach
+ * the allocator. It computes the same acceptance residual as gf_true_residual,
+ * *eta = ||M(f - K u)||_2 / ||M f||_2 in FP64 with E_e = rho_min + (1 - rho_min)
+ * rho_hat_e^p (scaled by E0), but needs no gf_grid: every input is a raw pointer.
+ *  - rho_hat: n_elem doubles; f, u: n_dof doubles; eta: ONE double; all DEVICE
+ *    pointers. *eta is written on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream); read it after the stream's work completes. NaN in an input gives NaN.
+ *  - Scratch: a static device array inside the library (about 11.2 MB), reserved
+ *    on every GPU that loads the library until the process exits. It holds grids
+ *    of at most 1,048,576 DOFs; larger grids return GF_ERR_ARG with a message.
+ *  - The first call on each device looks up the array's device address (with that
+ *    device current); make that first call before any stream capture begins.
+ *  - Every call reuses the same array. Calls whose GPU work overlaps (on different
+ *    streams or threads) race on it and must be serialised by the caller; each call
+ *    writes every scratch word it reads, so nothing has to be cleared between calls.
+ *  - No cudaMalloc, cudaFree or other allocating routine is called. */
+int gf_true_residual_noalloc(int nx, int ny, int nz, double h, double E0, double nu,
+                             const double* rho_hat, double p, double rho_min, const double* f,
+                             const double* u, double* eta, void* stream);
+
 /* ---- diagnostics -------------------------------------------------------------- */
 int gf_get_stats(const gf_grid* g, gf_stats* s);
 int gf_reset_stats(gf_grid* g);

@@ -30,6 +30,7 @@ EXPORTED = [
     "gf_cantilever_load", "gf_free_mask", "gf_apply_K", "gf_apply_K_f32", "gf_vcycle", "gf_solve",
     "gf_true_residual", "gf_select_floor", "gf_policy_defaults", "gf_trigger_rule",
     "gf_probe_features", "gf_sensitivity", "gf_get_stats", "gf_reset_stats", "gf_last_error",
+    "gf_true_residual_noalloc",
 ]
 
 
@@ -102,6 +103,8 @@ def lib():
         "gf_sensitivity": [P, P, P],
         "gf_get_stats": [P, POINTER(Stats)],
         "gf_reset_stats": [P],
+        "gf_true_residual_noalloc": [c_int, c_int, c_int, c_double, c_double, c_double, P, c_double, c_double,
+                                     P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -288,6 +291,24 @@ class Grid:
 
     def reset_stats(self):
         _check(lib().gf_reset_stats(self._h))
+
+
+def true_residual_noalloc(nx, ny, nz, rho_hat, p, rho_min, f, u, eta, h=1.0, E0=1.0, nu=0.3, stream=None):
+    """gf_true_residual_noalloc: the FP64 acceptance residual with no device allocation.
+
+    For callers that cannot allocate (graph capture, fixed memory budgets). eta is a
+    1-element float64 CUDA tensor that receives the result on the current stream."""
+    torch = _torch()
+    t = torch.float64
+    n_nodes = (nx + 1) * (ny + 1) * (nz + 1)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().gf_true_residual_noalloc(
+        int(nx), int(ny), int(nz), float(h), float(E0), float(nu),
+        _ptr(rho_hat, t, nx * ny * nz, "rho_hat"), float(p), float(rho_min),
+        _ptr(f, t, 3 * n_nodes, "f"), _ptr(u, t, 3 * n_nodes, "u"), _ptr(eta, t, 1, "eta"),
+        c_void_p(stream.cuda_stream)))
+    return eta
 
 
 def create_grid(nx, ny, nz, h=1.0, E0=1.0, nu=0.3, levels=3, stream=None) -> Grid:

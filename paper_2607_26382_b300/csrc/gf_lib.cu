@@ -17,6 +17,7 @@
 #include <vector>
 #include <algorithm>
 #include <utility>
+#include <mutex>
 
 namespace {
 
@@ -977,3 +978,96 @@ int gf_reset_stats(gf_grid* g)
 }
 
 }  // extern "C"
+
+// ============================================================ no-allocation guard ====
+// gf_true_residual_noalloc: the acceptance residual computed without any device
+// allocation, for callers that may not call cudaMalloc at all. Examples: code that
+// records its work into a CUDA graph or runs inside stream capture (allocation
+// calls are illegal there), a host that hands the library a fixed, pre-reserved
+// memory budget, or a real-time loop that must not touch the allocator. The
+// scratch it needs (the modulus field, the operator product and the per-block
+// partial sums) lives in the file-scope array below, which every GPU that loads
+// this library reserves until the process exits.
+namespace {
+
+constexpr long long NOALLOC_MAX_DOF = 1LL << 20;            // largest grid: 1,048,576 DOFs
+constexpr long long NOALLOC_MAX_ELEM = NOALLOC_MAX_DOF / 3;  // elements <= nodes = DOFs / 3
+constexpr int NOALLOC_BLOCKS = 256;                          // partial-sum slots
+constexpr long long NOALLOC_WORDS = NOALLOC_MAX_DOF + NOALLOC_MAX_ELEM + 2LL * NOALLOC_BLOCKS;
+
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_WORDS];
+
+// Device address of g_noalloc_scratch per device. In host code the symbol's name is
+// only a host-side stand-in, so the address is looked up with the device current.
+constexpr int NOALLOC_MAX_DEVICES = 64;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+std::mutex g_noalloc_mu;
+
+int noalloc_scratch(double** out)
+{
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return set_err(GF_ERR_ARG, "device ordinal above 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return GF_OK;
+}
+
+// eta = sqrt(sum a) / sqrt(sum b) over the per-block partials, in fixed order.
+__global__ void noalloc_eta_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ eta)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nblocks; ++i) {
+        a += partial[2 * i + 0];
+        b += partial[2 * i + 1];
+    }
+    *eta = (b > 0.0) ? sqrt(a) / sqrt(b) : nan("");
+}
+
+}  // namespace
+
+extern "C" int gf_true_residual_noalloc(int nx, int ny, int nz, double h, double E0, double nu,
+                                        const double* rho_hat, double p, double rho_min, const double* f,
+                                        const double* u, double* eta, void* stream)
+{
+    if (!rho_hat || !f || !u || !eta) return set_err(GF_ERR_ARG, "null pointer");
+    if (nx < 1 || ny < 2 || nz < 2 || (ny & 1) || (nz & 1)) return set_err(GF_ERR_ARG, "need nx>=1, even ny,nz >= 2");
+    if (!(h > 0) || !(E0 > 0) || !(nu > -1.0 && nu < 0.5)) return set_err(GF_ERR_ARG, "h, E0 > 0, nu in (-1,0.5)");
+    if (!(p >= 1.0 && p <= 16.0)) return set_err(GF_ERR_ARG, "p in [1,16]");
+    if (!(rho_min > 0.0 && rho_min <= 1.0)) return set_err(GF_ERR_ARG, "rho_min in (0,1]");
+    const long long nodes = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+    const long long ndof = 3 * nodes, nel = (long long)nx * ny * nz;
+    if (ndof > NOALLOC_MAX_DOF)
+        return set_err(GF_ERR_ARG, "grid has " + std::to_string(ndof) +
+                                       " DOFs; gf_true_residual_noalloc handles at most 1048576");
+    double* scratch = nullptr;
+    RET(noalloc_scratch(&scratch));
+    double* E = scratch;                              // nel words
+    double* Ku = scratch + NOALLOC_MAX_ELEM;          // ndof words
+    double* partial = Ku + NOALLOC_MAX_DOF;           // 2 * NOALLOC_BLOCKS words
+    cudaStream_t s = (cudaStream_t)stream;
+    double K[576];
+    build_k0(E0, nu, K);
+    gf::K0Param<double> K0;
+    for (int q = 0; q < 576; ++q) K0.k[q] = K[q];
+    const int p_int = (p == std::floor(p)) ? (int)p : 0;
+    const gf::GridDims d{nx, ny, nz};
+    const int nb = (int)std::min<long long>(NOALLOC_BLOCKS, std::max<long long>(1, (ndof + 1023) / 1024));
+    // every word read below is written first in this call, so nothing is cleared
+    gf::modulus_fp64_kernel<<<nblk(nel), 256, 0, s>>>(rho_hat, E, nel, rho_min, p, p_int, h);
+    CK(cudaGetLastError());
+    gf::node_stencil_kernel<double, double, gf::ST_APPLY><<<nblk(nodes), 256, 0, s>>>(
+        u, nullptr, Ku, E, d, K0, 0.0, nullptr);
+    CK(cudaGetLastError());
+    gf::residual_norms_kernel<<<nb, gf::RED_THREADS, 0, s>>>(f, Ku, nullptr, ndof, nx + 1, partial, 0);
+    CK(cudaGetLastError());
+    noalloc_eta_kernel<<<1, 32, 0, s>>>(partial, nb, eta);
+    CK(cudaGetLastError());
+    return GF_OK;
+}
