@@ -220,6 +220,32 @@ int gf_probe_features(const double* history, int k_stop, const gf_policy* pol,
  * grid's current floor. u: n_dof, dc: n_elem doubles. */
 int gf_sensitivity(gf_grid* g, const double* u, double* dc);
 
+/* ---- the optimisation loop around the solve (Sec. 3.1) --------------------------- */
+
+/* Linear-hat density filter: xt_e = sum_e' w_ee' x_e' / sum_e' w_ee', with
+ * w_ee' = max(0, r_min - |c_e - c_e'|) between element centres in cells (Sec. 3.1,
+ * "linear-hat density filter of radius r_min"). x, xt: n_elem doubles, distinct.
+ * 1 < r_min <= 8. */
+int gf_filter(gf_grid* g, const double* x, double* xt, double r_min);
+/* Its adjoint (chain rule of a sensitivity through the filter):
+ * out_e' = sum_e w_ee' gs_e / sum_e'' w_ee''. */
+int gf_filter_adjoint(gf_grid* g, const double* gs, double* out, double r_min);
+/* Optimality-criteria update with move limit and bisection on the volume
+ * multiplier (Sec. 3.1): xnew = clip(x sqrt(-dc / (lam dv)), max(0, x-move),
+ * min(1, x+move)); lam bisected on [0, 1e9] until (l2-l1)/(l1+l2) <= 1e-3 (at most
+ * 200 steps) so that mean(xnew) meets volfrac. All arrays n_elem doubles. */
+int gf_oc_update(gf_grid* g, const double* x, const double* dc, const double* dv, double volfrac,
+                 double move, double* xnew);
+/* *c (host) = f^T u (Eq. to_problem's objective), FP64, fixed summation order. */
+int gf_compliance(gf_grid* g, const double* f, const double* u, double* c);
+/* One guarded SIMP-OC iteration on the design x (n_elem, in/out): rho_hat =
+ * filter(x); gf_set_density(rho_hat, p); gf_select_floor (Algorithm 1) -> u,
+ * info; if accepted: *compliance = f^T u, dc = gf_sensitivity, chain both dc and
+ * the unit volume sensitivity through the filter adjoint, and x <- OC update.
+ * If no floor is admissible, x is left unchanged and *compliance is NaN. */
+int gf_oc_iteration(gf_grid* g, double* x, const double* f, double* u, const gf_policy* pol, double p,
+                    double volfrac, double r_min, double move, gf_select_info* info, double* compliance);
+
 /* ---- the one entry point that allocates nothing -------------------------------- */
 
 /* The paper has no counterpart to this call; it exists for callers that must not

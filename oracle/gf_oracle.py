@@ -721,3 +721,24 @@ def oc_update(x: np.ndarray, dc: np.ndarray, dv: np.ndarray, volfrac: float,
         else:
             l2 = lmid
     return xnew
+
+
+def oc_iteration(mesh: Mesh, x: np.ndarray, f: np.ndarray, p: float, volfrac: float, r_min: float,
+                 move: float, policy_kw: dict, n_levels: int):
+    """One guarded SIMP-OC iteration (Sec. 3.1 with Algorithm 1 as the state solve).
+
+    rho_hat = filter(x); select_floor on rho_hat; if accepted: C = f^T u,
+    dc = sensitivity at the accepted floor, chained through the filter adjoint
+    together with the unit volume sensitivity; x <- OC update. Returns
+    (x_new, SelectResult, C)."""
+    Hf = filter_weights(mesh, r_min)
+    rho = density_filter(Hf, x)
+    setup = SolverSetup(mesh, rho, p=p, n_levels=n_levels)
+    res = select_floor(setup, f, **policy_kw)
+    if res.status != ACCEPTED:
+        return x.copy(), res, float("nan")
+    C = compliance(f, res.u)
+    dc = sensitivity(mesh, rho, res.rho_min, p, element_stiffness(mesh.h), res.u)
+    dcx = density_filter_adjoint(Hf, dc)
+    dvx = density_filter_adjoint(Hf, np.ones(mesh.n_elem))
+    return oc_update(x, dcx, dvx, volfrac, move), res, C

@@ -30,7 +30,8 @@ EXPORTED = [
     "gf_cantilever_load", "gf_free_mask", "gf_apply_K", "gf_apply_K_f32", "gf_vcycle", "gf_solve",
     "gf_true_residual", "gf_select_floor", "gf_policy_defaults", "gf_trigger_rule",
     "gf_probe_features", "gf_sensitivity", "gf_get_stats", "gf_reset_stats", "gf_last_error",
-    "gf_true_residual_noalloc",
+    "gf_true_residual_noalloc", "gf_filter", "gf_filter_adjoint", "gf_oc_update", "gf_compliance",
+    "gf_oc_iteration",
 ]
 
 
@@ -105,6 +106,12 @@ def lib():
         "gf_reset_stats": [P],
         "gf_true_residual_noalloc": [c_int, c_int, c_int, c_double, c_double, c_double, P, c_double, c_double,
                                      P, P, P, P],
+        "gf_filter": [P, P, P, c_double],
+        "gf_filter_adjoint": [P, P, P, c_double],
+        "gf_oc_update": [P, P, P, P, c_double, c_double, P],
+        "gf_compliance": [P, P, P, POINTER(c_double)],
+        "gf_oc_iteration": [P, P, P, P, POINTER(Policy), c_double, c_double, c_double, c_double,
+                            POINTER(SelectInfo), POINTER(c_double)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -283,6 +290,44 @@ class Grid:
         t = _torch().float64
         _check(lib().gf_sensitivity(self._h, _ptr(u, t, self.n_dof, "u"), _ptr(dc, t, self.n_elem, "dc")))
         return dc
+
+    # optimisation loop
+    def filter(self, x, xt, r_min=1.5):
+        t = _torch().float64
+        _check(lib().gf_filter(self._h, _ptr(x, t, self.n_elem, "x"), _ptr(xt, t, self.n_elem, "xt"), float(r_min)))
+        return xt
+
+    def filter_adjoint(self, gs, out, r_min=1.5):
+        t = _torch().float64
+        _check(lib().gf_filter_adjoint(self._h, _ptr(gs, t, self.n_elem, "gs"), _ptr(out, t, self.n_elem, "out"),
+                                       float(r_min)))
+        return out
+
+    def oc_update(self, x, dc, dv, xnew, volfrac=0.3, move=0.2):
+        t = _torch().float64
+        n = self.n_elem
+        _check(lib().gf_oc_update(self._h, _ptr(x, t, n, "x"), _ptr(dc, t, n, "dc"), _ptr(dv, t, n, "dv"),
+                                  float(volfrac), float(move), _ptr(xnew, t, n, "xnew")))
+        return xnew
+
+    def compliance(self, f, u):
+        t = _torch().float64
+        c = c_double()
+        _check(lib().gf_compliance(self._h, _ptr(f, t, self.n_dof, "f"), _ptr(u, t, self.n_dof, "u"),
+                                   ctypes.byref(c)))
+        return c.value
+
+    def oc_iteration(self, x, f, u, policy: Policy, p=3.0, volfrac=0.3, r_min=1.5, move=0.2):
+        t = _torch().float64
+        info = SelectInfo()
+        c = c_double()
+        _check(lib().gf_oc_iteration(self._h, _ptr(x, t, self.n_elem, "x"), _ptr(f, t, self.n_dof, "f"),
+                                     _ptr(u, t, self.n_dof, "u"), ctypes.byref(policy), float(p), float(volfrac),
+                                     float(r_min), float(move), ctypes.byref(info), ctypes.byref(c)))
+        atts = [dict(rho_min=a.rho_min, iters=a.iters, flag=a.flag, stop_estimate=a.stop_estimate,
+                     eta=a.eta, accepted=bool(a.accepted)) for a in info.attempts[:info.n_attempts]]
+        return dict(status=info.status, floor_index=info.floor_index, rho_min=info.rho_min, eta=info.eta,
+                    escalated=bool(info.escalated), attempts=atts, compliance=c.value)
 
     def stats(self):
         s = Stats()

@@ -6,6 +6,7 @@
 #include "../../include/gf.h"
 #include "stencil.cuh"
 #include "krylov.cuh"
+#include "oc.cuh"
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -137,6 +138,9 @@ struct gf_grid {
     int gkey_prec = -1, gkey_nu1 = -1, gkey_nu2 = -1;
     double gkey_omega = -1.0;
     bool use_graphs = true;
+    // optimisation-loop scratch (allocated on first use)
+    double *oc_rho = nullptr, *oc_dc = nullptr, *oc_dcx = nullptr, *oc_dvx = nullptr, *oc_ones = nullptr;
+    gf::OCState* oc_st = nullptr;
 };
 
 namespace {
@@ -561,6 +565,69 @@ int guard_impl(gf_grid* g, const double* f, const double* u, double* eta)
     return GF_OK;
 }
 
+int filter_radius_cells(double r_min) { return (int)std::ceil(r_min) - 1; }
+
+int filter_impl(gf_grid* g, const double* x, double* out, double r_min, bool adjoint)
+{
+    const int R = filter_radius_cells(r_min);
+    if (adjoint)
+        LAUNCH(g, nblk(g->nel), 256, gf::hat_filter_kernel<true>, x, out, g->lv[0].dims(), r_min, R);
+    else
+        LAUNCH(g, nblk(g->nel), 256, gf::hat_filter_kernel<false>, x, out, g->lv[0].dims(), r_min, R);
+    return GF_OK;
+}
+
+int ensure_oc(gf_grid* g)
+{
+    if (g->oc_rho) return GF_OK;
+    RET(allocT(&g->oc_rho, g->nel));
+    RET(allocT(&g->oc_dc, g->nel));
+    RET(allocT(&g->oc_dcx, g->nel));
+    RET(allocT(&g->oc_dvx, g->nel));
+    RET(allocT(&g->oc_ones, g->nel));
+    RET(allocT(&g->oc_st, 1));
+    std::vector<double> ones((size_t)g->nel, 1.0);
+    CK(cudaMemcpy(g->oc_ones, ones.data(), sizeof(double) * g->nel, cudaMemcpyHostToDevice));
+    return GF_OK;
+}
+
+int oc_update_impl(gf_grid* g, const double* x, const double* dc, const double* dv, double volfrac, double move,
+                   double* xnew)
+{
+    RET(ensure_oc(g));
+    const long long n = g->nel;
+    const int nb = (int)std::min<long long>(2LL * g->sms, std::max<long long>(1, (n + 1023) / 1024));
+    const double tol = 1e-3;
+    const int max_iters = 200;
+    LAUNCH(g, 1, 1, gf::oc_init_kernel, g->oc_st);
+    // every bisection iteration is two launches; iterations after the stop test early-exit
+    for (int it = 0; it < max_iters; ++it) {
+        LAUNCH(g, nb, 256, gf::oc_partial_kernel, x, dc, dv, n, move, tol, g->oc_st, g->partial);
+        LAUNCH(g, 1, 32, gf::oc_bisect_kernel, (const double*)g->partial, nb, n, volfrac, tol, max_iters, g->oc_st);
+        if ((it & 15) == 15) {
+            int done = 0;
+            CK(cudaMemcpyAsync(&done, &g->oc_st->done, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            if (done) break;
+        }
+    }
+    LAUNCH(g, nblk(n), 256, gf::oc_apply_kernel, x, dc, dv, xnew, n, move, (const gf::OCState*)g->oc_st);
+    return GF_OK;
+}
+
+int dot_impl(gf_grid* g, const double* a, const double* b, long long n, double* out)
+{
+    const int nb = (int)std::min<long long>(2LL * g->sms, std::max<long long>(1, (n + 1023) / 1024));
+    LAUNCH(g, nb, 256, gf::dot_partial_kernel, a, b, n, g->partial);
+    std::vector<double> part((size_t)nb);
+    CK(cudaMemcpyAsync(part.data(), g->partial, sizeof(double) * nb, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += part[i];   // fixed order
+    *out = s;
+    return GF_OK;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI ====
@@ -655,6 +722,8 @@ int gf_destroy_grid(gf_grid* g)
     cudaFree(g->rho64); cudaFree(g->rho16); cudaFree(g->work); cudaFree(g->partial);
     cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Z); cudaFree(g->hist);
     cudaFree(g->xsave);
+    cudaFree(g->oc_rho); cudaFree(g->oc_dc); cudaFree(g->oc_dcx); cudaFree(g->oc_dvx); cudaFree(g->oc_ones);
+    cudaFree(g->oc_st);
     if (g->host_status) cudaFreeHost(g->host_status);
     drop_graphs(g);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
@@ -959,6 +1028,63 @@ int gf_sensitivity(gf_grid* g, const double* u, double* dc)
     const int pm1_int = (p == std::floor(p)) ? (int)p - 1 : -1;
     LAUNCH(g, nblk(g->nel), 256, gf::sensitivity_kernel, u, g->rho64, dc, g->lv[0].dims(), K,
            -p * (1.0 - g->rho_min), p - 1.0, pm1_int);
+    return GF_OK;
+}
+
+int gf_filter(gf_grid* g, const double* x, double* xt, double r_min)
+{
+    RET(check_grid(g));
+    if (!x || !xt || x == xt) return set_err(GF_ERR_ARG, "x, xt non-null and distinct");
+    if (!(r_min > 1.0 && r_min <= 8.0)) return set_err(GF_ERR_ARG, "r_min in (1, 8]");
+    RET(set_device(g));
+    return filter_impl(g, x, xt, r_min, false);
+}
+
+int gf_filter_adjoint(gf_grid* g, const double* gs, double* out, double r_min)
+{
+    RET(check_grid(g));
+    if (!gs || !out || gs == out) return set_err(GF_ERR_ARG, "inputs non-null and distinct");
+    if (!(r_min > 1.0 && r_min <= 8.0)) return set_err(GF_ERR_ARG, "r_min in (1, 8]");
+    RET(set_device(g));
+    return filter_impl(g, gs, out, r_min, true);
+}
+
+int gf_oc_update(gf_grid* g, const double* x, const double* dc, const double* dv, double volfrac, double move,
+                 double* xnew)
+{
+    RET(check_grid(g));
+    if (!x || !dc || !dv || !xnew) return set_err(GF_ERR_ARG, "null pointer");
+    if (!(volfrac > 0 && volfrac < 1) || !(move > 0 && move <= 1)) return set_err(GF_ERR_ARG, "volfrac/move");
+    RET(set_device(g));
+    return oc_update_impl(g, x, dc, dv, volfrac, move, xnew);
+}
+
+int gf_compliance(gf_grid* g, const double* f, const double* u, double* c)
+{
+    RET(check_grid(g));
+    if (!f || !u || !c) return set_err(GF_ERR_ARG, "null pointer");
+    RET(set_device(g));
+    return dot_impl(g, f, u, g->ndof, c);
+}
+
+int gf_oc_iteration(gf_grid* g, double* x, const double* f, double* u, const gf_policy* pol, double p,
+                    double volfrac, double r_min, double move, gf_select_info* info, double* compliance)
+{
+    RET(check_grid(g));
+    if (!x || !f || !u || !pol || !info || !compliance) return set_err(GF_ERR_ARG, "null pointer");
+    RET(set_device(g));
+    RET(ensure_oc(g));
+    RET(filter_impl(g, x, g->oc_rho, r_min, false));                 // physical density
+    RET(gf_set_density(g, g->oc_rho, p));
+    RET(gf_select_floor(g, f, u, pol, info));                          // guarded state solve
+    *compliance = std::nan("");
+    if (info->status != GF_ACCEPTED) return GF_OK;                     // design kept unchanged
+    RET(dot_impl(g, f, u, g->ndof, compliance));
+    RET(gf_sensitivity(g, u, g->oc_dc));
+    RET(filter_impl(g, g->oc_dc, g->oc_dcx, r_min, true));
+    RET(filter_impl(g, g->oc_ones, g->oc_dvx, r_min, true));
+    RET(oc_update_impl(g, x, g->oc_dcx, g->oc_dvx, volfrac, move, g->oc_rho));
+    CK(cudaMemcpyAsync(x, g->oc_rho, sizeof(double) * g->nel, cudaMemcpyDeviceToDevice, g->stream));
     return GF_OK;
 }
 

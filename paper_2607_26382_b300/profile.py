@@ -1,0 +1,62 @@
+"""Run one operation of the library a few times on a synthetic state (a profiling target).
+
+    python -m paper_2607_26382_b300.profile apply_k64 --grid 96 48 48 --levels 5 --reps 3
+    ops: apply_k64, apply_k32, vcycle_mixed, vcycle_fp64, solve_mixed, select_mixed
+
+The state is the smoothed-Gaussian density (sigma 2, 40% at floor) at rho_min 1e-6,
+p = 3, with the cantilever tip load. Used as the command under ncu so that a
+capture covers a known, small number of launches.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("op", choices=["apply_k64", "apply_k32", "vcycle_mixed", "vcycle_fp64", "solve_mixed",
+                                   "select_mixed"])
+    ap.add_argument("--grid", type=int, nargs=3, default=[96, 48, 48])
+    ap.add_argument("--levels", type=int, default=5)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    import synth
+    from . import _lib as gf
+
+    nx, ny, nz = a.grid
+    g = gf.create_grid(nx, ny, nz, levels=a.levels)
+    g.set_density(torch.as_tensor(synth.smoothed_gaussian_density(nx, ny, nz, a.seed), device="cuda"), 3.0)
+    g.set_floor(1e-6)
+    gen = torch.Generator(device="cuda").manual_seed(a.seed)
+    x = torch.randn(g.n_dof, dtype=torch.float64, device="cuda", generator=gen)
+    y = torch.empty_like(x)
+    f = torch.zeros_like(x)
+    g.cantilever_load(f)
+    for _ in range(a.reps):
+        if a.op == "apply_k64":
+            g.apply_K(x, y)
+        elif a.op == "apply_k32":
+            g.apply_K_f32(x.float(), y.float())
+        elif a.op == "vcycle_mixed":
+            g.vcycle(x, y, gf.GF_MIXED)
+        elif a.op == "vcycle_fp64":
+            g.vcycle(x, y, gf.GF_FP64)
+        elif a.op == "solve_mixed":
+            y.zero_()
+            g.solve(f, y, prec=gf.GF_MIXED)
+        else:
+            g.set_density(torch.as_tensor(synth.smoothed_gaussian_density(nx, ny, nz, a.seed), device="cuda"), 3.0)
+            g.select_floor(f, y, gf.policy_defaults(solve_prec=gf.GF_MIXED))
+    torch.cuda.synchronize()
+    print(f"{a.op} x{a.reps} on {nx}x{ny}x{nz}: ok", flush=True)
+    g.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
