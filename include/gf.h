@@ -246,6 +246,35 @@ int gf_compliance(gf_grid* g, const double* f, const double* u, double* c);
 int gf_oc_iteration(gf_grid* g, double* x, const double* f, double* u, const gf_policy* pol, double p,
                     double volfrac, double r_min, double move, gf_select_info* info, double* compliance);
 
+/* ---- batched frozen states --------------------------------------------------- */
+
+/* Many independent frozen states (grids of uneven size) run Algorithm 1 together.
+ * Each FGMRES step of the whole batch is one CUDA graph holding one concurrent
+ * chain per state; finished states drop out of the chains; decisions (probe
+ * features, Eq. trigger, guard, next floor) are the single-state ones, per state.
+ * dims: host array of 3*n_states ints (nx, ny, nz per state); every state shares
+ * `levels`, h, E0, nu and `stream`. The batch owns each state's load f and
+ * solution u (device). */
+typedef struct gf_batch gf_batch;
+int gf_create_batch(int n_states, const int* dims, int levels, double h, double E0, double nu,
+                    void* stream, gf_batch** out);
+int gf_destroy_batch(gf_batch* b);
+/* The per-state grid (for sizes; do not destroy it). */
+int gf_batch_grid(gf_batch* b, int i, gf_grid** g);
+/* State i: density (n_elem doubles, device, copied) with exponent p, load f (n_dof, device, copied). */
+int gf_batch_set_state(gf_batch* b, int i, const double* rho_hat, double p, const double* f);
+/* Copy state i's current solution into u (n_dof doubles, device); blocks. */
+int gf_batch_solution(gf_batch* b, int i, double* u);
+/* Autotuner: time the node stencils at 64/128/256 threads per block once per
+ * distinct grid shape and keep the fastest (results do not depend on the pick).
+ * tpb_out (host, optional): 2*n_states ints, [FP64, FP32] block size per state. */
+int gf_batch_autotune(gf_batch* b, int* tpb_out);
+/* Algorithm 1 on every state; infos: host array of n_states. The fused probe is
+ * always used for GF_SEL_RULE (requires probe_iters <= kmax). */
+int gf_batch_select_floor(gf_batch* b, const gf_policy* pol, gf_select_info* infos);
+/* Kernels launched so far on the batch (graph nodes counted per replay). */
+int gf_batch_stats(const gf_batch* b, long long* kernel_launches);
+
 /* ---- the one entry point that allocates nothing -------------------------------- */
 
 /* The paper has no counterpart to this call; it exists for callers that must not

@@ -31,7 +31,8 @@ EXPORTED = [
     "gf_true_residual", "gf_select_floor", "gf_policy_defaults", "gf_trigger_rule",
     "gf_probe_features", "gf_sensitivity", "gf_get_stats", "gf_reset_stats", "gf_last_error",
     "gf_true_residual_noalloc", "gf_filter", "gf_filter_adjoint", "gf_oc_update", "gf_compliance",
-    "gf_oc_iteration",
+    "gf_oc_iteration", "gf_create_batch", "gf_destroy_batch", "gf_batch_grid", "gf_batch_set_state",
+    "gf_batch_solution", "gf_batch_autotune", "gf_batch_select_floor", "gf_batch_stats",
 ]
 
 
@@ -112,6 +113,14 @@ def lib():
         "gf_compliance": [P, P, P, POINTER(c_double)],
         "gf_oc_iteration": [P, P, P, P, POINTER(Policy), c_double, c_double, c_double, c_double,
                             POINTER(SelectInfo), POINTER(c_double)],
+        "gf_create_batch": [c_int, POINTER(c_int), c_int, c_double, c_double, c_double, P, POINTER(P)],
+        "gf_destroy_batch": [P],
+        "gf_batch_grid": [P, c_int, POINTER(P)],
+        "gf_batch_set_state": [P, c_int, P, c_double, P],
+        "gf_batch_solution": [P, c_int, P],
+        "gf_batch_autotune": [P, POINTER(c_int)],
+        "gf_batch_select_floor": [P, POINTER(Policy), POINTER(SelectInfo)],
+        "gf_batch_stats": [P, POINTER(c_longlong)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -354,6 +363,70 @@ def true_residual_noalloc(nx, ny, nz, rho_hat, p, rho_min, f, u, eta, h=1.0, E0=
         _ptr(f, t, 3 * n_nodes, "f"), _ptr(u, t, 3 * n_nodes, "u"), _ptr(eta, t, 1, "eta"),
         c_void_p(stream.cuda_stream)))
     return eta
+
+
+def _select_dict(info):
+    atts = [dict(rho_min=a.rho_min, iters=a.iters, flag=a.flag, stop_estimate=a.stop_estimate,
+                 eta=a.eta, accepted=bool(a.accepted)) for a in info.attempts[:info.n_attempts]]
+    return dict(status=info.status, floor_index=info.floor_index, rho_min=info.rho_min, eta=info.eta,
+                r50=info.r50, r100=info.r100, escalated=bool(info.escalated),
+                probe_iters_run=info.probe_iters_run, attempts=atts)
+
+
+class Batch:
+    """Many frozen states of uneven size solved together (gf_batch)."""
+
+    def __init__(self, dims, levels=3, h=1.0, E0=1.0, nu=0.3, stream=None):
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        flat = (c_int * (3 * len(dims)))(*[int(v) for d in dims for v in d])
+        handle = c_void_p()
+        _check(lib().gf_create_batch(len(dims), flat, int(levels), float(h), float(E0), float(nu),
+                                     c_void_p(stream.cuda_stream), ctypes.byref(handle)))
+        self._h = handle
+        self.dims = [tuple(d) for d in dims]
+        self.n_dof = [3 * (d[0] + 1) * (d[1] + 1) * (d[2] + 1) for d in dims]
+        self.n_elem = [d[0] * d[1] * d[2] for d in dims]
+
+    def __len__(self):
+        return len(self.dims)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gf_destroy_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, i, rho_hat, f, p=3.0):
+        t = _torch().float64
+        _check(lib().gf_batch_set_state(self._h, int(i), _ptr(rho_hat, t, self.n_elem[i], "rho_hat"), float(p),
+                                        _ptr(f, t, self.n_dof[i], "f")))
+
+    def solution(self, i, u):
+        _check(lib().gf_batch_solution(self._h, int(i), _ptr(u, _torch().float64, self.n_dof[i], "u")))
+        return u
+
+    def autotune(self):
+        out = (c_int * (2 * len(self)))()
+        _check(lib().gf_batch_autotune(self._h, out))
+        return [(out[2 * i], out[2 * i + 1]) for i in range(len(self))]
+
+    def select_floor(self, policy: Policy):
+        infos = (SelectInfo * len(self))()
+        _check(lib().gf_batch_select_floor(self._h, ctypes.byref(policy), infos))
+        return [_select_dict(infos[i]) for i in range(len(self))]
+
+    def kernel_launches(self):
+        n = c_longlong()
+        _check(lib().gf_batch_stats(self._h, ctypes.byref(n)))
+        return n.value
 
 
 def create_grid(nx, ny, nz, h=1.0, E0=1.0, nu=0.3, levels=3, stream=None) -> Grid:

@@ -1,0 +1,668 @@
+// Batched frozen states (included at the end of gf_lib.cu; same translation unit).
+//
+// Many independent states of uneven size run Algorithm 1 together. Each FGMRES
+// step j for the whole batch is ONE CUDA graph: the per-state chains (V-cycle, FP64
+// K*z, CGS2, Givens tail) are captured on forked streams inside a single capture,
+// so the GPU runs them concurrently. A per-state skip flag makes the chains of
+// states that have finished (or sit out a phase) exit at once, so the same graphs
+// serve every phase of the policy. The per-state decisions (probe features, rule,
+// guard, next floor) are the single-state ones, applied state by state. The
+// coarsest inverses of all states are built with Gauss-Jordan pivots in lockstep.
+// Node-stencil block sizes are chosen per grid shape by timing (autotuner).
+#pragma once
+
+namespace gf {
+
+struct BatchTables {
+    KState** st;       // per state
+    double** hist;
+    double** A;        // coarsest dense matrices
+    double** col;
+    double** row;
+    int* n;            // coarsest sizes
+};
+
+__global__ void batch_mark_kernel(KState** st, const int* __restrict__ active, int B)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B || active[i]) return;
+    st[i]->skip = 1;
+    st[i]->status = KS_STOP;
+}
+
+// After a cycle end: a state that is no longer running sits out the next cycles,
+// so its (already applied) update is not repeated.
+__global__ void batch_retire_kernel(KState** st, int B)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    if (!st[i]->skip && st[i]->status != KS_RUN) st[i]->skip = 1;
+}
+
+// out[4i..4i+3] = status, k, history[min(a,k)], history[min(b,k)]
+__global__ void batch_gather_kernel(KState* const* st, double* const* hist, int B, int a, int b,
+                                    double* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    const int k = st[i]->k;
+    out[4 * i + 0] = (double)st[i]->status;
+    out[4 * i + 1] = (double)k;
+    out[4 * i + 2] = hist[i][a < k ? a : k];
+    out[4 * i + 3] = hist[i][b < k ? b : k];
+}
+
+__global__ void batch_abort_kernel(KState** st, const int* __restrict__ abort_flags, int B)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B || !abort_flags[i]) return;
+    st[i]->status = KS_STOP;
+    st[i]->flag = 3;
+    st[i]->skip = 1;
+}
+
+// Gauss-Jordan pivot k on every state's matrix at once (blockIdx.y = state).
+__global__ void batch_gj_prepare_kernel(BatchTables t, const int* __restrict__ active, int k)
+{
+    const int i = blockIdx.y;
+    if (!active[i]) return;
+    const int n = t.n[i];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n || c >= n) return;
+    double* A = t.A[i];
+    const double piv = 1.0 / A[(long long)k * n + k];
+    t.col[i][c] = A[(long long)c * n + k];
+    const double v = (c == k) ? 1.0 : A[(long long)k * n + c];
+    t.row[i][c] = v * piv;
+}
+
+__global__ void batch_gj_eliminate_kernel(BatchTables t, const int* __restrict__ active, int k)
+{
+    const int i = blockIdx.y;
+    if (!active[i]) return;
+    const int n = t.n[i];
+    if (k >= n) return;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long long)n * n) return;
+    double* A = t.A[i];
+    const int r = (int)(q / n), c = (int)(q % n);
+    if (r == k) {
+        A[q] = t.row[i][c];
+    } else {
+        const double base = (c == k) ? 0.0 : A[q];
+        A[q] = base - t.col[i][r] * t.row[i][c];
+    }
+}
+
+}  // namespace gf
+
+struct gf_batch {
+    int B = 0, L = 0, device = 0, sms = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<gf_grid*> g;
+    std::vector<double*> f, u;
+    std::vector<cudaStream_t> cap;
+    cudaStream_t capS = nullptr;
+    cudaEvent_t evFork = nullptr;
+    std::vector<cudaEvent_t> evJoin;
+    cudaEvent_t ev[3] = {};
+    // graphs over all states
+    cudaGraphExec_t step[gf::KRY_MMAX] = {};
+    cudaGraphExec_t start[2] = {};
+    cudaGraphExec_t end = nullptr;
+    long long nodes_step[gf::KRY_MMAX] = {}, nodes_start[2] = {}, nodes_end = 0;
+    int key_prec = -1, key_nu1 = -1, key_nu2 = -1, key_m = -1;
+    double key_omega = -1.0;
+    void* key_ptrs = nullptr;   // V of state 0 when captured (realloc invalidates)
+    // device tables
+    gf::BatchTables tab{};
+    int* d_active = nullptr;
+    int* d_abort = nullptr;
+    double* gather_host = nullptr;   // mapped, 4 * B
+    double* gather_dev = nullptr;
+    int nc_max = 0;
+    long long launches = 0;
+};
+
+namespace {
+
+void batch_drop_graphs(gf_batch* b)
+{
+    for (int j = 0; j < gf::KRY_MMAX; ++j) {
+        if (b->step[j]) cudaGraphExecDestroy(b->step[j]);
+        b->step[j] = nullptr;
+    }
+    for (int q = 0; q < 2; ++q) {
+        if (b->start[q]) cudaGraphExecDestroy(b->start[q]);
+        b->start[q] = nullptr;
+    }
+    if (b->end) cudaGraphExecDestroy(b->end);
+    b->end = nullptr;
+}
+
+// Capture per_state(i) for every state on its own forked stream into one graph.
+template <class F>
+int batch_capture(gf_batch* b, F per_state, cudaGraphExec_t* out, long long* nodes)
+{
+    std::vector<gf_stats> saved(b->B);
+    long long count = 0;
+    CK(cudaStreamBeginCapture(b->capS, cudaStreamCaptureModeThreadLocal));
+    int rc = GF_OK;
+    cudaError_t e = cudaEventRecord(b->evFork, b->capS);
+    for (int i = 0; i < b->B && rc == GF_OK && e == cudaSuccess; ++i) {
+        gf_grid* g = b->g[i];
+        e = cudaStreamWaitEvent(b->cap[i], b->evFork, 0);
+        if (e != cudaSuccess) break;
+        saved[i] = g->stats;
+        g->cur_stream = b->cap[i];
+        rc = per_state(i);
+        g->cur_stream = g->stream;
+        count += g->stats.kernel_launches - saved[i].kernel_launches;
+        g->stats = saved[i];
+        if (rc == GF_OK) e = cudaEventRecord(b->evJoin[i], b->cap[i]);
+        if (e == cudaSuccess && rc == GF_OK) e = cudaStreamWaitEvent(b->capS, b->evJoin[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->capS, &graph);
+    if (rc != GF_OK || e != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (rc != GF_OK) return rc;
+        return set_err(GF_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ei);
+    *nodes = count;
+    return GF_OK;
+}
+
+int batch_launch(gf_batch* b, cudaGraphExec_t ex, long long nodes)
+{
+    CK(cudaGraphLaunch(ex, b->stream));
+    b->launches += nodes;
+    return GF_OK;
+}
+
+int batch_graphs(gf_batch* b, const gf_solve_opts* o)
+{
+    const int m = o->restart;
+    uintptr_t key = 0;
+    for (gf_grid* g : b->g)
+        key = key * 1000003u ^ (uintptr_t)g->V ^ ((uintptr_t)g->Z << 1) ^ ((uintptr_t)g->hist << 2);
+    void* ptr0 = (void*)key;
+    if (b->key_prec != o->prec || b->key_nu1 != o->nu1 || b->key_nu2 != o->nu2 || b->key_omega != o->omega ||
+        b->key_m != m || b->key_ptrs != ptr0) {
+        batch_drop_graphs(b);
+        b->key_prec = o->prec;
+        b->key_nu1 = o->nu1;
+        b->key_nu2 = o->nu2;
+        b->key_omega = o->omega;
+        b->key_m = m;
+        b->key_ptrs = ptr0;
+    }
+    for (int first = 0; first < 2; ++first)
+        if (!b->start[first])
+            RET(batch_capture(b, [&](int i) { return cycle_start(b->g[i], b->f[i], b->u[i], first == 1, first == 1); },
+                              &b->start[first], &b->nodes_start[first]));
+    for (int j = 0; j < m; ++j)
+        if (!b->step[j])
+            RET(batch_capture(b, [&](int i) { return arnoldi_step(b->g[i], j, o); }, &b->step[j], &b->nodes_step[j]));
+    if (!b->end)
+        RET(batch_capture(b,
+                          [&](int i) {
+                              gf_grid* g = b->g[i];
+                              LAUNCH(g, 1, 1, gf::backsolve_kernel, g->st);
+                              LAUNCH(g, 2 * g->sms, 256, gf::update_x_kernel, b->u[i], (const double*)g->Z, g->ndof,
+                                     g->ndof, (const gf::KState*)g->st);
+                              return GF_OK;
+                          },
+                          &b->end, &b->nodes_end));
+    return GF_OK;
+}
+
+int batch_tables(gf_batch* b)
+{
+    std::vector<gf::KState*> st(b->B);
+    std::vector<double*> hist(b->B);
+    for (int i = 0; i < b->B; ++i) {
+        st[i] = b->g[i]->st;
+        hist[i] = b->g[i]->hist;
+    }
+    CK(cudaMemcpy(b->tab.st, st.data(), sizeof(void*) * b->B, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->tab.hist, hist.data(), sizeof(void*) * b->B, cudaMemcpyHostToDevice));
+    return GF_OK;
+}
+
+struct BatchOut {
+    int k = 0, flag = 0, status = 0;
+    double r50 = 0.0, r100 = 0.0, stop_estimate = 0.0;
+    bool decided = false, escalated = false;
+    std::vector<double> hist;
+};
+
+// One lockstep FGMRES solve of the active states from u = 0. probe_at > 0: at that
+// step, states still running get their r50/r100 read and the rule applied;
+// escalated states are stopped (their iterate is discarded).
+int batch_solve(gf_batch* b, const gf_solve_opts* o, const std::vector<int>& active, int probe_at,
+                const gf_policy* pol, std::vector<BatchOut>& out)
+{
+    const int B = b->B, m = o->restart;
+    for (int i = 0; i < B; ++i) RET(ensure_krylov(b->g[i], m, std::max(o->kmax, probe_at)));
+    RET(batch_tables(b));
+    RET(batch_graphs(b, o));
+    CK(cudaMemcpyAsync(b->d_active, active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, b->stream));
+    for (int i = 0; i < B; ++i) {
+        gf_grid* g = b->g[i];
+        if (!active[i]) continue;
+        CK(cudaMemsetAsync(b->u[i], 0, sizeof(double) * g->ndof, b->stream));
+        LAUNCH(g, 1, 1, init_state_kernel, g->st, o->kmax, m, o->tol);
+        *g->host_status = gf::KS_RUN;
+    }
+    LAUNCH(b->g[0], (B + 127) / 128, 128, gf::batch_mark_kernel, b->tab.st, (const int*)b->d_active, B);
+    CK(cudaStreamSynchronize(b->stream));
+    std::vector<int> aborted(B, 0), decided(B, 0);
+    out.assign(B, BatchOut());
+    auto any_running = [&]() {
+        for (int i = 0; i < B; ++i)
+            if (active[i] && !aborted[i] && *(volatile int*)b->g[i]->host_status == gf::KS_RUN) return true;
+        return false;
+    };
+    long long launched = 0;
+    bool first = true;
+    for (int cycle = 0;; ++cycle) {
+        RET(batch_launch(b, b->start[first ? 1 : 0], b->nodes_start[first ? 1 : 0]));
+        first = false;
+        CK(cudaStreamSynchronize(b->stream));
+        if (!any_running()) break;
+        for (int j = 0; j < m; ++j) {
+            RET(batch_launch(b, b->step[j], b->nodes_step[j]));
+            ++launched;
+            CK(cudaEventRecord(b->ev[j % 3], b->stream));
+            if (probe_at > 0 && launched == probe_at) {
+                LAUNCH(b->g[0], (B + 127) / 128, 128, gf::batch_gather_kernel, (gf::KState* const*)b->tab.st,
+                       (double* const*)b->tab.hist, B, pol->checkpoint_a, pol->checkpoint_b, b->gather_dev);
+                CK(cudaStreamSynchronize(b->stream));
+                std::vector<int> ab(B, 0);
+                bool any_ab = false;
+                for (int i = 0; i < B; ++i) {
+                    if (!active[i] || (int)b->gather_host[4 * i] != gf::KS_RUN) continue;
+                    decided[i] = 1;
+                    out[i].decided = true;
+                    out[i].r50 = b->gather_host[4 * i + 2];
+                    out[i].r100 = b->gather_host[4 * i + 3];
+                    out[i].escalated = gf_trigger_rule(out[i].r50, out[i].r100, pol) == 1;
+                    if (out[i].escalated) {
+                        ab[i] = aborted[i] = 1;
+                        any_ab = true;
+                    }
+                }
+                if (any_ab) {
+                    CK(cudaMemcpyAsync(b->d_abort, ab.data(), sizeof(int) * B, cudaMemcpyHostToDevice, b->stream));
+                    LAUNCH(b->g[0], (B + 127) / 128, 128, gf::batch_abort_kernel, b->tab.st, (const int*)b->d_abort, B);
+                }
+            }
+            if (j >= 1) {
+                CK(cudaEventSynchronize(b->ev[(j - 1) % 3]));
+                if (!any_running()) break;
+            }
+        }
+        RET(batch_launch(b, b->end, b->nodes_end));
+        LAUNCH(b->g[0], (B + 127) / 128, 128, gf::batch_retire_kernel, b->tab.st, B);
+        LAUNCH(b->g[0], (B + 127) / 128, 128, gf::batch_gather_kernel, (gf::KState* const*)b->tab.st,
+               (double* const*)b->tab.hist, B, 0, 0, b->gather_dev);
+        CK(cudaStreamSynchronize(b->stream));
+        bool run = false;
+        for (int i = 0; i < B; ++i)
+            if (active[i] && !aborted[i] && (int)b->gather_host[4 * i] == gf::KS_RUN) run = true;
+        if (!run) break;
+    }
+    for (int i = 0; i < B; ++i) {
+        if (!active[i]) continue;
+        gf_grid* g = b->g[i];
+        HostState hs{};
+        RET(read_state(g, &hs));
+        out[i].k = hs.k;
+        out[i].flag = hs.flag;
+        out[i].status = hs.status;
+        out[i].hist.resize((size_t)hs.k + 1);
+        CK(cudaMemcpy(out[i].hist.data(), g->hist, sizeof(double) * (hs.k + 1), cudaMemcpyDeviceToHost));
+        out[i].stop_estimate = out[i].hist[hs.k];
+    }
+    return GF_OK;
+}
+
+// Set the floor of the active states: moduli and hierarchy per state, then the
+// coarsest inverses with lockstep Gauss-Jordan pivots over the batch.
+int batch_set_floor(gf_batch* b, const std::vector<int>& active, const std::vector<double>& rho_min)
+{
+    const int B = b->B;
+    for (int i = 0; i < B; ++i) {
+        if (!active[i]) continue;
+        gf_grid* g = b->g[i];
+        g->skip_coarse_inverse = true;
+        const int rc = gf_set_floor(g, rho_min[i]);
+        g->skip_coarse_inverse = false;
+        if (rc != GF_OK) return rc;
+        Level& c = g->lv[g->L - 1];
+        const long long n = g->nc;
+        LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, (const double*)c.E64, g->Ainv, c.dims(), g->K0d);
+        LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, g->Ainv, c.dims());
+    }
+    CK(cudaMemcpyAsync(b->d_active, active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, b->stream));
+    int nmax = 0;
+    for (int i = 0; i < B; ++i)
+        if (active[i]) nmax = std::max(nmax, b->g[i]->nc);
+    for (int k = 0; k < nmax; ++k) {
+        const dim3 gp(nblk(nmax), B), ge(nblk((long long)nmax * nmax), B);
+        gf::batch_gj_prepare_kernel<<<gp, 256, 0, b->stream>>>(b->tab, b->d_active, k);
+        gf::batch_gj_eliminate_kernel<<<ge, 256, 0, b->stream>>>(b->tab, b->d_active, k);
+        b->launches += 2;
+        CK(cudaGetLastError());
+    }
+    return GF_OK;
+}
+
+// Time the FP64 and FP32 stencils at block sizes 64/128/256 and keep the fastest.
+int autotune_grid(gf_grid* g)
+{
+    if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor before autotuning");
+    const int cand[3] = {64, 128, 256};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float* xf = reinterpret_cast<float*>(g->work);
+    for (int prec = 0; prec < 2; ++prec) {
+        float best = 1e30f;
+        int pick = 256;
+        for (int c : cand) {
+            g->tpb[prec] = c;
+            for (int rep = 0; rep < 4; ++rep) {
+                if (rep == 1) CK(cudaEventRecord(e0, g->stream));
+                if (prec == 0)
+                    RET((stencil<double, double, gf::ST_APPLY>(g, 0, g->lv[0].x64, nullptr, g->lv[0].t64,
+                                                                g->lv[0].E64, g->K0d, 0.0, nullptr)));
+                else
+                    RET((stencil<float, float, gf::ST_APPLY>(g, 0, g->lv[0].x32, nullptr, xf, g->lv[0].E32,
+                                                              g->K0f, 0.0f, nullptr)));
+            }
+            CK(cudaEventRecord(e1, g->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                pick = c;
+            }
+        }
+        g->tpb[prec] = pick;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return GF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gf_create_batch(int n_states, const int* dims, int levels, double h, double E0, double nu, void* stream,
+                    gf_batch** out)
+{
+    if (!out || !dims || n_states < 1 || n_states > 4096) return set_err(GF_ERR_ARG, "n_states in [1,4096]");
+    *out = nullptr;
+    gf_batch* b = new gf_batch();
+    b->B = n_states;
+    b->L = levels;
+    b->stream = (cudaStream_t)stream;
+    auto fail = [&](int code) { gf_destroy_batch(b); return code; };
+    if (cudaGetDevice(&b->device) != cudaSuccess) return fail(set_err(GF_ERR_CUDA, "cudaGetDevice"));
+    for (int i = 0; i < n_states; ++i) {
+        gf_grid* g = nullptr;
+        const int rc = gf_create_grid(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], h, E0, nu, levels, stream, &g);
+        if (rc != GF_OK) return fail(rc);
+        b->g.push_back(g);
+        double *f = nullptr, *u = nullptr;
+        if (cudaMalloc(&f, sizeof(double) * g->ndof) != cudaSuccess ||
+            cudaMalloc(&u, sizeof(double) * g->ndof) != cudaSuccess) {
+            cudaFree(f);
+            return fail(set_err(GF_ERR_OOM, "batch vectors"));
+        }
+        b->f.push_back(f);
+        b->u.push_back(u);
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(set_err(GF_ERR_CUDA, "stream"));
+        b->cap.push_back(s);
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(set_err(GF_ERR_CUDA, "event"));
+        b->evJoin.push_back(e);
+        b->nc_max = std::max(b->nc_max, g->nc);
+    }
+    b->sms = b->g[0]->sms;
+    if (cudaStreamCreateWithFlags(&b->capS, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->evFork, cudaEventDisableTiming) != cudaSuccess)
+        return fail(set_err(GF_ERR_CUDA, "stream/event"));
+    for (int q = 0; q < 3; ++q)
+        if (cudaEventCreateWithFlags(&b->ev[q], cudaEventDisableTiming) != cudaSuccess)
+            return fail(set_err(GF_ERR_CUDA, "event"));
+    const size_t P = sizeof(void*) * n_states;
+    if (cudaMalloc(&b->tab.st, P) != cudaSuccess || cudaMalloc(&b->tab.hist, P) != cudaSuccess ||
+        cudaMalloc(&b->tab.A, P) != cudaSuccess || cudaMalloc(&b->tab.col, P) != cudaSuccess ||
+        cudaMalloc(&b->tab.row, P) != cudaSuccess || cudaMalloc(&b->tab.n, sizeof(int) * n_states) != cudaSuccess ||
+        cudaMalloc(&b->d_active, sizeof(int) * n_states) != cudaSuccess ||
+        cudaMalloc(&b->d_abort, sizeof(int) * n_states) != cudaSuccess)
+        return fail(set_err(GF_ERR_OOM, "batch tables"));
+    if (cudaHostAlloc((void**)&b->gather_host, sizeof(double) * 4 * n_states, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&b->gather_dev, b->gather_host, 0) != cudaSuccess)
+        return fail(set_err(GF_ERR_CUDA, "mapped gather"));
+    std::vector<double*> A(n_states), col(n_states), row(n_states);
+    std::vector<int> n(n_states);
+    for (int i = 0; i < n_states; ++i) {
+        A[i] = b->g[i]->Ainv;
+        col[i] = b->g[i]->gjcol;
+        row[i] = b->g[i]->gjrow;
+        n[i] = b->g[i]->nc;
+    }
+    if (cudaMemcpy(b->tab.A, A.data(), P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->tab.col, col.data(), P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->tab.row, row.data(), P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->tab.n, n.data(), sizeof(int) * n_states, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(set_err(GF_ERR_CUDA, "tables"));
+    *out = b;
+    return GF_OK;
+}
+
+int gf_destroy_batch(gf_batch* b)
+{
+    if (!b) return GF_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graphs(b);
+    for (gf_grid* g : b->g) gf_destroy_grid(g);
+    for (double* p : b->f) cudaFree(p);
+    for (double* p : b->u) cudaFree(p);
+    for (cudaStream_t s : b->cap) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->evJoin) cudaEventDestroy(e);
+    for (int q = 0; q < 3; ++q)
+        if (b->ev[q]) cudaEventDestroy(b->ev[q]);
+    if (b->evFork) cudaEventDestroy(b->evFork);
+    if (b->capS) cudaStreamDestroy(b->capS);
+    cudaFree(b->tab.st); cudaFree(b->tab.hist); cudaFree(b->tab.A); cudaFree(b->tab.col); cudaFree(b->tab.row);
+    cudaFree(b->tab.n); cudaFree(b->d_active); cudaFree(b->d_abort);
+    if (b->gather_host) cudaFreeHost(b->gather_host);
+    delete b;
+    return GF_OK;
+}
+
+int gf_batch_grid(gf_batch* b, int i, gf_grid** g)
+{
+    if (!b || !g || i < 0 || i >= b->B) return set_err(GF_ERR_ARG, "state index");
+    *g = b->g[i];
+    return GF_OK;
+}
+
+int gf_batch_set_state(gf_batch* b, int i, const double* rho_hat, double p, const double* f)
+{
+    if (!b || i < 0 || i >= b->B || !rho_hat || !f) return set_err(GF_ERR_ARG, "state index / null pointer");
+    gf_grid* g = b->g[i];
+    RET(set_device(g));
+    RET(gf_set_density(g, rho_hat, p));
+    CK(cudaMemcpyAsync(b->f[i], f, sizeof(double) * g->ndof, cudaMemcpyDeviceToDevice, b->stream));
+    return GF_OK;
+}
+
+int gf_batch_solution(gf_batch* b, int i, double* u)
+{
+    if (!b || i < 0 || i >= b->B || !u) return set_err(GF_ERR_ARG, "state index / null pointer");
+    CK(cudaMemcpyAsync(u, b->u[i], sizeof(double) * b->g[i]->ndof, cudaMemcpyDeviceToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return GF_OK;
+}
+
+int gf_batch_autotune(gf_batch* b, int* tpb_out)
+{
+    if (!b) return set_err(GF_ERR_ARG, "null batch");
+    // one timing per distinct grid shape; states of the same shape share the pick
+    std::vector<int> done(b->B, 0);
+    for (int i = 0; i < b->B; ++i) {
+        if (done[i]) continue;
+        gf_grid* g = b->g[i];
+        const bool had_density = g->has_density, had_floor = g->has_floor;
+        const double old_floor = g->rho_min;
+        if (!had_density) {
+            // time on a placeholder field (all voids); the state is reset afterwards
+            CK(cudaMemsetAsync(g->rho64, 0, sizeof(double) * g->nel, g->stream));
+            CK(cudaMemsetAsync(g->rho16, 0, sizeof(__nv_bfloat16) * g->nel, g->stream));
+            g->has_density = true;
+        }
+        if (!g->has_floor) RET(gf_set_floor(g, 1e-3));
+        RET(autotune_grid(g));
+        if (!had_density) {
+            g->has_density = false;
+            g->has_floor = false;
+        } else if (!had_floor) {
+            g->has_floor = false;
+        } else {
+            g->rho_min = old_floor;
+        }
+        for (int q = i; q < b->B; ++q)
+            if (b->g[q]->nx == g->nx && b->g[q]->ny == g->ny && b->g[q]->nz == g->nz) {
+                b->g[q]->tpb[0] = g->tpb[0];
+                b->g[q]->tpb[1] = g->tpb[1];
+                done[q] = 1;
+            }
+    }
+    batch_drop_graphs(b);
+    for (gf_grid* g : b->g) drop_graphs(g);
+    if (tpb_out)
+        for (int i = 0; i < b->B; ++i) {
+            tpb_out[2 * i] = b->g[i]->tpb[0];
+            tpb_out[2 * i + 1] = b->g[i]->tpb[1];
+        }
+    return GF_OK;
+}
+
+int gf_batch_select_floor(gf_batch* b, const gf_policy* pol, gf_select_info* infos)
+{
+    if (!b || !pol || !infos) return set_err(GF_ERR_ARG, "null pointer");
+    if (pol->n_ladder < 0 || pol->n_ladder > GF_MAX_LADDER) return set_err(GF_ERR_ARG, "n_ladder");
+    gf_solve_opts o = pol->solve;
+    o.history = nullptr;
+    o.tol = pol->tau;
+    o.kmax = pol->kmax;
+    RET(validate_opts(&o));
+    if (pol->selector == GF_SEL_RULE && pol->probe_iters > pol->kmax)
+        return set_err(GF_ERR_ARG, "batched policy needs probe_iters <= kmax");
+    const int B = b->B;
+    for (int i = 0; i < B; ++i)
+        if (!b->g[i]->has_density) return set_err(GF_ERR_STATE, "state " + std::to_string(i) + " has no density");
+    CK(cudaSetDevice(b->device));
+    double floors[GF_MAX_LADDER + 1];
+    floors[0] = pol->rho0;
+    for (int q = 0; q < pol->n_ladder; ++q) floors[q + 1] = pol->ladder[q];
+    const int nf = pol->n_ladder + 1;
+    std::vector<int> next(B, 0), done(B, 0);
+    for (int i = 0; i < B; ++i) {
+        std::memset(&infos[i], 0, sizeof(gf_select_info));
+        infos[i].status = GF_NO_ADMISSIBLE_FLOOR;
+        infos[i].floor_index = -1;
+        infos[i].r50 = infos[i].r100 = infos[i].rho_min = infos[i].eta = std::nan("");
+    }
+    const bool rule = pol->selector == GF_SEL_RULE;
+    if (pol->selector == GF_SEL_GIVEN) {
+        if (pol->first_index < 0 || pol->first_index >= nf) return set_err(GF_ERR_ARG, "first_index");
+        for (int i = 0; i < B; ++i) {
+            next[i] = pol->first_index;
+            infos[i].escalated = pol->first_index > 0;
+        }
+    }
+    for (int phase = 0;; ++phase) {
+        std::vector<int> active(B, 0);
+        std::vector<double> rm(B, 0.0);
+        bool any = false;
+        for (int i = 0; i < B; ++i)
+            if (!done[i] && next[i] < nf) {
+                active[i] = 1;
+                rm[i] = floors[next[i]];
+                any = true;
+            }
+        if (!any) break;
+        RET(batch_set_floor(b, active, rm));
+        const bool probe_phase = rule && phase == 0;
+        gf_solve_opts so = o;
+        if (probe_phase) so.kmax = std::max(o.kmax, pol->probe_iters);
+        std::vector<BatchOut> res;
+        RET(batch_solve(b, &so, active, probe_phase ? pol->probe_iters : 0, pol, res));
+        for (int i = 0; i < B; ++i) {
+            if (!active[i]) continue;
+            gf_select_info& inf = infos[i];
+            if (probe_phase) {
+                if (res[i].decided) {
+                    inf.r50 = res[i].r50;
+                    inf.r100 = res[i].r100;
+                    inf.escalated = res[i].escalated;
+                    inf.probe_iters_run = pol->probe_iters;
+                } else {
+                    inf.probe_iters_run = std::min(res[i].k, pol->probe_iters);
+                    RET(gf_probe_features(res[i].hist.data(), res[i].k, pol, &inf.r50, &inf.r100));
+                    inf.escalated = gf_trigger_rule(inf.r50, inf.r100, pol);
+                }
+                if (inf.escalated) {
+                    next[i] = 1;
+                    continue;
+                }
+            }
+            // guard on the selected solve
+            double eta = 0.0;
+            gf_grid* g = b->g[i];
+            RET(guard_impl(g, b->f[i], b->u[i], &eta));
+            gf_attempt& a = inf.attempts[inf.n_attempts++];
+            a.rho_min = rm[i];
+            a.iters = res[i].k;
+            a.flag = res[i].flag;
+            a.stop_estimate = res[i].stop_estimate;
+            a.eta = eta;
+            a.accepted = eta <= pol->tau;
+            if (a.accepted) {
+                inf.status = GF_ACCEPTED;
+                inf.floor_index = next[i];
+                inf.rho_min = rm[i];
+                inf.eta = eta;
+                done[i] = 1;
+            } else {
+                next[i] += 1;
+            }
+        }
+    }
+    return GF_OK;
+}
+
+int gf_batch_stats(const gf_batch* b, long long* kernel_launches)
+{
+    if (!b || !kernel_launches) return set_err(GF_ERR_ARG, "null pointer");
+    long long s = b->launches;
+    for (gf_grid* g : b->g) s += g->stats.kernel_launches;
+    *kernel_launches = s;
+    return GF_OK;
+}
+
+}  // extern "C"

@@ -138,6 +138,8 @@ struct gf_grid {
     int gkey_prec = -1, gkey_nu1 = -1, gkey_nu2 = -1;
     double gkey_omega = -1.0;
     bool use_graphs = true;
+    int tpb[2] = {256, 256};          // node-stencil block size: [0] FP64, [1] FP32 (autotuned)
+    bool skip_coarse_inverse = false; // batched set-up builds the coarsest inverse itself
     // optimisation-loop scratch (allocated on first use)
     double *oc_rho = nullptr, *oc_dc = nullptr, *oc_dcx = nullptr, *oc_dvx = nullptr, *oc_ones = nullptr;
     gf::OCState* oc_st = nullptr;
@@ -177,7 +179,8 @@ int stencil(gf_grid* g, int l, const T* x, const T* b, T* out, const ET* E, cons
             T omega, const int* halt)
 {
     const Level& L = g->lv[l];
-    LAUNCH(g, nblk(L.nodes), 256, (gf::node_stencil_kernel<T, ET, MODE>), x, b, out, E, L.dims(), K0, omega,
+    const int tpb = g->tpb[sizeof(T) == sizeof(double) ? 0 : 1];
+    LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_kernel<T, ET, MODE>), x, b, out, E, L.dims(), K0, omega,
            halt);
     return GF_OK;
 }
@@ -238,7 +241,8 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
         const T* b = (l == 0) ? b0 : B::b(lev);
         T* x = B::x(lev);
         T* t = B::t(lev);
-        LAUNCH(g, nblk(lev.nodes), 256, (gf::first_sweep_kernel<T, T, T>), b, x, B::E(lev), lev.dims(), k0<T>(g),
+        const int tpb = g->tpb[sizeof(T) == sizeof(double) ? 0 : 1];
+        LAUNCH(g, nblk(lev.nodes, tpb), tpb, (gf::first_sweep_kernel<T, T, T>), b, x, B::E(lev), lev.dims(), k0<T>(g),
                omega, halt);
         for (int s = 1; s < nu1; ++s) {
             RET((stencil<T, T, gf::ST_SWEEP>(g, l, x, b, t, B::E(lev), k0<T>(g), omega, halt)));
@@ -361,6 +365,7 @@ __global__ void init_state_kernel(gf::KState* st, int kmax, int m, double tol)
     st->flag = 1;
     st->J = 0;
     st->j = 0;
+    st->skip = 0;
 }
 
 struct HostState {
@@ -419,9 +424,10 @@ int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
 int cycle_start(gf_grid* g, const double* f, const double* x, bool x_zero, bool first)
 {
     double* v0 = g->V;
-    if (!x_zero) RET(applyK64(g, x, v0, nullptr));
+    const int* skip = &g->st->skip;
+    if (!x_zero) RET(applyK64(g, x, v0, skip));
     LAUNCH(g, g->nbr, gf::RED_THREADS, gf::residual_norms_kernel, f, v0, v0, g->ndof, g->nx + 1, g->partial,
-           x_zero ? 1 : 0);
+           x_zero ? 1 : 0, skip);
     LAUNCH(g, 1, 64, gf::reduce_partials_kernel, g->partial, g->nbr, 2, 2, g->st, 0, 0);
     LAUNCH(g, 1, 32, gf::cycle_start_tail_kernel, g->st, g->hist, g->host_status_dev, first ? 1 : 0);
     LAUNCH(g, 2 * g->sms, 256, gf::scale_kernel, v0, g->ndof, g->st, 1);
@@ -554,7 +560,7 @@ int guard_impl(gf_grid* g, const double* f, const double* u, double* eta)
 {
     RET(applyK64(g, u, g->work, nullptr));
     LAUNCH(g, g->nbr, gf::RED_THREADS, gf::residual_norms_kernel, f, g->work, (double*)nullptr, g->ndof,
-           g->nx + 1, g->partial, 0);
+           g->nx + 1, g->partial, 0, (const int*)nullptr);
     LAUNCH(g, 1, 64, gf::reduce_partials_kernel, g->partial, g->nbr, 2, 2, g->gst, 0, 0);
     double h[2];
     CK(cudaMemcpyAsync(h, g->gst->h1, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
@@ -781,7 +787,7 @@ int gf_set_floor(gf_grid* g, double rho_min)
         LAUNCH(g, nblk(c.nel), 256, gf::coarsen_kernel<double>, g->lv[l - 1].E64, c.E64, c.dims());
         LAUNCH(g, nblk(c.nel), 256, gf::coarsen_kernel<float>, g->lv[l - 1].E32, c.E32, c.dims());
     }
-    RET(build_coarse_inverse(g));
+    if (!g->skip_coarse_inverse) RET(build_coarse_inverse(g));
     g->rho_min = rho_min;
     g->has_floor = true;
     return GF_OK;
@@ -1191,9 +1197,11 @@ extern "C" int gf_true_residual_noalloc(int nx, int ny, int nz, double h, double
     gf::node_stencil_kernel<double, double, gf::ST_APPLY><<<nblk(nodes), 256, 0, s>>>(
         u, nullptr, Ku, E, d, K0, 0.0, nullptr);
     CK(cudaGetLastError());
-    gf::residual_norms_kernel<<<nb, gf::RED_THREADS, 0, s>>>(f, Ku, nullptr, ndof, nx + 1, partial, 0);
+    gf::residual_norms_kernel<<<nb, gf::RED_THREADS, 0, s>>>(f, Ku, nullptr, ndof, nx + 1, partial, 0, nullptr);
     CK(cudaGetLastError());
     noalloc_eta_kernel<<<1, 32, 0, s>>>(partial, nb, eta);
     CK(cudaGetLastError());
     return GF_OK;
 }
+
+#include "batch.cuh"

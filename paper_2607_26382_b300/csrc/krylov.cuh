@@ -26,6 +26,7 @@ struct KState {
     double ww;                             // ||w||^2 after CGS2
     double fnorm, tol, inv, beta;
     int k, kmax, m, J, status, flag, j;
+    int skip;                              // 1: this state sits out (batched solves)
 };
 
 // ---------------------------------------------------------------- reductions --
@@ -218,7 +219,7 @@ __global__ void arnoldi_tail_kernel(KState* __restrict__ st, double* __restrict_
 __global__ void cycle_start_tail_kernel(KState* __restrict__ st, double* __restrict__ hist,
                                         volatile int* host_status, int first)
 {
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x != 0 || st->skip) return;
     const double beta = sqrt(st->h1[0]);          // ||M f - K x||
     if (first) st->fnorm = sqrt(st->h1[1]);       // ||M f||
     st->beta = beta;
@@ -243,7 +244,7 @@ __global__ void cycle_start_tail_kernel(KState* __restrict__ st, double* __restr
 // Upper-triangular back substitution H[0:J,0:J] y = g[0:J].
 __global__ void backsolve_kernel(KState* __restrict__ st)
 {
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x != 0 || st->skip) return;
     const int ldh = KRY_MMAX + 1;
     const int J = st->J;
     for (int i = J - 1; i >= 0; --i) {
@@ -259,6 +260,7 @@ update_x_kernel(double* __restrict__ x, const double* __restrict__ Z, long long 
                 const KState* __restrict__ st)
 {
     __shared__ double ys[KRY_MMAX];
+    if (st->skip) return;
     const int J = st->J;
     if (threadIdx.x < J) ys[threadIdx.x] = st->y[threadIdx.x];
     __syncthreads();
@@ -284,8 +286,10 @@ __global__ void scale_kernel(double* __restrict__ v, long long n, const KState* 
 // fixed DOFs: (r/3) % NX == 0.
 __global__ void __launch_bounds__(RED_THREADS)
 residual_norms_kernel(const double* __restrict__ f, const double* y, double* r,
-                      long long n, int NX, double* __restrict__ partial, int y_is_zero)
+                      long long n, int NX, double* __restrict__ partial, int y_is_zero,
+                      const int* __restrict__ halt)
 {
+    if (halt != nullptr && *halt != 0) return;
     double acc[2] = {0.0, 0.0};
     long long r0, r1;
     block_rows(n, r0, r1);

@@ -1,0 +1,77 @@
+"""Batched frozen states: every state's Algorithm-1 result from the batch equals the
+single-state path bit for bit (same kernels, same reduction order), and the
+accepted solutions pass the oracle's own FP64 guard."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gf_oracle as O
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gf():
+    from paper_2607_26382_b300 import build
+    build.build()
+    import paper_2607_26382_b300 as gf
+    return gf
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+STATES = [((16, 8, 8), "bern", 43, 0.35), ((24, 12, 12), "smooth", 1, 0.4), ((32, 16, 16), "bern", 47, 0.30),
+          ((16, 8, 8), "smooth", 5, 0.3), ((20, 12, 8), "bern", 3, 0.25)]
+
+
+def _rho(dims, kind, seed, q):
+    nx, ny, nz = dims
+    if kind == "bern":
+        return synth.bernoulli_density(nx, ny, nz, seed, q)
+    return synth.smoothed_gaussian_density(nx, ny, nz, seed, 2.0, q)
+
+
+@pytest.mark.parametrize("selector,prec", [("rule", 0), ("full", 1)])
+def test_batch_matches_single_state(gf, selector, prec):
+    L = 3
+    sel = gf.GF_SEL_RULE if selector == "rule" else gf.GF_SEL_FULL
+    pol = gf.policy_defaults(rho0=1e-8, ladder=[1e-5, 1e-4, 1e-3], kmax=120, selector=sel, solve_prec=prec)
+    batch = gf.Batch([s[0] for s in STATES], levels=L)
+    tuned = batch.autotune()
+    assert all(t[0] in (64, 128, 256) and t[1] in (64, 128, 256) for t in tuned)
+    rhos, fs = [], []
+    for i, (dims, kind, seed, q) in enumerate(STATES):
+        rho = dev(_rho(dims, kind, seed, q))
+        f = dev(O.cantilever_load(O.Mesh(*dims)))
+        rhos.append(rho)
+        fs.append(f)
+        batch.set_state(i, rho, f, 3.0)
+    res = batch.select_floor(pol)
+    assert batch.kernel_launches() > 0
+    for i, (dims, kind, seed, q) in enumerate(STATES):
+        g = gf.create_grid(*dims, levels=L)
+        g.set_density(rhos[i], 3.0)
+        u1 = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        ref = g.select_floor(fs[i], u1, pol)
+        got = res[i]
+        for key in ("status", "floor_index", "escalated", "eta", "r50", "r100"):
+            a, b = got[key], ref[key]
+            assert a == b or (isinstance(a, float) and np.isnan(a) and np.isnan(b)), (i, key, a, b)
+        assert got["attempts"] == ref["attempts"], i
+        u2 = torch.zeros_like(u1)
+        batch.solution(i, u2)
+        if got["status"] == gf.GF_ACCEPTED:
+            assert torch.equal(u1, u2), i
+            m = O.Mesh(*dims)
+            E = O.young_modulus(_rho(dims, kind, seed, q), got["rho_min"], 3.0)
+            eta = O.true_residual(m, E, O.element_stiffness(), O.cantilever_load(m), u2.cpu().numpy())
+            assert eta <= 1e-6 * (1 + 1e-9)
+        g.close()
+    # a second run on the same batch (graphs reused) reproduces the first
+    res2 = batch.select_floor(pol)
+    strip = lambda r: {k: (None if isinstance(v, float) and np.isnan(v) else v) for k, v in r.items()}
+    assert [strip(r) for r in res2] == [strip(r) for r in res]
+    batch.close()
