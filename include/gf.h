@@ -66,10 +66,12 @@ extern "C" {
 #define GF_SEL_RULE   0   /* probe at rho0, Eq. (trigger) picks (rho0, ladder) or ladder */
 #define GF_SEL_FULL   1   /* no probe: try rho0 then every ladder floor in order */
 #define GF_SEL_GIVEN  2   /* no probe: start at first_index of (rho0, ladder...) */
+#define GF_SEL_MLP    3   /* probe at rho0 (fused), a trained gf_mlp picks the first floor */
 
 #define GF_MAX_LADDER 8
 
 typedef struct gf_grid gf_grid;
+typedef struct gf_mlp gf_mlp;
 
 typedef struct {
     int    restart;    /* FGMRES restart length m (>= 1, <= 64) */
@@ -105,6 +107,7 @@ typedef struct {
                                           independent solve, because the solver is deterministic);
                                           0: run the probe and the rho0 solve separately */
     gf_solve_opts solve;               /* restart, prec, smoother (kmax/tol/history ignored) */
+    gf_mlp* mlp;                       /* GF_SEL_MLP: trained selector (else ignored) */
 } gf_policy;
 
 typedef struct {
@@ -274,6 +277,33 @@ int gf_batch_autotune(gf_batch* b, int* tpb_out);
 int gf_batch_select_floor(gf_batch* b, const gf_policy* pol, gf_select_info* infos);
 /* Kernels launched so far on the batch (graph nodes counted per replay). */
 int gf_batch_stats(const gf_batch* b, long long* kernel_launches);
+
+/* ---- learned first-floor selector (no counterpart in the paper; its analogue is
+ *      the two-feature rule of Eq. trigger) ---------------------------------------- */
+
+/* MLP 6 -> 32 -> 32 -> 4 (tanh hidden layers, softmax), FP32, on the device.
+ * Parameters: one flat vector of 1412 floats, W1 (32x6, [out][in]), b1 (32),
+ * W2 (32x32), b2, W3 (4x32), b3. Inputs are standardised with (mu, sd) first.
+ * theta0: host, 1412 floats (the initial weights; the caller draws them). */
+int gf_mlp_create(const float* theta0, void* stream, gf_mlp** out);
+int gf_mlp_destroy(gf_mlp* M);
+int gf_mlp_set_norm(gf_mlp* M, const float* mu, const float* sd);      /* host, 6 each, sd > 0 */
+int gf_mlp_get_params(gf_mlp* M, float* theta);                        /* host, 1412 */
+/* logits (device n x 4) for rows of X (device n x 6). */
+int gf_mlp_forward(gf_mlp* M, const float* X, int n, float* logits);
+/* Mean cross-entropy over the rows (labels y, device ints in [0,4)) and its gradient;
+ * loss and grad (1412 floats) are HOST outputs. */
+int gf_mlp_loss_grad(gf_mlp* M, const float* X, const int* y, int n, float* loss, float* grad);
+/* Adam (beta 0.9/0.999, eps 1e-8) over `epochs` passes of full minibatches of size
+ * `batch`; perm (host, epochs*n sample indices, or NULL for the stored order) gives
+ * the minibatch order. *final_loss (host, optional) = loss of the last minibatch. */
+int gf_mlp_train(gf_mlp* M, const float* X, const int* y, int n, const int* perm, int epochs, int batch,
+                 float lr, float* final_loss);
+/* Class (argmax logit) for host feature rows (n x 6 doubles), n <= 4096, into cls (host). */
+int gf_mlp_predict(gf_mlp* M, const double* feat, int n, int* cls);
+/* The selector's 6 inputs for grid g: [log10 r50, log10 r100, r100/r50, fraction of
+ * voxels with rho_hat == 0, mean rho_hat, std rho_hat] (x: host, 6 doubles). */
+int gf_select_features(const gf_grid* g, double r50, double r100, double* x);
 
 /* ---- the one entry point that allocates nothing -------------------------------- */
 

@@ -742,3 +742,80 @@ def oc_iteration(mesh: Mesh, x: np.ndarray, f: np.ndarray, p: float, volfrac: fl
     dcx = density_filter_adjoint(Hf, dc)
     dvx = density_filter_adjoint(Hf, np.ones(mesh.n_elem))
     return oc_update(x, dcx, dvx, volfrac, move), res, C
+
+
+# ----------------------------------------------------------------------------
+# a11: learned first-floor selector (not in the paper; its analogue is Eq. trigger)
+# MLP 6 -> 32 -> 32 -> 4, tanh hidden layers, softmax + cross-entropy, Adam.
+# Parameters are one flat vector: W1 (32x6, [out][in]), b1 (32), W2 (32x32), b2,
+# W3 (4x32), b3 (4): 1412 numbers.
+# ----------------------------------------------------------------------------
+MLP_SIZES = (6, 32, 32, 4)
+
+
+def mlp_unpack(theta):
+    theta = np.asarray(theta, dtype=np.float64)
+    out, o = [], 0
+    for a, b in zip(MLP_SIZES[:-1], MLP_SIZES[1:]):
+        W = theta[o:o + a * b].reshape(b, a)
+        o += a * b
+        c = theta[o:o + b]
+        o += b
+        out.append((W, c))
+    assert o == theta.size
+    return out
+
+
+def mlp_n_params():
+    return sum(a * b + b for a, b in zip(MLP_SIZES[:-1], MLP_SIZES[1:]))
+
+
+def selector_features(r50, r100, rho_hat):
+    """x = [log10 r50, log10 r100, r100/r50, fraction of voxels at floor (rho_hat == 0),
+    mean rho_hat, std rho_hat] (population std)."""
+    rho_hat = np.asarray(rho_hat, dtype=np.float64)
+    return np.array([math.log10(max(r50, 1e-30)), math.log10(max(r100, 1e-30)), r100 / r50,
+                     float(np.mean(rho_hat == 0.0)), float(np.mean(rho_hat)), float(np.std(rho_hat))])
+
+
+def mlp_forward(theta, X, mu, sd):
+    """Logits for rows of X, after standardising with (mu, sd)."""
+    (W1, b1), (W2, b2), (W3, b3) = mlp_unpack(theta)
+    Z = (np.asarray(X, dtype=np.float64) - mu) / sd
+    H1 = np.tanh(Z @ W1.T + b1)
+    H2 = np.tanh(H1 @ W2.T + b2)
+    return H2 @ W3.T + b3
+
+
+def mlp_loss_grad(theta, X, y, mu, sd):
+    """Mean cross-entropy over the rows and its gradient (same flat layout as theta)."""
+    (W1, b1), (W2, b2), (W3, b3) = mlp_unpack(theta)
+    Z = (np.asarray(X, dtype=np.float64) - mu) / sd
+    n = Z.shape[0]
+    H1 = np.tanh(Z @ W1.T + b1)
+    H2 = np.tanh(H1 @ W2.T + b2)
+    L = H2 @ W3.T + b3
+    L = L - L.max(axis=1, keepdims=True)
+    P = np.exp(L)
+    P /= P.sum(axis=1, keepdims=True)
+    y = np.asarray(y, dtype=np.int64)
+    loss = float(-np.mean(np.log(P[np.arange(n), y])))
+    D3 = P.copy()
+    D3[np.arange(n), y] -= 1.0
+    D3 /= n
+    gW3, gb3 = D3.T @ H2, D3.sum(0)
+    D2 = (D3 @ W3) * (1.0 - H2 * H2)
+    gW2, gb2 = D2.T @ H1, D2.sum(0)
+    D1 = (D2 @ W2) * (1.0 - H1 * H1)
+    gW1, gb1 = D1.T @ Z, D1.sum(0)
+    g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
+    return loss, g
+
+
+def adam_step(theta, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (t counts from 1); returns (theta, m, v)."""
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mh = m / (1.0 - b1 ** t)
+    vh = v / (1.0 - b2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v

@@ -19,7 +19,8 @@ GF_OK = 0
 GF_FP64, GF_MIXED = 0, 1
 GF_FLAG_CONVERGED, GF_FLAG_MAX_ITERS, GF_FLAG_BREAKDOWN = 0, 1, 2
 GF_ACCEPTED, GF_NO_ADMISSIBLE_FLOOR = 0, 1
-GF_SEL_RULE, GF_SEL_FULL, GF_SEL_GIVEN = 0, 1, 2
+GF_SEL_RULE, GF_SEL_FULL, GF_SEL_GIVEN, GF_SEL_MLP = 0, 1, 2, 3
+MLP_PARAMS = 1412
 GF_MAX_LADDER = 8
 
 ERRORS = {-1: "GF_ERR_ARG", -2: "GF_ERR_OOM", -3: "GF_ERR_CUDA", -4: "GF_ERR_NONFINITE",
@@ -33,6 +34,8 @@ EXPORTED = [
     "gf_true_residual_noalloc", "gf_filter", "gf_filter_adjoint", "gf_oc_update", "gf_compliance",
     "gf_oc_iteration", "gf_create_batch", "gf_destroy_batch", "gf_batch_grid", "gf_batch_set_state",
     "gf_batch_solution", "gf_batch_autotune", "gf_batch_select_floor", "gf_batch_stats",
+    "gf_mlp_create", "gf_mlp_destroy", "gf_mlp_set_norm", "gf_mlp_get_params", "gf_mlp_forward",
+    "gf_mlp_loss_grad", "gf_mlp_train", "gf_mlp_predict", "gf_select_features",
 ]
 
 
@@ -56,7 +59,7 @@ class Policy(ctypes.Structure):
                 ("tau", c_double), ("kmax", c_int), ("probe_iters", c_int),
                 ("r50_escalate", c_double), ("r100_stall", c_double), ("plateau_ratio", c_double),
                 ("checkpoint_a", c_int), ("checkpoint_b", c_int), ("selector", c_int),
-                ("first_index", c_int), ("fuse_probe", c_int), ("solve", SolveOpts)]
+                ("first_index", c_int), ("fuse_probe", c_int), ("solve", SolveOpts), ("mlp", c_void_p)]
 
 
 class Attempt(ctypes.Structure):
@@ -121,6 +124,15 @@ def lib():
         "gf_batch_autotune": [P, POINTER(c_int)],
         "gf_batch_select_floor": [P, POINTER(Policy), POINTER(SelectInfo)],
         "gf_batch_stats": [P, POINTER(c_longlong)],
+        "gf_mlp_create": [POINTER(ctypes.c_float), P, POINTER(P)],
+        "gf_mlp_destroy": [P],
+        "gf_mlp_set_norm": [P, POINTER(ctypes.c_float), POINTER(ctypes.c_float)],
+        "gf_mlp_get_params": [P, POINTER(ctypes.c_float)],
+        "gf_mlp_forward": [P, P, c_int, P],
+        "gf_mlp_loss_grad": [P, P, P, c_int, POINTER(ctypes.c_float), POINTER(ctypes.c_float)],
+        "gf_mlp_train": [P, P, P, c_int, POINTER(c_int), c_int, c_int, ctypes.c_float, POINTER(ctypes.c_float)],
+        "gf_mlp_predict": [P, POINTER(c_double), c_int, POINTER(c_int)],
+        "gf_select_features": [P, c_double, c_double, POINTER(c_double)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -338,6 +350,9 @@ class Grid:
         return dict(status=info.status, floor_index=info.floor_index, rho_min=info.rho_min, eta=info.eta,
                     escalated=bool(info.escalated), attempts=atts, compliance=c.value)
 
+    def features(self, r50, r100):
+        return select_features(self._h, r50, r100)
+
     def stats(self):
         s = Stats()
         _check(lib().gf_get_stats(self._h, ctypes.byref(s)))
@@ -427,6 +442,100 @@ class Batch:
         n = c_longlong()
         _check(lib().gf_batch_stats(self._h, ctypes.byref(n)))
         return n.value
+
+    def features(self, i, r50, r100):
+        gh = c_void_p()
+        _check(lib().gf_batch_grid(self._h, int(i), ctypes.byref(gh)))
+        return select_features(gh, r50, r100)
+
+
+class MLP:
+    """The learned first-floor selector (gf_mlp): 6 -> 32 -> 32 -> 4, FP32, on the device."""
+
+    def __init__(self, theta0, stream=None):
+        import numpy as np
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        th = np.ascontiguousarray(theta0, dtype=np.float32)
+        if th.size != MLP_PARAMS:
+            raise ValueError(f"theta0 must have {MLP_PARAMS} entries")
+        handle = c_void_p()
+        _check(lib().gf_mlp_create(th.ctypes.data_as(POINTER(ctypes.c_float)), c_void_p(stream.cuda_stream),
+                                   ctypes.byref(handle)))
+        self._h = handle
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gf_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_norm(self, mu, sd):
+        mu = (ctypes.c_float * 6)(*[float(v) for v in mu])
+        sd = (ctypes.c_float * 6)(*[float(v) for v in sd])
+        _check(lib().gf_mlp_set_norm(self._h, mu, sd))
+
+    def params(self):
+        import numpy as np
+        out = np.zeros(MLP_PARAMS, dtype=np.float32)
+        _check(lib().gf_mlp_get_params(self._h, out.ctypes.data_as(POINTER(ctypes.c_float))))
+        return out
+
+    def forward(self, X, logits):
+        torch = _torch()
+        n = X.shape[0]
+        _check(lib().gf_mlp_forward(self._h, _ptr(X, torch.float32, 6 * n, "X"), int(n),
+                                    _ptr(logits, torch.float32, 4 * n, "logits")))
+        return logits
+
+    def loss_grad(self, X, y):
+        import numpy as np
+        torch = _torch()
+        n = X.shape[0]
+        loss = ctypes.c_float()
+        g = np.zeros(MLP_PARAMS, dtype=np.float32)
+        _check(lib().gf_mlp_loss_grad(self._h, _ptr(X, torch.float32, 6 * n, "X"), _ptr(y, torch.int32, n, "y"),
+                                      int(n), ctypes.byref(loss), g.ctypes.data_as(POINTER(ctypes.c_float))))
+        return loss.value, g
+
+    def train(self, X, y, epochs, batch, lr=1e-3, perm=None):
+        import numpy as np
+        torch = _torch()
+        n = X.shape[0]
+        p = None
+        if perm is not None:
+            perm = np.ascontiguousarray(perm, dtype=np.int32)
+            if perm.size != epochs * n:
+                raise ValueError("perm must hold epochs * n indices")
+            p = perm.ctypes.data_as(POINTER(c_int))
+        loss = ctypes.c_float()
+        _check(lib().gf_mlp_train(self._h, _ptr(X, torch.float32, 6 * n, "X"), _ptr(y, torch.int32, n, "y"), int(n),
+                                  p, int(epochs), int(batch), float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def predict(self, feats):
+        import numpy as np
+        f = np.ascontiguousarray(feats, dtype=np.float64).reshape(-1, 6)
+        cls = np.zeros(f.shape[0], dtype=np.int32)
+        _check(lib().gf_mlp_predict(self._h, f.ctypes.data_as(POINTER(c_double)), int(f.shape[0]),
+                                    cls.ctypes.data_as(POINTER(c_int))))
+        return cls
+
+
+def select_features(grid_handle, r50, r100):
+    x = (c_double * 6)()
+    _check(lib().gf_select_features(grid_handle, float(r50), float(r100), x))
+    return [x[i] for i in range(6)]
 
 
 def create_grid(nx, ny, nz, h=1.0, E0=1.0, nu=0.3, levels=3, stream=None) -> Grid:

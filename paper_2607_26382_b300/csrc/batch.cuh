@@ -234,11 +234,34 @@ int batch_tables(gf_batch* b)
 }
 
 struct BatchOut {
-    int k = 0, flag = 0, status = 0;
+    int k = 0, flag = 0, status = 0, first = 0;
     double r50 = 0.0, r100 = 0.0, stop_estimate = 0.0;
     bool decided = false, escalated = false;
     std::vector<double> hist;
 };
+
+// First floor for the listed states from their r50/r100: Eq. (trigger), or the MLP
+// on all rows at once.
+int batch_decide(gf_batch* b, const gf_policy* pol, const std::vector<int>& rows, std::vector<BatchOut>& out)
+{
+    if (rows.empty()) return GF_OK;
+    const int nf = pol->n_ladder + 1;
+    if (pol->selector == GF_SEL_MLP) {
+        std::vector<double> feat(rows.size() * 6);
+        for (size_t r = 0; r < rows.size(); ++r)
+            RET(gf_select_features(b->g[rows[r]], out[rows[r]].r50, out[rows[r]].r100, &feat[6 * r]));
+        std::vector<int> cls(rows.size());
+        for (size_t r0 = 0; r0 < rows.size(); r0 += 4096) {
+            const int n = (int)std::min<size_t>(4096, rows.size() - r0);
+            RET(mlp_predict_host(pol->mlp, &feat[6 * r0], n, &cls[r0]));
+        }
+        for (size_t r = 0; r < rows.size(); ++r) out[rows[r]].first = std::min(std::max(cls[r], 0), nf - 1);
+    } else {
+        for (int i : rows) out[i].first = gf_trigger_rule(out[i].r50, out[i].r100, pol) ? 1 : 0;
+    }
+    for (int i : rows) out[i].escalated = out[i].first > 0;
+    return GF_OK;
+}
 
 // One lockstep FGMRES solve of the active states from u = 0. probe_at > 0: at that
 // step, states still running get their r50/r100 read and the rule applied;
@@ -282,7 +305,7 @@ int batch_solve(gf_batch* b, const gf_solve_opts* o, const std::vector<int>& act
                 LAUNCH(b->g[0], (B + 127) / 128, 128, gf::batch_gather_kernel, (gf::KState* const*)b->tab.st,
                        (double* const*)b->tab.hist, B, pol->checkpoint_a, pol->checkpoint_b, b->gather_dev);
                 CK(cudaStreamSynchronize(b->stream));
-                std::vector<int> ab(B, 0);
+                std::vector<int> ab(B, 0), rows;
                 bool any_ab = false;
                 for (int i = 0; i < B; ++i) {
                     if (!active[i] || (int)b->gather_host[4 * i] != gf::KS_RUN) continue;
@@ -290,7 +313,10 @@ int batch_solve(gf_batch* b, const gf_solve_opts* o, const std::vector<int>& act
                     out[i].decided = true;
                     out[i].r50 = b->gather_host[4 * i + 2];
                     out[i].r100 = b->gather_host[4 * i + 3];
-                    out[i].escalated = gf_trigger_rule(out[i].r50, out[i].r100, pol) == 1;
+                    rows.push_back(i);
+                }
+                RET(batch_decide(b, pol, rows, out));
+                for (int i : rows) {
                     if (out[i].escalated) {
                         ab[i] = aborted[i] = 1;
                         any_ab = true;
@@ -570,7 +596,7 @@ int gf_batch_select_floor(gf_batch* b, const gf_policy* pol, gf_select_info* inf
     o.tol = pol->tau;
     o.kmax = pol->kmax;
     RET(validate_opts(&o));
-    if (pol->selector == GF_SEL_RULE && pol->probe_iters > pol->kmax)
+    if ((pol->selector == GF_SEL_RULE || pol->selector == GF_SEL_MLP) && pol->probe_iters > pol->kmax)
         return set_err(GF_ERR_ARG, "batched policy needs probe_iters <= kmax");
     const int B = b->B;
     for (int i = 0; i < B; ++i)
@@ -587,7 +613,8 @@ int gf_batch_select_floor(gf_batch* b, const gf_policy* pol, gf_select_info* inf
         infos[i].floor_index = -1;
         infos[i].r50 = infos[i].r100 = infos[i].rho_min = infos[i].eta = std::nan("");
     }
-    const bool rule = pol->selector == GF_SEL_RULE;
+    const bool rule = pol->selector == GF_SEL_RULE || pol->selector == GF_SEL_MLP;
+    if (pol->selector == GF_SEL_MLP && !pol->mlp) return set_err(GF_ERR_ARG, "GF_SEL_MLP needs a trained gf_mlp");
     if (pol->selector == GF_SEL_GIVEN) {
         if (pol->first_index < 0 || pol->first_index >= nf) return set_err(GF_ERR_ARG, "first_index");
         for (int i = 0; i < B; ++i) {
@@ -617,20 +644,22 @@ int gf_batch_select_floor(gf_batch* b, const gf_policy* pol, gf_select_info* inf
             gf_select_info& inf = infos[i];
             if (probe_phase) {
                 if (res[i].decided) {
-                    inf.r50 = res[i].r50;
-                    inf.r100 = res[i].r100;
-                    inf.escalated = res[i].escalated;
                     inf.probe_iters_run = pol->probe_iters;
                 } else {
                     inf.probe_iters_run = std::min(res[i].k, pol->probe_iters);
-                    RET(gf_probe_features(res[i].hist.data(), res[i].k, pol, &inf.r50, &inf.r100));
-                    inf.escalated = gf_trigger_rule(inf.r50, inf.r100, pol);
+                    RET(gf_probe_features(res[i].hist.data(), res[i].k, pol, &res[i].r50, &res[i].r100));
+                    RET(batch_decide(b, pol, std::vector<int>{i}, res));
                 }
+                inf.r50 = res[i].r50;
+                inf.r100 = res[i].r100;
+                inf.escalated = res[i].escalated;
                 if (inf.escalated) {
-                    next[i] = 1;
+                    next[i] = res[i].first;
                     continue;
                 }
             }
+            if (phase == 0 && pol->selector == GF_SEL_FULL && next[i] == 0)   // rho0 attempt's features
+                RET(gf_probe_features(res[i].hist.data(), res[i].k, pol, &inf.r50, &inf.r100));
             // guard on the selected solve
             double eta = 0.0;
             gf_grid* g = b->g[i];

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <utility>
 #include <mutex>
+#include <functional>
 
 namespace {
 
@@ -100,6 +101,10 @@ void build_k0(double E0, double nu, double* K)
 
 }  // namespace
 
+namespace {
+int mlp_predict_host(gf_mlp* M, const double* feat, int n, int* cls);
+}
+
 struct gf_grid {
     int nx, ny, nz, L;
     double h, E0, nu;
@@ -140,6 +145,7 @@ struct gf_grid {
     bool use_graphs = true;
     int tpb[2] = {256, 256};          // node-stencil block size: [0] FP64, [1] FP32 (autotuned)
     bool skip_coarse_inverse = false; // batched set-up builds the coarsest inverse itself
+    double dstat[3] = {0.0, 0.0, 0.0}; // fraction of rho_hat == 0, mean, std (at set_density)
     // optimisation-loop scratch (allocated on first use)
     double *oc_rho = nullptr, *oc_dc = nullptr, *oc_dcx = nullptr, *oc_dvx = nullptr, *oc_ones = nullptr;
     gf::OCState* oc_st = nullptr;
@@ -477,7 +483,9 @@ int run_step(gf_grid* g, int j, const gf_solve_opts* o)
 struct ProbeHook {
     int at = -1;
     const gf_policy* pol = nullptr;
+    std::function<int(double, double, int*)> decide;   // -> first floor index (0 = rho0)
     bool decided = false, escalate = false;
+    int first = 0, err = GF_OK;
     double r50 = 0.0, r100 = 0.0;
 };
 
@@ -514,7 +522,8 @@ int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, g
                     hook->decided = true;
                     hook->r50 = h2[0];
                     hook->r100 = h2[1];
-                    hook->escalate = gf_trigger_rule(h2[0], h2[1], hook->pol) == 1;
+                    RET(hook->decide(h2[0], h2[1], &hook->first));
+                    hook->escalate = hook->first > 0;
                     if (hook->escalate) {
                         aborted = true;
                         break;
@@ -765,6 +774,20 @@ int gf_set_density(gf_grid* g, const double* rho_hat, double p)
         g->has_density = false;
         return set_err(GF_ERR_NONFINITE, "density has NaN/Inf or values outside [0,1]");
     }
+    LAUNCH(g, g->nbr, 256, gf::density_stats_kernel, (const double*)g->rho64, g->nel, g->partial);
+    std::vector<double> part((size_t)g->nbr * 3);
+    CK(cudaMemcpyAsync(part.data(), g->partial, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    double z = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int b = 0; b < g->nbr; ++b) {
+        z += part[3 * b];
+        s1 += part[3 * b + 1];
+        s2 += part[3 * b + 2];
+    }
+    const double n = (double)g->nel, mean = s1 / n;
+    g->dstat[0] = z / n;
+    g->dstat[1] = mean;
+    g->dstat[2] = std::sqrt(std::max(0.0, s2 / n - mean * mean));
     g->p = p;
     g->has_density = true;
     return GF_OK;
@@ -925,7 +948,20 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
     for (int i = 0; i < pol->n_ladder; ++i) floors[i + 1] = pol->ladder[i];
     const int nf = pol->n_ladder + 1;
     int start = 0;
-    if (pol->selector == GF_SEL_RULE && pol->fuse_probe) {
+    if (pol->selector == GF_SEL_MLP && !pol->mlp) return set_err(GF_ERR_ARG, "GF_SEL_MLP needs a trained gf_mlp");
+    auto decide = [&](double r50, double r100, int* first) -> int {
+        if (pol->selector == GF_SEL_MLP) {
+            double x[6];
+            RET(gf_select_features(g, r50, r100, x));
+            int c = 0;
+            RET(mlp_predict_host(pol->mlp, x, 1, &c));
+            *first = std::min(std::max(c, 0), nf - 1);
+        } else {
+            *first = gf_trigger_rule(r50, r100, pol) ? 1 : 0;
+        }
+        return GF_OK;
+    };
+    if ((pol->selector == GF_SEL_RULE && pol->fuse_probe) || pol->selector == GF_SEL_MLP) {
         // Probe fused with the rho0 solve: run the rho0 solve with budget kmax and read
         // r50/r100 off its history after probe_iters steps (or at its stop).
         RET(gf_set_floor(g, pol->rho0));
@@ -937,6 +973,7 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
         ProbeHook hook;
         hook.at = pol->probe_iters;
         hook.pol = pol;
+        hook.decide = decide;
         std::vector<double> hist((size_t)so.kmax + 1);
         gf_solve_info si{};
         CK(cudaMemsetAsync(u, 0, sizeof(double) * g->ndof, g->stream));
@@ -944,14 +981,14 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
         if (hook.decided) {
             info->r50 = hook.r50;
             info->r100 = hook.r100;
-            info->escalated = hook.escalate;
+            start = hook.first;
             info->probe_iters_run = pol->probe_iters;
         } else {
             info->probe_iters_run = std::min(si.iters, pol->probe_iters);
             RET(gf_probe_features(hist.data(), si.iters, pol, &info->r50, &info->r100));
-            info->escalated = gf_trigger_rule(info->r50, info->r100, pol);
+            RET(decide(info->r50, info->r100, &start));
         }
-        start = info->escalated ? 1 : 0;
+        info->escalated = start > 0;
         if (!info->escalated && !cap) {
             // the rho0 solve is the first candidate's selected solve
             double eta = 0.0;
@@ -1001,7 +1038,11 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
         o.kmax = pol->kmax;
         gf_solve_info si{};
         CK(cudaMemsetAsync(u, 0, sizeof(double) * g->ndof, g->stream));
-        RET(solve_impl(g, f, u, &o, &si, true, nullptr));
+        const bool rho0_full = (idx == 0 && pol->selector == GF_SEL_FULL);
+        std::vector<double> h0(rho0_full ? (size_t)o.kmax + 1 : 0);
+        RET(solve_impl(g, f, u, &o, &si, true, rho0_full ? h0.data() : nullptr));
+        if (rho0_full)   // features of the rho0 attempt (what a probe would have recorded)
+            RET(gf_probe_features(h0.data(), si.iters, pol, &info->r50, &info->r100));
         double eta = 0.0;
         RET(guard_impl(g, f, u, &eta));
         gf_attempt& a = info->attempts[info->n_attempts++];
@@ -1091,6 +1132,20 @@ int gf_oc_iteration(gf_grid* g, double* x, const double* f, double* u, const gf_
     RET(filter_impl(g, g->oc_ones, g->oc_dvx, r_min, true));
     RET(oc_update_impl(g, x, g->oc_dcx, g->oc_dvx, volfrac, move, g->oc_rho));
     CK(cudaMemcpyAsync(x, g->oc_rho, sizeof(double) * g->nel, cudaMemcpyDeviceToDevice, g->stream));
+    return GF_OK;
+}
+
+int gf_select_features(const gf_grid* g, double r50, double r100, double* x)
+{
+    RET(check_grid(g));
+    if (!x) return set_err(GF_ERR_ARG, "null x");
+    if (!g->has_density) return set_err(GF_ERR_STATE, "set_density first");
+    x[0] = std::log10(std::max(r50, 1e-30));
+    x[1] = std::log10(std::max(r100, 1e-30));
+    x[2] = r100 / r50;
+    x[3] = g->dstat[0];
+    x[4] = g->dstat[1];
+    x[5] = g->dstat[2];
     return GF_OK;
 }
 
@@ -1204,4 +1259,5 @@ extern "C" int gf_true_residual_noalloc(int nx, int ny, int nz, double h, double
     return GF_OK;
 }
 
+#include "mlp.cuh"
 #include "batch.cuh"

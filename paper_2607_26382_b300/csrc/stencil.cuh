@@ -352,6 +352,36 @@ __global__ void density_check_kernel(const double* __restrict__ rho, __nv_bfloat
     r16[e] = __double2bfloat16(r);
 }
 
+// Per-block [count of rho == 0, sum rho, sum rho^2] for the selector's density inputs.
+__global__ void __launch_bounds__(256)
+density_stats_kernel(const double* __restrict__ rho, long long n, double* __restrict__ partial)
+{
+    __shared__ double red[3][8];
+    const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    const long long r0 = (long long)blockIdx.x * chunk;
+    const long long r1 = r0 + chunk < n ? r0 + chunk : n;
+    double a[3] = {0.0, 0.0, 0.0};
+    for (long long e = r0 + threadIdx.x; e < r1; e += blockDim.x) {
+        const double r = rho[e];
+        a[0] += (r == 0.0) ? 1.0 : 0.0;
+        a[1] += r;
+        a[2] = fma(r, r, a[2]);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        double v = a[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        partial[3 * blockIdx.x + threadIdx.x] = s;
+    }
+}
+
 // Dense coarsest operator (all DOFs of the coarsest level, row-major n x n), one
 // thread per entry: A[r][c] = sum over the elements e containing both nodes of
 // E_e h K0[3 a_r + c_r][3 a_c + c_c], summed in a fixed element order so that the

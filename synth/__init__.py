@@ -129,3 +129,37 @@ def batch_grid_sizes(n_states: int = 102):
     ny = nz = nx/2, assigned round-robin (every size divisible by 8)."""
     sizes = (32, 48, 64, 80)
     return [(sizes[i % 4], sizes[i % 4] // 2, sizes[i % 4] // 2) for i in range(n_states)]
+
+
+def mlp_init(seed: int, sizes=(6, 32, 32, 4)) -> np.ndarray:
+    """Initial weights for the selector MLP (flat, float32): W ~ N(0, 1/fan_in), b = 0,
+    in the layout W1, b1, W2, b2, W3, b3 ([out][in] rows)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        parts.append(rng.normal(0.0, 1.0 / np.sqrt(a), size=(b, a)).ravel())
+        parts.append(np.zeros(b))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def epoch_permutations(n: int, epochs: int, seed: int) -> np.ndarray:
+    """epochs concatenated random permutations of range(n) (minibatch order)."""
+    rng = np.random.default_rng(seed)
+    return np.concatenate([rng.permutation(n) for _ in range(epochs)]).astype(np.int32)
+
+
+def selector_training_states(n: int, dims, seed: int):
+    """A mix of hard-field states for selector training: Bernoulli fields with solid
+    probability q ~ U(0.15, 0.6) and smoothed-Gaussian fields with floor fraction
+    ~ U(0.1, 0.6) and sigma in {1, 2, 3}, alternating."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    out = []
+    for i in range(n):
+        s = int(rng.integers(0, 2**31 - 1))
+        if i % 2 == 0:
+            out.append(bernoulli_density(nx, ny, nz, s, float(rng.uniform(0.15, 0.6))))
+        else:
+            out.append(smoothed_gaussian_density(nx, ny, nz, s, float(rng.choice([1.0, 2.0, 3.0])),
+                                                 float(rng.uniform(0.1, 0.6))))
+    return out

@@ -552,3 +552,37 @@ def test_filtered_sensitivity_chain_matches_central_differences():
         xm[e] -= h
         fd = (C(xp)[0] - C(xm)[0]) / (2 * h)
         assert abs(fd - g[e]) < 1e-5 * abs(g[e])
+
+
+def test_mlp_gradient_central_differences_and_adam():
+    rng = np.random.default_rng(3)
+    n = O.mlp_n_params()
+    assert n == 1412
+    theta = rng.normal(0, 0.3, n)
+    X = rng.normal(0, 1, (17, 6))
+    y = rng.integers(0, 4, 17)
+    mu, sd = X.mean(0), X.std(0) + 0.1
+    loss, g = O.mlp_loss_grad(theta, X, y, mu, sd)
+    # loss equals -mean log softmax of the forward logits
+    Lg = O.mlp_forward(theta, X, mu, sd)
+    ref = -np.mean(Lg[np.arange(17), y] - np.log(np.exp(Lg).sum(1)))
+    assert abs(loss - ref) < 1e-12
+    for i in list(range(0, n, 97)) + [191, 223, 1247, 1279, 1407, 1411]:
+        h = 1e-6
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (O.mlp_loss_grad(tp, X, y, mu, sd)[0] - O.mlp_loss_grad(tm, X, y, mu, sd)[0]) / (2 * h)
+        assert abs(fd - g[i]) < 1e-7 + 1e-5 * abs(g[i]), i
+    # Adam: first step moves every parameter by lr * sign(g) (bias-corrected)
+    th2, m, v = O.adam_step(theta, g, np.zeros(n), np.zeros(n), 1, lr=1e-3)
+    nz = np.abs(g) > 1e-3     # eps = 1e-8 is negligible against |g| there
+    assert np.allclose((theta - th2)[nz], 1e-3 * np.sign(g[nz]), rtol=1e-4)
+    # and reduces the loss along a small step
+    assert O.mlp_loss_grad(th2, X, y, mu, sd)[0] < loss
+
+
+def test_selector_features():
+    rho = np.array([0.0, 0.0, 1.0, 0.5])
+    x = O.selector_features(1e-3, 1e-5, rho)
+    assert np.allclose(x, [-3, -5, 1e-2, 0.5, 0.375, np.std(rho)])
