@@ -81,6 +81,8 @@ typedef struct {
     int    nu1, nu2;   /* pre/post node-block Jacobi sweeps (>= 1) */
     double omega;      /* Jacobi damping */
     double* history;   /* host, optional: receives history[0..iters] (length >= kmax+1) */
+    int    outer;      /* outer (Krylov) operator: 0 = native FP64 K*u; 1 = split-integer
+                          FP64-class K*u (gf_apply_K_split). The guard is always native FP64. */
 } gf_solve_opts;
 
 typedef struct {
@@ -176,6 +178,15 @@ int gf_free_mask(gf_grid* g, uint8_t* mask);
 /* y = K(rho_min) u on free DOFs, FP64 (Eq. frozen_operator), matrix-free. u, y:
  * n_dof doubles, must not alias. */
 int gf_apply_K(gf_grid* g, const double* u, double* y);
+
+/* The same FP64 operator evaluated without FP64 multiply-adds: K0 = s*M with an
+ * integer matrix M (exists for nu = 0.3 and other Poisson ratios with a small
+ * integer form; GF_ERR_ARG otherwise). Each node tile writes its u values on a
+ * common exponent with 50 bits, cuts them into five 10-bit digits, forms M times
+ * each digit slice exactly in FP32, recombines the slices and applies s*E_e in
+ * double-float arithmetic. Error ~2^-46 of the tile's largest |u| times |M| (near
+ * FP64 rounding). u, y: n_dof doubles, distinct. */
+int gf_apply_K_split(gf_grid* g, const double* u, double* y);
 
 /* Same operator in FP32 with the moduli computed from the BF16 density copy (the
  * V-cycle's fine-level operator in GF_MIXED). u, y: n_dof floats. */

@@ -35,7 +35,7 @@ EXPORTED = [
     "gf_oc_iteration", "gf_create_batch", "gf_destroy_batch", "gf_batch_grid", "gf_batch_set_state",
     "gf_batch_solution", "gf_batch_autotune", "gf_batch_select_floor", "gf_batch_stats",
     "gf_mlp_create", "gf_mlp_destroy", "gf_mlp_set_norm", "gf_mlp_get_params", "gf_mlp_forward",
-    "gf_mlp_loss_grad", "gf_mlp_train", "gf_mlp_predict", "gf_select_features",
+    "gf_mlp_loss_grad", "gf_mlp_train", "gf_mlp_predict", "gf_select_features", "gf_apply_K_split",
 ]
 
 
@@ -47,7 +47,8 @@ class GFError(RuntimeError):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("restart", c_int), ("kmax", c_int), ("tol", c_double), ("prec", c_int),
-                ("nu1", c_int), ("nu2", c_int), ("omega", c_double), ("history", POINTER(c_double))]
+                ("nu1", c_int), ("nu2", c_int), ("omega", c_double), ("history", POINTER(c_double)),
+                ("outer", c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -133,6 +134,7 @@ def lib():
         "gf_mlp_train": [P, P, P, c_int, POINTER(c_int), c_int, c_int, ctypes.c_float, POINTER(ctypes.c_float)],
         "gf_mlp_predict": [P, POINTER(c_double), c_int, POINTER(c_int)],
         "gf_select_features": [P, c_double, c_double, POINTER(c_double)],
+        "gf_apply_K_split": [P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -261,6 +263,11 @@ class Grid:
         _check(lib().gf_apply_K(self._h, _ptr(u, t, self.n_dof, "u"), _ptr(y, t, self.n_dof, "y")))
         return y
 
+    def apply_K_split(self, u, y):
+        t = _torch().float64
+        _check(lib().gf_apply_K_split(self._h, _ptr(u, t, self.n_dof, "u"), _ptr(y, t, self.n_dof, "y")))
+        return y
+
     def apply_K_f32(self, u, y):
         t = _torch().float32
         _check(lib().gf_apply_K_f32(self._h, _ptr(u, t, self.n_dof, "u"), _ptr(y, t, self.n_dof, "y")))
@@ -274,11 +281,11 @@ class Grid:
 
     # solve / guard / policy
     def solve(self, f, u, restart=30, kmax=200, tol=1e-6, prec=GF_FP64, nu1=2, nu2=2, omega=0.6,
-              want_history=True):
+              want_history=True, outer=0):
         t = _torch().float64
         hist = (c_double * (kmax + 1))() if want_history else None
         o = SolveOpts(int(restart), int(kmax), float(tol), int(prec), int(nu1), int(nu2), float(omega),
-                      ctypes.cast(hist, POINTER(c_double)) if hist is not None else None)
+                      ctypes.cast(hist, POINTER(c_double)) if hist is not None else None, int(outer))
         info = SolveInfo()
         _check(lib().gf_solve(self._h, _ptr(f, t, self.n_dof, "f"), _ptr(u, t, self.n_dof, "u"),
                               ctypes.byref(o), ctypes.byref(info)))

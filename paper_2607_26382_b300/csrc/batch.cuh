@@ -111,7 +111,7 @@ struct gf_batch {
     cudaGraphExec_t start[2] = {};
     cudaGraphExec_t end = nullptr;
     long long nodes_step[gf::KRY_MMAX] = {}, nodes_start[2] = {}, nodes_end = 0;
-    int key_prec = -1, key_nu1 = -1, key_nu2 = -1, key_m = -1;
+    int key_prec = -1, key_nu1 = -1, key_nu2 = -1, key_m = -1, key_outer = -1;
     double key_omega = -1.0;
     void* key_ptrs = nullptr;   // V of state 0 when captured (realloc invalidates)
     // device tables
@@ -191,8 +191,9 @@ int batch_graphs(gf_batch* b, const gf_solve_opts* o)
         key = key * 1000003u ^ (uintptr_t)g->V ^ ((uintptr_t)g->Z << 1) ^ ((uintptr_t)g->hist << 2);
     void* ptr0 = (void*)key;
     if (b->key_prec != o->prec || b->key_nu1 != o->nu1 || b->key_nu2 != o->nu2 || b->key_omega != o->omega ||
-        b->key_m != m || b->key_ptrs != ptr0) {
+        b->key_m != m || b->key_ptrs != ptr0 || b->key_outer != o->outer) {
         batch_drop_graphs(b);
+        b->key_outer = o->outer;
         b->key_prec = o->prec;
         b->key_nu1 = o->nu1;
         b->key_nu2 = o->nu2;
@@ -202,7 +203,7 @@ int batch_graphs(gf_batch* b, const gf_solve_opts* o)
     }
     for (int first = 0; first < 2; ++first)
         if (!b->start[first])
-            RET(batch_capture(b, [&](int i) { return cycle_start(b->g[i], b->f[i], b->u[i], first == 1, first == 1); },
+            RET(batch_capture(b, [&](int i) { return cycle_start(b->g[i], b->f[i], b->u[i], first == 1, first == 1, o->outer); },
                               &b->start[first], &b->nodes_start[first]));
     for (int j = 0; j < m; ++j)
         if (!b->step[j])

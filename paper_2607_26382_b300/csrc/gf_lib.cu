@@ -7,6 +7,7 @@
 #include "stencil.cuh"
 #include "krylov.cuh"
 #include "oc.cuh"
+#include "split.cuh"
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -146,6 +147,12 @@ struct gf_grid {
     int tpb[2] = {256, 256};          // node-stencil block size: [0] FP64, [1] FP32 (autotuned)
     bool skip_coarse_inverse = false; // batched set-up builds the coarsest inverse itself
     double dstat[3] = {0.0, 0.0, 0.0}; // fraction of rho_hat == 0, mean, std (at set_density)
+    // split-integer operator: K0 = s_split * M with integer M (when it exists)
+    bool has_split = false;
+    double s_split = 0.0;
+    gf::MParam Msplit;
+    float2* Edf = nullptr;            // s_split * E_e (fine level) as float pairs
+    int gkey_outer = -1;
     // optimisation-loop scratch (allocated on first use)
     double *oc_rho = nullptr, *oc_dc = nullptr, *oc_dcx = nullptr, *oc_dvx = nullptr, *oc_ones = nullptr;
     gf::OCState* oc_st = nullptr;
@@ -303,6 +310,22 @@ int applyK64(gf_grid* g, const double* u, double* y, const int* halt)
     return stencil<double, double, gf::ST_APPLY>(g, 0, u, nullptr, y, g->lv[0].E64, g->K0d, 0.0, halt);
 }
 
+int applyKsplit(gf_grid* g, const double* u, double* y, const int* halt)
+{
+    g->stats.apply_K_fp64++;
+    const dim3 grid((g->nx + 1 + gf::SPX - 1) / gf::SPX, (g->ny + 1 + gf::SPY - 1) / gf::SPY,
+                    (g->nz + 1 + gf::SPZ - 1) / gf::SPZ);
+    LAUNCH(g, grid, dim3(gf::SPX, gf::SPY, gf::SPZ), gf::apply_split_kernel, u, y, (const float2*)g->Edf,
+           g->lv[0].dims(), g->Msplit, halt);
+    return GF_OK;
+}
+
+// The outer (Krylov) operator: native FP64, or the split-integer FP64-class one.
+int applyOuter(gf_grid* g, const double* u, double* y, const int* halt, int outer)
+{
+    return outer ? applyKsplit(g, u, y, halt) : applyK64(g, u, y, halt);
+}
+
 // ------------------------------------------------------------------ set-up ----
 int alloc(void** p, size_t bytes)
 {
@@ -416,7 +439,7 @@ int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
     double* w = g->V + (long long)(j + 1) * ld;
     const int* halt = &g->st->status;
     RET(vcycle_dispatch(g, vj, zj, o->prec, o->nu1, o->nu2, o->omega, halt));
-    RET(applyK64(g, zj, w, halt));
+    RET(applyOuter(g, zj, w, halt, o->outer));
     switch (pick_nv(j + 1)) {
         case 8: RET(cgs2_step<8>(g, j, w)); break;
         case 16: RET(cgs2_step<16>(g, j, w)); break;
@@ -427,11 +450,11 @@ int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
 }
 
 // r = M f - K x into V_0, ||r||, ||Mf||, history[k], g = beta e1, V_0 /= beta.
-int cycle_start(gf_grid* g, const double* f, const double* x, bool x_zero, bool first)
+int cycle_start(gf_grid* g, const double* f, const double* x, bool x_zero, bool first, int outer)
 {
     double* v0 = g->V;
     const int* skip = &g->st->skip;
-    if (!x_zero) RET(applyK64(g, x, v0, skip));
+    if (!x_zero) RET(applyOuter(g, x, v0, skip, outer));
     LAUNCH(g, g->nbr, gf::RED_THREADS, gf::residual_norms_kernel, f, v0, v0, g->ndof, g->nx + 1, g->partial,
            x_zero ? 1 : 0, skip);
     LAUNCH(g, 1, 64, gf::reduce_partials_kernel, g->partial, g->nbr, 2, 2, g->st, 0, 0);
@@ -444,8 +467,10 @@ int cycle_start(gf_grid* g, const double* f, const double* x, bool x_zero, bool 
 int run_step(gf_grid* g, int j, const gf_solve_opts* o)
 {
     if (!g->use_graphs) return arnoldi_step(g, j, o);
-    if (g->gkey_prec != o->prec || g->gkey_nu1 != o->nu1 || g->gkey_nu2 != o->nu2 || g->gkey_omega != o->omega) {
+    if (g->gkey_prec != o->prec || g->gkey_nu1 != o->nu1 || g->gkey_nu2 != o->nu2 || g->gkey_omega != o->omega ||
+        g->gkey_outer != o->outer) {
         drop_graphs(g);
+        g->gkey_outer = o->outer;
         g->gkey_prec = o->prec;
         g->gkey_nu1 = o->nu1;
         g->gkey_nu2 = o->nu2;
@@ -503,7 +528,7 @@ int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, g
     long long launched = 0;
     HostState hs{};
     for (;;) {
-        RET(cycle_start(g, f, u, x_zero && first, first));
+        RET(cycle_start(g, f, u, x_zero && first, first, o->outer));
         first = false;
         x_zero = false;
         CK(cudaStreamSynchronize(g->stream));
@@ -562,6 +587,7 @@ int validate_opts(const gf_solve_opts* o)
     if (o->prec != GF_FP64 && o->prec != GF_MIXED) return set_err(GF_ERR_ARG, "prec");
     if (o->nu1 < 1 || o->nu2 < 1 || o->nu1 > 16 || o->nu2 > 16) return set_err(GF_ERR_ARG, "nu1/nu2 in [1,16]");
     if (!(o->omega > 0.0 && o->omega < 2.0)) return set_err(GF_ERR_ARG, "omega in (0,2)");
+    if (o->outer != 0 && o->outer != 1) return set_err(GF_ERR_ARG, "outer must be 0 (FP64) or 1 (split)");
     return GF_OK;
 }
 
@@ -680,6 +706,20 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         g->K0d.k[q] = K[q];
         g->K0f.k[q] = (float)K[q];
     }
+    // K0 = s * M with integer M, |M| <= 682 (digit products stay exact in FP32)
+    for (int kk = 1; kk <= 682 && !g->has_split; ++kk) {
+        const double sc = K[0] / kk;
+        bool ok = true;
+        for (int q = 0; q < 576 && ok; ++q) {
+            const double mq = K[q] / sc, rq = std::nearbyint(mq);
+            ok = std::fabs(mq - rq) <= 1e-9 * std::max(1.0, std::fabs(mq)) && std::fabs(rq) <= 682.0;
+        }
+        if (ok) {
+            g->has_split = true;
+            g->s_split = sc;
+            for (int q = 0; q < 576; ++q) g->Msplit.m[q] = (float)std::nearbyint(K[q] / sc);
+        }
+    }
     for (int l = 0; l < levels; ++l) {
         Level L;
         L.nx = nx >> l; L.ny = ny >> l; L.nz = nz >> l;
@@ -703,7 +743,8 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     if ((r = allocT(&g->Ainv, (size_t)g->nc * g->nc)) || (r = allocT(&g->gjcol, g->nc)) ||
         (r = allocT(&g->gjrow, g->nc)) || (r = allocT(&g->dflag, 4)) || (r = allocT(&g->rho64, g->nel)) ||
         (r = allocT(&g->rho16, g->nel)) || (r = allocT(&g->work, g->ndof)) ||
-        (r = allocT(&g->partial, (size_t)g->nbr * 40)) || (r = allocT(&g->st, 1)) || (r = allocT(&g->gst, 1)))
+        (r = allocT(&g->partial, (size_t)g->nbr * 40)) || (r = allocT(&g->st, 1)) || (r = allocT(&g->gst, 1)) ||
+        (r = allocT(&g->Edf, g->nel)))
         return fail(r);
     if (cudaHostAlloc((void**)&g->host_status, sizeof(int), cudaHostAllocMapped) != cudaSuccess)
         return fail(set_err(GF_ERR_CUDA, "cudaHostAlloc"));
@@ -737,6 +778,7 @@ int gf_destroy_grid(gf_grid* g)
     cudaFree(g->rho64); cudaFree(g->rho16); cudaFree(g->work); cudaFree(g->partial);
     cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Z); cudaFree(g->hist);
     cudaFree(g->xsave);
+    cudaFree(g->Edf);
     cudaFree(g->oc_rho); cudaFree(g->oc_dc); cudaFree(g->oc_dcx); cudaFree(g->oc_dvx); cudaFree(g->oc_ones);
     cudaFree(g->oc_st);
     if (g->host_status) cudaFreeHost(g->host_status);
@@ -805,6 +847,7 @@ int gf_set_floor(gf_grid* g, double rho_min)
     LAUNCH(g, nblk(g->nel), 256, gf::modulus_fp64_kernel, g->rho64, f.E64, g->nel, rho_min, p, p_int, f.h);
     LAUNCH(g, nblk(g->nel), 256, gf::modulus_fp32_kernel, g->rho16, f.E32, g->nel, (float)rho_min, (float)p,
            p_int, (float)f.h);
+    if (g->has_split) LAUNCH(g, nblk(g->nel), 256, gf::edf_kernel, (const double*)f.E64, g->s_split, g->Edf, g->nel);
     for (int l = 1; l < g->L; ++l) {
         Level& c = g->lv[l];
         LAUNCH(g, nblk(c.nel), 256, gf::coarsen_kernel<double>, g->lv[l - 1].E64, c.E64, c.dims());
@@ -841,6 +884,16 @@ int gf_apply_K(gf_grid* g, const double* u, double* y)
     if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
     RET(set_device(g));
     return applyK64(g, u, y, nullptr);
+}
+
+int gf_apply_K_split(gf_grid* g, const double* u, double* y)
+{
+    RET(check_grid(g));
+    if (!u || !y || u == y) return set_err(GF_ERR_ARG, "u, y non-null and distinct");
+    if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
+    if (!g->has_split) return set_err(GF_ERR_ARG, "K0 has no small integer form for this Poisson ratio");
+    RET(set_device(g));
+    return applyKsplit(g, u, y, nullptr);
 }
 
 int gf_apply_K_f32(gf_grid* g, const float* u, float* y)
@@ -910,6 +963,8 @@ void gf_policy_defaults(gf_policy* pol)
     pol->solve.nu2 = 2;
     pol->solve.omega = 0.6;
     pol->solve.history = nullptr;
+    pol->solve.outer = 0;
+    pol->mlp = nullptr;
 }
 
 int gf_trigger_rule(double r50, double r100, const gf_policy* pol)

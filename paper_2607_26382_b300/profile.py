@@ -1,7 +1,7 @@
 """Run one operation of the library a few times on a synthetic state (a profiling target).
 
     python -m paper_2607_26382_b300.profile apply_k64 --grid 96 48 48 --levels 5 --reps 3
-    ops: apply_k64, apply_k32, vcycle_mixed, vcycle_fp64, solve_mixed, select_mixed
+    ops: apply_k64, apply_split, apply_k32, vcycle_mixed, vcycle_fp64, solve_mixed, select_mixed
 
 The state is the smoothed-Gaussian density (sigma 2, 40% at floor) at rho_min 1e-6,
 p = 3, with the cantilever tip load. Used as the command under ncu so that a
@@ -15,8 +15,8 @@ import sys
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("op", choices=["apply_k64", "apply_k32", "vcycle_mixed", "vcycle_fp64", "solve_mixed",
-                                   "select_mixed"])
+    ap.add_argument("op", choices=["apply_k64", "apply_split", "apply_k32", "vcycle_mixed", "vcycle_fp64",
+                                   "solve_mixed", "select_mixed"])
     ap.add_argument("--grid", type=int, nargs=3, default=[96, 48, 48])
     ap.add_argument("--levels", type=int, default=5)
     ap.add_argument("--reps", type=int, default=3)
@@ -40,6 +40,8 @@ def main(argv=None):
     for _ in range(a.reps):
         if a.op == "apply_k64":
             g.apply_K(x, y)
+        elif a.op == "apply_split":
+            g.apply_K_split(x, y)
         elif a.op == "apply_k32":
             g.apply_K_f32(x.float(), y.float())
         elif a.op == "vcycle_mixed":

@@ -384,3 +384,44 @@ def test_graph_replay_bit_identical(gf, monkeypatch):
         res.append((out, u.clone(), g.stats()))
     assert res[0][0] == res[1][0] and torch.equal(res[0][1], res[1][1])
     assert res[0][2]["kernel_launches"] == res[1][2]["kernel_launches"]
+
+
+# ------------------------------------------------------------- split-integer K*u --
+@pytest.mark.parametrize("nx,ny,nz,L", GRIDS)
+def test_apply_K_split_parity(gf, nx, ny, nz, L):
+    g, m, rho = make(gf, nx, ny, nz, L, seed=nx + 1, rho_min=1e-6)
+    E = O.young_modulus(rho, 1e-6, 3.0)
+    K0 = O.element_stiffness()
+    for seed, wide in ((3, False), (4, True)):
+        u = synth.random_vector(m.n_dof, seed)
+        if wide:   # values spread over 16 orders of magnitude
+            u = u * 10.0 ** (16.0 * synth.random_vector(m.n_dof, seed + 10))
+        y = torch.full((g.n_dof,), np.nan, dtype=torch.float64, device="cuda")
+        g.apply_K_split(dev(u), y)
+        ref = O.apply_K(m, E, K0, u)
+        got = host(y)
+        absref = O.apply_K(m, E, np.abs(K0), np.abs(u))      # |K| |u|, the rounding scale
+        assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(absref)
+        if not wide:
+            assert relerr(got, ref) <= 1e-12
+        assert np.all(got[m.fixed] == 0.0)
+        y64 = torch.zeros_like(y)
+        g.apply_K(dev(u), y64)
+        assert np.linalg.norm(got - host(y64)) <= 1e-12 * np.linalg.norm(absref)
+
+
+def test_solve_with_split_outer_operator(gf):
+    nx, ny, nz, L = 16, 8, 8, 3
+    g, m, rho = make(gf, nx, ny, nz, L, seed=4, rho_min=1e-6, kind="uniform")
+    f = O.cantilever_load(m)
+    outs = []
+    for outer in (0, 1):
+        u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        out = g.solve(dev(f), u, prec=gf.GF_MIXED, outer=outer)
+        outs.append((out, host(u)))
+    (a, ua), (b, ub) = outs
+    assert abs(a["iters"] - b["iters"]) <= 1 and a["flag"] == b["flag"] == gf.GF_FLAG_CONVERGED
+    h = min(a["iters"], b["iters"])
+    assert np.allclose(a["history"][:h], b["history"][:h], rtol=1e-6)
+    E = O.young_modulus(rho, 1e-6, 3.0)
+    assert O.true_residual(m, E, O.element_stiffness(), f, ub) <= 1.5e-6
