@@ -182,10 +182,10 @@ int gf_apply_K(gf_grid* g, const double* u, double* y);
 /* The same FP64 operator evaluated without FP64 multiply-adds: K0 = s*M with an
  * integer matrix M (exists for nu = 0.3 and other Poisson ratios with a small
  * integer form; GF_ERR_ARG otherwise). Each node tile writes its u values on a
- * common exponent with 50 bits, cuts them into five 10-bit digits, forms M times
+ * common exponent with 48 bits, cuts them into four 12-bit digits, forms M times
  * each digit slice exactly in FP32, recombines the slices and applies s*E_e in
- * double-float arithmetic. Error ~2^-46 of the tile's largest |u| times |M| (near
- * FP64 rounding). u, y: n_dof doubles, distinct. */
+ * double-float arithmetic. Error ~2^-44 of the tile's largest |u| times |M| (a few
+ * bits above FP64 rounding). u, y: n_dof doubles, distinct. */
 int gf_apply_K_split(gf_grid* g, const double* u, double* y);
 
 /* Same operator in FP32 with the moduli computed from the BF16 density copy (the
@@ -340,6 +340,12 @@ int gf_select_features(const gf_grid* g, double r50, double r100, double* x);
 int gf_true_residual_noalloc(int nx, int ny, int nz, double h, double E0, double nu,
                              const double* rho_hat, double p, double rho_min, const double* f,
                              const double* u, double* eta, void* stream);
+
+/* Node-stencil launch choice: threads per block of the FP64 kernel (64/128/256) and
+ * of the FP32 kernel (64/128/256, or 0 for the shared-memory-tiled FP32 kernel).
+ * FP64 results do not depend on the choice; FP32 results depend on it only through
+ * the summation order of the tiled kernel. gf_batch_autotune picks these by timing. */
+int gf_set_stencil_blocks(gf_grid* g, int tpb64, int tpb32);
 
 /* ---- diagnostics -------------------------------------------------------------- */
 int gf_get_stats(const gf_grid* g, gf_stats* s);

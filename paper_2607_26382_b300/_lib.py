@@ -135,6 +135,7 @@ def lib():
         "gf_mlp_predict": [P, POINTER(c_double), c_int, POINTER(c_int)],
         "gf_select_features": [P, c_double, c_double, POINTER(c_double)],
         "gf_apply_K_split": [P, P, P],
+        "gf_set_stencil_blocks": [P, c_int, c_int],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -359,6 +360,9 @@ class Grid:
 
     def features(self, r50, r100):
         return select_features(self._h, r50, r100)
+
+    def set_stencil_blocks(self, tpb64, tpb32):
+        _check(lib().gf_set_stencil_blocks(self._h, int(tpb64), int(tpb32)))
 
     def stats(self):
         s = Stats()

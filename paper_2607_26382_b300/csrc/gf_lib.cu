@@ -144,7 +144,7 @@ struct gf_grid {
     int gkey_prec = -1, gkey_nu1 = -1, gkey_nu2 = -1;
     double gkey_omega = -1.0;
     bool use_graphs = true;
-    int tpb[2] = {256, 256};          // node-stencil block size: [0] FP64, [1] FP32 (autotuned)
+    int tpb[2] = {256, 256};          // node-stencil block size: [0] FP64, [1] FP32 (0 = smem-tiled kernel)
     bool skip_coarse_inverse = false; // batched set-up builds the coarsest inverse itself
     double dstat[3] = {0.0, 0.0, 0.0}; // fraction of rho_hat == 0, mean, std (at set_density)
     // split-integer operator: K0 = s_split * M with integer M (when it exists)
@@ -187,11 +187,33 @@ int set_device(const gf_grid* g)
 }
 
 // ------------------------------------------------------------------ stencils --
+// FP32 shared-memory-tiled stencil on level l; b may be FP64 (level 0) and the
+// output FP64 (the V-cycle's last sweep writes the FP64 result directly).
+template <int MODE, typename BT, typename OT>
+int tiled_f32(gf_grid* g, int l, const float* x, const BT* b, OT* out, const float* E, float omega, const int* halt)
+{
+    const Level& L = g->lv[l];
+    if (g->tpb[1] > 0) {   // linear node-per-thread kernel with the autotuned block size
+        const int tpb = g->tpb[1];
+        LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_kernel<float, float, MODE, BT, OT>), x, b, out, E,
+               L.dims(), g->K0f, omega, halt);
+        return GF_OK;
+    }
+    const dim3 grid((L.nx + 1 + gf::TSX - 1) / gf::TSX, (L.ny + 1 + gf::TSY - 1) / gf::TSY,
+                    (L.nz + 1 + gf::TSZ - 1) / gf::TSZ);
+    LAUNCH(g, grid, dim3(gf::TSX, gf::TSY, gf::TSZ), (gf::tiled_stencil_f32_kernel<MODE, BT, OT>), x, b, out, E,
+           L.dims(), g->K0f, omega, halt);
+    return GF_OK;
+}
+
 template <typename T, typename ET, int MODE>
 int stencil(gf_grid* g, int l, const T* x, const T* b, T* out, const ET* E, const gf::K0Param<T>& K0,
             T omega, const int* halt)
 {
     const Level& L = g->lv[l];
+    if constexpr (sizeof(T) == sizeof(float)) {
+        if (g->tpb[1] == 0) return tiled_f32<MODE, float, float>(g, l, x, b, out, E, omega, halt);
+    }
     const int tpb = g->tpb[sizeof(T) == sizeof(double) ? 0 : 1];
     LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_kernel<T, ET, MODE>), x, b, out, E, L.dims(), K0, omega,
            halt);
@@ -297,10 +319,75 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
     return GF_OK;
 }
 
+// The mixed V-cycle (FP32 stencils, linear or tiled per the grid's tuning): level 0 reads the FP64 input v
+// as its right-hand side and the last post-sweep writes the FP64 result z, so no
+// conversion passes are needed.
+int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2, float omega, const int* halt)
+{
+    const int L = g->L;
+    g->stats.vcycles++;
+    std::vector<float*> cur(L);
+    for (int l = 0; l < L - 1; ++l) {
+        Level& lev = g->lv[l];
+        float* x = lev.x32;
+        float* t = lev.t32;
+        if (l == 0) {
+            LAUNCH(g, nblk(lev.nodes), 256, (gf::first_sweep_kernel<float, float, double>), v, x,
+                   (const float*)lev.E32, lev.dims(), g->K0f, omega, halt);
+            for (int s = 1; s < nu1; ++s) {
+                RET((tiled_f32<gf::ST_SWEEP, double, float>(g, l, x, v, t, lev.E32, omega, halt)));
+                std::swap(x, t);
+            }
+            RET((tiled_f32<gf::ST_RESID, double, float>(g, l, x, v, lev.r32, lev.E32, omega, halt)));
+        } else {
+            LAUNCH(g, nblk(lev.nodes), 256, (gf::first_sweep_kernel<float, float, float>), (const float*)lev.b32, x,
+                   (const float*)lev.E32, lev.dims(), g->K0f, omega, halt);
+            for (int s = 1; s < nu1; ++s) {
+                RET((tiled_f32<gf::ST_SWEEP, float, float>(g, l, x, lev.b32, t, lev.E32, omega, halt)));
+                std::swap(x, t);
+            }
+            RET((tiled_f32<gf::ST_RESID, float, float>(g, l, x, lev.b32, lev.r32, lev.E32, omega, halt)));
+        }
+        cur[l] = x;
+        Level& c = g->lv[l + 1];
+        LAUNCH(g, nblk(c.nodes), 256, gf::restrict_kernel<float>, (const float*)lev.r32, c.b32, c.dims(), halt);
+    }
+    {
+        Level& c = g->lv[L - 1];
+        LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<float, float>), (const double*)g->Ainv,
+               (const float*)c.b32, c.x32, g->nc, halt);
+        cur[L - 1] = c.x32;
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        Level& lev = g->lv[l];
+        float* x = cur[l];
+        float* t = (x == lev.x32) ? lev.t32 : lev.x32;
+        LAUNCH(g, nblk(lev.nodes), 256, (gf::prolong_add_kernel<float, float>), x, (const float*)cur[l + 1],
+               lev.dims(), halt);
+        for (int s = 0; s < nu2; ++s) {
+            const bool last = (s == nu2 - 1);
+            if (l == 0 && last) {
+                RET((tiled_f32<gf::ST_SWEEP, double, double>(g, 0, x, v, z, lev.E32, omega, halt)));
+            } else if (l == 0) {
+                RET((tiled_f32<gf::ST_SWEEP, double, float>(g, 0, x, v, t, lev.E32, omega, halt)));
+                std::swap(x, t);
+            } else {
+                RET((tiled_f32<gf::ST_SWEEP, float, float>(g, l, x, lev.b32, t, lev.E32, omega, halt)));
+                std::swap(x, t);
+            }
+        }
+        cur[l] = x;
+    }
+    return GF_OK;
+}
+
 int vcycle_dispatch(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2, double omega,
                     const int* halt)
 {
-    if (prec == GF_MIXED) return vcycle_impl<float>(g, v, z, nu1, nu2, (float)omega, halt);
+    if (prec == GF_MIXED) {
+        if (g->L > 1) return vcycle_mixed_tiled(g, v, z, nu1, nu2, (float)omega, halt);
+        return vcycle_impl<float>(g, v, z, nu1, nu2, (float)omega, halt);
+    }
     return vcycle_impl<double>(g, v, z, nu1, nu2, omega, halt);
 }
 
@@ -1204,6 +1291,17 @@ int gf_select_features(const gf_grid* g, double r50, double r100, double* x)
     return GF_OK;
 }
 
+int gf_set_stencil_blocks(gf_grid* g, int tpb64, int tpb32)
+{
+    RET(check_grid(g));
+    const auto ok = [](int t, bool allow0) { return t == 64 || t == 128 || t == 256 || (allow0 && t == 0); };
+    if (!ok(tpb64, false) || !ok(tpb32, true)) return set_err(GF_ERR_ARG, "block sizes: 64/128/256 (FP32 also 0)");
+    g->tpb[0] = tpb64;
+    g->tpb[1] = tpb32;
+    drop_graphs(g);
+    return GF_OK;
+}
+
 int gf_get_stats(const gf_grid* g, gf_stats* s)
 {
     RET(check_grid(g));
@@ -1304,8 +1402,8 @@ extern "C" int gf_true_residual_noalloc(int nx, int ny, int nz, double h, double
     // every word read below is written first in this call, so nothing is cleared
     gf::modulus_fp64_kernel<<<nblk(nel), 256, 0, s>>>(rho_hat, E, nel, rho_min, p, p_int, h);
     CK(cudaGetLastError());
-    gf::node_stencil_kernel<double, double, gf::ST_APPLY><<<nblk(nodes), 256, 0, s>>>(
-        u, nullptr, Ku, E, d, K0, 0.0, nullptr);
+    gf::node_stencil_kernel<double, double, gf::ST_APPLY, double, double><<<nblk(nodes), 256, 0, s>>>(
+        u, (const double*)nullptr, Ku, E, d, K0, 0.0, (const int*)nullptr);
     CK(cudaGetLastError());
     gf::residual_norms_kernel<<<nb, gf::RED_THREADS, 0, s>>>(f, Ku, nullptr, ndof, nx + 1, partial, 0, nullptr);
     CK(cudaGetLastError());

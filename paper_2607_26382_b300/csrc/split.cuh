@@ -5,11 +5,11 @@
 // matrix (|M| <= 88 for nu = 0.3), so the product can be formed exactly in FP32:
 //
 //  1. per node tile, every u value of the tile and its halo is written as
-//     u = sign * U * 2^(xmax - 1022 - P), U < 2^P (P = 50 bits kept below the tile's
-//     largest exponent xmax), and U is cut into 5 signed digits of 10 bits;
+//     u = sign * U * 2^(xmax - 1022 - P), U < 2^P (P = 48 bits kept below the tile's
+//     largest exponent xmax), and U is cut into 4 signed digits of 12 bits;
 //  2. per digit slice, t = sum_j M_ij d_j over an element's 24 DOFs is an integer of
-//     at most 24 * 88 * 1023 < 2^22, so FP32 FMAs compute it exactly;
-//  3. the slices are recombined, T = sum_k t_k 2^(10(4-k)), in double-float
+//     at most 24 * 88 * 4095 < 2^24, so FP32 FMAs compute it exactly;
+//  3. the slices are recombined, T = sum_k t_k 2^(12(3-k)), in double-float
 //     arithmetic (about 48 bits of the exact integer);
 //  4. T is weighted by s*E_e (held as a float pair) and summed over the node's 8
 //     elements in double-float arithmetic, then scaled by the tile's power of two
@@ -17,8 +17,8 @@
 // No step uses an FP64 multiply-add or an integer/float conversion instruction in
 // the inner loops: on B300 both run on the slow FP64 pipe.
 //
-// The error is ~2^-46 of the tile's largest |u| times |M|, close to FP64
-// element-by-element rounding. The acceptance guard keeps the native FP64 kernel.
+// The error is ~2^-44 of the tile's largest |u| times |M|, within a few bits of
+// FP64 element-by-element rounding. The acceptance guard keeps the native FP64 kernel.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -27,7 +27,7 @@ namespace gf {
 constexpr int SPX = 16, SPY = 4, SPZ = 2;                  // nodes per tile (128 threads)
 constexpr int SPHX = SPX + 2, SPHY = SPY + 2, SPHZ = SPZ + 2;
 constexpr int SPHN = SPHX * SPHY * SPHZ;                   // halo nodes (432)
-constexpr int SPLIT_P = 50, SPLIT_B = 10, SPLIT_K = 5;
+constexpr int SPLIT_P = 48, SPLIT_B = 12, SPLIT_K = 4;
 constexpr int SPLIT_VALS = (SPHN * 3 + 127) / 128;         // halo values held per thread
 
 struct MParam {
@@ -87,7 +87,7 @@ apply_split_kernel(const double* __restrict__ u, double* __restrict__ y, const f
     __syncthreads();
     const int xmax = max(max(wmax[0], wmax[1]), max(wmax[2], wmax[3]));
 
-    // pass 2: signed 10-bit digits on the common exponent
+    // pass 2: signed 12-bit digits on the common exponent
 #pragma unroll
     for (int r = 0; r < SPLIT_VALS; ++r) {
         const int q = tid + 128 * r;
@@ -98,7 +98,7 @@ apply_split_kernel(const double* __restrict__ u, double* __restrict__ y, const f
             const int shift = xmax - (e ? e : 1) + 53 - SPLIT_P;
             const long long U = (shift >= 63) ? 0LL : (mant >> shift);
             const float sg = (b < 0) ? -1.f : 1.f;
-            // 0 <= digit < 2^10: (2^23 | digit) as a float is 2^23 + digit exactly, so the
+            // 0 <= digit < 2^12: (2^23 | digit) as a float is 2^23 + digit exactly, so the
             // digit becomes a float without an integer-to-float conversion instruction
 #pragma unroll
             for (int k = 0; k < SPLIT_K; ++k) {
@@ -123,7 +123,7 @@ apply_split_kernel(const double* __restrict__ u, double* __restrict__ y, const f
     // pass 3: exact integer element products, slice by slice. Each digit of the 27
     // neighbouring nodes feeds every (element, row) accumulator that uses it, so the
     // 24 accumulators form independent FMA chains.
-    // T = sum_k t_k 2^(10 (4-k)) kept as a float pair (Horner: T <- 1024 T + t_k, the
+    // T = sum_k t_k 2^(12 (3-k)) kept as a float pair (Horner: T <- 4096 T + t_k, the
     // scaling exact and the addition by TwoSum), ~48 bits of the exact integer
     float Th[8][3], Tl[8][3];
 #pragma unroll
@@ -168,7 +168,7 @@ apply_split_kernel(const double* __restrict__ u, double* __restrict__ y, const f
         for (int e = 0; e < 8; ++e)
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                const float a = Th[e][r] * 1024.0f, b = Tl[e][r] * 1024.0f, tv = t[e][r];
+                const float a = Th[e][r] * 4096.0f, b = Tl[e][r] * 4096.0f, tv = t[e][r];
                 const float s = a + tv;
                 const float bb = s - a;
                 Th[e][r] = s;

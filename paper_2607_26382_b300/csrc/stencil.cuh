@@ -45,9 +45,9 @@ __device__ __forceinline__ void node_coords(long long n, int NX, int NY, int& i,
 // MODE == ST_SWEEP: out = x + omega * D_n^{-1} (b - K x)     (D_n: 3x3 node block)
 // Fixed nodes (i == 0) read as 0 and are written as 0. Element moduli E are
 // already multiplied by the element edge h (K_e(h) = h K_e(1) in 3D).
-template <typename T, typename ET, int MODE>
+template <typename T, typename ET, int MODE, typename BT = T, typename OT = T>
 __global__ void __launch_bounds__(256)
-node_stencil_kernel(const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ out,
+node_stencil_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __restrict__ out,
                     const ET* __restrict__ E, GridDims d, const __grid_constant__ K0Param<T> K0,
                     T omega, const int* __restrict__ halt)
 {
@@ -59,9 +59,9 @@ node_stencil_kernel(const T* __restrict__ x, const T* __restrict__ b, T* __restr
     int i, j, k;
     node_coords(n, NX, NY, i, j, k);
     if (i == 0) {
-        out[3 * n + 0] = T(0);
-        out[3 * n + 1] = T(0);
-        out[3 * n + 2] = T(0);
+        out[3 * n + 0] = OT(0);
+        out[3 * n + 1] = OT(0);
+        out[3 * n + 2] = OT(0);
         return;
     }
     T a0 = 0, a1 = 0, a2 = 0;
@@ -116,18 +116,18 @@ node_stencil_kernel(const T* __restrict__ x, const T* __restrict__ b, T* __restr
         }
     }
     if (MODE == ST_APPLY) {
-        out[3 * n + 0] = a0;
-        out[3 * n + 1] = a1;
-        out[3 * n + 2] = a2;
+        out[3 * n + 0] = OT(a0);
+        out[3 * n + 1] = OT(a1);
+        out[3 * n + 2] = OT(a2);
         return;
     }
-    const T r0 = b[3 * n + 0] - a0;
-    const T r1 = b[3 * n + 1] - a1;
-    const T r2 = b[3 * n + 2] - a2;
+    const T r0 = T(b[3 * n + 0]) - a0;
+    const T r1 = T(b[3 * n + 1]) - a1;
+    const T r2 = T(b[3 * n + 2]) - a2;
     if (MODE == ST_RESID) {
-        out[3 * n + 0] = r0;
-        out[3 * n + 1] = r1;
-        out[3 * n + 2] = r2;
+        out[3 * n + 0] = OT(r0);
+        out[3 * n + 1] = OT(r1);
+        out[3 * n + 2] = OT(r2);
         return;
     }
     // node-block solve by the adjugate
@@ -139,9 +139,9 @@ node_stencil_kernel(const T* __restrict__ x, const T* __restrict__ b, T* __restr
     const T c22 = d00 * d11 - d01 * d01;
     const T det = d00 * c00 + d01 * c01 + d02 * c02;
     const T s = omega / det;
-    out[3 * n + 0] = x[3 * n + 0] + s * (c00 * r0 + c01 * r1 + c02 * r2);
-    out[3 * n + 1] = x[3 * n + 1] + s * (c01 * r0 + c11 * r1 + c12 * r2);
-    out[3 * n + 2] = x[3 * n + 2] + s * (c02 * r0 + c12 * r1 + c22 * r2);
+    out[3 * n + 0] = OT(x[3 * n + 0] + s * (c00 * r0 + c01 * r1 + c02 * r2));
+    out[3 * n + 1] = OT(x[3 * n + 1] + s * (c01 * r0 + c11 * r1 + c12 * r2));
+    out[3 * n + 2] = OT(x[3 * n + 2] + s * (c02 * r0 + c12 * r1 + c22 * r2));
 }
 
 // First smoothing sweep from x = 0: out = omega * D_n^{-1} b. BT is b's type.
@@ -484,6 +484,143 @@ sensitivity_kernel(const double* __restrict__ u, const double* __restrict__ rho,
         rp = pow(r, pm1);
     }
     dc[e] = coef * rp * energy;
+}
+
+}  // namespace gf
+
+namespace gf {
+
+// FP32 node stencils on a shared-memory tile (the V-cycle's level operators).
+// A CTA stages the tile's nodes plus a one-node halo of x and the tile's elements
+// plus a one-element halo of E; each thread then reads its 27 neighbouring nodes
+// once and feeds every value to the (element, row) accumulators that use it, so
+// the inner loop is shared-memory loads and FMAs with K0 from the parameter bank.
+constexpr int TSX = 16, TSY = 4, TSZ = 2;                      // nodes per tile (128 threads)
+constexpr int THX = TSX + 2, THY = TSY + 2, THZ = TSZ + 2;      // node halo
+constexpr int TEX = TSX + 1, TEY = TSY + 1, TEZ = TSZ + 1;      // element halo
+
+template <int MODE, typename BT, typename OT>
+__global__ void __launch_bounds__(128)
+tiled_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, OT* __restrict__ out,
+                         const float* __restrict__ E, GridDims d, const __grid_constant__ K0Param<float> K0,
+                         float omega, const int* __restrict__ halt)
+{
+    if (halt != nullptr && *halt != 0) return;
+    __shared__ float sx[THX * THY * THZ * 3];
+    __shared__ float sE[TEX * TEY * TEZ];
+    const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
+    const int i0 = blockIdx.x * TSX, j0 = blockIdx.y * TSY, k0 = blockIdx.z * TSZ;
+    const int tid = threadIdx.x + TSX * (threadIdx.y + TSY * threadIdx.z);
+    for (int q = tid; q < THX * THY * THZ * 3; q += 128) {
+        const int c = q % 3, hn = q / 3;
+        const int hx = hn % THX, hy = (hn / THX) % THY, hz = hn / (THX * THY);
+        const int gi = i0 - 1 + hx, gj = j0 - 1 + hy, gk = k0 - 1 + hz;
+        float v = 0.f;
+        if (gi >= 1 && gi < NX && gj >= 0 && gj < NY && gk >= 0 && gk < NZ)
+            v = x[3 * ((long long)gi + (long long)NX * (gj + (long long)NY * gk)) + c];
+        sx[q] = v;
+    }
+    for (int q = tid; q < TEX * TEY * TEZ; q += 128) {
+        const int ex = q % TEX, ey = (q / TEX) % TEY, ez = q / (TEX * TEY);
+        const int ge = i0 - 1 + ex, gey = j0 - 1 + ey, gez = k0 - 1 + ez;
+        float v = 0.f;
+        if (ge >= 0 && ge < d.nx && gey >= 0 && gey < d.ny && gez >= 0 && gez < d.nz)
+            v = E[ge + (long long)d.nx * (gey + (long long)d.ny * gez)];
+        sE[q] = v;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+    const int gi = i0 + tx, gj = j0 + ty, gk = k0 + tz;
+    if (gi >= NX || gj >= NY || gk >= NZ) return;
+    const long long n = gi + (long long)NX * (gj + (long long)NY * gk);
+    if (gi == 0) {
+        out[3 * n + 0] = OT(0);
+        out[3 * n + 1] = OT(0);
+        out[3 * n + 2] = OT(0);
+        return;
+    }
+    float t[8][3];
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) t[e][r] = 0.f;
+#pragma unroll
+    for (int oz = 0; oz < 3; ++oz)
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox) {
+                const int hn = (tx + ox) + THX * ((ty + oy) + THY * (tz + oz));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float v = sx[3 * hn + c];
+#pragma unroll
+                    for (int ez = 0; ez < 2; ++ez)
+#pragma unroll
+                        for (int ey = 0; ey < 2; ++ey)
+#pragma unroll
+                            for (int ex = 0; ex < 2; ++ex) {
+                                const int bx = ox - ex, by = oy - ey, bz = oz - ez;
+                                if (bx < 0 || bx > 1 || by < 0 || by > 1 || bz < 0 || bz > 1) continue;
+                                const int e = ex + 2 * (ey + 2 * ez);
+                                const int a = local_index(1 - ex, 1 - ey, 1 - ez);
+                                const int bl = local_index(bx, by, bz);
+#pragma unroll
+                                for (int r = 0; r < 3; ++r)
+                                    t[e][r] = fmaf(K0.k[(3 * a + r) * 24 + 3 * bl + c], v, t[e][r]);
+                            }
+                }
+            }
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    float d00 = 0.f, d11 = 0.f, d22 = 0.f, d01 = 0.f, d02 = 0.f, d12 = 0.f;
+#pragma unroll
+    for (int ez = 0; ez < 2; ++ez)
+#pragma unroll
+        for (int ey = 0; ey < 2; ++ey)
+#pragma unroll
+            for (int ex = 0; ex < 2; ++ex) {
+                const int e = ex + 2 * (ey + 2 * ez);
+                const float Ee = sE[(tx + ex) + TEX * ((ty + ey) + TEY * (tz + ez))];
+                a0 = fmaf(Ee, t[e][0], a0);
+                a1 = fmaf(Ee, t[e][1], a1);
+                a2 = fmaf(Ee, t[e][2], a2);
+                if (MODE == ST_SWEEP) {
+                    const int a = local_index(1 - ex, 1 - ey, 1 - ez);
+                    d00 = fmaf(Ee, K0.k[(3 * a + 0) * 24 + 3 * a + 0], d00);
+                    d11 = fmaf(Ee, K0.k[(3 * a + 1) * 24 + 3 * a + 1], d11);
+                    d22 = fmaf(Ee, K0.k[(3 * a + 2) * 24 + 3 * a + 2], d22);
+                    d01 = fmaf(Ee, K0.k[(3 * a + 0) * 24 + 3 * a + 1], d01);
+                    d02 = fmaf(Ee, K0.k[(3 * a + 0) * 24 + 3 * a + 2], d02);
+                    d12 = fmaf(Ee, K0.k[(3 * a + 1) * 24 + 3 * a + 2], d12);
+                }
+            }
+    if (MODE == ST_APPLY) {
+        out[3 * n + 0] = OT(a0);
+        out[3 * n + 1] = OT(a1);
+        out[3 * n + 2] = OT(a2);
+        return;
+    }
+    const float r0 = (float)b[3 * n + 0] - a0;
+    const float r1 = (float)b[3 * n + 1] - a1;
+    const float r2 = (float)b[3 * n + 2] - a2;
+    if (MODE == ST_RESID) {
+        out[3 * n + 0] = OT(r0);
+        out[3 * n + 1] = OT(r1);
+        out[3 * n + 2] = OT(r2);
+        return;
+    }
+    const float c00 = d11 * d22 - d12 * d12;
+    const float c01 = d02 * d12 - d01 * d22;
+    const float c02 = d01 * d12 - d02 * d11;
+    const float c11 = d00 * d22 - d02 * d02;
+    const float c12 = d01 * d02 - d00 * d12;
+    const float c22 = d00 * d11 - d01 * d01;
+    const float det = d00 * c00 + d01 * c01 + d02 * c02;
+    const float s = omega / det;
+    const int hc = (tx + 1) + THX * ((ty + 1) + THY * (tz + 1));
+    out[3 * n + 0] = OT(sx[3 * hc + 0] + s * (c00 * r0 + c01 * r1 + c02 * r2));
+    out[3 * n + 1] = OT(sx[3 * hc + 1] + s * (c01 * r0 + c11 * r1 + c12 * r2));
+    out[3 * n + 2] = OT(sx[3 * hc + 2] + s * (c02 * r0 + c12 * r1 + c22 * r2));
 }
 
 }  // namespace gf
