@@ -342,9 +342,10 @@ int gf_true_residual_noalloc(int nx, int ny, int nz, double h, double E0, double
                              const double* u, double* eta, void* stream);
 
 /* Node-stencil launch choice: threads per block of the FP64 kernel (64/128/256) and
- * of the FP32 kernel (64/128/256, or 0 for the shared-memory-tiled FP32 kernel).
+ * of the FP32 kernel (64/128/256; 0 = the shared-memory-tiled FP32 kernel; -64/-128/
+ * -256 = the 27-neighbour register-gather FP32 kernel with that block size).
  * FP64 results do not depend on the choice; FP32 results depend on it only through
- * the summation order of the tiled kernel. gf_batch_autotune picks these by timing. */
+ * the summation order of the kernel variant. gf_batch_autotune picks these by timing. */
 int gf_set_stencil_blocks(gf_grid* g, int tpb64, int tpb32);
 
 /* ---- diagnostics -------------------------------------------------------------- */

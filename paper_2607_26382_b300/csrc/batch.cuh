@@ -389,12 +389,13 @@ int batch_set_floor(gf_batch* b, const std::vector<int>& active, const std::vect
     return GF_OK;
 }
 
-// Time the FP64 stencil at block sizes 64/128/256 and the FP32 one at 64/128/256
-// and as the shared-memory-tiled kernel (0), keeping the fastest of each.
+// Time the FP64 stencil at block sizes 64/128/256 and the FP32 one at 64/128/256,
+// as the shared-memory-tiled kernel (0) and as the 27-neighbour gather kernel
+// (-64/-128/-256), keeping the fastest of each.
 int autotune_grid(gf_grid* g)
 {
     if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor before autotuning");
-    const int cand[4] = {64, 128, 256, 0};
+    const int cand[7] = {64, 128, 256, 0, -64, -128, -256};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -403,7 +404,7 @@ int autotune_grid(gf_grid* g)
         float best = 1e30f;
         int pick = prec == 0 ? 256 : 0;
         for (int c : cand) {
-            if (prec == 0 && c == 0) continue;   // the tiled kernel is FP32 only
+            if (prec == 0 && c <= 0) continue;   // the tiled and 27-neighbour variants are FP32 only
             g->tpb[prec] = c;
             for (int rep = 0; rep < 4; ++rep) {
                 if (rep == 1) CK(cudaEventRecord(e0, g->stream));

@@ -199,6 +199,12 @@ int tiled_f32(gf_grid* g, int l, const float* x, const BT* b, OT* out, const flo
                L.dims(), g->K0f, omega, halt);
         return GF_OK;
     }
+    if (g->tpb[1] < 0) {   // 27-neighbour register-gather kernel
+        const int tpb = -g->tpb[1];
+        LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil27_kernel<float, MODE, BT, OT>), x, b, out, E,
+               L.dims(), g->K0f, omega, halt);
+        return GF_OK;
+    }
     const dim3 grid((L.nx + 1 + gf::TSX - 1) / gf::TSX, (L.ny + 1 + gf::TSY - 1) / gf::TSY,
                     (L.nz + 1 + gf::TSZ - 1) / gf::TSZ);
     LAUNCH(g, grid, dim3(gf::TSX, gf::TSY, gf::TSZ), (gf::tiled_stencil_f32_kernel<MODE, BT, OT>), x, b, out, E,
@@ -212,7 +218,7 @@ int stencil(gf_grid* g, int l, const T* x, const T* b, T* out, const ET* E, cons
 {
     const Level& L = g->lv[l];
     if constexpr (sizeof(T) == sizeof(float)) {
-        if (g->tpb[1] == 0) return tiled_f32<MODE, float, float>(g, l, x, b, out, E, omega, halt);
+        if (g->tpb[1] <= 0) return tiled_f32<MODE, float, float>(g, l, x, b, out, E, omega, halt);
     }
     const int tpb = g->tpb[sizeof(T) == sizeof(double) ? 0 : 1];
     LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_kernel<T, ET, MODE>), x, b, out, E, L.dims(), K0, omega,
@@ -1294,8 +1300,11 @@ int gf_select_features(const gf_grid* g, double r50, double r100, double* x)
 int gf_set_stencil_blocks(gf_grid* g, int tpb64, int tpb32)
 {
     RET(check_grid(g));
-    const auto ok = [](int t, bool allow0) { return t == 64 || t == 128 || t == 256 || (allow0 && t == 0); };
-    if (!ok(tpb64, false) || !ok(tpb32, true)) return set_err(GF_ERR_ARG, "block sizes: 64/128/256 (FP32 also 0)");
+    const auto ok = [](int t, bool f32) {
+        return t == 64 || t == 128 || t == 256 || (f32 && (t == 0 || t == -64 || t == -128 || t == -256));
+    };
+    if (!ok(tpb64, false) || !ok(tpb32, true))
+        return set_err(GF_ERR_ARG, "block sizes: 64/128/256 (FP32 also 0 = tiled, -64/-128/-256 = 27-neighbour)");
     g->tpb[0] = tpb64;
     g->tpb[1] = tpb32;
     drop_graphs(g);

@@ -624,3 +624,119 @@ tiled_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
 }
 
 }  // namespace gf
+
+namespace gf {
+
+// Node stencil that reads each of the 27 neighbouring nodes once (81 loads, 32-bit
+// offsets from the node's own address) and feeds every value to the (element, row)
+// accumulators that use it. Same modes and types as node_stencil_kernel.
+template <typename T, int MODE, typename BT, typename OT>
+__global__ void __launch_bounds__(256)
+node_stencil27_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __restrict__ out,
+                      const T* __restrict__ E, GridDims d, const __grid_constant__ K0Param<T> K0, T omega,
+                      const int* __restrict__ halt)
+{
+    if (halt != nullptr && *halt != 0) return;
+    const int NX = d.nx + 1, NY = d.ny + 1;
+    const int nn = NX * NY * (d.nz + 1);
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    const int i = n % NX, j = (n / NX) % NY, k = n / (NX * NY);
+    if (i == 0) {
+        out[3 * (long long)n + 0] = OT(0);
+        out[3 * (long long)n + 1] = OT(0);
+        out[3 * (long long)n + 2] = OT(0);
+        return;
+    }
+    const T* xn = x + 3 * (long long)n;
+    const int sy = 3 * NX, sz = 3 * NX * NY;
+    T t[8][3];
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) t[e][r] = T(0);
+#pragma unroll
+    for (int oz = 0; oz < 3; ++oz) {
+        const bool okz = (oz != 0 || k > 0) && (oz != 2 || k < d.nz);
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy) {
+            const bool oky = okz && (oy != 0 || j > 0) && (oy != 2 || j < d.ny);
+#pragma unroll
+            for (int ox = 0; ox < 3; ++ox) {
+                // the clamped face (i - 1 + ox == 0) reads as zero
+                const bool ok = oky && (ox != 0 || i > 1) && (ox != 2 || i < d.nx);
+                const T* p = xn + (ox - 1) * 3 + (oy - 1) * sy + (oz - 1) * sz;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const T v = ok ? p[c] : T(0);
+#pragma unroll
+                    for (int ez = 0; ez < 2; ++ez)
+#pragma unroll
+                        for (int ey = 0; ey < 2; ++ey)
+#pragma unroll
+                            for (int ex = 0; ex < 2; ++ex) {
+                                const int bx = ox - ex, by = oy - ey, bz = oz - ez;
+                                if (bx < 0 || bx > 1 || by < 0 || by > 1 || bz < 0 || bz > 1) continue;
+                                const int e = ex + 2 * (ey + 2 * ez);
+                                const int a = local_index(1 - ex, 1 - ey, 1 - ez);
+                                const int bl = local_index(bx, by, bz);
+#pragma unroll
+                                for (int r = 0; r < 3; ++r) t[e][r] = fma(K0.k[(3 * a + r) * 24 + 3 * bl + c], v, t[e][r]);
+                            }
+                }
+            }
+        }
+    }
+    T a0 = 0, a1 = 0, a2 = 0;
+    T d00 = 0, d11 = 0, d22 = 0, d01 = 0, d02 = 0, d12 = 0;
+#pragma unroll
+    for (int ez = 0; ez < 2; ++ez)
+#pragma unroll
+        for (int ey = 0; ey < 2; ++ey)
+#pragma unroll
+            for (int ex = 0; ex < 2; ++ex) {
+                const int cx = i - 1 + ex, cy = j - 1 + ey, cz = k - 1 + ez;
+                if (cx < 0 || cx >= d.nx || cy < 0 || cy >= d.ny || cz < 0 || cz >= d.nz) continue;
+                const int e = ex + 2 * (ey + 2 * ez);
+                const T Ee = E[cx + d.nx * (cy + d.ny * cz)];
+                a0 = fma(Ee, t[e][0], a0);
+                a1 = fma(Ee, t[e][1], a1);
+                a2 = fma(Ee, t[e][2], a2);
+                if (MODE == ST_SWEEP) {
+                    const int a = local_index(1 - ex, 1 - ey, 1 - ez);
+                    d00 = fma(Ee, K0.k[(3 * a + 0) * 24 + 3 * a + 0], d00);
+                    d11 = fma(Ee, K0.k[(3 * a + 1) * 24 + 3 * a + 1], d11);
+                    d22 = fma(Ee, K0.k[(3 * a + 2) * 24 + 3 * a + 2], d22);
+                    d01 = fma(Ee, K0.k[(3 * a + 0) * 24 + 3 * a + 1], d01);
+                    d02 = fma(Ee, K0.k[(3 * a + 0) * 24 + 3 * a + 2], d02);
+                    d12 = fma(Ee, K0.k[(3 * a + 1) * 24 + 3 * a + 2], d12);
+                }
+            }
+    const long long o = 3 * (long long)n;
+    if (MODE == ST_APPLY) {
+        out[o + 0] = OT(a0);
+        out[o + 1] = OT(a1);
+        out[o + 2] = OT(a2);
+        return;
+    }
+    const T r0 = T(b[o + 0]) - a0, r1 = T(b[o + 1]) - a1, r2 = T(b[o + 2]) - a2;
+    if (MODE == ST_RESID) {
+        out[o + 0] = OT(r0);
+        out[o + 1] = OT(r1);
+        out[o + 2] = OT(r2);
+        return;
+    }
+    const T c00 = d11 * d22 - d12 * d12;
+    const T c01 = d02 * d12 - d01 * d22;
+    const T c02 = d01 * d12 - d02 * d11;
+    const T c11 = d00 * d22 - d02 * d02;
+    const T c12 = d01 * d02 - d00 * d12;
+    const T c22 = d00 * d11 - d01 * d01;
+    const T det = d00 * c00 + d01 * c01 + d02 * c02;
+    const T s = omega / det;
+    out[o + 0] = OT(xn[0] + s * (c00 * r0 + c01 * r1 + c02 * r2));
+    out[o + 1] = OT(xn[1] + s * (c01 * r0 + c11 * r1 + c12 * r2));
+    out[o + 2] = OT(xn[2] + s * (c02 * r0 + c12 * r1 + c22 * r2));
+}
+
+}  // namespace gf

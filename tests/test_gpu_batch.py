@@ -41,7 +41,7 @@ def test_batch_matches_single_state(gf, selector, prec):
     pol = gf.policy_defaults(rho0=1e-8, ladder=[1e-5, 1e-4, 1e-3], kmax=120, selector=sel, solve_prec=prec)
     batch = gf.Batch([s[0] for s in STATES], levels=L)
     tuned = batch.autotune()
-    assert all(t[0] in (64, 128, 256) and t[1] in (0, 64, 128, 256) for t in tuned)
+    assert all(t[0] in (64, 128, 256) and t[1] in (0, 64, 128, 256, -64, -128, -256) for t in tuned)
     rhos, fs = [], []
     for i, (dims, kind, seed, q) in enumerate(STATES):
         rho = dev(_rho(dims, kind, seed, q))

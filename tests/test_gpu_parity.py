@@ -92,9 +92,11 @@ def test_apply_K_fp64_parity(gf, nx, ny, nz, L, p):
     assert np.all(got[m.fixed] == 0.0)
 
 
-@pytest.mark.parametrize("nx,ny,nz,L", GRIDS[:3])
-def test_apply_K_f32_parity(gf, nx, ny, nz, L):
+@pytest.mark.parametrize("nx,ny,nz,L", GRIDS[:3] + GRIDS[4:5])
+@pytest.mark.parametrize("variant", [256, 0, -128])
+def test_apply_K_f32_parity(gf, nx, ny, nz, L, variant):
     g, m, rho = make(gf, nx, ny, nz, L, seed=3)
+    g.set_stencil_blocks(256, variant)        # linear / shared-memory tiled / 27-neighbour gather
     u = synth.random_vector(m.n_dof, 5).astype(np.float32)
     y = torch.zeros(g.n_dof, dtype=torch.float32, device="cuda")
     g.apply_K_f32(dev(u, torch.float32), y)
