@@ -110,6 +110,11 @@ typedef struct {
                                           0: run the probe and the rho0 solve separately */
     gf_solve_opts solve;               /* restart, prec, smoother (kmax/tol/history ignored) */
     gf_mlp* mlp;                       /* GF_SEL_MLP: trained selector (else ignored) */
+    double mlp_confidence;             /* GF_SEL_MLP: 0 = start at the most probable floor; c in
+                                          (0,1] = start at the highest floor k with
+                                          P(first admissible floor >= k) >= c (k = 0 always
+                                          qualifies), so the selector skips a floor only
+                                          when confident that it fails */
 } gf_policy;
 
 typedef struct {
@@ -312,6 +317,8 @@ int gf_mlp_train(gf_mlp* M, const float* X, const int* y, int n, const int* perm
                  float lr, float* final_loss);
 /* Class (argmax logit) for host feature rows (n x 6 doubles), n <= 4096, into cls (host). */
 int gf_mlp_predict(gf_mlp* M, const double* feat, int n, int* cls);
+/* Softmax probabilities (host, n x 4) for host feature rows, n <= 4096. */
+int gf_mlp_probs(gf_mlp* M, const double* feat, int n, double* probs);
 /* The selector's 6 inputs for grid g: [log10 r50, log10 r100, r100/r50, fraction of
  * voxels with rho_hat == 0, mean rho_hat, std rho_hat] (x: host, 6 doubles). */
 int gf_select_features(const gf_grid* g, double r50, double r100, double* x);

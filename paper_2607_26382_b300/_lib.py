@@ -60,7 +60,8 @@ class Policy(ctypes.Structure):
                 ("tau", c_double), ("kmax", c_int), ("probe_iters", c_int),
                 ("r50_escalate", c_double), ("r100_stall", c_double), ("plateau_ratio", c_double),
                 ("checkpoint_a", c_int), ("checkpoint_b", c_int), ("selector", c_int),
-                ("first_index", c_int), ("fuse_probe", c_int), ("solve", SolveOpts), ("mlp", c_void_p)]
+                ("first_index", c_int), ("fuse_probe", c_int), ("solve", SolveOpts), ("mlp", c_void_p),
+                ("mlp_confidence", c_double)]
 
 
 class Attempt(ctypes.Structure):
@@ -136,6 +137,7 @@ def lib():
         "gf_select_features": [P, c_double, c_double, POINTER(c_double)],
         "gf_apply_K_split": [P, P, P],
         "gf_set_stencil_blocks": [P, c_int, c_int],
+        "gf_mlp_probs": [P, POINTER(c_double), c_int, POINTER(c_double)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -541,6 +543,18 @@ class MLP:
         _check(lib().gf_mlp_predict(self._h, f.ctypes.data_as(POINTER(c_double)), int(f.shape[0]),
                                     cls.ctypes.data_as(POINTER(c_int))))
         return cls
+
+
+def _mlp_probs(self, feats):
+    import numpy as np
+    f = np.ascontiguousarray(feats, dtype=np.float64).reshape(-1, 6)
+    p = np.zeros((f.shape[0], 4), dtype=np.float64)
+    _check(lib().gf_mlp_probs(self._h, f.ctypes.data_as(POINTER(c_double)), int(f.shape[0]),
+                              p.ctypes.data_as(POINTER(c_double))))
+    return p
+
+
+MLP.probs = _mlp_probs
 
 
 def select_features(grid_handle, r50, r100):

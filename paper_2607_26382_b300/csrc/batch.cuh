@@ -254,9 +254,9 @@ int batch_decide(gf_batch* b, const gf_policy* pol, const std::vector<int>& rows
         std::vector<int> cls(rows.size());
         for (size_t r0 = 0; r0 < rows.size(); r0 += 4096) {
             const int n = (int)std::min<size_t>(4096, rows.size() - r0);
-            RET(mlp_predict_host(pol->mlp, &feat[6 * r0], n, &cls[r0]));
+            RET(mlp_first_floors(pol->mlp, &feat[6 * r0], n, pol->mlp_confidence, nf, &cls[r0]));
         }
-        for (size_t r = 0; r < rows.size(); ++r) out[rows[r]].first = std::min(std::max(cls[r], 0), nf - 1);
+        for (size_t r = 0; r < rows.size(); ++r) out[rows[r]].first = cls[r];
     } else {
         for (int i : rows) out[i].first = gf_trigger_rule(out[i].r50, out[i].r100, pol) ? 1 : 0;
     }

@@ -104,6 +104,7 @@ void build_k0(double E0, double nu, double* K)
 
 namespace {
 int mlp_predict_host(gf_mlp* M, const double* feat, int n, int* cls);
+int mlp_first_floors(gf_mlp* M, const double* feat, int n, double c, int nf, int* first);
 }
 
 struct gf_grid {
@@ -1058,6 +1059,7 @@ void gf_policy_defaults(gf_policy* pol)
     pol->solve.history = nullptr;
     pol->solve.outer = 0;
     pol->mlp = nullptr;
+    pol->mlp_confidence = 0.0;
 }
 
 int gf_trigger_rule(double r50, double r100, const gf_policy* pol)
@@ -1101,9 +1103,7 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
         if (pol->selector == GF_SEL_MLP) {
             double x[6];
             RET(gf_select_features(g, r50, r100, x));
-            int c = 0;
-            RET(mlp_predict_host(pol->mlp, x, 1, &c));
-            *first = std::min(std::max(c, 0), nf - 1);
+            RET(mlp_first_floors(pol->mlp, x, 1, pol->mlp_confidence, nf, first));
         } else {
             *first = gf_trigger_rule(r50, r100, pol) ? 1 : 0;
         }

@@ -168,6 +168,7 @@ struct gf_mlp {
     int idx_cap = 0;
     float* feat = nullptr;    // inference scratch (up to 4096 rows)
     int* cls = nullptr;
+    float* logits = nullptr;
     long long t = 0;
     gf::MLPNorm norm{};
 };
@@ -201,9 +202,63 @@ int mlp_predict_host(gf_mlp* M, const double* feat, int n, int* cls)
     return GF_OK;
 }
 
+// Softmax probabilities for host feature rows (n <= 4096).
+int mlp_probs_host(gf_mlp* M, const double* feat, int n, double* probs)
+{
+    if (n > 4096) return set_err(GF_ERR_ARG, "at most 4096 rows per prediction");
+    std::vector<float> f((size_t)n * gf::MLP_IN), lg((size_t)n * gf::MLP_OUT);
+    for (size_t i = 0; i < f.size(); ++i) f[i] = (float)feat[i];
+    CK(cudaMemcpyAsync(M->feat, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice, M->stream));
+    gf::mlp_forward_kernel<<<(n + 127) / 128, 128, 0, M->stream>>>(M->theta, M->feat, n, M->norm, M->logits,
+                                                                   nullptr);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(lg.data(), M->logits, sizeof(float) * lg.size(), cudaMemcpyDeviceToHost, M->stream));
+    CK(cudaStreamSynchronize(M->stream));
+    for (int r = 0; r < n; ++r) {
+        double mx = lg[r * gf::MLP_OUT];
+        for (int o = 1; o < gf::MLP_OUT; ++o) mx = std::max(mx, (double)lg[r * gf::MLP_OUT + o]);
+        double den = 0.0;
+        for (int o = 0; o < gf::MLP_OUT; ++o) den += std::exp((double)lg[r * gf::MLP_OUT + o] - mx);
+        for (int o = 0; o < gf::MLP_OUT; ++o) probs[r * gf::MLP_OUT + o] = std::exp((double)lg[r * gf::MLP_OUT + o] - mx) / den;
+    }
+    return GF_OK;
+}
+
+// First floor from the selector: argmax (c == 0) or the highest k with
+// P(first admissible floor >= k) >= c.
+int mlp_first_floors(gf_mlp* M, const double* feat, int n, double c, int nf, int* first)
+{
+    if (c <= 0.0) {
+        RET(mlp_predict_host(M, feat, n, first));
+    } else {
+        std::vector<double> p((size_t)n * gf::MLP_OUT);
+        RET(mlp_probs_host(M, feat, n, p.data()));
+        for (int r = 0; r < n; ++r) {
+            int k = 0;
+            double tail = 0.0;
+            for (int q = gf::MLP_OUT - 1; q >= 1; --q) {
+                tail += p[r * gf::MLP_OUT + q];
+                if (tail >= c) {
+                    k = q;
+                    break;
+                }
+            }
+            first[r] = k;
+        }
+    }
+    for (int r = 0; r < n; ++r) first[r] = std::min(std::max(first[r], 0), nf - 1);
+    return GF_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int gf_mlp_probs(gf_mlp* M, const double* feat, int n, double* probs)
+{
+    if (!M || !feat || !probs || n < 1) return set_err(GF_ERR_ARG, "bad argument");
+    return mlp_probs_host(M, feat, n, probs);
+}
 
 int gf_mlp_create(const float* theta0, void* stream, gf_mlp** out)
 {
@@ -217,7 +272,8 @@ int gf_mlp_create(const float* theta0, void* stream, gf_mlp** out)
         cudaMalloc(&M->v, P) != cudaSuccess || cudaMalloc(&M->grad, P) != cudaSuccess ||
         cudaMalloc(&M->loss, sizeof(float)) != cudaSuccess ||
         cudaMalloc(&M->feat, sizeof(float) * 4096 * gf::MLP_IN) != cudaSuccess ||
-        cudaMalloc(&M->cls, sizeof(int) * 4096) != cudaSuccess)
+        cudaMalloc(&M->cls, sizeof(int) * 4096) != cudaSuccess ||
+        cudaMalloc(&M->logits, sizeof(float) * 4096 * gf::MLP_OUT) != cudaSuccess)
         return fail(set_err(GF_ERR_OOM, "mlp buffers"));
     if (cudaMemcpy(M->theta, theta0, P, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(M->m, 0, P) != cudaSuccess || cudaMemset(M->v, 0, P) != cudaSuccess)
@@ -235,6 +291,7 @@ int gf_mlp_destroy(gf_mlp* M)
     if (!M) return GF_OK;
     cudaFree(M->theta); cudaFree(M->m); cudaFree(M->v); cudaFree(M->grad); cudaFree(M->loss);
     cudaFree(M->gps); cudaFree(M->lps); cudaFree(M->idx); cudaFree(M->feat); cudaFree(M->cls);
+    cudaFree(M->logits);
     delete M;
     return GF_OK;
 }

@@ -1,0 +1,184 @@
+"""Workload drivers for the batched and learned forms (every solve runs in libgf_b300.so).
+
+    python -m paper_2607_26382_b300.experiments batch102 [--train 2000]
+    python -m paper_2607_26382_b300.experiments oc_loop [--iters 40]
+
+batch102: 102 frozen states of uneven size (nx in {32,48,64,80}, ny = nz = nx/2,
+  round-robin; 71 smoothed-Gaussian states with 40% of voxels at floor, 31
+  optimised-like states with 30% forced to floor), probe at rho0 = 1e-6, ladder
+  {1e-5, 1e-4, 1e-3}, tau = 1e-6, kmax = 200, 4-level GMG. Three forms, all with the
+  FP64 recomputed-residual guard as the only acceptance test:
+    plain   - FP64 V-cycle and Krylov, one state at a time, full ladder from rho0;
+    batched - mixed V-cycle, split-integer Krylov operator, all states in one batch,
+              Eq. (trigger) picks the first floor;
+    learned - as batched, with an MLP (trained on full-ladder outcomes of 48x24x24
+              states) picking the first floor: its most probable floor, and (c0.9)
+              the highest floor it is 90% sure the search must reach.
+oc_loop: a guarded SIMP-OC loop (vol 0.3, filter radius 1.5, p = 3, move 0.2) on the
+  96x48x48 cantilever, Algorithm 1 at every iteration, compared across selectors.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+import time
+
+import numpy as np
+
+from . import _lib as L
+from . import selector as S
+
+LADDER = [1e-5, 1e-4, 1e-3]
+
+
+def _policy(**kw):
+    base = dict(rho0=1e-6, ladder=LADDER, tau=1e-6, kmax=200, probe_iters=100)
+    base.update(kw)
+    return L.policy_defaults(**base)
+
+
+def batch_states(n=102, seed0=100):
+    import synth
+    dims = synth.batch_grid_sizes(n)
+    rhos, kinds = [], []
+    for i, (nx, ny, nz) in enumerate(dims):
+        if i % 10 < 7:   # 70% severe random, 30% optimised-like
+            rhos.append(synth.smoothed_gaussian_density(nx, ny, nz, seed0 + i, 2.0, 0.4))
+            kinds.append("random")
+        else:
+            rhos.append(synth.optimised_like_density(nx, ny, nz, seed0 + 100 + i, 0.3, 0.3))
+            kinds.append("optimised")
+    return dims, rhos, kinds
+
+
+def _summary(recs, seconds):
+    acc = sum(r["status"] == L.GF_ACCEPTED for r in recs)
+    return {"states": len(recs), "accepted": acc, "seconds": seconds, "guarded_solves_per_s": acc / seconds,
+            "arnoldi_steps": int(sum(S.work_of(r) for r in recs)),
+            "floors": [r["floor_index"] for r in recs]}
+
+
+def run_plain(dims, rhos):
+    import torch
+    pol = _policy(selector=L.GF_SEL_FULL, solve_prec=L.GF_FP64, solve_outer=0)
+    recs = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for d, rho in zip(dims, rhos):
+        g = L.create_grid(*d, levels=4)
+        f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        g.cantilever_load(f)
+        g.set_density(torch.as_tensor(rho, device="cuda"), 3.0)
+        u = torch.zeros_like(f)
+        recs.append(g.select_floor(f, u, pol))
+        g.close()
+    torch.cuda.synchronize()
+    return recs, time.perf_counter() - t0
+
+
+def run_batched(dims, rhos, pol, reps=1):
+    import torch
+    b = S._batch_for(dims, 4, rhos)
+    b.autotune()
+    b.select_floor(pol)                      # warm-up: graphs captured, buffers sized
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        recs = b.select_floor(pol)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    launches = b.kernel_launches()
+    b.close()
+    return recs, dt, launches
+
+
+def train_mlp(n_train, seed=7):
+    import synth
+    dims = (48, 24, 24)
+    rh = synth.selector_training_states(n_train, dims, seed)
+    pol = _policy(solve_prec=L.GF_MIXED, solve_outer=1)
+    t0 = time.perf_counter()
+    X, y, _ = S.ladder_dataset(dims, rh, 4, pol, chunk=100)
+    t_data = time.perf_counter() - t0
+    ntr = int(0.8 * len(y))
+    perm = synth.epoch_permutations(ntr, 200, seed + 1)
+    net, loss = S.train_selector(X[:ntr], y[:ntr], synth.mlp_init(seed + 2), perm, 200, 128, 3e-3)
+    acc = float((net.predict(X[ntr:]) == y[ntr:]).mean())
+    return net, {"train_states": ntr, "held_out": len(y) - ntr, "label_counts": np.bincount(y, minlength=4).tolist(),
+                 "held_out_accuracy": acc, "final_loss": loss, "data_seconds": t_data}
+
+
+def batch102(args):
+    dims, rhos, kinds = batch_states()
+    out = {"workload": "batch102", "n_dof_total": int(sum(3 * (a + 1) * (b + 1) * (c + 1) for a, b, c in dims))}
+    recs, dt = run_plain(dims, rhos)
+    out["plain_fp64_single_state_full_ladder"] = _summary(recs, dt)
+    recs, dt, launches = run_batched(dims, rhos, _policy(solve_prec=L.GF_MIXED, solve_outer=1))
+    out["batched_mixed_rule"] = _summary(recs, dt)
+    out["batched_mixed_rule"]["kernel_launches_total"] = launches
+    net, info = train_mlp(args.train)
+    out["selector_training"] = info
+    for name, conf in (("batched_mixed_learned", 0.0), ("batched_mixed_learned_c0.9", 0.9)):
+        pol = _policy(solve_prec=L.GF_MIXED, solve_outer=1, selector=L.GF_SEL_MLP, mlp_confidence=conf)
+        pol.mlp = net.handle
+        recs, dt, _ = run_batched(dims, rhos, pol)
+        out[name] = _summary(recs, dt)
+    full = out["plain_fp64_single_state_full_ladder"]["floors"]
+    for k in ("batched_mixed_rule", "batched_mixed_learned", "batched_mixed_learned_c0.9"):
+        fl = out[k]["floors"]
+        out[k]["floors_higher_than_full_ladder"] = int(sum(a > b >= 0 for a, b in zip(fl, full)))
+    out["speedup_learned_vs_plain"] = (out["batched_mixed_learned"]["guarded_solves_per_s"] /
+                                       out["plain_fp64_single_state_full_ladder"]["guarded_solves_per_s"])
+    return out
+
+
+def oc_loop(args):
+    import torch
+    nx, ny, nz = 96, 48, 48
+    out = {"workload": f"guarded SIMP-OC {nx}x{ny}x{nz}, {args.iters} iterations, vol 0.3, r_min 1.5, p 3"}
+    modes = [("plain_fp64_full", _policy(selector=L.GF_SEL_FULL, solve_prec=L.GF_FP64, solve_outer=0)),
+             ("mixed_rule", _policy(solve_prec=L.GF_MIXED, solve_outer=1))]
+    net = None
+    if args.train > 0:
+        net, info = train_mlp(args.train)
+        out["selector_training"] = info
+        pol = _policy(solve_prec=L.GF_MIXED, solve_outer=1, selector=L.GF_SEL_MLP)
+        pol.mlp = net.handle
+        modes.append(("mixed_learned", pol))
+    for name, pol in modes:
+        g = L.create_grid(nx, ny, nz, levels=5)
+        f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        g.cantilever_load(f)
+        x = torch.full((g.n_elem,), 0.3, dtype=torch.float64, device="cuda")
+        u = torch.zeros_like(f)
+        hist = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for it in range(args.iters):
+            r = g.oc_iteration(x, f, u, pol, p=3.0, volfrac=0.3, r_min=1.5, move=0.2)
+            hist.append(r)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        acc = sum(r["status"] == L.GF_ACCEPTED for r in hist)
+        out[name] = {"seconds": dt, "accepted": acc, "guarded_solves_per_s": acc / dt,
+                     "arnoldi_steps": int(sum(sum(a["iters"] for a in r["attempts"]) for r in hist)),
+                     "floors": [r["floor_index"] for r in hist],
+                     "compliance_first_last": [hist[0]["compliance"], hist[-1]["compliance"]]}
+        g.close()
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["batch102", "oc_loop"])
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--iters", type=int, default=40)
+    a = ap.parse_args(argv)
+    res = batch102(a) if a.what == "batch102" else oc_loop(a)
+    print(json.dumps(res), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

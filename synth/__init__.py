@@ -149,17 +149,21 @@ def epoch_permutations(n: int, epochs: int, seed: int) -> np.ndarray:
 
 
 def selector_training_states(n: int, dims, seed: int):
-    """A mix of hard-field states for selector training: Bernoulli fields with solid
-    probability q ~ U(0.15, 0.6) and smoothed-Gaussian fields with floor fraction
-    ~ U(0.1, 0.6) and sigma in {1, 2, 3}, alternating."""
+    """A mix of states for selector training, in turn: Bernoulli hard fields with solid
+    probability q ~ U(0.15, 0.6); smoothed-Gaussian fields with floor fraction
+    ~ U(0.1, 0.6) and sigma in {1, 2, 3}; optimised-like fields with volume
+    ~ U(0.2, 0.4) and forced-floor fraction ~ U(0.1, 0.5)."""
     rng = np.random.default_rng(seed)
     nx, ny, nz = dims
     out = []
     for i in range(n):
         s = int(rng.integers(0, 2**31 - 1))
-        if i % 2 == 0:
+        if i % 3 == 0:
             out.append(bernoulli_density(nx, ny, nz, s, float(rng.uniform(0.15, 0.6))))
-        else:
+        elif i % 3 == 1:
             out.append(smoothed_gaussian_density(nx, ny, nz, s, float(rng.choice([1.0, 2.0, 3.0])),
                                                  float(rng.uniform(0.1, 0.6))))
+        else:
+            out.append(optimised_like_density(nx, ny, nz, s, float(rng.uniform(0.2, 0.4)),
+                                              float(rng.uniform(0.1, 0.5))))
     return out

@@ -101,3 +101,15 @@ def test_selector_gain_over_rule_on_held_out_states(gf):
     for r in cmp["mlp"]:
         if r["status"] == gf.GF_ACCEPTED:
             assert r["eta"] <= 1e-6
+    # the confidence-gated form never starts above the argmax form and picks floors
+    # above the full ladder's no more often
+    feats = X[ntr:]
+    probs = net.probs(feats)
+    assert np.allclose(probs.sum(1), 1.0)
+    assert np.array_equal(probs.argmax(1), net.predict(feats))
+    pol_c = gf.policy_defaults(rho0=1e-9, ladder=[1e-6, 1e-4, 1e-2], kmax=60, probe_iters=50, checkpoint_a=25,
+                               checkpoint_b=50, solve_prec=gf.GF_MIXED, mlp_confidence=0.9)
+    cmp_c = S.compare_selectors(dims, rh[ntr:], L, pol_c, net)
+    higher = lambda name, c: sum(r["floor_index"] > f["floor_index"] >= 0
+                                 for r, f in zip(c[name], c["full"]) if r["status"] == gf.GF_ACCEPTED)
+    assert higher("mlp", cmp_c) <= higher("mlp", cmp)
