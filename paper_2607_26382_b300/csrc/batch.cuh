@@ -24,6 +24,7 @@ struct BatchTables {
 
 __global__ void batch_mark_kernel(KState** st, const int* __restrict__ active, int B)
 {
+    GF_PDL_ENTER();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B || active[i]) return;
     st[i]->skip = 1;
@@ -34,6 +35,7 @@ __global__ void batch_mark_kernel(KState** st, const int* __restrict__ active, i
 // so its (already applied) update is not repeated.
 __global__ void batch_retire_kernel(KState** st, int B)
 {
+    GF_PDL_ENTER();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B) return;
     if (!st[i]->skip && st[i]->status != KS_RUN) st[i]->skip = 1;
@@ -43,6 +45,7 @@ __global__ void batch_retire_kernel(KState** st, int B)
 __global__ void batch_gather_kernel(KState* const* st, double* const* hist, int B, int a, int b,
                                     double* __restrict__ out)
 {
+    GF_PDL_ENTER();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B) return;
     const int k = st[i]->k;
@@ -54,6 +57,7 @@ __global__ void batch_gather_kernel(KState* const* st, double* const* hist, int 
 
 __global__ void batch_abort_kernel(KState** st, const int* __restrict__ abort_flags, int B)
 {
+    GF_PDL_ENTER();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B || !abort_flags[i]) return;
     st[i]->status = KS_STOP;
@@ -64,6 +68,7 @@ __global__ void batch_abort_kernel(KState** st, const int* __restrict__ abort_fl
 // Gauss-Jordan pivot k on every state's matrix at once (blockIdx.y = state).
 __global__ void batch_gj_prepare_kernel(BatchTables t, const int* __restrict__ active, int k)
 {
+    GF_PDL_ENTER();
     const int i = blockIdx.y;
     if (!active[i]) return;
     const int n = t.n[i];
@@ -78,6 +83,7 @@ __global__ void batch_gj_prepare_kernel(BatchTables t, const int* __restrict__ a
 
 __global__ void batch_gj_eliminate_kernel(BatchTables t, const int* __restrict__ active, int k)
 {
+    GF_PDL_ENTER();
     const int i = blockIdx.y;
     if (!active[i]) return;
     const int n = t.n[i];
