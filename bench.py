@@ -35,7 +35,7 @@ RHO0, LADDER, TAU, KMAX, PROBE, RESTART = 1e-6, [1e-5, 1e-4, 1e-3], 1e-6, 200, 1
 FP64_PEAK_NOTE = "148 SMs x 2 FP64 FMA/clk x 2 flop x sm_max_mhz"
 WORKLOAD = ("cantilever 96x48x48 (698,691 DOF), smoothed-Gaussian density sigma=2 with 40% of voxels "
             "at floor, p=3; probe at 1e-6, ladder {1e-5,1e-4,1e-3}; FGMRES(30), 5-level GMG, "
-            "FP32/BF16 V-cycle, FP64 Krylov with the split-integer FP64-class operator, native FP64 guard, "
+            "FP32/BF16 V-cycle, FP64-class Krylov (split-integer operator, double-float CGS2), native FP64 guard, "
             "tau=1e-6, kmax=200")
 
 
@@ -242,7 +242,8 @@ def run_b300(args):
     f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
     g.cantilever_load(f)
     u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
-    outer = 1 if prec == gf.GF_MIXED else 0     # split-integer Krylov operator in the mixed form
+    # mixed form: split-integer Krylov operator and double-float CGS2 (FP64-class, FP32 pipe)
+    outer = 2 if prec == gf.GF_MIXED else 0
     pol = gf.policy_defaults(rho0=RHO0, ladder=LADDER, tau=TAU, kmax=KMAX, probe_iters=PROBE,
                              solve_restart=RESTART, solve_prec=prec, solve_outer=outer)
 

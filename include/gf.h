@@ -81,8 +81,11 @@ typedef struct {
     int    nu1, nu2;   /* pre/post node-block Jacobi sweeps (>= 1) */
     double omega;      /* Jacobi damping */
     double* history;   /* host, optional: receives history[0..iters] (length >= kmax+1) */
-    int    outer;      /* outer (Krylov) operator: 0 = native FP64 K*u; 1 = split-integer
-                          FP64-class K*u (gf_apply_K_split). The guard is always native FP64. */
+    int    outer;      /* outer (Krylov) arithmetic: 0 = native FP64 K*u and CGS2; 1 = split-integer
+                          FP64-class K*u (gf_apply_K_split), native FP64 CGS2; 2 = split-integer
+                          K*u and CGS2 in double-float arithmetic (FP32 instructions, ~48-bit
+                          basis vectors; h, rotations and least squares stay FP64). Other values:
+                          GF_ERR_ARG. The guard is always native FP64. */
 } gf_solve_opts;
 
 typedef struct {

@@ -277,7 +277,7 @@ int batch_solve(gf_batch* b, const gf_solve_opts* o, const std::vector<int>& act
                 const gf_policy* pol, std::vector<BatchOut>& out)
 {
     const int B = b->B, m = o->restart;
-    for (int i = 0; i < B; ++i) RET(ensure_krylov(b->g[i], m, std::max(o->kmax, probe_at)));
+    for (int i = 0; i < B; ++i) RET(ensure_krylov(b->g[i], m, std::max(o->kmax, probe_at), o->outer));
     RET(batch_tables(b));
     RET(batch_graphs(b, o));
     CK(cudaMemcpyAsync(b->d_active, active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, b->stream));

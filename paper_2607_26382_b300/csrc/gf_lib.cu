@@ -6,8 +6,10 @@
 #include "../../include/gf.h"
 #include "stencil.cuh"
 #include "krylov.cuh"
+#include "ddgs.cuh"
 #include "oc.cuh"
 #include "split.cuh"
+#include "vcycle_cluster.cuh"
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -128,6 +130,10 @@ struct gf_grid {
     // Krylov workspace
     int m_alloc = 0;
     double *V = nullptr, *Z = nullptr, *partial = nullptr, *work = nullptr, *xsave = nullptr;
+    float2* Vd = nullptr;             // double-float copy of the basis (outer == 2)
+    float2* pdd = nullptr;            // per-block partial pairs of the double-float passes
+    unsigned int* ddticket = nullptr; // arrival counter of their last-block finish
+    int md_alloc = 0, nbd = 0;        // nbd: blocks of the double-float passes
     gf::KState* st = nullptr;
     gf::KState* gst = nullptr;   // guard scratch
     double* hist = nullptr;
@@ -149,6 +155,7 @@ struct gf_grid {
     int tpb[2] = {256, 256};          // node-stencil block size: [0] FP64, [1] FP32 (0 = smem-tiled kernel)
     bool skip_coarse_inverse = false; // batched set-up builds the coarsest inverse itself
     double dstat[3] = {0.0, 0.0, 0.0}; // fraction of rho_hat == 0, mean, std (at set_density)
+    int vc_l0 = -1;                   // first level run by the cluster V-cycle kernel (-1: none)
     // split-integer operator: K0 = s_split * M with integer M (when it exists)
     bool has_split = false;
     double s_split = 0.0;
@@ -349,7 +356,9 @@ int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2,
     const int L = g->L;
     g->stats.vcycles++;
     std::vector<float*> cur(L);
-    for (int l = 0; l < L - 1; ++l) {
+    const int lc = g->vc_l0;             // levels >= lc run in one cluster launch
+    const int Ldown = (lc > 0) ? lc : L - 1;
+    for (int l = 0; l < Ldown; ++l) {
         Level& lev = g->lv[l];
         float* x = lev.x32;
         float* t = lev.t32;
@@ -374,13 +383,30 @@ int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2,
         Level& c = g->lv[l + 1];
         LAUNCH(g, nblk(c.nodes), 256, gf::restrict_kernel<float>, (const float*)lev.r32, c.b32, c.dims(), halt);
     }
-    {
+    if (lc > 0) {
+        gf::VcArgs va{};
+        for (int l = lc; l < L; ++l) {
+            Level& q = g->lv[l];
+            va.lv[l] = gf::VcLevel{q.dims(), q.nodes, q.E32, q.b32, q.x32, q.t32, q.r32};
+        }
+        va.l0 = lc;
+        va.L = L;
+        va.nu1 = nu1;
+        va.nu2 = nu2;
+        va.nc = g->nc;
+        va.omega = omega;
+        va.Ainv = g->Ainv;
+        va.halt = halt;
+        LAUNCH(g, gf::VC_CLUSTER, gf::VC_THREADS, gf::coarse_vcycle_kernel, va, g->K0f);
+        // the level-lc result sits in x32 or t32 by the parity of its smoothing swaps
+        cur[lc] = (((nu1 - 1) + nu2) & 1) ? g->lv[lc].t32 : g->lv[lc].x32;
+    } else {
         Level& c = g->lv[L - 1];
         LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<float, float>), (const double*)g->Ainv,
                (const float*)c.b32, c.x32, g->nc, halt);
         cur[L - 1] = c.x32;
     }
-    for (int l = L - 2; l >= 0; --l) {
+    for (int l = ((lc > 0) ? lc : L - 1) - 1; l >= 0; --l) {
         Level& lev = g->lv[l];
         float* x = cur[l];
         float* t = (x == lev.x32) ? lev.t32 : lev.x32;
@@ -424,8 +450,19 @@ int applyKsplit(gf_grid* g, const double* u, double* y, const int* halt)
     g->stats.apply_K_fp64++;
     const dim3 grid((g->nx + 1 + gf::SPX - 1) / gf::SPX, (g->ny + 1 + gf::SPY - 1) / gf::SPY,
                     (g->nz + 1 + gf::SPZ - 1) / gf::SPZ);
-    LAUNCH(g, grid, dim3(gf::SPX, gf::SPY, gf::SPZ), gf::apply_split_kernel, u, y, (const float2*)g->Edf,
-           g->lv[0].dims(), g->Msplit, halt);
+    LAUNCH(g, grid, dim3(gf::SPX, gf::SPY, gf::SPZ), gf::apply_split_kernel<false>, u, y, (float2*)nullptr,
+           (const float2*)g->Edf, g->lv[0].dims(), g->Msplit, halt);
+    return GF_OK;
+}
+
+// The same product written as double-float pairs (input of the double-float CGS2).
+int applyKsplit_dd(gf_grid* g, const double* u, float2* yd, const int* halt)
+{
+    g->stats.apply_K_fp64++;
+    const dim3 grid((g->nx + 1 + gf::SPX - 1) / gf::SPX, (g->ny + 1 + gf::SPY - 1) / gf::SPY,
+                    (g->nz + 1 + gf::SPZ - 1) / gf::SPZ);
+    LAUNCH(g, grid, dim3(gf::SPX, gf::SPY, gf::SPZ), gf::apply_split_kernel<true>, u, (double*)nullptr, yd,
+           (const float2*)g->Edf, g->lv[0].dims(), g->Msplit, halt);
     return GF_OK;
 }
 
@@ -471,9 +508,22 @@ void drop_graphs(gf_grid* g)
     }
 }
 
-int ensure_krylov(gf_grid* g, int m, int kmax)
+int ensure_krylov(gf_grid* g, int m, int kmax, int outer)
 {
-    if (m > g->m_alloc || kmax + 1 > g->hist_cap) drop_graphs(g);
+    if (m > g->m_alloc || kmax + 1 > g->hist_cap || (outer == 2 && m > g->md_alloc)) drop_graphs(g);
+    if (outer == 2 && m > g->md_alloc) {
+        cudaFree(g->Vd);
+        g->Vd = nullptr;
+        g->md_alloc = 0;
+        RET(allocT(&g->Vd, (size_t)(m + 1) * g->ndof));
+        if (!g->pdd) {
+            g->nbd = (int)std::min<long long>(4LL * g->sms, (g->ndof + gf::DD_TILE - 1) / gf::DD_TILE);
+            RET(allocT(&g->pdd, (size_t)g->nbd * (gf::KRY_MMAX + 1)));
+            RET(allocT(&g->ddticket, 1));
+            CK(cudaMemset(g->ddticket, 0, sizeof(unsigned int)));
+        }
+        g->md_alloc = m;
+    }
     if (m > g->m_alloc) {
         cudaFree(g->V);
         cudaFree(g->Z);
@@ -527,10 +577,22 @@ int pick_nv(int nv)
 }
 
 template <int NV>
-int cgs2_step(gf_grid* g, int j, double* w)
+int cgs2_step(gf_grid* g, int j, double* w, int outer)
 {
     const long long n = g->ndof, ld = g->ndof;
     const int nv = j + 1;
+    if (outer == 2) {   // double-float passes on the FP32 pipe; w arrives as wd
+        float2* wd = g->Vd + (long long)(j + 1) * ld;
+        const int nb = g->nbd;
+        LAUNCH(g, nb, gf::DD_THREADS, gf::ddgs_dots_kernel<NV>, (const float2*)g->Vd, ld, nv, (const float2*)wd, n,
+               g->pdd, g->st, g->ddticket);
+        LAUNCH(g, nb, gf::DD_THREADS, gf::ddgs_update_dots_kernel<NV>, (const float2*)g->Vd, ld, nv, wd, n, g->pdd,
+               g->st, g->ddticket);
+        LAUNCH(g, nb, gf::DD_THREADS, gf::ddgs_update_norm_kernel<NV>, (const float2*)g->Vd, ld, nv, wd, n, g->pdd,
+               g->st, g->ddticket);
+        LAUNCH(g, 1, 32, gf::arnoldi_tail_kernel, g->st, g->hist, j, NV, g->host_status_dev, 1e-14);
+        return GF_OK;
+    }
     LAUNCH(g, g->nbr, gf::RED_THREADS, gf::cgs_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
     LAUNCH(g, 1, 32 * 32, gf::reduce_partials_kernel, g->partial, g->nbr, NV + 1, NV + 1, g->st, 0, 1);
     LAUNCH(g, g->nbr, gf::RED_THREADS, gf::cgs_update_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
@@ -549,13 +611,17 @@ int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
     double* w = g->V + (long long)(j + 1) * ld;
     const int* halt = &g->st->status;
     RET(vcycle_dispatch(g, vj, zj, o->prec, o->nu1, o->nu2, o->omega, halt));
-    RET(applyOuter(g, zj, w, halt, o->outer));
+    if (o->outer == 2) RET(applyKsplit_dd(g, zj, g->Vd + (long long)(j + 1) * ld, halt));
+    else RET(applyOuter(g, zj, w, halt, o->outer));
     switch (pick_nv(j + 1)) {
-        case 8: RET(cgs2_step<8>(g, j, w)); break;
-        case 16: RET(cgs2_step<16>(g, j, w)); break;
-        default: RET(cgs2_step<32>(g, j, w)); break;
+        case 8: RET(cgs2_step<8>(g, j, w, o->outer)); break;
+        case 16: RET(cgs2_step<16>(g, j, w, o->outer)); break;
+        default: RET(cgs2_step<32>(g, j, w, o->outer)); break;
     }
-    LAUNCH(g, 2 * g->sms, 256, gf::scale_kernel, w, g->ndof, g->st, 1);
+    if (o->outer == 2)
+        LAUNCH(g, 2 * g->sms, 256, gf::ddgs_scale_kernel, g->Vd + (long long)(j + 1) * ld, w, g->ndof, g->st);
+    else
+        LAUNCH(g, 2 * g->sms, 256, gf::scale_kernel, w, g->ndof, g->st, 1);
     return GF_OK;
 }
 
@@ -569,7 +635,10 @@ int cycle_start(gf_grid* g, const double* f, const double* x, bool x_zero, bool 
            x_zero ? 1 : 0, skip);
     LAUNCH(g, 1, 64, gf::reduce_partials_kernel, g->partial, g->nbr, 2, 2, g->st, 0, 0);
     LAUNCH(g, 1, 32, gf::cycle_start_tail_kernel, g->st, g->hist, g->host_status_dev, first ? 1 : 0);
-    LAUNCH(g, 2 * g->sms, 256, gf::scale_kernel, v0, g->ndof, g->st, 1);
+    if (outer == 2)
+        LAUNCH(g, 2 * g->sms, 256, gf::ddgs_scale_fp64_kernel, v0, g->Vd, g->ndof, g->st);
+    else
+        LAUNCH(g, 2 * g->sms, 256, gf::scale_kernel, v0, g->ndof, g->st, 1);
     return GF_OK;
 }
 
@@ -628,7 +697,7 @@ int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, g
                bool x_zero, double* host_hist, ProbeHook* hook = nullptr)
 {
     const int m = o->restart;
-    RET(ensure_krylov(g, m, o->kmax));
+    RET(ensure_krylov(g, m, o->kmax, o->outer));
     const int NX0 = g->nx + 1;
     // fixed entries of u are written as 0
     LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, double>), u, u, g->ndof, NX0, nullptr);
@@ -697,7 +766,8 @@ int validate_opts(const gf_solve_opts* o)
     if (o->prec != GF_FP64 && o->prec != GF_MIXED) return set_err(GF_ERR_ARG, "prec");
     if (o->nu1 < 1 || o->nu2 < 1 || o->nu1 > 16 || o->nu2 > 16) return set_err(GF_ERR_ARG, "nu1/nu2 in [1,16]");
     if (!(o->omega > 0.0 && o->omega < 2.0)) return set_err(GF_ERR_ARG, "omega in (0,2)");
-    if (o->outer != 0 && o->outer != 1) return set_err(GF_ERR_ARG, "outer must be 0 (FP64) or 1 (split)");
+    if (o->outer < 0 || o->outer > 2)
+        return set_err(GF_ERR_ARG, "outer must be 0 (FP64), 1 (split K*u) or 2 (split K*u, double-float CGS2)");
     return GF_OK;
 }
 
@@ -848,6 +918,18 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         g->lv.push_back(L);
     }
     g->nc = (int)g->lv.back().ndof;
+    // Opt-in (GF_VC_CLUSTER=<max nodes>): the cluster kernel takes the levels from the
+    // first one (>= 1) with at most that many nodes, when at least one smoothing level
+    // lies above the coarsest. Off by default: in graph-replayed solves the per-level
+    // launches cost ~2 us each, and 8 SMs run the stages no faster than that.
+    if (const char* e = getenv("GF_VC_CLUSTER")) {
+        const long long maxn = atoll(e);
+        for (int l = 1; maxn > 0 && l < levels - 1; ++l)
+            if (g->lv[l].nodes <= maxn) {
+                g->vc_l0 = l;
+                break;
+            }
+    }
     int r = GF_OK;
     g->nbr = (int)std::min<long long>(2LL * g->sms, std::max<long long>(1, (g->ndof + 1023) / 1024));
     if ((r = allocT(&g->Ainv, (size_t)g->nc * g->nc)) || (r = allocT(&g->gjcol, g->nc)) ||
@@ -888,7 +970,7 @@ int gf_destroy_grid(gf_grid* g)
     }
     cudaFree(g->Ainv); cudaFree(g->gjcol); cudaFree(g->gjrow); cudaFree(g->dflag);
     cudaFree(g->rho64); cudaFree(g->rho16); cudaFree(g->work); cudaFree(g->partial);
-    cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Z); cudaFree(g->hist);
+    cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Vd); cudaFree(g->pdd); cudaFree(g->ddticket); cudaFree(g->Z); cudaFree(g->hist);
     cudaFree(g->xsave);
     cudaFree(g->Edf);
     cudaFree(g->oc_rho); cudaFree(g->oc_dc); cudaFree(g->oc_dcx); cudaFree(g->oc_dvx); cudaFree(g->oc_ones);

@@ -153,6 +153,8 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n
     const int i = threadIdx.x >> 5;
     for (int q = i; q < cnt; q += blockDim.x >> 5) {
         double s = 0.0;
+        // unrolled so the loads are in flight together; the additions keep their order
+#pragma unroll 8
         for (int b = lane; b < nblocks; b += 32) s += partial[(long long)b * stride + q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);

@@ -54,9 +54,16 @@ __device__ __forceinline__ void two_sum_acc(float& ah, float& al, float ph, floa
     al += pl + err;
 }
 
+// 2^k as a float for k in [-126, 127], from its exponent bits
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
+
+// DD = false: y (FP64). DD = true: yd, the result as a normalised double-float pair
+// (hi + lo), for the double-float Gram-Schmidt passes.
+template <bool DD>
 __global__ void __launch_bounds__(128)
-apply_split_kernel(const double* __restrict__ u, double* __restrict__ y, const float2* __restrict__ Edf,
-                   GridDims d, const __grid_constant__ MParam M, const int* __restrict__ halt)
+apply_split_kernel(const double* __restrict__ u, double* __restrict__ y, float2* __restrict__ yd,
+                   const float2* __restrict__ Edf, GridDims d, const __grid_constant__ MParam M,
+                   const int* __restrict__ halt)
 {
     GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
@@ -116,9 +123,11 @@ apply_split_kernel(const double* __restrict__ u, double* __restrict__ y, const f
     if (gi >= NX || gj >= NY || gk >= NZ) return;
     const long long n = gi + (long long)NX * (gj + (long long)NY * gk);
     if (gi == 0) {
-        y[3 * n + 0] = 0.0;
-        y[3 * n + 1] = 0.0;
-        y[3 * n + 2] = 0.0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            if (DD) yd[3 * n + r] = make_float2(0.f, 0.f);
+            else y[3 * n + r] = 0.0;
+        }
         return;
     }
 
@@ -200,6 +209,21 @@ apply_split_kernel(const double* __restrict__ u, double* __restrict__ y, const f
                     two_sum_acc(ah[r], al[r], ph, pl);
                 }
             }
+    if (DD) {
+        // scale by 2^(xmax - 1022 - P) in two exact power-of-two steps (the factor
+        // itself may lie outside the float range while the result does not), then
+        // renormalise the pair (Fast2Sum; |hi| >= |lo|)
+        const int k = xmax - 1022 - SPLIT_P;
+        const int k1 = k / 2, k2 = k - k1;
+        const float f1 = pow2f(max(-126, min(127, k1))), f2 = pow2f(max(-126, min(127, k2)));
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float h0 = ah[r] * f1 * f2, l0 = al[r] * f1 * f2;
+            const float h = h0 + l0;
+            yd[3 * n + r] = make_float2(h, l0 - (h - h0));
+        }
+        return;
+    }
     // 2^(xmax - 1022 - P) built from its exponent bits when it is a normal number
     const int sexp = xmax - 1022 - SPLIT_P + 1023;
     const double scale = (sexp >= 1) ? __longlong_as_double((long long)sexp << 52) : scalbn(1.0, sexp - 1023);

@@ -52,18 +52,12 @@ __device__ __forceinline__ void node_coords(long long n, int NX, int NY, int& i,
 // MODE == ST_SWEEP: out = x + omega * D_n^{-1} (b - K x)     (D_n: 3x3 node block)
 // Fixed nodes (i == 0) read as 0 and are written as 0. Element moduli E are
 // already multiplied by the element edge h (K_e(h) = h K_e(1) in 3D).
-template <typename T, typename ET, int MODE, typename BT = T, typename OT = T>
-__global__ void __launch_bounds__(256)
-node_stencil_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __restrict__ out,
-                    const ET* __restrict__ E, GridDims d, const __grid_constant__ K0Param<T> K0,
-                    T omega, const int* __restrict__ halt)
+template <typename T, typename ET, int MODE, typename BT, typename OT>
+__device__ __forceinline__ void stencil_node(long long n, const T* __restrict__ x, const BT* __restrict__ b,
+                                             OT* __restrict__ out, const ET* __restrict__ E, GridDims d,
+                                             const K0Param<T>& K0, T omega)
 {
-    GF_PDL_ENTER();
-    if (halt != nullptr && *halt != 0) return;
     const int NX = d.nx + 1, NY = d.ny + 1;
-    const long long nn = (long long)NX * NY * (d.nz + 1);
-    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= nn) return;
     int i, j, k;
     node_coords(n, NX, NY, i, j, k);
     if (i == 0) {
@@ -152,19 +146,27 @@ node_stencil_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __res
     out[3 * n + 2] = OT(x[3 * n + 2] + s * (c02 * r0 + c12 * r1 + c22 * r2));
 }
 
-// First smoothing sweep from x = 0: out = omega * D_n^{-1} b. BT is b's type.
-template <typename T, typename ET, typename BT>
+template <typename T, typename ET, int MODE, typename BT = T, typename OT = T>
 __global__ void __launch_bounds__(256)
-first_sweep_kernel(const BT* __restrict__ b, T* __restrict__ out, const ET* __restrict__ E,
-                   GridDims d, const __grid_constant__ K0Param<T> K0, T omega,
-                   const int* __restrict__ halt)
+node_stencil_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __restrict__ out,
+                    const ET* __restrict__ E, GridDims d, const __grid_constant__ K0Param<T> K0,
+                    T omega, const int* __restrict__ halt)
 {
     GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
-    const int NX = d.nx + 1, NY = d.ny + 1;
-    const long long nn = (long long)NX * NY * (d.nz + 1);
+    const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
+    stencil_node<T, ET, MODE, BT, OT>(n, x, b, out, E, d, K0, omega);
+}
+
+// First smoothing sweep from x = 0: out = omega * D_n^{-1} b. BT is b's type.
+template <typename T, typename ET, typename BT>
+__device__ __forceinline__ void first_sweep_node(long long n, const BT* __restrict__ b, T* __restrict__ out,
+                                                 const ET* __restrict__ E, GridDims d, const K0Param<T>& K0,
+                                                 T omega)
+{
+    const int NX = d.nx + 1, NY = d.ny + 1;
     int i, j, k;
     node_coords(n, NX, NY, i, j, k);
     if (i == 0) {
@@ -205,19 +207,27 @@ first_sweep_kernel(const BT* __restrict__ b, T* __restrict__ out, const ET* __re
     out[3 * n + 2] = s * (c02 * r0 + c12 * r1 + c22 * r2);
 }
 
+template <typename T, typename ET, typename BT>
+__global__ void __launch_bounds__(256)
+first_sweep_kernel(const BT* __restrict__ b, T* __restrict__ out, const ET* __restrict__ E,
+                   GridDims d, const __grid_constant__ K0Param<T> K0, T omega,
+                   const int* __restrict__ halt)
+{
+    GF_PDL_ENTER();
+    if (halt != nullptr && *halt != 0) return;
+    const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    first_sweep_node<T, ET, BT>(n, b, out, E, d, K0, omega);
+}
+
 // Restriction = transpose of trilinear prolongation, then mask: coarse node (I,J,K)
 // gathers the fine nodes (2I+di, 2J+dj, 2K+dk), di,dj,dk in {-1,0,1}, with weight
 // prod (1 if offset 0 else 1/2). `cd` are the coarse element counts.
 template <typename T>
-__global__ void __launch_bounds__(256)
-restrict_kernel(const T* __restrict__ r, T* __restrict__ bc, GridDims cd, const int* __restrict__ halt)
+__device__ __forceinline__ void restrict_node(long long n, const T* __restrict__ r, T* __restrict__ bc, GridDims cd)
 {
-    GF_PDL_ENTER();
-    if (halt != nullptr && *halt != 0) return;
     const int CX = cd.nx + 1, CY = cd.ny + 1;
-    const long long nn = (long long)CX * CY * (cd.nz + 1);
-    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= nn) return;
     int I, J, K;
     node_coords(n, CX, CY, I, J, K);
     if (I == 0) {
@@ -253,17 +263,23 @@ restrict_kernel(const T* __restrict__ r, T* __restrict__ bc, GridDims cd, const 
     bc[3 * n + 2] = s2;
 }
 
-// x += P xc (trilinear interpolation, fine nodes on the fixed face untouched).
-template <typename T, typename CT>
+template <typename T>
 __global__ void __launch_bounds__(256)
-prolong_add_kernel(T* __restrict__ x, const CT* __restrict__ xc, GridDims fd, const int* __restrict__ halt)
+restrict_kernel(const T* __restrict__ r, T* __restrict__ bc, GridDims cd, const int* __restrict__ halt)
 {
     GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
-    const int FX = fd.nx + 1, FY = fd.ny + 1;
-    const long long nn = (long long)FX * FY * (fd.nz + 1);
+    const long long nn = (long long)(cd.nx + 1) * (cd.ny + 1) * (cd.nz + 1);
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
+    restrict_node<T>(n, r, bc, cd);
+}
+
+// x += P xc (trilinear interpolation, fine nodes on the fixed face untouched).
+template <typename T, typename CT>
+__device__ __forceinline__ void prolong_node(long long n, T* __restrict__ x, const CT* __restrict__ xc, GridDims fd)
+{
+    const int FX = fd.nx + 1, FY = fd.ny + 1;
     int i, j, k;
     node_coords(n, FX, FY, i, j, k);
     if (i == 0) return;
@@ -290,6 +306,18 @@ prolong_add_kernel(T* __restrict__ x, const CT* __restrict__ xc, GridDims fd, co
     x[3 * n + 0] += s0;
     x[3 * n + 1] += s1;
     x[3 * n + 2] += s2;
+}
+
+template <typename T, typename CT>
+__global__ void __launch_bounds__(256)
+prolong_add_kernel(T* __restrict__ x, const CT* __restrict__ xc, GridDims fd, const int* __restrict__ halt)
+{
+    GF_PDL_ENTER();
+    if (halt != nullptr && *halt != 0) return;
+    const long long nn = (long long)(fd.nx + 1) * (fd.ny + 1) * (fd.nz + 1);
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    prolong_node<T, CT>(n, x, xc, fd);
 }
 
 // ---------------------------------------------------------------- setup -------

@@ -34,11 +34,12 @@ def _rho(dims, kind, seed, q):
     return synth.smoothed_gaussian_density(nx, ny, nz, seed, 2.0, q)
 
 
-@pytest.mark.parametrize("selector,prec", [("rule", 0), ("full", 1)])
-def test_batch_matches_single_state(gf, selector, prec):
+@pytest.mark.parametrize("selector,prec,outer", [("rule", 0, 0), ("full", 1, 0), ("rule", 1, 2)])
+def test_batch_matches_single_state(gf, selector, prec, outer):
     L = 3
     sel = gf.GF_SEL_RULE if selector == "rule" else gf.GF_SEL_FULL
-    pol = gf.policy_defaults(rho0=1e-8, ladder=[1e-5, 1e-4, 1e-3], kmax=120, selector=sel, solve_prec=prec)
+    pol = gf.policy_defaults(rho0=1e-8, ladder=[1e-5, 1e-4, 1e-3], kmax=120, selector=sel, solve_prec=prec,
+                             solve_outer=outer)
     batch = gf.Batch([s[0] for s in STATES], levels=L)
     tuned = batch.autotune()
     assert all(t[0] in (64, 128, 256) and t[1] in (0, 64, 128, 256, -64, -128, -256) for t in tuned)

@@ -153,15 +153,19 @@ def _oracle_solve(m, rho, rho_min, L, f, kmax=200, restart=30, tol=1e-6):
     return O.solve_at_floor(setup, f, rho_min, kmax, tol)
 
 
+# outer = 2 runs the same FP64 V-cycle with the FP64-class forms of the Krylov
+# operator (split-integer K*u) and of CGS2 (double-float passes): the oracle's FP64
+# history must still be matched to the same tolerance.
+@pytest.mark.parametrize("outer", [0, 2])
 @pytest.mark.parametrize("case", [(16, 8, 8, 3, "uniform", 1e-3, 30), (16, 8, 8, 3, "bernoulli", 1e-6, 30),
                                   (24, 12, 8, 3, "smooth", 1e-3, 8)])
-def test_solve_fp64_parity(gf, case):
+def test_solve_fp64_parity(gf, case, outer):
     nx, ny, nz, L, kind, rm, restart = case
     g, m, rho = make(gf, nx, ny, nz, L, seed=4, rho_min=rm, kind=kind)
     f = O.cantilever_load(m)
     res, E, K0 = _oracle_solve(m, rho, rm, L, f, restart=restart)
     u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
-    out = g.solve(dev(f), u, restart=restart, kmax=200, tol=1e-6, prec=gf.GF_FP64)
+    out = g.solve(dev(f), u, restart=restart, kmax=200, tol=1e-6, prec=gf.GF_FP64, outer=outer)
     assert abs(out["iters"] - res.iters) <= 1
     assert out["flag"] == res.flag
     k = min(out["iters"], res.iters)
@@ -246,6 +250,12 @@ def test_errors(gf):
         g.set_density(dev(bad), 3.0)
     with pytest.raises(TypeError):
         g.set_density(dev(np.ones(g.n_elem), torch.float32), 3.0)
+    g.set_density(dev(np.full(g.n_elem, 0.5)), 3.0)
+    g.set_floor(1e-3)
+    for outer in (-1, 3):                             # Krylov operator form out of range
+        with pytest.raises(gf.GFError) as e:
+            g.solve(u.clone(), u.clone(), outer=outer)
+        assert e.value.code == -1                     # GF_ERR_ARG
 
 
 # ------------------------------------------------------------- a8: policy --------
@@ -417,13 +427,14 @@ def test_solve_with_split_outer_operator(gf):
     g, m, rho = make(gf, nx, ny, nz, L, seed=4, rho_min=1e-6, kind="uniform")
     f = O.cantilever_load(m)
     outs = []
-    for outer in (0, 1):
+    for outer in (0, 1, 2):
         u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
         out = g.solve(dev(f), u, prec=gf.GF_MIXED, outer=outer)
         outs.append((out, host(u)))
-    (a, ua), (b, ub) = outs
-    assert abs(a["iters"] - b["iters"]) <= 1 and a["flag"] == b["flag"] == gf.GF_FLAG_CONVERGED
-    h = min(a["iters"], b["iters"])
-    assert np.allclose(a["history"][:h], b["history"][:h], rtol=1e-6)
+    a, ua = outs[0]
     E = O.young_modulus(rho, 1e-6, 3.0)
-    assert O.true_residual(m, E, O.element_stiffness(), f, ub) <= 1.5e-6
+    for b, ub in outs[1:]:
+        assert abs(a["iters"] - b["iters"]) <= 1 and a["flag"] == b["flag"] == gf.GF_FLAG_CONVERGED
+        h = min(a["iters"], b["iters"])
+        assert np.allclose(a["history"][:h], b["history"][:h], rtol=1e-6)
+        assert O.true_residual(m, E, O.element_stiffness(), f, ub) <= 1.5e-6
