@@ -166,24 +166,37 @@ def oracle_sample(rho):
             "apply_K_gdofs": gdofs, "seconds_sampled": t3 - t0}
 
 
-def profiled_traffic():
-    """DRAM bytes per FP64 K*u launch from the committed ncu summary, or None once the
-    kernel source has changed since the counters were taken."""
+def kernel_source_hash(source, start, end):
+    """sha1[:16] of the text between two markers of a kernel source file (None if absent)."""
     import hashlib
+    try:
+        src = open(os.path.join(ROOT, "paper_2607_26382_b300", "csrc", source)).read()
+        a = src.index(start)
+        b = src.index(end, a)
+    except (OSError, ValueError):
+        return None
+    return hashlib.sha1(src[a:b].encode()).hexdigest()[:16]
+
+
+def profiled_traffic(profile, source, start, end):
+    """DRAM bytes per launch from a committed ncu summary under profiles/, or None once
+    the kernel's source text has changed since the counters were taken."""
     import re
     try:
-        src = open(os.path.join(ROOT, "paper_2607_26382_b300", "csrc", "stencil.cuh")).read()
-        prof = open(os.path.join(ROOT, "profiles", "apply_K_fp64_96x48x48.md")).read()
+        prof = open(os.path.join(ROOT, "profiles", profile)).read()
     except OSError:
         return None
-    a = src.index("template <typename T, typename ET, int MODE>")
-    b = src.index("// First smoothing sweep from x = 0")
-    h = hashlib.sha1(src[a:b].encode()).hexdigest()[:16]
+    h = kernel_source_hash(source, start, end)
     m_h = re.search(r"kernel_source_sha1: ([0-9a-f]+)", prof)
     m_t = re.search(r"traffic_bytes_per_launch \| (\d+)", prof)
-    if not m_h or not m_t or m_h.group(1) != h:
+    if h is None or not m_h or not m_t or m_h.group(1) != h:
         return None
     return int(m_t.group(1))
+
+
+# kernel text spans hashed for the traffic figures
+FP64_KU_SPAN = ("stencil.cuh", "template <typename T, typename ET, int MODE, typename BT", "// First smoothing sweep")
+SPLIT_KU_SPAN = ("split.cuh", "// 2^k as a float", "}  // namespace gf")
 
 
 def emit(d):
@@ -314,13 +327,15 @@ def run_b300(args):
     gdofs = g.n_dof / t_k / 1e9
     gdofs_split = g.n_dof / t_s / 1e9
     native = {"bound": "alu", "achieved": flops / t_k / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
-              "frac": flops / t_k / 1e12 / fp64_peak, "traffic": profiled_traffic(),
+              "frac": flops / t_k / 1e12 / fp64_peak,
+              "traffic": profiled_traffic("apply_K_fp64_96x48x48.md", *FP64_KU_SPAN),
               "kernel": "node_stencil_kernel<double> (native FP64 K*u; the guard's operator)",
               "peak_source": f"derived: {FP64_PEAK_NOTE}", "gdofs": gdofs, "ms_per_launch": t_k * 1e3}
     # split-integer K*u: 4 digit slices x 1152 exact FP32 flops per element on the FMA pipe
     split_flops = 4 * 1152.0 * g.n_elem
     split = {"bound": "alu", "achieved": split_flops / t_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-             "frac": split_flops / t_s / 1e12 / fp32_peak, "traffic": None,
+             "frac": split_flops / t_s / 1e12 / fp32_peak,
+             "traffic": profiled_traffic("apply_K_split_96x48x48.md", *SPLIT_KU_SPAN),
              "kernel": "apply_split_kernel (split-integer FP64-class K*u, FP32 digit products)",
              "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 flop x sm_max_mhz", "gdofs": gdofs_split,
              "ms_per_launch": t_s * 1e3}

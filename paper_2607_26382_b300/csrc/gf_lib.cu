@@ -9,6 +9,7 @@
 #include "ddgs.cuh"
 #include "oc.cuh"
 #include "split.cuh"
+#include "split_tc.cuh"
 #include "vcycle_cluster.cuh"
 
 #include <cuda_runtime.h>
@@ -161,6 +162,8 @@ struct gf_grid {
     double s_split = 0.0;
     gf::MParam Msplit;
     float2* Edf = nullptr;            // s_split * E_e (fine level) as float pairs
+    gf::TcBFrag Btc;                  // M as per-lane fp16 MMA B fragments (tensor-core split)
+    bool split_tc = true;             // element products on the tensor cores (GF_SPLIT_TC=0: CUDA cores)
     int gkey_outer = -1;
     // optimisation-loop scratch (allocated on first use)
     double *oc_rho = nullptr, *oc_dc = nullptr, *oc_dcx = nullptr, *oc_dvx = nullptr, *oc_ones = nullptr;
@@ -170,13 +173,13 @@ struct gf_grid {
 namespace {
 // Launch a kernel on the grid's stream, count it, and report launch errors.
 template <typename... KArgs, typename... Args>
-int launch(gf_grid* g, dim3 grid, dim3 block, void (*kern)(KArgs...), Args... args)
+int launch_smem(gf_grid* g, dim3 grid, dim3 block, size_t smem, void (*kern)(KArgs...), Args... args)
 {
     if (g->use_pdl) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = grid;
         cfg.blockDim = block;
-        cfg.dynamicSmemBytes = 0;
+        cfg.dynamicSmemBytes = smem;
         cfg.stream = g->cur_stream;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -185,15 +188,23 @@ int launch(gf_grid* g, dim3 grid, dim3 block, void (*kern)(KArgs...), Args... ar
         cfg.numAttrs = 1;
         CK(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
     } else {
-        kern<<<grid, block, 0, g->cur_stream>>>(args...);
+        kern<<<grid, block, smem, g->cur_stream>>>(args...);
     }
     g->stats.kernel_launches++;
     CK(cudaGetLastError());
     return GF_OK;
 }
+
+template <typename... KArgs, typename... Args>
+int launch(gf_grid* g, dim3 grid, dim3 block, void (*kern)(KArgs...), Args... args)
+{
+    return launch_smem(g, grid, block, 0, kern, args...);
+}
 }  // namespace
 
 #define LAUNCH(g, grid, block, kern, ...) RET(launch((g), dim3(grid), dim3(block), kern, __VA_ARGS__))
+#define LAUNCH_SMEM(g, grid, block, smem, kern, ...) \
+    RET(launch_smem((g), dim3(grid), dim3(block), (smem), kern, __VA_ARGS__))
 
 namespace {
 
@@ -445,9 +456,21 @@ int applyK64(gf_grid* g, const double* u, double* y, const int* halt)
     return stencil<double, double, gf::ST_APPLY>(g, 0, u, nullptr, y, g->lv[0].E64, g->K0d, 0.0, halt);
 }
 
+// grid of the tensor-core split kernel: 15 x 7 nodes x 8 layers per CTA
+dim3 split_tc_grid(const gf_grid* g)
+{
+    return dim3((g->nx + 1 + gf::TC_NX - 1) / gf::TC_NX, (g->ny + 1 + gf::TC_NY - 1) / gf::TC_NY,
+                (g->nz + 1 + gf::TC_CZ - 1) / gf::TC_CZ);
+}
+
 int applyKsplit(gf_grid* g, const double* u, double* y, const int* halt)
 {
     g->stats.apply_K_fp64++;
+    if (g->split_tc) {
+        LAUNCH_SMEM(g, split_tc_grid(g), gf::TC_THREADS, sizeof(gf::TcSmem), gf::apply_split_tc_kernel<false>, u, y,
+                    (float2*)nullptr, (const float2*)g->Edf, g->lv[0].dims(), g->Btc, halt);
+        return GF_OK;
+    }
     const dim3 grid((g->nx + 1 + gf::SPX - 1) / gf::SPX, (g->ny + 1 + gf::SPY - 1) / gf::SPY,
                     (g->nz + 1 + gf::SPZ - 1) / gf::SPZ);
     LAUNCH(g, grid, dim3(gf::SPX, gf::SPY, gf::SPZ), gf::apply_split_kernel<false>, u, y, (float2*)nullptr,
@@ -459,6 +482,11 @@ int applyKsplit(gf_grid* g, const double* u, double* y, const int* halt)
 int applyKsplit_dd(gf_grid* g, const double* u, float2* yd, const int* halt)
 {
     g->stats.apply_K_fp64++;
+    if (g->split_tc) {
+        LAUNCH_SMEM(g, split_tc_grid(g), gf::TC_THREADS, sizeof(gf::TcSmem), gf::apply_split_tc_kernel<true>, u,
+                    (double*)nullptr, yd, (const float2*)g->Edf, g->lv[0].dims(), g->Btc, halt);
+        return GF_OK;
+    }
     const dim3 grid((g->nx + 1 + gf::SPX - 1) / gf::SPX, (g->ny + 1 + gf::SPY - 1) / gf::SPY,
                     (g->nz + 1 + gf::SPZ - 1) / gf::SPZ);
     LAUNCH(g, grid, dim3(gf::SPX, gf::SPY, gf::SPZ), gf::apply_split_kernel<true>, u, (double*)nullptr, yd,
@@ -849,6 +877,45 @@ int dot_impl(gf_grid* g, const double* a, const double* b, long long n, double* 
     return GF_OK;
 }
 
+// fp16 bit pattern of a small integer (|v| <= 2048, exact)
+unsigned short half_bits_of_int(int v)
+{
+    if (v == 0) return 0;
+    const unsigned short sg = v < 0 ? 0x8000 : 0;
+    const int a = v < 0 ? -v : v;
+    int e = 0;
+    while ((a >> (e + 1)) != 0) ++e;                       // a in [2^e, 2^(e+1))
+    const int mant = (a << (10 - e)) & 0x3FF;              // exact: a has <= 11 significant bits
+    return (unsigned short)(sg | ((e + 15) << 10) | mant);
+}
+
+// M' (24x24, row/col q' = comp * 8 + a', a' = x + 2y + 4z) as the m16n8k16 B fragments
+// of each lane: for output component t, K-step 0 holds columns comp 0 | comp 1, K-step
+// 1 holds comp 2 | zero padding. Lane (g = lane/4, c = lane%4) holds rows k = 2c, 2c+1
+// (and 2c+8, 2c+9) of column n = g.
+void build_tc_bfrag(const gf::MParam& M, gf::TcBFrag* B)
+{
+    auto orig = [](int qp) {   // original DOF index 3 a + comp of q'
+        const int comp = qp / 8, ap = qp % 8;
+        return 3 * gf::local_index(ap & 1, (ap >> 1) & 1, ap >> 2) + comp;
+    };
+    auto mp = [&](int ip, int jp) -> unsigned int {
+        if (ip >= 24 || jp >= 24) return 0u;
+        return half_bits_of_int((int)M.m[orig(ip) * 24 + orig(jp)]);
+    };
+    for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane >> 2, c = lane & 3;
+        for (int t = 0; t < 3; ++t) {
+            const int ip = 8 * t + g;
+            for (int ks = 0; ks < 2; ++ks)
+                for (int r = 0; r < 2; ++r) {
+                    const int j0 = 16 * ks + 8 * r + 2 * c;
+                    B->w[lane][4 * t + 2 * ks + r] = mp(ip, j0) | (mp(ip, j0 + 1) << 16);
+                }
+        }
+    }
+}
+
 }  // namespace
 
 // ====================================================================== C ABI ====
@@ -886,19 +953,33 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         g->K0d.k[q] = K[q];
         g->K0f.k[q] = (float)K[q];
     }
-    // K0 = s * M with integer M, |M| <= 682 (digit products stay exact in FP32)
-    for (int kk = 1; kk <= 682 && !g->has_split; ++kk) {
+    // K0 = s * M with integer M. The 24-term digit products stay exact in FP32 when
+    // 24 |M| (2^12 - 1) < 2^24, i.e. |M| <= 170 (88 for nu = 0.3).
+    for (int kk = 1; kk <= 170 && !g->has_split; ++kk) {
         const double sc = K[0] / kk;
         bool ok = true;
         for (int q = 0; q < 576 && ok; ++q) {
             const double mq = K[q] / sc, rq = std::nearbyint(mq);
-            ok = std::fabs(mq - rq) <= 1e-9 * std::max(1.0, std::fabs(mq)) && std::fabs(rq) <= 682.0;
+            ok = std::fabs(mq - rq) <= 1e-9 * std::max(1.0, std::fabs(mq)) && std::fabs(rq) <= 170.0;
         }
         if (ok) {
             g->has_split = true;
             g->s_split = sc;
             for (int q = 0; q < 576; ++q) g->Msplit.m[q] = (float)std::nearbyint(K[q] / sc);
         }
+    }
+    if (g->has_split) {
+        build_tc_bfrag(g->Msplit, &g->Btc);
+        const char* e = getenv("GF_SPLIT_TC");
+        g->split_tc = !(e && e[0] == '0');
+        if (g->split_tc &&
+            (cudaFuncSetAttribute(gf::apply_split_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sizeof(gf::TcSmem)) != cudaSuccess ||
+             cudaFuncSetAttribute(gf::apply_split_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sizeof(gf::TcSmem)) != cudaSuccess))
+            return fail(set_err(GF_ERR_CUDA, "shared-memory size of the tensor-core split kernel"));
+    } else {
+        g->split_tc = false;
     }
     for (int l = 0; l < levels; ++l) {
         Level L;

@@ -68,6 +68,26 @@ __device__ __forceinline__ void stencil_node(long long n, const T* __restrict__ 
     }
     T a0 = 0, a1 = 0, a2 = 0;
     T d00 = 0, d11 = 0, d22 = 0, d01 = 0, d02 = 0, d12 = 0;
+    // FP32: the 27 neighbour nodes are loaded once into registers (a node shared by
+    // several elements would otherwise be re-read per element); the FMAs below run in
+    // the same order either way. Out-of-domain and fixed neighbours read as 0.
+    constexpr bool REGS = sizeof(T) == 4;
+    T nb[REGS ? 3 : 1][REGS ? 3 : 1][REGS ? 3 : 1][3];
+    if constexpr (REGS) {
+        const int NZ = d.nz + 1;
+#pragma unroll
+        for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const int ni = i - 1 + dx, nj = j - 1 + dy, nk = k - 1 + dz;
+                    const bool ok = ni >= 1 && ni < NX && nj >= 0 && nj < NY && nk >= 0 && nk < NZ;
+                    const long long m = n + (dx - 1) + (long long)NX * ((dy - 1) + (long long)NY * (dz - 1));
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) nb[dz][dy][dx][c] = ok ? x[3 * m + c] : T(0);
+                }
+    }
 #pragma unroll
     for (int oz = 0; oz < 2; ++oz) {
 #pragma unroll
@@ -87,9 +107,13 @@ __device__ __forceinline__ void stencil_node(long long n, const T* __restrict__ 
                         for (int bx = 0; bx < 2; ++bx) {
                             const int bl = local_index(bx, by, bz);
                             const int ni = ex + bx;
-                            const long long m = ni + (long long)NX * ((ey + by) + (long long)NY * (ez + bz));
                             T u0 = 0, u1 = 0, u2 = 0;
-                            if (ni != 0) {
+                            if constexpr (REGS) {
+                                u0 = nb[oz + bz][oy + by][ox + bx][0];
+                                u1 = nb[oz + bz][oy + by][ox + bx][1];
+                                u2 = nb[oz + bz][oy + by][ox + bx][2];
+                            } else if (ni != 0) {
+                                const long long m = ni + (long long)NX * ((ey + by) + (long long)NY * (ez + bz));
                                 u0 = x[3 * m + 0];
                                 u1 = x[3 * m + 1];
                                 u2 = x[3 * m + 2];

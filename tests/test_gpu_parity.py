@@ -320,14 +320,16 @@ def test_full_size_apply_sampled(gf, dims):
     u = synth.random_vector(g.n_dof, 1)
     y = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
     g.apply_K(dev(u), y)
-    yh = host(y).reshape(-1, 3)
+    ys = torch.zeros_like(y)
+    g.apply_K_split(dev(u), ys)                 # the Krylov operator of the mixed form
     rng = np.random.default_rng(0)
     nodes = rng.choice(g.n_nodes, 300, replace=False)
     nodes[:3] = [0, g.n_nodes - 1, nx]          # corners / fixed face
     E = O.young_modulus(rho, 1e-6, 3.0)
     ref = _apply_at_nodes(nx, ny, nz, E, u, nodes)
     scale = np.abs(ref).max()
-    assert np.abs(yh[nodes] - ref).max() <= 1e-10 * scale
+    for out in (y, ys):
+        assert np.abs(host(out).reshape(-1, 3)[nodes] - ref).max() <= 1e-10 * scale
 
 
 def _apply_at_nodes(nx, ny, nz, E, u, nodes):
@@ -399,8 +401,11 @@ def test_graph_replay_bit_identical(gf, monkeypatch):
 
 
 # ------------------------------------------------------------- split-integer K*u --
+# tc = "1": element products on the tensor cores (default); "0": the CUDA-core kernel
+@pytest.mark.parametrize("tc", ["1", "0"])
 @pytest.mark.parametrize("nx,ny,nz,L", GRIDS)
-def test_apply_K_split_parity(gf, nx, ny, nz, L):
+def test_apply_K_split_parity(gf, nx, ny, nz, L, tc, monkeypatch):
+    monkeypatch.setenv("GF_SPLIT_TC", tc)
     g, m, rho = make(gf, nx, ny, nz, L, seed=nx + 1, rho_min=1e-6)
     E = O.young_modulus(rho, 1e-6, 3.0)
     K0 = O.element_stiffness()
