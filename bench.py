@@ -196,7 +196,8 @@ def profiled_traffic(profile, source, start, end):
 
 # kernel text spans hashed for the traffic figures
 FP64_KU_SPAN = ("stencil.cuh", "template <typename T, typename ET, int MODE, typename BT", "// First smoothing sweep")
-SPLIT_KU_SPAN = ("split.cuh", "// 2^k as a float", "}  // namespace gf")
+FP32_ST_SPAN = FP64_KU_SPAN                # one templated per-node body serves both
+SPLIT_KU_SPAN = ("split_tc.cuh", "template <bool DD>", "}  // namespace gf")
 
 
 def emit(d):
@@ -298,49 +299,58 @@ def run_b300(args):
         ms, accepted, launches = float(mx[0]), int(sm[1]), int(sm[2])
     value = accepted / (ms / 1000.0)
 
-    # ---- dominant kernel: FP64 matrix-free K*u, timed alone on the grid's stream
+    # ---- kernels timed alone on the grid's stream (CUDA events, after warm-up)
     g.set_density(rhos[0], P_SIMP)
     g.set_floor(RHO0)
     x = torch.randn(g.n_dof, dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
-    for _ in range(3):
-        g.apply_K(x, y)
-    torch.cuda.synchronize()
-    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 20
-    k0.record()
-    for _ in range(reps):
-        g.apply_K(x, y)
-    k1.record()
-    torch.cuda.synchronize()
-    t_k = k0.elapsed_time(k1) / reps / 1000.0
-    k0.record()
-    for _ in range(reps):
-        g.apply_K_split(x, y)
-    k1.record()
-    torch.cuda.synchronize()
-    t_s = k0.elapsed_time(k1) / reps / 1000.0
-    flops = 1152.0 * g.n_elem                  # 2*24*24 per element
+    xf, yf = x.float(), torch.empty(g.n_dof, dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record()
+        for _ in range(reps):
+            fn()
+        k1.record()
+        torch.cuda.synchronize()
+        return k0.elapsed_time(k1) / reps / 1000.0
+
+    t_32 = timed(lambda: g.apply_K_f32(xf, yf))
+    t_s = timed(lambda: g.apply_K_split(x, y))
+    t_k = timed(lambda: g.apply_K(x, y))
+    flops = 1152.0 * g.n_elem                  # 2*24*24 per element and application
     sm_max = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2032.0)
     fp64_peak = 148 * 2 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
     fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12
-    gdofs = g.n_dof / t_k / 1e9
-    gdofs_split = g.n_dof / t_s / 1e9
+    fp32_note = "derived: 148 SMs x 128 FP32 FMA/clk x 2 flop x sm_max_mhz"
+    # dominant kernel family (launch-list share): the FP32 node stencil of the V-cycle,
+    # here in its K*u form on the fine level (same per-node code as the sweeps)
+    stencil = {"bound": "alu", "achieved": flops / t_32 / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+               "frac": flops / t_32 / 1e12 / fp32_peak,
+               "traffic": profiled_traffic("node_stencil_fp32_96x48x48.md", *FP32_ST_SPAN),
+               "kernel": "node_stencil_kernel<float> (FP32 V-cycle stencil, fine level, 1152 flop/element)",
+               "peak_source": fp32_note, "gdofs": g.n_dof / t_32 / 1e9, "ms_per_launch": t_32 * 1e3}
+    # the Krylov operator: exact fp16 digit products on the tensor cores (5 slices),
+    # issue-bound on the CUDA-core epilogue; reported as FP64-class flops per second
+    split = {"bound": "alu", "achieved": flops / t_s / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+             "frac": flops / t_s / 1e12 / fp64_peak,
+             "traffic": profiled_traffic("apply_K_split_96x48x48.md", *SPLIT_KU_SPAN),
+             "kernel": "apply_split_tc_kernel (split-integer FP64-class K*u; frac > 1: above the FP64 pipe)",
+             "peak_source": f"derived: {FP64_PEAK_NOTE}", "gdofs": g.n_dof / t_s / 1e9, "ms_per_launch": t_s * 1e3}
     native = {"bound": "alu", "achieved": flops / t_k / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
               "frac": flops / t_k / 1e12 / fp64_peak,
               "traffic": profiled_traffic("apply_K_fp64_96x48x48.md", *FP64_KU_SPAN),
               "kernel": "node_stencil_kernel<double> (native FP64 K*u; the guard's operator)",
-              "peak_source": f"derived: {FP64_PEAK_NOTE}", "gdofs": gdofs, "ms_per_launch": t_k * 1e3}
-    # split-integer K*u: 4 digit slices x 1152 exact FP32 flops per element on the FMA pipe
-    split_flops = 4 * 1152.0 * g.n_elem
-    split = {"bound": "alu", "achieved": split_flops / t_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-             "frac": split_flops / t_s / 1e12 / fp32_peak,
-             "traffic": profiled_traffic("apply_K_split_96x48x48.md", *SPLIT_KU_SPAN),
-             "kernel": "apply_split_kernel (split-integer FP64-class K*u, FP32 digit products)",
-             "peak_source": "derived: 148 SMs x 128 FP32 FMA/clk x 2 flop x sm_max_mhz", "gdofs": gdofs_split,
-             "ms_per_launch": t_s * 1e3}
-    roofline = dict(split if prec == gf.GF_MIXED else native)
-    roofline["other_kernel"] = native if prec == gf.GF_MIXED else split
+              "peak_source": f"derived: {FP64_PEAK_NOTE}", "gdofs": g.n_dof / t_k / 1e9, "ms_per_launch": t_k * 1e3}
+    if prec == gf.GF_MIXED:
+        roofline = dict(stencil)
+        roofline["other_kernels"] = {"krylov_operator": split, "guard_operator": native}
+    else:
+        roofline = dict(native)
+    gdofs, gdofs_split = native["gdofs"], split["gdofs"]
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -385,7 +395,8 @@ def run_b300(args):
                          "l2": "inputs larger than L2 (Krylov bases V,Z = 342 MB per state solve)"},
               "accepted": accepted, "fgmres_iters_per_step": iters / args.steps, "records": records,
               "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
-              "cpu_baseline": cpu, "apply_K_fp64_gdofs": gdofs, "apply_K_split_gdofs": gdofs_split})
+              "cpu_baseline": cpu, "apply_K_fp64_gdofs": gdofs, "apply_K_split_gdofs": gdofs_split,
+              "apply_K_fp32_gdofs": stencil["gdofs"]})
     if dist is not None:
         dist.destroy_process_group()
 
