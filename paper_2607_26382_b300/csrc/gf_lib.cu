@@ -134,7 +134,8 @@ struct gf_grid {
     float2* Vd = nullptr;             // double-float copy of the basis (outer == 2)
     float2* pdd = nullptr;            // per-block partial pairs of the double-float passes
     unsigned int* ddticket = nullptr; // arrival counter of their last-block finish
-    int md_alloc = 0, nbd = 0;        // nbd: blocks of the double-float passes
+    int md_alloc = 0, nbd = 0;        // nbd: largest grid of the double-float passes (partials rows)
+    int nbd_k[3][3] = {};             // grid per pass (dots, update+dots, update+norm) and NV (8, 16, 32)
     gf::KState* st = nullptr;
     gf::KState* gst = nullptr;   // guard scratch
     double* hist = nullptr;
@@ -163,7 +164,7 @@ struct gf_grid {
     gf::MParam Msplit;
     float2* Edf = nullptr;            // s_split * E_e (fine level) as float pairs
     gf::TcBFrag Btc;                  // M as per-lane fp16 MMA B fragments (tensor-core split)
-    bool split_tc = true;             // element products on the tensor cores (GF_SPLIT_TC=0: CUDA cores)
+    bool split_tc = true;             // element products on the tensor cores (see gf_create_grid)
     int gkey_outer = -1;
     // optimisation-loop scratch (allocated on first use)
     double *oc_rho = nullptr, *oc_dc = nullptr, *oc_dcx = nullptr, *oc_dvx = nullptr, *oc_ones = nullptr;
@@ -251,9 +252,7 @@ int stencil(gf_grid* g, int l, const T* x, const T* b, T* out, const ET* E, cons
             T omega, const int* halt)
 {
     const Level& L = g->lv[l];
-    if constexpr (sizeof(T) == sizeof(float)) {
-        if (g->tpb[1] <= 0) return tiled_f32<MODE, float, float>(g, l, x, b, out, E, omega, halt);
-    }
+    if constexpr (sizeof(T) == sizeof(float)) return tiled_f32<MODE, float, float>(g, l, x, b, out, E, omega, halt);
     const int tpb = g->tpb[sizeof(T) == sizeof(double) ? 0 : 1];
     LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_kernel<T, ET, MODE>), x, b, out, E, L.dims(), K0, omega,
            halt);
@@ -316,9 +315,11 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
         const T* b = (l == 0) ? b0 : B::b(lev);
         T* x = B::x(lev);
         T* t = B::t(lev);
-        const int tpb = g->tpb[sizeof(T) == sizeof(double) ? 0 : 1];
-        LAUNCH(g, nblk(lev.nodes, tpb), tpb, (gf::first_sweep_kernel<T, T, T>), b, x, B::E(lev), lev.dims(), k0<T>(g),
-               omega, halt);
+        const int tpb = g->tpb[sizeof(T) == sizeof(double) ? 0 : 1] > 0 ? g->tpb[sizeof(T) == sizeof(double) ? 0 : 1]
+                                                                          : 256;
+        if (l == 0)   // levels >= 1 got their first sweep with the restriction
+            LAUNCH(g, nblk(lev.nodes, tpb), tpb, (gf::first_sweep_kernel<T, T, T>), b, x, B::E(lev), lev.dims(),
+                   k0<T>(g), omega, halt);
         for (int s = 1; s < nu1; ++s) {
             RET((stencil<T, T, gf::ST_SWEEP>(g, l, x, b, t, B::E(lev), k0<T>(g), omega, halt)));
             std::swap(x, t);
@@ -326,7 +327,11 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
         cur[l] = x;
         RET((stencil<T, T, gf::ST_RESID>(g, l, x, b, B::r(lev), B::E(lev), k0<T>(g), omega, halt)));
         Level& c = g->lv[l + 1];
-        LAUNCH(g, nblk(c.nodes), 256, gf::restrict_kernel<T>, B::r(lev), B::b(c), c.dims(), halt);
+        if (l + 1 < L - 1)
+            LAUNCH(g, nblk(c.nodes), 256, gf::restrict_first_sweep_kernel<T>, (const T*)B::r(lev), B::b(c), B::x(c),
+                   (const T*)B::E(c), c.dims(), k0<T>(g), omega, halt);
+        else
+            LAUNCH(g, nblk(c.nodes), 256, gf::restrict_kernel<T>, B::r(lev), B::b(c), c.dims(), halt);
     }
     {
         Level& c = g->lv[L - 1];
@@ -381,9 +386,7 @@ int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2,
                 std::swap(x, t);
             }
             RET((tiled_f32<gf::ST_RESID, double, float>(g, l, x, v, lev.r32, lev.E32, omega, halt)));
-        } else {
-            LAUNCH(g, nblk(lev.nodes), 256, (gf::first_sweep_kernel<float, float, float>), (const float*)lev.b32, x,
-                   (const float*)lev.E32, lev.dims(), g->K0f, omega, halt);
+        } else {   // first sweep done together with the restriction into this level
             for (int s = 1; s < nu1; ++s) {
                 RET((tiled_f32<gf::ST_SWEEP, float, float>(g, l, x, lev.b32, t, lev.E32, omega, halt)));
                 std::swap(x, t);
@@ -392,7 +395,11 @@ int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2,
         }
         cur[l] = x;
         Level& c = g->lv[l + 1];
-        LAUNCH(g, nblk(c.nodes), 256, gf::restrict_kernel<float>, (const float*)lev.r32, c.b32, c.dims(), halt);
+        if (l + 1 < Ldown)
+            LAUNCH(g, nblk(c.nodes), 256, gf::restrict_first_sweep_kernel<float>, (const float*)lev.r32, c.b32, c.x32,
+                   (const float*)c.E32, c.dims(), g->K0f, omega, halt);
+        else
+            LAUNCH(g, nblk(c.nodes), 256, gf::restrict_kernel<float>, (const float*)lev.r32, c.b32, c.dims(), halt);
     }
     if (lc > 0) {
         gf::VcArgs va{};
@@ -545,7 +552,26 @@ int ensure_krylov(gf_grid* g, int m, int kmax, int outer)
         g->md_alloc = 0;
         RET(allocT(&g->Vd, (size_t)(m + 1) * g->ndof));
         if (!g->pdd) {
-            g->nbd = (int)std::min<long long>(4LL * g->sms, (g->ndof + gf::DD_TILE - 1) / gf::DD_TILE);
+            // each pass's grid is the blocks resident at once on this GPU (one round),
+            // capped by the number of row tiles
+            const long long tiles = (g->ndof + gf::DD_TILE - 1) / gf::DD_TILE;
+            const void* kern[3][3] = {
+                {(const void*)gf::ddgs_dots_kernel<8>, (const void*)gf::ddgs_dots_kernel<16>,
+                 (const void*)gf::ddgs_dots_kernel<32>},
+                {(const void*)gf::ddgs_update_dots_kernel<8>, (const void*)gf::ddgs_update_dots_kernel<16>,
+                 (const void*)gf::ddgs_update_dots_kernel<32>},
+                {(const void*)gf::ddgs_update_norm_kernel<8>, (const void*)gf::ddgs_update_norm_kernel<16>,
+                 (const void*)gf::ddgs_update_norm_kernel<32>}};
+            g->nbd = 1;
+            for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q) {
+                    int nb = 0;
+                    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern[p][q], gf::DD_THREADS, 0) != cudaSuccess ||
+                        nb <= 0)
+                        nb = 2;
+                    g->nbd_k[p][q] = (int)std::max<long long>(1, std::min<long long>((long long)nb * g->sms, tiles));
+                    g->nbd = std::max(g->nbd, g->nbd_k[p][q]);
+                }
             RET(allocT(&g->pdd, (size_t)g->nbd * (gf::KRY_MMAX + 1)));
             RET(allocT(&g->ddticket, 1));
             CK(cudaMemset(g->ddticket, 0, sizeof(unsigned int)));
@@ -611,13 +637,13 @@ int cgs2_step(gf_grid* g, int j, double* w, int outer)
     const int nv = j + 1;
     if (outer == 2) {   // double-float passes on the FP32 pipe; w arrives as wd
         float2* wd = g->Vd + (long long)(j + 1) * ld;
-        const int nb = g->nbd;
-        LAUNCH(g, nb, gf::DD_THREADS, gf::ddgs_dots_kernel<NV>, (const float2*)g->Vd, ld, nv, (const float2*)wd, n,
-               g->pdd, g->st, g->ddticket);
-        LAUNCH(g, nb, gf::DD_THREADS, gf::ddgs_update_dots_kernel<NV>, (const float2*)g->Vd, ld, nv, wd, n, g->pdd,
-               g->st, g->ddticket);
-        LAUNCH(g, nb, gf::DD_THREADS, gf::ddgs_update_norm_kernel<NV>, (const float2*)g->Vd, ld, nv, wd, n, g->pdd,
-               g->st, g->ddticket);
+        const int q = NV == 8 ? 0 : (NV == 16 ? 1 : 2);
+        LAUNCH(g, g->nbd_k[0][q], gf::DD_THREADS, gf::ddgs_dots_kernel<NV>, (const float2*)g->Vd, ld, nv,
+               (const float2*)wd, n, g->pdd, g->st, g->ddticket);
+        LAUNCH(g, g->nbd_k[1][q], gf::DD_THREADS, gf::ddgs_update_dots_kernel<NV>, (const float2*)g->Vd, ld, nv, wd,
+               n, g->pdd, g->st, g->ddticket);
+        LAUNCH(g, g->nbd_k[2][q], gf::DD_THREADS, gf::ddgs_update_norm_kernel<NV>, (const float2*)g->Vd, ld, nv, wd,
+               n, g->pdd, g->st, g->ddticket);
         LAUNCH(g, 1, 32, gf::arnoldi_tail_kernel, g->st, g->hist, j, NV, g->host_status_dev, 1e-14);
         return GF_OK;
     }
@@ -970,8 +996,13 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     }
     if (g->has_split) {
         build_tc_bfrag(g->Msplit, &g->Btc);
+        // tensor cores when the grid gives every SM a CTA (fewer CTAs leave the kernel
+        // latency-bound and the CUDA-core one is faster: 35 vs 13 us at 16x8x8, 8 CTAs);
+        // GF_SPLIT_TC=1 / 0 forces either
+        const dim3 tg = split_tc_grid(g);
+        const long long ctas = (long long)tg.x * tg.y * tg.z;
         const char* e = getenv("GF_SPLIT_TC");
-        g->split_tc = !(e && e[0] == '0');
+        g->split_tc = e ? (e[0] != '0') : (ctas >= g->sms);
         if (g->split_tc &&
             (cudaFuncSetAttribute(gf::apply_split_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sizeof(gf::TcSmem)) != cudaSuccess ||

@@ -167,28 +167,45 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n
 }
 
 // ---------------------------------------------------------------- Arnoldi tail --
-// One thread: finish column j of H, apply the stored rotations, form the new
-// one, update g, record the history, decide whether to stop.
+// One warp: stage column j of H and the stored rotations in shared memory (one round
+// of parallel loads), then one thread applies the rotations, forms the new one,
+// updates g, records the history and decides whether to stop. The serial recurrence
+// reads only shared memory: from global memory, each step's loads would wait behind
+// the previous step's store to the same struct.
 __global__ void arnoldi_tail_kernel(KState* __restrict__ st, double* __restrict__ hist, int j,
                                     int ww0_slot, volatile int* host_status, double breakdown_rtol)
 {
     GF_PDL_ENTER();
-    if (threadIdx.x != 0 || st->status != KS_RUN) return;
-    const int ldh = KRY_MMAX + 1;
-    double* col = st->H + (long long)j * ldh;
-    const double wnorm0 = sqrt(st->h1[ww0_slot]);
-    for (int i = 0; i <= j; ++i) col[i] = st->h1[i] + st->h2[i];
-    const double hnext = sqrt(st->ww);
-    col[j + 1] = hnext;
-    for (int i = 0; i < j; ++i) {
-        const double a = col[i], b = col[i + 1];
-        col[i] = st->cs[i] * a + st->sn[i] * b;
-        col[i + 1] = -st->sn[i] * a + st->cs[i] * b;
+    __shared__ double col[KRY_MMAX + 1], cs[KRY_MMAX], sn[KRY_MMAX];
+    if (st->status != KS_RUN) return;   // uniform over the warp
+    const int lane = threadIdx.x;
+    for (int i = lane; i <= j; i += 32) col[i] = st->h1[i] + st->h2[i];
+    for (int i = lane; i < j; i += 32) {
+        cs[i] = st->cs[i];
+        sn[i] = st->sn[i];
     }
+    const double hnext = sqrt(st->ww);
+    __syncwarp();
+    if (lane == 0) {
+        col[j + 1] = hnext;
+        for (int i = 0; i < j; ++i) {
+            const double a = col[i], b = col[i + 1];
+            col[i] = cs[i] * a + sn[i] * b;
+            col[i + 1] = -sn[i] * a + cs[i] * b;
+        }
+    }
+    __syncwarp();
+    const int ldh = KRY_MMAX + 1;
+    double* Hc = st->H + (long long)j * ldh;
+    for (int i = lane; i < j; i += 32) Hc[i] = col[i];   // rows 0..j-1 are final
+    if (lane != 0) return;
+    const double wnorm0 = sqrt(st->h1[ww0_slot]);
     const double a = col[j], b = col[j + 1];
     const double rho = hypot(a, b);
     st->j = j;
     if (rho == 0.0) {            // degenerate column: breakdown, drop the step
+        Hc[j] = a;
+        Hc[j + 1] = b;
         st->status = KS_STOP;
         st->flag = 2;
         st->J = j;
@@ -198,8 +215,8 @@ __global__ void arnoldi_tail_kernel(KState* __restrict__ st, double* __restrict_
     const double c = a / rho, s = b / rho;
     st->cs[j] = c;
     st->sn[j] = s;
-    col[j] = rho;
-    col[j + 1] = 0.0;
+    Hc[j] = rho;
+    Hc[j + 1] = 0.0;
     const double gj = st->g[j];
     st->g[j + 1] = -s * gj;
     st->g[j] = c * gj;

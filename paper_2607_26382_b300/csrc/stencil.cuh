@@ -184,9 +184,9 @@ node_stencil_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __res
     stencil_node<T, ET, MODE, BT, OT>(n, x, b, out, E, d, K0, omega);
 }
 
-// First smoothing sweep from x = 0: out = omega * D_n^{-1} b. BT is b's type.
-template <typename T, typename ET, typename BT>
-__device__ __forceinline__ void first_sweep_node(long long n, const BT* __restrict__ b, T* __restrict__ out,
+// First smoothing sweep from x = 0: out = omega * D_n^{-1} b, b_n = (r0, r1, r2).
+template <typename T, typename ET>
+__device__ __forceinline__ void first_sweep_vals(long long n, T r0, T r1, T r2, T* __restrict__ out,
                                                  const ET* __restrict__ E, GridDims d, const K0Param<T>& K0,
                                                  T omega)
 {
@@ -217,7 +217,6 @@ __device__ __forceinline__ void first_sweep_node(long long n, const BT* __restri
                 d02 = fma(Ee, K0.k[(3 * a + 0) * 24 + 3 * a + 2], d02);
                 d12 = fma(Ee, K0.k[(3 * a + 1) * 24 + 3 * a + 2], d12);
             }
-    const T r0 = (T)b[3 * n + 0], r1 = (T)b[3 * n + 1], r2 = (T)b[3 * n + 2];
     const T c00 = d11 * d22 - d12 * d12;
     const T c01 = d02 * d12 - d01 * d22;
     const T c02 = d01 * d12 - d02 * d11;
@@ -229,6 +228,15 @@ __device__ __forceinline__ void first_sweep_node(long long n, const BT* __restri
     out[3 * n + 0] = s * (c00 * r0 + c01 * r1 + c02 * r2);
     out[3 * n + 1] = s * (c01 * r0 + c11 * r1 + c12 * r2);
     out[3 * n + 2] = s * (c02 * r0 + c12 * r1 + c22 * r2);
+}
+
+// The same with b read from memory. BT is b's type.
+template <typename T, typename ET, typename BT>
+__device__ __forceinline__ void first_sweep_node(long long n, const BT* __restrict__ b, T* __restrict__ out,
+                                                 const ET* __restrict__ E, GridDims d, const K0Param<T>& K0,
+                                                 T omega)
+{
+    first_sweep_vals<T, ET>(n, (T)b[3 * n + 0], (T)b[3 * n + 1], (T)b[3 * n + 2], out, E, d, K0, omega);
 }
 
 template <typename T, typename ET, typename BT>
@@ -249,19 +257,14 @@ first_sweep_kernel(const BT* __restrict__ b, T* __restrict__ out, const ET* __re
 // gathers the fine nodes (2I+di, 2J+dj, 2K+dk), di,dj,dk in {-1,0,1}, with weight
 // prod (1 if offset 0 else 1/2). `cd` are the coarse element counts.
 template <typename T>
-__device__ __forceinline__ void restrict_node(long long n, const T* __restrict__ r, T* __restrict__ bc, GridDims cd)
+__device__ __forceinline__ void restrict_vals(long long n, const T* __restrict__ r, GridDims cd, T& s0, T& s1, T& s2)
 {
     const int CX = cd.nx + 1, CY = cd.ny + 1;
     int I, J, K;
     node_coords(n, CX, CY, I, J, K);
-    if (I == 0) {
-        bc[3 * n + 0] = T(0);
-        bc[3 * n + 1] = T(0);
-        bc[3 * n + 2] = T(0);
-        return;
-    }
+    s0 = s1 = s2 = T(0);
+    if (I == 0) return;
     const int FX = 2 * cd.nx + 1, FY = 2 * cd.ny + 1, FZ = 2 * cd.nz + 1;
-    T s0 = 0, s1 = 0, s2 = 0;
 #pragma unroll
     for (int dk = -1; dk <= 1; ++dk) {
         const int fk = 2 * K + dk;
@@ -282,6 +285,13 @@ __device__ __forceinline__ void restrict_node(long long n, const T* __restrict__
             }
         }
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void restrict_node(long long n, const T* __restrict__ r, T* __restrict__ bc, GridDims cd)
+{
+    T s0, s1, s2;
+    restrict_vals<T>(n, r, cd, s0, s1, s2);
     bc[3 * n + 0] = s0;
     bc[3 * n + 1] = s1;
     bc[3 * n + 2] = s2;
@@ -297,6 +307,29 @@ restrict_kernel(const T* __restrict__ r, T* __restrict__ bc, GridDims cd, const 
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
     restrict_node<T>(n, r, bc, cd);
+}
+
+// Restriction into a coarse level fused with that level's first sweep from x = 0:
+// the sweep needs b only at its own node, so the thread that forms b_n sweeps it.
+// Stores b (for the level's later sweeps and residual) and x. Same arithmetic as
+// restrict_kernel followed by first_sweep_kernel.
+template <typename T>
+__global__ void __launch_bounds__(256)
+restrict_first_sweep_kernel(const T* __restrict__ r, T* __restrict__ bc, T* __restrict__ xc,
+                            const T* __restrict__ Ec, GridDims cd, const __grid_constant__ K0Param<T> K0, T omega,
+                            const int* __restrict__ halt)
+{
+    GF_PDL_ENTER();
+    if (halt != nullptr && *halt != 0) return;
+    const long long nn = (long long)(cd.nx + 1) * (cd.ny + 1) * (cd.nz + 1);
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    T s0, s1, s2;
+    restrict_vals<T>(n, r, cd, s0, s1, s2);
+    bc[3 * n + 0] = s0;
+    bc[3 * n + 1] = s1;
+    bc[3 * n + 2] = s2;
+    first_sweep_vals<T, T>(n, s0, s1, s2, xc, Ec, cd, K0, omega);
 }
 
 // x += P xc (trilinear interpolation, fine nodes on the fixed face untouched).

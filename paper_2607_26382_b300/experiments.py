@@ -9,7 +9,8 @@ batch102: 102 frozen states of uneven size (nx in {32,48,64,80}, ny = nz = nx/2,
   {1e-5, 1e-4, 1e-3}, tau = 1e-6, kmax = 200, 4-level GMG. Three forms, all with the
   FP64 recomputed-residual guard as the only acceptance test:
     plain   - FP64 V-cycle and Krylov, one state at a time, full ladder from rho0;
-    batched - mixed V-cycle, split-integer Krylov operator, all states in one batch,
+    batched - mixed V-cycle, split-integer Krylov operator and double-float CGS2
+              (outer = 2), all states in one batch,
               Eq. (trigger) picks the first floor;
     learned - as batched, with an MLP (trained on full-ladder outcomes of 48x24x24
               states) picking the first floor: its most probable floor, and (c0.9)
@@ -97,7 +98,7 @@ def train_mlp(n_train, seed=7):
     import synth
     dims = (48, 24, 24)
     rh = synth.selector_training_states(n_train, dims, seed)
-    pol = _policy(solve_prec=L.GF_MIXED, solve_outer=1)
+    pol = _policy(solve_prec=L.GF_MIXED, solve_outer=2)
     t0 = time.perf_counter()
     X, y, _ = S.ladder_dataset(dims, rh, 4, pol, chunk=100)
     t_data = time.perf_counter() - t0
@@ -114,13 +115,13 @@ def batch102(args):
     out = {"workload": "batch102", "n_dof_total": int(sum(3 * (a + 1) * (b + 1) * (c + 1) for a, b, c in dims))}
     recs, dt = run_plain(dims, rhos)
     out["plain_fp64_single_state_full_ladder"] = _summary(recs, dt)
-    recs, dt, launches = run_batched(dims, rhos, _policy(solve_prec=L.GF_MIXED, solve_outer=1))
+    recs, dt, launches = run_batched(dims, rhos, _policy(solve_prec=L.GF_MIXED, solve_outer=2))
     out["batched_mixed_rule"] = _summary(recs, dt)
     out["batched_mixed_rule"]["kernel_launches_total"] = launches
     net, info = train_mlp(args.train)
     out["selector_training"] = info
     for name, conf in (("batched_mixed_learned", 0.0), ("batched_mixed_learned_c0.9", 0.9)):
-        pol = _policy(solve_prec=L.GF_MIXED, solve_outer=1, selector=L.GF_SEL_MLP, mlp_confidence=conf)
+        pol = _policy(solve_prec=L.GF_MIXED, solve_outer=2, selector=L.GF_SEL_MLP, mlp_confidence=conf)
         pol.mlp = net.handle
         recs, dt, _ = run_batched(dims, rhos, pol)
         out[name] = _summary(recs, dt)
@@ -138,12 +139,12 @@ def oc_loop(args):
     nx, ny, nz = 96, 48, 48
     out = {"workload": f"guarded SIMP-OC {nx}x{ny}x{nz}, {args.iters} iterations, vol 0.3, r_min 1.5, p 3"}
     modes = [("plain_fp64_full", _policy(selector=L.GF_SEL_FULL, solve_prec=L.GF_FP64, solve_outer=0)),
-             ("mixed_rule", _policy(solve_prec=L.GF_MIXED, solve_outer=1))]
+             ("mixed_rule", _policy(solve_prec=L.GF_MIXED, solve_outer=2))]
     net = None
     if args.train > 0:
         net, info = train_mlp(args.train)
         out["selector_training"] = info
-        pol = _policy(solve_prec=L.GF_MIXED, solve_outer=1, selector=L.GF_SEL_MLP)
+        pol = _policy(solve_prec=L.GF_MIXED, solve_outer=2, selector=L.GF_SEL_MLP)
         pol.mlp = net.handle
         modes.append(("mixed_learned", pol))
     for name, pol in modes:
