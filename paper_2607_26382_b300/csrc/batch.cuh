@@ -24,7 +24,6 @@ struct BatchTables {
 
 __global__ void batch_mark_kernel(KState** st, const int* __restrict__ active, int B)
 {
-    GF_PDL_ENTER();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B || active[i]) return;
     st[i]->skip = 1;
@@ -35,7 +34,6 @@ __global__ void batch_mark_kernel(KState** st, const int* __restrict__ active, i
 // so its (already applied) update is not repeated.
 __global__ void batch_retire_kernel(KState** st, int B)
 {
-    GF_PDL_ENTER();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B) return;
     if (!st[i]->skip && st[i]->status != KS_RUN) st[i]->skip = 1;
@@ -45,7 +43,6 @@ __global__ void batch_retire_kernel(KState** st, int B)
 __global__ void batch_gather_kernel(KState* const* st, double* const* hist, int B, int a, int b,
                                     double* __restrict__ out)
 {
-    GF_PDL_ENTER();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B) return;
     const int k = st[i]->k;
@@ -57,7 +54,6 @@ __global__ void batch_gather_kernel(KState* const* st, double* const* hist, int 
 
 __global__ void batch_abort_kernel(KState** st, const int* __restrict__ abort_flags, int B)
 {
-    GF_PDL_ENTER();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B || !abort_flags[i]) return;
     st[i]->status = KS_STOP;
@@ -68,7 +64,6 @@ __global__ void batch_abort_kernel(KState** st, const int* __restrict__ abort_fl
 // Gauss-Jordan pivot k on every state's matrix at once (blockIdx.y = state).
 __global__ void batch_gj_prepare_kernel(BatchTables t, const int* __restrict__ active, int k)
 {
-    GF_PDL_ENTER();
     const int i = blockIdx.y;
     if (!active[i]) return;
     const int n = t.n[i];
@@ -83,7 +78,6 @@ __global__ void batch_gj_prepare_kernel(BatchTables t, const int* __restrict__ a
 
 __global__ void batch_gj_eliminate_kernel(BatchTables t, const int* __restrict__ active, int k)
 {
-    GF_PDL_ENTER();
     const int i = blockIdx.y;
     if (!active[i]) return;
     const int n = t.n[i];

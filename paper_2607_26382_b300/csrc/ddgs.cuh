@@ -124,7 +124,6 @@ __global__ void __launch_bounds__(DD_THREADS)
 ddgs_dots_kernel(const float2* __restrict__ Vd, long long ld, int nv, const float2* __restrict__ wd,
                  long long n, float2* __restrict__ partial, KState* __restrict__ st, unsigned int* ticket)
 {
-    GF_PDL_ENTER();
     if (st->status != KS_RUN) return;
     constexpr int QW = NV / DD_WARPS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -235,7 +234,6 @@ ddgs_update_dots_kernel(const float2* __restrict__ Vd, long long ld, int nv, flo
                         long long n, float2* __restrict__ partial, KState* __restrict__ st,
                         unsigned int* ticket)
 {
-    GF_PDL_ENTER();
     if (st->status != KS_RUN) return;
     constexpr int QW = NV / DD_WARPS;
     __shared__ float2 hs[NV];
@@ -275,7 +273,6 @@ ddgs_update_norm_kernel(const float2* __restrict__ Vd, long long ld, int nv, flo
                         long long n, float2* __restrict__ partial, KState* __restrict__ st,
                         unsigned int* ticket)
 {
-    GF_PDL_ENTER();
     if (st->status != KS_RUN) return;
     constexpr int QW = NV / DD_WARPS;
     __shared__ float2 hs[NV];
@@ -312,7 +309,6 @@ ddgs_update_norm_kernel(const float2* __restrict__ Vd, long long ld, int nv, flo
 __global__ void ddgs_scale_kernel(float2* __restrict__ wd, double* __restrict__ v, long long n,
                                   const KState* __restrict__ st)
 {
-    GF_PDL_ENTER();
     if (st->status != KS_RUN) return;
     const float2 s = dd_from_double(st->inv);
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
@@ -333,7 +329,6 @@ __global__ void ddgs_scale_kernel(float2* __restrict__ wd, double* __restrict__ 
 __global__ void ddgs_scale_fp64_kernel(double* __restrict__ v, float2* __restrict__ vd, long long n,
                                        const KState* __restrict__ st)
 {
-    GF_PDL_ENTER();
     if (st->status != KS_RUN) return;
     const double s = st->inv;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;

@@ -153,7 +153,6 @@ struct gf_grid {
     int gkey_prec = -1, gkey_nu1 = -1, gkey_nu2 = -1;
     double gkey_omega = -1.0;
     bool use_graphs = true;
-    bool use_pdl = false;             // programmatic dependent launch between kernels (GF_PDL=1)
     int tpb[2] = {256, 256};          // node-stencil block size: [0] FP64, [1] FP32 (0 = smem-tiled kernel)
     bool skip_coarse_inverse = false; // batched set-up builds the coarsest inverse itself
     double dstat[3] = {0.0, 0.0, 0.0}; // fraction of rho_hat == 0, mean, std (at set_density)
@@ -176,21 +175,7 @@ namespace {
 template <typename... KArgs, typename... Args>
 int launch_smem(gf_grid* g, dim3 grid, dim3 block, size_t smem, void (*kern)(KArgs...), Args... args)
 {
-    if (g->use_pdl) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = grid;
-        cfg.blockDim = block;
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = g->cur_stream;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        CK(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
-    } else {
-        kern<<<grid, block, smem, g->cur_stream>>>(args...);
-    }
+    kern<<<grid, block, smem, g->cur_stream>>>(static_cast<KArgs>(args)...);
     g->stats.kernel_launches++;
     CK(cudaGetLastError());
     return GF_OK;
@@ -599,7 +584,6 @@ int ensure_krylov(gf_grid* g, int m, int kmax, int outer)
 
 __global__ void init_state_kernel(gf::KState* st, int kmax, int m, double tol)
 {
-    GF_PDL_ENTER();
     st->k = 0;
     st->kmax = kmax;
     st->m = m;
@@ -1063,8 +1047,6 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     {
         const char* e = getenv("GF_GRAPHS");
         g->use_graphs = !(e && e[0] == '0');
-        const char* p = getenv("GF_PDL");
-        g->use_pdl = (p && p[0] == '1');
     }
     *out = g;
     return GF_OK;
@@ -1582,7 +1564,6 @@ int noalloc_scratch(double** out)
 // eta = sqrt(sum a) / sqrt(sum b) over the per-block partials, in fixed order.
 __global__ void noalloc_eta_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ eta)
 {
-    GF_PDL_ENTER();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double a = 0.0, b = 0.0;
     for (int i = 0; i < nblocks; ++i) {

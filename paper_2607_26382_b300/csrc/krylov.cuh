@@ -65,7 +65,6 @@ __global__ void __launch_bounds__(RED_THREADS)
 cgs_dots_kernel(const double* __restrict__ V, long long ld, int nv, const double* __restrict__ w,
                 long long n, double* __restrict__ partial, const KState* __restrict__ st)
 {
-    GF_PDL_ENTER();
     if (st->status != KS_RUN) return;
     double acc[NV + 1];
 #pragma unroll
@@ -89,7 +88,6 @@ __global__ void __launch_bounds__(RED_THREADS)
 cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
                        long long n, double* __restrict__ partial, const KState* __restrict__ st)
 {
-    GF_PDL_ENTER();
     if (st->status != KS_RUN) return;
     __shared__ double h[NV];
     double acc[NV];
@@ -121,7 +119,6 @@ __global__ void __launch_bounds__(RED_THREADS)
 cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
                        long long n, double* __restrict__ partial, const KState* __restrict__ st)
 {
-    GF_PDL_ENTER();
     if (st->status != KS_RUN) return;
     __shared__ double h[NV];
     if (threadIdx.x < NV) h[threadIdx.x] = threadIdx.x < nv ? st->h2[threadIdx.x] : 0.0;
@@ -147,7 +144,6 @@ cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, doubl
 __global__ void reduce_partials_kernel(const double* __restrict__ partial, int nblocks, int stride, int cnt,
                                        KState* __restrict__ st, int dst, int check_status)
 {
-    GF_PDL_ENTER();
     if (check_status && st->status != KS_RUN) return;
     const int lane = threadIdx.x & 31;
     const int i = threadIdx.x >> 5;
@@ -175,7 +171,6 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n
 __global__ void arnoldi_tail_kernel(KState* __restrict__ st, double* __restrict__ hist, int j,
                                     int ww0_slot, volatile int* host_status, double breakdown_rtol)
 {
-    GF_PDL_ENTER();
     __shared__ double col[KRY_MMAX + 1], cs[KRY_MMAX], sn[KRY_MMAX];
     if (st->status != KS_RUN) return;   // uniform over the warp
     const int lane = threadIdx.x;
@@ -243,7 +238,6 @@ __global__ void arnoldi_tail_kernel(KState* __restrict__ st, double* __restrict_
 __global__ void cycle_start_tail_kernel(KState* __restrict__ st, double* __restrict__ hist,
                                         volatile int* host_status, int first)
 {
-    GF_PDL_ENTER();
     if (threadIdx.x != 0 || st->skip) return;
     const double beta = sqrt(st->h1[0]);          // ||M f - K x||
     if (first) st->fnorm = sqrt(st->h1[1]);       // ||M f||
@@ -269,7 +263,6 @@ __global__ void cycle_start_tail_kernel(KState* __restrict__ st, double* __restr
 // Upper-triangular back substitution H[0:J,0:J] y = g[0:J].
 __global__ void backsolve_kernel(KState* __restrict__ st)
 {
-    GF_PDL_ENTER();
     if (threadIdx.x != 0 || st->skip) return;
     const int ldh = KRY_MMAX + 1;
     const int J = st->J;
@@ -285,7 +278,6 @@ __global__ void __launch_bounds__(256)
 update_x_kernel(double* __restrict__ x, const double* __restrict__ Z, long long ld, long long n,
                 const KState* __restrict__ st)
 {
-    GF_PDL_ENTER();
     __shared__ double ys[KRY_MMAX];
     if (st->skip) return;
     const int J = st->J;
@@ -302,7 +294,6 @@ update_x_kernel(double* __restrict__ x, const double* __restrict__ Z, long long 
 // v *= st->inv (skipped once stopped)
 __global__ void scale_kernel(double* __restrict__ v, long long n, const KState* __restrict__ st, int check_status)
 {
-    GF_PDL_ENTER();
     if (check_status && st->status != KS_RUN) return;
     const double s = st->inv;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
@@ -317,7 +308,6 @@ residual_norms_kernel(const double* __restrict__ f, const double* y, double* r,
                       long long n, int NX, double* __restrict__ partial, int y_is_zero,
                       const int* __restrict__ halt)
 {
-    GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
     double acc[2] = {0.0, 0.0};
     long long r0, r1;
@@ -338,7 +328,6 @@ template <typename TI, typename TO>
 __global__ void masked_convert_kernel(const TI* a, TO* b, long long n, int NX,
                                       const int* __restrict__ halt)
 {
-    GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
          q += (long long)gridDim.x * blockDim.x)
@@ -351,7 +340,6 @@ __global__ void __launch_bounds__(256)
 dense_gemv_kernel(const double* __restrict__ A, const TB* __restrict__ b, TX* __restrict__ x, int n,
                   const int* __restrict__ halt)
 {
-    GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= n) return;
@@ -368,7 +356,6 @@ dense_gemv_kernel(const double* __restrict__ A, const TB* __restrict__ b, TX* __
 __global__ void gj_prepare_kernel(double* __restrict__ A, double* __restrict__ col, double* __restrict__ row,
                                   int n, int k)
 {
-    GF_PDL_ENTER();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const double piv = 1.0 / A[(long long)k * n + k];
@@ -380,7 +367,6 @@ __global__ void gj_prepare_kernel(double* __restrict__ A, double* __restrict__ c
 __global__ void gj_eliminate_kernel(double* __restrict__ A, const double* __restrict__ col,
                                     const double* __restrict__ row, int n, int k)
 {
-    GF_PDL_ENTER();
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)n * n) return;
     const int i = (int)(t / n), c = (int)(t % n);

@@ -49,7 +49,6 @@ __global__ void __launch_bounds__(128)
 mlp_forward_kernel(const float* __restrict__ theta, const float* __restrict__ X, int n, MLPNorm nm,
                    float* __restrict__ logits, int* __restrict__ cls)
 {
-    GF_PDL_ENTER();
     __shared__ float th[MLP_P];
     for (int p = threadIdx.x; p < MLP_P; p += blockDim.x) th[p] = theta[p];
     __syncthreads();
@@ -72,7 +71,6 @@ __global__ void __launch_bounds__(128)
 mlp_grad_kernel(const float* __restrict__ theta, const float* __restrict__ X, const int* __restrict__ y,
                 const int* __restrict__ idx, int nb, MLPNorm nm, float* __restrict__ gps, float* __restrict__ lps)
 {
-    GF_PDL_ENTER();
     __shared__ float th[MLP_P];
     for (int p = threadIdx.x; p < MLP_P; p += blockDim.x) th[p] = theta[p];
     __syncthreads();
@@ -133,7 +131,6 @@ mlp_grad_kernel(const float* __restrict__ theta, const float* __restrict__ X, co
 __global__ void mlp_reduce_kernel(const float* __restrict__ gps, const float* __restrict__ lps, int nb,
                                   float* __restrict__ grad, float* __restrict__ loss)
 {
-    GF_PDL_ENTER();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p < MLP_P) {
         float s = 0.f;
@@ -149,7 +146,6 @@ __global__ void mlp_reduce_kernel(const float* __restrict__ gps, const float* __
 __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
                             const float* __restrict__ g, float lr, float b1, float b2, float eps, float bc1, float bc2)
 {
-    GF_PDL_ENTER();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= MLP_P) return;
     const float gp = g[p];

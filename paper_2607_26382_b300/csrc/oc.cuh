@@ -33,7 +33,6 @@ template <bool ADJOINT>
 __global__ void __launch_bounds__(256)
 hat_filter_kernel(const double* __restrict__ x, double* __restrict__ out, GridDims d, double r, int R)
 {
-    GF_PDL_ENTER();
     const long long ne = (long long)d.nx * d.ny * d.nz;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
@@ -74,7 +73,6 @@ __device__ __forceinline__ double oc_candidate(double x, double dc, double dv, d
 
 __global__ void oc_init_kernel(OCState* st)
 {
-    GF_PDL_ENTER();
     st->l1 = 0.0;
     st->l2 = 1e9;
     st->done = 0;
@@ -87,7 +85,6 @@ __global__ void __launch_bounds__(256)
 oc_partial_kernel(const double* __restrict__ x, const double* __restrict__ dc, const double* __restrict__ dv,
                   long long n, double move, double tol, OCState* __restrict__ st, double* __restrict__ partial)
 {
-    GF_PDL_ENTER();
     __shared__ double red[8];
     if (st->done) return;
     const double l1 = st->l1, l2 = st->l2;
@@ -114,7 +111,6 @@ oc_partial_kernel(const double* __restrict__ x, const double* __restrict__ dc, c
 __global__ void oc_bisect_kernel(const double* __restrict__ partial, int nblocks, long long n, double volfrac,
                                  double tol, int max_iters, OCState* __restrict__ st)
 {
-    GF_PDL_ENTER();
     if (threadIdx.x != 0 || st->done) return;
     double s = 0.0;
     for (int b = 0; b < nblocks; ++b) s += partial[b];
@@ -131,7 +127,6 @@ __global__ void oc_apply_kernel(const double* __restrict__ x, const double* __re
                                 const double* __restrict__ dv, double* __restrict__ xnew, long long n, double move,
                                 const OCState* __restrict__ st)
 {
-    GF_PDL_ENTER();
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     xnew[e] = oc_candidate(x[e], dc[e], dv[e], st->lmid, move);
@@ -142,7 +137,6 @@ __global__ void __launch_bounds__(256)
 dot_partial_kernel(const double* __restrict__ a, const double* __restrict__ b, long long n,
                    double* __restrict__ partial)
 {
-    GF_PDL_ENTER();
     __shared__ double red[8];
     const long long chunk = (n + gridDim.x - 1) / gridDim.x;
     const long long r0 = (long long)blockIdx.x * chunk;

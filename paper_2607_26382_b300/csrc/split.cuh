@@ -37,7 +37,6 @@ struct MParam {
 // E as a float pair (hi + lo = s * E_e to ~48 bits).
 __global__ void edf_kernel(const double* __restrict__ E, double s, float2* __restrict__ out, long long n)
 {
-    GF_PDL_ENTER();
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const double v = s * E[e];
@@ -65,7 +64,6 @@ apply_split_kernel(const double* __restrict__ u, double* __restrict__ y, float2*
                    const float2* __restrict__ Edf, GridDims d, const __grid_constant__ MParam M,
                    const int* __restrict__ halt)
 {
-    GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
     __shared__ float dig[SPLIT_K][SPHN * 3];
     __shared__ int wmax[4];

@@ -94,7 +94,6 @@ apply_split_tc_kernel(const double* __restrict__ u, double* __restrict__ y, floa
                       const float2* __restrict__ Edf, GridDims d, const __grid_constant__ TcBFrag B,
                       const int* __restrict__ halt)
 {
-    GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
     extern __shared__ __align__(16) unsigned char tc_smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(tc_smem_raw);

@@ -14,13 +14,6 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
-// Programmatic dependent launch (opt-in, GF_PDL=1): every kernel first waits for the
-// kernel before it in the stream to complete (a no-op when launched without the
-// attribute), then lets the next kernel begin launching. Measured on B300: -3% per
-// FGMRES step at 16x8x8, +3% at 96x48x48 (waiting blocks take SM slots), so it is
-// off by default.
-#define GF_PDL_ENTER() asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory")
-
 namespace gf {
 
 template <typename T>
@@ -176,7 +169,6 @@ node_stencil_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __res
                     const ET* __restrict__ E, GridDims d, const __grid_constant__ K0Param<T> K0,
                     T omega, const int* __restrict__ halt)
 {
-    GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
     const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -245,7 +237,6 @@ first_sweep_kernel(const BT* __restrict__ b, T* __restrict__ out, const ET* __re
                    GridDims d, const __grid_constant__ K0Param<T> K0, T omega,
                    const int* __restrict__ halt)
 {
-    GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
     const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -301,7 +292,6 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 restrict_kernel(const T* __restrict__ r, T* __restrict__ bc, GridDims cd, const int* __restrict__ halt)
 {
-    GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
     const long long nn = (long long)(cd.nx + 1) * (cd.ny + 1) * (cd.nz + 1);
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -319,7 +309,6 @@ restrict_first_sweep_kernel(const T* __restrict__ r, T* __restrict__ bc, T* __re
                             const T* __restrict__ Ec, GridDims cd, const __grid_constant__ K0Param<T> K0, T omega,
                             const int* __restrict__ halt)
 {
-    GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
     const long long nn = (long long)(cd.nx + 1) * (cd.ny + 1) * (cd.nz + 1);
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -369,7 +358,6 @@ template <typename T, typename CT>
 __global__ void __launch_bounds__(256)
 prolong_add_kernel(T* __restrict__ x, const CT* __restrict__ xc, GridDims fd, const int* __restrict__ halt)
 {
-    GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
     const long long nn = (long long)(fd.nx + 1) * (fd.ny + 1) * (fd.nz + 1);
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -384,7 +372,6 @@ prolong_add_kernel(T* __restrict__ x, const CT* __restrict__ xc, GridDims fd, co
 __global__ void modulus_fp64_kernel(const double* __restrict__ rho, double* __restrict__ E, long long n,
                                     double rho_min, double p, int p_int, double scale)
 {
-    GF_PDL_ENTER();
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const double r = rho[e];
@@ -402,7 +389,6 @@ __global__ void modulus_fp64_kernel(const double* __restrict__ rho, double* __re
 __global__ void modulus_fp32_kernel(const __nv_bfloat16* __restrict__ rho, float* __restrict__ E, long long n,
                                     float rho_min, float p, int p_int, float scale)
 {
-    GF_PDL_ENTER();
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const float r = __bfloat162float(rho[e]);
@@ -420,7 +406,6 @@ __global__ void modulus_fp32_kernel(const __nv_bfloat16* __restrict__ rho, float
 template <typename ET>
 __global__ void coarsen_kernel(const ET* __restrict__ Ef, ET* __restrict__ Ec, GridDims cd)
 {
-    GF_PDL_ENTER();
     const long long nc = (long long)cd.nx * cd.ny * cd.nz;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nc) return;
@@ -443,7 +428,6 @@ __global__ void coarsen_kernel(const ET* __restrict__ Ef, ET* __restrict__ Ec, G
 __global__ void density_check_kernel(const double* __restrict__ rho, __nv_bfloat16* __restrict__ r16,
                                      double* __restrict__ r64, long long n, int* __restrict__ bad)
 {
-    GF_PDL_ENTER();
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const double r = rho[e];
@@ -456,7 +440,6 @@ __global__ void density_check_kernel(const double* __restrict__ rho, __nv_bfloat
 __global__ void __launch_bounds__(256)
 density_stats_kernel(const double* __restrict__ rho, long long n, double* __restrict__ partial)
 {
-    GF_PDL_ENTER();
     __shared__ double red[3][8];
     const long long chunk = (n + gridDim.x - 1) / gridDim.x;
     const long long r0 = (long long)blockIdx.x * chunk;
@@ -490,7 +473,6 @@ density_stats_kernel(const double* __restrict__ rho, long long n, double* __rest
 __global__ void coarse_assemble_kernel(const double* __restrict__ E, double* __restrict__ A, GridDims d,
                                        const __grid_constant__ K0Param<double> K0)
 {
-    GF_PDL_ENTER();
     const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
     const long long ndof = 3LL * NX * NY * NZ;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -520,7 +502,6 @@ __global__ void coarse_assemble_kernel(const double* __restrict__ E, double* __r
 // Fixed DOFs (nodes with i == 0): zero row and column, unit diagonal.
 __global__ void coarse_fix_kernel(double* __restrict__ A, GridDims d)
 {
-    GF_PDL_ENTER();
     const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
     const long long ndof = 3LL * NX * NY * NZ;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -533,7 +514,6 @@ __global__ void coarse_fix_kernel(double* __restrict__ A, GridDims d)
 // Cantilever load and free mask.
 __global__ void cantilever_load_kernel(double* __restrict__ f, GridDims d)
 {
-    GF_PDL_ENTER();
     const long long ndof = 3LL * (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ndof) return;
@@ -543,7 +523,6 @@ __global__ void cantilever_load_kernel(double* __restrict__ f, GridDims d)
 
 __global__ void free_mask_kernel(uint8_t* __restrict__ mask, GridDims d)
 {
-    GF_PDL_ENTER();
     const long long ndof = 3LL * (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ndof) return;
@@ -556,7 +535,6 @@ sensitivity_kernel(const double* __restrict__ u, const double* __restrict__ rho,
                    GridDims d, const __grid_constant__ K0Param<double> K0, double coef, double pm1,
                    int pm1_int)
 {
-    GF_PDL_ENTER();
     const long long ne = (long long)d.nx * d.ny * d.nz;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
@@ -611,7 +589,6 @@ tiled_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
                          const float* __restrict__ E, GridDims d, const __grid_constant__ K0Param<float> K0,
                          float omega, const int* __restrict__ halt)
 {
-    GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
     __shared__ float sx[THX * THY * THZ * 3];
     __shared__ float sE[TEX * TEY * TEZ];
@@ -743,7 +720,6 @@ node_stencil27_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __r
                       const T* __restrict__ E, GridDims d, const __grid_constant__ K0Param<T> K0, T omega,
                       const int* __restrict__ halt)
 {
-    GF_PDL_ENTER();
     if (halt != nullptr && *halt != 0) return;
     const int NX = d.nx + 1, NY = d.ny + 1;
     const int nn = NX * NY * (d.nz + 1);

@@ -29,7 +29,6 @@ struct VcArgs {
 __global__ void __cluster_dims__(VC_CLUSTER, 1, 1) __launch_bounds__(VC_THREADS)
 coarse_vcycle_kernel(const __grid_constant__ VcArgs a, const __grid_constant__ K0Param<float> K0)
 {
-    GF_PDL_ENTER();
     namespace cg = cooperative_groups;
     if (a.halt != nullptr && *a.halt != 0) return;   // uniform over the cluster
     cg::cluster_group cl = cg::this_cluster();
