@@ -16,9 +16,8 @@ namespace gf {
 struct BatchTables {
     KState** st;       // per state
     double** hist;
-    double** A;        // coarsest dense matrices
-    double** col;
-    double** row;
+    double** A;        // coarsest dense matrices (the inverses, in the end)
+    double** W;        // their second Gauss-Jordan buffers
     int* n;            // coarsest sizes
 };
 
@@ -61,37 +60,20 @@ __global__ void batch_abort_kernel(KState** st, const int* __restrict__ abort_fl
     st[i]->skip = 1;
 }
 
-// Gauss-Jordan pivot k on every state's matrix at once (blockIdx.y = state).
-__global__ void batch_gj_prepare_kernel(BatchTables t, const int* __restrict__ active, int k)
+// Gauss-Jordan step s (pivots 2s, 2s+1) on every state's matrix at once
+// (blockIdx.z = state, tiles of GJ_T). State i runs ceil(n_i/2) steps; it starts in
+// W_i when that count is odd, so its last step always writes A_i.
+__global__ void __launch_bounds__(GJ_T * GJ_R)
+batch_gj_step_kernel(BatchTables t, const int* __restrict__ active, int s)
 {
-    const int i = blockIdx.y;
+    const int i = blockIdx.z;
     if (!active[i]) return;
-    const int n = t.n[i];
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n || c >= n) return;
-    double* A = t.A[i];
-    const double piv = 1.0 / A[(long long)k * n + k];
-    t.col[i][c] = A[(long long)c * n + k];
-    const double v = (c == k) ? 1.0 : A[(long long)k * n + c];
-    t.row[i][c] = v * piv;
-}
-
-__global__ void batch_gj_eliminate_kernel(BatchTables t, const int* __restrict__ active, int k)
-{
-    const int i = blockIdx.y;
-    if (!active[i]) return;
-    const int n = t.n[i];
-    if (k >= n) return;
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (long long)n * n) return;
-    double* A = t.A[i];
-    const int r = (int)(q / n), c = (int)(q % n);
-    if (r == k) {
-        A[q] = t.row[i][c];
-    } else {
-        const double base = (c == k) ? 0.0 : A[q];
-        A[q] = base - t.col[i][r] * t.row[i][c];
-    }
+    const int n = t.n[i], k = 2 * s;
+    const int p0 = blockIdx.y * GJ_T, q0 = blockIdx.x * GJ_T;
+    if (k >= n || p0 >= n || q0 >= n) return;   // uniform over the block
+    const int steps = (n + 1) / 2;
+    const bool from_w = ((steps & 1) ^ (s & 1)) != 0;
+    gj_tile(from_w ? t.W[i] : t.A[i], from_w ? t.A[i] : t.W[i], n, k, p0, q0);
 }
 
 }  // namespace gf
@@ -372,18 +354,18 @@ int batch_set_floor(gf_batch* b, const std::vector<int>& active, const std::vect
         if (rc != GF_OK) return rc;
         Level& c = g->lv[g->L - 1];
         const long long n = g->nc;
-        LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, (const double*)c.E64, g->Ainv, c.dims(), g->K0d);
-        LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, g->Ainv, c.dims());
+        double* start = (((n + 1) / 2) & 1) ? g->Agj : g->Ainv;   // see batch_gj_step_kernel
+        LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, (const double*)c.E64, start, c.dims(), g->K0d);
+        LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, start, c.dims());
     }
     CK(cudaMemcpyAsync(b->d_active, active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, b->stream));
     int nmax = 0;
     for (int i = 0; i < B; ++i)
         if (active[i]) nmax = std::max(nmax, b->g[i]->nc);
-    for (int k = 0; k < nmax; ++k) {
-        const dim3 gp(nblk(nmax), B), ge(nblk((long long)nmax * nmax), B);
-        gf::batch_gj_prepare_kernel<<<gp, 256, 0, b->stream>>>(b->tab, b->d_active, k);
-        gf::batch_gj_eliminate_kernel<<<ge, 256, 0, b->stream>>>(b->tab, b->d_active, k);
-        b->launches += 2;
+    const unsigned tiles = (unsigned)((nmax + gf::GJ_T - 1) / gf::GJ_T);
+    for (int s = 0; 2 * s < nmax; ++s) {
+        gf::batch_gj_step_kernel<<<dim3(tiles, tiles, B), dim3(gf::GJ_T, gf::GJ_R), 0, b->stream>>>(b->tab, b->d_active, s);
+        b->launches += 1;
         CK(cudaGetLastError());
     }
     return GF_OK;
@@ -476,25 +458,22 @@ int gf_create_batch(int n_states, const int* dims, int levels, double h, double 
             return fail(set_err(GF_ERR_CUDA, "event"));
     const size_t P = sizeof(void*) * n_states;
     if (cudaMalloc(&b->tab.st, P) != cudaSuccess || cudaMalloc(&b->tab.hist, P) != cudaSuccess ||
-        cudaMalloc(&b->tab.A, P) != cudaSuccess || cudaMalloc(&b->tab.col, P) != cudaSuccess ||
-        cudaMalloc(&b->tab.row, P) != cudaSuccess || cudaMalloc(&b->tab.n, sizeof(int) * n_states) != cudaSuccess ||
+        cudaMalloc(&b->tab.A, P) != cudaSuccess || cudaMalloc(&b->tab.W, P) != cudaSuccess || cudaMalloc(&b->tab.n, sizeof(int) * n_states) != cudaSuccess ||
         cudaMalloc(&b->d_active, sizeof(int) * n_states) != cudaSuccess ||
         cudaMalloc(&b->d_abort, sizeof(int) * n_states) != cudaSuccess)
         return fail(set_err(GF_ERR_OOM, "batch tables"));
     if (cudaHostAlloc((void**)&b->gather_host, sizeof(double) * 4 * n_states, cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer((void**)&b->gather_dev, b->gather_host, 0) != cudaSuccess)
         return fail(set_err(GF_ERR_CUDA, "mapped gather"));
-    std::vector<double*> A(n_states), col(n_states), row(n_states);
+    std::vector<double*> A(n_states), W(n_states);
     std::vector<int> n(n_states);
     for (int i = 0; i < n_states; ++i) {
         A[i] = b->g[i]->Ainv;
-        col[i] = b->g[i]->gjcol;
-        row[i] = b->g[i]->gjrow;
+        W[i] = b->g[i]->Agj;
         n[i] = b->g[i]->nc;
     }
     if (cudaMemcpy(b->tab.A, A.data(), P, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->tab.col, col.data(), P, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->tab.row, row.data(), P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->tab.W, W.data(), P, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->tab.n, n.data(), sizeof(int) * n_states, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(set_err(GF_ERR_CUDA, "tables"));
     *out = b;
@@ -516,7 +495,7 @@ int gf_destroy_batch(gf_batch* b)
         if (b->ev[q]) cudaEventDestroy(b->ev[q]);
     if (b->evFork) cudaEventDestroy(b->evFork);
     if (b->capS) cudaStreamDestroy(b->capS);
-    cudaFree(b->tab.st); cudaFree(b->tab.hist); cudaFree(b->tab.A); cudaFree(b->tab.col); cudaFree(b->tab.row);
+    cudaFree(b->tab.st); cudaFree(b->tab.hist); cudaFree(b->tab.A); cudaFree(b->tab.W);
     cudaFree(b->tab.n); cudaFree(b->d_active); cudaFree(b->d_abort);
     if (b->gather_host) cudaFreeHost(b->gather_host);
     delete b;

@@ -126,7 +126,7 @@ struct gf_grid {
     double rho_min = 0.0;
     double* Ainv = nullptr;
     int nc = 0;
-    double *gjcol = nullptr, *gjrow = nullptr;
+    double* Agj = nullptr;            // second buffer of the double-buffered Gauss-Jordan
     int* dflag = nullptr;
     // Krylov workspace
     int m_alloc = 0;
@@ -510,11 +510,16 @@ int build_coarse_inverse(gf_grid* g)
     Level& c = g->lv[g->L - 1];
     const long long n = g->nc;
     gf::K0Param<double> K = g->K0d;   // the level's E64 already carries h
-    LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, c.E64, g->Ainv, c.dims(), K);
-    LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, g->Ainv, c.dims());
-    for (int k = 0; k < n; ++k) {
-        LAUNCH(g, nblk(n), 256, gf::gj_prepare_kernel, g->Ainv, g->gjcol, g->gjrow, (int)n, k);
-        LAUNCH(g, nblk(n * n), 256, gf::gj_eliminate_kernel, g->Ainv, g->gjcol, g->gjrow, (int)n, k);
+    // ceil(n/2) double-buffered steps; start in the buffer that makes the last one land in Ainv
+    const long long steps = (n + 1) / 2;
+    double* src = (steps & 1) ? g->Agj : g->Ainv;
+    LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, c.E64, src, c.dims(), K);
+    LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, src, c.dims());
+    const unsigned tiles = (unsigned)((n + gf::GJ_T - 1) / gf::GJ_T);
+    for (int k = 0; k < n; k += 2) {
+        double* dst = (src == g->Ainv) ? g->Agj : g->Ainv;
+        LAUNCH(g, dim3(tiles, tiles), dim3(gf::GJ_T, gf::GJ_R), gf::gj_step_kernel, (const double*)src, dst, (int)n, k);
+        src = dst;
     }
     return GF_OK;
 }
@@ -1028,8 +1033,8 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     }
     int r = GF_OK;
     g->nbr = (int)std::min<long long>(2LL * g->sms, std::max<long long>(1, (g->ndof + 1023) / 1024));
-    if ((r = allocT(&g->Ainv, (size_t)g->nc * g->nc)) || (r = allocT(&g->gjcol, g->nc)) ||
-        (r = allocT(&g->gjrow, g->nc)) || (r = allocT(&g->dflag, 4)) || (r = allocT(&g->rho64, g->nel)) ||
+    if ((r = allocT(&g->Ainv, (size_t)g->nc * g->nc)) || (r = allocT(&g->Agj, (size_t)g->nc * g->nc)) ||
+        (r = allocT(&g->dflag, 4)) || (r = allocT(&g->rho64, g->nel)) ||
         (r = allocT(&g->rho16, g->nel)) || (r = allocT(&g->work, g->ndof)) ||
         (r = allocT(&g->partial, (size_t)g->nbr * 40)) || (r = allocT(&g->st, 1)) || (r = allocT(&g->gst, 1)) ||
         (r = allocT(&g->Edf, g->nel)))
@@ -1062,7 +1067,7 @@ int gf_destroy_grid(gf_grid* g)
         cudaFree(L.b64); cudaFree(L.x64); cudaFree(L.t64); cudaFree(L.r64);
         cudaFree(L.b32); cudaFree(L.x32); cudaFree(L.t32); cudaFree(L.r32);
     }
-    cudaFree(g->Ainv); cudaFree(g->gjcol); cudaFree(g->gjrow); cudaFree(g->dflag);
+    cudaFree(g->Ainv); cudaFree(g->Agj); cudaFree(g->dflag);
     cudaFree(g->rho64); cudaFree(g->rho16); cudaFree(g->work); cudaFree(g->partial);
     cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Vd); cudaFree(g->pdd); cudaFree(g->ddticket); cudaFree(g->Z); cudaFree(g->hist);
     cudaFree(g->xsave);

@@ -351,31 +351,69 @@ dense_gemv_kernel(const double* __restrict__ A, const TB* __restrict__ b, TX* __
     if (lane == 0) x[warp] = (TX)s;
 }
 
-// Gauss-Jordan inversion of an SPD matrix without pivoting, one pivot per pair of
-// launches: (1) save column k and the scaled pivot row, (2) eliminate.
-__global__ void gj_prepare_kernel(double* __restrict__ A, double* __restrict__ col, double* __restrict__ row,
-                                  int n, int k)
+// Gauss-Jordan inversion of an SPD matrix without pivoting, two pivots per launch on a
+// double-buffered matrix. The step on pivot k maps A to A' with
+//   row k:   A'_kq = A_kq / A_kk            (1 / A_kk at q = k)
+//   others:  A'_pq = A_pq - A_pk A'_kq      (-A_pk / A_kk at q = k)
+// and the step on pivot k+1 applies the same formula to A'. A block owns a 32 x 32
+// tile of the output: it forms the two reciprocals, the tile's row-k and row-(k+1)
+// factors and its column-k and column-(k+1) values once in shared memory, then every
+// entry costs one FMA per pivot. Same arithmetic as one launch per pivot.
+constexpr int GJ_T = 32, GJ_R = 8;   // tile edge; thread rows (each thread GJ_T / GJ_R rows)
+
+__device__ __forceinline__ void gj_tile(const double* __restrict__ A, double* __restrict__ D, int n, int k,
+                                        int p0, int q0)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const double piv = 1.0 / A[(long long)k * n + k];
-    col[t] = A[(long long)t * n + k];
-    const double v = (t == k) ? 1.0 : A[(long long)k * n + t];
-    row[t] = v * piv;
+    __shared__ double rq0[GJ_T], rq1[GJ_T], cp0[GJ_T], cp1[GJ_T], sc[3];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int k1 = k + 1;
+    const bool two = k1 < n;
+    if (tx == 0 && ty == 0) {
+        const double piv0 = 1.0 / A[(long long)k * n + k];
+        sc[0] = piv0;
+        if (two) {
+            const double r0k1 = A[(long long)k * n + k1] * piv0;                  // A'_{k,k1}
+            sc[2] = r0k1;
+            sc[1] = 1.0 / (A[(long long)k1 * n + k1] - A[(long long)k1 * n + k] * r0k1);   // 1 / A'_{k1,k1}
+        }
+    }
+    __syncthreads();
+    if (ty == 0) {   // row factors of the tile's columns
+        const int q = q0 + tx;
+        if (q < n) {
+            const double r0 = ((q == k) ? 1.0 : A[(long long)k * n + q]) * sc[0];
+            rq0[tx] = r0;
+            if (two) {
+                const double a1 = ((q == k) ? 0.0 : A[(long long)k1 * n + q]) - A[(long long)k1 * n + k] * r0;
+                rq1[tx] = ((q == k1) ? 1.0 : a1) * sc[1];
+            }
+        }
+    } else if (ty == 1) {   // column values of the tile's rows
+        const int p = p0 + tx;
+        if (p < n) {
+            const double c0 = A[(long long)p * n + k];
+            cp0[tx] = c0;
+            if (two) cp1[tx] = (p == k) ? sc[2] : (A[(long long)p * n + k1] - c0 * sc[2]);   // A'_{p,k1}
+        }
+    }
+    __syncthreads();
+    const int q = q0 + tx;
+    if (q >= n) return;
+    for (int r = ty; r < GJ_T; r += GJ_R) {
+        const int p = p0 + r;
+        if (p >= n) break;
+        const double a1 = (p == k) ? rq0[tx] : (((q == k) ? 0.0 : A[(long long)p * n + q]) - cp0[r] * rq0[tx]);
+        double out = a1;
+        if (two) out = (p == k1) ? rq1[tx] : (((q == k1) ? 0.0 : a1) - cp1[r] * rq1[tx]);
+        D[(long long)p * n + q] = out;
+    }
 }
 
-__global__ void gj_eliminate_kernel(double* __restrict__ A, const double* __restrict__ col,
-                                    const double* __restrict__ row, int n, int k)
+// Pivots k and k+1 (k alone when k+1 == n) from Ain into Aout. Grid: tiles of GJ_T.
+__global__ void __launch_bounds__(GJ_T * GJ_R)
+gj_step_kernel(const double* __restrict__ Ain, double* __restrict__ Aout, int n, int k)
 {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)n * n) return;
-    const int i = (int)(t / n), c = (int)(t % n);
-    if (i == k) {
-        A[t] = row[c];
-    } else {
-        const double base = (c == k) ? 0.0 : A[t];
-        A[t] = base - col[i] * row[c];
-    }
+    gj_tile(Ain, Aout, n, k, blockIdx.y * GJ_T, blockIdx.x * GJ_T);
 }
 
 }  // namespace gf
