@@ -16,6 +16,8 @@ Every function is in FP64 and names the passage it follows (paper arXiv
 * frozen operator K = sum_e E_e K_e on free DOFs ........ Eq. (frozen_operator)
 * relative residual eta = ||f - K u|| / ||f|| ........... Eq. (relative_residual)
 * GMG V-cycle, 2:1 trilinear transfer ................... Table "solver-config"
+* Chebyshev smoother (alternative to node-block Jacobi) . Table "solver-config" (names a
+  Chebyshev smoother; degree and interval are readings, see below)
 * right-preconditioned FGMRES, residual history ......... Sec. 3.2 "Which residual
   counts", Table "residual-semantics", Sec. 3.5 "Why a flexible Krylov method"
 * probe features r50/r100 and trigger rule .............. Sec. 3.4, Eq. (trigger)
@@ -31,6 +33,10 @@ high-contrast fields: omega*lambda_max(D^-1 K) exceeds 2); coarsest level is a
 dense Cholesky solve on free DOFs; FGMRES uses classical Gram-Schmidt with one
 re-orthogonalisation; a cycle-start true residual overwrites the history entry
 at that iteration count; happy breakdown when h_{j+1,j} <= 1e-14 * ||K z_j||.
+Chebyshev smoothing (optional): Chebyshev semi-iteration of degree nu1 / nu2 on
+D_b^{-1} K over [lambda_max / 30, 1.1 lambda_max], D_b the same 3x3 node blocks;
+lambda_max of each level from 15 power iterations started from the all-ones vector
+on free DOFs.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, invariants, brute force on tiny grids, paper values). None is
@@ -333,6 +339,7 @@ class Level:
     blockdiag: np.ndarray               # (n_nodes, 3, 3) node blocks of K
     P: sp.csr_matrix | None = None      # prolongation from the next coarser level
     chol: tuple | None = None           # coarsest only: Cholesky factor of free block
+    lam: float = 0.0                    # Chebyshev smoothing: lambda_max(D_b^{-1} K) estimate
 
 
 @dataclass
@@ -341,12 +348,14 @@ class Hierarchy:
     nu1: int = 2
     nu2: int = 2
     omega: float = 0.6
+    smoother: str = "jacobi"            # or "chebyshev"
 
 
 def build_hierarchy(mesh: Mesh, E_fine: np.ndarray, n_levels: int, nu: float = 0.3,
-                    nu1: int = 2, nu2: int = 2, omega: float = 0.6) -> Hierarchy:
-    """Level l has (nx, ny, nz)/2^l elements of edge h*2^l, modulus = child mean, K0(h_l)."""
-    H = Hierarchy(nu1=nu1, nu2=nu2, omega=omega)
+                    nu1: int = 2, nu2: int = 2, omega: float = 0.6, smoother: str = "jacobi") -> Hierarchy:
+    """Level l has (nx, ny, nz)/2^l elements of edge h*2^l, modulus = child mean, K0(h_l).
+    With smoother="chebyshev" every smoothing level also gets lam (its lambda_max)."""
+    H = Hierarchy(nu1=nu1, nu2=nu2, omega=omega, smoother=smoother)
     m, E = mesh, np.asarray(E_fine, dtype=np.float64)
     for l in range(n_levels):
         K0 = element_stiffness(m.h, 1.0, nu)
@@ -362,6 +371,9 @@ def build_hierarchy(mesh: Mesh, E_fine: np.ndarray, n_levels: int, nu: float = 0
     last = H.levels[-1]
     Kc = assemble_dense_free(last.mesh, last.E, last.K0)
     last.chol = sla.cho_factor(Kc, lower=True)
+    if smoother == "chebyshev":
+        for lev in H.levels[:-1]:
+            lev.lam = level_lambda_max(lev)
     return H
 
 
@@ -378,14 +390,72 @@ def jacobi_sweep(level: Level, x: np.ndarray, b: np.ndarray, omega: float) -> np
     return x + omega * dx
 
 
+def block_jacobi_apply(level: Level, r: np.ndarray) -> np.ndarray:
+    """D_b^{-1} r with the 3x3 node blocks."""
+    return np.linalg.solve(level.blockdiag, r.reshape(-1, 3, 1)).reshape(-1)
+
+
+def power_lambda_max(apply_M, v0: np.ndarray, iters: int = 15) -> float:
+    """Power method for the largest eigenvalue of M: v_0 = v0/||v0||, then at each step
+    w = M v, estimate ||w|| (with ||v|| = 1), v = w/||w||; the last estimate is returned."""
+    v = v0 / np.linalg.norm(v0)
+    lam = 0.0
+    for _ in range(iters):
+        w = apply_M(v)
+        lam = float(np.linalg.norm(w))
+        v = w / lam
+    return lam
+
+
+def level_lambda_max(level: Level, iters: int = 15) -> float:
+    """lambda_max(D_b^{-1} K) of a level by 15 power iterations from ones on free DOFs."""
+    v0 = np.where(level.mesh.fixed, 0.0, 1.0)
+    return power_lambda_max(lambda v: block_jacobi_apply(level, apply_K(level.mesh, level.E, level.K0, v)),
+                            v0, iters)
+
+
+def chebyshev_coefficients(lam: float, degree: int):
+    """Chebyshev semi-iteration on [lam/30, 1.1 lam] (theta = centre, delta = half
+    width, sigma = theta/delta): step 0 d = (1/theta) D^{-1} r; step k >= 1
+    rho_k = 1/(2 sigma - rho_{k-1}), d = rho_k rho_{k-1} d + (2 rho_k/delta) D^{-1} r,
+    rho_0 = 1/sigma. Returns [(c1, c2)] with d <- c1 d + c2 D^{-1} r."""
+    a, b = lam / 30.0, 1.1 * lam
+    theta, delta = 0.5 * (b + a), 0.5 * (b - a)
+    sigma = theta / delta
+    coefs = [(0.0, 1.0 / theta)]
+    rho = 1.0 / sigma
+    for _ in range(1, degree):
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        coefs.append((rho_new * rho, 2.0 * rho_new / delta))
+        rho = rho_new
+    return coefs
+
+
+def chebyshev_smooth(level: Level, x: np.ndarray, b: np.ndarray, lam: float, degree: int) -> np.ndarray:
+    """degree steps of Chebyshev semi-iteration for K x = b preconditioned by D_b: the
+    error is multiplied by T_m((theta - M)/delta) / T_m(theta/delta), M = D_b^{-1} K."""
+    d = np.zeros_like(b)
+    for c1, c2 in chebyshev_coefficients(lam, degree):
+        r = b - apply_K(level.mesh, level.E, level.K0, x)
+        d = c1 * d + c2 * block_jacobi_apply(level, r)
+        x = x + d
+    return x
+
+
+def _smooth(H: Hierarchy, lev: Level, x: np.ndarray, b: np.ndarray, nu: int) -> np.ndarray:
+    if H.smoother == "chebyshev":
+        return chebyshev_smooth(lev, x, b, lev.lam, nu)
+    for _ in range(nu):
+        x = jacobi_sweep(lev, x, b, H.omega)
+    return x
+
+
 def vcycle(H: Hierarchy, b: np.ndarray, l: int = 0) -> np.ndarray:
     """One V-cycle on level l for right-hand side b (fixed entries of b are zero)."""
     lev = H.levels[l]
     if l == len(H.levels) - 1:
         return coarse_solve(lev, b)
-    x = np.zeros_like(b)
-    for _ in range(H.nu1):
-        x = jacobi_sweep(lev, x, b, H.omega)
+    x = _smooth(H, lev, np.zeros_like(b), b, H.nu1)
     r = b - apply_K(lev.mesh, lev.E, lev.K0, x)
     coarse = H.levels[l + 1]
     bc = lev.P.T @ r
@@ -394,9 +464,7 @@ def vcycle(H: Hierarchy, b: np.ndarray, l: int = 0) -> np.ndarray:
     corr = lev.P @ xc
     corr[lev.mesh.fixed] = 0.0
     x = x + corr
-    for _ in range(H.nu2):
-        x = jacobi_sweep(lev, x, b, H.omega)
-    return x
+    return _smooth(H, lev, x, b, H.nu2)
 
 
 # ----------------------------------------------------------------------------
@@ -577,13 +645,14 @@ class SolverSetup:
     nu1: int = 2
     nu2: int = 2
     omega: float = 0.6
+    smoother: str = "jacobi"
 
 
 def solve_at_floor(setup: SolverSetup, f: np.ndarray, rho_min: float, kmax: int, tol: float):
     """Frozen-state solve K(rho_min) u = f with GMG-preconditioned FGMRES from u0 = 0."""
     mesh = setup.mesh
     E = young_modulus(setup.rho_hat, rho_min, setup.p)
-    H = build_hierarchy(mesh, E, setup.n_levels, setup.nu, setup.nu1, setup.nu2, setup.omega)
+    H = build_hierarchy(mesh, E, setup.n_levels, setup.nu, setup.nu1, setup.nu2, setup.omega, setup.smoother)
     K0 = H.levels[0].K0
     fm = np.where(mesh.fixed, 0.0, f)
     res = fgmres(lambda v: apply_K(mesh, E, K0, v), lambda v: vcycle(H, v), fm,

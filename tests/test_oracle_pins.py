@@ -586,3 +586,73 @@ def test_selector_features():
     rho = np.array([0.0, 0.0, 1.0, 0.5])
     x = O.selector_features(1e-3, 1e-5, rho)
     assert np.allclose(x, [-3, -5, 1e-2, 0.5, 0.375, np.std(rho)])
+
+
+# ------------------------------------------------------------- Chebyshev smoother ---
+def _free_block_diag(level):
+    """D_b restricted to the free DOFs as a dense matrix."""
+    m = level.mesh
+    n = m.n_dof
+    D = np.zeros((n, n))
+    for node in range(m.n_nodes):
+        D[3 * node:3 * node + 3, 3 * node:3 * node + 3] = level.blockdiag[node]
+    return D[np.ix_(m.free, m.free)]
+
+
+def test_chebyshev_smoother_damps_eigenvectors_by_the_chebyshev_polynomial():
+    """On a generalized eigenvector K e = lam D_b e with b = 0, degree-m smoothing maps e
+    to T_m((theta - lam)/delta) / T_m(theta/delta) e (T_2(t) = 2t^2 - 1, T_3 = 4t^3 - 3t),
+    for any interval -- here [lmax/30, 1.1 lmax] of the exact lambda_max."""
+    m, E, H = _hier(nx=4, ny=2, nz=2, levels=1)
+    lev = H.levels[0]
+    A = O.assemble_dense_free(m, E, lev.K0)
+    lams, vecs = sla.eigh(A, _free_block_diag(lev))
+    lmax = lams[-1]
+    a, b = lmax / 30.0, 1.1 * lmax
+    theta, delta = 0.5 * (b + a), 0.5 * (b - a)
+    T = {2: lambda t: 2 * t * t - 1, 3: lambda t: 4 * t ** 3 - 3 * t}
+    for deg in (2, 3):
+        for idx in (0, len(lams) // 3, len(lams) - 1):
+            e = np.zeros(m.n_dof)
+            e[m.free] = vecs[:, idx]
+            x = O.chebyshev_smooth(lev, e, np.zeros(m.n_dof), lmax, deg)
+            damp = T[deg]((theta - lams[idx]) / delta) / T[deg](theta / delta)
+            assert np.abs(x - damp * e).max() <= 1e-10 * np.abs(e).max(), (deg, idx)
+
+
+def test_power_method_closed_form_on_a_diagonal_operator():
+    """For M = diag(l_i) and v0 = ones the k-th estimate is sqrt(sum l^(2k) / sum l^(2k-2))."""
+    lam = np.array([0.3, 1.7, 2.5, 4.0, 3.9])
+    for iters in (1, 2, 5, 15):
+        got = O.power_lambda_max(lambda v: lam * v, np.ones(5), iters)
+        want = math.sqrt(np.sum(lam ** (2 * iters)) / np.sum(lam ** (2 * iters - 2)))
+        assert abs(got - want) <= 1e-13 * want, iters
+
+
+def test_level_lambda_max_is_a_lower_bound_close_to_the_true_value():
+    m, E, H = _hier(nx=4, ny=2, nz=2, levels=1, seed=5)
+    lev = H.levels[0]
+    lams = sla.eigh(O.assemble_dense_free(m, E, lev.K0), _free_block_diag(lev), eigvals_only=True)
+    est = O.level_lambda_max(lev)
+    assert est <= lams[-1] * (1 + 1e-12)
+    assert est >= 0.8 * lams[-1]
+    # the [lam/30, 1.1 lam] interval then covers the upper spectrum the smoother must damp
+    assert 1.1 * est >= lams[-1]
+
+
+def test_vcycle_with_chebyshev_is_symmetric_and_preconditions_fgmres():
+    m = O.Mesh(8, 4, 4)
+    E = O.young_modulus(synth.uniform_density(8, 4, 4, 0), 1e-3, 3)
+    H = O.build_hierarchy(m, E, 3, smoother="chebyshev")
+    assert all(lev.lam > 0 for lev in H.levels[:-1])
+    a, b = synth.random_vector(m.n_dof, 1), synth.random_vector(m.n_dof, 2)
+    a[m.fixed] = 0
+    b[m.fixed] = 0
+    Va, Vb = O.vcycle(H, a), O.vcycle(H, b)
+    assert abs(b @ Va - a @ Vb) < 1e-12 * np.linalg.norm(Va) * np.linalg.norm(b)
+    f = O.cantilever_load(m)
+    setup = O.SolverSetup(m, synth.uniform_density(8, 4, 4, 0), n_levels=3, smoother="chebyshev")
+    res, E2, K0 = O.solve_at_floor(setup, f, 1e-3, 200, 1e-6)
+    assert res.flag == O.CONVERGED and res.iters < 60
+    uh = res.x
+    assert O.true_residual(m, E2, K0, f, uh) <= 1.5e-6
