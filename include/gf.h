@@ -86,6 +86,12 @@ typedef struct {
                           K*u and CGS2 in double-float arithmetic (FP32 instructions, ~48-bit
                           basis vectors; h, rotations and least squares stay FP64). Other values:
                           GF_ERR_ARG. The guard is always native FP64. */
+    int    smoother;   /* V-cycle smoother: 0 = damped node-block Jacobi (nu sweeps, omega);
+                          1 = Chebyshev semi-iteration of degree nu1 / nu2 on D_b^{-1} K over
+                          [lambda_max/30, 1.1 lambda_max] (the Chebyshev smoother Table
+                          solver-config names; degree and interval are this library's readings),
+                          lambda_max of each level from 15 power iterations from ones on the
+                          free DOFs, computed on first use after each gf_set_floor. */
 } gf_solve_opts;
 
 typedef struct {
@@ -204,6 +210,16 @@ int gf_apply_K_f32(gf_grid* g, const float* u, float* y);
  * omega, restriction = transpose of trilinear prolongation, FP64 coarsest solve)
  * in precision `prec`. v, z: n_dof doubles; fixed entries of v are ignored. */
 int gf_vcycle(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2, double omega);
+/* The V-cycle with the V-cycle options of a solve-options struct: prec, nu1, nu2, omega, smoother;
+ * the other fields are ignored. Same buffers and errors as gf_vcycle. With smoother = 1
+ * the first call after gf_set_floor computes the levels' lambda_max (enqueue it
+ * outside any stream capture). */
+int gf_vcycle_ex(gf_grid* g, const double* v, double* z, const gf_solve_opts* opts);
+/* The Chebyshev smoother's lambda_max(D_b^{-1} K) estimate of levels 0 .. levels-2 for
+ * the V-cycle of precision prec (GF_FP64 on the FP64 moduli, GF_MIXED on the FP32 ones
+ * from the BF16 density) into lam (host, n >= levels-1 entries); computes them if
+ * needed. Blocks. GF_ERR_STATE before gf_set_floor. */
+int gf_chebyshev_lambda(gf_grid* g, int prec, double* lam, int n);
 
 /* ---- solve, guard, policy ----------------------------------------------------- */
 

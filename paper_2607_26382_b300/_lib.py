@@ -28,7 +28,7 @@ ERRORS = {-1: "GF_ERR_ARG", -2: "GF_ERR_OOM", -3: "GF_ERR_CUDA", -4: "GF_ERR_NON
 
 EXPORTED = [
     "gf_create_grid", "gf_destroy_grid", "gf_grid_sizes", "gf_set_density", "gf_set_floor",
-    "gf_cantilever_load", "gf_free_mask", "gf_apply_K", "gf_apply_K_f32", "gf_vcycle", "gf_solve",
+    "gf_cantilever_load", "gf_free_mask", "gf_apply_K", "gf_apply_K_f32", "gf_vcycle", "gf_vcycle_ex", "gf_chebyshev_lambda", "gf_solve",
     "gf_true_residual", "gf_select_floor", "gf_policy_defaults", "gf_trigger_rule",
     "gf_probe_features", "gf_sensitivity", "gf_get_stats", "gf_reset_stats", "gf_last_error",
     "gf_true_residual_noalloc", "gf_filter", "gf_filter_adjoint", "gf_oc_update", "gf_compliance",
@@ -48,7 +48,7 @@ class GFError(RuntimeError):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("restart", c_int), ("kmax", c_int), ("tol", c_double), ("prec", c_int),
                 ("nu1", c_int), ("nu2", c_int), ("omega", c_double), ("history", POINTER(c_double)),
-                ("outer", c_int)]
+                ("outer", c_int), ("smoother", c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -102,6 +102,8 @@ def lib():
         "gf_apply_K": [P, P, P],
         "gf_apply_K_f32": [P, P, P],
         "gf_vcycle": [P, P, P, c_int, c_int, c_int, c_double],
+        "gf_vcycle_ex": [P, P, P, P],
+        "gf_chebyshev_lambda": [P, c_int, P, c_int],
         "gf_solve": [P, P, P, POINTER(SolveOpts), POINTER(SolveInfo)],
         "gf_true_residual": [P, P, P, POINTER(c_double)],
         "gf_select_floor": [P, P, P, POINTER(Policy), POINTER(SelectInfo)],
@@ -276,19 +278,32 @@ class Grid:
         _check(lib().gf_apply_K_f32(self._h, _ptr(u, t, self.n_dof, "u"), _ptr(y, t, self.n_dof, "y")))
         return y
 
-    def vcycle(self, v, z, prec=GF_FP64, nu1=2, nu2=2, omega=0.6):
+    def vcycle(self, v, z, prec=GF_FP64, nu1=2, nu2=2, omega=0.6, smoother=0):
         t = _torch().float64
+        if smoother:
+            o = SolveOpts(30, 0, 0.0, int(prec), int(nu1), int(nu2), float(omega), None, 0, int(smoother))
+            _check(lib().gf_vcycle_ex(self._h, _ptr(v, t, self.n_dof, "v"), _ptr(z, t, self.n_dof, "z"),
+                                      ctypes.byref(o)))
+            return z
         _check(lib().gf_vcycle(self._h, _ptr(v, t, self.n_dof, "v"), _ptr(z, t, self.n_dof, "z"), int(prec),
                                int(nu1), int(nu2), float(omega)))
         return z
 
+    def chebyshev_lambda(self, prec=GF_FP64):
+        """The Chebyshev smoother's lambda_max estimates of levels 0 .. levels-2."""
+        n = max(1, self.levels - 1)
+        lam = (c_double * n)()
+        _check(lib().gf_chebyshev_lambda(self._h, int(prec), lam, n))
+        return [lam[i] for i in range(self.levels - 1)]
+
     # solve / guard / policy
     def solve(self, f, u, restart=30, kmax=200, tol=1e-6, prec=GF_FP64, nu1=2, nu2=2, omega=0.6,
-              want_history=True, outer=0):
+              want_history=True, outer=0, smoother=0):
         t = _torch().float64
         hist = (c_double * (kmax + 1))() if want_history else None
         o = SolveOpts(int(restart), int(kmax), float(tol), int(prec), int(nu1), int(nu2), float(omega),
-                      ctypes.cast(hist, POINTER(c_double)) if hist is not None else None, int(outer))
+                      ctypes.cast(hist, POINTER(c_double)) if hist is not None else None, int(outer),
+                      int(smoother))
         info = SolveInfo()
         _check(lib().gf_solve(self._h, _ptr(f, t, self.n_dof, "f"), _ptr(u, t, self.n_dof, "u"),
                               ctypes.byref(o), ctypes.byref(info)))

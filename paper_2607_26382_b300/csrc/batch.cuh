@@ -93,7 +93,7 @@ struct gf_batch {
     cudaGraphExec_t start[2] = {};
     cudaGraphExec_t end = nullptr;
     long long nodes_step[gf::KRY_MMAX] = {}, nodes_start[2] = {}, nodes_end = 0;
-    int key_prec = -1, key_nu1 = -1, key_nu2 = -1, key_m = -1, key_outer = -1;
+    int key_prec = -1, key_nu1 = -1, key_nu2 = -1, key_m = -1, key_outer = -1, key_smoother = -1;
     double key_omega = -1.0;
     void* key_ptrs = nullptr;   // V of state 0 when captured (realloc invalidates)
     // device tables
@@ -173,9 +173,10 @@ int batch_graphs(gf_batch* b, const gf_solve_opts* o)
         key = key * 1000003u ^ (uintptr_t)g->V ^ ((uintptr_t)g->Z << 1) ^ ((uintptr_t)g->hist << 2);
     void* ptr0 = (void*)key;
     if (b->key_prec != o->prec || b->key_nu1 != o->nu1 || b->key_nu2 != o->nu2 || b->key_omega != o->omega ||
-        b->key_m != m || b->key_ptrs != ptr0 || b->key_outer != o->outer) {
+        b->key_m != m || b->key_ptrs != ptr0 || b->key_outer != o->outer || b->key_smoother != o->smoother) {
         batch_drop_graphs(b);
         b->key_outer = o->outer;
+        b->key_smoother = o->smoother;
         b->key_prec = o->prec;
         b->key_nu1 = o->nu1;
         b->key_nu2 = o->nu2;
@@ -253,7 +254,10 @@ int batch_solve(gf_batch* b, const gf_solve_opts* o, const std::vector<int>& act
                 const gf_policy* pol, std::vector<BatchOut>& out)
 {
     const int B = b->B, m = o->restart;
-    for (int i = 0; i < B; ++i) RET(ensure_krylov(b->g[i], m, std::max(o->kmax, probe_at), o->outer));
+    for (int i = 0; i < B; ++i) {
+        RET(ensure_krylov(b->g[i], m, std::max(o->kmax, probe_at), o->outer));
+        if (o->smoother == 1 && active[i]) RET(ensure_cheb(b->g[i], o->prec));
+    }
     RET(batch_tables(b));
     RET(batch_graphs(b, o));
     CK(cudaMemcpyAsync(b->d_active, active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, b->stream));

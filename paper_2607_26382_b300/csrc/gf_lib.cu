@@ -10,6 +10,7 @@
 #include "oc.cuh"
 #include "split.cuh"
 #include "split_tc.cuh"
+#include "cheb.cuh"
 #include "vcycle_cluster.cuh"
 
 #include <cuda_runtime.h>
@@ -164,7 +165,12 @@ struct gf_grid {
     float2* Edf = nullptr;            // s_split * E_e (fine level) as float pairs
     gf::TcBFrag Btc;                  // M as per-lane fp16 MMA B fragments (tensor-core split)
     bool split_tc = true;             // element products on the tensor cores (see gf_create_grid)
-    int gkey_outer = -1;
+    int gkey_outer = -1, gkey_smoother = -1;
+    // Chebyshev smoothing: per precision (0 FP64, 1 FP32) and level, lambda_max and the
+    // step coefficients {c1, c2}[CHEB_MAXDEG] on the device; valid until the next floor
+    double* cheb = nullptr;           // [2][L][1 + 2*CHEB_MAXDEG] (lambda, then coefficients)
+    double* cheb_ss = nullptr;        // power-method scratch scalar
+    bool cheb_ready[2] = {false, false};
     // optimisation-loop scratch (allocated on first use)
     double *oc_rho = nullptr, *oc_dc = nullptr, *oc_dcx = nullptr, *oc_dvx = nullptr, *oc_ones = nullptr;
     gf::OCState* oc_st = nullptr;
@@ -432,9 +438,125 @@ int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2,
     return GF_OK;
 }
 
-int vcycle_dispatch(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2, double omega,
-                    const int* halt)
+int alloc(void** p, size_t bytes);
+template <typename T>
+int allocT(T** p, size_t n);
+
+// Chebyshev slot of precision p (0 FP64, 1 FP32) and level l: [lambda, c1_0, c2_0, c1_1, ...]
+double* cheb_slot(gf_grid* g, int p, int l) { return g->cheb + ((long long)p * g->L + l) * (1 + 2 * gf::CHEB_MAXDEG); }
+
+// lambda_max of D_b^{-1} K on every smoothing level by the power method, and the
+// Chebyshev coefficients; for the operator the V-cycle of precision prec smooths with
+// (FP64 moduli, or the FP32 ones from the BF16 density). Runs outside graph capture.
+template <typename T>
+int cheb_setup_impl(gf_grid* g)
 {
+    using B = LvBuf<T>;
+    const int p = sizeof(T) == sizeof(double) ? 0 : 1;
+    for (int l = 0; l < g->L - 1; ++l) {
+        Level& lev = g->lv[l];
+        const long long n = 3 * lev.nodes;
+        T* v = B::x(lev);
+        T* w = B::t(lev);
+        LAUNCH(g, nblk(n), 256, gf::cheb_ones_kernel<T>, v, n, lev.nx + 1);
+        LAUNCH(g, 1, 1024, gf::cheb_sumsq_kernel<T>, (const T*)v, n, g->cheb_ss);
+        LAUNCH(g, nblk(n), 256, gf::cheb_normalize_kernel<T>, (const T*)v, v, n, (const double*)g->cheb_ss);
+        for (int it = 0; it < gf::CHEB_POWER_ITERS; ++it) {
+            LAUNCH(g, nblk(lev.nodes), 256, (gf::dinvk_kernel<T, T>), (const T*)v, w, (const T*)B::E(lev), lev.dims(),
+                   k0<T>(g));
+            LAUNCH(g, 1, 1024, gf::cheb_sumsq_kernel<T>, (const T*)w, n, g->cheb_ss);
+            LAUNCH(g, nblk(n), 256, gf::cheb_normalize_kernel<T>, (const T*)w, v, n, (const double*)g->cheb_ss);
+        }
+        double* slot = cheb_slot(g, p, l);
+        LAUNCH(g, 1, 32, gf::cheb_coef_kernel, (const double*)g->cheb_ss, slot, slot + 1);
+    }
+    return GF_OK;
+}
+
+int ensure_cheb(gf_grid* g, int prec)
+{
+    const int p = prec == GF_FP64 ? 0 : 1;
+    if (g->cheb_ready[p]) return GF_OK;
+    if (!g->cheb) {
+        RET(allocT(&g->cheb, (size_t)2 * g->L * (1 + 2 * gf::CHEB_MAXDEG)));
+        RET(allocT(&g->cheb_ss, 1));
+    }
+    if (p == 0) RET(cheb_setup_impl<double>(g));
+    else RET(cheb_setup_impl<float>(g));
+    g->cheb_ready[p] = true;
+    return GF_OK;
+}
+
+// The V-cycle with Chebyshev smoothing (degree nu1 pre, nu2 post), otherwise as
+// vcycle_impl: FP64 or FP32 levels (the FP32 form converts the FP64 right-hand side
+// and result), restriction, coarsest GEMV, prolongation. The residual buffer of a
+// level holds the Chebyshev direction d while the level smooths.
+template <typename T>
+int vcycle_cheb(gf_grid* g, const double* v, double* z, int nu1, int nu2, const int* halt)
+{
+    using B = LvBuf<T>;
+    const int L = g->L, p = sizeof(T) == sizeof(double) ? 0 : 1;
+    const int NX0 = g->nx + 1;
+    g->stats.vcycles++;
+    if (L == 1) return vcycle_impl<T>(g, v, z, nu1, nu2, T(0.6), halt);
+    std::vector<T*> cur(L);
+    const T* b0;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        b0 = reinterpret_cast<const T*>(v);
+    } else {
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, T>), v, B::b(g->lv[0]), g->ndof, NX0, halt);
+        b0 = B::b(g->lv[0]);
+    }
+    auto smooth = [&](int l, const T* b, T*& x, T*& t, int degree, bool from_zero) -> int {
+        Level& lev = g->lv[l];
+        const double* coef = cheb_slot(g, p, l) + 1;
+        for (int k = 0; k < degree; ++k) {
+            LAUNCH(g, nblk(lev.nodes), 256, (gf::cheb_step_kernel<T, T>), (from_zero && k == 0) ? (const T*)nullptr : (const T*)x,
+                   b, t, B::r(lev), (const T*)B::E(lev), lev.dims(), k0<T>(g), coef + 2 * k, halt);
+            std::swap(x, t);
+        }
+        return GF_OK;
+    };
+    for (int l = 0; l < L - 1; ++l) {
+        Level& lev = g->lv[l];
+        const T* b = (l == 0) ? b0 : B::b(lev);
+        T* x = B::t(lev);   // the first step writes B::x (x and t swap after every step)
+        T* t = B::x(lev);
+        RET(smooth(l, b, x, t, nu1, true));
+        cur[l] = x;
+        RET((stencil<T, T, gf::ST_RESID>(g, l, x, b, B::r(lev), B::E(lev), k0<T>(g), T(0), halt)));
+        Level& c = g->lv[l + 1];
+        LAUNCH(g, nblk(c.nodes), 256, gf::restrict_kernel<T>, B::r(lev), B::b(c), c.dims(), halt);
+    }
+    {
+        Level& c = g->lv[L - 1];
+        LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<T, T>), g->Ainv, B::b(c), B::x(c), g->nc, halt);
+        cur[L - 1] = B::x(c);
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        Level& lev = g->lv[l];
+        const T* b = (l == 0) ? b0 : B::b(lev);
+        T* x = cur[l];
+        T* t = (x == B::x(lev)) ? B::t(lev) : B::x(lev);
+        LAUNCH(g, nblk(lev.nodes), 256, (gf::prolong_add_kernel<T, T>), x, cur[l + 1], lev.dims(), halt);
+        RET(smooth(l, b, x, t, nu2, false));
+        cur[l] = x;
+    }
+    if constexpr (sizeof(T) == sizeof(double))
+        CK(cudaMemcpyAsync(z, cur[0], sizeof(double) * g->ndof, cudaMemcpyDeviceToDevice, g->cur_stream));
+    else
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<T, double>), (const T*)cur[0], z, g->ndof, NX0, halt);
+    return GF_OK;
+}
+
+int vcycle_dispatch(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2, double omega,
+                    const int* halt, int smoother = 0)
+{
+    if (smoother == 1) {
+        if (!g->cheb_ready[prec == GF_FP64 ? 0 : 1]) return set_err(GF_ERR_STATE, "Chebyshev bounds not set up");
+        if (prec == GF_MIXED) return vcycle_cheb<float>(g, v, z, nu1, nu2, halt);
+        return vcycle_cheb<double>(g, v, z, nu1, nu2, halt);
+    }
     if (prec == GF_MIXED) {
         if (g->L > 1) return vcycle_mixed_tiled(g, v, z, nu1, nu2, (float)omega, halt);
         return vcycle_impl<float>(g, v, z, nu1, nu2, (float)omega, halt);
@@ -653,7 +775,7 @@ int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
     double* zj = g->Z + (long long)j * ld;
     double* w = g->V + (long long)(j + 1) * ld;
     const int* halt = &g->st->status;
-    RET(vcycle_dispatch(g, vj, zj, o->prec, o->nu1, o->nu2, o->omega, halt));
+    RET(vcycle_dispatch(g, vj, zj, o->prec, o->nu1, o->nu2, o->omega, halt, o->smoother));
     if (o->outer == 2) RET(applyKsplit_dd(g, zj, g->Vd + (long long)(j + 1) * ld, halt));
     else RET(applyOuter(g, zj, w, halt, o->outer));
     switch (pick_nv(j + 1)) {
@@ -690,9 +812,10 @@ int run_step(gf_grid* g, int j, const gf_solve_opts* o)
 {
     if (!g->use_graphs) return arnoldi_step(g, j, o);
     if (g->gkey_prec != o->prec || g->gkey_nu1 != o->nu1 || g->gkey_nu2 != o->nu2 || g->gkey_omega != o->omega ||
-        g->gkey_outer != o->outer) {
+        g->gkey_outer != o->outer || g->gkey_smoother != o->smoother) {
         drop_graphs(g);
         g->gkey_outer = o->outer;
+        g->gkey_smoother = o->smoother;
         g->gkey_prec = o->prec;
         g->gkey_nu1 = o->nu1;
         g->gkey_nu2 = o->nu2;
@@ -741,6 +864,7 @@ int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, g
 {
     const int m = o->restart;
     RET(ensure_krylov(g, m, o->kmax, o->outer));
+    if (o->smoother == 1) RET(ensure_cheb(g, o->prec));
     const int NX0 = g->nx + 1;
     // fixed entries of u are written as 0
     LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, double>), u, u, g->ndof, NX0, nullptr);
@@ -811,6 +935,7 @@ int validate_opts(const gf_solve_opts* o)
     if (!(o->omega > 0.0 && o->omega < 2.0)) return set_err(GF_ERR_ARG, "omega in (0,2)");
     if (o->outer < 0 || o->outer > 2)
         return set_err(GF_ERR_ARG, "outer must be 0 (FP64), 1 (split K*u) or 2 (split K*u, double-float CGS2)");
+    if (o->smoother != 0 && o->smoother != 1) return set_err(GF_ERR_ARG, "smoother must be 0 (Jacobi) or 1 (Chebyshev)");
     return GF_OK;
 }
 
@@ -1067,7 +1192,7 @@ int gf_destroy_grid(gf_grid* g)
         cudaFree(L.b64); cudaFree(L.x64); cudaFree(L.t64); cudaFree(L.r64);
         cudaFree(L.b32); cudaFree(L.x32); cudaFree(L.t32); cudaFree(L.r32);
     }
-    cudaFree(g->Ainv); cudaFree(g->Agj); cudaFree(g->dflag);
+    cudaFree(g->Ainv); cudaFree(g->Agj); cudaFree(g->dflag); cudaFree(g->cheb); cudaFree(g->cheb_ss);
     cudaFree(g->rho64); cudaFree(g->rho16); cudaFree(g->work); cudaFree(g->partial);
     cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Vd); cudaFree(g->pdd); cudaFree(g->ddticket); cudaFree(g->Z); cudaFree(g->hist);
     cudaFree(g->xsave);
@@ -1149,6 +1274,7 @@ int gf_set_floor(gf_grid* g, double rho_min)
     if (!g->skip_coarse_inverse) RET(build_coarse_inverse(g));
     g->rho_min = rho_min;
     g->has_floor = true;
+    g->cheb_ready[0] = g->cheb_ready[1] = false;
     return GF_OK;
 }
 
@@ -1207,6 +1333,32 @@ int gf_vcycle(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2
     if (nu1 < 1 || nu2 < 1 || nu1 > 16 || nu2 > 16 || !(omega > 0 && omega < 2)) return set_err(GF_ERR_ARG, "smoother");
     RET(set_device(g));
     return vcycle_dispatch(g, v, z, prec, nu1, nu2, omega, nullptr);
+}
+
+int gf_vcycle_ex(gf_grid* g, const double* v, double* z, const gf_solve_opts* o)
+{
+    RET(check_grid(g));
+    RET(validate_opts(o));
+    if (!v || !z || v == z) return set_err(GF_ERR_ARG, "v, z non-null and distinct");
+    if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
+    RET(set_device(g));
+    if (o->smoother == 1) RET(ensure_cheb(g, o->prec));
+    return vcycle_dispatch(g, v, z, o->prec, o->nu1, o->nu2, o->omega, nullptr, o->smoother);
+}
+
+int gf_chebyshev_lambda(gf_grid* g, int prec, double* lam, int n)
+{
+    RET(check_grid(g));
+    if (!lam || n < g->L - 1) return set_err(GF_ERR_ARG, "lam needs levels - 1 entries");
+    if (prec != GF_FP64 && prec != GF_MIXED) return set_err(GF_ERR_ARG, "prec");
+    if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
+    RET(set_device(g));
+    RET(ensure_cheb(g, prec));
+    for (int l = 0; l < g->L - 1; ++l)
+        CK(cudaMemcpyAsync(lam + l, cheb_slot(g, prec == GF_FP64 ? 0 : 1, l), sizeof(double), cudaMemcpyDeviceToHost,
+                           g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return GF_OK;
 }
 
 int gf_solve(gf_grid* g, const double* f, double* u, const gf_solve_opts* opts, gf_solve_info* info)

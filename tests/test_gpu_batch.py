@@ -34,12 +34,13 @@ def _rho(dims, kind, seed, q):
     return synth.smoothed_gaussian_density(nx, ny, nz, seed, 2.0, q)
 
 
-@pytest.mark.parametrize("selector,prec,outer", [("rule", 0, 0), ("full", 1, 0), ("rule", 1, 2)])
-def test_batch_matches_single_state(gf, selector, prec, outer):
+@pytest.mark.parametrize("selector,prec,outer,smoother", [("rule", 0, 0, 0), ("full", 1, 0, 0), ("rule", 1, 2, 0),
+                                                          ("rule", 1, 2, 1)])
+def test_batch_matches_single_state(gf, selector, prec, outer, smoother):
     L = 3
     sel = gf.GF_SEL_RULE if selector == "rule" else gf.GF_SEL_FULL
     pol = gf.policy_defaults(rho0=1e-8, ladder=[1e-5, 1e-4, 1e-3], kmax=120, selector=sel, solve_prec=prec,
-                             solve_outer=outer)
+                             solve_outer=outer, solve_smoother=smoother)
     batch = gf.Batch([s[0] for s in STATES], levels=L)
     tuned = batch.autotune()
     assert all(t[0] in (64, 128, 256) and t[1] in (0, 64, 128, 256, -64, -128, -256) for t in tuned)

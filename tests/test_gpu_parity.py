@@ -147,6 +147,74 @@ def test_vcycle_mixed_parity(gf):
     assert relerr(host(z), O.vcycle(H, v)) <= 1e-4
 
 
+# ------------------------------------------------------------- Chebyshev smoother --
+@pytest.mark.parametrize("nx,ny,nz,L", [(16, 8, 8, 3), (24, 10, 6, 2), (8, 4, 4, 3)])
+def test_chebyshev_lambda_and_vcycle_fp64_parity(gf, nx, ny, nz, L):
+    g, m, rho = make(gf, nx, ny, nz, L, seed=2)
+    E = O.young_modulus(rho, 1e-3, 3.0)
+    H = O.build_hierarchy(m, E, L, smoother="chebyshev")
+    lam = g.chebyshev_lambda(gf.GF_FP64)
+    ref = [lev.lam for lev in H.levels[:-1]]
+    assert len(lam) == L - 1
+    assert np.allclose(lam, ref, rtol=1e-10, atol=0)
+    v = np.where(m.fixed, 0, synth.random_vector(m.n_dof, 9))
+    for rep in range(2):   # the second call reuses the bounds
+        z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        g.vcycle(dev(v), z, gf.GF_FP64, smoother=1)
+        assert relerr(host(z), O.vcycle(H, v)) <= 1e-9
+    # a new floor recomputes the bounds
+    g.set_floor(1e-6)
+    H6 = O.build_hierarchy(m, O.young_modulus(rho, 1e-6, 3.0), L, smoother="chebyshev")
+    assert np.allclose(g.chebyshev_lambda(gf.GF_FP64), [lev.lam for lev in H6.levels[:-1]], rtol=1e-10, atol=0)
+
+
+def test_chebyshev_vcycle_mixed_parity(gf):
+    nx, ny, nz, L = 16, 8, 8, 3
+    g, m, rho = make(gf, nx, ny, nz, L, seed=2)
+    E16 = O.young_modulus(bf16_round(rho), 1e-3, 3.0)
+    H = O.build_hierarchy(m, E16, L, smoother="chebyshev")
+    H64 = O.build_hierarchy(m, O.young_modulus(rho, 1e-3, 3.0), L)
+    H.levels[-1].chol = H64.levels[-1].chol
+    lam = g.chebyshev_lambda(gf.GF_MIXED)
+    assert np.allclose(lam, [lev.lam for lev in H.levels[:-1]], rtol=1e-5, atol=0)
+    v = np.where(m.fixed, 0, synth.random_vector(m.n_dof, 9))
+    z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.vcycle(dev(v), z, gf.GF_MIXED, smoother=1)
+    assert relerr(host(z), O.vcycle(H, v)) <= 1e-4
+
+
+@pytest.mark.parametrize("case", [(16, 8, 8, 3, "uniform", 1e-3), (16, 8, 8, 3, "bernoulli", 1e-6)])
+def test_solve_chebyshev_fp64_parity(gf, case):
+    nx, ny, nz, L, kind, rm = case
+    g, m, rho = make(gf, nx, ny, nz, L, seed=4, rho_min=rm, kind=kind)
+    f = O.cantilever_load(m)
+    setup = O.SolverSetup(m, rho, p=3.0, n_levels=L, restart=30, smoother="chebyshev")
+    res, E, K0 = O.solve_at_floor(setup, f, rm, 200, 1e-6)
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    out = g.solve(dev(f), u, restart=30, kmax=200, tol=1e-6, prec=gf.GF_FP64, smoother=1)
+    assert abs(out["iters"] - res.iters) <= 1 and out["flag"] == res.flag
+    k = min(out["iters"], res.iters)
+    h_gpu, h_ref = np.array(out["history"][:k + 1]), res.history[:k + 1]
+    assert np.all(np.abs(h_gpu - h_ref) <= 1e-6 * h_ref + 1e-15)
+    if res.flag == O.CONVERGED:
+        assert O.true_residual(m, E, K0, f, host(u)) <= 1.5e-6
+
+
+def test_solve_chebyshev_mixed_converges(gf):
+    """The mixed form (FP32 Chebyshev V-cycle, FP64-class Krylov) converges in about the
+    oracle's FP64 iteration count (59 here) and passes the oracle's guard."""
+    nx, ny, nz, L = 16, 8, 8, 3
+    g, m, rho = make(gf, nx, ny, nz, L, seed=4, rho_min=1e-3, kind="bernoulli")
+    f = O.cantilever_load(m)
+    res, E, K0 = O.solve_at_floor(O.SolverSetup(m, rho, p=3.0, n_levels=L, smoother="chebyshev"), f, 1e-3, 200,
+                                  1e-6)
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    out = g.solve(dev(f), u, prec=gf.GF_MIXED, outer=2, smoother=1)
+    assert out["flag"] == gf.GF_FLAG_CONVERGED and res.flag == O.CONVERGED
+    assert abs(out["iters"] - res.iters) <= max(2, res.iters // 10)
+    assert O.true_residual(m, E, K0, f, host(u)) <= 1.5e-6
+
+
 # ------------------------------------------------------------- a6/a7: solve ------
 def _oracle_solve(m, rho, rho_min, L, f, kmax=200, restart=30, tol=1e-6):
     setup = O.SolverSetup(m, rho, p=3.0, n_levels=L, restart=restart)
@@ -256,6 +324,10 @@ def test_errors(gf):
         with pytest.raises(gf.GFError) as e:
             g.solve(u.clone(), u.clone(), outer=outer)
         assert e.value.code == -1                     # GF_ERR_ARG
+    for smoother in (-1, 2):                          # smoother out of range
+        with pytest.raises(gf.GFError) as e:
+            g.solve(u.clone(), u.clone(), smoother=smoother)
+        assert e.value.code == -1
 
 
 # ------------------------------------------------------------- a8: policy --------
