@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -352,6 +353,34 @@ def run_b300(args):
         roofline = dict(native)
     gdofs, gdofs_split = native["gdofs"], split["gdofs"]
 
+    # ---- the same states through the batched path (gf_batch: the states' FGMRES steps
+    # in lockstep, one CUDA graph per step over all states), reported beside value
+    batched = None
+    if prec == gf.GF_MIXED and not args.no_batch:
+        from paper_2607_26382_b300 import selector as gfsel
+        bt = gfsel._batch_for([(NX, NY, NZ)] * len(rhos_h), LEVELS, rhos_h, P_SIMP)
+        bt.autotune()
+        bt.select_floor(pol)                      # warm-up: graphs captured, buffers sized
+        passes = max(1, args.steps // len(rhos_h))
+        launches_b0 = bt.kernel_launches()
+        barrier()
+        t0 = time.perf_counter()
+        acc_b = 0
+        for _ in range(passes):
+            acc_b += sum(r["status"] == gf.GF_ACCEPTED for r in bt.select_floor(pol))
+        barrier()
+        dt_b = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt_b, acc_b], dtype=torch.float64, device="cuda")
+            mx, smv = t.clone(), t.clone()
+            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+            dist.all_reduce(smv, op=dist.ReduceOp.SUM)
+            dt_b, acc_b = float(mx[0]), int(smv[1])
+        batched = {"value": acc_b / dt_b, "unit": UNIT, "states_per_pass": len(rhos_h), "passes": passes,
+                   "timing": "host clock around blocking gf_batch_select_floor calls (barrier + synchronize)",
+                   "gpu_launches": bt.kernel_launches() - launches_b0}
+        bt.close()
+
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -396,7 +425,7 @@ def run_b300(args):
               "accepted": accepted, "fgmres_iters_per_step": iters / args.steps, "records": records,
               "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
               "cpu_baseline": cpu, "apply_K_fp64_gdofs": gdofs, "apply_K_split_gdofs": gdofs_split,
-              "apply_K_fp32_gdofs": stencil["gdofs"]})
+              "apply_K_fp32_gdofs": stencil["gdofs"], "batched": batched})
     if dist is not None:
         dist.destroy_process_group()
 
