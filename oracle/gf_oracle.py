@@ -670,10 +670,22 @@ def guarded_policy(probe_fn, attempt_fn, rho0: float, ladder, tau: float = 1e-6,
     followed by the recomputed FP64 true residual (the acceptance guard).
 
     selector: "rule" (Eq. trigger on the probe), "full" (no probe, C = (rho0, ladder)),
-    or "given" (no probe; start at ``first_index`` of (rho0, ladder) -- e.g. chosen by a
-    learned selector -- and continue up the ladder). Floor indices refer to (rho0, ladder...).
+    "given" (no probe; start at ``first_index`` of (rho0, ladder) -- e.g. chosen by a
+    learned selector -- and continue up the ladder), or "reuse" (the cost reduction the
+    paper names for the optimisation loop and leaves untested: attempt the previous
+    decision, ``first_index``, with no probe; if the guard rejects it, run "rule" from
+    scratch, the rejected attempt recorded first). Floor indices refer to (rho0, ladder...).
     """
     floors = [rho0] + list(ladder)
+    if selector == "reuse":
+        res, eta = attempt_fn(floors[int(first_index)], kmax)
+        first = Attempt(floors[int(first_index)], res.iters, res.flag, res.stop_estimate, eta, eta <= tau)
+        if eta <= tau:
+            return SelectResult(ACCEPTED, int(first_index), floors[int(first_index)], res.x, eta,
+                                float("nan"), float("nan"), int(first_index) > 0, [first], 0)
+        out = guarded_policy(probe_fn, attempt_fn, rho0, ladder, tau, kmax, probe_iters, th, "rule")
+        out.attempts = [first] + out.attempts
+        return out
     r50 = r100 = float("nan")
     escalated = False
     probe_k = 0

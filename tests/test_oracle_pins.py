@@ -432,9 +432,10 @@ def test_probe_features_early_convergence_gives_ratio_one():
 
 class _Fake:
     def __init__(self, etas, probe_hist):
-        self.etas, self.probe_hist, self.calls = etas, probe_hist, []
+        self.etas, self.probe_hist, self.calls, self.probes = etas, probe_hist, [], 0
 
     def probe(self, rm, iters):
+        self.probes += 1
         h = np.asarray(self.probe_hist)
         return O.SolveResult(np.zeros(1), h, len(h) - 1, O.MAX_ITERS, float(h[-1]))
 
@@ -465,6 +466,26 @@ def test_guarded_policy_algorithm_1():
     fk = _Fake({1e-6: 1.0, 1e-5: 1.0, 1e-4: 1e-7, 1e-3: 1e-7}, hist)
     r = O.guarded_policy(fk.probe, fk.attempt, 1e-6, ladder, selector="given", first_index=2)
     assert fk.calls == [1e-4] and r.floor_index == 2
+
+
+def test_reuse_previous_decision_until_the_guard_rejects():
+    """"reuse": the previous floor is attempted without a probe; accepted -> done; rejected
+    -> Algorithm 1 from scratch (probe at rho0, Eq. trigger, ladder), attempts in order."""
+    ladder = [1e-5, 1e-4, 1e-3]
+    hist = np.geomspace(1.0, 1e-6, 101)          # a probe that keeps rho0
+    fk = _Fake({1e-6: 2e-6, 1e-5: 5e-7, 1e-4: 1e-8, 1e-3: 1e-9}, hist)
+    r = O.guarded_policy(fk.probe, fk.attempt, 1e-6, ladder, selector="reuse", first_index=2)
+    assert fk.calls == [1e-4] and fk.probes == 0 and r.floor_index == 2 and r.escalated
+    assert r.probe_iters_run == 0 and len(r.attempts) == 1 and np.isnan(r.r50)
+    # the reused floor fails: the full policy runs (probe keeps rho0, rho0 fails, 1e-5 accepted)
+    fk = _Fake({1e-6: 2e-6, 1e-5: 5e-7, 1e-4: 1e-5, 1e-3: 1e-9}, hist)
+    r = O.guarded_policy(fk.probe, fk.attempt, 1e-6, ladder, selector="reuse", first_index=2)
+    assert fk.calls == [1e-4, 1e-6, 1e-5] and fk.probes == 1 and r.floor_index == 1
+    assert [a.rho_min for a in r.attempts] == [1e-4, 1e-6, 1e-5] and not r.attempts[0].accepted
+    # reusing rho0 (index 0) is the plain solve at rho0
+    fk = _Fake({1e-6: 1e-7, 1e-5: 1e-7, 1e-4: 1e-7, 1e-3: 1e-7}, hist)
+    r = O.guarded_policy(fk.probe, fk.attempt, 1e-6, ladder, selector="reuse", first_index=0)
+    assert fk.calls == [1e-6] and not r.escalated and r.floor_index == 0
 
 
 def test_select_floor_end_to_end_and_compliance_decreases_with_floor():
