@@ -67,6 +67,12 @@ extern "C" {
 #define GF_SEL_FULL   1   /* no probe: try rho0 then every ladder floor in order */
 #define GF_SEL_GIVEN  2   /* no probe: start at first_index of (rho0, ladder...) */
 #define GF_SEL_MLP    3   /* probe at rho0 (fused), a trained gf_mlp picks the first floor */
+#define GF_SEL_REUSE  4   /* optimisation loop (the cost reduction the Discussion, "When is the
+                             guarded policy worth its cost?", names and
+                             leaves untested): attempt floor first_index -- the previous
+                             iteration's decision -- with no probe; if the guard rejects it, run
+                             GF_SEL_RULE from scratch (the rejected attempt is attempts[0]).
+                             Requires n_ladder <= GF_MAX_LADDER-1; single grid only. */
 
 #define GF_MAX_LADDER 8
 

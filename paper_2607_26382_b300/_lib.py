@@ -19,7 +19,7 @@ GF_OK = 0
 GF_FP64, GF_MIXED = 0, 1
 GF_FLAG_CONVERGED, GF_FLAG_MAX_ITERS, GF_FLAG_BREAKDOWN = 0, 1, 2
 GF_ACCEPTED, GF_NO_ADMISSIBLE_FLOOR = 0, 1
-GF_SEL_RULE, GF_SEL_FULL, GF_SEL_GIVEN, GF_SEL_MLP = 0, 1, 2, 3
+GF_SEL_RULE, GF_SEL_FULL, GF_SEL_GIVEN, GF_SEL_MLP, GF_SEL_REUSE = 0, 1, 2, 3, 4
 MLP_PARAMS = 1412
 GF_MAX_LADDER = 8
 

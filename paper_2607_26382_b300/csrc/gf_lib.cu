@@ -1427,11 +1427,63 @@ int gf_probe_features(const double* history, int k_stop, const gf_policy* pol, d
     return GF_OK;
 }
 
+// GF_SEL_REUSE: the previous decision, then Algorithm 1 from scratch if the guard rejects it
+int select_floor_reuse(gf_grid* g, const double* f, double* u, const gf_policy* pol, gf_select_info* info)
+{
+    const int nf = pol->n_ladder + 1;
+    if (pol->first_index < 0 || pol->first_index >= nf) return set_err(GF_ERR_ARG, "first_index");
+    if (pol->n_ladder > GF_MAX_LADDER - 1) return set_err(GF_ERR_ARG, "GF_SEL_REUSE: n_ladder <= GF_MAX_LADDER - 1");
+    gf_solve_opts o = pol->solve;
+    o.history = nullptr;
+    o.tol = pol->tau;
+    o.kmax = pol->kmax;
+    RET(validate_opts(&o));
+    RET(set_device(g));
+    const double rm = pol->first_index == 0 ? pol->rho0 : pol->ladder[pol->first_index - 1];
+    if (!(g->has_floor && g->rho_min == rm)) RET(gf_set_floor(g, rm));
+    gf_solve_info si{};
+    CK(cudaMemsetAsync(u, 0, sizeof(double) * g->ndof, g->stream));
+    RET(solve_impl(g, f, u, &o, &si, true, nullptr));
+    double eta = 0.0;
+    RET(guard_impl(g, f, u, &eta));
+    gf_attempt a{};
+    a.rho_min = rm;
+    a.iters = si.iters;
+    a.flag = si.flag;
+    a.stop_estimate = si.stop_estimate;
+    a.eta = eta;
+    a.accepted = eta <= pol->tau;
+    if (a.accepted) {
+        std::memset(info, 0, sizeof(*info));
+        info->r50 = info->r100 = std::nan("");
+        info->status = GF_ACCEPTED;
+        info->floor_index = pol->first_index;
+        info->rho_min = rm;
+        info->eta = eta;
+        info->escalated = pol->first_index > 0;
+        info->n_attempts = 1;
+        info->attempts[0] = a;
+        return GF_OK;
+    }
+    gf_policy rule = *pol;
+    rule.selector = GF_SEL_RULE;
+    RET(gf_select_floor(g, f, u, &rule, info));
+    for (int i = info->n_attempts; i > 0; --i) info->attempts[i] = info->attempts[i - 1];
+    info->attempts[0] = a;
+    info->n_attempts += 1;
+    return GF_OK;
+}
+
 int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol, gf_select_info* info)
 {
     RET(check_grid(g));
     if (!f || !u || !pol || !info || f == u) return set_err(GF_ERR_ARG, "null pointer");
     if (!g->has_density) return set_err(GF_ERR_STATE, "set_density first");
+    if (pol->selector == GF_SEL_REUSE) {
+        if (pol->n_ladder < 0) return set_err(GF_ERR_ARG, "n_ladder");
+        if (!(pol->rho0 > 0) || pol->probe_iters < 0 || pol->kmax < 0) return set_err(GF_ERR_ARG, "policy");
+        return select_floor_reuse(g, f, u, pol, info);
+    }
     if (pol->n_ladder < 0 || pol->n_ladder > GF_MAX_LADDER) return set_err(GF_ERR_ARG, "n_ladder");
     if (!(pol->rho0 > 0) || pol->probe_iters < 0 || pol->kmax < 0) return set_err(GF_ERR_ARG, "policy");
     gf_solve_opts o = pol->solve;

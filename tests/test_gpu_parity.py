@@ -330,6 +330,35 @@ def test_errors(gf):
         assert e.value.code == -1
 
 
+# ------------------------------------------------------------- reuse selector ------
+@pytest.mark.parametrize("seed,q", [(43, 0.35), (47, 0.30)])
+@pytest.mark.parametrize("first", [0, 2])
+def test_reuse_selector_matches_oracle(gf, seed, q, first):
+    """GF_SEL_REUSE: the previous decision without a probe, Algorithm 1 from scratch when
+    the guard rejects it. Same attempts (floor, accepted) and outcome as the oracle."""
+    nx, ny, nz = 16, 8, 8
+    m = O.Mesh(nx, ny, nz)
+    rho = synth.bernoulli_density(nx, ny, nz, seed, q)
+    f = O.cantilever_load(m)
+    ladder = [1e-5, 1e-4, 1e-3]
+    ref = O.select_floor(O.SolverSetup(m, rho, p=3.0, n_levels=3), f, 1e-8, ladder, kmax=120,
+                         selector="reuse", first_index=first)
+    g = gf.create_grid(nx, ny, nz, levels=3)
+    g.set_density(dev(rho), 3.0)
+    pol = gf.policy_defaults(rho0=1e-8, ladder=ladder, kmax=120, selector=gf.GF_SEL_REUSE, first_index=first,
+                             solve_prec=gf.GF_FP64)
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    out = g.select_floor(dev(f), u, pol)
+    assert out["status"] == ref.status and out["floor_index"] == ref.floor_index
+    assert [(a["rho_min"], bool(a["accepted"])) for a in out["attempts"]] == \
+        [(a.rho_min, bool(a.accepted)) for a in ref.attempts]
+    for a, b in zip(out["attempts"], ref.attempts):
+        assert abs(a["iters"] - b.iters) <= 1
+    if ref.status == O.ACCEPTED:
+        E = O.young_modulus(rho, out["rho_min"], 3.0)
+        assert O.true_residual(m, E, O.element_stiffness(), f, host(u)) <= 1e-6 * (1 + 1e-9)
+
+
 # ------------------------------------------------------------- a8: policy --------
 @pytest.mark.parametrize("seed,q", [(43, 0.35), (47, 0.30)])
 def test_select_floor_parity(gf, seed, q):
