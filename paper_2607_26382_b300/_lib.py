@@ -373,7 +373,8 @@ class Grid:
         atts = [dict(rho_min=a.rho_min, iters=a.iters, flag=a.flag, stop_estimate=a.stop_estimate,
                      eta=a.eta, accepted=bool(a.accepted)) for a in info.attempts[:info.n_attempts]]
         return dict(status=info.status, floor_index=info.floor_index, rho_min=info.rho_min, eta=info.eta,
-                    escalated=bool(info.escalated), attempts=atts, compliance=c.value)
+                    escalated=bool(info.escalated), probe_iters_run=info.probe_iters_run, attempts=atts,
+                    compliance=c.value)
 
     def features(self, r50, r100):
         return select_features(self._h, r50, r100)

@@ -2,6 +2,7 @@
 
     python -m paper_2607_26382_b300.experiments batch102 [--train 2000]
     python -m paper_2607_26382_b300.experiments oc_loop [--iters 40]
+    python -m paper_2607_26382_b300.experiments oc_reuse [--iters 40]
 
 batch102: 102 frozen states of uneven size (nx in {32,48,64,80}, ny = nz = nx/2,
   round-robin; 71 smoothed-Gaussian states with 40% of voxels at floor, 31
@@ -17,6 +18,13 @@ batch102: 102 frozen states of uneven size (nx in {32,48,64,80}, ny = nz = nx/2,
               the highest floor it is 90% sure the search must reach.
 oc_loop: a guarded SIMP-OC loop (vol 0.3, filter radius 1.5, p = 3, move 0.2) on the
   96x48x48 cantilever, Algorithm 1 at every iteration, compared across selectors.
+oc_reuse: the in-loop settings of Section 4.1.2 (rho0 = 1e-12, ladder {1e-3, 1e-2},
+  kmax = 300, tau = 1e-6) on the same loop with the p continuation 1.5 -> 3.5 after
+  iteration 15 (no Heaviside projection), mixed solves. Three guarded selectors:
+    rule  - Algorithm 1 at every iteration;
+    reuse - Algorithm 1 at iteration 0, then the previous decision without a probe,
+            Algorithm 1 again only when the guard rejects it (GF_SEL_REUSE);
+    fixed - 1e-3 at every iteration (GF_SEL_GIVEN), still guarded.
 """
 from __future__ import annotations
 
@@ -170,13 +178,54 @@ def oc_loop(args):
     return out
 
 
+def oc_reuse(args):
+    import torch
+    nx, ny, nz = 96, 48, 48
+    cont = 15
+    out = {"workload": f"guarded SIMP-OC {nx}x{ny}x{nz}, {args.iters} iterations, vol 0.3, r_min 1.5, "
+                       f"p 1.5 -> 3.5 after iteration {cont}, rho0 1e-12, ladder [1e-3, 1e-2], kmax 300"}
+    base = dict(rho0=1e-12, ladder=[1e-3, 1e-2], tau=1e-6, kmax=300, probe_iters=100,
+                solve_prec=L.GF_MIXED, solve_outer=2)
+    for name in ("rule", "reuse", "fixed"):
+        g = L.create_grid(nx, ny, nz, levels=5)
+        f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        g.cantilever_load(f)
+        x = torch.full((g.n_elem,), 0.3, dtype=torch.float64, device="cuda")
+        u = torch.zeros_like(f)
+        hist = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for it in range(args.iters):
+            if name == "fixed":
+                pol = L.policy_defaults(selector=L.GF_SEL_GIVEN, first_index=1, **base)
+            elif name == "reuse" and hist:
+                pol = L.policy_defaults(selector=L.GF_SEL_REUSE, first_index=max(hist[-1]["floor_index"], 0),
+                                        **base)
+            else:
+                pol = L.policy_defaults(selector=L.GF_SEL_RULE, **base)
+            p = 1.5 if it < cont else 3.5
+            hist.append(g.oc_iteration(x, f, u, pol, p=p, volfrac=0.3, r_min=1.5, move=0.2))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        acc = [r for r in hist if r["status"] == L.GF_ACCEPTED]
+        out[name] = {"seconds": dt, "accepted": len(acc), "guarded_solves_per_s": len(acc) / dt,
+                     "arnoldi_steps": int(sum(sum(a["iters"] for a in r["attempts"]) for r in hist)),
+                     "probe_steps": int(sum(r["probe_iters_run"] for r in hist)),
+                     "attempts": int(sum(len(r["attempts"]) for r in hist)),
+                     "max_accepted_eta": max((r["eta"] for r in acc), default=None),
+                     "floors": [r["floor_index"] for r in hist],
+                     "compliance_last": hist[-1]["compliance"]}
+        g.close()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch102", "oc_loop"])
+    ap.add_argument("what", choices=["batch102", "oc_loop", "oc_reuse"])
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--iters", type=int, default=40)
     a = ap.parse_args(argv)
-    res = batch102(a) if a.what == "batch102" else oc_loop(a)
+    res = {"batch102": batch102, "oc_loop": oc_loop, "oc_reuse": oc_reuse}[a.what](a)
     print(json.dumps(res), flush=True)
     return 0
 
