@@ -10,6 +10,7 @@
 #include "oc.cuh"
 #include "split.cuh"
 #include "split_tc.cuh"
+#include "stencil_tc.cuh"
 #include "cheb.cuh"
 #include "vcycle_cluster.cuh"
 
@@ -120,6 +121,8 @@ struct gf_grid {
     std::vector<Level> lv;
     gf::K0Param<double> K0d;
     gf::K0Param<float> K0f;
+    gf::S3BFrag* B3 = nullptr;        // B fragments of M (K0 = s M) for stencil_tc32_kernel, device
+    int stc_cz[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // > 0: level l's FP32 stencils on the tensor cores, cz layers per CTA
     double* rho64 = nullptr;
     __nv_bfloat16* rho16 = nullptr;
     double p = 3.0;
@@ -163,7 +166,7 @@ struct gf_grid {
     double s_split = 0.0;
     gf::MParam Msplit;
     float2* Edf = nullptr;            // s_split * E_e (fine level) as float pairs
-    gf::TcBFrag Btc;                  // M as per-lane fp16 MMA B fragments (tensor-core split)
+    gf::TcBFrag* Btc = nullptr;       // M as per-lane fp16 MMA B fragments (tensor-core split), device
     bool split_tc = true;             // element products on the tensor cores (see gf_create_grid)
     int gkey_outer = -1, gkey_smoother = -1;
     // Chebyshev smoothing: per precision (0 FP64, 1 FP32) and level, lambda_max and the
@@ -219,6 +222,14 @@ template <int MODE, typename BT, typename OT>
 int tiled_f32(gf_grid* g, int l, const float* x, const BT* b, OT* out, const float* E, float omega, const int* halt)
 {
     const Level& L = g->lv[l];
+    if (g->stc_cz[l] > 0) {   // element products on the tensor cores (3xTF32)
+        const int cz = g->stc_cz[l];
+        const dim3 grid((L.nx + 1 + gf::S3_NX - 1) / gf::S3_NX, (L.ny + 1 + gf::S3_NY - 1) / gf::S3_NY,
+                        (L.nz + 1 + cz - 1) / cz);
+        LAUNCH_SMEM(g, grid, gf::S3_THREADS, sizeof(gf::S3Smem), (gf::stencil_tc32_kernel<MODE, BT, OT>), x, b, out,
+                    E, L.dims(), g->Msplit, (const gf::S3BFrag*)g->B3, (float)g->s_split, omega, cz, halt);
+        return GF_OK;
+    }
     if (g->tpb[1] > 0) {   // linear node-per-thread kernel with the autotuned block size
         const int tpb = g->tpb[1];
         LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_kernel<float, float, MODE, BT, OT>), x, b, out, E,
@@ -582,7 +593,7 @@ int applyKsplit(gf_grid* g, const double* u, double* y, const int* halt)
     g->stats.apply_K_fp64++;
     if (g->split_tc) {
         LAUNCH_SMEM(g, split_tc_grid(g), gf::TC_THREADS, sizeof(gf::TcSmem), gf::apply_split_tc_kernel<false>, u, y,
-                    (float2*)nullptr, (const float2*)g->Edf, g->lv[0].dims(), g->Btc, halt);
+                    (float2*)nullptr, (const float2*)g->Edf, g->lv[0].dims(), (const gf::TcBFrag*)g->Btc, halt);
         return GF_OK;
     }
     const dim3 grid((g->nx + 1 + gf::SPX - 1) / gf::SPX, (g->ny + 1 + gf::SPY - 1) / gf::SPY,
@@ -598,7 +609,7 @@ int applyKsplit_dd(gf_grid* g, const double* u, float2* yd, const int* halt)
     g->stats.apply_K_fp64++;
     if (g->split_tc) {
         LAUNCH_SMEM(g, split_tc_grid(g), gf::TC_THREADS, sizeof(gf::TcSmem), gf::apply_split_tc_kernel<true>, u,
-                    (double*)nullptr, yd, (const float2*)g->Edf, g->lv[0].dims(), g->Btc, halt);
+                    (double*)nullptr, yd, (const float2*)g->Edf, g->lv[0].dims(), (const gf::TcBFrag*)g->Btc, halt);
         return GF_OK;
     }
     const dim3 grid((g->nx + 1 + gf::SPX - 1) / gf::SPX, (g->ny + 1 + gf::SPY - 1) / gf::SPY,
@@ -1033,6 +1044,54 @@ unsigned short half_bits_of_int(int v)
 // of each lane: for output component t, K-step 0 holds columns comp 0 | comp 1, K-step
 // 1 holds comp 2 | zero padding. Lane (g = lane/4, c = lane%4) holds rows k = 2c, 2c+1
 // (and 2c+8, 2c+9) of column n = g.
+// B fragments of stencil_tc32_kernel: lane (g, cq) of output tile t and K-step c holds
+// M[(a' = g, t)][(a' = cq, c)] and M[(a' = g, t)][(a' = cq + 4, c)] (a' = x + 2y + 4z;
+// K0 = s M, integers exact in TF32).
+void build_s3_bfrag(const gf::MParam& M, gf::S3BFrag* B)
+{
+    auto li = [](int ap) { return gf::local_index(ap & 1, (ap >> 1) & 1, ap >> 2); };
+    for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane >> 2, cq = lane & 3;
+        for (int t = 0; t < 3; ++t)
+            for (int c = 0; c < 3; ++c)
+                for (int r = 0; r < 2; ++r)
+                    B->w[(t * 3 + c) * 2 + r][lane] = M.m[(3 * li(g) + t) * 24 + 3 * li(cq + 4 * r) + c];
+    }
+}
+
+// dynamic shared memory of every stencil_tc32_kernel instantiation the V-cycles launch
+template <int MODE, typename BT, typename OT>
+bool stc_smem_attr()
+{
+    return cudaFuncSetAttribute(gf::stencil_tc32_kernel<MODE, BT, OT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(gf::S3Smem)) == cudaSuccess;
+}
+bool stc_smem_attrs()
+{
+    return stc_smem_attr<gf::ST_APPLY, float, float>() && stc_smem_attr<gf::ST_RESID, float, float>() &&
+           stc_smem_attr<gf::ST_SWEEP, float, float>() && stc_smem_attr<gf::ST_RESID, double, float>() &&
+           stc_smem_attr<gf::ST_SWEEP, double, float>() && stc_smem_attr<gf::ST_SWEEP, double, double>();
+}
+
+// Node layers per CTA of stencil_tc32_kernel on a level: the fewest element layers per
+// SM slot over whole waves (each CTA computes cz + 1 element layers for cz node layers).
+int stc_layers(const Level& L, int slots)
+{
+    const long long txy = (long long)((L.nx + 1 + gf::S3_NX - 1) / gf::S3_NX) * ((L.ny + 1 + gf::S3_NY - 1) / gf::S3_NY);
+    const int NZ = L.nz + 1;
+    int best = 4;
+    long long best_cost = -1;
+    for (int cz = 4; cz <= 16; ++cz) {
+        const long long ctas = txy * ((NZ + cz - 1) / cz);
+        const long long cost = ((ctas + slots - 1) / slots) * (cz + 1);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = cz;
+        }
+    }
+    return best;
+}
+
 void build_tc_bfrag(const gf::MParam& M, gf::TcBFrag* B)
 {
     auto orig = [](int qp) {   // original DOF index 3 a + comp of q'
@@ -1050,7 +1109,7 @@ void build_tc_bfrag(const gf::MParam& M, gf::TcBFrag* B)
             for (int ks = 0; ks < 2; ++ks)
                 for (int r = 0; r < 2; ++r) {
                     const int j0 = 16 * ks + 8 * r + 2 * c;
-                    B->w[lane][4 * t + 2 * ks + r] = mp(ip, j0) | (mp(ip, j0 + 1) << 16);
+                    B->w[4 * t + 2 * ks + r][lane] = mp(ip, j0) | (mp(ip, j0 + 1) << 16);
                 }
         }
     }
@@ -1109,7 +1168,11 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         }
     }
     if (g->has_split) {
-        build_tc_bfrag(g->Msplit, &g->Btc);
+        gf::TcBFrag hb;
+        build_tc_bfrag(g->Msplit, &hb);
+        if (int r0 = allocT(&g->Btc, 1)) return fail(r0);
+        if (cudaMemcpy(g->Btc, &hb, sizeof(hb), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(set_err(GF_ERR_CUDA, "B fragments of the tensor-core split kernel"));
         // tensor cores when the grid gives every SM a CTA (fewer CTAs leave the kernel
         // latency-bound and the CUDA-core one is faster: 35 vs 13 us at 16x8x8, 8 CTAs);
         // GF_SPLIT_TC=1 / 0 forces either
@@ -1144,6 +1207,23 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         g->lv.push_back(L);
     }
     g->nc = (int)g->lv.back().ndof;
+    // FP32 level stencils on the tensor cores (opt-in, GF_STENCIL_TC=1, when K0 has its
+    // small-integer form): parity-tested, but slower than the CUDA-core kernel on B300
+    // (17.0 vs 14.4 us at 96x48x48, 86 vs 74 us at 192x96x96; each element layer of a CTA
+    // spends ~1.8k cycles on TF32 mma.sync and ~400 B of shared-memory traffic per element)
+    const char* stc_env = getenv("GF_STENCIL_TC");
+    if (g->has_split && stc_env && stc_env[0] != '0') {
+        gf::S3BFrag hb;
+        build_s3_bfrag(g->Msplit, &hb);
+        int occ = 0;
+        if (int r0 = allocT(&g->B3, 1)) return fail(r0);
+        if (cudaMemcpy(g->B3, &hb, sizeof(hb), cudaMemcpyHostToDevice) != cudaSuccess || !stc_smem_attrs() ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gf::stencil_tc32_kernel<gf::ST_SWEEP, double, float>,
+                                                          gf::S3_THREADS, sizeof(gf::S3Smem)) != cudaSuccess ||
+            occ < 1)
+            return fail(set_err(GF_ERR_CUDA, "set-up of the tensor-core stencil"));
+        for (int l = 0; l < levels; ++l) g->stc_cz[l] = stc_layers(g->lv[l], occ * g->sms);
+    }
     // Opt-in (GF_VC_CLUSTER=<max nodes>): the cluster kernel takes the levels from the
     // first one (>= 1) with at most that many nodes, when at least one smoothing level
     // lies above the coarsest. Off by default: in graph-replayed solves the per-level
@@ -1197,6 +1277,8 @@ int gf_destroy_grid(gf_grid* g)
     cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Vd); cudaFree(g->pdd); cudaFree(g->ddticket); cudaFree(g->Z); cudaFree(g->hist);
     cudaFree(g->xsave);
     cudaFree(g->Edf);
+    cudaFree(g->B3);
+    cudaFree(g->Btc);
     cudaFree(g->oc_rho); cudaFree(g->oc_dc); cudaFree(g->oc_dcx); cudaFree(g->oc_dvx); cudaFree(g->oc_ones);
     cudaFree(g->oc_st);
     if (g->host_status) cudaFreeHost(g->host_status);

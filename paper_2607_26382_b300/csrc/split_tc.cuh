@@ -41,7 +41,7 @@ constexpr int TC_SLOT_WORDS = TC_K * 3 * TC_WY * TC_PAIRS + 8;
 constexpr int TC_THREADS = 32 * TC_EY;
 
 struct TcBFrag {
-    unsigned int w[32][12];   // per lane: [t = out comp][kstep][2] packed half2 of M' (see below)
+    unsigned int w[12][32];   // [t = out comp][kstep][2] packed half2 of M', by lane (device memory)
 };
 
 // Shared-memory layout (dynamic): two digit slots, two element-result layers.
@@ -91,7 +91,7 @@ __device__ __forceinline__ void tc_digits(long long b, int xmax, unsigned short 
 template <bool DD>
 __global__ void __launch_bounds__(TC_THREADS, 3)
 apply_split_tc_kernel(const double* __restrict__ u, double* __restrict__ y, float2* __restrict__ yd,
-                      const float2* __restrict__ Edf, GridDims d, const __grid_constant__ TcBFrag B,
+                      const float2* __restrict__ Edf, GridDims d, const TcBFrag* __restrict__ B,
                       const int* __restrict__ halt)
 {
     if (halt != nullptr && *halt != 0) return;
@@ -104,7 +104,8 @@ apply_split_tc_kernel(const double* __restrict__ u, double* __restrict__ y, floa
     const int kz1 = min(kz0 + TC_CZ, NZ);                                 // one past the last
 
     // ---- region exponent: node window x layers kz0-1 .. kz1 (free nodes only)
-    for (int q = tid; q < 12 * 32; q += TC_THREADS) S.bfrag[q / 32][q % 32] = B.w[q % 32][q / 32];
+    // (lane-indexed reads of a kernel parameter would serialise in the constant cache)
+    for (int q = tid; q < 12 * 32; q += TC_THREADS) S.bfrag[q / 32][q % 32] = B->w[q / 32][q % 32];
     int emax = 0;
     {
         // only the high words (sign, exponent) are read, 9 in flight per thread

@@ -147,6 +147,67 @@ def test_vcycle_mixed_parity(gf):
     assert relerr(host(z), O.vcycle(H, v)) <= 1e-4
 
 
+# ------------------------------------------------- FP32 stencil on the tensor cores --
+# GF_STENCIL_TC=1 runs every FP32 level stencil as stencil_tc32_kernel (3xTF32 element
+# products); 0 keeps the CUDA-core kernel. Grids span several 16x8-element tiles in x
+# and y, ragged tiles, and z chunks of 4..16 node layers with a ragged last chunk.
+TC_GRIDS = [(16, 8, 8, 3), (24, 10, 6, 2), (2, 2, 2, 1), (1, 2, 2, 1), (38, 6, 4, 2), (52, 24, 20, 3)]
+
+
+@pytest.mark.parametrize("nx,ny,nz,L", TC_GRIDS)
+def test_apply_K_f32_tensor_core_parity(gf, nx, ny, nz, L, monkeypatch):
+    monkeypatch.setenv("GF_STENCIL_TC", "1")
+    g, m, rho = make(gf, nx, ny, nz, L, seed=3)
+    monkeypatch.setenv("GF_STENCIL_TC", "0")
+    g0, _, _ = make(gf, nx, ny, nz, L, seed=3)
+    u = synth.random_vector(m.n_dof, 5).astype(np.float32)
+    y, y0 = (torch.full((g.n_dof,), np.nan, dtype=torch.float32, device="cuda") for _ in range(2))
+    g.apply_K_f32(dev(u, torch.float32), y)
+    g0.apply_K_f32(dev(u, torch.float32), y0)
+    E = O.young_modulus(bf16_round(rho), 1e-3, 3.0)
+    ref = O.apply_K(m, E, O.element_stiffness(), u.astype(np.float64))
+    got = host(y)
+    assert relerr(got, ref) <= 2e-5
+    assert np.all(got[m.fixed] == 0.0)
+    # within 3xTF32 rounding of the CUDA-core kernel, and not the same kernel
+    absref = O.apply_K(m, E, np.abs(O.element_stiffness()), np.abs(u.astype(np.float64)))
+    assert np.linalg.norm(got - host(y0)) <= 2e-6 * np.linalg.norm(absref)
+    if m.n_dof > 3000:
+        assert not np.array_equal(got, host(y0))
+
+
+@pytest.mark.parametrize("nx,ny,nz,L", [(16, 8, 8, 3), (52, 24, 20, 3)])
+def test_vcycle_mixed_tensor_core_parity(gf, nx, ny, nz, L, monkeypatch):
+    monkeypatch.setenv("GF_STENCIL_TC", "1")
+    g, m, rho = make(gf, nx, ny, nz, L, seed=2)
+    E16 = O.young_modulus(bf16_round(rho), 1e-3, 3.0)
+    H64 = O.build_hierarchy(m, O.young_modulus(rho, 1e-3, 3.0), L)
+    v = np.where(m.fixed, 0, synth.random_vector(m.n_dof, 9))
+    for nu in (1, 2, 3):
+        H = O.build_hierarchy(m, E16, L, nu1=nu, nu2=nu)
+        H.levels[-1].chol = H64.levels[-1].chol
+        z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        g.vcycle(dev(v), z, gf.GF_MIXED, nu1=nu, nu2=nu)
+        assert relerr(host(z), O.vcycle(H, v)) <= 1e-4
+
+
+def test_solve_mixed_tensor_core_stencil(gf, monkeypatch):
+    # the mixed solve with every FP32 stencil on the tensor cores reaches the FP64
+    # oracle's iteration count (within one) and an accepted true residual
+    nx, ny, nz, L = 16, 8, 8, 3
+    res = {}
+    for tc in ("1", "0"):
+        monkeypatch.setenv("GF_STENCIL_TC", tc)
+        g, m, rho = make(gf, nx, ny, nz, L, seed=4, rho_min=1e-6, kind="uniform")
+        f = O.cantilever_load(m)
+        u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        res[tc] = (g.solve(dev(f), u, prec=gf.GF_MIXED, outer=2), host(u))
+    a, b = res["1"][0], res["0"][0]
+    assert a["flag"] == b["flag"] == gf.GF_FLAG_CONVERGED and abs(a["iters"] - b["iters"]) <= 1
+    E = O.young_modulus(rho, 1e-6, 3.0)
+    assert O.true_residual(m, E, O.element_stiffness(), f, res["1"][1]) <= 1.5e-6
+
+
 # ------------------------------------------------------------- Chebyshev smoother --
 @pytest.mark.parametrize("nx,ny,nz,L", [(16, 8, 8, 3), (24, 10, 6, 2), (8, 4, 4, 3)])
 def test_chebyshev_lambda_and_vcycle_fp64_parity(gf, nx, ny, nz, L):
