@@ -196,7 +196,7 @@ def profiled_traffic(profile, source, start, end):
 
 
 # kernel text spans hashed for the traffic figures
-FP64_KU_SPAN = ("stencil.cuh", "template <typename T, typename ET, int MODE, typename BT", "// First smoothing sweep")
+FP64_KU_SPAN = ("stencil.cuh", "// (i, j, k) of node n", "// First smoothing sweep")
 FP32_ST_SPAN = FP64_KU_SPAN                # one templated per-node body serves both
 SPLIT_KU_SPAN = ("split_tc.cuh", "template <bool DD>", "}  // namespace gf")
 

@@ -1144,6 +1144,7 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     if (cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
         return fail(set_err(GF_ERR_CUDA, "SM count"));
     g->nodes = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+    if (g->nodes >= (1LL << 31)) return fail(set_err(GF_ERR_ARG, "grid of 2^31 nodes or more"));
     g->ndof = 3 * g->nodes;
     g->nel = (long long)nx * ny * nz;
     double K[576];

@@ -33,11 +33,14 @@ struct GridDims {
     int nx, ny, nz;   // elements per axis
 };
 
+// (i, j, k) of node n = i + NX (j + NY k). Grids hold fewer than 2^31 nodes
+// (gf_create_grid checks), so 32-bit unsigned division suffices.
 __device__ __forceinline__ void node_coords(long long n, int NX, int NY, int& i, int& j, int& k) {
-    i = (int)(n % NX);
-    long long t = n / NX;
-    j = (int)(t % NY);
-    k = (int)(t / NY);
+    const unsigned u = (unsigned)n;
+    const unsigned t = u / (unsigned)NX;
+    i = (int)(u - t * (unsigned)NX);
+    j = (int)(t % (unsigned)NY);
+    k = (int)(t / (unsigned)NY);
 }
 
 // MODE == ST_APPLY: out = K x
