@@ -22,6 +22,8 @@ Every function is in FP64 and names the passage it follows (paper arXiv
   counts", Table "residual-semantics", Sec. 3.5 "Why a flexible Krylov method"
 * probe features r50/r100 and trigger rule .............. Sec. 3.4, Eq. (trigger)
 * guarded policy ........................................ Algorithm 1 (floor_policy)
+* true-residual checks during the probe, their detector . Sec. 4.1.1 (the checkpointed
+  variant the paper leaves untested; the detector is a reading, see below)
 * compliance and sensitivity ............................ Sec. 3.1 (after Eq. projection)
 
 Readings where the paper is silent (the CUDA side takes the same ones):
@@ -37,6 +39,10 @@ Chebyshev smoothing (optional): Chebyshev semi-iteration of degree nu1 / nu2 on
 D_b^{-1} K over [lambda_max / 30, 1.1 lambda_max], D_b the same 3x3 node blocks;
 lambda_max of each level from 15 power iterations started from the all-ones vector
 on free DOFs.
+True-residual checks (optional): every c steps of the probe the current iterate is
+formed as at a cycle end and its guard residual recomputed; the detector fires when
+one exceeds ratio (default 10) times the projected estimate of the same step, and a
+firing detector escalates like Eq. (trigger).
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, invariants, brute force on tiny grids, paper values). None is
@@ -477,11 +483,13 @@ class SolveResult:
     iters: int
     flag: int
     stop_estimate: float
+    checks: list = field(default_factory=list)   # (k, history[k], recomputed eta_k) per true-residual check
 
 
 def fgmres(apply_A, precond, f: np.ndarray, restart: int = 30, kmax: int = 200,
            tol: float = 1e-6, x0: np.ndarray | None = None,
-           breakdown_rtol: float = 1e-14) -> SolveResult:
+           breakdown_rtol: float = 1e-14, check_every: int = 0, check_upto: int = 0,
+           true_res=None) -> SolveResult:
     """Flexible GMRES (Saad 1993) preconditioned on the right, restarted every `restart` steps.
 
     History semantics (Table residual-semantics): at the start of every cycle the
@@ -489,10 +497,17 @@ def fgmres(apply_A, precond, f: np.ndarray, restart: int = 30, kmax: int = 200,
     within the cycle each Arnoldi step k records the Givens-projected estimate
     |g_{j+1}| / ||f||. The solver stops when the recorded value is <= tol
     (converged), at k = kmax, or on breakdown.
+
+    True-residual checks (the periodic checkpoints Sec. 4.1.1 names as untested): with
+    check_every = c > 0, after every step k with k % c == 0 and k <= check_upto that
+    does not end the solve, the iterate x_k = x + Z_J y_J (y_J from the current
+    triangular system, as at a cycle end) is formed and eta_k = true_res(x_k) (default
+    ||f - A x_k|| / ||f||) recorded beside history[k]. The solve itself is unchanged.
     """
     fnorm = float(np.linalg.norm(f))
     x = np.zeros_like(f) if x0 is None else x0.astype(np.float64).copy()
     hist = {}
+    checks = []
     k = 0
     flag = MAX_ITERS
     while True:
@@ -558,6 +573,13 @@ def fgmres(apply_A, precond, f: np.ndarray, restart: int = 30, kmax: int = 200,
             if hnext <= breakdown_rtol * w_norm0:
                 stop = BREAKDOWN
                 break
+            if check_every > 0 and k % check_every == 0 and k <= check_upto:
+                yk = sla.solve_triangular(Hm[:J, :J], g[:J], lower=False)
+                xk = x.copy()
+                for i in range(J):
+                    xk = xk + yk[i] * Z[i]
+                eta = true_res(xk) if true_res is not None else float(np.linalg.norm(f - apply_A(xk))) / fnorm
+                checks.append((k, hist[k], eta))
             V.append(w / hnext)
         if J > 0:
             y = sla.solve_triangular(Hm[:J, :J], g[:J], lower=False)
@@ -567,7 +589,7 @@ def fgmres(apply_A, precond, f: np.ndarray, restart: int = 30, kmax: int = 200,
             flag = stop
             break
     history = np.array([hist[i] for i in range(k + 1)])
-    return SolveResult(x=x, history=history, iters=k, flag=flag, stop_estimate=float(history[k]))
+    return SolveResult(x=x, history=history, iters=k, flag=flag, stop_estimate=float(history[k]), checks=checks)
 
 
 # ----------------------------------------------------------------------------
@@ -604,6 +626,14 @@ def trigger_rule(r50: float, r100: float, th: Thresholds = Thresholds()) -> bool
     return (r50 >= th.r50_escalate) or (r100 >= th.r100_stall and r100 / r50 >= th.plateau_ratio)
 
 
+def true_check_detector(checks, ratio: float) -> bool:
+    """The checkpointed detector (our reading of the variant Sec. 4.1.1 leaves untested):
+    it fires when a recomputed true residual exceeds ratio times the projected estimate
+    recorded at the same step, i.e. the estimate the probe features are read from no
+    longer tracks the residual the guard will measure."""
+    return any(eta > ratio * est for (_, est, eta) in checks)
+
+
 def candidate_floors(escalate: bool, rho0: float, ladder):
     """Algorithm 1: C = ladder if the rule fires, else (rho0, ladder) in order."""
     return list(ladder) if escalate else [rho0] + list(ladder)
@@ -631,6 +661,8 @@ class SelectResult:
     escalated: bool
     attempts: list
     probe_iters_run: int = 0
+    checks: list = field(default_factory=list)   # the probe's true-residual checks
+    detector: bool = False                       # true_check_detector fired
 
 
 @dataclass
@@ -648,21 +680,25 @@ class SolverSetup:
     smoother: str = "jacobi"
 
 
-def solve_at_floor(setup: SolverSetup, f: np.ndarray, rho_min: float, kmax: int, tol: float):
-    """Frozen-state solve K(rho_min) u = f with GMG-preconditioned FGMRES from u0 = 0."""
+def solve_at_floor(setup: SolverSetup, f: np.ndarray, rho_min: float, kmax: int, tol: float,
+                   check_every: int = 0, check_upto: int = 0):
+    """Frozen-state solve K(rho_min) u = f with GMG-preconditioned FGMRES from u0 = 0
+    (with check_every > 0: true-residual checks, the guard's eta, up to step check_upto)."""
     mesh = setup.mesh
     E = young_modulus(setup.rho_hat, rho_min, setup.p)
     H = build_hierarchy(mesh, E, setup.n_levels, setup.nu, setup.nu1, setup.nu2, setup.omega, setup.smoother)
     K0 = H.levels[0].K0
     fm = np.where(mesh.fixed, 0.0, f)
     res = fgmres(lambda v: apply_K(mesh, E, K0, v), lambda v: vcycle(H, v), fm,
-                 restart=setup.restart, kmax=kmax, tol=tol)
+                 restart=setup.restart, kmax=kmax, tol=tol, check_every=check_every, check_upto=check_upto,
+                 true_res=lambda x: true_residual(mesh, E, K0, f, x))
     return res, E, K0
 
 
 def guarded_policy(probe_fn, attempt_fn, rho0: float, ladder, tau: float = 1e-6,
                    kmax: int = 200, probe_iters: int = 100, th: Thresholds = Thresholds(),
-                   selector: str = "rule", first_index: int | None = None) -> SelectResult:
+                   selector: str = "rule", first_index: int | None = None,
+                   true_check_ratio: float | None = None) -> SelectResult:
     """Algorithm 1 as pure control logic.
 
     probe_fn(rho0, iters) -> SolveResult of the probe solve (history used for r50/r100);
@@ -675,6 +711,10 @@ def guarded_policy(probe_fn, attempt_fn, rho0: float, ladder, tau: float = 1e-6,
     paper names for the optimisation loop and leaves untested: attempt the previous
     decision, ``first_index``, with no probe; if the guard rejects it, run "rule" from
     scratch, the rejected attempt recorded first). Floor indices refer to (rho0, ladder...).
+
+    true_check_ratio (rule selector): when given, the probe's true-residual checks
+    (probe.checks) also escalate if true_check_detector fires (our reading of the
+    checkpointed detector variant of Sec. 4.1.1).
     """
     floors = [rho0] + list(ladder)
     if selector == "reuse":
@@ -683,17 +723,21 @@ def guarded_policy(probe_fn, attempt_fn, rho0: float, ladder, tau: float = 1e-6,
         if eta <= tau:
             return SelectResult(ACCEPTED, int(first_index), floors[int(first_index)], res.x, eta,
                                 float("nan"), float("nan"), int(first_index) > 0, [first], 0)
-        out = guarded_policy(probe_fn, attempt_fn, rho0, ladder, tau, kmax, probe_iters, th, "rule")
+        out = guarded_policy(probe_fn, attempt_fn, rho0, ladder, tau, kmax, probe_iters, th, "rule",
+                             true_check_ratio=true_check_ratio)
         out.attempts = [first] + out.attempts
         return out
     r50 = r100 = float("nan")
     escalated = False
     probe_k = 0
+    checks, detector = [], False
     if selector == "rule":
         probe = probe_fn(rho0, probe_iters)
         probe_k = probe.iters
         r50, r100 = probe_features(probe.history, probe.iters, th)
-        escalated = trigger_rule(r50, r100, th)
+        checks = list(probe.checks)
+        detector = true_check_ratio is not None and true_check_detector(checks, true_check_ratio)
+        escalated = trigger_rule(r50, r100, th) or detector
         cand = candidate_floors(escalated, rho0, ladder)
         start = 1 if escalated else 0
     elif selector == "full":
@@ -711,25 +755,27 @@ def guarded_policy(probe_fn, attempt_fn, rho0: float, ladder, tau: float = 1e-6,
         attempts.append(Attempt(rm, res.iters, res.flag, res.stop_estimate, eta, ok))
         if ok:
             return SelectResult(ACCEPTED, start + idx, rm, res.x, eta, r50, r100, escalated, attempts,
-                                probe_k)
+                                probe_k, checks, detector)
     return SelectResult(NO_ADMISSIBLE_FLOOR, -1, float("nan"), None, float("nan"), r50, r100,
-                        escalated, attempts, probe_k)
+                        escalated, attempts, probe_k, checks, detector)
 
 
 def select_floor(setup: SolverSetup, f: np.ndarray, rho0: float, ladder, tau: float = 1e-6,
                  kmax: int = 200, probe_iters: int = 100, th: Thresholds = Thresholds(),
-                 selector: str = "rule", first_index: int | None = None) -> SelectResult:
-    """Algorithm 1 on a frozen state: GMG-FGMRES solves plus the FP64 acceptance guard."""
+                 selector: str = "rule", first_index: int | None = None,
+                 true_check_every: int = 0, true_check_ratio: float = 10.0) -> SelectResult:
+    """Algorithm 1 on a frozen state: GMG-FGMRES solves plus the FP64 acceptance guard
+    (with true_check_every > 0: the probe's true-residual checks and their detector)."""
 
     def probe_fn(rm, iters):
-        return solve_at_floor(setup, f, rm, iters, tau)[0]
+        return solve_at_floor(setup, f, rm, iters, tau, true_check_every, iters)[0]
 
     def attempt_fn(rm, km):
         res, E, K0 = solve_at_floor(setup, f, rm, km, tau)
         return res, true_residual(setup.mesh, E, K0, f, res.x)
 
     return guarded_policy(probe_fn, attempt_fn, rho0, ladder, tau, kmax, probe_iters, th,
-                          selector, first_index)
+                          selector, first_index, true_check_ratio if true_check_every > 0 else None)
 
 
 # ----------------------------------------------------------------------------

@@ -328,6 +328,69 @@ def test_fgmres_projected_estimate_equals_true_residual_each_step():
     assert full.history[0] == 1.0
 
 
+def test_true_residual_checks_leave_the_solve_unchanged_and_match_the_estimate():
+    """Checks every 4 steps: taken only at steps that do not end the solve, the solve
+    itself unchanged, and (right-preconditioned FGMRES with stored Z) the recomputed
+    residual of the step's iterate equals the projected estimate up to rounding."""
+    m, E, H = _hier(seed=2)
+    K0 = H.levels[0].K0
+    f = O.cantilever_load(m)
+    A = lambda v: O.apply_K(m, E, K0, v)
+    B = lambda v: O.vcycle(H, v)
+    plain = O.fgmres(A, B, f, restart=6, kmax=20, tol=1e-14)
+    chk = O.fgmres(A, B, f, restart=6, kmax=20, tol=1e-14, check_every=4, check_upto=20)
+    assert np.array_equal(plain.history, chk.history) and np.array_equal(plain.x, chk.x)
+    assert plain.checks == [] and [c[0] for c in chk.checks] == [4, 8, 12, 16]   # step 20 ends the solve
+    for k, est, eta in chk.checks:
+        if k % 6:
+            assert est == plain.history[k]       # restart boundaries later hold the true residual
+        assert abs(eta - est) <= 1e-9 * eta
+    assert O.fgmres(A, B, f, restart=6, kmax=20, tol=1e-14, check_every=4, check_upto=9).checks[-1][0] == 8
+
+
+def test_true_residual_check_detector_fires_on_an_operator_mismatch():
+    """A planted mismatch: the solver's operator is (1+delta) A while the check recomputes
+    with A. Then f - A x_k = (delta f + r_k) / (1+delta) with r_k the solver's residual, so
+    |eta_k - delta/(1+delta)| <= est_k/(1+delta) at every check (triangle inequality), and
+    the detector fires once the estimate drops below the plateau by the ratio."""
+    d = np.linspace(1.0, 10.0, 40)
+    f = np.ones(40)
+    delta = 1e-3
+    res = O.fgmres(lambda v: (1 + delta) * d * v, lambda v: v, f, restart=50, kmax=39, tol=1e-15,
+                   check_every=3, check_upto=39,
+                   true_res=lambda x: float(np.linalg.norm(f - d * x) / np.linalg.norm(f)))
+    assert len(res.checks) >= 8
+    for _, est, eta in res.checks:
+        assert abs(eta - delta / (1 + delta)) <= est / (1 + delta) + 1e-13
+    fired = [eta > 10 * est for _, est, eta in res.checks]
+    assert not fired[0] and fired[-1]
+    assert O.true_check_detector(res.checks, 10.0)
+    assert not O.true_check_detector(res.checks, 1e30)
+
+
+def test_true_check_detector_boundary_and_policy():
+    assert not O.true_check_detector([(5, 1e-4, 1e-3)], 10.0)        # equal: does not fire
+    assert O.true_check_detector([(5, 1e-4, 1.0000001e-3)], 10.0)
+    assert not O.true_check_detector([], 10.0)
+    ladder = [1e-5, 1e-4, 1e-3]
+    hist = np.geomspace(1.0, 1e-6, 101)                               # Eq. (trigger) preserves rho0
+
+    class Probe(_Fake):
+        def probe(self, rm, iters):
+            r = super().probe(rm, iters)
+            r.checks = [(25, 1e-2, 1e-2), (50, 1e-3, 5e-2)]           # second check: 50x the estimate
+            return r
+    fk = Probe({1e-6: 1e-7, 1e-5: 1e-7, 1e-4: 1e-7, 1e-3: 1e-7}, hist)
+    r = O.guarded_policy(fk.probe, fk.attempt, 1e-6, ladder, true_check_ratio=10.0)
+    assert r.detector and r.escalated and fk.calls == [1e-5] and r.floor_index == 1 and len(r.checks) == 2
+    fk = Probe({1e-6: 1e-7, 1e-5: 1e-7, 1e-4: 1e-7, 1e-3: 1e-7}, hist)
+    r = O.guarded_policy(fk.probe, fk.attempt, 1e-6, ladder)          # detector off
+    assert not r.detector and not r.escalated and fk.calls == [1e-6] and r.floor_index == 0
+    fk = Probe({1e-6: 1e-7, 1e-5: 1e-7, 1e-4: 1e-7, 1e-3: 1e-7}, hist)
+    r = O.guarded_policy(fk.probe, fk.attempt, 1e-6, ladder, true_check_ratio=100.0)
+    assert not r.detector and fk.calls == [1e-6]
+
+
 def test_fgmres_equals_independent_right_preconditioned_gmres():
     """With a fixed linear preconditioner FGMRES coincides with right-preconditioned GMRES
     (Sec. 4.5.3): residual = min over the Krylov space K_k(K B, f), computed here from an
