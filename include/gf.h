@@ -75,6 +75,7 @@ extern "C" {
                              Requires n_ladder <= GF_MAX_LADDER-1; single grid only. */
 
 #define GF_MAX_LADDER 8
+#define GF_MAX_TRUE_CHECKS 16   /* true-residual checks recorded per probe */
 
 typedef struct gf_grid gf_grid;
 typedef struct gf_mlp gf_mlp;
@@ -130,6 +131,17 @@ typedef struct {
                                           P(first admissible floor >= k) >= c (k = 0 always
                                           qualifies), so the selector skips a floor only
                                           when confident that it fails */
+    int    true_check_every;           /* GF_SEL_RULE (and GF_SEL_REUSE's fallback): 0 = off; c > 0 =
+                                          true-residual checks during the probe, the checkpointed
+                                          variant Sec. 4.1.1 leaves untested. After every probe step
+                                          k with k % c == 0 that does not end the solve, the iterate
+                                          is formed as at a cycle end and its FP64 guard residual
+                                          eta_k recomputed beside the projected estimate history[k].
+                                          probe_iters / c <= GF_MAX_TRUE_CHECKS. The solve itself is
+                                          unchanged. */
+    double true_check_ratio;           /* detector (this library's reading): fires when some
+                                          eta_k > ratio * history[k]; a firing detector escalates
+                                          like Eq. (trigger). Default 10. */
 } gf_policy;
 
 typedef struct {
@@ -151,6 +163,11 @@ typedef struct {
     int    probe_iters_run;
     int    n_attempts;
     gf_attempt attempts[GF_MAX_LADDER + 1];
+    int    n_true_checks;                        /* probe true-residual checks taken */
+    int    true_check_k[GF_MAX_TRUE_CHECKS];     /* their steps */
+    double true_check_est[GF_MAX_TRUE_CHECKS];   /* projected estimate history[k] */
+    double true_check_eta[GF_MAX_TRUE_CHECKS];   /* recomputed FP64 guard residual of the step's iterate */
+    int    true_check_fired;                     /* the detector escalated (1) or not (0) */
 } gf_select_info;
 
 typedef struct {

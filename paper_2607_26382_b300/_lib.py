@@ -22,6 +22,7 @@ GF_ACCEPTED, GF_NO_ADMISSIBLE_FLOOR = 0, 1
 GF_SEL_RULE, GF_SEL_FULL, GF_SEL_GIVEN, GF_SEL_MLP, GF_SEL_REUSE = 0, 1, 2, 3, 4
 MLP_PARAMS = 1412
 GF_MAX_LADDER = 8
+GF_MAX_TRUE_CHECKS = 16
 
 ERRORS = {-1: "GF_ERR_ARG", -2: "GF_ERR_OOM", -3: "GF_ERR_CUDA", -4: "GF_ERR_NONFINITE",
           -5: "GF_ERR_TIMEOUT", -6: "GF_ERR_STATE"}
@@ -61,7 +62,7 @@ class Policy(ctypes.Structure):
                 ("r50_escalate", c_double), ("r100_stall", c_double), ("plateau_ratio", c_double),
                 ("checkpoint_a", c_int), ("checkpoint_b", c_int), ("selector", c_int),
                 ("first_index", c_int), ("fuse_probe", c_int), ("solve", SolveOpts), ("mlp", c_void_p),
-                ("mlp_confidence", c_double)]
+                ("mlp_confidence", c_double), ("true_check_every", c_int), ("true_check_ratio", c_double)]
 
 
 class Attempt(ctypes.Structure):
@@ -72,7 +73,10 @@ class Attempt(ctypes.Structure):
 class SelectInfo(ctypes.Structure):
     _fields_ = [("status", c_int), ("floor_index", c_int), ("rho_min", c_double), ("eta", c_double),
                 ("r50", c_double), ("r100", c_double), ("escalated", c_int), ("probe_iters_run", c_int),
-                ("n_attempts", c_int), ("attempts", Attempt * (GF_MAX_LADDER + 1))]
+                ("n_attempts", c_int), ("attempts", Attempt * (GF_MAX_LADDER + 1)),
+                ("n_true_checks", c_int), ("true_check_k", c_int * GF_MAX_TRUE_CHECKS),
+                ("true_check_est", c_double * GF_MAX_TRUE_CHECKS), ("true_check_eta", c_double * GF_MAX_TRUE_CHECKS),
+                ("true_check_fired", c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -324,13 +328,9 @@ class Grid:
         info = SelectInfo()
         _check(lib().gf_select_floor(self._h, _ptr(f, t, self.n_dof, "f"), _ptr(u, t, self.n_dof, "u"),
                                      ctypes.byref(policy), ctypes.byref(info)))
-        atts = [dict(rho_min=a.rho_min, iters=a.iters, flag=a.flag, stop_estimate=a.stop_estimate,
-                     eta=a.eta, accepted=bool(a.accepted)) for a in info.attempts[:info.n_attempts]]
         if info.status == GF_ACCEPTED:
             self.rho_min = info.rho_min
-        return dict(status=info.status, floor_index=info.floor_index, rho_min=info.rho_min, eta=info.eta,
-                    r50=info.r50, r100=info.r100, escalated=bool(info.escalated),
-                    probe_iters_run=info.probe_iters_run, attempts=atts)
+        return _select_dict(info)
 
     def sensitivity(self, u, dc):
         t = _torch().float64
@@ -412,9 +412,12 @@ def true_residual_noalloc(nx, ny, nz, rho_hat, p, rho_min, f, u, eta, h=1.0, E0=
 def _select_dict(info):
     atts = [dict(rho_min=a.rho_min, iters=a.iters, flag=a.flag, stop_estimate=a.stop_estimate,
                  eta=a.eta, accepted=bool(a.accepted)) for a in info.attempts[:info.n_attempts]]
+    checks = [(info.true_check_k[q], info.true_check_est[q], info.true_check_eta[q])
+              for q in range(info.n_true_checks)]
     return dict(status=info.status, floor_index=info.floor_index, rho_min=info.rho_min, eta=info.eta,
                 r50=info.r50, r100=info.r100, escalated=bool(info.escalated),
-                probe_iters_run=info.probe_iters_run, attempts=atts)
+                probe_iters_run=info.probe_iters_run, attempts=atts, true_checks=checks,
+                true_check_fired=bool(info.true_check_fired))
 
 
 class Batch:

@@ -134,7 +134,8 @@ struct gf_grid {
     int* dflag = nullptr;
     // Krylov workspace
     int m_alloc = 0;
-    double *V = nullptr, *Z = nullptr, *partial = nullptr, *work = nullptr, *xsave = nullptr;
+    double *V = nullptr, *Z = nullptr, *partial = nullptr, *work = nullptr;
+    double* ckx = nullptr;            // iterate of a probe true-residual check
     float2* Vd = nullptr;             // double-float copy of the basis (outer == 2)
     float2* pdd = nullptr;            // per-block partial pairs of the double-float passes
     unsigned int* ddticket = nullptr; // arrival counter of their last-block finish
@@ -861,6 +862,9 @@ int run_step(gf_grid* g, int j, const gf_solve_opts* o)
 // Optional pause after `at` Arnoldi steps: the probe of Algorithm 1 read off the
 // running solve. Because the solver is deterministic, the first `at` steps of the
 // selected solve at rho0 are the probe's steps, bit for bit.
+// Optional true-residual checks during the first `upto` steps (every `every` steps):
+// the iterate of the step (cycle-start iterate plus Z y of the current triangular
+// system) and its FP64 guard residual, beside the projected estimate of the step.
 struct ProbeHook {
     int at = -1;
     const gf_policy* pol = nullptr;
@@ -868,7 +872,31 @@ struct ProbeHook {
     bool decided = false, escalate = false;
     int first = 0, err = GF_OK;
     double r50 = 0.0, r100 = 0.0;
+    int every = 0, upto = 0, n = 0;
+    double ratio = 10.0;
+    int ck[GF_MAX_TRUE_CHECKS];
+    double est[GF_MAX_TRUE_CHECKS], eta[GF_MAX_TRUE_CHECKS];
+    bool fired = false;
 };
+
+int guard_impl(gf_grid* g, const double* f, const double* u, double* eta);
+
+int true_check(gf_grid* g, const double* f, const double* u, ProbeHook* hook, int k)
+{
+    if (!g->ckx) RET(allocT(&g->ckx, g->ndof));
+    LAUNCH(g, 1, 1, gf::backsolve_kernel, g->st);   // y of the current J columns (recomputed at the cycle end)
+    CK(cudaMemcpyAsync(g->ckx, u, sizeof(double) * g->ndof, cudaMemcpyDeviceToDevice, g->stream));
+    LAUNCH(g, 2 * g->sms, 256, gf::update_x_kernel, g->ckx, g->Z, g->ndof, g->ndof, g->st);
+    double eta = 0.0, est = 0.0;
+    RET(guard_impl(g, f, g->ckx, &eta));
+    CK(cudaMemcpy(&est, g->hist + k, sizeof(double), cudaMemcpyDeviceToHost));
+    hook->ck[hook->n] = k;
+    hook->est[hook->n] = est;
+    hook->eta[hook->n] = eta;
+    hook->n++;
+    if (eta > hook->ratio * est) hook->fired = true;
+    return GF_OK;
+}
 
 int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, gf_solve_info* info,
                bool x_zero, double* host_hist, ProbeHook* hook = nullptr)
@@ -894,6 +922,11 @@ int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, g
             RET(run_step(g, j, o));
             ++launched;
             CK(cudaEventRecord(g->ev[j % 3], g->stream));
+            if (hook && hook->every > 0 && launched % hook->every == 0 && launched <= hook->upto &&
+                hook->n < GF_MAX_TRUE_CHECKS) {
+                RET(read_state(g, &hs));
+                if (hs.status == gf::KS_RUN) RET(true_check(g, f, u, hook, (int)launched));
+            }
             if (hook && !hook->decided && launched == hook->at) {
                 RET(read_state(g, &hs));
                 if (hs.status == gf::KS_RUN) {
@@ -1276,7 +1309,7 @@ int gf_destroy_grid(gf_grid* g)
     cudaFree(g->Ainv); cudaFree(g->Agj); cudaFree(g->dflag); cudaFree(g->cheb); cudaFree(g->cheb_ss);
     cudaFree(g->rho64); cudaFree(g->rho16); cudaFree(g->work); cudaFree(g->partial);
     cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Vd); cudaFree(g->pdd); cudaFree(g->ddticket); cudaFree(g->Z); cudaFree(g->hist);
-    cudaFree(g->xsave);
+    cudaFree(g->ckx);
     cudaFree(g->Edf);
     cudaFree(g->B3);
     cudaFree(g->Btc);
@@ -1494,6 +1527,8 @@ void gf_policy_defaults(gf_policy* pol)
     pol->solve.outer = 0;
     pol->mlp = nullptr;
     pol->mlp_confidence = 0.0;
+    pol->true_check_every = 0;
+    pol->true_check_ratio = 10.0;
 }
 
 int gf_trigger_rule(double r50, double r100, const gf_policy* pol)
@@ -1507,6 +1542,19 @@ int gf_probe_features(const double* history, int k_stop, const gf_policy* pol, d
     if (!history || !pol || !r50 || !r100 || k_stop < 0) return set_err(GF_ERR_ARG, "bad argument");
     *r50 = history[std::min(pol->checkpoint_a, k_stop)];
     *r100 = history[std::min(pol->checkpoint_b, k_stop)];
+    return GF_OK;
+}
+
+// true-residual checks: GF_SEL_RULE (also GF_SEL_REUSE's fallback) on one grid
+int validate_true_checks(const gf_policy* pol)
+{
+    if (pol->true_check_every < 0) return set_err(GF_ERR_ARG, "true_check_every < 0");
+    if (pol->true_check_every == 0) return GF_OK;
+    if (pol->selector != GF_SEL_RULE && pol->selector != GF_SEL_REUSE)
+        return set_err(GF_ERR_ARG, "true_check_every needs GF_SEL_RULE or GF_SEL_REUSE");
+    if (pol->probe_iters / pol->true_check_every > GF_MAX_TRUE_CHECKS)
+        return set_err(GF_ERR_ARG, "probe_iters / true_check_every > GF_MAX_TRUE_CHECKS");
+    if (!(pol->true_check_ratio > 0.0)) return set_err(GF_ERR_ARG, "true_check_ratio must be > 0");
     return GF_OK;
 }
 
@@ -1565,10 +1613,12 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
     if (pol->selector == GF_SEL_REUSE) {
         if (pol->n_ladder < 0) return set_err(GF_ERR_ARG, "n_ladder");
         if (!(pol->rho0 > 0) || pol->probe_iters < 0 || pol->kmax < 0) return set_err(GF_ERR_ARG, "policy");
+        RET(validate_true_checks(pol));
         return select_floor_reuse(g, f, u, pol, info);
     }
     if (pol->n_ladder < 0 || pol->n_ladder > GF_MAX_LADDER) return set_err(GF_ERR_ARG, "n_ladder");
     if (!(pol->rho0 > 0) || pol->probe_iters < 0 || pol->kmax < 0) return set_err(GF_ERR_ARG, "policy");
+    RET(validate_true_checks(pol));
     gf_solve_opts o = pol->solve;
     o.history = nullptr;
     o.tol = pol->tau;
@@ -1585,15 +1635,28 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
     const int nf = pol->n_ladder + 1;
     int start = 0;
     if (pol->selector == GF_SEL_MLP && !pol->mlp) return set_err(GF_ERR_ARG, "GF_SEL_MLP needs a trained gf_mlp");
+    ProbeHook hook;   // the fused probe's decision point and the probe's true-residual checks
+    hook.every = pol->true_check_every;
+    hook.upto = pol->probe_iters;
+    hook.ratio = pol->true_check_ratio;
     auto decide = [&](double r50, double r100, int* first) -> int {
         if (pol->selector == GF_SEL_MLP) {
             double x[6];
             RET(gf_select_features(g, r50, r100, x));
             RET(mlp_first_floors(pol->mlp, x, 1, pol->mlp_confidence, nf, first));
-        } else {
-            *first = gf_trigger_rule(r50, r100, pol) ? 1 : 0;
+        } else {   // Eq. (trigger), or the checkpointed detector
+            *first = (gf_trigger_rule(r50, r100, pol) || hook.fired) ? 1 : 0;
         }
         return GF_OK;
+    };
+    auto record_checks = [&]() {
+        info->n_true_checks = hook.n;
+        for (int q = 0; q < hook.n; ++q) {
+            info->true_check_k[q] = hook.ck[q];
+            info->true_check_est[q] = hook.est[q];
+            info->true_check_eta[q] = hook.eta[q];
+        }
+        info->true_check_fired = hook.fired ? 1 : 0;
     };
     if ((pol->selector == GF_SEL_RULE && pol->fuse_probe) || pol->selector == GF_SEL_MLP) {
         // Probe fused with the rho0 solve: run the rho0 solve with budget kmax and read
@@ -1604,7 +1667,6 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
         const bool cap = pol->probe_iters > pol->kmax;   // the probe may run past kmax
         gf_solve_opts so2 = o;
         so2.kmax = pol->kmax;
-        ProbeHook hook;
         hook.at = pol->probe_iters;
         hook.pol = pol;
         hook.decide = decide;
@@ -1622,6 +1684,7 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
             RET(gf_probe_features(hist.data(), si.iters, pol, &info->r50, &info->r100));
             RET(decide(info->r50, info->r100, &start));
         }
+        record_checks();
         info->escalated = start > 0;
         if (!info->escalated && !cap) {
             // the rho0 solve is the first candidate's selected solve
@@ -1650,10 +1713,11 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
         po.kmax = pol->probe_iters;
         gf_solve_info pi{};
         CK(cudaMemsetAsync(u, 0, sizeof(double) * g->ndof, g->stream));
-        RET(solve_impl(g, f, u, &po, &pi, true, hist.data()));
+        RET(solve_impl(g, f, u, &po, &pi, true, hist.data(), &hook));   // hook.at < 0: checks only
         info->probe_iters_run = pi.iters;
         RET(gf_probe_features(hist.data(), pi.iters, pol, &info->r50, &info->r100));
-        info->escalated = gf_trigger_rule(info->r50, info->r100, pol);
+        record_checks();
+        info->escalated = gf_trigger_rule(info->r50, info->r100, pol) || hook.fired;
         start = info->escalated ? 1 : 0;
     } else if (pol->selector == GF_SEL_FULL) {
         start = 0;

@@ -3,6 +3,7 @@
     python -m paper_2607_26382_b300.experiments batch102 [--train 2000]
     python -m paper_2607_26382_b300.experiments oc_loop [--iters 40]
     python -m paper_2607_26382_b300.experiments oc_reuse [--iters 40]
+    python -m paper_2607_26382_b300.experiments true_checks
 
 batch102: 102 frozen states of uneven size (nx in {32,48,64,80}, ny = nz = nx/2,
   round-robin; 71 smoothed-Gaussian states with 40% of voxels at floor, 31
@@ -25,6 +26,11 @@ oc_reuse: the in-loop settings of Section 4.1.2 (rho0 = 1e-12, ladder {1e-3, 1e-
     reuse - Algorithm 1 at iteration 0, then the previous decision without a probe,
             Algorithm 1 again only when the guard rejects it (GF_SEL_REUSE);
     fixed - 1e-3 at every iteration (GF_SEL_GIVEN), still guarded.
+true_checks: the 102 batch102 states one at a time (mixed, outer = 2), Algorithm 1 with
+  and without true-residual checks every 25 probe steps (detector ratio 10), at the
+  workload's floors (rho0 1e-6, ladder {1e-5, 1e-4, 1e-3}) and at the paper's
+  (rho0 1e-12, ladder {1e-3, 1e-2}, kmax 300): detector firings, the largest
+  eta / estimate ratio seen, decisions that change, and the cost.
 """
 from __future__ import annotations
 
@@ -219,13 +225,59 @@ def oc_reuse(args):
     return out
 
 
+def true_checks(args):
+    import torch
+    dims, rhos, kinds = batch_states()
+    out = {"workload": f"{len(dims)} batch102 states one at a time, mixed (outer 2), checks every 25 probe steps, ratio 10"}
+    for tag, base in (("workload floors", dict(rho0=1e-6, ladder=LADDER, kmax=200)),
+                      ("paper floors", dict(rho0=1e-12, ladder=[1e-3, 1e-2], kmax=300))):
+        rec = {}
+        for every in (0, 25):
+            t_total, fired, changed, worst, floors, n_checks = 0.0, 0, 0, 0.0, [], 0
+            steps, rule_esc, rho0_rejected, fired_and_rule = 0, 0, 0, 0
+            for (nx, ny, nz), rho in zip(dims, rhos):
+                g = L.create_grid(nx, ny, nz, levels=4)
+                g.set_density(torch.as_tensor(rho, device="cuda"), 3.0)
+                f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+                g.cantilever_load(f)
+                u = torch.zeros_like(f)
+                pol = _policy(solve_prec=L.GF_MIXED, solve_outer=2, true_check_every=every, true_check_ratio=10.0,
+                              **base)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = g.select_floor(f, u, pol)
+                torch.cuda.synchronize()
+                t_total += time.perf_counter() - t0
+                floors.append(r["floor_index"])
+                fired += int(r["true_check_fired"])
+                steps += sum(a["iters"] for a in r["attempts"])
+                tr = L.trigger_rule(r["r50"], r["r100"], pol)
+                rule_esc += int(tr)
+                fired_and_rule += int(tr and r["true_check_fired"])
+                rho0_rejected += int(any(a["rho_min"] == base["rho0"] and not a["accepted"] for a in r["attempts"]))
+                n_checks += len(r["true_checks"])
+                for _, est, eta in r["true_checks"]:
+                    worst = max(worst, eta / est)
+                g.close()
+            rec[f"every {every}"] = {"seconds": t_total, "guarded_solves_per_s": len(dims) / t_total,
+                                     "detector_fired": fired, "rule_escalated": rule_esc,
+                                     "fired_where_rule_escalated": fired_and_rule,
+                                     "rho0_solved_and_rejected_by_guard": rho0_rejected, "arnoldi_steps": steps,
+                                     "checks": n_checks, "max_eta_over_estimate": worst, "floors": floors}
+        a, b = rec["every 0"]["floors"], rec["every 25"]["floors"]
+        rec["decisions_changed"] = sum(x != y for x, y in zip(a, b))
+        rec["overhead"] = rec["every 25"]["seconds"] / rec["every 0"]["seconds"] - 1.0
+        out[tag] = rec
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch102", "oc_loop", "oc_reuse"])
+    ap.add_argument("what", choices=["batch102", "oc_loop", "oc_reuse", "true_checks"])
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--iters", type=int, default=40)
     a = ap.parse_args(argv)
-    res = {"batch102": batch102, "oc_loop": oc_loop, "oc_reuse": oc_reuse}[a.what](a)
+    res = {"batch102": batch102, "oc_loop": oc_loop, "oc_reuse": oc_reuse, "true_checks": true_checks}[a.what](a)
     print(json.dumps(res), flush=True)
     return 0
 

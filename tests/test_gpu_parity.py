@@ -420,6 +420,67 @@ def test_reuse_selector_matches_oracle(gf, seed, q, first):
         assert O.true_residual(m, E, O.element_stiffness(), f, host(u)) <= 1e-6 * (1 + 1e-9)
 
 
+# Periodic true-residual checks during the probe and their detector (Sec. 4.1.1's
+# untested checkpointed variant; the detector rule is a reading). ratio 10: the estimate
+# tracks the residual, nothing fires; ratio 0.5: every check fires, the probe escalates.
+@pytest.mark.parametrize("fuse", [1, 0])
+@pytest.mark.parametrize("ratio", [10.0, 0.5])
+def test_true_checks_match_oracle(gf, ratio, fuse):
+    nx, ny, nz = 16, 8, 8
+    m = O.Mesh(nx, ny, nz)
+    rho = synth.bernoulli_density(nx, ny, nz, 43, 0.35)
+    f = O.cantilever_load(m)
+    ladder = [1e-5, 1e-4, 1e-3]
+    ref = O.select_floor(O.SolverSetup(m, rho, p=3.0, n_levels=3), f, 1e-8, ladder, kmax=120,
+                         probe_iters=60, true_check_every=7, true_check_ratio=ratio)
+    g = gf.create_grid(nx, ny, nz, levels=3)
+    g.set_density(dev(rho), 3.0)
+    pol = gf.policy_defaults(rho0=1e-8, ladder=ladder, kmax=120, probe_iters=60, true_check_every=7,
+                             true_check_ratio=ratio, fuse_probe=fuse, solve_prec=gf.GF_FP64)
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    out = g.select_floor(dev(f), u, pol)
+    assert [c[0] for c in out["true_checks"]] == [c[0] for c in ref.checks] and len(ref.checks) >= 3
+    for (k, est, eta), (_, est_r, eta_r) in zip(out["true_checks"], ref.checks):
+        assert abs(est - est_r) <= 1e-6 * est_r and abs(eta - eta_r) <= 1e-6 * eta_r
+    assert out["true_check_fired"] == ref.detector == (ratio < 1)
+    assert out["escalated"] == ref.escalated and out["floor_index"] == ref.floor_index
+    assert [(a["rho_min"], bool(a["accepted"])) for a in out["attempts"]] == \
+        [(a.rho_min, bool(a.accepted)) for a in ref.attempts]
+
+
+def test_true_checks_leave_the_solve_unchanged(gf):
+    """Checks only read the state: the accepted iterate is bit-identical with and without them."""
+    nx, ny, nz = 16, 8, 8
+    rho = synth.bernoulli_density(nx, ny, nz, 47, 0.30)
+    f = dev(O.cantilever_load(O.Mesh(nx, ny, nz)))
+    outs = []
+    for every in (0, 9):
+        g = gf.create_grid(nx, ny, nz, levels=3)
+        g.set_density(dev(rho), 3.0)
+        pol = gf.policy_defaults(rho0=1e-6, kmax=120, true_check_every=every, solve_prec=gf.GF_MIXED,
+                                 solve_outer=2)
+        u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        outs.append((g.select_floor(f, u, pol), u.clone()))
+        g.close()
+    (a, ua), (b, ub) = outs
+    assert a["true_checks"] == [] and len(b["true_checks"]) >= 1 and not b["true_check_fired"]
+    assert a["floor_index"] == b["floor_index"] and torch.equal(ua, ub)
+    assert [x["iters"] for x in a["attempts"]] == [x["iters"] for x in b["attempts"]]
+
+
+def test_true_check_arguments(gf):
+    g = gf.create_grid(8, 4, 4, levels=2)
+    g.set_density(dev(np.full(8 * 4 * 4, 0.5)), 3.0)
+    f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.cantilever_load(f)
+    u = torch.zeros_like(f)
+    for kw in (dict(true_check_every=-1), dict(true_check_every=5, probe_iters=100),
+               dict(true_check_every=10, true_check_ratio=0.0),
+               dict(true_check_every=10, selector=gf.GF_SEL_FULL)):
+        with pytest.raises(gf.GFError):
+            g.select_floor(f, u, gf.policy_defaults(**kw))
+
+
 # ------------------------------------------------------------- a8: policy --------
 @pytest.mark.parametrize("seed,q", [(43, 0.35), (47, 0.30)])
 def test_select_floor_parity(gf, seed, q):
