@@ -27,8 +27,9 @@ Every function is in FP64 and names the passage it follows (paper arXiv
 * compliance and sensitivity ............................ Sec. 3.1 (after Eq. projection)
 
 Readings where the paper is silent (the CUDA side takes the same ones):
-coarse levels are rediscretised with the mean of the 8 child moduli (not
-Galerkin); restriction is the transpose of trilinear prolongation, both masked;
+coarse levels are rediscretised with the mean of the 8 child moduli (the paper's
+Galerkin operators P^T K P are available as coarse="galerkin", to compare the two);
+restriction is the transpose of trilinear prolongation, both masked;
 damped 3x3 node-block Jacobi (the node-block operator of Table solver-config) with
 omega=0.6, 2 pre + 2 post sweeps from x=0 (point Jacobi at omega=0.6 is unstable on
 high-contrast fields: omega*lambda_max(D^-1 K) exceeds 2); coarsest level is a
@@ -346,6 +347,7 @@ class Level:
     P: sp.csr_matrix | None = None      # prolongation from the next coarser level
     chol: tuple | None = None           # coarsest only: Cholesky factor of free block
     lam: float = 0.0                    # Chebyshev smoothing: lambda_max(D_b^{-1} K) estimate
+    K: sp.csr_matrix | None = None      # Galerkin coarse levels: the assembled P^T K P (else matrix-free)
 
 
 @dataclass
@@ -355,27 +357,66 @@ class Hierarchy:
     nu2: int = 2
     omega: float = 0.6
     smoother: str = "jacobi"            # or "chebyshev"
+    coarse: str = "rediscretised"       # or "galerkin"
+
+
+def level_apply(level: Level, x: np.ndarray) -> np.ndarray:
+    """K_l x on a level: matrix-free sum_e E_e K0 (rediscretised), or the assembled
+    Galerkin operator; fixed entries of the result are 0 either way."""
+    if level.K is not None:
+        return level.K @ np.where(level.mesh.fixed, 0.0, x)
+    return apply_K(level.mesh, level.E, level.K0, x)
+
+
+def _blocks_of(K: sp.csr_matrix, mesh: Mesh) -> np.ndarray:
+    """The 3x3 diagonal blocks of an assembled operator (fixed nodes: identity)."""
+    n = mesh.n_nodes
+    D = np.zeros((n, 3, 3))
+    for a in range(3):
+        for b in range(3):
+            D[:, a, b] = np.asarray(K[np.arange(n) * 3 + a, np.arange(n) * 3 + b]).ravel()
+    D[mesh.fixed[0::3]] = np.eye(3)
+    return D
 
 
 def build_hierarchy(mesh: Mesh, E_fine: np.ndarray, n_levels: int, nu: float = 0.3,
-                    nu1: int = 2, nu2: int = 2, omega: float = 0.6, smoother: str = "jacobi") -> Hierarchy:
-    """Level l has (nx, ny, nz)/2^l elements of edge h*2^l, modulus = child mean, K0(h_l).
+                    nu1: int = 2, nu2: int = 2, omega: float = 0.6, smoother: str = "jacobi",
+                    coarse: str = "rediscretised") -> Hierarchy:
+    """Level l has (nx, ny, nz)/2^l elements of edge h*2^l. coarse="rediscretised":
+    modulus = child mean and K0(h_l), applied matrix-free (this build's reading);
+    coarse="galerkin": K_{l+1} = P^T K_l P with P the masked trilinear prolongation, the
+    coarse operator of Table solver-config, assembled (used to compare the two).
     With smoother="chebyshev" every smoothing level also gets lam (its lambda_max)."""
-    H = Hierarchy(nu1=nu1, nu2=nu2, omega=omega, smoother=smoother)
+    if coarse not in ("rediscretised", "galerkin"):
+        raise ValueError(coarse)
+    H = Hierarchy(nu1=nu1, nu2=nu2, omega=omega, smoother=smoother, coarse=coarse)
     m, E = mesh, np.asarray(E_fine, dtype=np.float64)
+    Kg = None
     for l in range(n_levels):
         K0 = element_stiffness(m.h, 1.0, nu)
-        H.levels.append(Level(m, E, K0, node_block_diagonal(m, E, K0)))
+        if Kg is None:
+            H.levels.append(Level(m, E, K0, node_block_diagonal(m, E, K0)))
+        else:
+            H.levels.append(Level(m, E, K0, _blocks_of(Kg, m), K=Kg))
         if l == n_levels - 1:
             break
         if m.nx % 2 or m.ny % 2 or m.nz % 2:
             raise ValueError("grid not divisible for the requested level count")
-        H.levels[-1].P = prolongation(m)
-        Ec = coarsen_modulus(m, E)
-        m = Mesh(m.nx // 2, m.ny // 2, m.nz // 2, m.h * 2.0)
-        E = Ec
+        P = prolongation(m)
+        H.levels[-1].P = P
+        mc = Mesh(m.nx // 2, m.ny // 2, m.nz // 2, m.h * 2.0)
+        if coarse == "galerkin":
+            Kf = H.levels[-1].K if H.levels[-1].K is not None else assemble_sparse(m, E, K0)
+            Pm = sp.diags(m.free.astype(np.float64)) @ P @ sp.diags(mc.free.astype(np.float64))
+            Kg = (Pm.T @ Kf @ Pm).tocsr()
+        E = coarsen_modulus(m, E)
+        m = mc
     last = H.levels[-1]
-    Kc = assemble_dense_free(last.mesh, last.E, last.K0)
+    if last.K is not None:
+        f = last.mesh.free
+        Kc = last.K.toarray()[np.ix_(f, f)]
+    else:
+        Kc = assemble_dense_free(last.mesh, last.E, last.K0)
     last.chol = sla.cho_factor(Kc, lower=True)
     if smoother == "chebyshev":
         for lev in H.levels[:-1]:
@@ -391,7 +432,7 @@ def coarse_solve(level: Level, b: np.ndarray) -> np.ndarray:
 
 def jacobi_sweep(level: Level, x: np.ndarray, b: np.ndarray, omega: float) -> np.ndarray:
     """Damped node-block Jacobi: x <- x + omega D_b^{-1} (b - K x), D_b the 3x3 node blocks."""
-    r = b - apply_K(level.mesh, level.E, level.K0, x)
+    r = b - level_apply(level, x)
     dx = np.linalg.solve(level.blockdiag, r.reshape(-1, 3, 1)).reshape(-1)
     return x + omega * dx
 
@@ -416,7 +457,7 @@ def power_lambda_max(apply_M, v0: np.ndarray, iters: int = 15) -> float:
 def level_lambda_max(level: Level, iters: int = 15) -> float:
     """lambda_max(D_b^{-1} K) of a level by 15 power iterations from ones on free DOFs."""
     v0 = np.where(level.mesh.fixed, 0.0, 1.0)
-    return power_lambda_max(lambda v: block_jacobi_apply(level, apply_K(level.mesh, level.E, level.K0, v)),
+    return power_lambda_max(lambda v: block_jacobi_apply(level, level_apply(level, v)),
                             v0, iters)
 
 
@@ -442,7 +483,7 @@ def chebyshev_smooth(level: Level, x: np.ndarray, b: np.ndarray, lam: float, deg
     error is multiplied by T_m((theta - M)/delta) / T_m(theta/delta), M = D_b^{-1} K."""
     d = np.zeros_like(b)
     for c1, c2 in chebyshev_coefficients(lam, degree):
-        r = b - apply_K(level.mesh, level.E, level.K0, x)
+        r = b - level_apply(level, x)
         d = c1 * d + c2 * block_jacobi_apply(level, r)
         x = x + d
     return x
@@ -462,7 +503,7 @@ def vcycle(H: Hierarchy, b: np.ndarray, l: int = 0) -> np.ndarray:
     if l == len(H.levels) - 1:
         return coarse_solve(lev, b)
     x = _smooth(H, lev, np.zeros_like(b), b, H.nu1)
-    r = b - apply_K(lev.mesh, lev.E, lev.K0, x)
+    r = b - level_apply(lev, x)
     coarse = H.levels[l + 1]
     bc = lev.P.T @ r
     bc[coarse.mesh.fixed] = 0.0
@@ -678,6 +719,7 @@ class SolverSetup:
     nu2: int = 2
     omega: float = 0.6
     smoother: str = "jacobi"
+    coarse: str = "rediscretised"
 
 
 def solve_at_floor(setup: SolverSetup, f: np.ndarray, rho_min: float, kmax: int, tol: float,
@@ -686,7 +728,8 @@ def solve_at_floor(setup: SolverSetup, f: np.ndarray, rho_min: float, kmax: int,
     (with check_every > 0: true-residual checks, the guard's eta, up to step check_upto)."""
     mesh = setup.mesh
     E = young_modulus(setup.rho_hat, rho_min, setup.p)
-    H = build_hierarchy(mesh, E, setup.n_levels, setup.nu, setup.nu1, setup.nu2, setup.omega, setup.smoother)
+    H = build_hierarchy(mesh, E, setup.n_levels, setup.nu, setup.nu1, setup.nu2, setup.omega, setup.smoother,
+                        setup.coarse)
     K0 = H.levels[0].K0
     fm = np.where(mesh.fixed, 0.0, f)
     res = fgmres(lambda v: apply_K(mesh, E, K0, v), lambda v: vcycle(H, v), fm,

@@ -236,6 +236,41 @@ def test_prolongation_interpolates_linears_and_galerkin_equals_rediscretisation(
     assert np.abs(G - Kc.toarray()).max() < 1e-13
 
 
+def test_galerkin_hierarchy_equals_rediscretised_at_constant_modulus():
+    m = O.Mesh(8, 4, 4)
+    E = np.full(m.n_elem, 0.37)
+    v = np.where(m.fixed, 0.0, synth.random_vector(m.n_dof, 3))
+    a = O.vcycle(O.build_hierarchy(m, E, 3), v)
+    b = O.vcycle(O.build_hierarchy(m, E, 3, coarse="galerkin"), v)
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a)
+
+
+def test_galerkin_coarse_correction_is_an_energy_orthogonal_projector():
+    """With K_c = P^T K P the exact coarse correction T = P K_c^{-1} P^T K satisfies T T = T
+    and K T = T^T K (a K-orthogonal projector). The rediscretised coarse operator does not
+    on a heterogeneous field, so the property pins the Galerkin product itself."""
+    m = O.Mesh(8, 4, 4)
+    E = O.young_modulus(synth.bernoulli_density(8, 4, 4, 43, 0.35), 1e-3, 3.0)
+    K = O.assemble_sparse(m, E, O.element_stiffness())
+    e1, e2 = (np.where(m.fixed, 0.0, synth.random_vector(m.n_dof, s)) for s in (5, 6))
+    for coarse, is_projector in (("galerkin", True), ("rediscretised", False)):
+        H = O.build_hierarchy(m, E, 2, coarse=coarse)
+        fine, c = H.levels
+        def T(e):
+            bc = fine.P.T @ (K @ e)
+            bc[c.mesh.fixed] = 0.0
+            x = fine.P @ O.coarse_solve(c, bc)
+            x[m.fixed] = 0.0
+            return x
+        t1 = T(e1)
+        proj = np.linalg.norm(T(t1) - t1) / np.linalg.norm(t1)
+        sym = abs(e2 @ (K @ T(e1)) - T(e2) @ (K @ e1)) / (np.linalg.norm(e1) * np.linalg.norm(e2) * abs(K).max())
+        if is_projector:
+            assert proj < 1e-10 and sym < 1e-12
+        else:
+            assert proj > 1e-3
+
+
 def test_coarsen_modulus_mean():
     m = O.Mesh(4, 2, 2)
     E = np.arange(m.n_elem, dtype=float)
