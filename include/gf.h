@@ -181,7 +181,7 @@ typedef struct {
 /* Create a grid of nx*ny*nz cubic elements of edge h, Young's modulus E0 (solid),
  * Poisson ratio nu, and a `levels`-level hierarchy (level l has (nx,ny,nz)/2^l
  * elements of edge h*2^l). Requires nx, ny, nz divisible by 2^(levels-1), ny and
- * nz even, 1 <= levels <= 8, and the coarsest level at most 6144 DOFs. `stream` is
+ * nz even, 1 <= levels <= 8, and the coarsest level at most 8192 DOFs. `stream` is
  * a cudaStream_t (NULL = legacy default stream). Allocates all level workspace.
  * Sec. 3.1 (Discretization), Table solver-config. */
 int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int levels,
@@ -264,6 +264,30 @@ int gf_true_residual(gf_grid* g, const double* f, const double* u, double* eta);
  * and the grid's floor is the accepted floor; otherwise u holds the last attempt. */
 int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol,
                     gf_select_info* info);
+
+/* ---- floor-conditioning diagnostic (Sec. 4.1.3) ------------------------------ */
+
+/* Extreme eigenvalues of the free-DOF operator K(rho_min) of Eq. (frozen_operator) on a
+ * one-level grid (levels == 1, at most 8192 DOFs: gf_set_floor then holds K's dense
+ * FP64 inverse, built by Gauss-Jordan). *lambda_max: `iters` Lanczos steps on K
+ * (matrix-free FP64 operator); *lambda_min: 1 / the largest eigenvalue after `iters`
+ * Lanczos steps on the dense inverse. Both start from the all-ones vector on the free
+ * DOFs, re-orthogonalise against the two previous vectors, and take the extreme
+ * eigenvalue of the tridiagonal matrix by bisection; they are lower/upper estimates
+ * that converge from inside the spectrum. eta_direct (optional, needs f, device):
+ * the FP64 guard residual of the direct solution u = K^{-1} f -- the attained
+ * direct-solve residual the paper correlates with kappa * eps. Host outputs.
+ * 2 <= iters <= 512. Errors: GF_ERR_STATE without levels == 1 or before
+ * gf_set_floor; GF_ERR_NONFINITE if an estimate is not positive. */
+int gf_conditioning(gf_grid* g, const double* f, int iters, double* lambda_min, double* lambda_max,
+                    double* eta_direct);
+
+/* The floor screen of Sec. 4.1.3 (host-only): with kappa ~ c / rho_min and c = kappa *
+ * rho_min measured at rho_min, *rho_screen = c * eps / tau (eps = DBL_EPSILON, 2^-52):
+ * floors below it have kappa * eps > tau, the region where the paper's reduced direct
+ * solves stop reaching tau. Needs 0 < lambda_min <= lambda_max, rho_min > 0, tau > 0. */
+int gf_conditioning_screen(double lambda_min, double lambda_max, double rho_min, double tau,
+                           double* rho_screen);
 
 /* ---- host-only policy logic (no device work; usable without a GPU) ----------- */
 

@@ -22,6 +22,7 @@ Every function is in FP64 and names the passage it follows (paper arXiv
   counts", Table "residual-semantics", Sec. 3.5 "Why a flexible Krylov method"
 * probe features r50/r100 and trigger rule .............. Sec. 3.4, Eq. (trigger)
 * guarded policy ........................................ Algorithm 1 (floor_policy)
+* conditioning diagnostic kappa, direct residual, screen  Sec. 4.1.3 (Figure conditioning)
 * true-residual checks during the probe, their detector . Sec. 4.1.1 (the checkpointed
   variant the paper leaves untested; the detector is a reading, see below)
 * compliance and sensitivity ............................ Sec. 3.1 (after Eq. projection)
@@ -641,6 +642,27 @@ def true_residual(mesh: Mesh, E: np.ndarray, K0: np.ndarray, f: np.ndarray, u: n
     fm = np.where(mesh.fixed, 0.0, f)
     r = fm - apply_K(mesh, E, K0, u)
     return float(np.linalg.norm(r) / np.linalg.norm(fm))
+
+
+# ----------------------------------------------------------------------------
+# floor-conditioning diagnostic (Sec. 4.1.3)
+# ----------------------------------------------------------------------------
+def conditioning(mesh: Mesh, E: np.ndarray, K0: np.ndarray, f: np.ndarray):
+    """Extreme eigenvalues of the free-DOF operator (dense symmetric eigensolver) and the
+    guard residual of the direct solution (Cholesky of the free block): the reduced
+    diagnostic that relates kappa = lambda_max / lambda_min to the attained residual."""
+    Kf = assemble_dense_free(mesh, E, K0)
+    ev = sla.eigvalsh(Kf)
+    u = np.zeros(mesh.n_dof)
+    u[mesh.free] = sla.cho_solve(sla.cho_factor(Kf, lower=True), np.asarray(f)[mesh.free])
+    return float(ev[0]), float(ev[-1]), true_residual(mesh, E, K0, f, u)
+
+
+def conditioning_screen(lambda_min: float, lambda_max: float, rho_min: float, tau: float) -> float:
+    """The floor screen: kappa ~ c / rho_min with c = kappa rho_min measured at rho_min, so
+    kappa eps <= tau needs rho_min >= c eps / tau (eps = 2^-52, our reading of the paper's eps)."""
+    c = lambda_max / lambda_min * rho_min
+    return c * 2.0 ** -52 / tau
 
 
 # ----------------------------------------------------------------------------

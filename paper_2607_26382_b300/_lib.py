@@ -29,7 +29,7 @@ ERRORS = {-1: "GF_ERR_ARG", -2: "GF_ERR_OOM", -3: "GF_ERR_CUDA", -4: "GF_ERR_NON
 
 EXPORTED = [
     "gf_create_grid", "gf_destroy_grid", "gf_grid_sizes", "gf_set_density", "gf_set_floor",
-    "gf_cantilever_load", "gf_free_mask", "gf_apply_K", "gf_apply_K_f32", "gf_vcycle", "gf_vcycle_ex", "gf_chebyshev_lambda", "gf_solve",
+    "gf_cantilever_load", "gf_free_mask", "gf_apply_K", "gf_apply_K_f32", "gf_vcycle", "gf_vcycle_ex", "gf_chebyshev_lambda", "gf_conditioning", "gf_conditioning_screen", "gf_solve",
     "gf_true_residual", "gf_select_floor", "gf_policy_defaults", "gf_trigger_rule",
     "gf_probe_features", "gf_sensitivity", "gf_get_stats", "gf_reset_stats", "gf_last_error",
     "gf_true_residual_noalloc", "gf_filter", "gf_filter_adjoint", "gf_oc_update", "gf_compliance",
@@ -105,6 +105,8 @@ def lib():
         "gf_free_mask": [P, P],
         "gf_apply_K": [P, P, P],
         "gf_apply_K_f32": [P, P, P],
+        "gf_conditioning": [P, P, c_int, POINTER(c_double), POINTER(c_double), POINTER(c_double)],
+        "gf_conditioning_screen": [c_double, c_double, c_double, c_double, POINTER(c_double)],
         "gf_vcycle": [P, P, P, c_int, c_int, c_int, c_double],
         "gf_vcycle_ex": [P, P, P, P],
         "gf_chebyshev_lambda": [P, c_int, P, c_int],
@@ -181,6 +183,14 @@ def policy_defaults(**kw) -> Policy:
         else:
             setattr(p, k, v)
     return p
+
+
+def conditioning_screen(lambda_min: float, lambda_max: float, rho_min: float, tau: float = 1e-6) -> float:
+    """gf_conditioning_screen: the floor below which kappa * eps exceeds tau (c = kappa rho_min)."""
+    out = c_double()
+    _check(lib().gf_conditioning_screen(float(lambda_min), float(lambda_max), float(rho_min), float(tau),
+                                        ctypes.byref(out)))
+    return out.value
 
 
 def trigger_rule(r50: float, r100: float, policy: Policy | None = None) -> bool:
@@ -375,6 +385,17 @@ class Grid:
         return dict(status=info.status, floor_index=info.floor_index, rho_min=info.rho_min, eta=info.eta,
                     escalated=bool(info.escalated), probe_iters_run=info.probe_iters_run, attempts=atts,
                     compliance=c.value)
+
+    def conditioning(self, f=None, iters=60):
+        """gf_conditioning on a one-level grid: extreme eigenvalues of K(rho_min), kappa, and
+        (with f) the guard residual of the direct solution."""
+        t = _torch().float64
+        lo, hi, eta = c_double(), c_double(), c_double()
+        fp = _ptr(f, t, self.n_dof, "f") if f is not None else None
+        _check(lib().gf_conditioning(self._h, fp, int(iters), ctypes.byref(lo), ctypes.byref(hi),
+                                     ctypes.byref(eta) if f is not None else None))
+        return dict(lambda_min=lo.value, lambda_max=hi.value, kappa=hi.value / lo.value,
+                    eta_direct=eta.value if f is not None else None)
 
     def features(self, r50, r100):
         return select_features(self._h, r50, r100)

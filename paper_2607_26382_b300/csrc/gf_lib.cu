@@ -13,11 +13,13 @@
 #include "stencil_tc.cuh"
 #include "cheb.cuh"
 #include "vcycle_cluster.cuh"
+#include "lanczos.cuh"
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cfloat>
 #include <cstring>
 #include <cstdlib>
 #include <string>
@@ -136,6 +138,8 @@ struct gf_grid {
     int m_alloc = 0;
     double *V = nullptr, *Z = nullptr, *partial = nullptr, *work = nullptr;
     double* ckx = nullptr;            // iterate of a probe true-residual check
+    gf::LzState* lz = nullptr;        // conditioning diagnostic: Lanczos coefficients
+    double* lzv = nullptr;            // its three vectors
     float2* Vd = nullptr;             // double-float copy of the basis (outer == 2)
     float2* pdd = nullptr;            // per-block partial pairs of the double-float passes
     unsigned int* ddticket = nullptr; // arrival counter of their last-block finish
@@ -1166,7 +1170,7 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     if (nx % div || ny % div || nz % div) return set_err(GF_ERR_ARG, "grid not divisible by 2^(levels-1)");
     if (!(h > 0) || !(E0 > 0) || !(nu > -1.0 && nu < 0.5)) return set_err(GF_ERR_ARG, "h, E0 > 0, nu in (-1,0.5)");
     const long long cn = 3LL * (nx / div + 1) * (ny / div + 1) * (nz / div + 1);
-    if (cn > 6144) return set_err(GF_ERR_ARG, "coarsest level above 6144 DOFs: add levels");
+    if (cn > 8192) return set_err(GF_ERR_ARG, "coarsest level above 8192 DOFs: add levels");
     gf_grid* g = new gf_grid();
     g->nx = nx; g->ny = ny; g->nz = nz; g->L = levels;
     g->h = h; g->E0 = E0; g->nu = nu;
@@ -1310,6 +1314,8 @@ int gf_destroy_grid(gf_grid* g)
     cudaFree(g->rho64); cudaFree(g->rho16); cudaFree(g->work); cudaFree(g->partial);
     cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Vd); cudaFree(g->pdd); cudaFree(g->ddticket); cudaFree(g->Z); cudaFree(g->hist);
     cudaFree(g->ckx);
+    cudaFree(g->lz);
+    cudaFree(g->lzv);
     cudaFree(g->Edf);
     cudaFree(g->B3);
     cudaFree(g->Btc);
@@ -1485,6 +1491,56 @@ int gf_solve(gf_grid* g, const double* f, double* u, const gf_solve_opts* opts, 
     if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
     RET(set_device(g));
     return solve_impl(g, f, u, opts, info, false, opts->history);
+}
+
+int gf_conditioning(gf_grid* g, const double* f, int iters, double* lambda_min, double* lambda_max,
+                    double* eta_direct)
+{
+    RET(check_grid(g));
+    if (!lambda_min || !lambda_max || (eta_direct && !f)) return set_err(GF_ERR_ARG, "null pointer");
+    if (g->L != 1) return set_err(GF_ERR_STATE, "gf_conditioning needs a one-level grid (levels = 1)");
+    if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
+    if (iters < 2 || iters > gf::LZ_MAX) return set_err(GF_ERR_ARG, "iters in [2, 512]");
+    RET(set_device(g));
+    const long long n = g->ndof;
+    if (!g->lz) RET(allocT(&g->lz, 1));
+    if (!g->lzv) RET(allocT(&g->lzv, (size_t)3 * n));
+    for (int pass = 0; pass < 2; ++pass) {   // 0: K (lambda_max), 1: K^{-1} (1 / lambda_min)
+        double *v = g->lzv, *vp = g->lzv + n, *w = g->lzv + 2 * n;
+        LAUNCH(g, 1, gf::LZ_THREADS, gf::lanczos_start_kernel, v, vp, n, g->nx + 1, g->lz);
+        for (int j = 0; j < iters; ++j) {
+            if (pass == 0)
+                RET(applyK64(g, v, w, nullptr));
+            else
+                LAUNCH(g, nblk(32LL * n), 256, (gf::dense_gemv_kernel<double, double>), (const double*)g->Ainv,
+                       (const double*)v, w, (int)n, (const int*)nullptr);
+            LAUNCH(g, 1, gf::LZ_THREADS, gf::lanczos_step_kernel, w, (const double*)v, vp, n, j, g->lz);
+            std::swap(v, vp);   // v_{j+1} was written over v_{j-1}
+        }
+        LAUNCH(g, 1, 32, gf::lanczos_tridiag_kernel, g->lz, iters);
+        double hi = 0.0;
+        CK(cudaMemcpyAsync(&hi, &g->lz->hi, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        if (!(hi > 0.0) || !std::isfinite(hi)) return set_err(GF_ERR_NONFINITE, "Lanczos estimate not positive");
+        if (pass == 0) *lambda_max = hi;
+        else *lambda_min = 1.0 / hi;
+    }
+    if (eta_direct) {   // the direct solution u = K^{-1} f and its guard residual
+        double* u = g->lzv;
+        LAUNCH(g, nblk(32LL * n), 256, (gf::dense_gemv_kernel<double, double>), (const double*)g->Ainv, f, u, (int)n,
+               (const int*)nullptr);
+        RET(guard_impl(g, f, u, eta_direct));
+    }
+    return GF_OK;
+}
+
+int gf_conditioning_screen(double lambda_min, double lambda_max, double rho_min, double tau, double* rho_screen)
+{
+    if (!rho_screen || !(lambda_min > 0.0) || !(lambda_max >= lambda_min) || !(rho_min > 0.0) || !(tau > 0.0))
+        return set_err(GF_ERR_ARG, "need 0 < lambda_min <= lambda_max, rho_min > 0, tau > 0");
+    const double c = lambda_max / lambda_min * rho_min;   // kappa ~ c / rho_min
+    *rho_screen = c * DBL_EPSILON / tau;
+    return GF_OK;
 }
 
 int gf_true_residual(gf_grid* g, const double* f, const double* u, double* eta)

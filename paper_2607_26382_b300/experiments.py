@@ -4,6 +4,7 @@
     python -m paper_2607_26382_b300.experiments oc_loop [--iters 40]
     python -m paper_2607_26382_b300.experiments oc_reuse [--iters 40]
     python -m paper_2607_26382_b300.experiments true_checks
+    python -m paper_2607_26382_b300.experiments conditioning
 
 batch102: 102 frozen states of uneven size (nx in {32,48,64,80}, ny = nz = nx/2,
   round-robin; 71 smoothed-Gaussian states with 40% of voxels at floor, 31
@@ -31,6 +32,12 @@ true_checks: the 102 batch102 states one at a time (mixed, outer = 2), Algorithm
   workload's floors (rho0 1e-6, ladder {1e-5, 1e-4, 1e-3}) and at the paper's
   (rho0 1e-12, ladder {1e-3, 1e-2}, kmax 300): detector firings, the largest
   eta / estimate ratio seen, decisions that change, and the cost.
+conditioning: the reduced floor-conditioning diagnostic of Sec. 4.1.3 on the 24x12x6
+  cantilever (6,825 DOF, one level: dense FP64 inverse by Gauss-Jordan), 18 fields
+  (9 Bernoulli, q in {0.08..0.35}, 9 smoothed-Gaussian) x 8 floors (1e-12 .. 1e-2),
+  p = 4.5: kappa from Lanczos (60 steps on K and on the inverse), the direct
+  solution's guard residual, the log-log fit of residual against kappa * eps, the
+  split at kappa * eps = tau, and c = kappa * rho_min per field.
 """
 from __future__ import annotations
 
@@ -271,13 +278,65 @@ def true_checks(args):
     return out
 
 
+def conditioning(args):
+    import torch
+    import synth
+    nx, ny, nz = 24, 12, 6
+    floors = [1e-12, 1e-10, 1e-8, 1e-7, 1e-6, 1e-5, 1e-4, 1e-2]
+    qs = [0.08, 0.11, 0.14, 0.17, 0.20, 0.23, 0.26, 0.30, 0.35]
+    fields = [("bernoulli", synth.bernoulli_density(nx, ny, nz, 41 + 2 * i, q)) for i, q in enumerate(qs)]
+    fields += [("gaussian", synth.smoothed_gaussian_density(nx, ny, nz, 200 + i, 1.5, 0.3 + 0.05 * i)) for i in range(9)]
+    eps, tau = 2.0 ** -52, 1e-6
+    g = L.create_grid(nx, ny, nz, levels=1)
+    f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.cantilever_load(f)
+    rows, t0 = [], time.perf_counter()
+    for kind, rho in fields:
+        g.set_density(torch.as_tensor(rho, device="cuda"), 4.5)
+        for rm in floors:
+            g.set_floor(rm)
+            o = g.conditioning(f, iters=60)
+            rows.append(dict(kind=kind, rho_min=rm, kappa=o["kappa"], eta=o["eta_direct"], c=o["kappa"] * rm))
+    secs = time.perf_counter() - t0
+    g.close()
+    k_eps = np.array([r["kappa"] * eps for r in rows])
+    eta = np.array([r["eta"] for r in rows])
+    x, y = np.log10(k_eps), np.log10(np.maximum(eta, 1e-300))
+    def fit(mask):
+        A = np.vstack([x[mask], np.ones(mask.sum())]).T
+        slope = float(np.linalg.lstsq(A, y[mask], rcond=None)[0][0])
+        return {"n": int(mask.sum()), "slope": slope, "corr": float(np.corrcoef(x[mask], y[mask])[0, 1])}
+    floor_ = eta <= 1e-14                        # at the backward-stability floor
+    below = k_eps <= tau
+    cs = {}
+    for i in range(len(fields)):
+        c = [r["c"] for r in rows[i * len(floors):(i + 1) * len(floors)]]
+        c_small = c[:5]                          # floors 1e-12 .. 1e-6
+        cs[i] = max(c_small) / min(c_small)
+    return {"workload": f"24x12x6 cantilever, {len(fields)} fields x {len(floors)} floors, p 4.5",
+            "seconds": secs, "matrices": len(rows),
+            "kappa_range_at_1e-12": [min(r["kappa"] for r in rows if r["rho_min"] == 1e-12),
+                                     max(r["kappa"] for r in rows if r["rho_min"] == 1e-12)],
+            "fit_all": fit(np.ones(len(rows), bool)), "fit_above_stability_floor": fit(~floor_),
+            "fit_bernoulli": fit(np.array([r["kind"] == "bernoulli" for r in rows])),
+            "fit_gaussian": fit(np.array([r["kind"] == "gaussian" for r in rows])),
+            "at_stability_floor": int(floor_.sum()),
+            "kappa_eps_le_tau": {"n": int(below.sum()), "reach_tau": int((eta[below] <= tau).sum())},
+            "kappa_eps_gt_tau": {"n": int((~below).sum()), "miss_tau": int((eta[~below] > tau).sum())},
+            "upper_envelope_max_eta_over_kappa_eps": float((eta / k_eps).max()),
+            "c_spread_1e-12_to_1e-6_per_field_max": float(max(cs.values())),
+            "c_spread_median": float(np.median(list(cs.values()))),
+            "rows": rows}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch102", "oc_loop", "oc_reuse", "true_checks"])
+    ap.add_argument("what", choices=["batch102", "oc_loop", "oc_reuse", "true_checks", "conditioning"])
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--iters", type=int, default=40)
     a = ap.parse_args(argv)
-    res = {"batch102": batch102, "oc_loop": oc_loop, "oc_reuse": oc_reuse, "true_checks": true_checks}[a.what](a)
+    res = {"batch102": batch102, "oc_loop": oc_loop, "oc_reuse": oc_reuse, "true_checks": true_checks,
+           "conditioning": conditioning}[a.what](a)
     print(json.dumps(res), flush=True)
     return 0
 

@@ -81,3 +81,12 @@ def test_missing_library_fails_loudly(gflib, monkeypatch):
     monkeypatch.setattr(gflib, "LIB_PATH", "/nonexistent/libgf_b300.so")
     with pytest.raises(RuntimeError):
         gflib.lib()
+
+
+def test_conditioning_screen_matches_oracle(gflib):
+    from oracle import gf_oracle as O
+    for args in ((1e-8, 2.5, 1e-6, 1e-6), (3e-15, 4.0, 1e-12, 1e-6), (0.5, 0.5, 1e-2, 1e-8)):
+        assert gflib.conditioning_screen(*args) == O.conditioning_screen(*args)
+    for bad in ((0.0, 1.0, 1e-6, 1e-6), (2.0, 1.0, 1e-6, 1e-6), (1e-3, 1.0, 0.0, 1e-6), (1e-3, 1.0, 1e-6, 0.0)):
+        with pytest.raises(gflib.GFError):
+            gflib.conditioning_screen(*bad)

@@ -481,6 +481,43 @@ def test_true_check_arguments(gf):
             g.select_floor(f, u, gf.policy_defaults(**kw))
 
 
+# Floor-conditioning diagnostic (Sec. 4.1.3): extreme eigenvalues by Lanczos on K and on
+# its dense inverse (one-level grid), against the oracle's dense eigensolver; the direct
+# solution's guard residual within the backward-error envelope kappa * eps.
+@pytest.mark.parametrize("nx,ny,nz,rm", [(4, 2, 2, 1e-3), (8, 4, 4, 1e-6), (6, 2, 2, 1e-8)])
+def test_conditioning_matches_oracle(gf, nx, ny, nz, rm):
+    m = O.Mesh(nx, ny, nz)
+    rho = synth.bernoulli_density(nx, ny, nz, 43, 0.35)
+    f = O.cantilever_load(m)
+    lo, hi, eta = O.conditioning(m, O.young_modulus(rho, rm, 3.0), O.element_stiffness(), f)
+    g = gf.create_grid(nx, ny, nz, levels=1)
+    g.set_density(dev(rho), 3.0)
+    g.set_floor(rm)
+    out = g.conditioning(dev(f), iters=min(512, m.n_dof))
+    kappa_eps = hi / lo * 2.0 ** -52
+    assert abs(out["lambda_max"] / hi - 1) <= 1e-9
+    assert abs(out["lambda_min"] / lo - 1) <= max(1e-7, 100 * kappa_eps)
+    assert out["eta_direct"] <= 1e3 * kappa_eps + 1e-13 and eta <= 1e3 * kappa_eps + 1e-13
+    assert gf.conditioning_screen(out["lambda_min"], out["lambda_max"], rm, 1e-6) == \
+        pytest.approx(O.conditioning_screen(lo, hi, rm, 1e-6), rel=max(1e-6, 200 * kappa_eps))
+
+
+def test_conditioning_arguments(gf):
+    g = gf.create_grid(4, 2, 2, levels=2)
+    g.set_density(dev(np.full(16, 0.5)), 3.0)
+    g.set_floor(1e-3)
+    with pytest.raises(gf.GFError):
+        g.conditioning(iters=20)                  # needs levels == 1
+    g1 = gf.create_grid(4, 2, 2, levels=1)
+    g1.set_density(dev(np.full(16, 0.5)), 3.0)
+    with pytest.raises(gf.GFError):
+        g1.conditioning(iters=20)                 # before set_floor
+    g1.set_floor(1e-3)
+    for it in (1, 513):
+        with pytest.raises(gf.GFError):
+            g1.conditioning(iters=it)
+
+
 # ------------------------------------------------------------- a8: policy --------
 @pytest.mark.parametrize("seed,q", [(43, 0.35), (47, 0.30)])
 def test_select_floor_parity(gf, seed, q):

@@ -333,6 +333,42 @@ def test_vcycle_contracts_error_in_energy_norm():
     assert math.sqrt(e @ O.apply_K(m, E, K0, e)) < 0.5 * err0
 
 
+# ------------------------------------------------------ conditioning diagnostic --
+def test_conditioning_bounds_homogeneity_and_backward_error():
+    m = O.Mesh(4, 2, 2)
+    K0 = O.element_stiffness()
+    rho = synth.bernoulli_density(4, 2, 2, 43, 0.35)
+    f = O.cantilever_load(m)
+    Kf = O.assemble_dense_free(m, O.young_modulus(rho, 1e-3, 3.0), K0)
+    lo, hi, eta = O.conditioning(m, O.young_modulus(rho, 1e-3, 3.0), K0, f)
+    assert hi <= np.abs(Kf).sum(axis=1).max() * (1 + 1e-14)              # Gershgorin
+    for s in range(5):                                                   # Rayleigh quotients lie inside
+        v = synth.random_vector(Kf.shape[0], s)
+        rq = v @ Kf @ v / (v @ v)
+        assert lo <= rq <= hi
+    lo2, hi2, _ = O.conditioning(m, 7.5 * O.young_modulus(rho, 1e-3, 3.0), K0, f)
+    assert abs(hi2 / lo2 / (hi / lo) - 1) < 1e-10                        # kappa(aK) = kappa(K)
+    for rm in (1e-3, 1e-6, 1e-9):                                        # Cholesky backward error
+        lo, hi, eta = O.conditioning(m, O.young_modulus(rho, rm, 3.0), K0, f)
+        assert eta <= 1e3 * 2.0 ** -52 * hi / lo + 1e-14
+
+
+def test_conditioning_follows_c_over_rho_min_and_screen():
+    """A field with a void region: lambda_min scales with the floor, so kappa rho_min is
+    nearly fixed over decades (the c(rho) of Sec. 4.1.3), and the screen is c eps / tau."""
+    m = O.Mesh(6, 2, 2)
+    K0 = O.element_stiffness()
+    rho = np.ones(m.n_elem)
+    rho[[e for e in range(m.n_elem) if e % 6 >= 3]] = 0.0                # far half void
+    f = O.cantilever_load(m)
+    cs = []
+    for rm in (1e-4, 1e-6, 1e-8):
+        lo, hi, _ = O.conditioning(m, O.young_modulus(rho, rm, 3.0), K0, f)
+        cs.append(hi / lo * rm)
+    assert max(cs) / min(cs) < 1.05
+    assert O.conditioning_screen(1e-8, 1.0, 1e-6, 1e-6) == pytest.approx(1e2 * 2.0 ** -52 / 1e-6 * 1e0, rel=1e-15)
+
+
 # ---------------------------------------------------------------- FGMRES ----
 def test_fgmres_diagonal_distinct_eigenvalues():
     d = np.array([1.0, 2.0, 2.0, 3.0, 3.0, 3.0, 5.0])
