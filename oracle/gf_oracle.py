@@ -16,6 +16,7 @@ Every function is in FP64 and names the passage it follows (paper arXiv
 * frozen operator K = sum_e E_e K_e on free DOFs ........ Eq. (frozen_operator)
 * relative residual eta = ||f - K u|| / ||f|| ........... Eq. (relative_residual)
 * GMG V-cycle, 2:1 trilinear transfer ................... Table "solver-config"
+* line-searched, rejectable coarse correction ......... Table "solver-config" (coarse correction)
 * Chebyshev smoother (alternative to node-block Jacobi) . Table "solver-config" (names a
   Chebyshev smoother; degree and interval are readings, see below)
 * right-preconditioned FGMRES, residual history ......... Sec. 3.2 "Which residual
@@ -41,6 +42,10 @@ Chebyshev smoothing (optional): Chebyshev semi-iteration of degree nu1 / nu2 on
 D_b^{-1} K over [lambda_max / 30, 1.1 lambda_max], D_b the same 3x3 node blocks;
 lambda_max of each level from 15 power iterations started from the all-ones vector
 on free DOFs.
+Line-searched coarse correction (optional, ls_ratio = theta > 0; the first adaptive
+component of Table solver-config, acceptance ratio a reading): the prolongated
+correction c is scaled by alpha = (r.q)/(q.q), q = K c, and dropped unless alpha > 0
+and ||r - alpha q|| <= theta ||r||.
 True-residual checks (optional): every c steps of the probe the current iterate is
 formed as at a cycle end and its guard residual recomputed; the detector fires when
 one exceeds ratio (default 10) times the projected estimate of the same step, and a
@@ -359,6 +364,7 @@ class Hierarchy:
     omega: float = 0.6
     smoother: str = "jacobi"            # or "chebyshev"
     coarse: str = "rediscretised"       # or "galerkin"
+    ls_ratio: float = 0.0               # > 0: line-searched, rejectable coarse correction (theta)
 
 
 def level_apply(level: Level, x: np.ndarray) -> np.ndarray:
@@ -382,7 +388,7 @@ def _blocks_of(K: sp.csr_matrix, mesh: Mesh) -> np.ndarray:
 
 def build_hierarchy(mesh: Mesh, E_fine: np.ndarray, n_levels: int, nu: float = 0.3,
                     nu1: int = 2, nu2: int = 2, omega: float = 0.6, smoother: str = "jacobi",
-                    coarse: str = "rediscretised") -> Hierarchy:
+                    coarse: str = "rediscretised", ls_ratio: float = 0.0) -> Hierarchy:
     """Level l has (nx, ny, nz)/2^l elements of edge h*2^l. coarse="rediscretised":
     modulus = child mean and K0(h_l), applied matrix-free (this build's reading);
     coarse="galerkin": K_{l+1} = P^T K_l P with P the masked trilinear prolongation, the
@@ -390,7 +396,7 @@ def build_hierarchy(mesh: Mesh, E_fine: np.ndarray, n_levels: int, nu: float = 0
     With smoother="chebyshev" every smoothing level also gets lam (its lambda_max)."""
     if coarse not in ("rediscretised", "galerkin"):
         raise ValueError(coarse)
-    H = Hierarchy(nu1=nu1, nu2=nu2, omega=omega, smoother=smoother, coarse=coarse)
+    H = Hierarchy(nu1=nu1, nu2=nu2, omega=omega, smoother=smoother, coarse=coarse, ls_ratio=ls_ratio)
     m, E = mesh, np.asarray(E_fine, dtype=np.float64)
     Kg = None
     for l in range(n_levels):
@@ -498,6 +504,19 @@ def _smooth(H: Hierarchy, lev: Level, x: np.ndarray, b: np.ndarray, nu: int) -> 
     return x
 
 
+def line_search(r: np.ndarray, q: np.ndarray, theta: float):
+    """The residual line search on a coarse correction c with q = K c (Table solver-config,
+    "coarse correction"; the acceptance ratio is a reading): alpha minimises ||r - alpha q||,
+    alpha = (r.q)/(q.q), and the scaled correction is kept only when alpha > 0 and
+    ||r - alpha q||^2 = ||r||^2 - (r.q)^2/(q.q) <= theta^2 ||r||^2. Returns (alpha, kept)."""
+    rq, qq, rr = float(r @ q), float(q @ q), float(r @ r)
+    if not qq > 0.0:
+        return 0.0, False
+    alpha = rq / qq
+    kept = alpha > 0.0 and rr - rq * rq / qq <= theta * theta * rr
+    return (alpha if kept else 0.0), kept
+
+
 def vcycle(H: Hierarchy, b: np.ndarray, l: int = 0) -> np.ndarray:
     """One V-cycle on level l for right-hand side b (fixed entries of b are zero)."""
     lev = H.levels[l]
@@ -511,7 +530,11 @@ def vcycle(H: Hierarchy, b: np.ndarray, l: int = 0) -> np.ndarray:
     xc = vcycle(H, bc, l + 1)
     corr = lev.P @ xc
     corr[lev.mesh.fixed] = 0.0
-    x = x + corr
+    if H.ls_ratio > 0.0:   # the correction scaled by the residual line search, or rejected
+        alpha, _ = line_search(r, level_apply(lev, corr), H.ls_ratio)
+        x = x + alpha * corr
+    else:
+        x = x + corr
     return _smooth(H, lev, x, b, H.nu2)
 
 
@@ -742,6 +765,7 @@ class SolverSetup:
     omega: float = 0.6
     smoother: str = "jacobi"
     coarse: str = "rediscretised"
+    ls_ratio: float = 0.0
 
 
 def solve_at_floor(setup: SolverSetup, f: np.ndarray, rho_min: float, kmax: int, tol: float,
@@ -751,7 +775,7 @@ def solve_at_floor(setup: SolverSetup, f: np.ndarray, rho_min: float, kmax: int,
     mesh = setup.mesh
     E = young_modulus(setup.rho_hat, rho_min, setup.p)
     H = build_hierarchy(mesh, E, setup.n_levels, setup.nu, setup.nu1, setup.nu2, setup.omega, setup.smoother,
-                        setup.coarse)
+                        setup.coarse, setup.ls_ratio)
     K0 = H.levels[0].K0
     fm = np.where(mesh.fixed, 0.0, f)
     res = fgmres(lambda v: apply_K(mesh, E, K0, v), lambda v: vcycle(H, v), fm,
