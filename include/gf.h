@@ -99,6 +99,14 @@ typedef struct {
                           solver-config names; degree and interval are this library's readings),
                           lambda_max of each level from 15 power iterations from ones on the
                           free DOFs, computed on first use after each gf_set_floor. */
+    double ls_ratio;   /* 0 = plain coarse correction x += P x_c. theta > 0: the line-searched,
+                          rejectable coarse correction of Table solver-config's adaptive preconditioner
+                          on every level: with c = P x_c, r the level's residual before the correction
+                          and q = K c, alpha = (c.r)/(c.q) (the energy-optimal step, computed from r),
+                          kept (x += alpha c) iff alpha >= theta (this library's reading of the
+                          acceptance ratio). Needs smoother 0 and >= 2 levels; single grid only. The
+                          preconditioner is then iterate-dependent, which FGMRES allows. Errors:
+                          GF_ERR_ARG for a negative or non-finite value. */
 } gf_solve_opts;
 
 typedef struct {

@@ -43,9 +43,10 @@ D_b^{-1} K over [lambda_max / 30, 1.1 lambda_max], D_b the same 3x3 node blocks;
 lambda_max of each level from 15 power iterations started from the all-ones vector
 on free DOFs.
 Line-searched coarse correction (optional, ls_ratio = theta > 0; the first adaptive
-component of Table solver-config, acceptance ratio a reading): the prolongated
-correction c is scaled by alpha = (r.q)/(q.q), q = K c, and dropped unless alpha > 0
-and ||r - alpha q|| <= theta ||r||.
+component of Table solver-config, step and acceptance test readings): the prolongated
+correction c is scaled by the energy-optimal alpha = (c.r)/(c.K c), computed from the
+residual, and dropped unless alpha >= theta. (Minimising ||r - alpha K c|| instead, or
+rejecting on the residual norm before post-smoothing, cripples this V-cycle: measured.)
 True-residual checks (optional): every c steps of the probe the current iterate is
 formed as at a cycle end and its guard residual recomputed; the detector fires when
 one exceeds ratio (default 10) times the projected estimate of the same step, and a
@@ -504,16 +505,18 @@ def _smooth(H: Hierarchy, lev: Level, x: np.ndarray, b: np.ndarray, nu: int) -> 
     return x
 
 
-def line_search(r: np.ndarray, q: np.ndarray, theta: float):
-    """The residual line search on a coarse correction c with q = K c (Table solver-config,
-    "coarse correction"; the acceptance ratio is a reading): alpha minimises ||r - alpha q||,
-    alpha = (r.q)/(q.q), and the scaled correction is kept only when alpha > 0 and
-    ||r - alpha q||^2 = ||r||^2 - (r.q)^2/(q.q) <= theta^2 ||r||^2. Returns (alpha, kept)."""
-    rq, qq, rr = float(r @ q), float(q @ q), float(r @ r)
-    if not qq > 0.0:
+def line_search(r: np.ndarray, c: np.ndarray, q: np.ndarray, theta: float):
+    """The line search on a coarse correction c with q = K c (Table solver-config, "coarse
+    correction"; both the step and the acceptance test are readings): the step minimising
+    the energy error along c, alpha = (c.r)/(c.q) -- computed from the residual r, and 1
+    for an exact Galerkin coarse correction -- and the correction is kept only when that
+    ratio passes the acceptance test alpha >= theta. Returns (alpha, kept), alpha = 0
+    when rejected.""" 
+    cr, cq = float(c @ r), float(c @ q)
+    if not cq > 0.0:
         return 0.0, False
-    alpha = rq / qq
-    kept = alpha > 0.0 and rr - rq * rq / qq <= theta * theta * rr
+    alpha = cr / cq
+    kept = alpha >= theta
     return (alpha if kept else 0.0), kept
 
 
@@ -531,7 +534,7 @@ def vcycle(H: Hierarchy, b: np.ndarray, l: int = 0) -> np.ndarray:
     corr = lev.P @ xc
     corr[lev.mesh.fixed] = 0.0
     if H.ls_ratio > 0.0:   # the correction scaled by the residual line search, or rejected
-        alpha, _ = line_search(r, level_apply(lev, corr), H.ls_ratio)
+        alpha, _ = line_search(r, corr, level_apply(lev, corr), H.ls_ratio)
         x = x + alpha * corr
     else:
         x = x + corr

@@ -14,6 +14,7 @@
 #include "cheb.cuh"
 #include "vcycle_cluster.cuh"
 #include "lanczos.cuh"
+#include "linesearch.cuh"
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -63,6 +64,8 @@ struct Level {
     float* E32 = nullptr;
     double *b64 = nullptr, *x64 = nullptr, *t64 = nullptr, *r64 = nullptr;
     float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr, *r32 = nullptr;
+    double* q64 = nullptr;            // line-searched coarse correction: K c (allocated on first use)
+    float* q32 = nullptr;
     gf::GridDims dims() const { return gf::GridDims{nx, ny, nz}; }
 };
 
@@ -138,6 +141,10 @@ struct gf_grid {
     int m_alloc = 0;
     double *V = nullptr, *Z = nullptr, *partial = nullptr, *work = nullptr;
     double* ckx = nullptr;            // iterate of a probe true-residual check
+    double* ls_partial = nullptr;     // line search: per-block dot products
+    double* ls_alpha = nullptr;       // line search: alpha of each level (device)
+    int ls_nb = 0;
+    double gkey_ls = -1.0;            // line-search ratio the captured Arnoldi steps were built with
     gf::LzState* lz = nullptr;        // conditioning diagnostic: Lanczos coefficients
     double* lzv = nullptr;            // its three vectors
     float2* Vd = nullptr;             // double-float copy of the basis (outer == 2)
@@ -281,6 +288,7 @@ struct LvBuf<double> {
     static double* x(Level& L) { return L.x64; }
     static double* t(Level& L) { return L.t64; }
     static double* r(Level& L) { return L.r64; }
+    static double* q(Level& L) { return L.q64; }
     static const double* E(Level& L) { return L.E64; }
 };
 template <>
@@ -289,13 +297,20 @@ struct LvBuf<float> {
     static float* x(Level& L) { return L.x32; }
     static float* t(Level& L) { return L.t32; }
     static float* r(Level& L) { return L.r32; }
+    static float* q(Level& L) { return L.q32; }
     static const float* E(Level& L) { return L.E32; }
 };
+
+// Coarse-grid correction of level l: x += P xc, or (theta > 0) the line-searched,
+// rejectable form x += alpha P xc (csrc/linesearch.cuh); c is free scratch of the level,
+// r the level's residual before the correction.
+template <typename T>
+int coarse_correct(gf_grid* g, int l, T* x, const T* xc, T* c, const T* r, double theta, const int* halt);
 
 // One V-cycle z = B v in precision T (Table solver-config: 2:1 trilinear transfer,
 // damped node-block Jacobi smoothing, coarsest solve by the FP64 dense inverse).
 template <typename T>
-int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omega, const int* halt)
+int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omega, const int* halt, double ls = 0.0)
 {
     using B = LvBuf<T>;
     const int L = g->L;
@@ -350,7 +365,7 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
         const T* b = (l == 0) ? b0 : B::b(lev);
         T* x = cur[l];
         T* t = (x == B::x(lev)) ? B::t(lev) : B::x(lev);
-        LAUNCH(g, nblk(lev.nodes), 256, (gf::prolong_add_kernel<T, T>), x, cur[l + 1], lev.dims(), halt);
+        RET(coarse_correct<T>(g, l, x, cur[l + 1], t, B::r(lev), ls, halt));
         for (int s = 0; s < nu2; ++s) {
             T* out = t;
             const bool last = (l == 0 && s == nu2 - 1);
@@ -374,7 +389,8 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
 // The mixed V-cycle (FP32 stencils, linear or tiled per the grid's tuning): level 0 reads the FP64 input v
 // as its right-hand side and the last post-sweep writes the FP64 result z, so no
 // conversion passes are needed.
-int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2, float omega, const int* halt)
+int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2, float omega, const int* halt,
+                       double ls = 0.0)
 {
     const int L = g->L;
     g->stats.vcycles++;
@@ -435,8 +451,7 @@ int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2,
         Level& lev = g->lv[l];
         float* x = cur[l];
         float* t = (x == lev.x32) ? lev.t32 : lev.x32;
-        LAUNCH(g, nblk(lev.nodes), 256, (gf::prolong_add_kernel<float, float>), x, (const float*)cur[l + 1],
-               lev.dims(), halt);
+        RET(coarse_correct<float>(g, l, x, (const float*)cur[l + 1], t, lev.r32, ls, halt));
         for (int s = 0; s < nu2; ++s) {
             const bool last = (s == nu2 - 1);
             if (l == 0 && last) {
@@ -566,18 +581,55 @@ int vcycle_cheb(gf_grid* g, const double* v, double* z, int nu1, int nu2, const 
 }
 
 int vcycle_dispatch(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2, double omega,
-                    const int* halt, int smoother = 0)
+                    const int* halt, int smoother = 0, double ls = 0.0)
 {
+    if (ls > 0.0 && (smoother == 1 || g->vc_l0 > 0 || g->L < 2 || !g->ls_alpha))
+        return set_err(GF_ERR_ARG, "the line-searched coarse correction needs Jacobi smoothing, >= 2 levels and no "
+                                   "cluster V-cycle");
     if (smoother == 1) {
         if (!g->cheb_ready[prec == GF_FP64 ? 0 : 1]) return set_err(GF_ERR_STATE, "Chebyshev bounds not set up");
         if (prec == GF_MIXED) return vcycle_cheb<float>(g, v, z, nu1, nu2, halt);
         return vcycle_cheb<double>(g, v, z, nu1, nu2, halt);
     }
     if (prec == GF_MIXED) {
-        if (g->L > 1) return vcycle_mixed_tiled(g, v, z, nu1, nu2, (float)omega, halt);
-        return vcycle_impl<float>(g, v, z, nu1, nu2, (float)omega, halt);
+        if (g->L > 1) return vcycle_mixed_tiled(g, v, z, nu1, nu2, (float)omega, halt, ls);
+        return vcycle_impl<float>(g, v, z, nu1, nu2, (float)omega, halt, ls);
     }
-    return vcycle_impl<double>(g, v, z, nu1, nu2, omega, halt);
+    return vcycle_impl<double>(g, v, z, nu1, nu2, omega, halt, ls);
+}
+
+// buffers of the line-searched coarse correction (outside any graph capture)
+int ensure_ls(gf_grid* g)
+{
+    if (g->ls_alpha) return GF_OK;
+    for (int l = 0; l < g->L - 1; ++l) {
+        RET(allocT(&g->lv[l].q64, g->lv[l].ndof));
+        RET(allocT(&g->lv[l].q32, g->lv[l].ndof));
+    }
+    g->ls_nb = (int)std::min<long long>(2LL * g->sms, std::max<long long>(1, (g->ndof + 1023) / 1024));
+    RET(allocT(&g->ls_partial, (size_t)2 * g->ls_nb));
+    RET(allocT(&g->ls_alpha, 8));
+    return GF_OK;
+}
+
+template <typename T>
+int coarse_correct(gf_grid* g, int l, T* x, const T* xc, T* c, const T* r, double theta, const int* halt)
+{
+    Level& lev = g->lv[l];
+    if (!(theta > 0.0)) {
+        LAUNCH(g, nblk(lev.nodes), 256, (gf::prolong_add_kernel<T, T>), x, xc, lev.dims(), halt);
+        return GF_OK;
+    }
+    CK(cudaMemsetAsync(c, 0, sizeof(T) * lev.ndof, g->cur_stream));
+    LAUNCH(g, nblk(lev.nodes), 256, (gf::prolong_add_kernel<T, T>), c, xc, lev.dims(), halt);
+    RET((stencil<T, T, gf::ST_APPLY>(g, l, (const T*)c, (const T*)nullptr, LvBuf<T>::q(lev), LvBuf<T>::E(lev),
+                                     k0<T>(g), T(0), halt)));
+    const int nb = (int)std::min<long long>(g->ls_nb, std::max<long long>(1, (lev.ndof + 1023) / 1024));
+    LAUNCH(g, nb, gf::LS_THREADS, gf::ls_dots_kernel<T>, (const T*)c, r, (const T*)LvBuf<T>::q(lev), lev.ndof,
+           g->ls_partial, halt);
+    LAUNCH(g, 1, 32, gf::ls_finish_kernel, (const double*)g->ls_partial, nb, theta, g->ls_alpha + l, halt);
+    LAUNCH(g, 2 * g->sms, 256, gf::ls_axpy_kernel<T>, x, (const T*)c, lev.ndof, (const double*)(g->ls_alpha + l), halt);
+    return GF_OK;
 }
 
 int applyK64(gf_grid* g, const double* u, double* y, const int* halt)
@@ -791,7 +843,7 @@ int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
     double* zj = g->Z + (long long)j * ld;
     double* w = g->V + (long long)(j + 1) * ld;
     const int* halt = &g->st->status;
-    RET(vcycle_dispatch(g, vj, zj, o->prec, o->nu1, o->nu2, o->omega, halt, o->smoother));
+    RET(vcycle_dispatch(g, vj, zj, o->prec, o->nu1, o->nu2, o->omega, halt, o->smoother, o->ls_ratio));
     if (o->outer == 2) RET(applyKsplit_dd(g, zj, g->Vd + (long long)(j + 1) * ld, halt));
     else RET(applyOuter(g, zj, w, halt, o->outer));
     switch (pick_nv(j + 1)) {
@@ -828,8 +880,9 @@ int run_step(gf_grid* g, int j, const gf_solve_opts* o)
 {
     if (!g->use_graphs) return arnoldi_step(g, j, o);
     if (g->gkey_prec != o->prec || g->gkey_nu1 != o->nu1 || g->gkey_nu2 != o->nu2 || g->gkey_omega != o->omega ||
-        g->gkey_outer != o->outer || g->gkey_smoother != o->smoother) {
+        g->gkey_outer != o->outer || g->gkey_smoother != o->smoother || g->gkey_ls != o->ls_ratio) {
         drop_graphs(g);
+        g->gkey_ls = o->ls_ratio;
         g->gkey_outer = o->outer;
         g->gkey_smoother = o->smoother;
         g->gkey_prec = o->prec;
@@ -908,6 +961,7 @@ int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, g
     const int m = o->restart;
     RET(ensure_krylov(g, m, o->kmax, o->outer));
     if (o->smoother == 1) RET(ensure_cheb(g, o->prec));
+    if (o->ls_ratio > 0.0) RET(ensure_ls(g));
     const int NX0 = g->nx + 1;
     // fixed entries of u are written as 0
     LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, double>), u, u, g->ndof, NX0, nullptr);
@@ -984,6 +1038,8 @@ int validate_opts(const gf_solve_opts* o)
     if (o->outer < 0 || o->outer > 2)
         return set_err(GF_ERR_ARG, "outer must be 0 (FP64), 1 (split K*u) or 2 (split K*u, double-float CGS2)");
     if (o->smoother != 0 && o->smoother != 1) return set_err(GF_ERR_ARG, "smoother must be 0 (Jacobi) or 1 (Chebyshev)");
+    if (!(o->ls_ratio >= 0.0 && std::isfinite(o->ls_ratio))) return set_err(GF_ERR_ARG, "ls_ratio must be finite and >= 0");
+    if (o->ls_ratio > 0.0 && o->smoother != 0) return set_err(GF_ERR_ARG, "ls_ratio > 0 needs smoother 0");
     return GF_OK;
 }
 
@@ -1309,7 +1365,9 @@ int gf_destroy_grid(gf_grid* g)
         cudaFree(L.E64); cudaFree(L.E32);
         cudaFree(L.b64); cudaFree(L.x64); cudaFree(L.t64); cudaFree(L.r64);
         cudaFree(L.b32); cudaFree(L.x32); cudaFree(L.t32); cudaFree(L.r32);
+        cudaFree(L.q64); cudaFree(L.q32);
     }
+    cudaFree(g->ls_partial); cudaFree(g->ls_alpha);
     cudaFree(g->Ainv); cudaFree(g->Agj); cudaFree(g->dflag); cudaFree(g->cheb); cudaFree(g->cheb_ss);
     cudaFree(g->rho64); cudaFree(g->rho16); cudaFree(g->work); cudaFree(g->partial);
     cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Vd); cudaFree(g->pdd); cudaFree(g->ddticket); cudaFree(g->Z); cudaFree(g->hist);
@@ -1465,7 +1523,8 @@ int gf_vcycle_ex(gf_grid* g, const double* v, double* z, const gf_solve_opts* o)
     if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
     RET(set_device(g));
     if (o->smoother == 1) RET(ensure_cheb(g, o->prec));
-    return vcycle_dispatch(g, v, z, o->prec, o->nu1, o->nu2, o->omega, nullptr, o->smoother);
+    if (o->ls_ratio > 0.0) RET(ensure_ls(g));
+    return vcycle_dispatch(g, v, z, o->prec, o->nu1, o->nu2, o->omega, nullptr, o->smoother, o->ls_ratio);
 }
 
 int gf_chebyshev_lambda(gf_grid* g, int prec, double* lam, int n)

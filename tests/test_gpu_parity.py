@@ -208,6 +208,64 @@ def test_solve_mixed_tensor_core_stencil(gf, monkeypatch):
     assert O.true_residual(m, E, O.element_stiffness(), f, res["1"][1]) <= 1.5e-6
 
 
+# -------------------------------------------- line-searched coarse correction --
+# gf_solve_opts.ls_ratio = theta: every level's coarse correction scaled by the
+# energy-optimal alpha = (c.r)/(c.Kc) and kept only if alpha >= theta (theta 1e30
+# rejects all corrections: the V-cycle is then smoothing only).
+@pytest.mark.parametrize("theta", [0.1, 0.9, 1e30])
+@pytest.mark.parametrize("nx,ny,nz,L", [(16, 8, 8, 3), (24, 10, 6, 2), (8, 4, 4, 3)])
+def test_vcycle_line_search_fp64_parity(gf, nx, ny, nz, L, theta):
+    g, m, rho = make(gf, nx, ny, nz, L, seed=2, kind="bernoulli")
+    E = O.young_modulus(rho, 1e-3, 3.0)
+    H = O.build_hierarchy(m, E, L, ls_ratio=theta)
+    v = np.where(m.fixed, 0, synth.random_vector(m.n_dof, 9))
+    z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.vcycle(dev(v), z, gf.GF_FP64, ls_ratio=theta)
+    assert relerr(host(z), O.vcycle(H, v)) <= 1e-10
+
+
+def test_vcycle_line_search_mixed_parity(gf):
+    nx, ny, nz, L = 16, 8, 8, 3
+    g, m, rho = make(gf, nx, ny, nz, L, seed=2, kind="bernoulli")
+    H = O.build_hierarchy(m, O.young_modulus(bf16_round(rho), 1e-3, 3.0), L, ls_ratio=0.1)
+    H.levels[-1].chol = O.build_hierarchy(m, O.young_modulus(rho, 1e-3, 3.0), L).levels[-1].chol
+    v = np.where(m.fixed, 0, synth.random_vector(m.n_dof, 9))
+    z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.vcycle(dev(v), z, gf.GF_MIXED, ls_ratio=0.1)
+    assert relerr(host(z), O.vcycle(H, v)) <= 1e-4
+
+
+def test_solve_line_search_fp64_parity(gf):
+    nx, ny, nz, L = 16, 8, 8, 3
+    g, m, rho = make(gf, nx, ny, nz, L, seed=43, rho_min=1e-6, kind="bernoulli")
+    E = O.young_modulus(rho, 1e-6, 3.0)
+    f = O.cantilever_load(m)
+    ref = O.solve_at_floor(O.SolverSetup(m, rho, p=3.0, n_levels=L, ls_ratio=0.1), f, 1e-6, 120, 1e-6)[0]
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    out = g.solve(dev(f), u, kmax=120, prec=gf.GF_FP64, ls_ratio=0.1)
+    assert abs(out["iters"] - ref.iters) <= 1 and out["flag"] == ref.flag
+    h = min(out["iters"], ref.iters)
+    assert np.allclose(out["history"][:h], ref.history[:h], rtol=1e-6)
+    for prec, outer in ((gf.GF_MIXED, 2), (gf.GF_FP64, 0)):   # mixed runs the tiled V-cycle, captured graphs
+        u.zero_()
+        o2 = g.solve(dev(f), u, kmax=120, prec=prec, outer=outer, ls_ratio=0.1)
+        if o2["flag"] == gf.GF_FLAG_CONVERGED:
+            assert O.true_residual(m, E, O.element_stiffness(), f, host(u)) <= 1.5e-6
+
+
+def test_line_search_arguments(gf):
+    g, m, rho = make(gf, 8, 4, 4, 2, seed=1)
+    f = dev(O.cantilever_load(m))
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    for kw in (dict(ls_ratio=float("inf")), dict(ls_ratio=-0.1), dict(ls_ratio=0.9, smoother=1)):
+        with pytest.raises(gf.GFError):
+            g.solve(f, u, kmax=5, **kw)
+    g1, m1, _ = make(gf, 4, 2, 2, 1, seed=1)
+    with pytest.raises(gf.GFError):
+        g1.solve(dev(O.cantilever_load(m1)), torch.zeros(g1.n_dof, dtype=torch.float64, device="cuda"),
+                 kmax=5, ls_ratio=0.9)
+
+
 # ------------------------------------------------------------- Chebyshev smoother --
 @pytest.mark.parametrize("nx,ny,nz,L", [(16, 8, 8, 3), (24, 10, 6, 2), (8, 4, 4, 3)])
 def test_chebyshev_lambda_and_vcycle_fp64_parity(gf, nx, ny, nz, L):

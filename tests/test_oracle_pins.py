@@ -369,32 +369,39 @@ def test_conditioning_follows_c_over_rho_min_and_screen():
     assert O.conditioning_screen(1e-8, 1.0, 1e-6, 1e-6) == pytest.approx(1e2 * 2.0 ** -52 / 1e-6 * 1e0, rel=1e-15)
 
 
-def test_line_search_closed_forms():
-    r = synth.random_vector(50, 1)
-    a, kept = O.line_search(r, 2.0 * r, 0.99)
-    assert kept and a == pytest.approx(0.5, rel=1e-15)                 # q = 2r: alpha 1/2, residual 0
-    p = synth.random_vector(50, 2)
-    p -= (p @ r) / (r @ r) * r                                           # q orthogonal to r
-    assert O.line_search(r, p, 0.99) == (0.0, False)
-    assert O.line_search(r, -r, 0.99) == (0.0, False)                    # alpha = -1: rejected
-    assert O.line_search(r, np.zeros(50), 0.99) == (0.0, False)
-    # q at angle phi to r: kept iff sin(phi) <= theta (||r - alpha q|| = sin(phi) ||r||)
-    for phi in (0.3, 1.0, 1.4):
-        q = 3.0 * (np.cos(phi) * r / np.linalg.norm(r) + np.sin(phi) * p / np.linalg.norm(p))
-        a, kept = O.line_search(r, q, math.sin(1.0) + 1e-12)
-        assert kept == (phi <= 1.0)
-        if kept:
-            assert a == pytest.approx(np.cos(phi) * np.linalg.norm(r) / 3.0, rel=1e-12)
+def test_line_search_closed_forms_and_galerkin_step_one():
+    """alpha = (c.r)/(c.Kc): r = gamma K c gives gamma exactly; kept iff alpha >= theta.
+    For a two-level Galerkin hierarchy with the exact coarse solve, c = P K_c^{-1} P^T r,
+    so c.r = c.K c and alpha = 1: the energy-optimal step of an exact Galerkin correction."""
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((30, 30))
+    K = B @ B.T + 30 * np.eye(30)
+    c = synth.random_vector(30, 1)
+    for gamma, kept in ((0.5, True), (1.7, True), (0.05, False), (-1.0, False)):
+        a, k = O.line_search(gamma * (K @ c), c, K @ c, 0.1)
+        assert k == kept and (a == pytest.approx(gamma, rel=1e-13) if kept else a == 0.0)
+    assert O.line_search(K @ c, np.zeros(30), np.zeros(30), 0.1) == (0.0, False)
+    m = O.Mesh(8, 4, 4)
+    E = O.young_modulus(synth.bernoulli_density(8, 4, 4, 43, 0.35), 1e-3, 3.0)
+    H = O.build_hierarchy(m, E, 2, coarse="galerkin")
+    fine, crs = H.levels
+    r = np.where(m.fixed, 0.0, synth.random_vector(m.n_dof, 7))
+    bc = fine.P.T @ r
+    bc[crs.mesh.fixed] = 0.0
+    cc = fine.P @ O.coarse_solve(crs, bc)
+    cc[m.fixed] = 0.0
+    a, kept = O.line_search(r, cc, O.level_apply(fine, cc), 0.1)
+    assert kept and abs(a - 1.0) < 1e-10
 
 
-def test_line_searched_vcycle_never_raises_the_corrected_residual():
-    """Inside the V-cycle the kept correction leaves r - alpha K c, whose norm is at most
-    theta ||r||; the V-cycle still preconditions FGMRES, and theta -> 0 rejects everything
-    (the V-cycle is then two-sided smoothing only)."""
+def test_line_searched_vcycle_decreases_energy_and_preconditions():
+    """The kept step lowers the energy J(x) = x.Kx/2 - b.x by (c.r)^2 / (2 c.Kc) exactly;
+    the line-searched V-cycle still preconditions FGMRES; theta above every alpha rejects
+    all corrections (the V-cycle is then smoothing only)."""
     m, E, H = _hier(seed=5)
     K0 = H.levels[0].K0
     b = np.where(m.fixed, 0.0, synth.random_vector(m.n_dof, 4))
-    Hl = O.build_hierarchy(m, E, len(H.levels), ls_ratio=0.99)
+    Hl = O.build_hierarchy(m, E, len(H.levels), ls_ratio=0.1)
     lev = Hl.levels[0]
     x = O._smooth(Hl, lev, np.zeros_like(b), b, Hl.nu1)
     r = b - O.level_apply(lev, x)
@@ -402,12 +409,14 @@ def test_line_searched_vcycle_never_raises_the_corrected_residual():
     bc[Hl.levels[1].mesh.fixed] = 0.0
     c = lev.P @ O.vcycle(Hl, bc, 1)
     c[m.fixed] = 0.0
-    a, kept = O.line_search(r, O.level_apply(lev, c), 0.99)
-    assert kept and np.linalg.norm(b - O.level_apply(lev, x + a * c)) <= 0.99 * np.linalg.norm(r) * (1 + 1e-12)
+    q = O.level_apply(lev, c)
+    a, kept = O.line_search(r, c, q, 0.1)
+    J = lambda y: 0.5 * y @ O.level_apply(lev, y) - b @ y
+    assert kept and J(x + a * c) - J(x) == pytest.approx(-(c @ r) ** 2 / (2 * (c @ q)), rel=1e-8)
     f = O.cantilever_load(m)
     res = O.fgmres(lambda v: O.apply_K(m, E, K0, v), lambda v: O.vcycle(Hl, v), f, restart=30, kmax=200, tol=1e-8)
     assert res.flag == O.CONVERGED
-    H0 = O.build_hierarchy(m, E, len(H.levels), ls_ratio=1e-12)        # rejects every correction
+    H0 = O.build_hierarchy(m, E, len(H.levels), ls_ratio=1e30)         # rejects every correction
     smooth_only = O._smooth(H0, H0.levels[0], O._smooth(H0, H0.levels[0], np.zeros_like(b), b, 2), b, 2)
     assert np.array_equal(O.vcycle(H0, b), smooth_only)
 
