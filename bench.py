@@ -108,6 +108,20 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def over_ranks(dist, device, maxes, sums):
+    """Job-wide figures across ranks: the slowest rank's values (max: times) and the
+    totals (sum: units processed, launches). With one process they pass through."""
+    if dist is None:
+        return [float(v) for v in maxes], [float(v) for v in sums]
+    import torch
+    t = torch.tensor([float(v) for v in maxes] + [float(v) for v in sums], dtype=torch.float64, device=device)
+    mx, sm = t.clone(), t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    k = len(maxes)
+    return [float(v) for v in mx[:k]], [float(v) for v in sm[k:]]
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -291,13 +305,8 @@ def run_b300(args):
     clocks = clock.stop()
     ms = e0.elapsed_time(e1)
     launches = g.stats()["kernel_launches"]
-    if dist is not None:
-        t = torch.tensor([ms, accepted, launches], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms, accepted, launches = float(mx[0]), int(sm[1]), int(sm[2])
+    (ms,), (accepted, launches) = over_ranks(dist, "cuda", [ms], [accepted, launches])
+    accepted, launches = int(accepted), int(launches)
     value = accepted / (ms / 1000.0)
 
     # ---- kernels timed alone on the grid's stream (CUDA events, after warm-up)
@@ -370,12 +379,8 @@ def run_b300(args):
             acc_b += sum(r["status"] == gf.GF_ACCEPTED for r in bt.select_floor(pol))
         barrier()
         dt_b = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt_b, acc_b], dtype=torch.float64, device="cuda")
-            mx, smv = t.clone(), t.clone()
-            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-            dist.all_reduce(smv, op=dist.ReduceOp.SUM)
-            dt_b, acc_b = float(mx[0]), int(smv[1])
+        (dt_b,), (acc_b,) = over_ranks(dist, "cuda", [dt_b], [acc_b])
+        acc_b = int(acc_b)
         batched = {"value": acc_b / dt_b, "unit": UNIT, "states_per_pass": len(rhos_h), "passes": passes,
                    "timing": "host clock around blocking gf_batch_select_floor calls (barrier + synchronize)",
                    "gpu_launches": bt.kernel_launches() - launches_b0}
@@ -402,12 +407,8 @@ def run_b300(args):
             acc_e2e += int(out["status"] == gf.GF_ACCEPTED)
         barrier()
         dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt, acc_e2e], dtype=torch.float64, device="cuda")
-            mx, smv = t.clone(), t.clone()
-            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-            dist.all_reduce(smv, op=dist.ReduceOp.SUM)
-            dt, acc_e2e = float(mx[0]), int(smv[1])
+        (dt,), (acc_e2e,) = over_ranks(dist, "cuda", [dt], [acc_e2e])
+        acc_e2e = int(acc_e2e)
         e2e = {"value": acc_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * (g.n_elem + g.n_dof),
                "d2h_bytes_per_step": 8 * g.n_dof}
 
