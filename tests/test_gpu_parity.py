@@ -648,6 +648,30 @@ def test_full_size_apply_sampled(gf, dims):
     scale = np.abs(ref).max()
     for out in (y, ys):
         assert np.abs(host(out).reshape(-1, 3)[nodes] - ref).max() <= 1e-10 * scale
+    # the FP32 V-cycle operator (BF16-stored densities) at the same nodes
+    y32 = torch.zeros(g.n_dof, dtype=torch.float32, device="cuda")
+    u32 = u.astype(np.float32)
+    g.apply_K_f32(dev(u32, torch.float32), y32)
+    ref32 = _apply_at_nodes(nx, ny, nz, O.young_modulus(bf16_round(rho), 1e-6, 3.0), u32.astype(np.float64), nodes)
+    assert np.abs(host(y32).reshape(-1, 3)[nodes] - ref32).max() <= 2e-5 * np.abs(ref32).max()
+
+
+@pytest.mark.parametrize("dims", [(96, 48, 48, 5), (192, 96, 96, 5)])
+def test_full_size_guard_matches_oracle(gf, dims):
+    """At the full sizes, in the bench's mixed configuration: the library's FP64 guard on
+    the accepted solution equals the oracle's recomputed residual over every DOF."""
+    nx, ny, nz, L = dims
+    m = O.Mesh(nx, ny, nz)
+    rho = synth.smoothed_gaussian_density(nx, ny, nz, 0)
+    g = gf.create_grid(nx, ny, nz, levels=L)
+    g.set_density(dev(rho), 3.0)
+    f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.cantilever_load(f)
+    u = torch.zeros_like(f)
+    out = g.select_floor(f, u, gf.policy_defaults(solve_prec=gf.GF_MIXED, solve_outer=2))
+    assert out["status"] == gf.GF_ACCEPTED
+    eta_ref = O.true_residual(m, O.young_modulus(rho, out["rho_min"], 3.0), O.element_stiffness(), host(f), host(u))
+    assert eta_ref <= 1e-6 * (1 + 1e-9) and abs(out["eta"] - eta_ref) <= 1e-8 * eta_ref
 
 
 def _apply_at_nodes(nx, ny, nz, E, u, nodes):
