@@ -47,6 +47,10 @@ component of Table solver-config, step and acceptance test readings): the prolon
 correction c is scaled by the energy-optimal alpha = (c.r)/(c.K c), computed from the
 residual, and dropped unless alpha >= theta. (Minimising ||r - alpha K c|| instead, or
 rejecting on the residual norm before post-smoothing, cripples this V-cycle: measured.)
+Fine-level adaptive correction (optional, fine_steps > 0; Table solver-config): after
+the V-cycle, fine_steps steps of an inner FGMRES(fine_steps) on the fine-level residual
+equation, preconditioned by the node-block Jacobi operator, applied only if it lowers
+the recomputed residual norm.
 True-residual checks (optional): every c steps of the probe the current iterate is
 formed as at a cycle end and its guard residual recomputed; the detector fires when
 one exceeds ratio (default 10) times the projected estimate of the same step, and a
@@ -366,6 +370,7 @@ class Hierarchy:
     smoother: str = "jacobi"            # or "chebyshev"
     coarse: str = "rediscretised"       # or "galerkin"
     ls_ratio: float = 0.0               # > 0: line-searched, rejectable coarse correction (theta)
+    fine_steps: int = 0                 # > 0: fine-level adaptive correction, inner FGMRES(fine_steps)
 
 
 def level_apply(level: Level, x: np.ndarray) -> np.ndarray:
@@ -389,7 +394,7 @@ def _blocks_of(K: sp.csr_matrix, mesh: Mesh) -> np.ndarray:
 
 def build_hierarchy(mesh: Mesh, E_fine: np.ndarray, n_levels: int, nu: float = 0.3,
                     nu1: int = 2, nu2: int = 2, omega: float = 0.6, smoother: str = "jacobi",
-                    coarse: str = "rediscretised", ls_ratio: float = 0.0) -> Hierarchy:
+                    coarse: str = "rediscretised", ls_ratio: float = 0.0, fine_steps: int = 0) -> Hierarchy:
     """Level l has (nx, ny, nz)/2^l elements of edge h*2^l. coarse="rediscretised":
     modulus = child mean and K0(h_l), applied matrix-free (this build's reading);
     coarse="galerkin": K_{l+1} = P^T K_l P with P the masked trilinear prolongation, the
@@ -397,7 +402,8 @@ def build_hierarchy(mesh: Mesh, E_fine: np.ndarray, n_levels: int, nu: float = 0
     With smoother="chebyshev" every smoothing level also gets lam (its lambda_max)."""
     if coarse not in ("rediscretised", "galerkin"):
         raise ValueError(coarse)
-    H = Hierarchy(nu1=nu1, nu2=nu2, omega=omega, smoother=smoother, coarse=coarse, ls_ratio=ls_ratio)
+    H = Hierarchy(nu1=nu1, nu2=nu2, omega=omega, smoother=smoother, coarse=coarse, ls_ratio=ls_ratio,
+                  fine_steps=fine_steps)
     m, E = mesh, np.asarray(E_fine, dtype=np.float64)
     Kg = None
     for l in range(n_levels):
@@ -544,6 +550,24 @@ def vcycle(H: Hierarchy, b: np.ndarray, l: int = 0) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # a6: right-preconditioned FGMRES(m) with CGS2 and Givens rotations
 # ----------------------------------------------------------------------------
+def precondition(H: Hierarchy, v: np.ndarray) -> np.ndarray:
+    """The preconditioner the outer FGMRES applies: one V-cycle, then (fine_steps > 0) the
+    fine-level adaptive correction of Table solver-config: fine_steps steps of an inner
+    FGMRES(fine_steps) from d = 0 on K d = r, r = v - K z, preconditioned by the 3x3
+    node-block Jacobi operator, applied only if it reduces the recomputed residual norm
+    (||v - K (z + d)|| < ||r||)."""
+    z = vcycle(H, v)
+    if H.fine_steps <= 0:
+        return z
+    lev = H.levels[0]
+    r = v - level_apply(lev, z)
+    d = fgmres(lambda w: level_apply(lev, w), lambda w: block_jacobi_apply(lev, w), r,
+               restart=H.fine_steps, kmax=H.fine_steps, tol=0.0).x
+    if np.linalg.norm(v - level_apply(lev, z + d)) < np.linalg.norm(r):
+        z = z + d
+    return z
+
+
 @dataclass
 class SolveResult:
     x: np.ndarray
@@ -769,6 +793,7 @@ class SolverSetup:
     smoother: str = "jacobi"
     coarse: str = "rediscretised"
     ls_ratio: float = 0.0
+    fine_steps: int = 0
 
 
 def solve_at_floor(setup: SolverSetup, f: np.ndarray, rho_min: float, kmax: int, tol: float,
@@ -778,10 +803,10 @@ def solve_at_floor(setup: SolverSetup, f: np.ndarray, rho_min: float, kmax: int,
     mesh = setup.mesh
     E = young_modulus(setup.rho_hat, rho_min, setup.p)
     H = build_hierarchy(mesh, E, setup.n_levels, setup.nu, setup.nu1, setup.nu2, setup.omega, setup.smoother,
-                        setup.coarse, setup.ls_ratio)
+                        setup.coarse, setup.ls_ratio, setup.fine_steps)
     K0 = H.levels[0].K0
     fm = np.where(mesh.fixed, 0.0, f)
-    res = fgmres(lambda v: apply_K(mesh, E, K0, v), lambda v: vcycle(H, v), fm,
+    res = fgmres(lambda v: apply_K(mesh, E, K0, v), lambda v: precondition(H, v), fm,
                  restart=setup.restart, kmax=kmax, tol=tol, check_every=check_every, check_upto=check_upto,
                  true_res=lambda x: true_residual(mesh, E, K0, f, x))
     return res, E, K0

@@ -421,6 +421,27 @@ def test_line_searched_vcycle_decreases_energy_and_preconditions():
     assert np.array_equal(O.vcycle(H0, b), smooth_only)
 
 
+def test_fine_level_correction_never_raises_the_residual_and_can_be_exact():
+    """precondition(): the correction is kept only if it lowers ||v - K z||, so the result
+    is never worse than the V-cycle's; with as many inner steps as free DOFs the inner
+    Krylov solve is exact and the outer FGMRES converges at once."""
+    m, E, H = _hier(seed=5)
+    Hf = O.build_hierarchy(m, E, len(H.levels), fine_steps=12)
+    lev = Hf.levels[0]
+    for s_ in (1, 2, 3):
+        v = np.where(m.fixed, 0.0, synth.random_vector(m.n_dof, s_))
+        zv, zf = O.vcycle(Hf, v), O.precondition(Hf, v)
+        assert np.linalg.norm(v - O.level_apply(lev, zf)) <= np.linalg.norm(v - O.level_apply(lev, zv))
+        assert not np.array_equal(zv, zf)                                 # the correction was applied
+    mt = O.Mesh(2, 2, 2)
+    Et = O.young_modulus(synth.bernoulli_density(2, 2, 2, 3, 0.3), 1e-3, 3.0)
+    Ht = O.build_hierarchy(mt, Et, 2, fine_steps=int(mt.free.sum()))
+    f = O.cantilever_load(mt)
+    res = O.fgmres(lambda v: O.apply_K(mt, Et, Ht.levels[0].K0, v), lambda v: O.precondition(Ht, v), f,
+                   restart=30, kmax=10, tol=1e-10)
+    assert res.flag == O.CONVERGED and res.iters <= 2
+
+
 # ---------------------------------------------------------------- FGMRES ----
 def test_fgmres_diagonal_distinct_eigenvalues():
     d = np.array([1.0, 2.0, 2.0, 3.0, 3.0, 3.0, 5.0])
