@@ -107,6 +107,12 @@ typedef struct {
                           acceptance ratio). Needs smoother 0 and >= 2 levels; single grid only. The
                           preconditioner is then iterate-dependent, which FGMRES allows. Errors:
                           GF_ERR_ARG for a negative or non-finite value. */
+    int    fine_steps; /* 0 = off. k in [1, 32]: the fine-level adaptive correction of Table
+                          solver-config after every V-cycle: k steps of an inner FGMRES(k) from d = 0
+                          on K d = r (r = v - K z, z the V-cycle's output), preconditioned by the 3x3
+                          node-block Jacobi operator, in the V-cycle's precision; z += d only if the
+                          recomputed ||r - K d|| < ||r||. All on the device (inside the captured
+                          steps). Single grid only. Other values: GF_ERR_ARG. */
 } gf_solve_opts;
 
 typedef struct {

@@ -588,6 +588,7 @@ int gf_batch_select_floor(gf_batch* b, const gf_policy* pol, gf_select_info* inf
     if (pol->selector == GF_SEL_REUSE) return set_err(GF_ERR_ARG, "GF_SEL_REUSE is single-grid only");
     if (pol->true_check_every != 0) return set_err(GF_ERR_ARG, "true_check_every is single-grid only");
     if (pol->solve.ls_ratio != 0.0) return set_err(GF_ERR_ARG, "ls_ratio is single-grid only");
+    if (pol->solve.fine_steps != 0) return set_err(GF_ERR_ARG, "fine_steps is single-grid only");
     const int B = b->B;
     for (int i = 0; i < B; ++i)
         if (!b->g[i]->has_density) return set_err(GF_ERR_STATE, "state " + std::to_string(i) + " has no density");

@@ -15,6 +15,7 @@
 #include "vcycle_cluster.cuh"
 #include "lanczos.cuh"
 #include "linesearch.cuh"
+#include "finecorr.cuh"
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -141,6 +142,13 @@ struct gf_grid {
     int m_alloc = 0;
     double *V = nullptr, *Z = nullptr, *partial = nullptr, *work = nullptr;
     double* ckx = nullptr;            // iterate of a probe true-residual check
+    // fine-level adaptive correction: inner basis V (steps + 1), Z (steps), r, d, q, z in the
+    // V-cycle's precision (fc_es bytes per entry), the inner solver's state and partial sums
+    void *fcV = nullptr, *fcZ = nullptr, *fcR = nullptr, *fcD = nullptr, *fcQ = nullptr, *fcZT = nullptr;
+    gf::FcState* fc = nullptr;
+    double* fc_partial = nullptr;
+    int fc_steps = 0, fc_es = 0, fc_nb = 0;
+    int gkey_fine = -1;               // fine_steps the captured Arnoldi steps were built with
     double* ls_partial = nullptr;     // line search: per-block dot products
     double* ls_alpha = nullptr;       // line search: alpha of each level (device)
     int ls_nb = 0;
@@ -580,8 +588,25 @@ int vcycle_cheb(gf_grid* g, const double* v, double* z, int nu1, int nu2, const 
     return GF_OK;
 }
 
+int vcycle_dispatch_plain(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2, double omega,
+                          const int* halt, int smoother, double ls);
+template <typename T>
+int fine_correct(gf_grid* g, const double* v, double* z, int steps, const int* halt);
+
+// The preconditioner: one V-cycle, then (fine > 0) the fine-level adaptive correction.
 int vcycle_dispatch(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2, double omega,
-                    const int* halt, int smoother = 0, double ls = 0.0)
+                    const int* halt, int smoother = 0, double ls = 0.0, int fine = 0)
+{
+    RET(vcycle_dispatch_plain(g, v, z, prec, nu1, nu2, omega, halt, smoother, ls));
+    if (fine <= 0) return GF_OK;
+    if (!g->fc || g->fc_steps < fine || g->fc_es != (prec == GF_MIXED ? (int)sizeof(float) : (int)sizeof(double)))
+        return set_err(GF_ERR_STATE, "fine-level correction buffers not set up");
+    if (prec == GF_MIXED) return fine_correct<float>(g, v, z, fine, halt);
+    return fine_correct<double>(g, v, z, fine, halt);
+}
+
+int vcycle_dispatch_plain(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2, double omega,
+                          const int* halt, int smoother, double ls)
 {
     if (ls > 0.0 && (smoother == 1 || g->vc_l0 > 0 || g->L < 2 || !g->ls_alpha))
         return set_err(GF_ERR_ARG, "the line-searched coarse correction needs Jacobi smoothing, >= 2 levels and no "
@@ -596,6 +621,81 @@ int vcycle_dispatch(gf_grid* g, const double* v, double* z, int prec, int nu1, i
         return vcycle_impl<float>(g, v, z, nu1, nu2, (float)omega, halt, ls);
     }
     return vcycle_impl<double>(g, v, z, nu1, nu2, omega, halt, ls);
+}
+
+void drop_graphs(gf_grid* g);
+
+// buffers of the fine-level adaptive correction for `steps` inner steps in the V-cycle
+// precision of `prec` (outside any graph capture)
+int ensure_fc(gf_grid* g, int steps, int prec)
+{
+    const int es = (prec == GF_MIXED) ? (int)sizeof(float) : (int)sizeof(double);
+    if (g->fc && g->fc_steps >= steps && g->fc_es == es) return GF_OK;
+    drop_graphs(g);
+    void** bufs[6] = {&g->fcV, &g->fcZ, &g->fcR, &g->fcD, &g->fcQ, &g->fcZT};
+    for (void** b : bufs) {
+        cudaFree(*b);
+        *b = nullptr;
+    }
+    const size_t n = (size_t)g->ndof;
+    RET(allocT((unsigned char**)&g->fcV, (size_t)(steps + 1) * n * es));
+    RET(allocT((unsigned char**)&g->fcZ, (size_t)steps * n * es));
+    RET(allocT((unsigned char**)&g->fcR, n * es));
+    RET(allocT((unsigned char**)&g->fcD, n * es));
+    RET(allocT((unsigned char**)&g->fcQ, n * es));
+    RET(allocT((unsigned char**)&g->fcZT, n * es));
+    if (!g->fc) {
+        RET(allocT(&g->fc, 1));
+        CK(cudaMemset(g->fc, 0, sizeof(gf::FcState)));
+        // 2 blocks per SM (8 per SM measured slower: 2.4 -> 3.6 ms per outer step at 96x48x48)
+        g->fc_nb = (int)std::min<long long>(2LL * g->sms, std::max<long long>(1, (g->ndof + 1023) / 1024));
+        RET(allocT(&g->fc_partial, (size_t)g->fc_nb * gf::FC_SLOTS));
+    }
+    g->fc_steps = steps;
+    g->fc_es = es;
+    return GF_OK;
+}
+
+// the fine-level adaptive correction of z = V-cycle(v), in precision T (finecorr.cuh)
+template <typename T>
+int fine_correct(gf_grid* g, const double* v, double* z, int steps, const int* halt)
+{
+    Level& lev = g->lv[0];
+    const long long n = g->ndof;
+    T *V = (T*)g->fcV, *Z = (T*)g->fcZ, *r = (T*)g->fcR, *d = (T*)g->fcD, *q = (T*)g->fcQ;
+    gf::FcState* st = g->fc;
+    const int nb = g->fc_nb;
+    if constexpr (sizeof(T) == sizeof(double)) {   // r = v - K z
+        RET((stencil<double, double, gf::ST_RESID>(g, 0, z, v, (double*)r, lev.E64, g->K0d, 0.0, halt)));
+    } else {
+        float* zt = (float*)g->fcZT;
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, float>), (const double*)z, zt, n, g->nx + 1,
+               halt);
+        RET((tiled_f32<gf::ST_RESID, double, float>(g, 0, zt, v, (float*)r, lev.E32, 0.0f, halt)));
+    }
+    LAUNCH(g, nb, gf::FC_THREADS, gf::fc_start_kernel<T>, (const T*)r, n, st, g->fc_partial, halt);
+    LAUNCH(g, 2 * g->sms, 256, gf::fc_scale_kernel<T>, (const T*)r, V, n, (const gf::FcState*)st);
+    const int* stop = &st->stop;
+    for (int j = 0; j < steps; ++j) {
+        T* vj = V + (long long)j * n;
+        T* zj = Z + (long long)j * n;
+        T* w = V + (long long)(j + 1) * n;
+        LAUNCH(g, nblk(lev.nodes), 256, (gf::first_sweep_kernel<T, T, T>), (const T*)vj, zj, LvBuf<T>::E(lev),
+               lev.dims(), k0<T>(g), T(1), stop);
+        RET((stencil<T, T, gf::ST_APPLY>(g, 0, (const T*)zj, (const T*)nullptr, w, LvBuf<T>::E(lev), k0<T>(g), T(0),
+                                         stop)));
+        LAUNCH(g, nb, gf::FC_THREADS, gf::fc_dots1_kernel<T>, (const T*)V, n, (const T*)w, n, j, st, g->fc_partial);
+        LAUNCH(g, nb, gf::FC_THREADS, gf::fc_dots2_kernel<T>, (const T*)V, n, w, n, j, st, g->fc_partial);
+        LAUNCH(g, nb, gf::FC_THREADS, gf::fc_norm_kernel<T>, (const T*)V, n, w, n, j, steps, st, g->fc_partial);
+        if (j + 1 < steps) LAUNCH(g, 2 * g->sms, 256, gf::fc_vscale_kernel<T>, w, n, (const gf::FcState*)st);
+    }
+    LAUNCH(g, 1, 32, gf::fc_backsolve_kernel, st);
+    LAUNCH(g, 2 * g->sms, 256, gf::fc_combine_kernel<T>, (const T*)Z, n, d, n, (const gf::FcState*)st);
+    RET((stencil<T, T, gf::ST_APPLY>(g, 0, (const T*)d, (const T*)nullptr, q, LvBuf<T>::E(lev), k0<T>(g), T(0),
+                                     &st->skip)));
+    LAUNCH(g, nb, gf::FC_THREADS, gf::fc_accept_kernel<T>, (const T*)r, (const T*)q, n, st, g->fc_partial);
+    LAUNCH(g, 2 * g->sms, 256, gf::fc_apply_kernel<T>, z, (const T*)d, n, (const gf::FcState*)st);
+    return GF_OK;
 }
 
 // buffers of the line-searched coarse correction (outside any graph capture)
@@ -843,7 +943,8 @@ int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
     double* zj = g->Z + (long long)j * ld;
     double* w = g->V + (long long)(j + 1) * ld;
     const int* halt = &g->st->status;
-    RET(vcycle_dispatch(g, vj, zj, o->prec, o->nu1, o->nu2, o->omega, halt, o->smoother, o->ls_ratio));
+    RET(vcycle_dispatch(g, vj, zj, o->prec, o->nu1, o->nu2, o->omega, halt, o->smoother, o->ls_ratio,
+                        o->fine_steps));
     if (o->outer == 2) RET(applyKsplit_dd(g, zj, g->Vd + (long long)(j + 1) * ld, halt));
     else RET(applyOuter(g, zj, w, halt, o->outer));
     switch (pick_nv(j + 1)) {
@@ -880,9 +981,11 @@ int run_step(gf_grid* g, int j, const gf_solve_opts* o)
 {
     if (!g->use_graphs) return arnoldi_step(g, j, o);
     if (g->gkey_prec != o->prec || g->gkey_nu1 != o->nu1 || g->gkey_nu2 != o->nu2 || g->gkey_omega != o->omega ||
-        g->gkey_outer != o->outer || g->gkey_smoother != o->smoother || g->gkey_ls != o->ls_ratio) {
+        g->gkey_outer != o->outer || g->gkey_smoother != o->smoother || g->gkey_ls != o->ls_ratio ||
+        g->gkey_fine != o->fine_steps) {
         drop_graphs(g);
         g->gkey_ls = o->ls_ratio;
+        g->gkey_fine = o->fine_steps;
         g->gkey_outer = o->outer;
         g->gkey_smoother = o->smoother;
         g->gkey_prec = o->prec;
@@ -962,6 +1065,7 @@ int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, g
     RET(ensure_krylov(g, m, o->kmax, o->outer));
     if (o->smoother == 1) RET(ensure_cheb(g, o->prec));
     if (o->ls_ratio > 0.0) RET(ensure_ls(g));
+    if (o->fine_steps > 0) RET(ensure_fc(g, o->fine_steps, o->prec));
     const int NX0 = g->nx + 1;
     // fixed entries of u are written as 0
     LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, double>), u, u, g->ndof, NX0, nullptr);
@@ -1040,6 +1144,7 @@ int validate_opts(const gf_solve_opts* o)
     if (o->smoother != 0 && o->smoother != 1) return set_err(GF_ERR_ARG, "smoother must be 0 (Jacobi) or 1 (Chebyshev)");
     if (!(o->ls_ratio >= 0.0 && std::isfinite(o->ls_ratio))) return set_err(GF_ERR_ARG, "ls_ratio must be finite and >= 0");
     if (o->ls_ratio > 0.0 && o->smoother != 0) return set_err(GF_ERR_ARG, "ls_ratio > 0 needs smoother 0");
+    if (o->fine_steps < 0 || o->fine_steps > gf::FC_MAX) return set_err(GF_ERR_ARG, "fine_steps in [0, 32]");
     return GF_OK;
 }
 
@@ -1368,6 +1473,8 @@ int gf_destroy_grid(gf_grid* g)
         cudaFree(L.q64); cudaFree(L.q32);
     }
     cudaFree(g->ls_partial); cudaFree(g->ls_alpha);
+    cudaFree(g->fcV); cudaFree(g->fcZ); cudaFree(g->fcR); cudaFree(g->fcD); cudaFree(g->fcQ); cudaFree(g->fcZT);
+    cudaFree(g->fc); cudaFree(g->fc_partial);
     cudaFree(g->Ainv); cudaFree(g->Agj); cudaFree(g->dflag); cudaFree(g->cheb); cudaFree(g->cheb_ss);
     cudaFree(g->rho64); cudaFree(g->rho16); cudaFree(g->work); cudaFree(g->partial);
     cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Vd); cudaFree(g->pdd); cudaFree(g->ddticket); cudaFree(g->Z); cudaFree(g->hist);
@@ -1524,7 +1631,9 @@ int gf_vcycle_ex(gf_grid* g, const double* v, double* z, const gf_solve_opts* o)
     RET(set_device(g));
     if (o->smoother == 1) RET(ensure_cheb(g, o->prec));
     if (o->ls_ratio > 0.0) RET(ensure_ls(g));
-    return vcycle_dispatch(g, v, z, o->prec, o->nu1, o->nu2, o->omega, nullptr, o->smoother, o->ls_ratio);
+    if (o->fine_steps > 0) RET(ensure_fc(g, o->fine_steps, o->prec));
+    return vcycle_dispatch(g, v, z, o->prec, o->nu1, o->nu2, o->omega, nullptr, o->smoother, o->ls_ratio,
+                           o->fine_steps);
 }
 
 int gf_chebyshev_lambda(gf_grid* g, int prec, double* lam, int n)

@@ -266,6 +266,68 @@ def test_line_search_arguments(gf):
                  kmax=5, ls_ratio=0.9)
 
 
+# ---------------------------------------------- fine-level adaptive correction --
+# gf_solve_opts.fine_steps = k: after the V-cycle, k steps of an inner FGMRES(k) with the
+# node-block Jacobi operator on the fine-level residual equation, applied only if the
+# recomputed residual norm drops (oracle precondition()).
+@pytest.mark.parametrize("steps", [1, 5, 20])
+@pytest.mark.parametrize("nx,ny,nz,L", [(16, 8, 8, 3), (8, 4, 4, 3)])
+def test_fine_correction_fp64_parity(gf, nx, ny, nz, L, steps):
+    g, m, rho = make(gf, nx, ny, nz, L, seed=2, kind="bernoulli")
+    H = O.build_hierarchy(m, O.young_modulus(rho, 1e-3, 3.0), L, fine_steps=steps)
+    v = np.where(m.fixed, 0, synth.random_vector(m.n_dof, 9))
+    z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.vcycle(dev(v), z, gf.GF_FP64, fine_steps=steps)
+    ref = O.precondition(H, v)
+    assert relerr(host(z), ref) <= 1e-9
+    assert not np.allclose(ref, O.vcycle(H, v))                 # the correction took effect
+
+
+def test_fine_correction_mixed_lowers_the_residual(gf):
+    nx, ny, nz, L = 16, 8, 8, 3
+    g, m, rho = make(gf, nx, ny, nz, L, seed=2, kind="bernoulli")
+    E = O.young_modulus(rho, 1e-3, 3.0)
+    H = O.build_hierarchy(m, O.young_modulus(bf16_round(rho), 1e-3, 3.0), L, fine_steps=20)
+    H.levels[-1].chol = O.build_hierarchy(m, E, L).levels[-1].chol
+    v = np.where(m.fixed, 0, synth.random_vector(m.n_dof, 9))
+    z0, z1 = (torch.zeros(g.n_dof, dtype=torch.float64, device="cuda") for _ in range(2))
+    g.vcycle(dev(v), z0, gf.GF_MIXED)
+    g.vcycle(dev(v), z1, gf.GF_MIXED, fine_steps=20)
+    K0 = O.element_stiffness()
+    r0 = np.linalg.norm(v - O.apply_K(m, E, K0, host(z0)))
+    r1 = np.linalg.norm(v - O.apply_K(m, E, K0, host(z1)))
+    assert r1 < 0.5 * r0
+    assert relerr(host(z1), O.precondition(H, v)) <= 1e-3
+
+
+def test_solve_fine_correction_fp64_parity(gf):
+    nx, ny, nz, L = 16, 8, 8, 3
+    g, m, rho = make(gf, nx, ny, nz, L, seed=43, rho_min=1e-3, kind="bernoulli")
+    f = O.cantilever_load(m)
+    ref = O.solve_at_floor(O.SolverSetup(m, rho, p=3.0, n_levels=L, fine_steps=20), f, 1e-3, 120, 1e-6)[0]
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    out = g.solve(dev(f), u, kmax=120, prec=gf.GF_FP64, fine_steps=20)
+    assert abs(out["iters"] - ref.iters) <= 1 and out["flag"] == ref.flag == gf.GF_FLAG_CONVERGED
+    h = min(out["iters"], ref.iters)
+    assert np.allclose(out["history"][:h], ref.history[:h], rtol=1e-6)
+    plain = g.solve(dev(f), torch.zeros_like(u), kmax=120, prec=gf.GF_FP64)
+    assert out["iters"] < plain["iters"]
+    u2 = torch.zeros_like(u)                       # mixed, captured graphs
+    o2 = g.solve(dev(f), u2, kmax=120, prec=gf.GF_MIXED, outer=2, fine_steps=20)
+    assert o2["flag"] == gf.GF_FLAG_CONVERGED and abs(o2["iters"] - ref.iters) <= 3
+    E = O.young_modulus(rho, 1e-3, 3.0)
+    assert O.true_residual(m, E, O.element_stiffness(), f, host(u2)) <= 1.5e-6
+
+
+def test_fine_correction_arguments(gf):
+    g, m, rho = make(gf, 8, 4, 4, 2, seed=1)
+    f = dev(O.cantilever_load(m))
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    for k in (-1, 33):
+        with pytest.raises(gf.GFError):
+            g.solve(f, u, kmax=5, fine_steps=k)
+
+
 # ------------------------------------------------------------- Chebyshev smoother --
 @pytest.mark.parametrize("nx,ny,nz,L", [(16, 8, 8, 3), (24, 10, 6, 2), (8, 4, 4, 3)])
 def test_chebyshev_lambda_and_vcycle_fp64_parity(gf, nx, ny, nz, L):
