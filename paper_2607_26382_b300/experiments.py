@@ -5,6 +5,7 @@
     python -m paper_2607_26382_b300.experiments oc_reuse [--iters 40]
     python -m paper_2607_26382_b300.experiments true_checks
     python -m paper_2607_26382_b300.experiments conditioning
+    python -m paper_2607_26382_b300.experiments adaptive
 
 batch102: 102 frozen states of uneven size (nx in {32,48,64,80}, ny = nz = nx/2,
   round-robin; 71 smoothed-Gaussian states with 40% of voxels at floor, 31
@@ -38,6 +39,11 @@ conditioning: the reduced floor-conditioning diagnostic of Sec. 4.1.3 on the 24x
   p = 4.5: kappa from Lanczos (60 steps on K and on the inverse), the direct
   solution's guard residual, the log-log fit of residual against kappa * eps, the
   split at kappa * eps = tau, and c = kappa * rho_min per field.
+adaptive: the paper's adaptive preconditioner components (Table solver-config) against
+  the plain V-cycle, Algorithm 1 in the mixed form: the line-searched coarse
+  correction (ls_ratio 0.1) and the fine-level correction (fine_steps 20) on the four
+  96x48x48 bench states (outer 2) and on the 102 batch102 states one at a time
+  (outer 0) at rho0 1e-6 and 1e-12: FGMRES iterations, floors, accepted states, time.
 """
 from __future__ import annotations
 
@@ -336,14 +342,66 @@ def conditioning(args):
             "rows": rows}
 
 
+def adaptive(args):
+    import torch
+    import synth
+    out = {}
+    variants = (("plain", {}), ("line search 0.1", {"solve_ls_ratio": 0.1}), ("fine 20", {"solve_fine_steps": 20}))
+    for name, kw in variants:
+        t, its, acc, floors = 0.0, 0, 0, []
+        for seed in range(4):
+            g = L.create_grid(96, 48, 48, levels=5)
+            g.set_density(torch.as_tensor(synth.smoothed_gaussian_density(96, 48, 48, seed), device="cuda"), 3.0)
+            f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+            g.cantilever_load(f)
+            u = torch.zeros_like(f)
+            pol = L.policy_defaults(solve_prec=L.GF_MIXED, solve_outer=2, **kw)
+            g.select_floor(f, u, pol)                 # warm-up: graphs captured
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = g.select_floor(f, u, pol)
+            torch.cuda.synchronize()
+            t += time.perf_counter() - t0
+            its += sum(a["iters"] for a in r["attempts"])
+            acc += int(r["status"] == L.GF_ACCEPTED)
+            floors.append(r["floor_index"])
+            g.close()
+        out[f"96x48x48 bench states, {name}"] = {"guarded_solves_per_s": 4 / t, "fgmres_iters": its, "accepted": acc,
+                                                  "floors": floors, "ms_per_iter": t / its * 1e3}
+    dims, rhos, kinds = batch_states()
+    for name, kw in variants:
+        for rho0, ladder, kmax in ((1e-6, LADDER, 200), (1e-12, [1e-3, 1e-2], 300)):
+            t, its, acc, fl = 0.0, 0, 0, []
+            for (nx, ny, nz), rho in zip(dims, rhos):
+                g = L.create_grid(nx, ny, nz, levels=4)
+                g.set_density(torch.as_tensor(rho, device="cuda"), 3.0)
+                f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+                g.cantilever_load(f)
+                u = torch.zeros_like(f)
+                pol = _policy(rho0=rho0, ladder=ladder, kmax=kmax, solve_prec=L.GF_MIXED, solve_outer=0, **kw)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = g.select_floor(f, u, pol)
+                torch.cuda.synchronize()
+                t += time.perf_counter() - t0
+                its += sum(a["iters"] for a in r["attempts"])
+                acc += int(r["status"] == L.GF_ACCEPTED)
+                fl.append(r["floor_index"])
+                g.close()
+            out[f"batch102 single, rho0 {rho0:g}, {name}"] = {
+                "seconds": t, "fgmres_iters": its, "accepted": acc,
+                "floor_index_counts": [fl.count(i) for i in range(len(ladder) + 1)]}
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch102", "oc_loop", "oc_reuse", "true_checks", "conditioning"])
+    ap.add_argument("what", choices=["batch102", "oc_loop", "oc_reuse", "true_checks", "conditioning", "adaptive"])
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--iters", type=int, default=40)
     a = ap.parse_args(argv)
     res = {"batch102": batch102, "oc_loop": oc_loop, "oc_reuse": oc_reuse, "true_checks": true_checks,
-           "conditioning": conditioning}[a.what](a)
+           "conditioning": conditioning, "adaptive": adaptive}[a.what](a)
     print(json.dumps(res), flush=True)
     return 0
 
