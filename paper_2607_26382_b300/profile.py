@@ -24,6 +24,7 @@ def main(argv=None):
     ap.add_argument("--outer", type=int, default=1,
                     help="Krylov arithmetic: 0 native FP64, 1 split-integer K*u, 2 split K*u + double-float CGS2")
     ap.add_argument("--kmax", type=int, default=200, help="iteration budget of solve_mixed")
+    ap.add_argument("--fine", type=int, default=0, help="fine-level adaptive correction steps (solve_mixed)")
     a = ap.parse_args(argv)
 
     import torch
@@ -53,7 +54,7 @@ def main(argv=None):
             g.vcycle(x, y, gf.GF_FP64)
         elif a.op == "solve_mixed":
             y.zero_()
-            g.solve(f, y, prec=gf.GF_MIXED, outer=a.outer, kmax=a.kmax)
+            g.solve(f, y, prec=gf.GF_MIXED, outer=a.outer, kmax=a.kmax, fine_steps=a.fine)
         else:
             g.set_density(torch.as_tensor(synth.smoothed_gaussian_density(nx, ny, nz, a.seed), device="cuda"), 3.0)
             g.select_floor(f, y, gf.policy_defaults(solve_prec=gf.GF_MIXED, solve_outer=a.outer))
