@@ -211,7 +211,7 @@ def profiled_traffic(profile, source, start, end):
 
 # kernel text spans hashed for the traffic figures
 FP64_KU_SPAN = ("stencil.cuh", "// (i, j, k) of node n", "// First smoothing sweep")
-FP32_ST_SPAN = FP64_KU_SPAN                # one templated per-node body serves both
+FP32_ST_SPAN = FP64_KU_SPAN                # both node-stencil bodies and their shared block update
 SPLIT_KU_SPAN = ("split_tc.cuh", "template <bool DD>", "}  // namespace gf")
 
 
@@ -341,7 +341,7 @@ def run_b300(args):
     stencil = {"bound": "alu", "achieved": flops / t_32 / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                "frac": flops / t_32 / 1e12 / fp32_peak,
                "traffic": profiled_traffic("node_stencil_fp32_96x48x48.md", *FP32_ST_SPAN),
-               "kernel": "node_stencil_kernel<float> (FP32 V-cycle stencil, fine level, 1152 flop/element)",
+               "kernel": "node_stencil_f32x2_kernel (FP32 V-cycle stencil, paired FMAs, fine level, 1152 flop/element)",
                "peak_source": fp32_note, "gdofs": g.n_dof / t_32 / 1e9, "ms_per_launch": t_32 * 1e3}
     # the Krylov operator: exact fp16 digit products on the tensor cores (5 slices),
     # issue-bound on the CUDA-core epilogue; reported as FP64-class flops per second

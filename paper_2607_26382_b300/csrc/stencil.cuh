@@ -43,6 +43,27 @@ __device__ __forceinline__ void node_coords(long long n, int NX, int NY, int& i,
     k = (int)(t / (unsigned)NY);
 }
 
+// Damped node-block Jacobi update out = x + omega * D_n^{-1} r, D_n solved by its adjugate.
+// Every product and sum is an explicit fma or a single rounded operation, so each stencil
+// kernel that calls this rounds the update identically, whatever contractions the
+// compiler picks around it.
+template <typename T, typename OT>
+__device__ __forceinline__ void node_block_update(T d00, T d11, T d22, T d01, T d02, T d12, T r0, T r1, T r2,
+                                                  const T* __restrict__ x, OT* __restrict__ out, T omega)
+{
+    const T c00 = fma(d11, d22, -(d12 * d12));
+    const T c01 = fma(d02, d12, -(d01 * d22));
+    const T c02 = fma(d01, d12, -(d02 * d11));
+    const T c11 = fma(d00, d22, -(d02 * d02));
+    const T c12 = fma(d01, d02, -(d00 * d12));
+    const T c22 = fma(d00, d11, -(d01 * d01));
+    const T det = fma(d00, c00, fma(d01, c01, d02 * c02));
+    const T s = omega / det;
+    out[0] = OT(fma(s, fma(c00, r0, fma(c01, r1, c02 * r2)), x[0]));
+    out[1] = OT(fma(s, fma(c01, r0, fma(c11, r1, c12 * r2)), x[1]));
+    out[2] = OT(fma(s, fma(c02, r0, fma(c12, r1, c22 * r2)), x[2]));
+}
+
 // MODE == ST_APPLY: out = K x
 // MODE == ST_RESID: out = b - K x
 // MODE == ST_SWEEP: out = x + omega * D_n^{-1} (b - K x)     (D_n: 3x3 node block)
@@ -157,18 +178,7 @@ __device__ __forceinline__ void stencil_node(long long n, const T* __restrict__ 
         out[3 * n + 2] = OT(r2);
         return;
     }
-    // node-block solve by the adjugate
-    const T c00 = d11 * d22 - d12 * d12;
-    const T c01 = d02 * d12 - d01 * d22;
-    const T c02 = d01 * d12 - d02 * d11;
-    const T c11 = d00 * d22 - d02 * d02;
-    const T c12 = d01 * d02 - d00 * d12;
-    const T c22 = d00 * d11 - d01 * d01;
-    const T det = d00 * c00 + d01 * c01 + d02 * c02;
-    const T s = omega / det;
-    out[3 * n + 0] = OT(x[3 * n + 0] + s * (c00 * r0 + c01 * r1 + c02 * r2));
-    out[3 * n + 1] = OT(x[3 * n + 1] + s * (c01 * r0 + c11 * r1 + c12 * r2));
-    out[3 * n + 2] = OT(x[3 * n + 2] + s * (c02 * r0 + c12 * r1 + c22 * r2));
+    node_block_update<T, OT>(d00, d11, d22, d01, d02, d12, r0, r1, r2, x + 3 * n, out + 3 * n, omega);
 }
 
 // FP32: at most 80 registers (3 blocks of 256 per SM), which the plane-wise neighbour
@@ -185,6 +195,129 @@ node_stencil_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __res
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
     stencil_node<T, ET, MODE, BT, OT>(n, x, b, out, E, d, K0, omega);
+}
+
+// ---- FP32 node stencil with paired FMAs (fma.rn.f32x2) ------------------------------
+// K0 rows 3a and 3a+1 stored as adjacent pairs, so one paired FMA advances the x and y
+// output chains of an element together; the z chain stays scalar. Every K*u chain keeps
+// the order of stencil_node (K*u bit-identical to node_stencil_kernel<float>; the sweep's
+// node-block solve may round differently in its last bit). The FP32 V-cycle default.
+struct K0Pair {
+    float2 p[8][8][3];   // (K0[3a][3b+k], K0[3a+1][3b+k]), a = output node, b = input node
+    float s[8][8][3];    // K0[3a+2][3b+k]
+};
+
+__device__ __forceinline__ void fma_f32x2(float& d0, float& d1, float2 a, float b)
+{
+    asm("{\n .reg .b64 ra, rb, rc;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %4};\n mov.b64 rc, {%0, %1};\n"
+        " fma.rn.f32x2 rc, ra, rb, rc;\n mov.b64 {%0, %1}, rc;\n}\n"
+        : "+f"(d0), "+f"(d1) : "f"(a.x), "f"(a.y), "f"(b));
+}
+
+template <int MODE, typename BT, typename OT>
+__device__ __forceinline__ void stencil_node_f32x2(long long n, const float* __restrict__ x, const BT* __restrict__ b,
+                                                   OT* __restrict__ out, const float* __restrict__ E, GridDims d,
+                                                   const K0Pair& K0, float omega)
+{
+    const int NX = d.nx + 1, NY = d.ny + 1;
+    int i, j, k;
+    node_coords(n, NX, NY, i, j, k);
+    if (i == 0) {
+        out[3 * n + 0] = OT(0);
+        out[3 * n + 1] = OT(0);
+        out[3 * n + 2] = OT(0);
+        return;
+    }
+    float a0 = 0, a1 = 0, a2 = 0;
+    float d00 = 0, d11 = 0, d22 = 0, d01 = 0, d02 = 0, d12 = 0;
+    float nb[3][3][3][3];
+    auto load_plane = [&](int dz) {
+        const int NZ = d.nz + 1;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const int ni = i - 1 + dx, nj = j - 1 + dy, nk = k - 1 + dz;
+                const bool ok = ni >= 1 && ni < NX && nj >= 0 && nj < NY && nk >= 0 && nk < NZ;
+                const long long m = n + (dx - 1) + (long long)NX * ((dy - 1) + (long long)NY * (dz - 1));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) nb[dz][dy][dx][c] = ok ? x[3 * m + c] : 0.f;
+            }
+    };
+    load_plane(0);
+    load_plane(1);
+#pragma unroll
+    for (int oz = 0; oz < 2; ++oz) {
+        if (oz == 1) load_plane(2);
+#pragma unroll
+        for (int oy = 0; oy < 2; ++oy) {
+#pragma unroll
+            for (int ox = 0; ox < 2; ++ox) {
+                const int ex = i - 1 + ox, ey = j - 1 + oy, ez = k - 1 + oz;
+                if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny || ez < 0 || ez >= d.nz) continue;
+                const float Ee = E[ex + (long long)d.nx * (ey + (long long)d.ny * ez)];
+                const int a = local_index(1 - ox, 1 - oy, 1 - oz);
+                float t0 = 0, t1 = 0, t2 = 0;
+#pragma unroll
+                for (int bz = 0; bz < 2; ++bz) {
+#pragma unroll
+                    for (int by = 0; by < 2; ++by) {
+#pragma unroll
+                        for (int bx = 0; bx < 2; ++bx) {
+                            const int bl = local_index(bx, by, bz);
+                            const float u0 = nb[oz + bz][oy + by][ox + bx][0];
+                            const float u1 = nb[oz + bz][oy + by][ox + bx][1];
+                            const float u2 = nb[oz + bz][oy + by][ox + bx][2];
+                            fma_f32x2(t0, t1, K0.p[a][bl][2], u2);
+                            fma_f32x2(t0, t1, K0.p[a][bl][1], u1);
+                            fma_f32x2(t0, t1, K0.p[a][bl][0], u0);
+                            t2 = fmaf(K0.s[a][bl][0], u0, fmaf(K0.s[a][bl][1], u1, fmaf(K0.s[a][bl][2], u2, t2)));
+                        }
+                    }
+                }
+                a0 = fmaf(Ee, t0, a0);
+                a1 = fmaf(Ee, t1, a1);
+                a2 = fmaf(Ee, t2, a2);
+                if (MODE == ST_SWEEP) {
+                    d00 = fmaf(Ee, K0.p[a][a][0].x, d00);
+                    d11 = fmaf(Ee, K0.p[a][a][1].y, d11);
+                    d22 = fmaf(Ee, K0.s[a][a][2], d22);
+                    d01 = fmaf(Ee, K0.p[a][a][1].x, d01);
+                    d02 = fmaf(Ee, K0.p[a][a][2].x, d02);
+                    d12 = fmaf(Ee, K0.p[a][a][2].y, d12);
+                }
+            }
+        }
+    }
+    if (MODE == ST_APPLY) {
+        out[3 * n + 0] = OT(a0);
+        out[3 * n + 1] = OT(a1);
+        out[3 * n + 2] = OT(a2);
+        return;
+    }
+    const float r0 = float(b[3 * n + 0]) - a0;
+    const float r1 = float(b[3 * n + 1]) - a1;
+    const float r2 = float(b[3 * n + 2]) - a2;
+    if (MODE == ST_RESID) {
+        out[3 * n + 0] = OT(r0);
+        out[3 * n + 1] = OT(r1);
+        out[3 * n + 2] = OT(r2);
+        return;
+    }
+    node_block_update<float, OT>(d00, d11, d22, d01, d02, d12, r0, r1, r2, x + 3 * n, out + 3 * n, omega);
+}
+
+template <int MODE, typename BT, typename OT>
+__global__ void __launch_bounds__(256, 3)
+node_stencil_f32x2_kernel(const float* __restrict__ x, const BT* __restrict__ b, OT* __restrict__ out,
+                          const float* __restrict__ E, GridDims d, const __grid_constant__ K0Pair K0, float omega,
+                          const int* __restrict__ halt)
+{
+    if (halt != nullptr && *halt != 0) return;
+    const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    stencil_node_f32x2<MODE, BT, OT>(n, x, b, out, E, d, K0, omega);
 }
 
 // First smoothing sweep from x = 0: out = omega * D_n^{-1} b, b_n = (r0, r1, r2).

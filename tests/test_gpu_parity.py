@@ -147,6 +147,32 @@ def test_vcycle_mixed_parity(gf):
     assert relerr(host(z), O.vcycle(H, v)) <= 1e-4
 
 
+# ----------------------------------------------- FP32 node stencil with paired FMAs --
+# The default FP32 node stencil advances the x and y output chains of each element with
+# one paired FMA; GF_F32X2=0 selects the scalar kernel. Every chain keeps the scalar
+# kernel's order and the node-block update is written out in explicit FMAs, so K*u, the
+# V-cycle and a whole mixed solve are bit-identical between the two.
+@pytest.mark.parametrize("nx,ny,nz,L", [(16, 8, 8, 3), (38, 6, 4, 2), (52, 24, 20, 3)])
+def test_paired_fma_stencil_bit_identical(gf, nx, ny, nz, L, monkeypatch):
+    outs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GF_F32X2", flag)
+        g, m, rho = make(gf, nx, ny, nz, L, seed=6, rho_min=1e-6)
+        u = synth.random_vector(m.n_dof, 8)
+        yf = torch.full((g.n_dof,), np.nan, dtype=torch.float32, device="cuda")
+        g.apply_K_f32(dev(u, torch.float32), yf)
+        z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        g.vcycle(dev(np.where(m.fixed, 0, u)), z, gf.GF_MIXED)
+        x = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        out = g.solve(dev(O.cantilever_load(m)), x, prec=gf.GF_MIXED, outer=2)
+        outs.append((yf, z, x, out["iters"]))
+    (a_y, a_z, a_x, a_it), (b_y, b_z, b_x, b_it) = outs
+    assert relerr(host(a_y), O.apply_K(m, O.young_modulus(bf16_round(rho), 1e-6, 3.0),
+                                       O.element_stiffness(), u.astype(np.float32).astype(np.float64))) <= 2e-5
+    assert torch.equal(a_y, b_y) and torch.equal(a_z, b_z)
+    assert a_it == b_it and torch.equal(a_x, b_x)
+
+
 # ------------------------------------------------- FP32 stencil on the tensor cores --
 # GF_STENCIL_TC=1 runs every FP32 level stencil as stencil_tc32_kernel (3xTF32 element
 # products); 0 keeps the CUDA-core kernel. Grids span several 16x8-element tiles in x
