@@ -860,7 +860,7 @@ int ensure_krylov(gf_grid* g, int m, int kmax, int outer)
                     g->nbd_k[p][q] = (int)std::max<long long>(1, std::min<long long>((long long)nb * g->sms, tiles));
                     g->nbd = std::max(g->nbd, g->nbd_k[p][q]);
                 }
-            RET(allocT(&g->pdd, (size_t)g->nbd * (gf::KRY_MMAX + 1)));
+            RET(allocT(&g->pdd, (size_t)g->nbd * (gf::KRY_NV + 1)));
             RET(allocT(&g->ddticket, 1));
             CK(cudaMemset(g->ddticket, 0, sizeof(unsigned int)));
         }
@@ -944,6 +944,42 @@ int cgs2_step(gf_grid* g, int j, double* w, int outer)
     return GF_OK;
 }
 
+// CGS2 for step j with j + 1 > KRY_NV basis vectors: the FP64 passes of cgs2_step
+// run over slices of KRY_NV vectors. Pass 1 dots every slice against w (and ||w||^2 for
+// the breakdown test into h1[KRY_MMAX + 1]); w -= V h1 slice by slice; the second dots
+// into h2; w -= V h2 slice by slice, the last slice also forming ||w||^2.
+int cgs2_step_long(gf_grid* g, int j, double* w)
+{
+    constexpr int NS = gf::KRY_NV;
+    const long long n = g->ndof, ld = g->ndof;
+    const int nv = j + 1, slices = (nv + NS - 1) / NS;
+    double* h1 = g->st->h1;   // device addresses of the state's slots
+    double* h2 = g->st->h2;
+    for (int pass = 0; pass < 2; ++pass) {
+        double* h = pass == 0 ? h1 : h2;
+        for (int c = 0; c < slices; ++c) {
+            const int off = c * NS, cnt = std::min(NS, nv - off);
+            LAUNCH(g, g->nbr, gf::RED_THREADS, gf::cgs_dots_kernel<NS>, (const double*)(g->V + off * ld), ld, cnt,
+                   (const double*)w, n, g->partial, (const gf::KState*)g->st);
+            LAUNCH(g, 1, 32 * 32, gf::reduce_slice_kernel, (const double*)g->partial, g->nbr, NS + 1, 0, cnt, h + off,
+                   (const gf::KState*)g->st);
+            if (pass == 0 && c == 0)
+                LAUNCH(g, 1, 32, gf::reduce_slice_kernel, (const double*)g->partial, g->nbr, NS + 1, NS, 1,
+                       h1 + gf::KRY_MMAX + 1, (const gf::KState*)g->st);
+        }
+        for (int c = 0; c < slices; ++c) {
+            const int off = c * NS, cnt = std::min(NS, nv - off);
+            double* part = (pass == 1 && c == slices - 1) ? g->partial : nullptr;
+            LAUNCH(g, g->nbr, gf::RED_THREADS, gf::cgs_slice_update_kernel<NS>, (const double*)(g->V + off * ld), ld,
+                   cnt, w, n, (const double*)(h + off), part, (const gf::KState*)g->st);
+        }
+    }
+    LAUNCH(g, 1, 32, gf::reduce_slice_kernel, (const double*)g->partial, g->nbr, 1, 0, 1, &g->st->ww,
+           (const gf::KState*)g->st);
+    LAUNCH(g, 1, 32, gf::arnoldi_tail_kernel, g->st, g->hist, j, gf::KRY_MMAX + 1, g->host_status_dev, 1e-14);
+    return GF_OK;
+}
+
 int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
 {
     const long long ld = g->ndof;
@@ -955,7 +991,8 @@ int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
                         o->fine_steps));
     if (o->outer == 2) RET(applyKsplit_dd(g, zj, g->Vd + (long long)(j + 1) * ld, halt));
     else RET(applyOuter(g, zj, w, halt, o->outer));
-    switch (pick_nv(j + 1)) {
+    if (j + 1 > gf::KRY_NV) RET(cgs2_step_long(g, j, w));   // outer 0 or 1 (validated)
+    else switch (pick_nv(j + 1)) {
         case 8: RET(cgs2_step<8>(g, j, w, o->outer)); break;
         case 16: RET(cgs2_step<16>(g, j, w, o->outer)); break;
         default: RET(cgs2_step<32>(g, j, w, o->outer)); break;
@@ -1141,7 +1178,7 @@ int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, g
 int validate_opts(const gf_solve_opts* o)
 {
     if (!o) return set_err(GF_ERR_ARG, "null opts");
-    if (o->restart < 1 || o->restart > gf::KRY_MMAX) return set_err(GF_ERR_ARG, "restart must be in [1, 32]");
+    if (o->restart < 1 || o->restart > gf::KRY_MMAX) return set_err(GF_ERR_ARG, "restart must be in [1, 300]");
     if (o->kmax < 0) return set_err(GF_ERR_ARG, "kmax < 0");
     if (!(o->tol >= 0.0)) return set_err(GF_ERR_ARG, "tol must be >= 0");
     if (o->prec != GF_FP64 && o->prec != GF_MIXED) return set_err(GF_ERR_ARG, "prec");
@@ -1149,6 +1186,8 @@ int validate_opts(const gf_solve_opts* o)
     if (!(o->omega > 0.0 && o->omega < 2.0)) return set_err(GF_ERR_ARG, "omega in (0,2)");
     if (o->outer < 0 || o->outer > 2)
         return set_err(GF_ERR_ARG, "outer must be 0 (FP64), 1 (split K*u) or 2 (split K*u, double-float CGS2)");
+    if (o->outer == 2 && o->restart > gf::KRY_NV)
+        return set_err(GF_ERR_ARG, "outer 2 (double-float CGS2) needs restart <= 32");
     if (o->smoother != 0 && o->smoother != 1) return set_err(GF_ERR_ARG, "smoother must be 0 (Jacobi) or 1 (Chebyshev)");
     if (!(o->ls_ratio >= 0.0 && std::isfinite(o->ls_ratio))) return set_err(GF_ERR_ARG, "ls_ratio must be finite and >= 0");
     if (o->ls_ratio > 0.0 && o->smoother != 0) return set_err(GF_ERR_ARG, "ls_ratio > 0 needs smoother 0");

@@ -12,7 +12,8 @@
 
 namespace gf {
 
-constexpr int KRY_MMAX = 32;
+constexpr int KRY_NV = 32;      // basis vectors per fused Gram-Schmidt pass (one register accumulator each)
+constexpr int KRY_MMAX = 300;   // restart cap; past KRY_NV vectors the passes run over slices of KRY_NV
 constexpr int RED_THREADS = 256;
 
 enum { KS_RUN = 0, KS_STOP = 1 };
@@ -136,6 +137,53 @@ cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, doubl
         acc[0] = fma(wn, wn, acc[0]);
     }
     block_reduce_store<1>(acc, 1, partial + blockIdx.x);
+}
+
+// ---- long restarts: the basis in slices of KRY_NV vectors -------------------------
+// Past KRY_NV basis vectors, each dot pass runs cgs_dots_kernel<KRY_NV> once per slice
+// of V against the same w (classical Gram-Schmidt: every dot of a pass sees the same w),
+// and the update w -= V h runs slice after slice with this kernel; hsl points at the
+// slice's coefficients in the state. With partial != nullptr (the last slice of the
+// second update) it also leaves the block parts of ||w_new||^2 in partial[b].
+template <int NV>
+__global__ void __launch_bounds__(RED_THREADS)
+cgs_slice_update_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
+                        long long n, const double* hsl, double* __restrict__ partial, const KState* st)
+{
+    if (st->status != KS_RUN) return;
+    __shared__ double h[NV];
+    if (threadIdx.x < NV) h[threadIdx.x] = threadIdx.x < nv ? hsl[threadIdx.x] : 0.0;
+    __syncthreads();
+    double acc[1] = {0.0};
+    long long r0, r1;
+    block_rows(n, r0, r1);
+    for (long long r = r0 + threadIdx.x; r < r1; r += RED_THREADS) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < NV; ++q)
+            if (q < nv) s = fma(h[q], V[q * ld + r], s);
+        const double wn = w[r] - s;
+        w[r] = wn;
+        acc[0] = fma(wn, wn, acc[0]);
+    }
+    if (partial != nullptr) block_reduce_store<1>(acc, 1, partial + blockIdx.x);
+}
+
+// dst[i] = sum_b partial[b * stride + src0 + i], i < cnt, in reduce_partials_kernel's
+// order; dst is a slot range of the state (a slice of h1 or h2, ||w||^2).
+__global__ void reduce_slice_kernel(const double* __restrict__ partial, int nblocks, int stride, int src0, int cnt,
+                                    double* dst, const KState* st)
+{
+    if (st->status != KS_RUN) return;
+    const int lane = threadIdx.x & 31;
+    for (int q = threadIdx.x >> 5; q < cnt; q += blockDim.x >> 5) {
+        double s = 0.0;
+#pragma unroll 8
+        for (int b = lane; b < nblocks; b += 32) s += partial[(long long)b * stride + src0 + q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) dst[q] = s;
+    }
 }
 
 // Sum partial[b][i] over blocks b (fixed order: deterministic). One warp per i.
@@ -281,7 +329,7 @@ update_x_kernel(double* __restrict__ x, const double* __restrict__ Z, long long 
     __shared__ double ys[KRY_MMAX];
     if (st->skip) return;
     const int J = st->J;
-    if (threadIdx.x < J) ys[threadIdx.x] = st->y[threadIdx.x];
+    for (int i = threadIdx.x; i < J; i += blockDim.x) ys[i] = st->y[i];
     __syncthreads();
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
          r += (long long)gridDim.x * blockDim.x) {

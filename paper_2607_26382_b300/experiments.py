@@ -6,6 +6,7 @@
     python -m paper_2607_26382_b300.experiments true_checks
     python -m paper_2607_26382_b300.experiments conditioning
     python -m paper_2607_26382_b300.experiments adaptive
+    python -m paper_2607_26382_b300.experiments false_accept
 
 batch102: 102 frozen states of uneven size (nx in {32,48,64,80}, ny = nz = nx/2,
   round-robin; 71 smoothed-Gaussian states with 40% of voxels at floor, 31
@@ -44,6 +45,15 @@ adaptive: the paper's adaptive preconditioner components (Table solver-config) a
   correction (ls_ratio 0.1) and the fine-level correction (fine_steps 20) on the four
   96x48x48 bench states (outer 2) and on the 102 batch102 states one at a time
   (outer 0) at rho0 1e-6 and 1e-12: FGMRES iterations, floors, accepted states, time.
+false_accept: the projected-versus-true stopping mismatch of Sec. 4.1.1 on regenerated
+  Bernoulli states: the 80x40x20 cantilever (3 levels), seeds 41..71 with the void
+  fraction q cycling over {0.08 .. 0.35}, p = 4.5, rho0 = 1e-12, tau = 1e-6,
+  k_max = restart = 300 (one Arnoldi cycle). Per solver form: the rho0 solve's flag,
+  steps, final projected estimate and FP64 recomputed residual (a false acceptance is a
+  converged flag with eta > tau), then Algorithm 1 with Eq. (trigger) and the ladder
+  {1e-3, 1e-2}. Forms: FP64 with the fixed V-cycle (the paper's fixed-preconditioner
+  control), FP64 with the adaptive preconditioner (line search 0.1, fine correction 20),
+  and the mixed V-cycle with the split-integer Krylov operator and FP64 CGS2 (outer 1).
 """
 from __future__ import annotations
 
@@ -394,14 +404,72 @@ def adaptive(args):
     return out
 
 
+def false_accept(args):
+    import torch
+    import synth
+    nx, ny, nz, levels, p, tau, kmax = 80, 40, 20, 3, 4.5, 1e-6, 300
+    rho0, ladder = 1e-12, [1e-3, 1e-2]
+    qs = [0.08, 0.11, 0.14, 0.17, 0.20, 0.23, 0.26, 0.30, 0.35]
+    states = [(seed, qs[i % len(qs)]) for i, seed in enumerate(range(41, 72))]
+    forms = (("FP64, fixed V-cycle", dict(prec=L.GF_FP64, outer=0)),
+             ("FP64, adaptive (line search 0.1, fine correction 20)",
+              dict(prec=L.GF_FP64, outer=0, ls_ratio=0.1, fine_steps=20)),
+             ("mixed V-cycle, split-integer K*u, FP64 CGS2", dict(prec=L.GF_MIXED, outer=1)))
+    g = L.create_grid(nx, ny, nz, levels=levels)
+    f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.cantilever_load(f)
+    out = {"grid": f"{nx}x{ny}x{nz}, {g.n_dof} DOF, {levels} levels", "states": len(states)}
+    for name, kw in forms:
+        rows, t_solve, t_sel, steps_sel, floors, accepted = [], 0.0, 0.0, 0, [], 0
+        for seed, q in states:
+            g.set_density(torch.as_tensor(synth.bernoulli_density(nx, ny, nz, seed, q), device="cuda"), p)
+            g.set_floor(rho0)
+            u = torch.zeros_like(f)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            o = g.solve(f, u, restart=kmax, kmax=kmax, tol=tau, **kw)
+            eta = g.true_residual(f, u)
+            t_solve += time.perf_counter() - t0
+            rows.append((o["flag"], o["iters"], o["history"][o["iters"]], eta))
+            pol = L.policy_defaults(rho0=rho0, ladder=ladder, tau=tau, kmax=kmax, probe_iters=100,
+                                    selector=L.GF_SEL_RULE, solve_restart=kmax, solve_prec=kw["prec"],
+                                    solve_outer=kw["outer"], solve_ls_ratio=kw.get("ls_ratio", 0.0),
+                                    solve_fine_steps=kw.get("fine_steps", 0))
+            u.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = g.select_floor(f, u, pol)
+            t_sel += time.perf_counter() - t0
+            steps_sel += r["probe_iters_run"] + sum(a["iters"] for a in r["attempts"])
+            floors.append(r["floor_index"])
+            accepted += int(r["status"] == L.GF_ACCEPTED)
+        conv = [(it, est, eta) for fl, it, est, eta in rows if fl == L.GF_FLAG_CONVERGED]
+        out[name] = {
+            "rho0 solves": {
+                "converged_flag": len(conv),
+                "false_acceptances": sum(eta > tau for _, _, eta in conv),
+                "visible_failures": sum(fl != L.GF_FLAG_CONVERGED for fl, _, _, _ in rows),
+                "max_eta_over_estimate": max((eta / est for _, est, eta in conv if est > 0), default=None),
+                "steps_mean": float(np.mean([it for _, it, _, _ in rows])),
+                "steps_max": max(it for _, it, _, _ in rows),
+                "seconds": t_solve},
+            "algorithm 1 (Eq. trigger)": {
+                "accepted": accepted, "floor_index_counts": [floors.count(i) for i in range(len(ladder) + 1)],
+                "arnoldi_steps": steps_sel, "seconds": t_sel}}
+        print(name, json.dumps(out[name]), flush=True)
+    g.close()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch102", "oc_loop", "oc_reuse", "true_checks", "conditioning", "adaptive"])
+    ap.add_argument("what", choices=["batch102", "oc_loop", "oc_reuse", "true_checks", "conditioning", "adaptive",
+                                     "false_accept"])
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--iters", type=int, default=40)
     a = ap.parse_args(argv)
     res = {"batch102": batch102, "oc_loop": oc_loop, "oc_reuse": oc_reuse, "true_checks": true_checks,
-           "conditioning": conditioning, "adaptive": adaptive}[a.what](a)
+           "conditioning": conditioning, "adaptive": adaptive, "false_accept": false_accept}[a.what](a)
     print(json.dumps(res), flush=True)
     return 0
 
