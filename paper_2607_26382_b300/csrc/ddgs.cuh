@@ -92,8 +92,9 @@ __device__ __forceinline__ void dd_warp_sum(float& h, float& l)
 // blocks and then a fixed shuffle tree, writes dst[0..cnt) in FP64 and re-arms the
 // ticket. No block waits on another, and the order of the sum does not depend on
 // the order of arrival (deterministic).
+// With xdst != nullptr, column xcol is summed the same way into *xdst as well.
 __device__ __forceinline__ void dd_finish(const float2* pdd, int stride, int cnt, double* dst,
-                                          unsigned int* ticket)
+                                          unsigned int* ticket, int xcol = 0, double* xdst = nullptr)
 {
     __shared__ bool last;
     __threadfence();
@@ -104,15 +105,17 @@ __device__ __forceinline__ void dd_finish(const float2* pdd, int stride, int cnt
     __threadfence();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nb = gridDim.x;
-    for (int q = warp; q < cnt; q += DD_WARPS) {
+    const int total = cnt + (xdst != nullptr ? 1 : 0);
+    for (int q = warp; q < total; q += DD_WARPS) {
+        const int col = q < cnt ? q : xcol;
         float h = 0.f, l = 0.f;
 #pragma unroll 4
         for (int b = lane; b < nb; b += 32) {
-            const float2 v = __ldcg(pdd + (long long)b * stride + q);
+            const float2 v = __ldcg(pdd + (long long)b * stride + col);
             dd_add(h, l, v.x, v.y);
         }
         dd_warp_sum(h, l);
-        if (lane == 0) dst[q] = dd_to_double(h, l);
+        if (lane == 0) *(q < cnt ? dst + q : xdst) = dd_to_double(h, l);
     }
     if (threadIdx.x == 0) *ticket = 0u;
 }
@@ -120,11 +123,9 @@ __device__ __forceinline__ void dd_finish(const float2* pdd, int stride, int cnt
 // pass 1: partial[b][q] = sum_r Vd_q[r] wd[r] (q < NV, zero for q >= nv),
 //         partial[b][NV] = ||wd||^2; the sums land in st->h1
 template <int NV>
-__global__ void __launch_bounds__(DD_THREADS)
-ddgs_dots_kernel(const float2* __restrict__ Vd, long long ld, int nv, const float2* __restrict__ wd,
-                 long long n, float2* __restrict__ partial, KState* __restrict__ st, unsigned int* ticket)
+__device__ __forceinline__ void dd_dots_row(const float2* __restrict__ Vd, long long ld, int nv,
+                                            const float2* __restrict__ wd, long long n, float2* __restrict__ partial)
 {
-    if (st->status != KS_RUN) return;
     constexpr int QW = NV / DD_WARPS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float ah[QW + 1], al[QW + 1];
@@ -168,6 +169,15 @@ ddgs_dots_kernel(const float2* __restrict__ Vd, long long ld, int nv, const floa
         dd_warp_sum(ah[QW], al[QW]);
         if (lane == 0) row[NV] = make_float2(ah[QW], al[QW]);
     }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(DD_THREADS)
+ddgs_dots_kernel(const float2* __restrict__ Vd, long long ld, int nv, const float2* __restrict__ wd,
+                 long long n, float2* __restrict__ partial, KState* __restrict__ st, unsigned int* ticket)
+{
+    if (st->status != KS_RUN) return;
+    dd_dots_row<NV>(Vd, ld, nv, wd, n, partial);
     dd_finish(partial, NV + 1, NV + 1, st->h1, ticket);   // h1[0..NV), ||w||^2 in h1[NV]
 }
 
@@ -267,19 +277,18 @@ ddgs_update_dots_kernel(const float2* __restrict__ Vd, long long ld, int nv, flo
 }
 
 // pass 3: wd -= sum_q h2_q Vd_q ; partial[b][0] = ||wd_new||^2 (block part); sum in st->ww
+// wd -= sum_q h_q Vd_q over this block's rows; partial[b] = the block part of ||wd_new||^2
 template <int NV>
-__global__ void __launch_bounds__(DD_THREADS)
-ddgs_update_norm_kernel(const float2* __restrict__ Vd, long long ld, int nv, float2* __restrict__ wd,
-                        long long n, float2* __restrict__ partial, KState* __restrict__ st,
-                        unsigned int* ticket)
+__device__ __forceinline__ void dd_update_norm_row(const float2* __restrict__ Vd, long long ld, int nv,
+                                                   float2* __restrict__ wd, long long n,
+                                                   float2* __restrict__ partial, const double* h)
 {
-    if (st->status != KS_RUN) return;
     constexpr int QW = NV / DD_WARPS;
     __shared__ float2 hs[NV];
     __shared__ float2 part[DD_WARPS][DD_TILE];
     __shared__ float2 wn_s[DD_TILE];
     __shared__ float2 red[DD_WARPS];
-    dd_load_h<NV>(st->h2, nv, hs);
+    dd_load_h<NV>(h, nv, hs);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float nh = 0.f, nl = 0.f;
     long long r0, r1;
@@ -301,7 +310,43 @@ ddgs_update_norm_kernel(const float2* __restrict__ Vd, long long ld, int nv, flo
         for (int w = 0; w < DD_WARPS; ++w) dd_add(h, l, red[w].x, red[w].y);
         partial[blockIdx.x] = make_float2(h, l);
     }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(DD_THREADS)
+ddgs_update_norm_kernel(const float2* __restrict__ Vd, long long ld, int nv, float2* __restrict__ wd,
+                        long long n, float2* __restrict__ partial, KState* __restrict__ st,
+                        unsigned int* ticket)
+{
+    if (st->status != KS_RUN) return;
+    dd_update_norm_row<NV>(Vd, ld, nv, wd, n, partial, st->h2);
     dd_finish(partial, 1, 1, &st->ww, ticket);
+}
+
+// ---- long restarts: the basis in slices of NV vectors ------------------------------
+// The double-float counterparts of the FP64 slice passes: dots of one slice against
+// wd into dst[0..nv) (and ||wd||^2 into *wwdst when given), and wd -= Vd_slice h_slice
+// (with ||wd_new||^2 into *wwdst when given: the last slice of the second update).
+template <int NV>
+__global__ void __launch_bounds__(DD_THREADS)
+ddgs_slice_dots_kernel(const float2* __restrict__ Vd, long long ld, int nv, const float2* __restrict__ wd,
+                       long long n, float2* __restrict__ partial, const KState* st, unsigned int* ticket,
+                       double* dst, double* wwdst)
+{
+    if (st->status != KS_RUN) return;
+    dd_dots_row<NV>(Vd, ld, nv, wd, n, partial);
+    dd_finish(partial, NV + 1, nv, dst, ticket, NV, wwdst);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(DD_THREADS)
+ddgs_slice_update_kernel(const float2* __restrict__ Vd, long long ld, int nv, float2* __restrict__ wd,
+                         long long n, float2* __restrict__ partial, const KState* st, unsigned int* ticket,
+                         const double* h, double* wwdst)
+{
+    if (st->status != KS_RUN) return;
+    dd_update_norm_row<NV>(Vd, ld, nv, wd, n, partial, h);
+    if (wwdst != nullptr) dd_finish(partial, 1, 1, wwdst, ticket);
 }
 
 // v_{j+1} = wd * inv: the double-float basis vector in place, and its FP64 value

@@ -944,17 +944,41 @@ int cgs2_step(gf_grid* g, int j, double* w, int outer)
     return GF_OK;
 }
 
-// CGS2 for step j with j + 1 > KRY_NV basis vectors: the FP64 passes of cgs2_step
-// run over slices of KRY_NV vectors. Pass 1 dots every slice against w (and ||w||^2 for
-// the breakdown test into h1[KRY_MMAX + 1]); w -= V h1 slice by slice; the second dots
-// into h2; w -= V h2 slice by slice, the last slice also forming ||w||^2.
-int cgs2_step_long(gf_grid* g, int j, double* w)
+// CGS2 for step j with j + 1 > KRY_NV basis vectors: the passes of cgs2_step run over
+// slices of KRY_NV vectors. Pass 1 dots every slice against w (and ||w||^2 for the
+// breakdown test into h1[KRY_MMAX + 1]); w -= V h1 slice by slice; the second dots into
+// h2; w -= V h2 slice by slice, the last slice also forming ||w||^2. outer == 2 runs
+// the double-float passes on Vd and wd, otherwise FP64 on V and w.
+int cgs2_step_long(gf_grid* g, int j, double* w, int outer)
 {
     constexpr int NS = gf::KRY_NV;
     const long long n = g->ndof, ld = g->ndof;
     const int nv = j + 1, slices = (nv + NS - 1) / NS;
     double* h1 = g->st->h1;   // device addresses of the state's slots
     double* h2 = g->st->h2;
+    const gf::KState* cst = g->st;
+    if (outer == 2) {
+        float2* wd = g->Vd + (long long)(j + 1) * ld;
+        for (int pass = 0; pass < 2; ++pass) {
+            double* h = pass == 0 ? h1 : h2;
+            for (int c = 0; c < slices; ++c) {
+                const int off = c * NS, cnt = std::min(NS, nv - off);
+                double* wwdst = (pass == 0 && c == 0) ? h1 + gf::KRY_MMAX + 1 : nullptr;
+                LAUNCH(g, g->nbd_k[0][2], gf::DD_THREADS, gf::ddgs_slice_dots_kernel<NS>,
+                       (const float2*)(g->Vd + off * ld), ld, cnt, (const float2*)wd, n, g->pdd, cst, g->ddticket,
+                       h + off, wwdst);
+            }
+            for (int c = 0; c < slices; ++c) {
+                const int off = c * NS, cnt = std::min(NS, nv - off);
+                double* wwdst = (pass == 1 && c == slices - 1) ? &g->st->ww : nullptr;
+                LAUNCH(g, g->nbd_k[2][2], gf::DD_THREADS, gf::ddgs_slice_update_kernel<NS>,
+                       (const float2*)(g->Vd + off * ld), ld, cnt, wd, n, g->pdd, cst, g->ddticket,
+                       (const double*)(h + off), wwdst);
+            }
+        }
+        LAUNCH(g, 1, 32, gf::arnoldi_tail_kernel, g->st, g->hist, j, gf::KRY_MMAX + 1, g->host_status_dev, 1e-14);
+        return GF_OK;
+    }
     for (int pass = 0; pass < 2; ++pass) {
         double* h = pass == 0 ? h1 : h2;
         for (int c = 0; c < slices; ++c) {
@@ -991,7 +1015,7 @@ int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
                         o->fine_steps));
     if (o->outer == 2) RET(applyKsplit_dd(g, zj, g->Vd + (long long)(j + 1) * ld, halt));
     else RET(applyOuter(g, zj, w, halt, o->outer));
-    if (j + 1 > gf::KRY_NV) RET(cgs2_step_long(g, j, w));   // outer 0 or 1 (validated)
+    if (j + 1 > gf::KRY_NV) RET(cgs2_step_long(g, j, w, o->outer));
     else switch (pick_nv(j + 1)) {
         case 8: RET(cgs2_step<8>(g, j, w, o->outer)); break;
         case 16: RET(cgs2_step<16>(g, j, w, o->outer)); break;
@@ -1186,8 +1210,6 @@ int validate_opts(const gf_solve_opts* o)
     if (!(o->omega > 0.0 && o->omega < 2.0)) return set_err(GF_ERR_ARG, "omega in (0,2)");
     if (o->outer < 0 || o->outer > 2)
         return set_err(GF_ERR_ARG, "outer must be 0 (FP64), 1 (split K*u) or 2 (split K*u, double-float CGS2)");
-    if (o->outer == 2 && o->restart > gf::KRY_NV)
-        return set_err(GF_ERR_ARG, "outer 2 (double-float CGS2) needs restart <= 32");
     if (o->smoother != 0 && o->smoother != 1) return set_err(GF_ERR_ARG, "smoother must be 0 (Jacobi) or 1 (Chebyshev)");
     if (!(o->ls_ratio >= 0.0 && std::isfinite(o->ls_ratio))) return set_err(GF_ERR_ARG, "ls_ratio must be finite and >= 0");
     if (o->ls_ratio > 0.0 && o->smoother != 0) return set_err(GF_ERR_ARG, "ls_ratio > 0 needs smoother 0");

@@ -459,10 +459,11 @@ def test_solve_fp64_parity(gf, case, outer):
 
 
 # Restarts above 32 basis vectors: the Gram-Schmidt passes run over slices of 32
-# vectors (FP64, outer 0 or 1). The Bernoulli state needs 148 steps at restart 45
-# (cycles whose bases end in a ragged slice) and 99 / 122 at restart 300 (one cycle,
-# four slices), so the histories are matched well past the fused passes' 32 vectors.
-@pytest.mark.parametrize("outer", [0, 1])
+# vectors (FP64 for outer 0 and 1, double-float for outer 2). The Bernoulli state needs
+# 148 steps at restart 45 (cycles whose bases end in a ragged slice) and 99 / 122 at
+# restart 300 (one cycle, four slices), so the histories are matched well past the
+# fused passes' 32 vectors.
+@pytest.mark.parametrize("outer", [0, 1, 2])
 @pytest.mark.parametrize("case", [(16, 8, 8, 3, 45), (16, 8, 8, 3, 300), (24, 12, 8, 3, 300)])
 def test_solve_long_restart_parity(gf, case, outer):
     nx, ny, nz, L, restart = case
@@ -475,9 +476,10 @@ def test_solve_long_restart_parity(gf, case, outer):
     assert abs(out["iters"] - res.iters) <= 1 and out["flag"] == res.flag
     k = min(out["iters"], res.iters)
     h_gpu, h_ref = np.array(out["history"][:k + 1]), res.history[:k + 1]
-    # outer 1: the split-integer operator is exact to ~2^-48 relative, not FP64's 2^-53;
-    # over ~150 slowly converging steps on this kappa ~ 1e10 state the histories then part
-    # by up to ~1e-12 absolute (measured 1.6e-14 at step 1, 1e-12 near the stop)
+    # outer 1 and 2: the split-integer operator is exact to ~2^-48 relative (and the
+    # double-float passes to ~2^-47), not FP64's 2^-53; over ~150 slowly converging steps
+    # on this kappa ~ 1e10 state the histories then part by up to ~1e-12 absolute
+    # (measured for outer 1: 1.6e-14 at step 1, 1e-12 near the stop)
     atol = 1e-15 if outer == 0 else 2e-12
     assert np.all(np.abs(h_gpu - h_ref) <= 1e-6 * h_ref + atol)
     assert O.true_residual(m, E, K0, f, host(u)) <= 1.5e-6
@@ -486,10 +488,12 @@ def test_solve_long_restart_parity(gf, case, outer):
 def test_long_restart_limits(gf):
     g, m, _ = make(gf, 8, 4, 4, 2, seed=1)
     f, u = dev(O.cantilever_load(m)), torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
-    for kw in (dict(restart=301), dict(restart=33, outer=2), dict(restart=0)):
+    for kw in (dict(restart=301), dict(restart=301, outer=2), dict(restart=0)):
         with pytest.raises(gf.GFError):
             g.solve(f, u, **kw)
-    assert g.solve(f, u, restart=300, outer=1, kmax=40)["flag"] in (gf.GF_FLAG_CONVERGED, gf.GF_FLAG_MAX_ITERS)
+    for outer in (1, 2):
+        assert g.solve(f, u, restart=300, outer=outer, kmax=40)["flag"] in (gf.GF_FLAG_CONVERGED,
+                                                                          gf.GF_FLAG_MAX_ITERS)
 
 
 def test_solve_mixed_converges_and_guard(gf):
