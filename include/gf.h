@@ -218,6 +218,22 @@ int gf_set_density(gf_grid* g, const double* rho_hat, double p);
  * coarsest operator. 0 < rho_min <= 1. */
 int gf_set_floor(gf_grid* g, double rho_min);
 
+/* Coarse-level operators of the V-cycle, used from the next gf_set_floor on:
+ * GF_COARSE_REDISCRETISED (default): every coarse level applies K0(h_l) with the mean of
+ *   the 8 child moduli, matrix-free.
+ * GF_COARSE_GALERKIN: K_{l+1} = P^T K_l P with the 2:1 trilinear prolongation P (Table
+ *   solver-config), held as one dense 24x24 matrix per coarse element and summed from
+ *   the 8 children's matrices; node-block Jacobi smoothing on it and the dense inverse of
+ *   the assembled coarsest level. FP64 matrices from the FP64 moduli, and FP32 ones (the
+ *   mixed V-cycle) from the BF16-density moduli. Takes Jacobi smoothing without the line
+ *   search (other solve options return GF_ERR_ARG); the batch keeps the default.
+ * Switching clears the floor (gf_set_floor again before solving) and the captured steps.
+ * Memory: 576 * (8 + 4) bytes per coarse element, plus FP64 scratch for two levels.
+ * Errors: GF_ERR_ARG for an unknown kind. */
+#define GF_COARSE_REDISCRETISED 0
+#define GF_COARSE_GALERKIN      1
+int gf_set_coarse_operator(gf_grid* g, int kind);
+
 /* f = unit point load in -z at the node (nx, ny/2, nz/2) (n_dof doubles, device);
  * the cantilever of Table geometries. */
 int gf_cantilever_load(gf_grid* g, double* f);

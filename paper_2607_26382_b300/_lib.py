@@ -23,6 +23,7 @@ GF_SEL_RULE, GF_SEL_FULL, GF_SEL_GIVEN, GF_SEL_MLP, GF_SEL_REUSE = 0, 1, 2, 3, 4
 MLP_PARAMS = 1412
 GF_MAX_LADDER = 8
 GF_MAX_TRUE_CHECKS = 16
+GF_COARSE_REDISCRETISED, GF_COARSE_GALERKIN = 0, 1
 
 ERRORS = {-1: "GF_ERR_ARG", -2: "GF_ERR_OOM", -3: "GF_ERR_CUDA", -4: "GF_ERR_NONFINITE",
           -5: "GF_ERR_TIMEOUT", -6: "GF_ERR_STATE"}
@@ -37,6 +38,7 @@ EXPORTED = [
     "gf_batch_solution", "gf_batch_autotune", "gf_batch_select_floor", "gf_batch_stats",
     "gf_mlp_create", "gf_mlp_destroy", "gf_mlp_set_norm", "gf_mlp_get_params", "gf_mlp_forward",
     "gf_mlp_loss_grad", "gf_mlp_train", "gf_mlp_predict", "gf_select_features", "gf_apply_K_split",
+    "gf_set_coarse_operator",
 ]
 
 
@@ -101,6 +103,7 @@ def lib():
         "gf_grid_sizes": [P, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int)],
         "gf_set_density": [P, P, c_double],
         "gf_set_floor": [P, c_double],
+        "gf_set_coarse_operator": [P, c_int],
         "gf_cantilever_load": [P, P],
         "gf_free_mask": [P, P],
         "gf_apply_K": [P, P, P],
@@ -267,6 +270,11 @@ class Grid:
     def set_floor(self, rho_min):
         _check(lib().gf_set_floor(self._h, float(rho_min)))
         self.rho_min = float(rho_min)
+
+    def set_coarse_operator(self, kind):
+        """gf_set_coarse_operator: GF_COARSE_REDISCRETISED or GF_COARSE_GALERKIN, used from
+        the next set_floor on (switching clears the floor)."""
+        _check(lib().gf_set_coarse_operator(self._h, int(kind)))
 
     def cantilever_load(self, f):
         _check(lib().gf_cantilever_load(self._h, _ptr(f, _torch().float64, self.n_dof, "f")))

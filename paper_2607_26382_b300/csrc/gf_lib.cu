@@ -16,6 +16,7 @@
 #include "lanczos.cuh"
 #include "linesearch.cuh"
 #include "finecorr.cuh"
+#include "galerkin.cuh"
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -67,6 +68,8 @@ struct Level {
     float *b32 = nullptr, *x32 = nullptr, *t32 = nullptr, *r32 = nullptr;
     double* q64 = nullptr;            // line-searched coarse correction: K c (allocated on first use)
     float* q32 = nullptr;
+    double* Ke64 = nullptr;           // Galerkin levels (l >= 1): 24x24 element matrices, FP64 moduli
+    float* Ke32 = nullptr;            //   and from the BF16-density moduli, rounded to FP32
     gf::GridDims dims() const { return gf::GridDims{nx, ny, nz}; }
 };
 
@@ -129,6 +132,9 @@ struct gf_grid {
     gf::K0Param<float> K0f;
     gf::K0Pair K0p;                   // K0f with rows 3a, 3a+1 paired (node_stencil_f32x2_kernel)
     bool f32x2 = true;                // FP32 node stencil with paired FMAs (GF_F32X2=0: scalar FMAs)
+    int coarse_kind = GF_COARSE_REDISCRETISED;   // gf_set_coarse_operator; applied by gf_set_floor
+    double* galG = nullptr;           // G_c = T_c^T K0 T_c, 8 x 576 (Galerkin first coarse level)
+    double* gal_s[2] = {nullptr, nullptr};   // FP64 scratch for the BF16-moduli chain
     gf::S3BFrag* B3 = nullptr;        // B fragments of M (K0 = s M) for stencil_tc32_kernel, device
     int stc_cz[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // > 0: level l's FP32 stencils on the tensor cores, cz layers per CTA
     double* rho64 = nullptr;
@@ -601,6 +607,103 @@ int vcycle_dispatch_plain(gf_grid* g, const double* v, double* z, int prec, int 
 template <typename T>
 int fine_correct(gf_grid* g, const double* v, double* z, int steps, const int* halt);
 
+template <typename T>
+const T* gal_ke(const Level& L);
+template <>
+const double* gal_ke<double>(const Level& L) { return L.Ke64; }
+template <>
+const float* gal_ke<float>(const Level& L) { return L.Ke32; }
+
+// Galerkin level operator (csrc/galerkin.cuh) on level l >= 1
+template <typename T, int MODE>
+int gal_level(gf_grid* g, int l, const T* x, const T* b, T* out, T omega, const int* halt)
+{
+    const Level& L = g->lv[l];
+    LAUNCH(g, nblk(L.nodes), 256, (gf::gal_node_kernel<T, MODE, T, T>), x, b, out, gal_ke<T>(L), L.dims(), omega,
+           halt);
+    return GF_OK;
+}
+
+// The V-cycle on the Galerkin hierarchy: vcycle_impl's schedule, with every level
+// l >= 1 smoothed, and its residual formed, by the assembled coarse operator
+// (first sweep from x = 0, then nu1 - 1 sweeps, residual, restriction; prolongation,
+// nu2 sweeps). Level 0 keeps the matrix-free stencils; the coarsest solve uses the
+// dense inverse of the assembled Galerkin matrix.
+template <typename T>
+int vcycle_galerkin(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omega, const int* halt)
+{
+    using B = LvBuf<T>;
+    const int L = g->L;
+    const int NX0 = g->nx + 1;
+    g->stats.vcycles++;
+    std::vector<T*> cur(L);
+    const T* b0;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        b0 = reinterpret_cast<const T*>(v);
+    } else {
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, T>), v, B::b(g->lv[0]), g->ndof, NX0, halt);
+        b0 = B::b(g->lv[0]);
+    }
+    for (int l = 0; l < L - 1; ++l) {
+        Level& lev = g->lv[l];
+        const T* b = (l == 0) ? b0 : B::b(lev);
+        T* x = B::x(lev);
+        T* t = B::t(lev);
+        if (l == 0) {
+            const int tpb = g->tpb[sizeof(T) == sizeof(double) ? 0 : 1] > 0 ? g->tpb[sizeof(T) == sizeof(double) ? 0 : 1]
+                                                                              : 256;
+            LAUNCH(g, nblk(lev.nodes, tpb), tpb, (gf::first_sweep_kernel<T, T, T>), b, x, B::E(lev), lev.dims(),
+                   k0<T>(g), omega, halt);
+            for (int s = 1; s < nu1; ++s) {
+                RET((stencil<T, T, gf::ST_SWEEP>(g, 0, x, b, t, B::E(lev), k0<T>(g), omega, halt)));
+                std::swap(x, t);
+            }
+            RET((stencil<T, T, gf::ST_RESID>(g, 0, x, b, B::r(lev), B::E(lev), k0<T>(g), omega, halt)));
+        } else {
+            RET((gal_level<T, gf::GAL_FIRST>(g, l, (const T*)nullptr, b, x, omega, halt)));
+            for (int s = 1; s < nu1; ++s) {
+                RET((gal_level<T, gf::ST_SWEEP>(g, l, x, b, t, omega, halt)));
+                std::swap(x, t);
+            }
+            RET((gal_level<T, gf::ST_RESID>(g, l, x, b, B::r(lev), omega, halt)));
+        }
+        cur[l] = x;
+        Level& c = g->lv[l + 1];
+        LAUNCH(g, nblk(c.nodes), 256, gf::restrict_kernel<T>, (const T*)B::r(lev), B::b(c), c.dims(), halt);
+    }
+    {
+        Level& c = g->lv[L - 1];
+        LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<T, T>), (const double*)g->Ainv, (const T*)B::b(c),
+               B::x(c), g->nc, halt);
+        cur[L - 1] = B::x(c);
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        Level& lev = g->lv[l];
+        const T* b = (l == 0) ? b0 : B::b(lev);
+        T* x = cur[l];
+        T* t = (x == B::x(lev)) ? B::t(lev) : B::x(lev);
+        RET(coarse_correct<T>(g, l, x, cur[l + 1], t, B::r(lev), 0.0, halt));
+        for (int s = 0; s < nu2; ++s) {
+            T* out = t;
+            const bool last = (l == 0 && s == nu2 - 1);
+            if constexpr (sizeof(T) == sizeof(double)) {
+                if (last) out = reinterpret_cast<T*>(z);
+            }
+            if (l == 0) RET((stencil<T, T, gf::ST_SWEEP>(g, 0, x, b, out, B::E(lev), k0<T>(g), omega, halt)));
+            else RET((gal_level<T, gf::ST_SWEEP>(g, l, x, b, out, omega, halt)));
+            if (last && sizeof(T) == sizeof(double)) {
+                x = out;
+                break;
+            }
+            std::swap(x, t);
+        }
+        cur[l] = x;
+    }
+    if constexpr (sizeof(T) != sizeof(double))
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<T, double>), (const T*)cur[0], z, g->ndof, NX0, halt);
+    return GF_OK;
+}
+
 // The preconditioner: one V-cycle, then (fine > 0) the fine-level adaptive correction.
 int vcycle_dispatch(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2, double omega,
                     const int* halt, int smoother = 0, double ls = 0.0, int fine = 0)
@@ -619,6 +722,12 @@ int vcycle_dispatch_plain(gf_grid* g, const double* v, double* z, int prec, int 
     if (ls > 0.0 && (smoother == 1 || g->vc_l0 > 0 || g->L < 2 || !g->ls_alpha))
         return set_err(GF_ERR_ARG, "the line-searched coarse correction needs Jacobi smoothing, >= 2 levels and no "
                                    "cluster V-cycle");
+    if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1) {
+        if (smoother != 0 || ls > 0.0)
+            return set_err(GF_ERR_ARG, "Galerkin coarse operators take Jacobi smoothing without the line search");
+        if (prec == GF_MIXED) return vcycle_galerkin<float>(g, v, z, nu1, nu2, (float)omega, halt);
+        return vcycle_galerkin<double>(g, v, z, nu1, nu2, omega, halt);
+    }
     if (smoother == 1) {
         if (!g->cheb_ready[prec == GF_FP64 ? 0 : 1]) return set_err(GF_ERR_STATE, "Chebyshev bounds not set up");
         if (prec == GF_MIXED) return vcycle_cheb<float>(g, v, z, nu1, nu2, halt);
@@ -803,6 +912,53 @@ int allocT(T** p, size_t n)
     return alloc(reinterpret_cast<void**>(p), n * sizeof(T));
 }
 
+// Galerkin element matrices of levels 1 .. L-1 (csrc/galerkin.cuh): Ke64 from the FP64
+// moduli; Ke32 from the BF16-density moduli, that chain carried in FP64 scratch and
+// rounded to FP32 per level (the mixed V-cycle's coarse operators).
+int build_galerkin(gf_grid* g)
+{
+    const int L = g->L;
+    if (L < 2) return GF_OK;
+    if (!g->galG) {
+        std::vector<double> G(8 * gf::GAL_KE);
+        for (int c = 0; c < 8; ++c)
+            for (int R = 0; R < 24; ++R)
+                for (int S = 0; S < 24; ++S) {
+                    const int b = R / 3, i = R % 3, bp = S / 3, j = S % 3;
+                    double acc = 0.0;
+                    for (int a = 0; a < 8; ++a)
+                        for (int ap = 0; ap < 8; ++ap)
+                            acc += gf::gal_weight(c, a, b) * g->K0d.k[(3 * a + i) * 24 + 3 * ap + j] *
+                                   gf::gal_weight(c, ap, bp);
+                    G[(c * 24 + R) * 24 + S] = acc;
+                }
+        RET(allocT(&g->galG, G.size()));
+        CK(cudaMemcpy(g->galG, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice));
+        for (int l = 1; l < L; ++l) {
+            Level& c = g->lv[l];
+            RET(allocT(&c.Ke64, (size_t)c.nel * gf::GAL_KE));
+            RET(allocT(&c.Ke32, (size_t)c.nel * gf::GAL_KE));
+        }
+        RET(allocT(&g->gal_s[0], (size_t)g->lv[1].nel * gf::GAL_KE));
+        if (L > 2) RET(allocT(&g->gal_s[1], (size_t)g->lv[2].nel * gf::GAL_KE));
+    }
+    Level& c1 = g->lv[1];
+    const long long n1 = c1.nel * gf::GAL_KE;
+    LAUNCH(g, nblk(n1), 256, gf::gal_first_level_kernel<double>, (const double*)g->lv[0].E64,
+           (const double*)g->galG, c1.Ke64, (float*)nullptr, c1.dims());
+    LAUNCH(g, nblk(n1), 256, gf::gal_first_level_kernel<float>, (const float*)g->lv[0].E32, (const double*)g->galG,
+           g->gal_s[0], c1.Ke32, c1.dims());
+    for (int l = 2; l < L; ++l) {
+        Level& c = g->lv[l];
+        const long long nl = c.nel * gf::GAL_KE;
+        LAUNCH(g, nblk(nl), 256, gf::gal_coarsen_kernel, (const double*)g->lv[l - 1].Ke64, c.Ke64, (float*)nullptr,
+               c.dims());
+        LAUNCH(g, nblk(nl), 256, gf::gal_coarsen_kernel, (const double*)g->gal_s[(l - 2) & 1], g->gal_s[(l - 1) & 1],
+               c.Ke32, c.dims());
+    }
+    return GF_OK;
+}
+
 int build_coarse_inverse(gf_grid* g)
 {
     Level& c = g->lv[g->L - 1];
@@ -811,7 +967,10 @@ int build_coarse_inverse(gf_grid* g)
     // ceil(n/2) double-buffered steps; start in the buffer that makes the last one land in Ainv
     const long long steps = (n + 1) / 2;
     double* src = (steps & 1) ? g->Agj : g->Ainv;
-    LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, c.E64, src, c.dims(), K);
+    if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1)
+        LAUNCH(g, nblk(n * n), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, src, c.dims());
+    else
+        LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, c.E64, src, c.dims(), K);
     LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, src, c.dims());
     const unsigned tiles = (unsigned)((n + gf::GJ_T - 1) / gf::GJ_T);
     for (int k = 0; k < n; k += 2) {
@@ -1217,6 +1376,15 @@ int validate_opts(const gf_solve_opts* o)
     return GF_OK;
 }
 
+// validate_opts, plus what the grid's coarse operators allow
+int validate_grid_opts(const gf_grid* g, const gf_solve_opts* o)
+{
+    RET(validate_opts(o));
+    if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1 && (o->smoother != 0 || o->ls_ratio > 0.0))
+        return set_err(GF_ERR_ARG, "Galerkin coarse operators take Jacobi smoothing without the line search");
+    return GF_OK;
+}
+
 int guard_impl(gf_grid* g, const double* f, const double* u, double* eta)
 {
     RET(applyK64(g, u, g->work, nullptr));
@@ -1551,7 +1719,9 @@ int gf_destroy_grid(gf_grid* g)
         cudaFree(L.b64); cudaFree(L.x64); cudaFree(L.t64); cudaFree(L.r64);
         cudaFree(L.b32); cudaFree(L.x32); cudaFree(L.t32); cudaFree(L.r32);
         cudaFree(L.q64); cudaFree(L.q32);
+        cudaFree(L.Ke64); cudaFree(L.Ke32);
     }
+    cudaFree(g->galG); cudaFree(g->gal_s[0]); cudaFree(g->gal_s[1]);
     cudaFree(g->ls_partial); cudaFree(g->ls_alpha);
     cudaFree(g->fcV); cudaFree(g->fcZ); cudaFree(g->fcR); cudaFree(g->fcD); cudaFree(g->fcQ); cudaFree(g->fcZT);
     cudaFree(g->fc); cudaFree(g->fc_partial);
@@ -1638,10 +1808,24 @@ int gf_set_floor(gf_grid* g, double rho_min)
         LAUNCH(g, nblk(c.nel), 256, gf::coarsen_kernel<double>, g->lv[l - 1].E64, c.E64, c.dims());
         LAUNCH(g, nblk(c.nel), 256, gf::coarsen_kernel<float>, g->lv[l - 1].E32, c.E32, c.dims());
     }
+    if (g->coarse_kind == GF_COARSE_GALERKIN) RET(build_galerkin(g));
     if (!g->skip_coarse_inverse) RET(build_coarse_inverse(g));
     g->rho_min = rho_min;
     g->has_floor = true;
     g->cheb_ready[0] = g->cheb_ready[1] = false;
+    return GF_OK;
+}
+
+int gf_set_coarse_operator(gf_grid* g, int kind)
+{
+    RET(check_grid(g));
+    if (kind != GF_COARSE_REDISCRETISED && kind != GF_COARSE_GALERKIN)
+        return set_err(GF_ERR_ARG, "kind must be GF_COARSE_REDISCRETISED or GF_COARSE_GALERKIN");
+    if (kind == g->coarse_kind) return GF_OK;
+    RET(set_device(g));
+    drop_graphs(g);            // captured Arnoldi steps hold the other V-cycle
+    g->coarse_kind = kind;
+    g->has_floor = false;      // the next gf_set_floor builds the hierarchy
     return GF_OK;
 }
 
@@ -1705,7 +1889,7 @@ int gf_vcycle(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2
 int gf_vcycle_ex(gf_grid* g, const double* v, double* z, const gf_solve_opts* o)
 {
     RET(check_grid(g));
-    RET(validate_opts(o));
+    RET(validate_grid_opts(g, o));
     if (!v || !z || v == z) return set_err(GF_ERR_ARG, "v, z non-null and distinct");
     if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
     RET(set_device(g));
@@ -1734,7 +1918,7 @@ int gf_chebyshev_lambda(gf_grid* g, int prec, double* lam, int n)
 int gf_solve(gf_grid* g, const double* f, double* u, const gf_solve_opts* opts, gf_solve_info* info)
 {
     RET(check_grid(g));
-    RET(validate_opts(opts));
+    RET(validate_grid_opts(g, opts));
     if (!f || !u || f == u) return set_err(GF_ERR_ARG, "f, u non-null and distinct");
     if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
     RET(set_device(g));
@@ -1872,7 +2056,7 @@ int select_floor_reuse(gf_grid* g, const double* f, double* u, const gf_policy* 
     o.history = nullptr;
     o.tol = pol->tau;
     o.kmax = pol->kmax;
-    RET(validate_opts(&o));
+    RET(validate_grid_opts(g, &o));
     RET(set_device(g));
     const double rm = pol->first_index == 0 ? pol->rho0 : pol->ladder[pol->first_index - 1];
     if (!(g->has_floor && g->rho_min == rm)) RET(gf_set_floor(g, rm));
@@ -1926,7 +2110,7 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
     gf_solve_opts o = pol->solve;
     o.history = nullptr;
     o.tol = pol->tau;
-    RET(validate_opts(&o));
+    RET(validate_grid_opts(g, &o));
     RET(set_device(g));
     std::memset(info, 0, sizeof(*info));
     info->r50 = info->r100 = std::nan("");

@@ -7,6 +7,7 @@
     python -m paper_2607_26382_b300.experiments conditioning
     python -m paper_2607_26382_b300.experiments adaptive
     python -m paper_2607_26382_b300.experiments false_accept
+    python -m paper_2607_26382_b300.experiments galerkin
 
 batch102: 102 frozen states of uneven size (nx in {32,48,64,80}, ny = nz = nx/2,
   round-robin; 71 smoothed-Gaussian states with 40% of voxels at floor, 31
@@ -54,6 +55,10 @@ false_accept: the projected-versus-true stopping mismatch of Sec. 4.1.1 on regen
   {1e-3, 1e-2}. Forms: FP64 with the fixed V-cycle (the paper's fixed-preconditioner
   control), FP64 with the adaptive preconditioner (line search 0.1, fine correction 20),
   and the mixed V-cycle with the split-integer Krylov operator and FP64 CGS2 (outer 1).
+galerkin: rediscretised against Galerkin coarse operators (gf_set_coarse_operator) on
+  the four 96x48x48 bench states at rho_min 1e-6 and 1e-3, 5 levels, FGMRES(30) to
+  1e-6: steps, time per step and per V-cycle, mixed (outer 2) and FP64; plus the
+  Galerkin hierarchy's set-up time (gf_set_floor).
 """
 from __future__ import annotations
 
@@ -461,15 +466,66 @@ def false_accept(args):
     return out
 
 
+def galerkin(args):
+    import torch
+    import synth
+    nx, ny, nz, levels = 96, 48, 48, 5
+    out = {}
+    for kind_name, kind in (("rediscretised", L.GF_COARSE_REDISCRETISED), ("galerkin", L.GF_COARSE_GALERKIN)):
+        g = L.create_grid(nx, ny, nz, levels=levels)
+        g.set_coarse_operator(kind)
+        f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        g.cantilever_load(f)
+        for prec, outer, pname in ((L.GF_MIXED, 2, "mixed"), (L.GF_FP64, 0, "fp64")):
+            for rho_min in (1e-6, 1e-3):
+                its, t_solve, t_floor, etas = [], 0.0, 0.0, []
+                for seed in range(4):
+                    g.set_density(torch.as_tensor(synth.smoothed_gaussian_density(nx, ny, nz, seed), device="cuda"), 3.0)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    g.set_floor(rho_min)
+                    torch.cuda.synchronize()
+                    t_floor += time.perf_counter() - t0
+                    u = torch.zeros_like(f)
+                    g.solve(f, u, restart=30, kmax=200, prec=prec, outer=outer)    # graphs captured
+                    u.zero_()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    o = g.solve(f, u, restart=30, kmax=200, prec=prec, outer=outer)
+                    torch.cuda.synchronize()
+                    t_solve += time.perf_counter() - t0
+                    its.append(o["iters"])
+                    etas.append(g.true_residual(f, u))
+                x = torch.randn(g.n_dof, dtype=torch.float64, device="cuda")
+                z = torch.empty_like(x)
+                for _ in range(3):
+                    g.vcycle(x, z, prec)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(20):
+                    g.vcycle(x, z, prec)
+                e1.record()
+                torch.cuda.synchronize()
+                out[f"{kind_name}, {pname}, rho_min {rho_min:g}"] = {
+                    "steps": its, "max_eta": max(etas), "ms_per_step": t_solve / sum(its) * 1e3,
+                    "vcycle_ms": e0.elapsed_time(e1) / 20, "set_floor_ms": t_floor / 4 * 1e3}
+                print(kind_name, pname, rho_min, json.dumps(out[f"{kind_name}, {pname}, rho_min {rho_min:g}"]),
+                      flush=True)
+        g.close()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["batch102", "oc_loop", "oc_reuse", "true_checks", "conditioning", "adaptive",
-                                     "false_accept"])
+                                     "false_accept", "galerkin"])
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--iters", type=int, default=40)
     a = ap.parse_args(argv)
     res = {"batch102": batch102, "oc_loop": oc_loop, "oc_reuse": oc_reuse, "true_checks": true_checks,
-           "conditioning": conditioning, "adaptive": adaptive, "false_accept": false_accept}[a.what](a)
+           "conditioning": conditioning, "adaptive": adaptive, "false_accept": false_accept,
+           "galerkin": galerkin}[a.what](a)
     print(json.dumps(res), flush=True)
     return 0
 
