@@ -104,57 +104,81 @@ __global__ void gal_coarsen_kernel(const double* __restrict__ Kf, double* __rest
     if (Kc32) Kc32[t] = (float)s;
 }
 
-// The level operator from element matrices, node per thread (node_stencil_kernel's
-// modes, plus GAL_FIRST). Row 3a+i of the matrix of each adjacent element (a = this
-// node's local index there) times the element's node values; fixed nodes read as 0.
+// The level operator from element matrices (node_stencil_kernel's modes, plus
+// GAL_FIRST), eight threads per node: thread el of a node's group takes the adjacent
+// element (i - 1 + (el & 1), j - 1 + (el >> 1 & 1), k - 1 + (el >> 2)), where the node is
+// local node a, and forms rows 3a..3a+2 of that element's matrix times its node values
+// (fixed nodes read as 0) and, to smooth, the element's 3x3 block at (a, a). A xor
+// butterfly over the eight lanes sums the elements in a fixed order, and the group's
+// first lane writes the node. Coarse levels have few nodes; eight threads per node
+// keep several blocks on every SM and the element rows' loads in parallel.
 template <typename T, int MODE, typename BT, typename OT>
 __global__ void __launch_bounds__(256)
 gal_node_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __restrict__ out,
                 const T* __restrict__ Ke, GridDims d, T omega, const int* __restrict__ halt)
 {
-    if (halt != nullptr && *halt != 0) return;
+    if (halt != nullptr && *halt != 0) return;   // uniform over the grid
     const int NX = d.nx + 1, NY = d.ny + 1;
     const long long nn = (long long)NX * NY * (d.nz + 1);
-    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= nn) return;
-    int i, j, k;
-    node_coords(n, NX, NY, i, j, k);
+    const long long n = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int el = threadIdx.x & 7;
+    const bool active = n < nn;                  // uniform over the node's eight lanes
+    int i = 0, j = 0, k = 0;
+    if (active) node_coords(n, NX, NY, i, j, k);
+    T a0 = 0, a1 = 0, a2 = 0;
+    T d00 = 0, d11 = 0, d22 = 0, d01 = 0, d02 = 0, d12 = 0;
+    const int ox = el & 1, oy = (el >> 1) & 1, oz = el >> 2;
+    const int ex = i - 1 + ox, ey = j - 1 + oy, ez = k - 1 + oz;
+    if (active && i != 0 && ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny && ez >= 0 && ez < d.nz) {
+        const int a = local_index(1 - ox, 1 - oy, 1 - oz);
+        const T* Kr = Ke + (ex + (long long)d.nx * (ey + (long long)d.ny * ez)) * GAL_KE + 3 * a * 24;
+        if (MODE != GAL_FIRST) {
+#pragma unroll
+            for (int bl = 0; bl < 8; ++bl) {
+                int bx, by, bz;
+                local_xyz(bl, bx, by, bz);
+                T u0 = 0, u1 = 0, u2 = 0;
+                if (ex + bx != 0) {   // fixed node: reads as 0
+                    const long long m = (ex + bx) + (long long)NX * ((ey + by) + (long long)NY * (ez + bz));
+                    u0 = x[3 * m + 0];
+                    u1 = x[3 * m + 1];
+                    u2 = x[3 * m + 2];
+                }
+                a0 = fma(Kr[3 * bl + 0], u0, fma(Kr[3 * bl + 1], u1, fma(Kr[3 * bl + 2], u2, a0)));
+                a1 = fma(Kr[24 + 3 * bl + 0], u0, fma(Kr[24 + 3 * bl + 1], u1, fma(Kr[24 + 3 * bl + 2], u2, a1)));
+                a2 = fma(Kr[48 + 3 * bl + 0], u0, fma(Kr[48 + 3 * bl + 1], u1, fma(Kr[48 + 3 * bl + 2], u2, a2)));
+            }
+        }
+        if (MODE == ST_SWEEP || MODE == GAL_FIRST) {
+            d00 = Kr[3 * a + 0];
+            d01 = Kr[3 * a + 1];
+            d02 = Kr[3 * a + 2];
+            d11 = Kr[24 + 3 * a + 1];
+            d12 = Kr[24 + 3 * a + 2];
+            d22 = Kr[48 + 3 * a + 2];
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        if (MODE == ST_SWEEP || MODE == GAL_FIRST) {
+            d00 += __shfl_xor_sync(0xffffffffu, d00, o);
+            d11 += __shfl_xor_sync(0xffffffffu, d11, o);
+            d22 += __shfl_xor_sync(0xffffffffu, d22, o);
+            d01 += __shfl_xor_sync(0xffffffffu, d01, o);
+            d02 += __shfl_xor_sync(0xffffffffu, d02, o);
+            d12 += __shfl_xor_sync(0xffffffffu, d12, o);
+        }
+    }
+    if (!active || el != 0) return;
     if (i == 0) {
         out[3 * n + 0] = OT(0);
         out[3 * n + 1] = OT(0);
         out[3 * n + 2] = OT(0);
         return;
     }
-    T a0 = 0, a1 = 0, a2 = 0;
-    T d00 = 0, d11 = 0, d22 = 0, d01 = 0, d02 = 0, d12 = 0;
-    for (int oz = 0; oz < 2; ++oz)
-        for (int oy = 0; oy < 2; ++oy)
-            for (int ox = 0; ox < 2; ++ox) {
-                const int ex = i - 1 + ox, ey = j - 1 + oy, ez = k - 1 + oz;
-                if (ex < 0 || ex >= d.nx || ey < 0 || ey >= d.ny || ez < 0 || ez >= d.nz) continue;
-                const int a = local_index(1 - ox, 1 - oy, 1 - oz);
-                const T* Kr = Ke + (ex + (long long)d.nx * (ey + (long long)d.ny * ez)) * GAL_KE + 3 * a * 24;
-                if (MODE != GAL_FIRST) {
-                    for (int bl = 0; bl < 8; ++bl) {
-                        int bx, by, bz;
-                        local_xyz(bl, bx, by, bz);
-                        if (ex + bx == 0) continue;   // fixed node: reads as 0
-                        const long long m = (ex + bx) + (long long)NX * ((ey + by) + (long long)NY * (ez + bz));
-                        const T u0 = x[3 * m + 0], u1 = x[3 * m + 1], u2 = x[3 * m + 2];
-                        a0 = fma(Kr[3 * bl + 0], u0, fma(Kr[3 * bl + 1], u1, fma(Kr[3 * bl + 2], u2, a0)));
-                        a1 = fma(Kr[24 + 3 * bl + 0], u0, fma(Kr[24 + 3 * bl + 1], u1, fma(Kr[24 + 3 * bl + 2], u2, a1)));
-                        a2 = fma(Kr[48 + 3 * bl + 0], u0, fma(Kr[48 + 3 * bl + 1], u1, fma(Kr[48 + 3 * bl + 2], u2, a2)));
-                    }
-                }
-                if (MODE == ST_SWEEP || MODE == GAL_FIRST) {
-                    d00 += Kr[3 * a + 0];
-                    d01 += Kr[3 * a + 1];
-                    d02 += Kr[3 * a + 2];
-                    d11 += Kr[24 + 3 * a + 1];
-                    d12 += Kr[24 + 3 * a + 2];
-                    d22 += Kr[48 + 3 * a + 2];
-                }
-            }
     if (MODE == ST_APPLY) {
         out[3 * n + 0] = OT(a0);
         out[3 * n + 1] = OT(a1);

@@ -619,8 +619,8 @@ template <typename T, int MODE>
 int gal_level(gf_grid* g, int l, const T* x, const T* b, T* out, T omega, const int* halt)
 {
     const Level& L = g->lv[l];
-    LAUNCH(g, nblk(L.nodes), 256, (gf::gal_node_kernel<T, MODE, T, T>), x, b, out, gal_ke<T>(L), L.dims(), omega,
-           halt);
+    LAUNCH(g, nblk(8 * L.nodes), 256, (gf::gal_node_kernel<T, MODE, T, T>), x, b, out, gal_ke<T>(L), L.dims(),
+           omega, halt);
     return GF_OK;
 }
 
