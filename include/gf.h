@@ -114,6 +114,13 @@ typedef struct {
                           node-block Jacobi operator, in the V-cycle's precision; z += d only if the
                           recomputed ||r - K d|| < ||r||. All on the device (inside the captured
                           steps). Single grid only. Other values: GF_ERR_ARG. */
+    int    coarse_steps; /* 0 = off: the coarsest level is solved exactly (dense FP64 inverse).
+                          k in [1, 32]: the coarse-level solve of Table solver-config instead, k
+                          steps of an inner FGMRES(k) from 0 on the coarsest level's operator,
+                          preconditioned by its 3x3 node-block Jacobi operator, in the V-cycle's
+                          precision (on the device, inside the captured steps). Needs >= 2 levels;
+                          the cluster V-cycle is not used with it. Single grid only. Other values:
+                          GF_ERR_ARG. */
 } gf_solve_opts;
 
 typedef struct {

@@ -51,6 +51,12 @@ Fine-level adaptive correction (optional, fine_steps > 0; Table solver-config): 
 the V-cycle, fine_steps steps of an inner FGMRES(fine_steps) on the fine-level residual
 equation, preconditioned by the node-block Jacobi operator, applied only if it lowers
 the recomputed residual norm.
+Coarse-level inner Krylov solve (optional, coarse_steps > 0; Table solver-config's "10
+inner Krylov steps with restart 10 on the coarse level"): the coarsest level of a
+hierarchy with two or more levels is solved by coarse_steps steps of an inner
+FGMRES(coarse_steps) from 0, preconditioned by its node-block Jacobi operator, instead
+of exactly (reading: the coarse level is the coarsest one, the inner preconditioner the
+one the fine-level correction uses).
 True-residual checks (optional): every c steps of the probe the current iterate is
 formed as at a cycle end and its guard residual recomputed; the detector fires when
 one exceeds ratio (default 10) times the projected estimate of the same step, and a
@@ -371,6 +377,7 @@ class Hierarchy:
     coarse: str = "rediscretised"       # or "galerkin"
     ls_ratio: float = 0.0               # > 0: line-searched, rejectable coarse correction (theta)
     fine_steps: int = 0                 # > 0: fine-level adaptive correction, inner FGMRES(fine_steps)
+    coarse_steps: int = 0               # > 0: coarsest level by inner FGMRES(coarse_steps), not exactly
 
 
 def level_apply(level: Level, x: np.ndarray) -> np.ndarray:
@@ -394,7 +401,8 @@ def _blocks_of(K: sp.csr_matrix, mesh: Mesh) -> np.ndarray:
 
 def build_hierarchy(mesh: Mesh, E_fine: np.ndarray, n_levels: int, nu: float = 0.3,
                     nu1: int = 2, nu2: int = 2, omega: float = 0.6, smoother: str = "jacobi",
-                    coarse: str = "rediscretised", ls_ratio: float = 0.0, fine_steps: int = 0) -> Hierarchy:
+                    coarse: str = "rediscretised", ls_ratio: float = 0.0, fine_steps: int = 0,
+                    coarse_steps: int = 0) -> Hierarchy:
     """Level l has (nx, ny, nz)/2^l elements of edge h*2^l. coarse="rediscretised":
     modulus = child mean and K0(h_l), applied matrix-free (this build's reading);
     coarse="galerkin": K_{l+1} = P^T K_l P with P the masked trilinear prolongation, the
@@ -403,7 +411,7 @@ def build_hierarchy(mesh: Mesh, E_fine: np.ndarray, n_levels: int, nu: float = 0
     if coarse not in ("rediscretised", "galerkin"):
         raise ValueError(coarse)
     H = Hierarchy(nu1=nu1, nu2=nu2, omega=omega, smoother=smoother, coarse=coarse, ls_ratio=ls_ratio,
-                  fine_steps=fine_steps)
+                  fine_steps=fine_steps, coarse_steps=coarse_steps)
     m, E = mesh, np.asarray(E_fine, dtype=np.float64)
     Kg = None
     for l in range(n_levels):
@@ -442,6 +450,16 @@ def coarse_solve(level: Level, b: np.ndarray) -> np.ndarray:
     x = np.zeros_like(b)
     x[level.mesh.free] = sla.cho_solve(level.chol, b[level.mesh.free])
     return x
+
+
+def coarse_krylov(level: Level, b: np.ndarray, steps: int) -> np.ndarray:
+    """The coarse-level solve of Table solver-config: `steps` steps of an inner
+    FGMRES(steps) from x = 0 on the level's operator, preconditioned by its 3x3 node-block
+    Jacobi operator (b = 0 gives x = 0)."""
+    if not np.any(b):
+        return np.zeros_like(b)
+    return fgmres(lambda w: level_apply(level, w), lambda w: block_jacobi_apply(level, w), b,
+                  restart=steps, kmax=steps, tol=0.0).x
 
 
 def jacobi_sweep(level: Level, x: np.ndarray, b: np.ndarray, omega: float) -> np.ndarray:
@@ -530,6 +548,8 @@ def vcycle(H: Hierarchy, b: np.ndarray, l: int = 0) -> np.ndarray:
     """One V-cycle on level l for right-hand side b (fixed entries of b are zero)."""
     lev = H.levels[l]
     if l == len(H.levels) - 1:
+        if H.coarse_steps > 0 and l > 0:
+            return coarse_krylov(lev, b, H.coarse_steps)
         return coarse_solve(lev, b)
     x = _smooth(H, lev, np.zeros_like(b), b, H.nu1)
     r = b - level_apply(lev, x)
@@ -794,6 +814,7 @@ class SolverSetup:
     coarse: str = "rediscretised"
     ls_ratio: float = 0.0
     fine_steps: int = 0
+    coarse_steps: int = 0
 
 
 def solve_at_floor(setup: SolverSetup, f: np.ndarray, rho_min: float, kmax: int, tol: float,
@@ -803,7 +824,7 @@ def solve_at_floor(setup: SolverSetup, f: np.ndarray, rho_min: float, kmax: int,
     mesh = setup.mesh
     E = young_modulus(setup.rho_hat, rho_min, setup.p)
     H = build_hierarchy(mesh, E, setup.n_levels, setup.nu, setup.nu1, setup.nu2, setup.omega, setup.smoother,
-                        setup.coarse, setup.ls_ratio, setup.fine_steps)
+                        setup.coarse, setup.ls_ratio, setup.fine_steps, setup.coarse_steps)
     K0 = H.levels[0].K0
     fm = np.where(mesh.fixed, 0.0, f)
     res = fgmres(lambda v: apply_K(mesh, E, K0, v), lambda v: precondition(H, v), fm,

@@ -51,7 +51,8 @@ class GFError(RuntimeError):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("restart", c_int), ("kmax", c_int), ("tol", c_double), ("prec", c_int),
                 ("nu1", c_int), ("nu2", c_int), ("omega", c_double), ("history", POINTER(c_double)),
-                ("outer", c_int), ("smoother", c_int), ("ls_ratio", c_double), ("fine_steps", c_int)]
+                ("outer", c_int), ("smoother", c_int), ("ls_ratio", c_double), ("fine_steps", c_int),
+                ("coarse_steps", c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -300,11 +301,12 @@ class Grid:
         _check(lib().gf_apply_K_f32(self._h, _ptr(u, t, self.n_dof, "u"), _ptr(y, t, self.n_dof, "y")))
         return y
 
-    def vcycle(self, v, z, prec=GF_FP64, nu1=2, nu2=2, omega=0.6, smoother=0, ls_ratio=0.0, fine_steps=0):
+    def vcycle(self, v, z, prec=GF_FP64, nu1=2, nu2=2, omega=0.6, smoother=0, ls_ratio=0.0, fine_steps=0,
+               coarse_steps=0):
         t = _torch().float64
-        if smoother or ls_ratio or fine_steps:
+        if smoother or ls_ratio or fine_steps or coarse_steps:
             o = SolveOpts(30, 0, 0.0, int(prec), int(nu1), int(nu2), float(omega), None, 0, int(smoother),
-                          float(ls_ratio), int(fine_steps))
+                          float(ls_ratio), int(fine_steps), int(coarse_steps))
             _check(lib().gf_vcycle_ex(self._h, _ptr(v, t, self.n_dof, "v"), _ptr(z, t, self.n_dof, "z"),
                                       ctypes.byref(o)))
             return z
@@ -321,12 +323,12 @@ class Grid:
 
     # solve / guard / policy
     def solve(self, f, u, restart=30, kmax=200, tol=1e-6, prec=GF_FP64, nu1=2, nu2=2, omega=0.6,
-              want_history=True, outer=0, smoother=0, ls_ratio=0.0, fine_steps=0):
+              want_history=True, outer=0, smoother=0, ls_ratio=0.0, fine_steps=0, coarse_steps=0):
         t = _torch().float64
         hist = (c_double * (kmax + 1))() if want_history else None
         o = SolveOpts(int(restart), int(kmax), float(tol), int(prec), int(nu1), int(nu2), float(omega),
                       ctypes.cast(hist, POINTER(c_double)) if hist is not None else None, int(outer),
-                      int(smoother), float(ls_ratio), int(fine_steps))
+                      int(smoother), float(ls_ratio), int(fine_steps), int(coarse_steps))
         info = SolveInfo()
         _check(lib().gf_solve(self._h, _ptr(f, t, self.n_dof, "f"), _ptr(u, t, self.n_dof, "u"),
                               ctypes.byref(o), ctypes.byref(info)))

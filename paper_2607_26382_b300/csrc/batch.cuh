@@ -589,6 +589,7 @@ int gf_batch_select_floor(gf_batch* b, const gf_policy* pol, gf_select_info* inf
     if (pol->true_check_every != 0) return set_err(GF_ERR_ARG, "true_check_every is single-grid only");
     if (pol->solve.ls_ratio != 0.0) return set_err(GF_ERR_ARG, "ls_ratio is single-grid only");
     if (pol->solve.fine_steps != 0) return set_err(GF_ERR_ARG, "fine_steps is single-grid only");
+    if (pol->solve.coarse_steps != 0) return set_err(GF_ERR_ARG, "coarse_steps is single-grid only");
     if (pol->solve.restart > gf::KRY_NV) return set_err(GF_ERR_ARG, "batched restart must be in [1, 32]");
     const int B = b->B;
     for (int i = 0; i < B; ++i)

@@ -157,6 +157,8 @@ struct gf_grid {
     double* fc_partial = nullptr;
     int fc_steps = 0, fc_es = 0, fc_nb = 0;
     int gkey_fine = -1;               // fine_steps the captured Arnoldi steps were built with
+    int gkey_coarse = -1;             // coarse_steps the captured Arnoldi steps were built with
+    int coarse_steps = 0;             // coarse-level inner FGMRES steps of the current solve (0: exact)
     double* ls_partial = nullptr;     // line search: per-block dot products
     double* ls_alpha = nullptr;       // line search: alpha of each level (device)
     int ls_nb = 0;
@@ -329,6 +331,9 @@ struct LvBuf<float> {
 template <typename T>
 int coarse_correct(gf_grid* g, int l, T* x, const T* xc, T* c, const T* r, double theta, const int* halt);
 
+template <typename T>
+int coarsest_solve(gf_grid* g, const T* b, T* x, const int* halt);
+
 // One V-cycle z = B v in precision T (Table solver-config: 2:1 trilinear transfer,
 // damped node-block Jacobi smoothing, coarsest solve by the FP64 dense inverse).
 template <typename T>
@@ -379,7 +384,7 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
     }
     {
         Level& c = g->lv[L - 1];
-        LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<T, T>), g->Ainv, B::b(c), B::x(c), g->nc, halt);
+        RET(coarsest_solve<T>(g, (const T*)B::b(c), B::x(c), halt));
         cur[L - 1] = B::x(c);
     }
     for (int l = L - 2; l >= 0; --l) {
@@ -417,7 +422,7 @@ int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2,
     const int L = g->L;
     g->stats.vcycles++;
     std::vector<float*> cur(L);
-    const int lc = g->vc_l0;             // levels >= lc run in one cluster launch
+    const int lc = g->coarse_steps > 0 ? 0 : g->vc_l0;   // levels >= lc run in one cluster launch
     const int Ldown = (lc > 0) ? lc : L - 1;
     for (int l = 0; l < Ldown; ++l) {
         Level& lev = g->lv[l];
@@ -465,8 +470,7 @@ int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2,
         cur[lc] = (((nu1 - 1) + nu2) & 1) ? g->lv[lc].t32 : g->lv[lc].x32;
     } else {
         Level& c = g->lv[L - 1];
-        LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<float, float>), (const double*)g->Ainv,
-               (const float*)c.b32, c.x32, g->nc, halt);
+        RET(coarsest_solve<float>(g, (const float*)c.b32, c.x32, halt));
         cur[L - 1] = c.x32;
     }
     for (int l = ((lc > 0) ? lc : L - 1) - 1; l >= 0; --l) {
@@ -583,7 +587,7 @@ int vcycle_cheb(gf_grid* g, const double* v, double* z, int nu1, int nu2, const 
     }
     {
         Level& c = g->lv[L - 1];
-        LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<T, T>), g->Ainv, B::b(c), B::x(c), g->nc, halt);
+        RET(coarsest_solve<T>(g, (const T*)B::b(c), B::x(c), halt));
         cur[L - 1] = B::x(c);
     }
     for (int l = L - 2; l >= 0; --l) {
@@ -673,8 +677,7 @@ int vcycle_galerkin(gf_grid* g, const double* v, double* z, int nu1, int nu2, T 
     }
     {
         Level& c = g->lv[L - 1];
-        LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<T, T>), (const double*)g->Ainv, (const T*)B::b(c),
-               B::x(c), g->nc, halt);
+        RET(coarsest_solve<T>(g, (const T*)B::b(c), B::x(c), halt));
         cur[L - 1] = B::x(c);
     }
     for (int l = L - 2; l >= 0; --l) {
@@ -773,13 +776,77 @@ int ensure_fc(gf_grid* g, int steps, int prec)
     return GF_OK;
 }
 
+// The fine-level correction's and the coarse-level solve's inner FGMRES buffers, and
+// the coarse-level steps the V-cycles of this call use (outside any graph capture).
+int set_coarse_steps(gf_grid* g, const gf_solve_opts* o)
+{
+    const int coarse = g->L > 1 ? o->coarse_steps : 0;
+    const int steps = std::max(o->fine_steps, coarse);
+    if (steps > 0) RET(ensure_fc(g, steps, o->prec));
+    g->coarse_steps = coarse;
+    return GF_OK;
+}
+
+// steps steps of an inner FGMRES(steps) from d = 0 on K_l d = r on level l, preconditioned
+// by the level's 3x3 node-block Jacobi operator (first_sweep_kernel with omega = 1, or
+// the Galerkin form), in precision T (finecorr.cuh); d = Z y unless the solve is skipped
+// (r = 0 or halted), when d is left as it was. nb blocks for the reductions (<= fc_nb).
+template <typename T>
+int inner_fgmres(gf_grid* g, int l, const T* r, T* d, int steps, const int* halt, int nb)
+{
+    Level& lev = g->lv[l];
+    const long long n = lev.ndof;
+    const bool gal = l > 0 && g->coarse_kind == GF_COARSE_GALERKIN;
+    T *V = (T*)g->fcV, *Z = (T*)g->fcZ;
+    gf::FcState* st = g->fc;
+    LAUNCH(g, nb, gf::FC_THREADS, gf::fc_start_kernel<T>, r, n, st, g->fc_partial, halt);
+    LAUNCH(g, 2 * g->sms, 256, gf::fc_scale_kernel<T>, r, V, n, (const gf::FcState*)st);
+    const int* stop = &st->stop;
+    for (int j = 0; j < steps; ++j) {
+        T* vj = V + (long long)j * n;
+        T* zj = Z + (long long)j * n;
+        T* w = V + (long long)(j + 1) * n;
+        if (gal) {
+            RET((gal_level<T, gf::GAL_FIRST>(g, l, (const T*)nullptr, (const T*)vj, zj, T(1), stop)));
+            RET((gal_level<T, gf::ST_APPLY>(g, l, (const T*)zj, (const T*)nullptr, w, T(0), stop)));
+        } else {
+            LAUNCH(g, nblk(lev.nodes), 256, (gf::first_sweep_kernel<T, T, T>), (const T*)vj, zj, LvBuf<T>::E(lev),
+                   lev.dims(), k0<T>(g), T(1), stop);
+            RET((stencil<T, T, gf::ST_APPLY>(g, l, (const T*)zj, (const T*)nullptr, w, LvBuf<T>::E(lev), k0<T>(g),
+                                             T(0), stop)));
+        }
+        LAUNCH(g, nb, gf::FC_THREADS, gf::fc_dots1_kernel<T>, (const T*)V, n, (const T*)w, n, j, st, g->fc_partial);
+        LAUNCH(g, nb, gf::FC_THREADS, gf::fc_dots2_kernel<T>, (const T*)V, n, w, n, j, st, g->fc_partial);
+        LAUNCH(g, nb, gf::FC_THREADS, gf::fc_norm_kernel<T>, (const T*)V, n, w, n, j, steps, st, g->fc_partial);
+        if (j + 1 < steps) LAUNCH(g, 2 * g->sms, 256, gf::fc_vscale_kernel<T>, w, n, (const gf::FcState*)st);
+    }
+    LAUNCH(g, 1, 32, gf::fc_backsolve_kernel, st);
+    LAUNCH(g, 2 * g->sms, 256, gf::fc_combine_kernel<T>, (const T*)Z, n, d, n, (const gf::FcState*)st);
+    return GF_OK;
+}
+
+// The coarsest level's solve x = A_c^{-1} b: the dense FP64 inverse, or (coarse_steps > 0)
+// Table solver-config's inner Krylov solve on the coarse level, from x = 0.
+template <typename T>
+int coarsest_solve(gf_grid* g, const T* b, T* x, const int* halt)
+{
+    if (g->coarse_steps > 0 && g->L > 1) {
+        const Level& c = g->lv[g->L - 1];
+        CK(cudaMemsetAsync(x, 0, sizeof(T) * c.ndof, g->cur_stream));
+        const int nb = (int)std::min<long long>(g->fc_nb, std::max<long long>(1, (c.ndof + 1023) / 1024));
+        return inner_fgmres<T>(g, g->L - 1, b, x, g->coarse_steps, halt, nb);
+    }
+    LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<T, T>), (const double*)g->Ainv, b, x, g->nc, halt);
+    return GF_OK;
+}
+
 // the fine-level adaptive correction of z = V-cycle(v), in precision T (finecorr.cuh)
 template <typename T>
 int fine_correct(gf_grid* g, const double* v, double* z, int steps, const int* halt)
 {
     Level& lev = g->lv[0];
     const long long n = g->ndof;
-    T *V = (T*)g->fcV, *Z = (T*)g->fcZ, *r = (T*)g->fcR, *d = (T*)g->fcD, *q = (T*)g->fcQ;
+    T *r = (T*)g->fcR, *d = (T*)g->fcD, *q = (T*)g->fcQ;
     gf::FcState* st = g->fc;
     const int nb = g->fc_nb;
     if constexpr (sizeof(T) == sizeof(double)) {   // r = v - K z
@@ -790,24 +857,7 @@ int fine_correct(gf_grid* g, const double* v, double* z, int steps, const int* h
                halt);
         RET((tiled_f32<gf::ST_RESID, double, float>(g, 0, zt, v, (float*)r, lev.E32, 0.0f, halt)));
     }
-    LAUNCH(g, nb, gf::FC_THREADS, gf::fc_start_kernel<T>, (const T*)r, n, st, g->fc_partial, halt);
-    LAUNCH(g, 2 * g->sms, 256, gf::fc_scale_kernel<T>, (const T*)r, V, n, (const gf::FcState*)st);
-    const int* stop = &st->stop;
-    for (int j = 0; j < steps; ++j) {
-        T* vj = V + (long long)j * n;
-        T* zj = Z + (long long)j * n;
-        T* w = V + (long long)(j + 1) * n;
-        LAUNCH(g, nblk(lev.nodes), 256, (gf::first_sweep_kernel<T, T, T>), (const T*)vj, zj, LvBuf<T>::E(lev),
-               lev.dims(), k0<T>(g), T(1), stop);
-        RET((stencil<T, T, gf::ST_APPLY>(g, 0, (const T*)zj, (const T*)nullptr, w, LvBuf<T>::E(lev), k0<T>(g), T(0),
-                                         stop)));
-        LAUNCH(g, nb, gf::FC_THREADS, gf::fc_dots1_kernel<T>, (const T*)V, n, (const T*)w, n, j, st, g->fc_partial);
-        LAUNCH(g, nb, gf::FC_THREADS, gf::fc_dots2_kernel<T>, (const T*)V, n, w, n, j, st, g->fc_partial);
-        LAUNCH(g, nb, gf::FC_THREADS, gf::fc_norm_kernel<T>, (const T*)V, n, w, n, j, steps, st, g->fc_partial);
-        if (j + 1 < steps) LAUNCH(g, 2 * g->sms, 256, gf::fc_vscale_kernel<T>, w, n, (const gf::FcState*)st);
-    }
-    LAUNCH(g, 1, 32, gf::fc_backsolve_kernel, st);
-    LAUNCH(g, 2 * g->sms, 256, gf::fc_combine_kernel<T>, (const T*)Z, n, d, n, (const gf::FcState*)st);
+    RET(inner_fgmres<T>(g, 0, (const T*)r, d, steps, halt, nb));
     RET((stencil<T, T, gf::ST_APPLY>(g, 0, (const T*)d, (const T*)nullptr, q, LvBuf<T>::E(lev), k0<T>(g), T(0),
                                      &st->skip)));
     LAUNCH(g, nb, gf::FC_THREADS, gf::fc_accept_kernel<T>, (const T*)r, (const T*)q, n, st, g->fc_partial);
@@ -1210,8 +1260,9 @@ int run_step(gf_grid* g, int j, const gf_solve_opts* o)
     if (!g->use_graphs) return arnoldi_step(g, j, o);
     if (g->gkey_prec != o->prec || g->gkey_nu1 != o->nu1 || g->gkey_nu2 != o->nu2 || g->gkey_omega != o->omega ||
         g->gkey_outer != o->outer || g->gkey_smoother != o->smoother || g->gkey_ls != o->ls_ratio ||
-        g->gkey_fine != o->fine_steps) {
+        g->gkey_fine != o->fine_steps || g->gkey_coarse != o->coarse_steps) {
         drop_graphs(g);
+        g->gkey_coarse = o->coarse_steps;
         g->gkey_ls = o->ls_ratio;
         g->gkey_fine = o->fine_steps;
         g->gkey_outer = o->outer;
@@ -1293,7 +1344,7 @@ int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, g
     RET(ensure_krylov(g, m, o->kmax, o->outer));
     if (o->smoother == 1) RET(ensure_cheb(g, o->prec));
     if (o->ls_ratio > 0.0) RET(ensure_ls(g));
-    if (o->fine_steps > 0) RET(ensure_fc(g, o->fine_steps, o->prec));
+    RET(set_coarse_steps(g, o));
     const int NX0 = g->nx + 1;
     // fixed entries of u are written as 0
     LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, double>), u, u, g->ndof, NX0, nullptr);
@@ -1373,6 +1424,7 @@ int validate_opts(const gf_solve_opts* o)
     if (!(o->ls_ratio >= 0.0 && std::isfinite(o->ls_ratio))) return set_err(GF_ERR_ARG, "ls_ratio must be finite and >= 0");
     if (o->ls_ratio > 0.0 && o->smoother != 0) return set_err(GF_ERR_ARG, "ls_ratio > 0 needs smoother 0");
     if (o->fine_steps < 0 || o->fine_steps > gf::FC_MAX) return set_err(GF_ERR_ARG, "fine_steps in [0, 32]");
+    if (o->coarse_steps < 0 || o->coarse_steps > gf::FC_MAX) return set_err(GF_ERR_ARG, "coarse_steps in [0, 32]");
     return GF_OK;
 }
 
@@ -1883,6 +1935,7 @@ int gf_vcycle(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2
     if (prec != GF_FP64 && prec != GF_MIXED) return set_err(GF_ERR_ARG, "prec");
     if (nu1 < 1 || nu2 < 1 || nu1 > 16 || nu2 > 16 || !(omega > 0 && omega < 2)) return set_err(GF_ERR_ARG, "smoother");
     RET(set_device(g));
+    g->coarse_steps = 0;
     return vcycle_dispatch(g, v, z, prec, nu1, nu2, omega, nullptr);
 }
 
@@ -1895,7 +1948,7 @@ int gf_vcycle_ex(gf_grid* g, const double* v, double* z, const gf_solve_opts* o)
     RET(set_device(g));
     if (o->smoother == 1) RET(ensure_cheb(g, o->prec));
     if (o->ls_ratio > 0.0) RET(ensure_ls(g));
-    if (o->fine_steps > 0) RET(ensure_fc(g, o->fine_steps, o->prec));
+    RET(set_coarse_steps(g, o));
     return vcycle_dispatch(g, v, z, o->prec, o->nu1, o->nu2, o->omega, nullptr, o->smoother, o->ls_ratio,
                            o->fine_steps);
 }

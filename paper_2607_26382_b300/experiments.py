@@ -8,6 +8,7 @@
     python -m paper_2607_26382_b300.experiments adaptive
     python -m paper_2607_26382_b300.experiments false_accept
     python -m paper_2607_26382_b300.experiments galerkin
+    python -m paper_2607_26382_b300.experiments coarse_krylov
 
 batch102: 102 frozen states of uneven size (nx in {32,48,64,80}, ny = nz = nx/2,
   round-robin; 71 smoothed-Gaussian states with 40% of voxels at floor, 31
@@ -59,6 +60,11 @@ galerkin: rediscretised against Galerkin coarse operators (gf_set_coarse_operato
   the four 96x48x48 bench states at rho_min 1e-6 and 1e-3, 5 levels, FGMRES(30) to
   1e-6: steps, time per step and per V-cycle, mixed (outer 2) and FP64; plus the
   Galerkin hierarchy's set-up time (gf_set_floor).
+coarse_krylov: the coarsest level solved exactly against 10 inner FGMRES steps
+  (coarse_steps, Table solver-config's coarse level), and the paper's whole adaptive
+  preconditioner (line search 0.1, fine correction 20, coarse Krylov 10), on the four
+  96x48x48 bench states at rho_min 1e-6 and 1e-3: steps, time per step, accepted
+  (FP64 recomputed residual <= 1e-6), mixed (outer 2) and FP64.
 """
 from __future__ import annotations
 
@@ -516,16 +522,50 @@ def galerkin(args):
     return out
 
 
+def coarse_krylov(args):
+    import torch
+    import synth
+    nx, ny, nz, levels = 96, 48, 48, 5
+    forms = (("exact coarse solve", {}), ("coarse Krylov 10", {"coarse_steps": 10}),
+             ("line search 0.1 + fine 20 + coarse Krylov 10", {"coarse_steps": 10, "fine_steps": 20, "ls_ratio": 0.1}))
+    g = L.create_grid(nx, ny, nz, levels=levels)
+    f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.cantilever_load(f)
+    out = {}
+    for prec, outer, pname in ((L.GF_MIXED, 2, "mixed"), (L.GF_FP64, 0, "fp64")):
+        for rho_min in (1e-6, 1e-3):
+            for name, kw in forms:
+                its, t, acc = [], 0.0, 0
+                for seed in range(4):
+                    g.set_density(torch.as_tensor(synth.smoothed_gaussian_density(nx, ny, nz, seed), device="cuda"), 3.0)
+                    g.set_floor(rho_min)
+                    u = torch.zeros_like(f)
+                    g.solve(f, u, restart=30, kmax=200, prec=prec, outer=outer, **kw)    # graphs captured
+                    u.zero_()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    o = g.solve(f, u, restart=30, kmax=200, prec=prec, outer=outer, **kw)
+                    torch.cuda.synchronize()
+                    t += time.perf_counter() - t0
+                    its.append(o["iters"])
+                    acc += int(g.true_residual(f, u) <= 1e-6)
+                key = f"{pname}, rho_min {rho_min:g}, {name}"
+                out[key] = {"steps": its, "accepted": acc, "ms_per_step": t / sum(its) * 1e3, "seconds": t}
+                print(key, json.dumps(out[key]), flush=True)
+    g.close()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["batch102", "oc_loop", "oc_reuse", "true_checks", "conditioning", "adaptive",
-                                     "false_accept", "galerkin"])
+                                     "false_accept", "galerkin", "coarse_krylov"])
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--iters", type=int, default=40)
     a = ap.parse_args(argv)
     res = {"batch102": batch102, "oc_loop": oc_loop, "oc_reuse": oc_reuse, "true_checks": true_checks,
            "conditioning": conditioning, "adaptive": adaptive, "false_accept": false_accept,
-           "galerkin": galerkin}[a.what](a)
+           "galerkin": galerkin, "coarse_krylov": coarse_krylov}[a.what](a)
     print(json.dumps(res), flush=True)
     return 0
 

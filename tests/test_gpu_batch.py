@@ -82,12 +82,13 @@ def test_batch_matches_single_state(gf, selector, prec, outer, smoother):
 
 def test_batch_rejects_single_grid_options(gf):
     """The reuse selector, true-residual checks, the line-searched coarse correction, the
-    fine-level correction and restarts above 32 are single-grid options; the batch refuses them."""
+    fine-level correction, restarts above 32 and the coarse-level Krylov solve are single-grid
+    options; the batch refuses them."""
     dims, kind, seed, q = STATES[0]
     batch = gf.Batch([dims], levels=3)
     batch.set_state(0, dev(_rho(dims, kind, seed, q)), dev(O.cantilever_load(O.Mesh(*dims))), 3.0)
     for kw in (dict(selector=gf.GF_SEL_REUSE), dict(true_check_every=10), dict(solve_ls_ratio=0.1),
-               dict(solve_fine_steps=5), dict(solve_restart=33)):
+               dict(solve_fine_steps=5), dict(solve_restart=33), dict(solve_coarse_steps=10)):
         with pytest.raises(gf.GFError):
             batch.select_floor(gf.policy_defaults(**kw))
     assert batch.select_floor(gf.policy_defaults())[0]["status"] in (gf.GF_ACCEPTED, gf.GF_NO_ADMISSIBLE_FLOOR)

@@ -83,6 +83,20 @@ def test_vcycle_mixed_galerkin_parity(gf, nx, ny, nz, L):
     g.close()
 
 
+def test_vcycle_galerkin_with_coarse_krylov_parity(gf):
+    # the coarse-level inner Krylov solve on the assembled Galerkin coarsest operator
+    nx, ny, nz, L = 32, 16, 16, 4
+    rho = synth.bernoulli_density(nx, ny, nz, 5, 0.3)
+    m = O.Mesh(nx, ny, nz)
+    g = galerkin_grid(gf, nx, ny, nz, L, rho, 1e-3)
+    H = O.build_hierarchy(m, O.young_modulus(rho, 1e-3, 3.0), L, coarse="galerkin", coarse_steps=10)
+    v = np.where(m.fixed, 0, synth.random_vector(m.n_dof, 9))
+    z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.vcycle(dev(v), z, gf.GF_FP64, coarse_steps=10)
+    assert relerr(host(z), O.vcycle(H, v)) <= 1e-9
+    g.close()
+
+
 def test_galerkin_equals_rediscretised_at_constant_modulus(gf):
     # Q1 spaces are nested: at constant modulus P^T K_h P = K_2h, so both coarse forms
     # give the same V-cycle (to rounding)

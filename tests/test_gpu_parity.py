@@ -496,6 +496,58 @@ def test_long_restart_limits(gf):
                                                                           gf.GF_FLAG_MAX_ITERS)
 
 
+# ------------------------------------------------ coarse-level inner Krylov solve --
+# coarse_steps = k replaces the coarsest level's dense inverse by k steps of an inner
+# FGMRES(k) from 0, preconditioned by the coarsest level's node-block Jacobi operator
+# (Table solver-config's inner Krylov steps on the coarse level), on the device.
+@pytest.mark.parametrize("nx,ny,nz,L", [(16, 8, 8, 3), (24, 10, 6, 2), (32, 16, 16, 4)])
+@pytest.mark.parametrize("k", [1, 10])
+def test_vcycle_coarse_krylov_fp64_parity(gf, nx, ny, nz, L, k):
+    g, m, rho = make(gf, nx, ny, nz, L, seed=2, rho_min=1e-3, kind="bernoulli")
+    H = O.build_hierarchy(m, O.young_modulus(rho, 1e-3, 3.0), L, coarse_steps=k)
+    v = np.where(m.fixed, 0, synth.random_vector(m.n_dof, 9))
+    z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.vcycle(dev(v), z, gf.GF_FP64, coarse_steps=k)
+    ref = O.vcycle(H, v)
+    assert relerr(host(z), ref) <= 1e-9
+    z0 = torch.zeros_like(z)
+    g.vcycle(dev(v), z0, gf.GF_FP64)                     # the exact coarse solve differs
+    assert relerr(host(z0), ref) > 1e-6
+
+
+def test_vcycle_coarse_krylov_mixed_parity(gf):
+    # FP32 levels from the BF16 density; the coarse inner solve accumulates its Gram-
+    # Schmidt dots per thread in FP32 (block and grid sums in FP64), so its solution
+    # carries FP32 rounding amplified by the coarse operator's conditioning
+    nx, ny, nz, L = 16, 8, 8, 3
+    g, m, rho = make(gf, nx, ny, nz, L, seed=2, rho_min=1e-3)
+    H = O.build_hierarchy(m, O.young_modulus(bf16_round(rho), 1e-3, 3.0), L, coarse_steps=10)
+    v = np.where(m.fixed, 0, synth.random_vector(m.n_dof, 9))
+    z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.vcycle(dev(v), z, gf.GF_MIXED, coarse_steps=10)
+    assert relerr(host(z), O.vcycle(H, v)) <= 1e-3
+
+
+@pytest.mark.parametrize("kind,rho_min", [("bernoulli", 1e-3), ("gauss", 1e-6)])
+def test_solve_coarse_krylov_fp64_parity(gf, kind, rho_min):
+    nx, ny, nz, L = 16, 8, 8, 3
+    g, m, rho = make(gf, nx, ny, nz, L, seed=4, rho_min=rho_min, kind=kind)
+    f = O.cantilever_load(m)
+    res, E, K0 = O.solve_at_floor(O.SolverSetup(m, rho, p=3.0, n_levels=L, coarse_steps=10), f, rho_min, 200, 1e-6)
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    out = g.solve(dev(f), u, restart=30, kmax=200, tol=1e-6, prec=gf.GF_FP64, coarse_steps=10)
+    assert abs(out["iters"] - res.iters) <= 1 and out["flag"] == res.flag
+    k = min(out["iters"], res.iters)
+    h_gpu, h_ref = np.array(out["history"][:k + 1]), res.history[:k + 1]
+    assert np.all(np.abs(h_gpu - h_ref) <= 1e-6 * h_ref + 1e-15)
+    if res.flag == O.CONVERGED:
+        assert O.true_residual(m, E, K0, f, host(u)) <= 1.5e-6
+    with pytest.raises(gf.GFError):
+        g.solve(dev(f), u, coarse_steps=33)
+    mixed = g.solve(dev(f), u.zero_(), prec=gf.GF_MIXED, outer=2, coarse_steps=10, fine_steps=5, kmax=200)
+    assert mixed["flag"] == gf.GF_FLAG_CONVERGED
+
+
 def test_solve_mixed_converges_and_guard(gf):
     nx, ny, nz, L = 16, 8, 8, 3
     g, m, rho = make(gf, nx, ny, nz, L, seed=0, rho_min=1e-3)

@@ -442,6 +442,33 @@ def test_fine_level_correction_never_raises_the_residual_and_can_be_exact():
     assert res.flag == O.CONVERGED and res.iters <= 2
 
 
+def test_coarse_krylov_one_step_closed_form_monotone_and_exact():
+    """coarse_krylov (Table solver-config's inner Krylov solve on the coarse level): one
+    step from 0 is the minimal-residual step along z = D^{-1} b, x = alpha z with
+    alpha = (b . A z) / (A z . A z); the residual never grows with more steps (GMRES);
+    with as many steps as the coarsest level has free DOFs it is the exact solve, so the
+    V-cycle equals the one with the Cholesky coarse solve."""
+    m = O.Mesh(4, 2, 2)
+    E = O.young_modulus(synth.bernoulli_density(4, 2, 2, 7, 0.3), 1e-3, 3.0)
+    H = O.build_hierarchy(m, E, 2)
+    c = H.levels[-1]
+    b = np.where(c.mesh.fixed, 0.0, synth.random_vector(c.mesh.n_dof, 11))
+    z = O.block_jacobi_apply(c, b)
+    Az = O.level_apply(c, z)
+    x1 = O.coarse_krylov(c, b, 1)
+    assert np.allclose(x1, (b @ Az) / (Az @ Az) * z, rtol=1e-12, atol=1e-14 * np.abs(z).max())
+    res = [np.linalg.norm(b - O.level_apply(c, O.coarse_krylov(c, b, k))) for k in range(1, 9)]
+    assert all(r1 <= r0 * (1 + 1e-12) for r0, r1 in zip(res, res[1:])) and res[-1] < res[0]
+    assert not np.any(O.coarse_krylov(c, np.zeros_like(b), 5))
+    n_free = int(c.mesh.free.sum())                        # 24: the 2x1x1 coarsest level
+    v = np.where(m.fixed, 0.0, synth.random_vector(m.n_dof, 12))
+    Hk = O.build_hierarchy(m, E, 2, coarse_steps=n_free)
+    ref = O.vcycle(H, v)
+    assert np.linalg.norm(O.vcycle(Hk, v) - ref) <= 1e-8 * np.linalg.norm(ref)
+    H10 = O.build_hierarchy(m, E, 2, coarse_steps=10)
+    assert np.linalg.norm(O.vcycle(H10, v) - ref) > 1e-6 * np.linalg.norm(ref)   # ten steps are not exact
+
+
 # ---------------------------------------------------------------- FGMRES ----
 def test_fgmres_diagonal_distinct_eigenvalues():
     d = np.array([1.0, 2.0, 2.0, 3.0, 3.0, 3.0, 5.0])
