@@ -132,6 +132,7 @@ struct gf_grid {
     gf::K0Param<float> K0f;
     gf::K0Pair K0p;                   // K0f with rows 3a, 3a+1 paired (node_stencil_f32x2_kernel)
     bool f32x2 = true;                // FP32 node stencil with paired FMAs (GF_F32X2=0: scalar FMAs)
+    int ctpb = 128;                   // block size for levels too small to fill the SMs (0: as level 0)
     int coarse_kind = GF_COARSE_REDISCRETISED;   // gf_set_coarse_operator; applied by gf_set_floor
     double* galG = nullptr;           // G_c = T_c^T K0 T_c, 8 x 576 (Galerkin first coarse level)
     double* gal_s[2] = {nullptr, nullptr};   // FP64 scratch for the BF16-moduli chain
@@ -233,6 +234,14 @@ int launch(gf_grid* g, dim3 grid, dim3 block, void (*kern)(KArgs...), Args... ar
 
 namespace {
 
+// Block size for a launch over `nodes` nodes: levels with fewer than two 256-thread
+// blocks per SM take ctpb-thread blocks, so that every SM gets work (the results do not
+// depend on the block size: one node per thread).
+int level_tpb(const gf_grid* g, long long nodes, int base)
+{
+    return (g->ctpb > 0 && nodes < 512LL * g->sms) ? g->ctpb : base;
+}
+
 int check_grid(const gf_grid* g)
 {
     if (!g) return set_err(GF_ERR_ARG, "null grid");
@@ -261,13 +270,13 @@ int tiled_f32(gf_grid* g, int l, const float* x, const BT* b, OT* out, const flo
         return GF_OK;
     }
     if (g->tpb[1] > 0 && g->f32x2) {   // the same, with paired FMAs
-        const int tpb = g->tpb[1];
+        const int tpb = level_tpb(g, L.nodes, g->tpb[1]);
         LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_f32x2_kernel<MODE, BT, OT>), x, b, out, E, L.dims(),
                g->K0p, omega, halt);
         return GF_OK;
     }
     if (g->tpb[1] > 0) {   // linear node-per-thread kernel with the autotuned block size
-        const int tpb = g->tpb[1];
+        const int tpb = level_tpb(g, L.nodes, g->tpb[1]);
         LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_kernel<float, float, MODE, BT, OT>), x, b, out, E,
                L.dims(), g->K0f, omega, halt);
         return GF_OK;
@@ -377,10 +386,10 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
         RET((stencil<T, T, gf::ST_RESID>(g, l, x, b, B::r(lev), B::E(lev), k0<T>(g), omega, halt)));
         Level& c = g->lv[l + 1];
         if (l + 1 < L - 1)
-            LAUNCH(g, nblk(c.nodes), 256, gf::restrict_first_sweep_kernel<T>, (const T*)B::r(lev), B::b(c), B::x(c),
+            LAUNCH(g, nblk(c.nodes, level_tpb(g, c.nodes, 256)), level_tpb(g, c.nodes, 256), gf::restrict_first_sweep_kernel<T>, (const T*)B::r(lev), B::b(c), B::x(c),
                    (const T*)B::E(c), c.dims(), k0<T>(g), omega, halt);
         else
-            LAUNCH(g, nblk(c.nodes), 256, gf::restrict_kernel<T>, B::r(lev), B::b(c), c.dims(), halt);
+            LAUNCH(g, nblk(c.nodes, level_tpb(g, c.nodes, 256)), level_tpb(g, c.nodes, 256), gf::restrict_kernel<T>, B::r(lev), B::b(c), c.dims(), halt);
     }
     {
         Level& c = g->lv[L - 1];
@@ -446,10 +455,10 @@ int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2,
         cur[l] = x;
         Level& c = g->lv[l + 1];
         if (l + 1 < Ldown)
-            LAUNCH(g, nblk(c.nodes), 256, gf::restrict_first_sweep_kernel<float>, (const float*)lev.r32, c.b32, c.x32,
+            LAUNCH(g, nblk(c.nodes, level_tpb(g, c.nodes, 256)), level_tpb(g, c.nodes, 256), gf::restrict_first_sweep_kernel<float>, (const float*)lev.r32, c.b32, c.x32,
                    (const float*)c.E32, c.dims(), g->K0f, omega, halt);
         else
-            LAUNCH(g, nblk(c.nodes), 256, gf::restrict_kernel<float>, (const float*)lev.r32, c.b32, c.dims(), halt);
+            LAUNCH(g, nblk(c.nodes, level_tpb(g, c.nodes, 256)), level_tpb(g, c.nodes, 256), gf::restrict_kernel<float>, (const float*)lev.r32, c.b32, c.dims(), halt);
     }
     if (lc > 0) {
         gf::VcArgs va{};
@@ -583,7 +592,7 @@ int vcycle_cheb(gf_grid* g, const double* v, double* z, int nu1, int nu2, const 
         cur[l] = x;
         RET((stencil<T, T, gf::ST_RESID>(g, l, x, b, B::r(lev), B::E(lev), k0<T>(g), T(0), halt)));
         Level& c = g->lv[l + 1];
-        LAUNCH(g, nblk(c.nodes), 256, gf::restrict_kernel<T>, B::r(lev), B::b(c), c.dims(), halt);
+        LAUNCH(g, nblk(c.nodes, level_tpb(g, c.nodes, 256)), level_tpb(g, c.nodes, 256), gf::restrict_kernel<T>, B::r(lev), B::b(c), c.dims(), halt);
     }
     {
         Level& c = g->lv[L - 1];
@@ -595,7 +604,7 @@ int vcycle_cheb(gf_grid* g, const double* v, double* z, int nu1, int nu2, const 
         const T* b = (l == 0) ? b0 : B::b(lev);
         T* x = cur[l];
         T* t = (x == B::x(lev)) ? B::t(lev) : B::x(lev);
-        LAUNCH(g, nblk(lev.nodes), 256, (gf::prolong_add_kernel<T, T>), x, cur[l + 1], lev.dims(), halt);
+        LAUNCH(g, nblk(lev.nodes, level_tpb(g, lev.nodes, 256)), level_tpb(g, lev.nodes, 256), (gf::prolong_add_kernel<T, T>), x, cur[l + 1], lev.dims(), halt);
         RET(smooth(l, b, x, t, nu2, false));
         cur[l] = x;
     }
@@ -673,7 +682,7 @@ int vcycle_galerkin(gf_grid* g, const double* v, double* z, int nu1, int nu2, T 
         }
         cur[l] = x;
         Level& c = g->lv[l + 1];
-        LAUNCH(g, nblk(c.nodes), 256, gf::restrict_kernel<T>, (const T*)B::r(lev), B::b(c), c.dims(), halt);
+        LAUNCH(g, nblk(c.nodes, level_tpb(g, c.nodes, 256)), level_tpb(g, c.nodes, 256), gf::restrict_kernel<T>, (const T*)B::r(lev), B::b(c), c.dims(), halt);
     }
     {
         Level& c = g->lv[L - 1];
@@ -884,11 +893,11 @@ int coarse_correct(gf_grid* g, int l, T* x, const T* xc, T* c, const T* r, doubl
 {
     Level& lev = g->lv[l];
     if (!(theta > 0.0)) {
-        LAUNCH(g, nblk(lev.nodes), 256, (gf::prolong_add_kernel<T, T>), x, xc, lev.dims(), halt);
+        LAUNCH(g, nblk(lev.nodes, level_tpb(g, lev.nodes, 256)), level_tpb(g, lev.nodes, 256), (gf::prolong_add_kernel<T, T>), x, xc, lev.dims(), halt);
         return GF_OK;
     }
     CK(cudaMemsetAsync(c, 0, sizeof(T) * lev.ndof, g->cur_stream));
-    LAUNCH(g, nblk(lev.nodes), 256, (gf::prolong_add_kernel<T, T>), c, xc, lev.dims(), halt);
+    LAUNCH(g, nblk(lev.nodes, level_tpb(g, lev.nodes, 256)), level_tpb(g, lev.nodes, 256), (gf::prolong_add_kernel<T, T>), c, xc, lev.dims(), halt);
     RET((stencil<T, T, gf::ST_APPLY>(g, l, (const T*)c, (const T*)nullptr, LvBuf<T>::q(lev), LvBuf<T>::E(lev),
                                      k0<T>(g), T(0), halt)));
     const int nb = (int)std::min<long long>(g->ls_nb, std::max<long long>(1, (lev.ndof + 1023) / 1024));
@@ -1648,6 +1657,11 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
             }
     {   // paired FMAs in the FP32 node stencil (default; GF_F32X2=0 selects the scalar kernel):
         // 14.6 -> 12.5 us per fine-level launch at 96x48x48, 76.1 -> 67.9 us at 192x96x96
+        // 128-thread blocks on levels below two 256-thread blocks per SM (GF_COARSE_TPB=0:
+        // 256 as before, or 32/64): 96x48x48 V-cycle 191.6 -> 184-189 us, bit-identical
+        const char* ct = getenv("GF_COARSE_TPB");
+        if (ct) g->ctpb = atoi(ct);
+        if (g->ctpb != 0 && g->ctpb != 32 && g->ctpb != 64 && g->ctpb != 128) g->ctpb = 128;
         const char* e = getenv("GF_F32X2");
         g->f32x2 = !(e && e[0] == '0');
     }
