@@ -17,6 +17,7 @@
 #include "linesearch.cuh"
 #include "finecorr.cuh"
 #include "galerkin.cuh"
+#include "coarse_krylov.cuh"
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -133,6 +134,7 @@ struct gf_grid {
     gf::K0Pair K0p;                   // K0f with rows 3a, 3a+1 paired (node_stencil_f32x2_kernel)
     bool f32x2 = true;                // FP32 node stencil with paired FMAs (GF_F32X2=0: scalar FMAs)
     int ctpb = 128;                   // block size for levels too small to fill the SMs (0: as level 0)
+    bool ck_fused = true;             // coarse-level Krylov solve in one CTA (GF_COARSE_FUSED=0: multi-launch)
     int coarse_kind = GF_COARSE_REDISCRETISED;   // gf_set_coarse_operator; applied by gf_set_floor
     double* galG = nullptr;           // G_c = T_c^T K0 T_c, 8 x 576 (Galerkin first coarse level)
     double* gal_s[2] = {nullptr, nullptr};   // FP64 scratch for the BF16-moduli chain
@@ -840,8 +842,15 @@ template <typename T>
 int coarsest_solve(gf_grid* g, const T* b, T* x, const int* halt)
 {
     if (g->coarse_steps > 0 && g->L > 1) {
-        const Level& c = g->lv[g->L - 1];
+        Level& c = g->lv[g->L - 1];
         CK(cudaMemsetAsync(x, 0, sizeof(T) * c.ndof, g->cur_stream));
+        const size_t smem = sizeof(T) * (size_t)(2 * g->coarse_steps + 1) * (size_t)c.ndof;
+        if (g->ck_fused && g->coarse_kind != GF_COARSE_GALERKIN && smem <= (size_t)gf::CK_SMEM_MAX) {
+            // one CTA, basis in shared memory (csrc/coarse_krylov.cuh)
+            LAUNCH_SMEM(g, 1, gf::CK_THREADS, smem, gf::coarse_fgmres_kernel<T>, b, x, (const T*)LvBuf<T>::E(c),
+                        c.dims(), k0<T>(g), g->coarse_steps, halt);
+            return GF_OK;
+        }
         const int nb = (int)std::min<long long>(g->fc_nb, std::max<long long>(1, (c.ndof + 1023) / 1024));
         return inner_fgmres<T>(g, g->L - 1, b, x, g->coarse_steps, halt, nb);
     }
@@ -1659,6 +1668,8 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         // 14.6 -> 12.5 us per fine-level launch at 96x48x48, 76.1 -> 67.9 us at 192x96x96
         // 128-thread blocks on levels below two 256-thread blocks per SM (GF_COARSE_TPB=0:
         // 256 as before, or 32/64): 96x48x48 V-cycle 191.6 -> 184-189 us, bit-identical
+        const char* cf = getenv("GF_COARSE_FUSED");
+        g->ck_fused = !(cf && cf[0] == '0');
         const char* ct = getenv("GF_COARSE_TPB");
         if (ct) g->ctpb = atoi(ct);
         if (g->ctpb != 0 && g->ctpb != 32 && g->ctpb != 64 && g->ctpb != 128) g->ctpb = 128;
@@ -1702,6 +1713,11 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     } else {
         g->split_tc = false;
     }
+    if (cudaFuncSetAttribute(gf::coarse_fgmres_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             gf::CK_SMEM_MAX) != cudaSuccess ||
+        cudaFuncSetAttribute(gf::coarse_fgmres_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             gf::CK_SMEM_MAX) != cudaSuccess)
+        return fail(set_err(GF_ERR_CUDA, "shared-memory size of the coarse-level Krylov kernel"));
     for (int l = 0; l < levels; ++l) {
         Level L;
         L.nx = nx >> l; L.ny = ny >> l; L.nz = nz >> l;

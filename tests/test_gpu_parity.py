@@ -528,6 +528,23 @@ def test_vcycle_coarse_krylov_mixed_parity(gf):
     assert relerr(host(z), O.vcycle(H, v)) <= 1e-3
 
 
+@pytest.mark.parametrize("nx,ny,nz,L", [(16, 8, 8, 3), (32, 16, 16, 4), (24, 10, 6, 2)])
+def test_coarse_krylov_one_cta_matches_multi_launch(gf, nx, ny, nz, L, monkeypatch):
+    # the default one-CTA coarse solve (coarse_fgmres_kernel) against the multi-launch
+    # inner solve (GF_COARSE_FUSED=0): the same steps, sums in another order
+    for prec, tol in ((gf.GF_FP64, 1e-11), (gf.GF_MIXED, 1e-4)):
+        zs = []
+        for fused in ("1", "0"):
+            monkeypatch.setenv("GF_COARSE_FUSED", fused)
+            g, m, rho = make(gf, nx, ny, nz, L, seed=3, rho_min=1e-3, kind="bernoulli")
+            v = np.where(m.fixed, 0, synth.random_vector(m.n_dof, 9))
+            z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+            g.vcycle(dev(v), z, prec, coarse_steps=10)
+            zs.append(host(z))
+            g.close()
+        assert relerr(zs[0], zs[1]) <= tol
+
+
 @pytest.mark.parametrize("kind,rho_min", [("bernoulli", 1e-3), ("gauss", 1e-6)])
 def test_solve_coarse_krylov_fp64_parity(gf, kind, rho_min):
     nx, ny, nz, L = 16, 8, 8, 3
