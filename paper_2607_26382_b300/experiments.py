@@ -55,7 +55,8 @@ false_accept: the projected-versus-true stopping mismatch of Sec. 4.1.1 on regen
   converged flag with eta > tau), then Algorithm 1 with Eq. (trigger) and the ladder
   {1e-3, 1e-2}. Forms: FP64 with the fixed V-cycle (the paper's fixed-preconditioner
   control), FP64 with the adaptive preconditioner (line search 0.1, fine correction 20),
-  and the mixed V-cycle with the split-integer Krylov operator and FP64 CGS2 (outer 1).
+  the mixed V-cycle with the split-integer Krylov operator and FP64 CGS2 (outer 1), and
+  FP64 with all three adaptive components (plus the coarse Krylov solve, 10 steps).
 galerkin: rediscretised against Galerkin coarse operators (gf_set_coarse_operator) on
   the four 96x48x48 bench states at rho_min 1e-6 and 1e-3, 5 levels, FGMRES(30) to
   1e-6: steps, time per step and per V-cycle, mixed (outer 2) and FP64; plus the
@@ -425,7 +426,11 @@ def false_accept(args):
     forms = (("FP64, fixed V-cycle", dict(prec=L.GF_FP64, outer=0)),
              ("FP64, adaptive (line search 0.1, fine correction 20)",
               dict(prec=L.GF_FP64, outer=0, ls_ratio=0.1, fine_steps=20)),
-             ("mixed V-cycle, split-integer K*u, FP64 CGS2", dict(prec=L.GF_MIXED, outer=1)))
+             ("mixed V-cycle, split-integer K*u, FP64 CGS2", dict(prec=L.GF_MIXED, outer=1)),
+             ("FP64, adaptive (line search 0.1, fine correction 20, coarse Krylov 10)",
+              dict(prec=L.GF_FP64, outer=0, ls_ratio=0.1, fine_steps=20, coarse_steps=10)))
+    if args.forms:
+        forms = tuple(forms[int(i)] for i in args.forms.split(","))
     g = L.create_grid(nx, ny, nz, levels=levels)
     f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
     g.cantilever_load(f)
@@ -445,7 +450,8 @@ def false_accept(args):
             pol = L.policy_defaults(rho0=rho0, ladder=ladder, tau=tau, kmax=kmax, probe_iters=100,
                                     selector=L.GF_SEL_RULE, solve_restart=kmax, solve_prec=kw["prec"],
                                     solve_outer=kw["outer"], solve_ls_ratio=kw.get("ls_ratio", 0.0),
-                                    solve_fine_steps=kw.get("fine_steps", 0))
+                                    solve_fine_steps=kw.get("fine_steps", 0),
+                                    solve_coarse_steps=kw.get("coarse_steps", 0))
             u.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -562,6 +568,7 @@ def main(argv=None):
                                      "false_accept", "galerkin", "coarse_krylov"])
     ap.add_argument("--train", type=int, default=2000)
     ap.add_argument("--iters", type=int, default=40)
+    ap.add_argument("--forms", default="", help="false_accept: comma-separated form indices (default: all)")
     a = ap.parse_args(argv)
     res = {"batch102": batch102, "oc_loop": oc_loop, "oc_reuse": oc_reuse, "true_checks": true_checks,
            "conditioning": conditioning, "adaptive": adaptive, "false_accept": false_accept,
