@@ -81,8 +81,8 @@ typedef struct gf_grid gf_grid;
 typedef struct gf_mlp gf_mlp;
 
 typedef struct {
-    int    restart;    /* FGMRES restart length m, in [1, 300]; at most 32 in batched solves. Past 32
-                          basis vectors the CGS2 passes run over slices of 32 vectors. */
+    int    restart;    /* FGMRES restart length m, in [1, 300]. Past 32 basis vectors the CGS2 passes
+                          run over slices of 32 vectors. */
     int    kmax;       /* iteration budget (Arnoldi steps over all cycles) */
     double tol;        /* stop when the recorded relative residual <= tol */
     int    prec;       /* GF_FP64 or GF_MIXED */

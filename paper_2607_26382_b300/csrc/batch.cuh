@@ -89,10 +89,10 @@ struct gf_batch {
     std::vector<cudaEvent_t> evJoin;
     cudaEvent_t ev[3] = {};
     // graphs over all states
-    cudaGraphExec_t step[gf::KRY_NV] = {};
+    cudaGraphExec_t step[gf::KRY_MMAX] = {};
     cudaGraphExec_t start[2] = {};
     cudaGraphExec_t end = nullptr;
-    long long nodes_step[gf::KRY_NV] = {}, nodes_start[2] = {}, nodes_end = 0;
+    long long nodes_step[gf::KRY_MMAX] = {}, nodes_start[2] = {}, nodes_end = 0;
     int key_prec = -1, key_nu1 = -1, key_nu2 = -1, key_m = -1, key_outer = -1, key_smoother = -1;
     double key_omega = -1.0;
     void* key_ptrs = nullptr;   // V of state 0 when captured (realloc invalidates)
@@ -110,7 +110,7 @@ namespace {
 
 void batch_drop_graphs(gf_batch* b)
 {
-    for (int j = 0; j < gf::KRY_NV; ++j) {
+    for (int j = 0; j < gf::KRY_MMAX; ++j) {
         if (b->step[j]) cudaGraphExecDestroy(b->step[j]);
         b->step[j] = nullptr;
     }
@@ -590,7 +590,6 @@ int gf_batch_select_floor(gf_batch* b, const gf_policy* pol, gf_select_info* inf
     if (pol->solve.ls_ratio != 0.0) return set_err(GF_ERR_ARG, "ls_ratio is single-grid only");
     if (pol->solve.fine_steps != 0) return set_err(GF_ERR_ARG, "fine_steps is single-grid only");
     if (pol->solve.coarse_steps != 0) return set_err(GF_ERR_ARG, "coarse_steps is single-grid only");
-    if (pol->solve.restart > gf::KRY_NV) return set_err(GF_ERR_ARG, "batched restart must be in [1, 32]");
     const int B = b->B;
     for (int i = 0; i < B; ++i)
         if (!b->g[i]->has_density) return set_err(GF_ERR_STATE, "state " + std::to_string(i) + " has no density");

@@ -2,6 +2,7 @@
 
     python -m paper_2607_26382_b300.profile apply_k64 --grid 96 48 48 --levels 5 --reps 3
     ops: apply_k64, apply_split, apply_k32, vcycle_mixed, vcycle_fp64, solve_mixed, select_mixed
+    (--galerkin: the V-cycles on Galerkin coarse operators)
 
 The state is the smoothed-Gaussian density (sigma 2, 40% at floor) at rho_min 1e-6,
 p = 3, with the cantilever tip load. Used as the command under ncu so that a
@@ -25,6 +26,7 @@ def main(argv=None):
                     help="Krylov arithmetic: 0 native FP64, 1 split-integer K*u, 2 split K*u + double-float CGS2")
     ap.add_argument("--kmax", type=int, default=200, help="iteration budget of solve_mixed")
     ap.add_argument("--fine", type=int, default=0, help="fine-level adaptive correction steps (solve_mixed)")
+    ap.add_argument("--galerkin", action="store_true", help="Galerkin coarse operators (gf_set_coarse_operator)")
     a = ap.parse_args(argv)
 
     import torch
@@ -35,6 +37,8 @@ def main(argv=None):
     nx, ny, nz = a.grid
     g = gf.create_grid(nx, ny, nz, levels=a.levels)
     g.set_density(torch.as_tensor(synth.smoothed_gaussian_density(nx, ny, nz, a.seed), device="cuda"), 3.0)
+    if a.galerkin:
+        g.set_coarse_operator(gf.GF_COARSE_GALERKIN)
     g.set_floor(1e-6)
     gen = torch.Generator(device="cuda").manual_seed(a.seed)
     x = torch.randn(g.n_dof, dtype=torch.float64, device="cuda", generator=gen)

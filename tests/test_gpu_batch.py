@@ -34,13 +34,15 @@ def _rho(dims, kind, seed, q):
     return synth.smoothed_gaussian_density(nx, ny, nz, seed, 2.0, q)
 
 
-@pytest.mark.parametrize("selector,prec,outer,smoother", [("rule", 0, 0, 0), ("full", 1, 0, 0), ("rule", 1, 2, 0),
-                                                          ("rule", 1, 2, 1)])
-def test_batch_matches_single_state(gf, selector, prec, outer, smoother):
+# restart 45: past 32 basis vectors the Gram-Schmidt passes run over 32-vector slices
+@pytest.mark.parametrize("selector,prec,outer,smoother,restart", [("rule", 0, 0, 0, 30), ("full", 1, 0, 0, 30),
+                                                                  ("rule", 1, 2, 0, 30), ("rule", 1, 2, 1, 30),
+                                                                  ("rule", 1, 2, 0, 45), ("full", 0, 0, 0, 45)])
+def test_batch_matches_single_state(gf, selector, prec, outer, smoother, restart):
     L = 3
     sel = gf.GF_SEL_RULE if selector == "rule" else gf.GF_SEL_FULL
     pol = gf.policy_defaults(rho0=1e-8, ladder=[1e-5, 1e-4, 1e-3], kmax=120, selector=sel, solve_prec=prec,
-                             solve_outer=outer, solve_smoother=smoother)
+                             solve_outer=outer, solve_smoother=smoother, solve_restart=restart)
     batch = gf.Batch([s[0] for s in STATES], levels=L)
     tuned = batch.autotune()
     assert all(t[0] in (64, 128, 256) and t[1] in (0, 64, 128, 256, -64, -128, -256) for t in tuned)
@@ -82,13 +84,13 @@ def test_batch_matches_single_state(gf, selector, prec, outer, smoother):
 
 def test_batch_rejects_single_grid_options(gf):
     """The reuse selector, true-residual checks, the line-searched coarse correction, the
-    fine-level correction, restarts above 32 and the coarse-level Krylov solve are single-grid
-    options; the batch refuses them."""
+    fine-level correction and the coarse-level Krylov solve are single-grid options; the batch
+    refuses them."""
     dims, kind, seed, q = STATES[0]
     batch = gf.Batch([dims], levels=3)
     batch.set_state(0, dev(_rho(dims, kind, seed, q)), dev(O.cantilever_load(O.Mesh(*dims))), 3.0)
     for kw in (dict(selector=gf.GF_SEL_REUSE), dict(true_check_every=10), dict(solve_ls_ratio=0.1),
-               dict(solve_fine_steps=5), dict(solve_restart=33), dict(solve_coarse_steps=10)):
+               dict(solve_fine_steps=5), dict(solve_coarse_steps=10)):
         with pytest.raises(gf.GFError):
             batch.select_floor(gf.policy_defaults(**kw))
     assert batch.select_floor(gf.policy_defaults())[0]["status"] in (gf.GF_ACCEPTED, gf.GF_NO_ADMISSIBLE_FLOOR)
