@@ -72,6 +72,7 @@ def test_policy_defaults(gflib):
     assert (p.r50_escalate, p.r100_stall, p.plateau_ratio) == (1e-2, 1e-4, 0.6)
     assert (p.solve.restart, p.solve.nu1, p.solve.nu2, p.solve.omega) == (30, 2, 2, 0.6)
     assert (p.true_check_every, p.true_check_ratio) == (0, 10.0)    # the struct's last fields line up
+    assert (p.solve.ls_ratio, p.solve.fine_steps, p.solve.coarse_steps) == (0.0, 0, 0)   # adaptive parts off
     p2 = gflib.policy_defaults(ladder=[1e-3, 1e-2], rho0=1e-12, solve_prec=gflib.GF_MIXED)
     assert p2.n_ladder == 2 and p2.rho0 == 1e-12 and p2.solve.prec == gflib.GF_MIXED
 
