@@ -13,6 +13,7 @@
 // The matrices are kept unmasked; the kernels read fixed nodes as 0 and write them as 0.
 #pragma once
 #include <cuda_runtime.h>
+#include <type_traits>
 
 namespace gf {
 
@@ -133,21 +134,43 @@ gal_node_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __restric
         const int a = local_index(1 - ox, 1 - oy, 1 - oz);
         const T* Kr = Ke + (ex + (long long)d.nx * (ey + (long long)d.ny * ez)) * GAL_KE + 3 * a * 24;
         if (MODE != GAL_FIRST) {
+            T u[24];   // the element's node values, local node order (fixed nodes read as 0)
 #pragma unroll
             for (int bl = 0; bl < 8; ++bl) {
                 int bx, by, bz;
                 local_xyz(bl, bx, by, bz);
-                T u0 = 0, u1 = 0, u2 = 0;
-                if (ex + bx != 0) {   // fixed node: reads as 0
-                    const long long m = (ex + bx) + (long long)NX * ((ey + by) + (long long)NY * (ez + bz));
-                    u0 = x[3 * m + 0];
-                    u1 = x[3 * m + 1];
-                    u2 = x[3 * m + 2];
-                }
-                a0 = fma(Kr[3 * bl + 0], u0, fma(Kr[3 * bl + 1], u1, fma(Kr[3 * bl + 2], u2, a0)));
-                a1 = fma(Kr[24 + 3 * bl + 0], u0, fma(Kr[24 + 3 * bl + 1], u1, fma(Kr[24 + 3 * bl + 2], u2, a1)));
-                a2 = fma(Kr[48 + 3 * bl + 0], u0, fma(Kr[48 + 3 * bl + 1], u1, fma(Kr[48 + 3 * bl + 2], u2, a2)));
+                const bool fixed = ex + bx == 0;
+                const long long m = (ex + bx) + (long long)NX * ((ey + by) + (long long)NY * (ez + bz));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) u[3 * bl + c] = fixed ? T(0) : x[3 * m + c];
             }
+            // rows 3a..3a+2 as 16-byte vectors: the element's 576 values start on a 16-byte
+            // boundary (cudaMalloc base), and 72 a and 24 r values are multiples of 16 bytes
+            using V = typename std::conditional<sizeof(T) == sizeof(float), float4, double2>::type;
+            constexpr int PER = (int)(sizeof(V) / sizeof(T));
+            T acc[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const V* row = reinterpret_cast<const V*>(Kr + 24 * r);
+                T s = 0;
+#pragma unroll
+                for (int q = 0; q < 24 / PER; ++q) {
+                    const V kv = row[q];
+                    if constexpr (PER == 4) {
+                        s = fma(kv.x, u[4 * q + 0], s);
+                        s = fma(kv.y, u[4 * q + 1], s);
+                        s = fma(kv.z, u[4 * q + 2], s);
+                        s = fma(kv.w, u[4 * q + 3], s);
+                    } else {
+                        s = fma(kv.x, u[2 * q + 0], s);
+                        s = fma(kv.y, u[2 * q + 1], s);
+                    }
+                }
+                acc[r] = s;
+            }
+            a0 = acc[0];
+            a1 = acc[1];
+            a2 = acc[2];
         }
         if (MODE == ST_SWEEP || MODE == GAL_FIRST) {
             d00 = Kr[3 * a + 0];
