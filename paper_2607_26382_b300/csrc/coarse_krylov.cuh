@@ -7,11 +7,11 @@
 //
 // The basis V and the preconditioned vectors Z, (2k + 1) n values, live in the CTA's
 // shared memory (the caller uses this kernel only when they fit; a single SM waiting on
-// L2 round trips was latency-bound). Dots: warp q
-// takes basis vector q (lanes over rows, then a fixed shuffle tree), accumulated in the
-// vectors' precision per lane (as in finecorr.cuh) and stored in FP64. Stop rules are
-// the inner solve's: a zero rotated pivot drops the step, h_{j+1,j} <= 1e-14 ||K z_j||
-// or a zero projected residual ends the solve.
+// L2 round trips was latency-bound). Dots: warp q takes basis vector q (lanes over rows,
+// then a fixed shuffle tree), accumulated in the vectors' precision per lane (as in
+// finecorr.cuh) and stored in FP64. Stop rules are the inner solve's: a zero rotated
+// pivot drops the step, h_{j+1,j} <= 1e-14 ||K z_j|| or a zero projected residual ends
+// the solve.
 #pragma once
 #include <cuda_runtime.h>
 
