@@ -244,6 +244,10 @@ int level_tpb(const gf_grid* g, long long nodes, int base)
     return (g->ctpb > 0 && nodes < 512LL * g->sms) ? g->ctpb : base;
 }
 
+// grid and block of a node-per-thread launch over `nodes` nodes (256 threads, or ctpb)
+dim3 lv_grid(const gf_grid* g, long long nodes) { return dim3(nblk(nodes, level_tpb(g, nodes, 256))); }
+dim3 lv_block(const gf_grid* g, long long nodes) { return dim3(level_tpb(g, nodes, 256)); }
+
 int check_grid(const gf_grid* g)
 {
     if (!g) return set_err(GF_ERR_ARG, "null grid");
@@ -388,10 +392,12 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
         RET((stencil<T, T, gf::ST_RESID>(g, l, x, b, B::r(lev), B::E(lev), k0<T>(g), omega, halt)));
         Level& c = g->lv[l + 1];
         if (l + 1 < L - 1)
-            LAUNCH(g, nblk(c.nodes, level_tpb(g, c.nodes, 256)), level_tpb(g, c.nodes, 256), gf::restrict_first_sweep_kernel<T>, (const T*)B::r(lev), B::b(c), B::x(c),
+            LAUNCH(g, lv_grid(g, c.nodes), lv_block(g, c.nodes), gf::restrict_first_sweep_kernel<T>,
+                   (const T*)B::r(lev), B::b(c), B::x(c),
                    (const T*)B::E(c), c.dims(), k0<T>(g), omega, halt);
         else
-            LAUNCH(g, nblk(c.nodes, level_tpb(g, c.nodes, 256)), level_tpb(g, c.nodes, 256), gf::restrict_kernel<T>, B::r(lev), B::b(c), c.dims(), halt);
+            LAUNCH(g, lv_grid(g, c.nodes), lv_block(g, c.nodes), gf::restrict_kernel<T>,
+                   B::r(lev), B::b(c), c.dims(), halt);
     }
     {
         Level& c = g->lv[L - 1];
@@ -457,10 +463,12 @@ int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2,
         cur[l] = x;
         Level& c = g->lv[l + 1];
         if (l + 1 < Ldown)
-            LAUNCH(g, nblk(c.nodes, level_tpb(g, c.nodes, 256)), level_tpb(g, c.nodes, 256), gf::restrict_first_sweep_kernel<float>, (const float*)lev.r32, c.b32, c.x32,
+            LAUNCH(g, lv_grid(g, c.nodes), lv_block(g, c.nodes), gf::restrict_first_sweep_kernel<float>,
+                   (const float*)lev.r32, c.b32, c.x32,
                    (const float*)c.E32, c.dims(), g->K0f, omega, halt);
         else
-            LAUNCH(g, nblk(c.nodes, level_tpb(g, c.nodes, 256)), level_tpb(g, c.nodes, 256), gf::restrict_kernel<float>, (const float*)lev.r32, c.b32, c.dims(), halt);
+            LAUNCH(g, lv_grid(g, c.nodes), lv_block(g, c.nodes), gf::restrict_kernel<float>,
+                   (const float*)lev.r32, c.b32, c.dims(), halt);
     }
     if (lc > 0) {
         gf::VcArgs va{};
@@ -594,7 +602,8 @@ int vcycle_cheb(gf_grid* g, const double* v, double* z, int nu1, int nu2, const 
         cur[l] = x;
         RET((stencil<T, T, gf::ST_RESID>(g, l, x, b, B::r(lev), B::E(lev), k0<T>(g), T(0), halt)));
         Level& c = g->lv[l + 1];
-        LAUNCH(g, nblk(c.nodes, level_tpb(g, c.nodes, 256)), level_tpb(g, c.nodes, 256), gf::restrict_kernel<T>, B::r(lev), B::b(c), c.dims(), halt);
+        LAUNCH(g, lv_grid(g, c.nodes), lv_block(g, c.nodes), gf::restrict_kernel<T>,
+               B::r(lev), B::b(c), c.dims(), halt);
     }
     {
         Level& c = g->lv[L - 1];
@@ -606,7 +615,8 @@ int vcycle_cheb(gf_grid* g, const double* v, double* z, int nu1, int nu2, const 
         const T* b = (l == 0) ? b0 : B::b(lev);
         T* x = cur[l];
         T* t = (x == B::x(lev)) ? B::t(lev) : B::x(lev);
-        LAUNCH(g, nblk(lev.nodes, level_tpb(g, lev.nodes, 256)), level_tpb(g, lev.nodes, 256), (gf::prolong_add_kernel<T, T>), x, cur[l + 1], lev.dims(), halt);
+        LAUNCH(g, lv_grid(g, lev.nodes), lv_block(g, lev.nodes), (gf::prolong_add_kernel<T, T>), x, cur[l + 1],
+               lev.dims(), halt);
         RET(smooth(l, b, x, t, nu2, false));
         cur[l] = x;
     }
@@ -645,7 +655,8 @@ int gal_level(gf_grid* g, int l, const T* x, const T* b, T* out, T omega, const 
 // nu2 sweeps). Level 0 keeps the matrix-free stencils; the coarsest solve uses the
 // dense inverse of the assembled Galerkin matrix.
 template <typename T>
-int vcycle_galerkin(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omega, const int* halt)
+int vcycle_galerkin(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omega, const int* halt,
+                    double ls = 0.0)
 {
     using B = LvBuf<T>;
     const int L = g->L;
@@ -684,7 +695,8 @@ int vcycle_galerkin(gf_grid* g, const double* v, double* z, int nu1, int nu2, T 
         }
         cur[l] = x;
         Level& c = g->lv[l + 1];
-        LAUNCH(g, nblk(c.nodes, level_tpb(g, c.nodes, 256)), level_tpb(g, c.nodes, 256), gf::restrict_kernel<T>, (const T*)B::r(lev), B::b(c), c.dims(), halt);
+        LAUNCH(g, lv_grid(g, c.nodes), lv_block(g, c.nodes), gf::restrict_kernel<T>,
+               (const T*)B::r(lev), B::b(c), c.dims(), halt);
     }
     {
         Level& c = g->lv[L - 1];
@@ -696,7 +708,7 @@ int vcycle_galerkin(gf_grid* g, const double* v, double* z, int nu1, int nu2, T 
         const T* b = (l == 0) ? b0 : B::b(lev);
         T* x = cur[l];
         T* t = (x == B::x(lev)) ? B::t(lev) : B::x(lev);
-        RET(coarse_correct<T>(g, l, x, cur[l + 1], t, B::r(lev), 0.0, halt));
+        RET(coarse_correct<T>(g, l, x, cur[l + 1], t, B::r(lev), ls, halt));
         for (int s = 0; s < nu2; ++s) {
             T* out = t;
             const bool last = (l == 0 && s == nu2 - 1);
@@ -737,10 +749,9 @@ int vcycle_dispatch_plain(gf_grid* g, const double* v, double* z, int prec, int 
         return set_err(GF_ERR_ARG, "the line-searched coarse correction needs Jacobi smoothing, >= 2 levels and no "
                                    "cluster V-cycle");
     if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1) {
-        if (smoother != 0 || ls > 0.0)
-            return set_err(GF_ERR_ARG, "Galerkin coarse operators take Jacobi smoothing without the line search");
-        if (prec == GF_MIXED) return vcycle_galerkin<float>(g, v, z, nu1, nu2, (float)omega, halt);
-        return vcycle_galerkin<double>(g, v, z, nu1, nu2, omega, halt);
+        if (smoother != 0) return set_err(GF_ERR_ARG, "Galerkin coarse operators take Jacobi smoothing");
+        if (prec == GF_MIXED) return vcycle_galerkin<float>(g, v, z, nu1, nu2, (float)omega, halt, ls);
+        return vcycle_galerkin<double>(g, v, z, nu1, nu2, omega, halt, ls);
     }
     if (smoother == 1) {
         if (!g->cheb_ready[prec == GF_FP64 ? 0 : 1]) return set_err(GF_ERR_STATE, "Chebyshev bounds not set up");
@@ -901,14 +912,18 @@ template <typename T>
 int coarse_correct(gf_grid* g, int l, T* x, const T* xc, T* c, const T* r, double theta, const int* halt)
 {
     Level& lev = g->lv[l];
+    const int tpb = level_tpb(g, lev.nodes, 256);
     if (!(theta > 0.0)) {
-        LAUNCH(g, nblk(lev.nodes, level_tpb(g, lev.nodes, 256)), level_tpb(g, lev.nodes, 256), (gf::prolong_add_kernel<T, T>), x, xc, lev.dims(), halt);
+        LAUNCH(g, nblk(lev.nodes, tpb), tpb, (gf::prolong_add_kernel<T, T>), x, xc, lev.dims(), halt);
         return GF_OK;
     }
     CK(cudaMemsetAsync(c, 0, sizeof(T) * lev.ndof, g->cur_stream));
-    LAUNCH(g, nblk(lev.nodes, level_tpb(g, lev.nodes, 256)), level_tpb(g, lev.nodes, 256), (gf::prolong_add_kernel<T, T>), c, xc, lev.dims(), halt);
-    RET((stencil<T, T, gf::ST_APPLY>(g, l, (const T*)c, (const T*)nullptr, LvBuf<T>::q(lev), LvBuf<T>::E(lev),
-                                     k0<T>(g), T(0), halt)));
+    LAUNCH(g, nblk(lev.nodes, tpb), tpb, (gf::prolong_add_kernel<T, T>), c, xc, lev.dims(), halt);
+    if (l > 0 && g->coarse_kind == GF_COARSE_GALERKIN)   // q = K_l c with the level's Galerkin operator
+        RET((gal_level<T, gf::ST_APPLY>(g, l, (const T*)c, (const T*)nullptr, LvBuf<T>::q(lev), T(0), halt)));
+    else
+        RET((stencil<T, T, gf::ST_APPLY>(g, l, (const T*)c, (const T*)nullptr, LvBuf<T>::q(lev), LvBuf<T>::E(lev),
+                                         k0<T>(g), T(0), halt)));
     const int nb = (int)std::min<long long>(g->ls_nb, std::max<long long>(1, (lev.ndof + 1023) / 1024));
     LAUNCH(g, nb, gf::LS_THREADS, gf::ls_dots_kernel<T>, (const T*)c, r, (const T*)LvBuf<T>::q(lev), lev.ndof,
            g->ls_partial, halt);
@@ -1450,8 +1465,8 @@ int validate_opts(const gf_solve_opts* o)
 int validate_grid_opts(const gf_grid* g, const gf_solve_opts* o)
 {
     RET(validate_opts(o));
-    if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1 && (o->smoother != 0 || o->ls_ratio > 0.0))
-        return set_err(GF_ERR_ARG, "Galerkin coarse operators take Jacobi smoothing without the line search");
+    if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1 && o->smoother != 0)
+        return set_err(GF_ERR_ARG, "Galerkin coarse operators take Jacobi smoothing");
     return GF_OK;
 }
 
