@@ -232,9 +232,10 @@ int gf_set_floor(gf_grid* g, double rho_min);
  *   solver-config), held as one dense 24x24 matrix per coarse element and summed from
  *   the 8 children's matrices; node-block Jacobi smoothing on it and the dense inverse of
  *   the assembled coarsest level. FP64 matrices from the FP64 moduli, and FP32 ones (the
- *   mixed V-cycle) from the BF16-density moduli. Takes Jacobi smoothing (Chebyshev
- *   returns GF_ERR_ARG); the line-searched coarse correction and the coarse-level Krylov
- *   solve apply the assembled operators; the batch keeps the default.
+ *   mixed V-cycle) from the BF16-density moduli. Jacobi and Chebyshev smoothing (its
+ *   lambda_max from the assembled operators), the line-searched coarse correction and
+ *   the coarse-level Krylov solve all apply the assembled operators; the batch keeps the
+ *   default.
  * Switching clears the floor (gf_set_floor again before solving) and the captured steps.
  * Memory: 576 * (8 + 4) bytes per coarse element, plus FP64 scratch for two levels.
  * Errors: GF_ERR_ARG for an unknown kind. */

@@ -18,6 +18,7 @@
 namespace gf {
 
 constexpr int GAL_FIRST = 3;   // out = omega D_n^{-1} b: the first sweep from x = 0
+constexpr int GAL_CHEB = 4;    // Chebyshev step: d = c1 d + c2 D_n^{-1} (b - K x), out = x + d (x may be null)
 constexpr int GAL_KE = 576;    // 24 x 24 entries per element, row-major
 
 // (x, y, z) offsets of element-local node a (inverse of local_index)
@@ -116,7 +117,8 @@ __global__ void gal_coarsen_kernel(const double* __restrict__ Kf, double* __rest
 template <typename T, int MODE, typename BT, typename OT>
 __global__ void __launch_bounds__(256)
 gal_node_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __restrict__ out,
-                const T* __restrict__ Ke, GridDims d, T omega, const int* __restrict__ halt)
+                const T* __restrict__ Ke, GridDims d, T omega, const int* __restrict__ halt,
+                T* __restrict__ dv, const double* __restrict__ coef)
 {
     if (halt != nullptr && *halt != 0) return;   // uniform over the grid
     const int NX = d.nx + 1, NY = d.ny + 1;
@@ -133,7 +135,7 @@ gal_node_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __restric
     if (active && i != 0 && ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny && ez >= 0 && ez < d.nz) {
         const int a = local_index(1 - ox, 1 - oy, 1 - oz);
         const T* Kr = Ke + (ex + (long long)d.nx * (ey + (long long)d.ny * ez)) * GAL_KE + 3 * a * 24;
-        if (MODE != GAL_FIRST) {
+        if (MODE != GAL_FIRST && !(MODE == GAL_CHEB && x == nullptr)) {
             T u[24];   // the element's node values, local node order (fixed nodes read as 0)
 #pragma unroll
             for (int bl = 0; bl < 8; ++bl) {
@@ -172,7 +174,7 @@ gal_node_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __restric
             a1 = acc[1];
             a2 = acc[2];
         }
-        if (MODE == ST_SWEEP || MODE == GAL_FIRST) {
+        if (MODE == ST_SWEEP || MODE == GAL_FIRST || MODE == GAL_CHEB) {
             d00 = Kr[3 * a + 0];
             d01 = Kr[3 * a + 1];
             d02 = Kr[3 * a + 2];
@@ -186,7 +188,7 @@ gal_node_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __restric
         a0 += __shfl_xor_sync(0xffffffffu, a0, o);
         a1 += __shfl_xor_sync(0xffffffffu, a1, o);
         a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-        if (MODE == ST_SWEEP || MODE == GAL_FIRST) {
+        if (MODE == ST_SWEEP || MODE == GAL_FIRST || MODE == GAL_CHEB) {
             d00 += __shfl_xor_sync(0xffffffffu, d00, o);
             d11 += __shfl_xor_sync(0xffffffffu, d11, o);
             d22 += __shfl_xor_sync(0xffffffffu, d22, o);
@@ -200,6 +202,21 @@ gal_node_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __restric
         out[3 * n + 0] = OT(0);
         out[3 * n + 1] = OT(0);
         out[3 * n + 2] = OT(0);
+        if (MODE == GAL_CHEB) dv[3 * n + 0] = dv[3 * n + 1] = dv[3 * n + 2] = T(0);
+        return;
+    }
+    if (MODE == GAL_CHEB) {   // z = D^{-1} (b - K x), d = c1 d + c2 z, out = x + d
+        const T zero[3] = {T(0), T(0), T(0)};
+        T z[3];
+        node_block_update<T, T>(d00, d11, d22, d01, d02, d12, T(b[3 * n + 0]) - a0, T(b[3 * n + 1]) - a1,
+                                T(b[3 * n + 2]) - a2, zero, z, T(1));
+        const T c1 = (T)coef[0], c2 = (T)coef[1];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T dn = (coef[0] != 0.0) ? c1 * dv[3 * n + c] + c2 * z[c] : c2 * z[c];
+            dv[3 * n + c] = dn;
+            out[3 * n + c] = OT((x != nullptr ? x[3 * n + c] : T(0)) + dn);
+        }
         return;
     }
     if (MODE == ST_APPLY) {

@@ -340,6 +340,23 @@ struct LvBuf<float> {
     static const float* E(Level& L) { return L.E32; }
 };
 
+template <typename T>
+const T* gal_ke(const Level& L);
+template <>
+const double* gal_ke<double>(const Level& L) { return L.Ke64; }
+template <>
+const float* gal_ke<float>(const Level& L) { return L.Ke32; }
+
+// Galerkin level operator (csrc/galerkin.cuh) on level l >= 1
+template <typename T, int MODE>
+int gal_level(gf_grid* g, int l, const T* x, const T* b, T* out, T omega, const int* halt)
+{
+    const Level& L = g->lv[l];
+    LAUNCH(g, nblk(8 * L.nodes), 256, (gf::gal_node_kernel<T, MODE, T, T>), x, b, out, gal_ke<T>(L), L.dims(),
+           omega, halt, (T*)nullptr, (const double*)nullptr);
+    return GF_OK;
+}
+
 // Coarse-grid correction of level l: x += P xc, or (theta > 0) the line-searched,
 // rejectable form x += alpha P xc (csrc/linesearch.cuh); c is free scratch of the level,
 // r the level's residual before the correction.
@@ -537,9 +554,15 @@ int cheb_setup_impl(gf_grid* g)
         LAUNCH(g, nblk(n), 256, gf::cheb_ones_kernel<T>, v, n, lev.nx + 1);
         LAUNCH(g, 1, 1024, gf::cheb_sumsq_kernel<T>, (const T*)v, n, g->cheb_ss);
         LAUNCH(g, nblk(n), 256, gf::cheb_normalize_kernel<T>, (const T*)v, v, n, (const double*)g->cheb_ss);
+        const bool gal = l > 0 && g->coarse_kind == GF_COARSE_GALERKIN;
         for (int it = 0; it < gf::CHEB_POWER_ITERS; ++it) {
-            LAUNCH(g, nblk(lev.nodes), 256, (gf::dinvk_kernel<T, T>), (const T*)v, w, (const T*)B::E(lev), lev.dims(),
-                   k0<T>(g));
+            if (gal) {   // w = D^{-1} K v with the level's Galerkin operator (r as scratch)
+                RET((gal_level<T, gf::ST_APPLY>(g, l, (const T*)v, (const T*)nullptr, B::r(lev), T(0), nullptr)));
+                RET((gal_level<T, gf::GAL_FIRST>(g, l, (const T*)nullptr, (const T*)B::r(lev), w, T(1), nullptr)));
+            } else {
+                LAUNCH(g, nblk(lev.nodes), 256, (gf::dinvk_kernel<T, T>), (const T*)v, w, (const T*)B::E(lev),
+                       lev.dims(), k0<T>(g));
+            }
             LAUNCH(g, 1, 1024, gf::cheb_sumsq_kernel<T>, (const T*)w, n, g->cheb_ss);
             LAUNCH(g, nblk(n), 256, gf::cheb_normalize_kernel<T>, (const T*)w, v, n, (const double*)g->cheb_ss);
         }
@@ -586,9 +609,15 @@ int vcycle_cheb(gf_grid* g, const double* v, double* z, int nu1, int nu2, const 
     auto smooth = [&](int l, const T* b, T*& x, T*& t, int degree, bool from_zero) -> int {
         Level& lev = g->lv[l];
         const double* coef = cheb_slot(g, p, l) + 1;
+        const bool gal = l > 0 && g->coarse_kind == GF_COARSE_GALERKIN;
         for (int k = 0; k < degree; ++k) {
-            LAUNCH(g, nblk(lev.nodes), 256, (gf::cheb_step_kernel<T, T>), (from_zero && k == 0) ? (const T*)nullptr : (const T*)x,
-                   b, t, B::r(lev), (const T*)B::E(lev), lev.dims(), k0<T>(g), coef + 2 * k, halt);
+            const T* xin = (from_zero && k == 0) ? (const T*)nullptr : (const T*)x;
+            if (gal)
+                LAUNCH(g, nblk(8 * lev.nodes), 256, (gf::gal_node_kernel<T, gf::GAL_CHEB, T, T>), xin, b, t,
+                       gal_ke<T>(lev), lev.dims(), T(1), halt, B::r(lev), coef + 2 * k);
+            else
+                LAUNCH(g, nblk(lev.nodes), 256, (gf::cheb_step_kernel<T, T>), xin, b, t, B::r(lev),
+                       (const T*)B::E(lev), lev.dims(), k0<T>(g), coef + 2 * k, halt);
             std::swap(x, t);
         }
         return GF_OK;
@@ -600,7 +629,10 @@ int vcycle_cheb(gf_grid* g, const double* v, double* z, int nu1, int nu2, const 
         T* t = B::x(lev);
         RET(smooth(l, b, x, t, nu1, true));
         cur[l] = x;
-        RET((stencil<T, T, gf::ST_RESID>(g, l, x, b, B::r(lev), B::E(lev), k0<T>(g), T(0), halt)));
+        if (l > 0 && g->coarse_kind == GF_COARSE_GALERKIN)
+            RET((gal_level<T, gf::ST_RESID>(g, l, (const T*)x, b, B::r(lev), T(0), halt)));
+        else
+            RET((stencil<T, T, gf::ST_RESID>(g, l, x, b, B::r(lev), B::E(lev), k0<T>(g), T(0), halt)));
         Level& c = g->lv[l + 1];
         LAUNCH(g, lv_grid(g, c.nodes), lv_block(g, c.nodes), gf::restrict_kernel<T>,
                B::r(lev), B::b(c), c.dims(), halt);
@@ -631,23 +663,6 @@ int vcycle_dispatch_plain(gf_grid* g, const double* v, double* z, int prec, int 
                           const int* halt, int smoother, double ls);
 template <typename T>
 int fine_correct(gf_grid* g, const double* v, double* z, int steps, const int* halt);
-
-template <typename T>
-const T* gal_ke(const Level& L);
-template <>
-const double* gal_ke<double>(const Level& L) { return L.Ke64; }
-template <>
-const float* gal_ke<float>(const Level& L) { return L.Ke32; }
-
-// Galerkin level operator (csrc/galerkin.cuh) on level l >= 1
-template <typename T, int MODE>
-int gal_level(gf_grid* g, int l, const T* x, const T* b, T* out, T omega, const int* halt)
-{
-    const Level& L = g->lv[l];
-    LAUNCH(g, nblk(8 * L.nodes), 256, (gf::gal_node_kernel<T, MODE, T, T>), x, b, out, gal_ke<T>(L), L.dims(),
-           omega, halt);
-    return GF_OK;
-}
 
 // The V-cycle on the Galerkin hierarchy: vcycle_impl's schedule, with every level
 // l >= 1 smoothed, and its residual formed, by the assembled coarse operator
@@ -748,8 +763,7 @@ int vcycle_dispatch_plain(gf_grid* g, const double* v, double* z, int prec, int 
     if (ls > 0.0 && (smoother == 1 || g->vc_l0 > 0 || g->L < 2 || !g->ls_alpha))
         return set_err(GF_ERR_ARG, "the line-searched coarse correction needs Jacobi smoothing, >= 2 levels and no "
                                    "cluster V-cycle");
-    if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1) {
-        if (smoother != 0) return set_err(GF_ERR_ARG, "Galerkin coarse operators take Jacobi smoothing");
+    if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1 && smoother == 0) {   // Chebyshev: vcycle_cheb
         if (prec == GF_MIXED) return vcycle_galerkin<float>(g, v, z, nu1, nu2, (float)omega, halt, ls);
         return vcycle_galerkin<double>(g, v, z, nu1, nu2, omega, halt, ls);
     }
@@ -1465,8 +1479,7 @@ int validate_opts(const gf_solve_opts* o)
 int validate_grid_opts(const gf_grid* g, const gf_solve_opts* o)
 {
     RET(validate_opts(o));
-    if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1 && o->smoother != 0)
-        return set_err(GF_ERR_ARG, "Galerkin coarse operators take Jacobi smoothing");
+    (void)g;   // every option combines with either coarse operator
     return GF_OK;
 }
 
