@@ -1475,14 +1475,6 @@ int validate_opts(const gf_solve_opts* o)
     return GF_OK;
 }
 
-// validate_opts, plus what the grid's coarse operators allow
-int validate_grid_opts(const gf_grid* g, const gf_solve_opts* o)
-{
-    RET(validate_opts(o));
-    (void)g;   // every option combines with either coarse operator
-    return GF_OK;
-}
-
 int guard_impl(gf_grid* g, const double* f, const double* u, double* eta)
 {
     RET(applyK64(g, u, g->work, nullptr));
@@ -2000,7 +1992,7 @@ int gf_vcycle(gf_grid* g, const double* v, double* z, int prec, int nu1, int nu2
 int gf_vcycle_ex(gf_grid* g, const double* v, double* z, const gf_solve_opts* o)
 {
     RET(check_grid(g));
-    RET(validate_grid_opts(g, o));
+    RET(validate_opts(o));
     if (!v || !z || v == z) return set_err(GF_ERR_ARG, "v, z non-null and distinct");
     if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
     RET(set_device(g));
@@ -2029,7 +2021,7 @@ int gf_chebyshev_lambda(gf_grid* g, int prec, double* lam, int n)
 int gf_solve(gf_grid* g, const double* f, double* u, const gf_solve_opts* opts, gf_solve_info* info)
 {
     RET(check_grid(g));
-    RET(validate_grid_opts(g, opts));
+    RET(validate_opts(opts));
     if (!f || !u || f == u) return set_err(GF_ERR_ARG, "f, u non-null and distinct");
     if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
     RET(set_device(g));
@@ -2167,7 +2159,7 @@ int select_floor_reuse(gf_grid* g, const double* f, double* u, const gf_policy* 
     o.history = nullptr;
     o.tol = pol->tau;
     o.kmax = pol->kmax;
-    RET(validate_grid_opts(g, &o));
+    RET(validate_opts(&o));
     RET(set_device(g));
     const double rm = pol->first_index == 0 ? pol->rho0 : pol->ladder[pol->first_index - 1];
     if (!(g->has_floor && g->rho_min == rm)) RET(gf_set_floor(g, rm));
@@ -2221,7 +2213,7 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
     gf_solve_opts o = pol->solve;
     o.history = nullptr;
     o.tol = pol->tau;
-    RET(validate_grid_opts(g, &o));
+    RET(validate_opts(&o));
     RET(set_device(g));
     std::memset(info, 0, sizeof(*info));
     info->r50 = info->r100 = std::nan("");
