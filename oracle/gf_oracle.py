@@ -62,6 +62,11 @@ formed as at a cycle end and its guard residual recomputed; the detector fires w
 one exceeds ratio (default 10) times the projected estimate of the same step, and a
 firing detector escalates like Eq. (trigger).
 
+Bridge geometry (Table geometries; oracle only, the CUDA path keeps the clamped face):
+BridgeMesh fixes every DOF of the nodes (0, 0, z) and y, z of the nodes (x_max, 0, z) for
+z in {0, Lz/2, Lz}; bridge_load is a unit pressure on the top face as consistent nodal
+forces. Coarse meshes inherit their fixed sets by injection (Mesh.coarsen).
+
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, invariants, brute force on tiny grids, paper values). None is
 "parity unpinned".
@@ -124,6 +129,18 @@ class Mesh:
     def node(self, i, j, k):
         return i + (self.nx + 1) * (j + (self.ny + 1) * k)
 
+    def coarsen(self) -> "Mesh":
+        """The 2:1 coarser mesh (edge 2h). Its fixed set is the fine one injected: coarse
+        node (I, J, K) fixes component c iff fine node (2I, 2J, 2K) does (for the clamped
+        face this is again every DOF of the x = 0 nodes)."""
+        mc = Mesh(self.nx // 2, self.ny // 2, self.nz // 2, self.h * 2.0)
+        n = np.arange(mc.n_nodes)
+        I, J, K = n % (mc.nx + 1), (n // (mc.nx + 1)) % (mc.ny + 1), n // ((mc.nx + 1) * (mc.ny + 1))
+        fine = self.node(2 * I, 2 * J, 2 * K)
+        mc.fixed = self.fixed.reshape(-1, 3)[fine].ravel().copy()
+        mc.free = ~mc.fixed
+        return mc
+
     def _element_coords(self):
         e = np.arange(self.n_elem)
         ex = e % self.nx
@@ -137,6 +154,41 @@ class Mesh:
         j = (n // (self.nx + 1)) % (self.ny + 1)
         k = n // ((self.nx + 1) * (self.ny + 1))
         return i * self.h, j * self.h, k * self.h
+
+
+class BridgeMesh(Mesh):
+    """The paper's bridge geometry (Table geometries: a 3.0 x 1.0 x 0.5 box, y up): every
+    DOF fixed at the nodes (0, 0, z) and rollers free in x at (x_max, 0, z), for z at the
+    two faces and the mid-plane of the depth. Reading: the supports sit on nodes
+    k in {0, nz/2, nz}, so nz is even (the paper's 90x30x15 and 210x70x35 meshes put
+    z = 0.25 between nodes). The x-extent carries no constraint (any nx)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, h: float = 1.0):
+        if nz % 2:
+            raise ValueError("bridge supports need even nz")
+        super().__init__(nx, ny, nz, h)
+        fixed = np.zeros(self.n_dof, dtype=bool)
+        for k in (0, nz // 2, nz):
+            n0, n1 = self.node(0, 0, k), self.node(nx, 0, k)
+            fixed[3 * n0:3 * n0 + 3] = True        # fully fixed
+            fixed[3 * n1 + 1:3 * n1 + 3] = True    # roller: y and z fixed, free in x
+        self.fixed = fixed
+        self.free = ~fixed
+
+
+def bridge_load(mesh: Mesh, p: float = 1.0) -> np.ndarray:
+    """Unit pressure on the top face y = ny h, pointing down (-y), as consistent nodal
+    forces by tributary area (Sec. 3.1): each top face of area h^2 gives -p h^2 / 4 to
+    each of its four corner nodes (bilinear face, uniform pressure)."""
+    f = np.zeros(mesh.n_dof)
+    ex, ez = np.meshgrid(np.arange(mesh.nx), np.arange(mesh.nz), indexing="ij")
+    share = -p * mesh.h * mesh.h / 4.0
+    for dx in (0, 1):
+        for dz in (0, 1):
+            nodes = mesh.node(ex + dx, mesh.ny, ez + dz).ravel()
+            np.add.at(f, 3 * nodes + 1, share)
+    f[mesh.fixed] = 0.0
+    return f
 
 
 def cantilever_load(mesh: Mesh) -> np.ndarray:
@@ -268,7 +320,7 @@ def apply_K_at_nodes(mesh: Mesh, E: np.ndarray, K0: np.ndarray, u: np.ndarray,
         i = n % (nx + 1)
         j = (n // (nx + 1)) % (ny + 1)
         k = n // ((nx + 1) * (ny + 1))
-        if i == 0:
+        if mesh.fixed[3 * n:3 * n + 3].all():
             continue
         acc = np.zeros(3)
         for a, (ox, oy, oz) in enumerate(LOCAL_NODES):
@@ -279,7 +331,7 @@ def apply_K_at_nodes(mesh: Mesh, E: np.ndarray, K0: np.ndarray, u: np.ndarray,
             dofs = mesh.edof[e]
             ue = np.where(mesh.fixed[dofs], 0.0, u[dofs])
             acc += E[e] * (K0[3 * a:3 * a + 3, :] @ ue)
-        out[t] = acc
+        out[t] = np.where(mesh.fixed[3 * n:3 * n + 3], 0.0, acc)
     return out
 
 
@@ -326,8 +378,15 @@ def node_block_diagonal(mesh: Mesh, E: np.ndarray, K0: np.ndarray) -> np.ndarray
             for c in range(3):
                 Db[:, r, c] += np.bincount(mesh.conn[:, a], weights=contrib[:, r, c],
                                            minlength=mesh.n_nodes)
-    fixed_node = mesh.fixed[0::3]
-    Db[fixed_node] = np.eye(3)
+    return _mask_blocks(Db, mesh)
+
+
+def _mask_blocks(Db: np.ndarray, mesh: Mesh) -> np.ndarray:
+    """Node blocks of the constrained operator: fixed rows and columns become those of
+    the identity (a fully fixed node gets I; a roller keeps only its free entries)."""
+    m = (~mesh.fixed).reshape(-1, 3).astype(np.float64)
+    Db = Db * m[:, :, None] * m[:, None, :]
+    Db[:, np.arange(3), np.arange(3)] += 1.0 - m
     return Db
 
 
@@ -395,8 +454,7 @@ def _blocks_of(K: sp.csr_matrix, mesh: Mesh) -> np.ndarray:
     for a in range(3):
         for b in range(3):
             D[:, a, b] = np.asarray(K[np.arange(n) * 3 + a, np.arange(n) * 3 + b]).ravel()
-    D[mesh.fixed[0::3]] = np.eye(3)
-    return D
+    return _mask_blocks(D, mesh)
 
 
 def build_hierarchy(mesh: Mesh, E_fine: np.ndarray, n_levels: int, nu: float = 0.3,
@@ -426,7 +484,7 @@ def build_hierarchy(mesh: Mesh, E_fine: np.ndarray, n_levels: int, nu: float = 0
             raise ValueError("grid not divisible for the requested level count")
         P = prolongation(m)
         H.levels[-1].P = P
-        mc = Mesh(m.nx // 2, m.ny // 2, m.nz // 2, m.h * 2.0)
+        mc = m.coarsen()
         if coarse == "galerkin":
             Kf = H.levels[-1].K if H.levels[-1].K is not None else assemble_sparse(m, E, K0)
             Pm = sp.diags(m.free.astype(np.float64)) @ P @ sp.diags(mc.free.astype(np.float64))

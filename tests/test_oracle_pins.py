@@ -469,6 +469,74 @@ def test_coarse_krylov_one_step_closed_form_monotone_and_exact():
     assert np.linalg.norm(O.vcycle(H10, v) - ref) > 1e-6 * np.linalg.norm(ref)   # ten steps are not exact
 
 
+# ---------------------------------------------------------------- bridge ----
+def test_bridge_pressure_load_is_the_consistent_load_of_a_uniform_pressure():
+    """bridge_load equals int N_a p dA over the top face, computed here by 2x2 Gauss on
+    each bilinear face; the total is p times the top area, all in -y, and the load is
+    symmetric about the mid-planes x = Lx/2 and z = Lz/2."""
+    m = O.BridgeMesh(6, 2, 4, h=0.5)
+    f = O.bridge_load(m, p=2.0)
+    ref = np.zeros(m.n_dof)
+    g = np.array([-1.0, 1.0]) / np.sqrt(3.0)
+    for ex in range(m.nx):
+        for ez in range(m.nz):
+            for s_ in g:
+                for t_ in g:
+                    for dx in (0, 1):
+                        for dz in (0, 1):
+                            N = 0.25 * (1 + (2 * dx - 1) * s_) * (1 + (2 * dz - 1) * t_)
+                            n = m.node(ex + dx, m.ny, ez + dz)
+                            ref[3 * n + 1] -= 2.0 * N * (m.h / 2) ** 2     # weight 1, Jacobian (h/2)^2
+    assert np.allclose(f, ref, rtol=0, atol=1e-14)
+    F = f.reshape(-1, 3)
+    assert np.isclose(F[:, 1].sum(), -2.0 * (m.nx * m.h) * (m.nz * m.h)) and not F[:, [0, 2]].any()
+    Fy = F[:, 1].reshape(m.nz + 1, m.ny + 1, m.nx + 1)
+    assert np.array_equal(Fy, Fy[::-1, :, :]) and np.array_equal(Fy, Fy[:, :, ::-1])
+
+
+def test_bridge_supports_make_the_operator_positive_definite():
+    """Three fully fixed nodes on the line (0, 0, z) leave one rigid mode, the rotation
+    about that line; the rollers at (x_max, 0, z) (y fixed) remove it. Without them the
+    constrained operator is singular, with them positive definite."""
+    m = O.BridgeMesh(4, 2, 2)
+    assert m.fixed.sum() == 3 * 3 + 3 * 2
+    E = O.young_modulus(np.ones(m.n_elem), 1e-3, 3.0)
+    K0 = O.element_stiffness()
+    w = np.linalg.eigvalsh(O.assemble_dense_free(m, E, K0))
+    assert w[0] > 1e-6 * w[-1]
+    loose = O.BridgeMesh(4, 2, 2)
+    for k in (0, 1, 2):
+        n1 = loose.node(4, 0, k)
+        loose.fixed[3 * n1:3 * n1 + 3] = False
+    loose.free = ~loose.fixed
+    wl = np.linalg.eigvalsh(O.assemble_dense_free(loose, E, K0))
+    assert wl[0] < 1e-10 * wl[-1]
+    # that zero mode is the rotation about the z-axis through the supports
+    X, Y, Z = loose.node_coords()
+    r = np.stack([-Y, X, np.zeros_like(Z)], axis=1).ravel()
+    assert np.linalg.norm(O.apply_K(loose, E, K0, r)[loose.free]) < 1e-10 * np.linalg.norm(r)
+
+
+def test_bridge_hierarchy_injects_supports_and_the_solve_reaches_the_direct_solution():
+    """coarsen() injects the supports (coarse node (I, J, K) fixes what fine node
+    (2I, 2J, 2K) fixes); GMG-preconditioned FGMRES on the bridge reaches the dense
+    direct solution of the constrained system."""
+    m = O.BridgeMesh(16, 4, 8)
+    mc = m.coarsen()
+    Fc = mc.fixed.reshape(-1, 3)
+    for k in (0, 2, 4):
+        assert Fc[mc.node(0, 0, k)].all() and list(Fc[mc.node(8, 0, k)]) == [False, True, True]
+    assert Fc.sum() == 15
+    rho = synth.smoothed_gaussian_density(16, 4, 8, 2)
+    f = O.bridge_load(m)
+    res, E, K0 = O.solve_at_floor(O.SolverSetup(m, rho, p=3.0, n_levels=3), f, 1e-3, 200, 1e-10)
+    assert res.flag == O.CONVERGED
+    K = O.assemble_dense_free(m, E, K0)
+    x = np.zeros(m.n_dof)
+    x[m.free] = np.linalg.solve(K, f[m.free])
+    assert np.linalg.norm(res.x - x) <= 1e-8 * np.linalg.norm(x)
+
+
 # ---------------------------------------------------------------- FGMRES ----
 def test_fgmres_diagonal_distinct_eigenvalues():
     d = np.array([1.0, 2.0, 2.0, 3.0, 3.0, 3.0, 5.0])
