@@ -504,6 +504,14 @@ def test_bridge_supports_make_the_operator_positive_definite():
     K0 = O.element_stiffness()
     w = np.linalg.eigvalsh(O.assemble_dense_free(m, E, K0))
     assert w[0] > 1e-6 * w[-1]
+    # node blocks of the constrained operator: a roller keeps its x entry (K's diagonal
+    # there) and identity rows and columns for y and z; a full support is the identity
+    Db = O.node_block_diagonal(m, E, K0)
+    Kfull = O.assemble_sparse(m, E, K0, constrained=False).toarray()
+    nr, ns = m.node(4, 0, 1), m.node(0, 0, 1)
+    assert np.isclose(Db[nr, 0, 0], Kfull[3 * nr, 3 * nr]) and Db[nr, 0, 0] > 0
+    assert np.array_equal(Db[nr, 1:, 1:], np.eye(2)) and not Db[nr, 0, 1:].any() and not Db[nr, 1:, 0].any()
+    assert np.array_equal(Db[ns], np.eye(3))
     loose = O.BridgeMesh(4, 2, 2)
     for k in (0, 1, 2):
         n1 = loose.node(4, 0, k)
