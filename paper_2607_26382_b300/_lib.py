@@ -324,6 +324,11 @@ class Grid:
     # solve / guard / policy
     def solve(self, f, u, restart=30, kmax=200, tol=1e-6, prec=GF_FP64, nu1=2, nu2=2, omega=0.6,
               want_history=True, outer=0, smoother=0, ls_ratio=0.0, fine_steps=0, coarse_steps=0):
+        """gf_solve: FGMRES(restart <= 300) on K(rho_min) u = f from the given u, preconditioned
+        by the V-cycle (prec GF_FP64 or GF_MIXED; outer 0/1/2 the Krylov arithmetic; smoother 0
+        node-block Jacobi, 1 Chebyshev) and, when set, the adaptive components: ls_ratio (the
+        line-searched coarse correction), fine_steps (fine-level inner FGMRES), coarse_steps
+        (coarse-level inner Krylov solve). Returns iters, flag, stop_estimate and the history."""
         t = _torch().float64
         hist = (c_double * (kmax + 1))() if want_history else None
         o = SolveOpts(int(restart), int(kmax), float(tol), int(prec), int(nu1), int(nu2), float(omega),
