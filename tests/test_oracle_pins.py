@@ -987,3 +987,102 @@ def test_vcycle_with_chebyshev_is_symmetric_and_preconditions_fgmres():
     assert res.flag == O.CONVERGED and res.iters < 60
     uh = res.x
     assert O.true_residual(m, E2, K0, f, uh) <= 1.5e-6
+
+
+# ------------------------------------------- damped node-block Jacobi smoother ---
+def _assembled_block_diag_free(m, E, K0):
+    """D_b from the assembled operator's 3x3 diagonal blocks (not from the oracle's own
+    node_block_diagonal), restricted to the free DOFs."""
+    Kd = O.assemble_sparse(m, E, K0, constrained=False).toarray()
+    D = np.zeros_like(Kd)
+    for n in range(m.n_nodes):
+        s = slice(3 * n, 3 * n + 3)
+        D[s, s] = Kd[s, s]
+    return D[np.ix_(m.free, m.free)]
+
+
+def _generalized_modes(m, E, K0):
+    """(lam, e) pairs of K e = lam D_b e on the free DOFs, e padded with zeros on fixed DOFs."""
+    A = O.assemble_dense_free(m, E, K0)
+    lams, vecs = sla.eigh(A, _assembled_block_diag_free(m, E, K0))
+    out = []
+    for idx in (0, len(lams) // 4, len(lams) // 2, (3 * len(lams)) // 4, len(lams) - 1):
+        e = np.zeros(m.n_dof)
+        e[m.free] = vecs[:, idx]
+        out.append((float(lams[idx]), e))
+    return out
+
+
+def test_jacobi_sweep_multiplies_generalized_eigenvectors_by_one_minus_omega_lambda():
+    """Damped node-block Jacobi from x = e with b = 0 is x <- (I - omega D_b^{-1} K) x; on a
+    generalized eigenvector K e = lam D_b e that is exactly (1 - omega lam) e, and nu
+    sweeps give (1 - omega lam)^nu. The modes come from scipy's generalized eigh of the
+    assembled operator and its 3x3 diagonal blocks; omega = 0.6 is the workload's
+    damping. A wrong omega, a point-diagonal D or a dropped minus sign each miss it."""
+    m = O.Mesh(4, 2, 2)
+    E = O.young_modulus(synth.bernoulli_density(4, 2, 2, 5, 0.5), 1e-3, 3)
+    lev = O.build_hierarchy(m, E, 1).levels[0]
+    zero = np.zeros(m.n_dof)
+    modes = _generalized_modes(m, E, lev.K0)
+    assert modes[-1][0] > 2.0 and modes[0][0] < 0.1       # the factors span both signs
+    for lam, e in modes:
+        x1 = O.jacobi_sweep(lev, e, zero, 0.6)
+        assert np.abs(x1 - (1.0 - 0.6 * lam) * e).max() <= 1e-11 * np.abs(e).max(), lam
+        x2 = O.jacobi_sweep(lev, x1, zero, 0.6)
+        assert np.abs(x2 - (1.0 - 0.6 * lam) ** 2 * e).max() <= 1e-11 * np.abs(e).max(), lam
+
+
+def test_vcycle_smooths_with_two_plus_two_sweeps_at_omega_0_6(monkeypatch):
+    """With the coarse correction removed (the coarsest solve replaced by zero), a
+    V-cycle from x = 0 on b = K e is smoothing alone: the error e - z after nu1 + nu2
+    sweeps is (1 - omega lam)^(nu1 + nu2) e on a generalized eigenvector e. The default
+    hierarchy must give nu1 + nu2 = 4 and omega = 0.6 (the workload's 2 Jacobi sweeps at
+    omega = 0.6 before and after the coarse correction); the symmetry pin of the V-cycle
+    fixes nu1 = nu2. Three sweeps, five, or omega = 0.5 each miss the factor on the
+    modes used here by more than 1e-3."""
+    m = O.Mesh(4, 2, 2)
+    E = O.young_modulus(synth.bernoulli_density(4, 2, 2, 6, 0.5), 1e-3, 3)
+    H = O.build_hierarchy(m, E, 2)
+    monkeypatch.setattr(O, "coarse_solve", lambda level, b: np.zeros_like(b))
+    K0 = H.levels[0].K0
+    for lam, e in _generalized_modes(m, E, K0):
+        b = O.apply_K(m, E, K0, e)
+        z = O.vcycle(H, b)
+        factor = (1.0 - 0.6 * lam) ** 4
+        assert np.abs((e - z) - factor * e).max() <= 1e-10 * np.abs(e).max(), lam
+        for wrong in ((1.0 - 0.6 * lam) ** 3, (1.0 - 0.6 * lam) ** 5, (1.0 - 0.5 * lam) ** 4):
+            if abs(wrong - factor) > 1e-3:
+                assert np.abs((e - z) - wrong * e).max() > 1e-4 * np.abs(e).max()
+
+
+# ------------------------------------------------------------- OC update -----
+def test_oc_update_closed_forms():
+    """The OC update x_e <- clip(x_e sqrt(-dc_e / (lam dv_e)), max(0, x_e - move),
+    min(1, x_e + move)) with lam fixed by mean(x_new) = volfrac, on cases solved by hand
+    (bisection tolerance tightened so the closed forms hold to 1e-9):
+      (a) uniform dc from x = volfrac: x is unchanged;
+      (b) two groups with -dc = 1 and 4 (dv = 1), no clipping: x_new is proportional
+          to sqrt(-dc), so volfrac * (2/3, 4/3) = (0.2, 0.4) at volfrac 0.3;
+      (c) a quarter with -dc = 100, the rest 1, move 0.2 from 0.3: the upper group
+          clips at 0.5, and the rest share the remaining volume, 0.7/3;
+      (d) dv = 1 and 4 with uniform dc: x_new proportional to 1/sqrt(dv), so
+          (0.4, 0.2) at volfrac 0.3.
+    An update without the square root, or with the sign of dc flipped, fails (b)-(d)."""
+    n = 16
+    x = np.full(n, 0.3)
+    one = np.ones(n)
+    kw = dict(move=0.2, tol=1e-13, max_bisect=400)
+    xa = O.oc_update(x, -2.5 * one, one, 0.3, **kw)
+    assert np.abs(xa - 0.3).max() < 1e-9
+    dc = -np.where(np.arange(n) % 2 == 0, 1.0, 4.0)
+    xb = O.oc_update(x, dc, one, 0.3, **kw)
+    assert np.abs(xb - np.where(np.arange(n) % 2 == 0, 0.2, 0.4)).max() < 1e-9
+    dc = -np.where(np.arange(n) < n // 4, 100.0, 1.0)
+    xc = O.oc_update(x, dc, one, 0.3, **kw)
+    assert np.abs(xc - np.where(np.arange(n) < n // 4, 0.5, 0.7 / 3.0)).max() < 1e-9
+    dv = np.where(np.arange(n) % 2 == 0, 1.0, 4.0)
+    xd = O.oc_update(x, -one, dv, 0.3, **kw)
+    assert np.abs(xd - np.where(np.arange(n) % 2 == 0, 0.4, 0.2)).max() < 1e-9
+    # the default tolerance still holds the volume to its stated relative bracket width
+    xb_default = O.oc_update(x, -np.where(np.arange(n) % 2 == 0, 1.0, 4.0), one, 0.3)
+    assert abs(xb_default.mean() - 0.3) < 1e-3 and np.abs(xb_default - xb).max() < 1e-3
