@@ -439,8 +439,16 @@ int gf_select_features(const gf_grid* g, double r50, double r100, double* x);
  * *eta = ||M(f - K u)||_2 / ||M f||_2 in FP64 with E_e = rho_min + (1 - rho_min)
  * rho_hat_e^p (scaled by E0), but needs no gf_grid: every input is a raw pointer.
  *  - rho_hat: n_elem doubles; f, u: n_dof doubles; eta: ONE double; all DEVICE
- *    pointers. *eta is written on `stream` (a cudaStream_t, NULL = legacy default
- *    stream); read it after the stream's work completes. NaN in an input gives NaN.
+ *    pointers, allocated on the device that is current when the call is made: the
+ *    call never switches devices, and it launches on, and uses the scratch array
+ *    of, the current device. Pointers into another GPU's memory are not detected
+ *    and make the kernels fault. *eta is written on `stream` (a cudaStream_t,
+ *    NULL = legacy default stream); read it after the stream's work completes.
+ *  - Bad values give a non-finite *eta, not an error code: *eta is NaN when
+ *    ||M f|| = 0 (a load that is zero on every free DOF; gf_true_residual returns
+ *    GF_ERR_ARG there), and NaN or Inf when an input holds NaN or Inf or the sums
+ *    overflow (gf_true_residual returns GF_ERR_NONFINITE). A caller must treat a
+ *    non-finite *eta as "not accepted"; the comparison *eta <= tau already does.
  *  - Scratch: a static device array inside the library (about 11.2 MB), reserved
  *    on every GPU that loads the library until the process exits. It holds grids
  *    of at most 1,048,576 DOFs; larger grids return GF_ERR_ARG with a message.
