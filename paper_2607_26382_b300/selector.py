@@ -12,9 +12,15 @@ Workflow (every solve, feature and network step runs in libgf_b300.so):
 """
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 
 from . import _lib as L
+
+# weights written by ``python -m paper_2607_26382_b300.train_selector``
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "selector_weights.json")
 
 
 def _batch_for(dims_list, levels, rhos, p=3.0):
@@ -48,15 +54,21 @@ def ladder_dataset(dims, rhos, levels, policy: L.Policy, chunk=64):
     return np.array(X), np.array(y, dtype=np.int32), recs
 
 
+def feature_norm(X):
+    """Standardisation of the selector's inputs: per-feature mean and std (+1e-6), from
+    the training rows; the device MLP applies it (gf_mlp_set_norm)."""
+    return X.mean(axis=0), X.std(axis=0) + 1e-6
+
+
 def train_selector(X, y, theta0, perm, epochs, batch=128, lr=3e-3):
     import torch
-    mu = X.mean(axis=0)
-    sd = X.std(axis=0) + 1e-6
+    mu, sd = feature_norm(X)
     net = L.MLP(theta0)
     net.set_norm(mu, sd)
     Xd = torch.as_tensor(X, dtype=torch.float32, device="cuda").contiguous()
     yd = torch.as_tensor(y, dtype=torch.int32, device="cuda").contiguous()
     loss = net.train(Xd, yd, epochs, batch, lr, perm)
+    net.mu, net.sd = mu, sd
     return net, loss
 
 
@@ -86,3 +98,19 @@ def compare_selectors(dims, rhos, levels, policy: L.Policy, net: L.MLP, chunk=64
             b.close()
         out[name] = recs
     return out
+
+
+def save_trained(net: L.MLP, mu, sd, info, path=WEIGHTS):
+    rec = dict(info, theta=[float(v) for v in net.params()], mu=[float(v) for v in mu],
+               sd=[float(v) for v in sd])
+    with open(path, "w") as fh:
+        json.dump(rec, fh, indent=0)
+
+
+def load_trained(path=WEIGHTS):
+    """(MLP on the device, metadata) from a weights file written by train_selector."""
+    rec = json.load(open(path))
+    net = L.MLP(np.asarray(rec["theta"], dtype=np.float32))
+    net.set_norm(rec["mu"], rec["sd"])
+    meta = {k: v for k, v in rec.items() if k not in ("theta", "mu", "sd")}
+    return net, meta

@@ -21,8 +21,13 @@ Recipes (stated for the workloads the paper's states are shaped like):
 * ``optimised_like_density`` -- a smooth load-path-shaped field built from a few
   seeded, randomly placed tapered bars between the clamped face and the load
   point, blurred and thresholded to a target volume; then a seeded random
-  ``floor_frac`` of voxels is forced to 0. It stands in for SIMP-optimised fields,
-  which the paper does not publish.
+  ``floor_frac`` of voxels is forced to 0. A cheap stand-in for SIMP-optimised
+  fields, which the paper does not publish (used where no SIMP-OC run is at hand).
+* ``force_to_floor`` -- a seeded uniform-random choice of exactly
+  floor(frac * n_e) voxels of a given field set to 0 ("forced to floor"); applied
+  to a SIMP-OC design it gives the optimised-like states of the large and batched
+  workloads (the SIMP-OC run itself is the method's arithmetic and happens in the
+  library or in the oracle, never here).
 """
 from __future__ import annotations
 
@@ -34,6 +39,7 @@ __all__ = [
     "bernoulli_density",
     "smoothed_gaussian_density",
     "optimised_like_density",
+    "force_to_floor",
     "random_vector",
     "batch_grid_sizes",
 ]
@@ -118,6 +124,17 @@ def optimised_like_density(nx: int, ny: int, nz: int, seed: int,
     return rho
 
 
+def force_to_floor(rho: np.ndarray, frac: float, seed: int) -> np.ndarray:
+    """A copy of rho with a seeded uniform-random set of exactly floor(frac * n) voxels
+    set to 0 (the choice is the first floor(frac * n) entries of a permutation drawn
+    from ``default_rng(seed)``)."""
+    out = np.array(rho, dtype=np.float64, copy=True).ravel()
+    rng = np.random.default_rng(seed)
+    k = int(np.floor(frac * out.size))
+    out[rng.permutation(out.size)[:k]] = 0.0
+    return out
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     """U(-1,1) float64 test vector."""
     rng = np.random.default_rng(seed)
@@ -148,11 +165,13 @@ def epoch_permutations(n: int, epochs: int, seed: int) -> np.ndarray:
     return np.concatenate([rng.permutation(n) for _ in range(epochs)]).astype(np.int32)
 
 
-def selector_training_states(n: int, dims, seed: int):
+def selector_training_states(n: int, dims, seed: int, designs=None):
     """A mix of states for selector training, in turn: Bernoulli hard fields with solid
     probability q ~ U(0.15, 0.6); smoothed-Gaussian fields with floor fraction
-    ~ U(0.1, 0.6) and sigma in {1, 2, 3}; optimised-like fields with volume
-    ~ U(0.2, 0.4) and forced-floor fraction ~ U(0.1, 0.5)."""
+    ~ U(0.1, 0.6) and sigma in {1, 2, 3}; optimised-like fields with forced-floor
+    fraction ~ U(0.1, 0.5): with ``designs`` (a list of SIMP-OC designs of this size)
+    a seeded choice among them passed through ``force_to_floor``, else
+    ``optimised_like_density`` with volume ~ U(0.2, 0.4)."""
     rng = np.random.default_rng(seed)
     nx, ny, nz = dims
     out = []
@@ -163,6 +182,9 @@ def selector_training_states(n: int, dims, seed: int):
         elif i % 3 == 1:
             out.append(smoothed_gaussian_density(nx, ny, nz, s, float(rng.choice([1.0, 2.0, 3.0])),
                                                  float(rng.uniform(0.1, 0.6))))
+        elif designs:
+            base = designs[int(rng.integers(0, len(designs)))]
+            out.append(force_to_floor(base, float(rng.uniform(0.1, 0.5)), s))
         else:
             out.append(optimised_like_density(nx, ny, nz, s, float(rng.uniform(0.2, 0.4)),
                                               float(rng.uniform(0.1, 0.5))))

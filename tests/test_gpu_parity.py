@@ -985,3 +985,38 @@ def test_solve_with_split_outer_operator(gf):
         h = min(a["iters"], b["iters"])
         assert np.allclose(a["history"][:h], b["history"][:h], rtol=1e-6)
         assert O.true_residual(m, E, O.element_stiffness(), f, ub) <= 1.5e-6
+
+
+# ------------------------------------------------------------- full-size decision --
+@pytest.mark.parametrize("prec,outer", [("mixed", 0), ("mixed", 2), ("fp64", 0)])
+def test_full_size_select_floor_matches_oracle_record(gf, prec, outer):
+    """Algorithm 1 on the 96x48x48 smoothed-Gaussian state (seed 0, 40% at floor, 5
+    levels, probe at 1e-6, ladder {1e-5, 1e-4, 1e-3}, FGMRES(30), tau 1e-6, kmax 200)
+    against the oracle's own full-size record (tests/golden/policy_c2_seed0.json,
+    written by tests/golden/make_policy_records.py from oracle/ alone): the same status,
+    floor and escalation, the same attempted floors, iterations within +-2 of the
+    oracle's, and r50 / r100 within 1e-4 relative. Run in the native FP64 form and in
+    the mixed form with native FP64 Krylov (outer 0) and with the FP64-class one (2)."""
+    import json
+    import os
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "policy_c2_seed0.json")))
+    w = rec["workload"]
+    rho = synth.smoothed_gaussian_density(w["nx"], w["ny"], w["nz"], rec["seed"], w["sigma"], w["floor_frac"])
+    g = gf.create_grid(w["nx"], w["ny"], w["nz"], levels=w["levels"])
+    g.set_density(dev(rho), w["p"])
+    f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.cantilever_load(f)
+    u = torch.zeros_like(f)
+    pol = gf.policy_defaults(rho0=w["rho0"], ladder=w["ladder"], tau=w["tau"], kmax=w["kmax"],
+                             probe_iters=w["probe_iters"], solve_restart=w["restart"],
+                             solve_prec=gf.GF_MIXED if prec == "mixed" else gf.GF_FP64, solve_outer=outer)
+    out = g.select_floor(f, u, pol)
+    assert out["status"] == rec["status"] and out["floor_index"] == rec["floor_index"]
+    assert out["escalated"] == rec["escalated"]
+    assert abs(out["r50"] - rec["r50"]) <= 1e-4 * rec["r50"]
+    assert abs(out["r100"] - rec["r100"]) <= 1e-4 * rec["r100"]
+    assert len(out["attempts"]) == len(rec["attempts"])
+    for a, b in zip(out["attempts"], rec["attempts"]):
+        assert a["rho_min"] == b["rho_min"] and abs(a["iters"] - b["iters"]) <= 2
+        assert a["accepted"] == b["accepted"]
+    assert out["eta"] <= w["tau"]

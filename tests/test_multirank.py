@@ -27,8 +27,7 @@ def _rank(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
     mx, sm = bench.over_ranks(dist, "cpu", [10.0 * (rank + 1), -rank], [rank + 1, 3])
-    rhos = bench.states(rank, 2)
-    q.put((rank, mx, sm, [float((r.ravel() * np.arange(r.size)).sum()) for r in rhos]))
+    q.put((rank, mx, sm, _state_hashes(bench, rank)))
     dist.destroy_process_group()
 
 
@@ -50,10 +49,19 @@ def test_over_ranks_max_time_sum_units_and_distinct_states():
     assert bench_states_single_process() == out[0][2]
 
 
+def _state_hashes(bench, rank):
+    """The rank's bench states applied to a fixed design (the design itself is made on the
+    device; the per-rank, per-state part is the seeded forced-floor set)."""
+    import synth
+    base = np.linspace(0.05, 1.0, 4096)
+    return [float((synth.force_to_floor(base, 0.3, s) * np.arange(base.size)).sum())
+            for s in bench.state_seeds(rank, 2)]
+
+
 def bench_states_single_process():
     sys.path.insert(0, ROOT)
     import bench
-    return [float((r.ravel() * np.arange(r.size)).sum()) for r in bench.states(0, 2)]
+    return _state_hashes(bench, 0)
 
 
 def test_reference_arm_under_two_ranks_prints_once():
