@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 102-state comparison")
     ap.add_argument("--cpu-full", action="store_true",
                     help="also time one complete oracle Algorithm-1 pass on the 96x48x48 state (~2 min)")
+    ap.add_argument("--cpu-worker", choices=["passes", "apply", "full_c2"], default=None,
+                    help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -158,11 +160,19 @@ def host_cores():
 
 
 def blas_threads():
+    """Threads of the BLAS pool this process uses (threadpoolctl where installed, else the
+    thread-count environment variables, else every CPU the process may run on)."""
     try:
         from threadpoolctl import threadpool_info
         return max([1] + [int(i.get("num_threads", 1)) for i in threadpool_info()])
     except Exception:
-        return 1
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            if os.environ.get(var, "").isdigit():
+                return int(os.environ[var])
+        return host_cores()[1]
+
+
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
 
 
 def kernel_source_hash(source, start, end):
@@ -256,36 +266,59 @@ def oracle_kernel_gdofs(dims):
     return m.n_dof / (time.perf_counter() - t0) / 1e9
 
 
+def cpu_worker(kind):
+    """Runs in a child process whose thread-count variables the parent set: prints one JSON
+    line with the timed oracle work of `kind` ("passes", "apply", "full_c2")."""
+    if kind == "passes":
+        t0 = time.perf_counter()
+        m, f, rhos = oracle_state(0)
+        t_state = time.perf_counter() - t0
+        acc, sec, steps = 0, 0.0, 0
+        for rho in rhos * 2:
+            a, dt, k = oracle_pass(m, f, rho)
+            acc, sec, steps = acc + a, sec + dt, steps + k
+        out = {"value": acc / sec, "passes": 2 * len(rhos), "accepted": acc, "seconds": sec,
+               "arnoldi_steps": steps, "seconds_state": t_state}
+    elif kind == "apply":
+        out = {"gdofs": oracle_kernel_gdofs(LARGE)}
+    else:
+        out = oracle_full_c2()
+    out["blas_threads"] = blas_threads()
+    print(json.dumps(out), flush=True)
+
+
+def run_cpu_worker(kind, threads):
+    env = dict(os.environ)
+    for var in THREAD_VARS:
+        env[var] = str(threads)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", kind], env=env,
+                       capture_output=True, text=True, timeout=3600)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle worker {kind} failed: {r.stderr[-2000:]}")
+    return json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+
+
 def cpu_baseline(full_c2=False):
-    """Complete oracle Algorithm-1 passes on the 24x12x12 sample (one thread, then every
-    host thread for BLAS), plus one complete oracle K*u at 192x96x96. Nothing is
-    extrapolated."""
-    from threadpoolctl import threadpool_limits
+    """Complete oracle Algorithm-1 passes on the 24x12x12 sample in child processes with
+    one thread and with every host CPU for BLAS, plus one complete oracle K*u at
+    192x96x96. Nothing is extrapolated."""
     ncpu, aff = host_cores()
-    t0 = time.perf_counter()
-    m, f, rhos = oracle_state(0)
-    t_state = time.perf_counter() - t0
     runs = {}
     for label, nthreads in (("single_thread", 1), ("all_threads", aff)):
-        with threadpool_limits(limits=nthreads):
-            acc, sec, steps = 0, 0.0, 0
-            for rho in rhos * 2:
-                a, dt, k = oracle_pass(m, f, rho)
-                acc, sec, steps = acc + a, sec + dt, steps + k
-            runs[label] = {"value": acc / sec, "passes": 2 * len(rhos), "accepted": acc, "seconds": sec,
-                           "arnoldi_steps": steps, "threads": nthreads}
-    with threadpool_limits(limits=1):
-        gd = oracle_kernel_gdofs(LARGE)
+        r = run_cpu_worker("passes", nthreads)
+        r["threads"] = nthreads
+        runs[label] = r
+    gd = run_cpu_worker("apply", 1)["gdofs"]
     best = max(runs.values(), key=lambda r: r["value"])
     out = {"value": best["value"], "unit": UNIT, "cores": best["threads"], "kind": "oracle",
            "sample": (f"{best['passes']} complete oracle Algorithm-1 passes (2 states, each twice) on the "
                       f"24x12x12 state of the headline recipe, made by the oracle's own SIMP-OC "
-                      f"({t_state:.1f} s, untimed); not extrapolated. The bench states are 512x larger"),
+                      f"({best['seconds_state']:.1f} s, untimed); not extrapolated. The bench states are 512x larger"),
            "nproc": ncpu, "affinity_cpus": aff, "runs": runs,
            "apply_K_gdofs_192x96x96": gd,
            "apply_K_note": "one complete oracle FP64 K*u on the 192x96x96 grid, 1 thread"}
     if full_c2:
-        out["full_96x48x48"] = oracle_full_c2()
+        out["full_96x48x48"] = run_cpu_worker("full_c2", 1)
     return out
 
 
@@ -293,17 +326,15 @@ def oracle_full_c2():
     """One complete oracle Algorithm-1 pass on the 96x48x48 smoothed-Gaussian state (seed 0)."""
     import synth
     from oracle import gf_oracle as O
-    from threadpoolctl import threadpool_limits
     m = O.Mesh(*MID)
     f = O.cantilever_load(m)
     rho = synth.smoothed_gaussian_density(*MID, 0, 2.0, 0.4)
-    with threadpool_limits(limits=1):
-        t0 = time.perf_counter()
-        setup = O.SolverSetup(m, rho, p=P_SIMP, n_levels=5, restart=RESTART)
-        r = O.select_floor(setup, f, RHO0, LADDER, tau=TAU, kmax=KMAX, probe_iters=PROBE)
-        dt = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    setup = O.SolverSetup(m, rho, p=P_SIMP, n_levels=5, restart=RESTART)
+    r = O.select_floor(setup, f, RHO0, LADDER, tau=TAU, kmax=KMAX, probe_iters=PROBE)
+    dt = time.perf_counter() - t0
     return {"seconds": dt, "accepted": int(r.status == O.ACCEPTED), "value": int(r.status == O.ACCEPTED) / dt,
-            "unit": UNIT, "threads": 1, "iters": [a.iters for a in r.attempts]}
+            "unit": UNIT, "iters": [a.iters for a in r.attempts]}
 
 
 def run_reference(args):
@@ -633,7 +664,9 @@ def run_b300(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.cpu_worker:
+        cpu_worker(args.cpu_worker)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_b300(args)

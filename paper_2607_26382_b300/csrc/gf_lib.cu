@@ -18,6 +18,7 @@
 #include "finecorr.cuh"
 #include "galerkin.cuh"
 #include "coarse_krylov.cuh"
+#include "modal.cuh"
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -130,6 +131,8 @@ struct gf_grid {
     long long nodes, ndof, nel;
     std::vector<Level> lv;
     gf::K0Param<double> K0d;
+    gf::ModalCoef Kmodal;             // K0 in the sum/difference basis (apply_modal_kernel)
+    int modal_chunk = 0;              // node planes per CTA of the modal FP64 K*u (0: dense stencil)
     gf::K0Param<float> K0f;
     gf::K0Pair K0p;                   // K0f with rows 3a, 3a+1 paired (node_stencil_f32x2_kernel)
     bool f32x2 = true;                // FP32 node stencil with paired FMAs (GF_F32X2=0: scalar FMAs)
@@ -949,6 +952,14 @@ int coarse_correct(gf_grid* g, int l, T* x, const T* xc, T* c, const T* r, doubl
 int applyK64(gf_grid* g, const double* u, double* y, const int* halt)
 {
     g->stats.apply_K_fp64++;
+    if (g->modal_chunk > 0) {   // modal factorisation of K0 (default; GF_MODAL=0: dense node stencil)
+        const dim3 grid((g->nx + 1 + gf::MODAL_BX - 2) / (gf::MODAL_BX - 1),
+                        (g->ny + 1 + gf::MODAL_BY - 2) / (gf::MODAL_BY - 1),
+                        (g->nz + 1 + g->modal_chunk - 1) / g->modal_chunk);
+        LAUNCH(g, grid, dim3(gf::MODAL_BX, gf::MODAL_BY), (gf::apply_modal_kernel<gf::MODAL_BX, gf::MODAL_BY>), u, y,
+               (const double*)g->lv[0].E64, g->lv[0].dims(), g->Kmodal, g->modal_chunk, halt);
+        return GF_OK;
+    }
     return stencil<double, double, gf::ST_APPLY>(g, 0, u, nullptr, y, g->lv[0].E64, g->K0d, 0.0, halt);
 }
 
@@ -1677,6 +1688,34 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     for (int q = 0; q < 576; ++q) {
         g->K0d.k[q] = K[q];
         g->K0f.k[q] = (float)K[q];
+    }
+    g->Kmodal = gf::modal_coef(E0, nu);
+    {   // modal FP64 K*u (GF_MODAL=0: the dense node stencil): node planes per CTA chosen so
+        // that the CTAs fill whole waves, each CTA costing one element step per plane + 1
+        const char* e = getenv("GF_MODAL");
+        if (!(e && e[0] == '0')) {
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per_sm, gf::apply_modal_kernel<gf::MODAL_BX, gf::MODAL_BY>, gf::MODAL_BX * gf::MODAL_BY, 0) !=
+                cudaSuccess || per_sm < 1)
+                per_sm = 1;
+            const long long tiles = (long long)((nx + 1 + gf::MODAL_BX - 2) / (gf::MODAL_BX - 1)) *
+                                    ((ny + 1 + gf::MODAL_BY - 2) / (gf::MODAL_BY - 1));
+            const int NZ = nz + 1;
+            double best = 1e300;
+            for (int c = 1; c <= NZ; ++c) {
+                const int Lc = (NZ + c - 1) / c;
+                const long long ctas = tiles * ((NZ + Lc - 1) / Lc);
+                const long long waves = (ctas + (long long)g->sms * per_sm - 1) / ((long long)g->sms * per_sm);
+                const double cost = (double)waves * (Lc + 1);
+                if (cost < best) {
+                    best = cost;
+                    g->modal_chunk = Lc;
+                }
+            }
+            const char* ch = getenv("GF_MODAL_CHUNK");   // forced chunk (tests of the launch shape)
+            if (ch && atoi(ch) > 0) g->modal_chunk = std::min(atoi(ch), NZ);
+        }
     }
     for (int a = 0; a < 8; ++a)
         for (int bl = 0; bl < 8; ++bl)

@@ -1,0 +1,215 @@
+// FP64 matrix-free K*u through the modal (sum/difference) factorisation of K0.
+//
+// The frozen operator of Eq. (frozen_operator) (arXiv 2607.26382) is
+// y = sum_e E_e P_e^T K0 P_e u with one 24x24 hex8 stiffness K0. Write the trilinear
+// field of an element in the product basis P_beta = p_bx(x) p_by(y) p_bz(z),
+// p_0 = 1, p_1 = 2s - 1 on the unit cube. Its coefficients are the unnormalised
+// sums and differences m = H u_e (H: the 8x8 matrix of signs prod_k s_k^beta_k,
+// s = -1 at offset 0, +1 at offset 1), so K0 = H^T Km H / 64. In that basis the 1D
+// mass, stiffness and mixed integrals are diag(1, 1/3), diag(0, 4) and one entry 2,
+// so Km = a(P_alpha e_d, P_beta e_c) has 45 non-zeros of 9 kinds (lambda, mu, and
+// powers of 1/3):
+//   diagonal (c, beta):  4 (lam + mu) b_c 3^-n + 4 mu (b_c 3^-n + n 3^-(b_c + n - 1))
+//                        with b_c = beta_c and n = number of other axes with beta = 1;
+//   cross (c, d != c):   beta_c = 1, beta_d = 0:  4 lam w(beta_o) m_d[beta ^ e_c ^ e_d]
+//                        beta_c = 0, beta_d = 1:  4 mu  w(beta_o) m_d[beta ^ e_c ^ e_d]
+//                        (o the third axis, w(0) = 1, w(1) = 1/3).
+// (Checked numerically against the Gauss-integrated K0 on the host: both are the
+// exact integral, and they agree to rounding.)
+//
+// Cost per element: the sum/difference network forward (48 FP64 adds, a face of
+// the column's next node plane transformed once and reused by the element above),
+// 9 scalings by E_e and 45 multiply-adds in modal space, the transposed network back
+// (60), and the 9 adds of the node gather -- about 170 FP64 instructions against the
+// 576 FMAs of the dense 24x24 product. B300 issues FP64 at 1/64 of the FP32 rate, so
+// this count, not memory, bounds the kernel.
+//
+// Layout of the work: a CTA owns BX x BY element columns (a tile plus a one-element
+// halo on the low x and y sides) and walks them up a chunk of node planes. At each
+// step every thread forms its element's forces, sums its bottom face with the top
+// face of the element below (carried in registers, in modal form), transforms the
+// face back to its four nodes and stores them in shared memory; after a barrier each
+// node of the (BX-1) x (BY-1) output tile adds the four columns around it in a fixed
+// order. No atomics: the result does not depend on the launch shape.
+#pragma once
+#include <cuda_runtime.h>
+#include "stencil.cuh"
+
+namespace gf {
+
+struct ModalCoef {
+    double diag[6];    // [b_c * 3 + n], entry 0 (the constant mode) unused; already / 64
+    double cross[4];   // [lam w=1, lam w=1/3, mu w=1, mu w=1/3], already / 64
+};
+
+__host__ inline ModalCoef modal_coef(double E0, double nu)
+{
+    const double lam = E0 * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    const double mu = E0 / (2.0 * (1.0 + nu));
+    ModalCoef c{};
+    const double inv3[3] = {1.0, 1.0 / 3.0, 1.0 / 9.0};
+    for (int bc = 0; bc < 2; ++bc)
+        for (int n = 0; n < 3; ++n) {
+            double v = 4.0 * (lam + mu) * bc * inv3[n] + 4.0 * mu * bc * inv3[n];
+            if (n >= 1) v += 4.0 * mu * n * (bc ? inv3[n] : inv3[n - 1]);
+            c.diag[bc * 3 + n] = v / 64.0;
+        }
+    c.cross[0] = 4.0 * lam / 64.0;
+    c.cross[1] = 4.0 * lam / 3.0 / 64.0;
+    c.cross[2] = 4.0 * mu / 64.0;
+    c.cross[3] = 4.0 * mu / 3.0 / 64.0;
+    return c;
+}
+
+constexpr int MODAL_BX = 32, MODAL_BY = 16;   // element columns per CTA (threads)
+
+// 2D sum/difference transform of a face: v[x + 2y] -> f[bx + 2by] = sum s_x^bx s_y^by v.
+__device__ __forceinline__ void face_fwd(const double v[4], double f[4])
+{
+    const double sx0 = v[1] + v[0], dx0 = v[1] - v[0];
+    const double sx1 = v[3] + v[2], dx1 = v[3] - v[2];
+    f[0] = sx0 + sx1;
+    f[2] = sx1 - sx0;
+    f[1] = dx0 + dx1;
+    f[3] = dx1 - dx0;
+}
+
+// Its transpose: f[bx + 2by] -> v[x + 2y] = sum_beta s_x^bx s_y^by f[beta].
+__device__ __forceinline__ void face_inv(const double f[4], double v[4])
+{
+    const double lo0 = f[0] - f[2], hi0 = f[0] + f[2];   // bx = 0: y offset 0 / 1
+    const double lo1 = f[1] - f[3], hi1 = f[1] + f[3];   // bx = 1
+    v[0] = lo0 - lo1;
+    v[1] = lo0 + lo1;
+    v[2] = hi0 - hi1;
+    v[3] = hi0 + hi1;
+}
+
+template <int BX, int BY>
+__global__ void __launch_bounds__(BX * BY, 1)
+apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const double* __restrict__ E,
+                   GridDims d, ModalCoef C, int planes_per_chunk, const int* __restrict__ halt)
+{
+    if (halt != nullptr && *halt != 0) return;
+    __shared__ double part[12][BY][BX];     // [corner * 3 + comp][column]
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
+    const int i0 = blockIdx.x * (BX - 1), j0 = blockIdx.y * (BY - 1);
+    const int k0 = blockIdx.z * planes_per_chunk;
+    const int k1 = min(NZ, k0 + planes_per_chunk);
+    const int ex = i0 - 1 + tx, ey = j0 - 1 + ty;         // this thread's element column
+    const bool col = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
+    const long long plane = (long long)NX * NY;
+
+    // face transform of node plane kz for this column (zero outside the domain; the
+    // clamped face x = 0 reads as 0)
+    auto load_face = [&](int kz, double f[3][4]) {
+        double v[3][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ni = ex + (q & 1), nj = ey + (q >> 1);
+            const bool ok = col && kz >= 0 && kz < NZ && ni >= 1;
+            const long long n = ni + (long long)NX * nj + plane * kz;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[c][q] = ok ? __ldg(u + 3 * n + c) : 0.0;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) face_fwd(v[c], f[c]);
+    };
+
+    double bot[3][4];     // modal face of the current element's bottom node plane
+    double carry[3][4];   // modal face forces of the element below at that plane
+    load_face(k0 - 1, bot);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) carry[c][q] = 0.0;
+
+    for (int ez = k0 - 1; ez < k1; ++ez) {
+        double top[3][4];
+        load_face(ez + 1, top);
+        double face[3][4];    // modal forces of node plane ez from this column
+        if (col && ez >= 0 && ez < d.nz) {
+            // m[c][beta], beta = bx + 2 by + 4 bz: z stage of the sum/difference network
+            double m[3][8];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    m[c][q] = top[c][q] + bot[c][q];
+                    m[c][q + 4] = top[c][q] - bot[c][q];
+                }
+            const double s = __ldg(E + ex + (long long)d.nx * (ey + (long long)d.ny * ez));
+            double sd[6], sc[4];
+#pragma unroll
+            for (int k = 1; k < 6; ++k) sd[k] = s * C.diag[k];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sc[k] = s * C.cross[k];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double G[8];
+#pragma unroll
+                for (int beta = 0; beta < 8; ++beta) {
+                    const int bc = (beta >> c) & 1;
+                    const int n = ((beta >> ((c + 1) % 3)) & 1) + ((beta >> ((c + 2) % 3)) & 1);
+                    double t = (bc == 0 && n == 0) ? 0.0 : sd[bc * 3 + n] * m[c][beta];
+#pragma unroll
+                    for (int dd = 1; dd < 3; ++dd) {
+                        const int dc = (c + dd) % 3;
+                        const int o = 3 - c - dc;
+                        const int bd = (beta >> dc) & 1;
+                        if (bc != bd) {
+                            const int alpha = beta ^ (1 << c) ^ (1 << dc);
+                            const int k = (bc ? 0 : 2) + ((beta >> o) & 1);
+                            t = fma(sc[k], m[dc][alpha], t);
+                        }
+                    }
+                    G[beta] = t;
+                }
+                // z stage of the transposed network: bottom face G0 - G1, top face G0 + G1
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    face[c][q] = carry[c][q] + (G[q] - G[q + 4]);
+                    carry[c][q] = G[q] + G[q + 4];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    face[c][q] = carry[c][q];
+                    carry[c][q] = 0.0;
+                }
+        }
+        // node plane ez: this column's four corner forces, then the gather
+        __syncthreads();   // the previous step's gather has read `part`
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double v[4];
+            face_inv(face[c], v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) part[q * 3 + c][ty][tx] = v[q];
+        }
+        __syncthreads();
+        const int ni = i0 + tx, nj = j0 + ty;
+        if (ez >= k0 && tx < BX - 1 && ty < BY - 1 && ni < NX && nj < NY) {
+            const long long n = ni + (long long)NX * nj + plane * ez;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                // node (ni, nj) is corner (1,1) of column (tx, ty), (0,1) of (tx+1, ty),
+                // (1,0) of (tx, ty+1) and (0,0) of (tx+1, ty+1)
+                double acc = part[3 * 3 + c][ty][tx] + part[2 * 3 + c][ty][tx + 1];
+                acc += part[1 * 3 + c][ty + 1][tx];
+                acc += part[0 * 3 + c][ty + 1][tx + 1];
+                y[3 * n + c] = (ni == 0) ? 0.0 : acc;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bot[c][q] = top[c][q];
+    }
+}
+
+}  // namespace gf
