@@ -76,6 +76,55 @@ batch_gj_step_kernel(BatchTables t, const int* __restrict__ active, int s)
     gj_tile(from_w ? t.W[i] : t.A[i], from_w ? t.A[i] : t.W[i], n, k, p0, q0);
 }
 
+// The blocked symmetric sweep (sym_gj_kernel) on every state's matrix at once: step s
+// takes pivots SGJ_B*s .. SGJ_B*s + SGJ_B - 1. State i runs ceil(n_i/SGJ_B) steps and
+// starts in W_i when that count is odd, so its last step writes the upper triangle of A_i.
+// The P buffers of state i sit past its second matrix buffer, W_i + n_i^2 (as for one grid).
+__global__ void __launch_bounds__(256)
+batch_sym_gj_kernel(BatchTables t, const int* __restrict__ active, int s)
+{
+    const int i = blockIdx.z;
+    if (!active[i] || blockIdx.y > blockIdx.x) return;
+    const int n = t.n[i], k = SGJ_B * s;
+    if (k >= n || (int)blockIdx.y * SGJ_T >= n || (int)blockIdx.x * SGJ_T >= n) return;   // uniform over the block
+    const int steps = (n + SGJ_B - 1) / SGJ_B;
+    const bool from_w = ((steps & 1) ^ (s & 1)) != 0;
+    double* Pb = t.W[i] + (long long)n * n;
+    sym_gj_tile(from_w ? t.W[i] : t.A[i], from_w ? t.A[i] : t.W[i], n, k, blockIdx.y, blockIdx.x,
+                Pb + SGJ_B * SGJ_B * (s & 1), Pb + SGJ_B * SGJ_B * ((s + 1) & 1));
+}
+
+// P of every active state's first pivot block (from the start buffer of its sweep).
+__global__ void __launch_bounds__(256) batch_sym_gj_first_kernel(BatchTables t, const int* __restrict__ active)
+{
+    const int i = blockIdx.x;
+    if (!active[i]) return;
+    const int n = t.n[i];
+    const int steps = (n + SGJ_B - 1) / SGJ_B;
+    const double* M = (steps & 1) ? t.W[i] : t.A[i];
+    __shared__ double S[SGJ_B][SGJ_B];
+    const int tid = threadIdx.x, bb = min(SGJ_B, n);
+    const int bi = tid / SGJ_B, bj = tid % SGJ_B;
+    if (tid < SGJ_B * SGJ_B && bi < bb && bj < bb) S[bi][bj] = M[(long long)min(bi, bj) * n + max(bi, bj)];
+    __syncthreads();
+    sgj_invert_block(S, bb, tid);
+    if (tid < SGJ_B * SGJ_B) t.W[i][(long long)n * n + tid] = (bi < bb && bj < bb) ? S[bi][bj] : 0.0;
+}
+
+// Lower triangles of the active states' A_i from their upper triangles (in place).
+__global__ void batch_sym_mirror_kernel(BatchTables t, const int* __restrict__ active)
+{
+    const int i = blockIdx.y;
+    if (!active[i]) return;
+    const int n = t.n[i];
+    double* A = t.A[i];
+    const long long nn = (long long)n * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(e / n), q = (int)(e % n);
+        if (p > q) A[e] = A[(long long)q * n + p];
+    }
+}
+
 }  // namespace gf
 
 struct gf_batch {
@@ -358,7 +407,8 @@ int batch_set_floor(gf_batch* b, const std::vector<int>& active, const std::vect
         if (rc != GF_OK) return rc;
         Level& c = g->lv[g->L - 1];
         const long long n = g->nc;
-        double* start = (((n + 1) / 2) & 1) ? g->Agj : g->Ainv;   // see batch_gj_step_kernel
+        const long long steps = g->sym_gj ? (n + gf::SGJ_B - 1) / gf::SGJ_B : (n + 1) / 2;
+        double* start = (steps & 1) ? g->Agj : g->Ainv;   // see batch_gj_step_kernel / batch_sym_gj_kernel
         LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, (const double*)c.E64, start, c.dims(), g->K0d);
         LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, start, c.dims());
     }
@@ -366,6 +416,21 @@ int batch_set_floor(gf_batch* b, const std::vector<int>& active, const std::vect
     int nmax = 0;
     for (int i = 0; i < B; ++i)
         if (active[i]) nmax = std::max(nmax, b->g[i]->nc);
+    if (b->g[0]->sym_gj) {   // the single grid's algorithm, so that states stay bit-identical to it
+        const unsigned st = (unsigned)((nmax + gf::SGJ_T - 1) / gf::SGJ_T);
+        gf::batch_sym_gj_first_kernel<<<B, 256, 0, b->stream>>>(b->tab, b->d_active);
+        b->launches += 1;
+        CK(cudaGetLastError());
+        for (int s = 0; gf::SGJ_B * s < nmax; ++s) {
+            gf::batch_sym_gj_kernel<<<dim3(st, st, B), dim3(16, 16), 0, b->stream>>>(b->tab, b->d_active, s);
+            b->launches += 1;
+            CK(cudaGetLastError());
+        }
+        gf::batch_sym_mirror_kernel<<<dim3((unsigned)std::max(1, b->sms), B), 256, 0, b->stream>>>(b->tab, b->d_active);
+        b->launches += 1;
+        CK(cudaGetLastError());
+        return GF_OK;
+    }
     const unsigned tiles = (unsigned)((nmax + gf::GJ_T - 1) / gf::GJ_T);
     for (int s = 0; 2 * s < nmax; ++s) {
         gf::batch_gj_step_kernel<<<dim3(tiles, tiles, B), dim3(gf::GJ_T, gf::GJ_R), 0, b->stream>>>(b->tab, b->d_active, s);

@@ -132,7 +132,9 @@ struct gf_grid {
     std::vector<Level> lv;
     gf::K0Param<double> K0d;
     gf::ModalCoef Kmodal;             // K0 in the sum/difference basis (apply_modal_kernel)
-    int modal_chunk = 0;              // node planes per CTA of the modal FP64 K*u (0: dense stencil)
+    int4* modal_items = nullptr;      // work items of the modal FP64 K*u (device; null: dense stencil)
+    int modal_n = 0, modal_bx = 32;   // item count; CTA tile 32 x 16 or 16 x 32 element columns
+    bool sym_gj = true;               // coarsest inverse by the blocked symmetric sweep (GF_SYM_GJ=0: two-pivot form)
     gf::K0Param<float> K0f;
     gf::K0Pair K0p;                   // K0f with rows 3a, 3a+1 paired (node_stencil_f32x2_kernel)
     bool f32x2 = true;                // FP32 node stencil with paired FMAs (GF_F32X2=0: scalar FMAs)
@@ -952,12 +954,13 @@ int coarse_correct(gf_grid* g, int l, T* x, const T* xc, T* c, const T* r, doubl
 int applyK64(gf_grid* g, const double* u, double* y, const int* halt)
 {
     g->stats.apply_K_fp64++;
-    if (g->modal_chunk > 0) {   // modal factorisation of K0 (default; GF_MODAL=0: dense node stencil)
-        const dim3 grid((g->nx + 1 + gf::MODAL_BX - 2) / (gf::MODAL_BX - 1),
-                        (g->ny + 1 + gf::MODAL_BY - 2) / (gf::MODAL_BY - 1),
-                        (g->nz + 1 + g->modal_chunk - 1) / g->modal_chunk);
-        LAUNCH(g, grid, dim3(gf::MODAL_BX, gf::MODAL_BY), (gf::apply_modal_kernel<gf::MODAL_BX, gf::MODAL_BY>), u, y,
-               (const double*)g->lv[0].E64, g->lv[0].dims(), g->Kmodal, g->modal_chunk, halt);
+    if (g->modal_items) {   // modal factorisation of K0 (default; GF_MODAL=0: dense node stencil)
+        if (g->modal_bx == 32)
+            LAUNCH(g, g->modal_n, dim3(32, 16), (gf::apply_modal_kernel<32, 16>), u, y, (const double*)g->lv[0].E64,
+                   g->lv[0].dims(), g->Kmodal, (const int4*)g->modal_items, halt);
+        else
+            LAUNCH(g, g->modal_n, dim3(16, 32), (gf::apply_modal_kernel<16, 32>), u, y, (const double*)g->lv[0].E64,
+                   g->lv[0].dims(), g->Kmodal, (const int4*)g->modal_items, halt);
         return GF_OK;
     }
     return stencil<double, double, gf::ST_APPLY>(g, 0, u, nullptr, y, g->lv[0].E64, g->K0d, 0.0, halt);
@@ -1080,6 +1083,21 @@ int build_coarse_inverse(gf_grid* g)
     else
         LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, c.E64, src, c.dims(), K);
     LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, src, c.dims());
+    if (g->sym_gj) {   // blocked symmetric sweep on the upper triangle, then the mirror into Ainv
+        const unsigned tiles = (unsigned)((n + gf::SGJ_T - 1) / gf::SGJ_T);
+        double* Pb = g->Agj + n * n;   // two P buffers past the matrix
+        LAUNCH(g, 1, 256, gf::sym_gj_first_kernel, (const double*)src, (int)n, Pb);
+        for (long long k = 0; k < n; k += gf::SGJ_B) {
+            double* dst = (src == g->Ainv) ? g->Agj : g->Ainv;
+            const int s = (int)(k / gf::SGJ_B);
+            LAUNCH(g, dim3(tiles, tiles), dim3(16, 16), gf::sym_gj_kernel, (const double*)src, dst, (int)n, (int)k,
+                   (const double*)(Pb + gf::SGJ_B * gf::SGJ_B * (s & 1)), Pb + gf::SGJ_B * gf::SGJ_B * ((s + 1) & 1));
+            src = dst;
+        }
+        LAUNCH(g, std::min<long long>(nblk(n * n), 4LL * g->sms), 256, gf::sym_mirror_kernel, (const double*)src,
+               g->Ainv, (int)n);
+        return GF_OK;
+    }
     const unsigned tiles = (unsigned)((n + gf::GJ_T - 1) / gf::GJ_T);
     for (int k = 0; k < n; k += 2) {
         double* dst = (src == g->Ainv) ? g->Agj : g->Ainv;
@@ -1658,6 +1676,11 @@ extern "C" {
 
 const char* gf_last_error(void) { return g_err.c_str(); }
 
+}  // extern "C"
+namespace {
+int modal_autotune(gf_grid* g);
+}
+extern "C" {
 int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int levels, void* stream,
                    gf_grid** out)
 {
@@ -1690,31 +1713,33 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         g->K0f.k[q] = (float)K[q];
     }
     g->Kmodal = gf::modal_coef(E0, nu);
-    {   // modal FP64 K*u (GF_MODAL=0: the dense node stencil): node planes per CTA chosen so
-        // that the CTAs fill whole waves, each CTA costing one element step per plane + 1
+    {
+        const char* e = getenv("GF_SYM_GJ");
+        g->sym_gj = !(e && e[0] == '0');
+    }
+    {   // modal FP64 K*u (GF_MODAL=0: the dense node stencil); GF_MODAL_CHUNK=<planes> forces
+        // runs of that many node planes per CTA and GF_MODAL_BX=32/16 the tile shape (tests)
         const char* e = getenv("GF_MODAL");
         if (!(e && e[0] == '0')) {
             int per_sm = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &per_sm, gf::apply_modal_kernel<gf::MODAL_BX, gf::MODAL_BY>, gf::MODAL_BX * gf::MODAL_BY, 0) !=
-                cudaSuccess || per_sm < 1)
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gf::apply_modal_kernel<32, 16>,
+                                                              gf::MODAL_THREADS, 0) != cudaSuccess ||
+                per_sm < 1)
                 per_sm = 1;
-            const long long tiles = (long long)((nx + 1 + gf::MODAL_BX - 2) / (gf::MODAL_BX - 1)) *
-                                    ((ny + 1 + gf::MODAL_BY - 2) / (gf::MODAL_BY - 1));
-            const int NZ = nz + 1;
-            double best = 1e300;
-            for (int c = 1; c <= NZ; ++c) {
-                const int Lc = (NZ + c - 1) / c;
-                const long long ctas = tiles * ((NZ + Lc - 1) / Lc);
-                const long long waves = (ctas + (long long)g->sms * per_sm - 1) / ((long long)g->sms * per_sm);
-                const double cost = (double)waves * (Lc + 1);
-                if (cost < best) {
-                    best = cost;
-                    g->modal_chunk = Lc;
-                }
-            }
-            const char* ch = getenv("GF_MODAL_CHUNK");   // forced chunk (tests of the launch shape)
-            if (ch && atoi(ch) > 0) g->modal_chunk = std::min(atoi(ch), NZ);
+            const char* ch = getenv("GF_MODAL_CHUNK");
+            const char* bxs = getenv("GF_MODAL_BX");
+            const int forced = ch ? std::max(0, atoi(ch)) : 0;
+            double c32 = 0, c16 = 0;
+            std::vector<int4> i32 = gf::modal_plan(nx, ny, nz, 32, 16, g->sms * per_sm, forced, &c32);
+            std::vector<int4> i16 = gf::modal_plan(nx, ny, nz, 16, 32, g->sms * per_sm, forced, &c16);
+            const bool use32 = bxs ? atoi(bxs) == 32 : c32 <= c16;
+            const std::vector<int4>& items = use32 ? i32 : i16;
+            g->modal_bx = use32 ? 32 : 16;
+            g->modal_n = (int)items.size();
+            if (alloc((void**)&g->modal_items, sizeof(int4) * items.size()) != GF_OK) return fail(GF_ERR_OOM);
+            if (cudaMemcpy(g->modal_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+                return fail(set_err(GF_ERR_CUDA, "modal work items"));
         }
     }
     for (int a = 0; a < 8; ++a)
@@ -1826,7 +1851,7 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     }
     int r = GF_OK;
     g->nbr = (int)std::min<long long>(2LL * g->sms, std::max<long long>(1, (g->ndof + 1023) / 1024));
-    if ((r = allocT(&g->Ainv, (size_t)g->nc * g->nc)) || (r = allocT(&g->Agj, (size_t)g->nc * g->nc)) ||
+    if ((r = allocT(&g->Ainv, (size_t)g->nc * g->nc)) || (r = allocT(&g->Agj, (size_t)g->nc * g->nc + 2 * gf::SGJ_B * gf::SGJ_B)) ||
         (r = allocT(&g->dflag, 4)) || (r = allocT(&g->rho64, g->nel)) ||
         (r = allocT(&g->rho16, g->nel)) || (r = allocT(&g->work, g->ndof)) ||
         (r = allocT(&g->partial, (size_t)g->nbr * 40)) || (r = allocT(&g->st, 1)) || (r = allocT(&g->gst, 1)) ||
@@ -1846,9 +1871,101 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         const char* e = getenv("GF_GRAPHS");
         g->use_graphs = !(e && e[0] == '0');
     }
+    if (g->modal_items && !getenv("GF_MODAL_CHUNK") && !getenv("GF_MODAL_BX"))
+        if ((r = modal_autotune(g)) != GF_OK) return fail(r);
     *out = g;
     return GF_OK;
 }
+
+}  // extern "C"
+namespace {
+// Time the modal FP64 K*u under a few launch plans -- the cheapest ones by modal_plan's
+// cost model over both tile shapes and several run lengths -- and keep the fastest. The
+// plan changes which CTA computes what, never the arithmetic of a node, so K*u does not
+// depend on it. Runs once per grid, on zeroed level-0 scratch, on the grid's stream.
+int modal_autotune(gf_grid* g)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gf::apply_modal_kernel<32, 16>, gf::MODAL_THREADS, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    struct Cand {
+        int bx;
+        double cost;
+        std::vector<int4> items;
+    };
+    std::vector<Cand> cand;
+    const int NZ = g->nz + 1;
+    for (int bx : {32, 16})
+        for (int L : {0, 2, 3, 4, 6, 8, 12, 16, 24, 33, 48, 64}) {
+            if (L > NZ) continue;
+            Cand c{bx, 0.0, {}};
+            c.items = gf::modal_plan(g->nx, g->ny, g->nz, bx, gf::MODAL_THREADS / bx, g->sms * per_sm, L, &c.cost);
+            cand.push_back(std::move(c));
+        }
+    std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.cost < b.cost; });
+    if (cand.size() > 6) cand.resize(6);
+    size_t maxn = 0;
+    for (const Cand& c : cand) maxn = std::max(maxn, c.items.size());
+    int4* dev = nullptr;
+    RET(alloc((void**)&dev, sizeof(int4) * maxn));
+    Level& f = g->lv[0];
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = GF_OK;
+    float best = 1e30f;
+    int best_i = -1;
+    auto run = [&](const Cand& c) {
+        if (c.bx == 32)
+            gf::apply_modal_kernel<32, 16><<<(unsigned)c.items.size(), dim3(32, 16), 0, g->stream>>>(
+                f.x64, f.t64, f.E64, f.dims(), g->Kmodal, dev, nullptr);
+        else
+            gf::apply_modal_kernel<16, 32><<<(unsigned)c.items.size(), dim3(16, 32), 0, g->stream>>>(
+                f.x64, f.t64, f.E64, f.dims(), g->Kmodal, dev, nullptr);
+    };
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMemsetAsync(f.E64, 0, sizeof(double) * f.nel, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(f.x64, 0, sizeof(double) * f.ndof, g->stream) != cudaSuccess)
+        rc = set_err(GF_ERR_CUDA, "modal autotune set-up");
+    for (size_t i = 0; rc == GF_OK && i < cand.size(); ++i) {
+        const Cand& c = cand[i];
+        if (cudaMemcpyAsync(dev, c.items.data(), sizeof(int4) * c.items.size(), cudaMemcpyHostToDevice, g->stream) !=
+            cudaSuccess) {
+            rc = set_err(GF_ERR_CUDA, "modal autotune items");
+            break;
+        }
+        run(c);
+        cudaEventRecord(e0, g->stream);
+        for (int r = 0; r < 3; ++r) run(c);
+        cudaEventRecord(e1, g->stream);
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+            cudaGetLastError() != cudaSuccess) {
+            rc = set_err(GF_ERR_CUDA, "modal autotune launch");
+            break;
+        }
+        if (ms < best) {
+            best = ms;
+            best_i = (int)i;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(dev);
+    RET(rc);
+    if (best_i >= 0) {
+        const Cand& c = cand[best_i];
+        cudaFree(g->modal_items);
+        g->modal_items = nullptr;
+        RET(alloc((void**)&g->modal_items, sizeof(int4) * c.items.size()));
+        CK(cudaMemcpy(g->modal_items, c.items.data(), sizeof(int4) * c.items.size(), cudaMemcpyHostToDevice));
+        g->modal_n = (int)c.items.size();
+        g->modal_bx = c.bx;
+    }
+    return GF_OK;
+}
+}  // namespace
+extern "C" {
 
 int gf_destroy_grid(gf_grid* g)
 {
@@ -1873,6 +1990,7 @@ int gf_destroy_grid(gf_grid* g)
     cudaFree(g->lz);
     cudaFree(g->lzv);
     cudaFree(g->Edf);
+    cudaFree(g->modal_items);
     cudaFree(g->B3);
     cudaFree(g->Btc);
     cudaFree(g->oc_rho); cudaFree(g->oc_dc); cudaFree(g->oc_dcx); cudaFree(g->oc_dvx); cudaFree(g->oc_ones);

@@ -464,4 +464,149 @@ gj_step_kernel(const double* __restrict__ Ain, double* __restrict__ Aout, int n,
     gj_tile(Ain, Aout, n, k, blockIdx.y * GJ_T, blockIdx.x * GJ_T);
 }
 
+// Symmetric blocked Gauss-Jordan (the sweep on a block of SGJ_B pivots per launch),
+// keeping only the upper triangle. With the pivots K = {0..k-1} already swept the
+// matrix is [[A_KK^-1, A_KK^-1 A_KU], [-A_UK A_KK^-1, S]] (S the Schur complement,
+// symmetric), so its upper triangle determines it. Sweeping the next block B with
+// P = (M_BB)^-1 and, for p outside B, V_p = M_{p,B} (read from the upper triangle) and
+// W_p = P V_p gives, for p <= q:
+//   p, q in B:        P
+//   p in B, q > B:    (W_q)_p
+//   p < B, q in B:    -(W_p)_q
+//   otherwise:        M_pq - s V_p . W_q,  s = -1 when q < k (both already swept), else +1.
+// Every entry costs SGJ_B FMAs per launch on n^2/2 entries: n^3/2 FMAs in all, half of
+// the full-matrix two-pivot form. A block owns a SGJ_T x SGJ_T upper tile and forms W
+// for its columns (and rows, when the tile holds the pivot columns). P of each step is
+// computed once: the block holding the next pivot block on its diagonal inverts that
+// block from its own outputs and leaves P for the next launch in a small buffer
+// (sym_gj_first_kernel makes the first one).
+constexpr int SGJ_B = 8, SGJ_T = 64;
+
+// In-place inverse of the bb x bb SPD block S by the sweep (threads 0 .. SGJ_B^2 - 1 own
+// one entry each; every thread of the block must call it).
+__device__ __forceinline__ void sgj_invert_block(double (*S)[SGJ_B], int bb, int tid)
+{
+    const int bi = tid / SGJ_B, bj = tid % SGJ_B;
+    const bool own = tid < SGJ_B * SGJ_B && bi < bb && bj < bb;
+    for (int j = 0; j < bb; ++j) {
+        double nv = 0.0;
+        if (own) {
+            const double piv = S[j][j], rj = S[j][bj], ci = S[bi][j], old = S[bi][bj];
+            if (bi == j) nv = (bj == j) ? 1.0 / piv : rj / piv;
+            else nv = (bj == j) ? -ci / piv : old - ci * (rj / piv);
+        }
+        __syncthreads();
+        if (own) S[bi][bj] = nv;
+        __syncthreads();
+    }
+}
+
+// P of the first pivot block (pivots 0 .. SGJ_B-1) from the upper triangle of M. One block.
+__global__ void __launch_bounds__(256) sym_gj_first_kernel(const double* __restrict__ M, int n, double* __restrict__ Pout)
+{
+    __shared__ double S[SGJ_B][SGJ_B];
+    const int tid = threadIdx.x, bb = min(SGJ_B, n);
+    const int bi = tid / SGJ_B, bj = tid % SGJ_B;
+    if (tid < SGJ_B * SGJ_B && bi < bb && bj < bb) S[bi][bj] = M[(long long)min(bi, bj) * n + max(bi, bj)];
+    __syncthreads();
+    sgj_invert_block(S, bb, tid);
+    if (tid < SGJ_B * SGJ_B) Pout[tid] = (bi < bb && bj < bb) ? S[bi][bj] : 0.0;
+}
+
+__device__ __forceinline__ void sym_gj_tile(const double* __restrict__ Min, double* __restrict__ Mout, int n, int k,
+                                            int tp, int tq, const double* __restrict__ Pin, double* __restrict__ Pout)
+{
+    __shared__ double Pm[SGJ_B][SGJ_B], Pn[SGJ_B][SGJ_B];
+    __shared__ double Vp[SGJ_B][SGJ_T], Vq[SGJ_B][SGJ_T], Wq[SGJ_B][SGJ_T], Wp[SGJ_B][SGJ_T];
+    const int tid = threadIdx.y * 16 + threadIdx.x;
+    const int bb = min(SGJ_B, n - k);
+    const int p0 = tp * SGJ_T, q0 = tq * SGJ_T;
+    const int kn = k + SGJ_B, bbn = min(SGJ_B, n - kn);        // next pivot block
+    const bool next_here = bbn > 0 && tp == tq && kn / SGJ_T == tp;
+    if (tid < SGJ_B * SGJ_B) Pm[tid / SGJ_B][tid % SGJ_B] = Pin[tid];
+    // V for the tile's rows and columns (0 inside the pivot block and outside the matrix)
+    auto vrow = [&](int p, int i) -> double {
+        if (p >= n || i >= bb) return 0.0;
+        if (p < k) return Min[(long long)p * n + k + i];
+        if (p >= k + bb) return Min[(long long)(k + i) * n + p];
+        return 0.0;
+    };
+    for (int e = tid; e < SGJ_B * SGJ_T; e += 256) {
+        const int i = e / SGJ_T, r = e % SGJ_T;
+        Vp[i][r] = vrow(p0 + r, i);
+        Vq[i][r] = vrow(q0 + r, i);
+    }
+    __syncthreads();
+    const bool need_wp = q0 < k + bb && q0 + SGJ_T > k;   // the tile holds pivot columns
+    for (int e = tid; e < SGJ_B * SGJ_T; e += 256) {
+        const int i = e / SGJ_T, r = e % SGJ_T;
+        double a = 0.0, c = 0.0;
+        for (int j = 0; j < bb; ++j) {
+            a = fma(Pm[i < bb ? i : 0][j], Vq[j][r], a);
+            if (need_wp) c = fma(Pm[i < bb ? i : 0][j], Vp[j][r], c);
+        }
+        Wq[i][r] = (i < bb) ? a : 0.0;
+        Wp[i][r] = (i < bb) ? c : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = threadIdx.y + 16 * a, p = p0 + r;
+        if (p >= n) break;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int c = threadIdx.x + 16 * b, q = q0 + c;
+            if (q >= n || q < p) continue;
+            const bool inp = p >= k && p < k + bb, inq = q >= k && q < k + bb;
+            double out;
+            if (inp && inq) {
+                out = Pm[p - k][q - k];
+            } else if (inp) {
+                out = Wq[p - k][c];
+            } else if (inq) {
+                out = -Wp[q - k][r];
+            } else {
+                double dot = 0.0;
+#pragma unroll
+                for (int i = 0; i < SGJ_B; ++i) dot = fma(Vp[i][r], Wq[i][c], dot);
+                const double old = Min[(long long)p * n + q];
+                out = (q < k) ? old + dot : old - dot;
+            }
+            Mout[(long long)p * n + q] = out;
+            if (next_here && p >= kn && q < kn + bbn) {   // (p <= q, so p < kn + bbn too)
+                Pn[p - kn][q - kn] = out;
+                Pn[q - kn][p - kn] = out;
+            }
+        }
+    }
+    if (next_here) {   // uniform over the block
+        __syncthreads();
+        sgj_invert_block(Pn, bbn, tid);
+        if (tid < SGJ_B * SGJ_B) {
+            const int bi = tid / SGJ_B, bj = tid % SGJ_B;
+            Pout[tid] = (bi < bbn && bj < bbn) ? Pn[bi][bj] : 0.0;
+        }
+    }
+}
+
+// Pivots k .. k+SGJ_B-1 from Min into Mout (upper triangles) with P = Pin, leaving the next
+// block's P in Pout; grid: SGJ_T tiles, lower ones idle.
+__global__ void __launch_bounds__(256)
+sym_gj_kernel(const double* __restrict__ Min, double* __restrict__ Mout, int n, int k, const double* __restrict__ Pin,
+              double* __restrict__ Pout)
+{
+    if (blockIdx.y > blockIdx.x) return;
+    sym_gj_tile(Min, Mout, n, k, blockIdx.y, blockIdx.x, Pin, Pout);
+}
+
+// Full symmetric matrix from the upper triangle of U into A (A may be U).
+__global__ void sym_mirror_kernel(const double* __restrict__ U, double* __restrict__ A, int n)
+{
+    const long long nn = (long long)n * n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(e / n), q = (int)(e % n);
+        A[e] = (p <= q) ? U[e] : U[(long long)q * n + p];
+    }
+}
+
 }  // namespace gf

@@ -25,7 +25,8 @@
 // this count, not memory, bounds the kernel.
 //
 // Layout of the work: a CTA owns BX x BY element columns (a tile plus a one-element
-// halo on the low x and y sides) and walks them up a chunk of node planes. At each
+// halo on the low x and y sides; 32 x 16 or 16 x 32, whichever wastes fewer warps on
+// the grid) and walks them up a run of node planes. At each
 // step every thread forms its element's forces, sums its bottom face with the top
 // face of the element below (carried in registers, in modal form), transforms the
 // face back to its four nodes and stores them in shared memory; after a barrier each
@@ -33,6 +34,8 @@
 // order. No atomics: the result does not depend on the launch shape.
 #pragma once
 #include <cuda_runtime.h>
+#include <algorithm>
+#include <vector>
 #include "stencil.cuh"
 
 namespace gf {
@@ -61,7 +64,89 @@ __host__ inline ModalCoef modal_coef(double E0, double nu)
     return c;
 }
 
-constexpr int MODAL_BX = 32, MODAL_BY = 16;   // element columns per CTA (threads)
+constexpr int MODAL_THREADS = 512;   // element columns per CTA: 32 x 16 or 16 x 32
+
+// Work items of apply_modal_kernel<BX, BY> for a grid of nx x ny x nz elements on `slots`
+// concurrent CTAs. A CTA step costs the busiest of the SM's four sub-partitions (warp w
+// runs on w mod 4), counting the warps that hold at least one element column inside
+// the grid (a warp issues its FP64 instructions for 32 lanes whatever its active mask):
+// far-edge tiles whose whole warps fall outside are cheaper and take longer runs of
+// node planes, while a tile cut by the x edge costs as much as a full one. The planes of
+// every tile are cut into near-equal runs, and the run lengths are chosen to minimise
+// waves x (largest item cost), with (planes + 1) steps per run. *cost receives that
+// product. Plain host arithmetic, deterministic.
+inline std::vector<int4> modal_plan(int nx, int ny, int nz, int bx, int by, int slots, int forced_planes,
+                                    double* cost)
+{
+    const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
+    const int tx = (NX + bx - 2) / (bx - 1), ty = (NY + by - 2) / (by - 1);
+    std::vector<long long> v(tx * ty);
+    for (int b = 0; b < ty; ++b)
+        for (int a = 0; a < tx; ++a) {
+            long long per_smsp[4] = {0, 0, 0, 0};
+            for (int w = 0; w < bx * by / 32; ++w) {
+                bool any = false;
+                for (int l = 0; l < 32 && !any; ++l) {
+                    const int t = 32 * w + l, ex = a * (bx - 1) - 1 + t % bx, ey = b * (by - 1) - 1 + t / bx;
+                    any = ex >= 0 && ex < nx && ey >= 0 && ey < ny;
+                }
+                per_smsp[w % 4] += any;
+            }
+            v[b * tx + a] = 4 * std::max(std::max(per_smsp[0], per_smsp[1]), std::max(per_smsp[2], per_smsp[3]));
+        }
+    auto runs_for = [&](long long vt, long long cap) -> int {   // planes per run within the cap
+        if (forced_planes > 0) return std::min(forced_planes, NZ);
+        if (vt <= 0) return NZ;
+        return (int)std::max<long long>(1, std::min<long long>(NZ, cap / vt - 1));
+    };
+    auto count = [&](long long cap, long long* maxcost) {
+        long long n = 0, mc = 0;
+        for (long long vt : v) {
+            const int L = runs_for(vt, cap);
+            const int pieces = (NZ + L - 1) / L;
+            const int len = (NZ + pieces - 1) / pieces;
+            n += pieces;
+            mc = std::max(mc, std::max<long long>(vt, 1) * (len + 1));
+        }
+        *maxcost = mc;
+        return n;
+    };
+    long long best_cap = 0, vmax = 1;
+    double best = 1e300;
+    for (long long vt : v) vmax = std::max(vmax, vt);
+    for (int waves = 1; waves <= 16; ++waves) {
+        // smallest cap whose item count fits in `waves` rounds of the slots
+        long long lo = 2 * vmax, hi = vmax * (long long)(NZ + 1), mc;
+        if (count(hi, &mc) > (long long)waves * slots) continue;
+        while (lo < hi) {
+            const long long mid = (lo + hi) / 2;
+            if (count(mid, &mc) <= (long long)waves * slots) hi = mid;
+            else lo = mid + 1;
+        }
+        const long long n = count(hi, &mc);
+        const double t = (double)((n + slots - 1) / slots) * mc;
+        if (t < best) {
+            best = t;
+            best_cap = hi;
+        }
+        if (forced_planes > 0) break;
+    }
+    if (best_cap == 0) best_cap = vmax * (long long)(NZ + 1);
+    long long mc;
+    const long long n = count(best_cap, &mc);
+    if (cost) *cost = (double)((n + slots - 1) / slots) * mc;
+    std::vector<int4> items;
+    for (int b = 0; b < ty; ++b)
+        for (int a = 0; a < tx; ++a) {
+            const int L = runs_for(v[b * tx + a], best_cap);
+            const int pieces = (NZ + L - 1) / L;
+            for (int p = 0; p < pieces; ++p) {
+                const int z0 = (int)((long long)NZ * p / pieces), z1 = (int)((long long)NZ * (p + 1) / pieces);
+                items.push_back(make_int4(a, b, z0, z1));
+            }
+        }
+    return items;
+}
 
 // 2D sum/difference transform of a face: v[x + 2y] -> f[bx + 2by] = sum s_x^bx s_y^by v.
 __device__ __forceinline__ void face_fwd(const double v[4], double f[4])
@@ -85,18 +170,22 @@ __device__ __forceinline__ void face_inv(const double f[4], double v[4])
     v[3] = hi0 + hi1;
 }
 
+// One CTA per work item: node tile (x, y) of (BX-1) x (BY-1) nodes and node planes [z, w).
+// The host balances the items (modal_plan): tiles at the far edges of the grid hold fewer
+// element columns and take longer runs of planes, so that every CTA costs about the same.
 template <int BX, int BY>
-__global__ void __launch_bounds__(BX * BY, 1)
+__global__ void __launch_bounds__(MODAL_THREADS, 1)
 apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const double* __restrict__ E,
-                   GridDims d, ModalCoef C, int planes_per_chunk, const int* __restrict__ halt)
+                   GridDims d, ModalCoef C, const int4* __restrict__ items, const int* __restrict__ halt)
 {
     if (halt != nullptr && *halt != 0) return;
     __shared__ double part[12][BY][BX];     // [corner * 3 + comp][column]
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
-    const int i0 = blockIdx.x * (BX - 1), j0 = blockIdx.y * (BY - 1);
-    const int k0 = blockIdx.z * planes_per_chunk;
-    const int k1 = min(NZ, k0 + planes_per_chunk);
+    const int4 it = items[blockIdx.x];
+    const int i0 = it.x * (BX - 1), j0 = it.y * (BY - 1);
+    const int k0 = it.z;
+    const int k1 = min(NZ, it.w);
     const int ex = i0 - 1 + tx, ey = j0 - 1 + ty;         // this thread's element column
     const bool col = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
     const long long plane = (long long)NX * NY;

@@ -1,12 +1,14 @@
 """Run one operation of the library a few times on a synthetic state (a profiling target).
 
     python -m paper_2607_26382_b300.profile apply_k64 --grid 96 48 48 --levels 5 --reps 3
-    ops: apply_k64, apply_split, apply_k32, vcycle_mixed, vcycle_fp64, solve_mixed, select_mixed
+    ops: apply_k64, apply_split, apply_k32, vcycle_mixed, vcycle_fp64, solve_mixed, select_mixed, set_floor
     (--galerkin: the V-cycles on Galerkin coarse operators)
 
 The state is the smoothed-Gaussian density (sigma 2, 40% at floor) at rho_min 1e-6,
 p = 3, with the cantilever tip load. Used as the command under ncu so that a
-capture covers a known, small number of launches.
+capture covers a known, small number of launches. The repeated operation runs
+between cudaProfilerStart and cudaProfilerStop, so `ncu --profile-from-start off`
+captures it without the set-up (density, floor, coarsest inverse).
 """
 from __future__ import annotations
 
@@ -17,7 +19,7 @@ import sys
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("op", choices=["apply_k64", "apply_split", "apply_k32", "vcycle_mixed", "vcycle_fp64",
-                                   "solve_mixed", "select_mixed"])
+                                   "solve_mixed", "select_mixed", "set_floor"])
     ap.add_argument("--grid", type=int, nargs=3, default=[96, 48, 48])
     ap.add_argument("--levels", type=int, default=5)
     ap.add_argument("--reps", type=int, default=3)
@@ -45,6 +47,8 @@ def main(argv=None):
     y = torch.empty_like(x)
     f = torch.zeros_like(x)
     g.cantilever_load(f)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
     for _ in range(a.reps):
         if a.op == "apply_k64":
             g.apply_K(x, y)
@@ -56,6 +60,8 @@ def main(argv=None):
             g.vcycle(x, y, gf.GF_MIXED)
         elif a.op == "vcycle_fp64":
             g.vcycle(x, y, gf.GF_FP64)
+        elif a.op == "set_floor":
+            g.set_floor(1e-6)
         elif a.op == "solve_mixed":
             y.zero_()
             g.solve(f, y, prec=gf.GF_MIXED, outer=a.outer, kmax=a.kmax, fine_steps=a.fine)
@@ -63,6 +69,7 @@ def main(argv=None):
             g.set_density(torch.as_tensor(synth.smoothed_gaussian_density(nx, ny, nz, a.seed), device="cuda"), 3.0)
             g.select_floor(f, y, gf.policy_defaults(solve_prec=gf.GF_MIXED, solve_outer=a.outer))
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     print(f"{a.op} x{a.reps} on {nx}x{ny}x{nz}: ok", flush=True)
     g.close()
     return 0

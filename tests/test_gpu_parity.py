@@ -1024,16 +1024,16 @@ def test_full_size_select_floor_matches_oracle_record(gf, prec, outer):
 
 # ------------------------------------------------------------- modal FP64 K*u -----
 @pytest.mark.parametrize("chunk", ["0", "1", "3", "7"])
-@pytest.mark.parametrize("dims", [(40, 20, 10), (33, 17, 9), (1, 2, 2), (62, 30, 14), (31, 15, 4)])
+@pytest.mark.parametrize("dims", [(40, 20, 10, 2), (34, 18, 10, 2), (1, 2, 2, 1), (60, 28, 12, 3), (31, 14, 4, 1)])
 def test_modal_apply_matches_oracle_and_dense(gf, dims, chunk, monkeypatch):
     """The FP64 K*u through the sum/difference factorisation of K0 (the default operator of
     gf_apply_K) against the oracle's element-by-element product to 1e-10, on grids whose
     extents leave ragged CTA tiles (31 x 15 nodes per tile) and for forced chunks of 1, 3
     and 7 node planes per CTA (0: the library's own choice); and against the dense node
     stencil (GF_MODAL=0) to the same bound."""
-    nx, ny, nz = dims
+    nx, ny, nz, L = dims
     monkeypatch.setenv("GF_MODAL_CHUNK", chunk)
-    g, m, rho = make(gf, nx, ny, nz, 1, seed=nx + ny, rho_min=1e-6, kind="uniform")
+    g, m, rho = make(gf, nx, ny, nz, L, seed=nx + ny, rho_min=1e-6, kind="uniform")
     E = O.young_modulus(rho, 1e-6, 3.0)
     for seed in (5, 6):
         u = synth.random_vector(m.n_dof, seed)
@@ -1046,7 +1046,36 @@ def test_modal_apply_matches_oracle_and_dense(gf, dims, chunk, monkeypatch):
         assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
         assert np.all(got[m.fixed] == 0.0)
     monkeypatch.setenv("GF_MODAL", "0")
-    gd, _, _ = make(gf, nx, ny, nz, 1, seed=nx + ny, rho_min=1e-6, kind="uniform")
+    gd, _, _ = make(gf, nx, ny, nz, L, seed=nx + ny, rho_min=1e-6, kind="uniform")
     yd = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
     gd.apply_K(dev(u), yd)
     assert relerr(got, host(yd)) <= 1e-10
+
+
+# ------------------------------------------------------------- coarsest inverse -----
+@pytest.mark.parametrize("dims", [(16, 8, 8, 3), (24, 10, 6, 2), (2, 2, 2, 1), (8, 4, 4, 1), (12, 6, 6, 2)])
+def test_symmetric_blocked_inverse_matches_two_pivot_form(gf, dims, monkeypatch):
+    """The coarsest level's dense FP64 inverse by the blocked symmetric sweep (8 pivots per
+    launch on the upper triangle; default) against the two-pivot full-matrix Gauss-Jordan
+    (GF_SYM_GJ=0): FP64 V-cycles agree to 1e-10 relative, on coarsest levels whose size is
+    not always a multiple of the pivot block (135 / 936 / 81 / 675 / 336 DOFs); on one-level
+    grids the inverse is the whole operator's, and its direct solution meets the oracle's
+    guard."""
+    nx, ny, nz, L = dims
+    outs = []
+    for sym in ("1", "0"):
+        monkeypatch.setenv("GF_SYM_GJ", sym)
+        g, m, rho = make(gf, nx, ny, nz, L, seed=3, rho_min=1e-4, kind="bernoulli")
+        v = synth.random_vector(m.n_dof, 9)
+        z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        g.vcycle(dev(v), z, gf.GF_FP64)
+        outs.append(host(z))
+        if L == 1 and sym == "1":
+            f = O.cantilever_load(m)
+            res = g.conditioning(dev(f), iters=20)
+            E = O.young_modulus(rho, 1e-4, 3.0)
+            # the direct solution's recomputed residual is at rounding level
+            assert res["eta_direct"] <= 1e-9
+            ref = O.vcycle(O.build_hierarchy(m, E, 1), v * m.free)
+            assert relerr(outs[-1], ref) <= 1e-8
+    assert relerr(outs[0], outs[1]) <= 1e-10
