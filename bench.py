@@ -205,6 +205,8 @@ def profiled_traffic(profile, source, start, end):
 
 # kernel text spans hashed for the traffic figures
 FP64_KU_SPAN = ("stencil.cuh", "// (i, j, k) of node n", "// First smoothing sweep")
+MODAL_SPAN = ("modal.cuh", "// 2D sum/difference transform", "}  // namespace gf")
+MODAL_INSTR, MODAL_FLOPS = 171, 195     # FP64 instructions and flops per element of the modal K*u
 FP32_ST_SPAN = FP64_KU_SPAN                # both node-stencil bodies and their shared block update
 SPLIT_KU_SPAN = ("split_tc.cuh", "template <bool DD>", "}  // namespace gf")
 
@@ -545,22 +547,34 @@ def run_b300(args):
     t_k = timed_kernel(lambda: g.apply_K(x, y))
     t_32 = timed_kernel(lambda: g.apply_K_f32(xf, yf))
     t_s = timed_kernel(lambda: g.apply_K_split(x, y))
-    flops = 1152.0 * g.n_elem                  # 2*24*24 per element and application
+    flops = 1152.0 * g.n_elem                  # 2*24*24 per element and application (dense product)
     sm_max = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2032.0)
-    fp64_peak = 148 * 2 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    fp64_peak = 148 * 2 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FMAs only
     fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12
     hbm = measured_peaks().get("hbm_gbs", 6400.0)
+    # the modal K*u executes MODAL_INSTR FP64 instructions per element (48 adds forward,
+    # 9 scalings, 21 multiplies + 24 FMAs in modal space, 60 adds back, 9 adds of the node
+    # gather) = MODAL_FLOPS flops; its ceiling is the FP64 issue rate (2 FP64 instructions
+    # per clock and SM) times this mix's flops per instruction
+    modal_flops = MODAL_FLOPS * g.n_elem
+    modal_peak = 148 * 2 * sm_max * 1e6 * (MODAL_FLOPS / MODAL_INSTR) / 1e12
     # share of the timed region spent in the native FP64 operator (Arnoldi K*z, cycle-start
     # residuals, guards): its launches in the timed region x its duration timed alone
     share_fp64 = st["apply_K_fp64"] * t_k / (ms / 1000.0) if ms > 0 else None
-    native = {"bound": "alu", "achieved": flops / t_k / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
-              "frac": flops / t_k / 1e12 / fp64_peak,
-              "traffic": profiled_traffic("apply_K_fp64_96x48x48.md", *FP64_KU_SPAN),
-              "kernel": "node_stencil_kernel<double> (native FP64 K*u: the Krylov operator and the guard)",
-              "peak_source": FP64_PEAK_NOTE + " (no measured FP64 peak on this pool)",
+    native = {"bound": "alu", "achieved": modal_flops / t_k / 1e12, "peak": modal_peak, "unit": "TFLOP/s",
+              "frac": modal_flops / t_k / 1e12 / modal_peak,
+              "traffic": profiled_traffic("apply_modal_kernel_192x96x96.md", *MODAL_SPAN),
+              "kernel": ("apply_modal_kernel (native FP64 K*u in the sum/difference basis of K0: the Krylov "
+                         "operator and the guard)"),
+              "peak_source": ("derived: 148 SMs x 2 FP64 instructions/clk x sm_max_mhz x "
+                              f"{MODAL_FLOPS}/{MODAL_INSTR} flop per instruction of this kernel's mix "
+                              "(no measured FP64 peak on this pool)"),
+              "algorithmic_flops_per_launch": modal_flops, "algorithmic_bytes_per_launch": 18.7 * g.n_dof,
+              "dense_equivalent": {"tflops": flops / t_k / 1e12, "fp64_fma_peak": fp64_peak,
+                                   "ratio": flops / t_k / 1e12 / fp64_peak,
+                                   "note": "1152 flop/element of the dense 24x24 product per launch time"},
               "gdofs": g.n_dof / t_k / 1e9, "ms_per_launch": t_k * 1e3,
-              "launches_in_timed_region": st["apply_K_fp64"], "share_of_timed_region_est": share_fp64,
-              "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": 18.7 * g.n_dof}
+              "launches_in_timed_region": st["apply_K_fp64"], "share_of_timed_region_est": share_fp64}
     stencil = {"bound": "alu", "achieved": flops / t_32 / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                "frac": flops / t_32 / 1e12 / fp32_peak,
                "traffic": profiled_traffic("node_stencil_fp32_96x48x48.md", *FP32_ST_SPAN),

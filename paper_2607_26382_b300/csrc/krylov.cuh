@@ -74,9 +74,14 @@ cgs_dots_kernel(const double* __restrict__ V, long long ld, int nv, const double
     block_rows(n, r0, r1);
     for (long long r = r0 + threadIdx.x; r < r1; r += RED_THREADS) {
         const double wr = w[r];
+        double v[NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q)
-            if (q < nv) acc[q] = fma(V[q * ld + r], wr, acc[q]);
+        for (int q = 0; q < NV; ++q) v[q] = q < nv ? V[q * ld + r] : 0.0;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            if (q >= nv) break;
+            acc[q] = fma(v[q], wr, acc[q]);
+        }
         acc[NV] = fma(wr, wr, acc[NV]);
     }
     // row layout: dots in slots [0, nv), ||w||^2 in slot NV (row stride NV + 1)
@@ -98,18 +103,26 @@ cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, doubl
     __syncthreads();
     long long r0, r1;
     block_rows(n, r0, r1);
+    // all loads of a row first (predicated, so they are in flight together), then FP64
+    // multiply-adds for the nv live vectors only: the FP64 pipe, not memory, bounds this
+    // pass on B300, and a multiply-add by a zero entry would cost as much as a real one
     for (long long r = r0 + threadIdx.x; r < r1; r += RED_THREADS) {
         double v[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = q < nv ? V[q * ld + r] : 0.0;
         double s = 0.0;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-            v[q] = q < nv ? V[q * ld + r] : 0.0;
+            if (q >= nv) break;
             s = fma(h[q], v[q], s);
         }
         const double wn = w[r] - s;
         w[r] = wn;
 #pragma unroll
-        for (int q = 0; q < NV; ++q) acc[q] = fma(v[q], wn, acc[q]);
+        for (int q = 0; q < NV; ++q) {
+            if (q >= nv) break;
+            acc[q] = fma(v[q], wn, acc[q]);
+        }
     }
     block_reduce_store<NV>(acc, nv, partial + (long long)blockIdx.x * NV);
 }
@@ -128,10 +141,15 @@ cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, doubl
     long long r0, r1;
     block_rows(n, r0, r1);
     for (long long r = r0 + threadIdx.x; r < r1; r += RED_THREADS) {
+        double v[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = q < nv ? V[q * ld + r] : 0.0;
         double s = 0.0;
 #pragma unroll
-        for (int q = 0; q < NV; ++q)
-            if (q < nv) s = fma(h[q], V[q * ld + r], s);
+        for (int q = 0; q < NV; ++q) {
+            if (q >= nv) break;
+            s = fma(h[q], v[q], s);
+        }
         const double wn = w[r] - s;
         w[r] = wn;
         acc[0] = fma(wn, wn, acc[0]);
@@ -158,10 +176,15 @@ cgs_slice_update_kernel(const double* __restrict__ V, long long ld, int nv, doub
     long long r0, r1;
     block_rows(n, r0, r1);
     for (long long r = r0 + threadIdx.x; r < r1; r += RED_THREADS) {
+        double v[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = q < nv ? V[q * ld + r] : 0.0;
         double s = 0.0;
 #pragma unroll
-        for (int q = 0; q < NV; ++q)
-            if (q < nv) s = fma(h[q], V[q * ld + r], s);
+        for (int q = 0; q < NV; ++q) {
+            if (q >= nv) break;
+            s = fma(h[q], v[q], s);
+        }
         const double wn = w[r] - s;
         w[r] = wn;
         acc[0] = fma(wn, wn, acc[0]);
