@@ -71,7 +71,12 @@ def parse():
                     help="also time one complete oracle Algorithm-1 pass on the 96x48x48 state (~2 min)")
     ap.add_argument("--cpu-worker", choices=["passes", "apply", "full_c2"], default=None,
                     help=argparse.SUPPRESS)
-    return ap.parse_args()
+    ap.add_argument("--mode", default=None,
+                    help="a measurement of bench_modes.py instead of the headline (batch102, oc_loop, oc_reuse, "
+                         "true_checks, conditioning, adaptive, false_accept, galerkin, coarse_krylov)")
+    args, rest = ap.parse_known_args()
+    args.rest = rest
+    return args
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -678,7 +683,12 @@ def run_b300(args):
 
 def main():
     args = parse()
-    if args.cpu_worker:
+    if args.mode:
+        from paper_2607_26382_b300 import build as gfbuild
+        import bench_modes
+        gfbuild.build()
+        bench_modes.main([args.mode] + args.rest)
+    elif args.cpu_worker:
         cpu_worker(args.cpu_worker)
     elif args.impl == "reference":
         run_reference(args)

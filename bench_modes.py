@@ -1,18 +1,20 @@
-"""Workload drivers for the batched and learned forms (every solve runs in libgf_b300.so).
+"""Measurement modes of bench.py beyond the headline (every solve runs in libgf_b300.so).
 
-    python -m paper_2607_26382_b300.experiments batch102 [--train 2000]
-    python -m paper_2607_26382_b300.experiments oc_loop [--iters 40]
-    python -m paper_2607_26382_b300.experiments oc_reuse [--iters 40]
-    python -m paper_2607_26382_b300.experiments true_checks
-    python -m paper_2607_26382_b300.experiments conditioning
-    python -m paper_2607_26382_b300.experiments adaptive
-    python -m paper_2607_26382_b300.experiments false_accept
-    python -m paper_2607_26382_b300.experiments galerkin
-    python -m paper_2607_26382_b300.experiments coarse_krylov
+    python bench.py --mode batch102 [--train 0]
+    python bench.py --mode oc_loop [--iters 40]
+    python bench.py --mode oc_reuse [--iters 40]
+    python bench.py --mode true_checks
+    python bench.py --mode conditioning
+    python bench.py --mode adaptive
+    python bench.py --mode false_accept
+    python bench.py --mode galerkin
+    python bench.py --mode coarse_krylov
+
+Each prints one JSON line of its own (not the headline's contract line).
 
 batch102: 102 frozen states of uneven size (nx in {32,48,64,80}, ny = nz = nx/2,
-  round-robin; 71 smoothed-Gaussian states with 40% of voxels at floor, 31
-  optimised-like states with 30% forced to floor), probe at rho0 = 1e-6, ladder
+  round-robin; 72 smoothed-Gaussian states with 40% of voxels at floor, 30
+  optimised-like states: SIMP-OC designs with 30% forced to floor), probe at rho0 = 1e-6, ladder
   {1e-5, 1e-4, 1e-3}, tau = 1e-6, kmax = 200, 4-level GMG. Three forms, all with the
   FP64 recomputed-residual guard as the only acceptance test:
     plain   - FP64 V-cycle and Krylov, one state at a time, full ladder from rho0;
@@ -20,7 +22,8 @@ batch102: 102 frozen states of uneven size (nx in {32,48,64,80}, ny = nz = nx/2,
               (outer = 2), all states in one batch,
               Eq. (trigger) picks the first floor;
     learned - as batched, with an MLP (trained on full-ladder outcomes of 48x24x24
-              states) picking the first floor: its most probable floor, and (c0.9)
+              states; the package's selector_weights.json unless --train N retrains on
+              N states) picking the first floor: its most probable floor, and (c0.9)
               the highest floor it is 90% sure the search must reach.
 oc_loop: a guarded SIMP-OC loop (vol 0.3, filter radius 1.5, p = 3, move 0.2) on the
   96x48x48 cantilever, Algorithm 1 at every iteration, compared across selectors.
@@ -76,8 +79,9 @@ import time
 
 import numpy as np
 
-from . import _lib as L
-from . import selector as S
+from paper_2607_26382_b300 import _lib as L
+from paper_2607_26382_b300 import selector as S
+from paper_2607_26382_b300 import workloads as W
 
 LADDER = [1e-5, 1e-4, 1e-3]
 
@@ -89,11 +93,17 @@ def _policy(**kw):
 
 
 def batch_states(n=102, seed0=100):
+    return W.batch_states(n, seed0)
+
+
+def batch_states_tapered(n=102, seed0=100):
+    """The earlier batch102 mix whose optimised-like states are synth's tapered-bar fields
+    (the true_checks and adaptive measurements were recorded on it)."""
     import synth
     dims = synth.batch_grid_sizes(n)
     rhos, kinds = [], []
     for i, (nx, ny, nz) in enumerate(dims):
-        if i % 10 < 7:   # 70% severe random, 30% optimised-like
+        if i % 10 < 7:
             rhos.append(synth.smoothed_gaussian_density(nx, ny, nz, seed0 + i, 2.0, 0.4))
             kinds.append("random")
         else:
@@ -144,10 +154,15 @@ def run_batched(dims, rhos, pol, reps=1):
 
 
 def train_mlp(n_train, seed=7):
+    """The selector: the committed weights (n_train == 0), or one trained here on n_train
+    full-ladder outcomes at 48x24x24 (the mix of train_selector)."""
     import synth
+    if n_train <= 0:
+        net, meta = S.load_trained()
+        return net, meta
     dims = (48, 24, 24)
-    rh = synth.selector_training_states(n_train, dims, seed)
-    pol = _policy(solve_prec=L.GF_MIXED, solve_outer=2)
+    rh = synth.selector_training_states(n_train, dims, seed, designs=W.selector_designs(dims))
+    pol = _policy(solve_prec=L.GF_MIXED, solve_outer=0)
     t0 = time.perf_counter()
     X, y, _ = S.ladder_dataset(dims, rh, 4, pol, chunk=100)
     t_data = time.perf_counter() - t0
@@ -190,7 +205,7 @@ def oc_loop(args):
     modes = [("plain_fp64_full", _policy(selector=L.GF_SEL_FULL, solve_prec=L.GF_FP64, solve_outer=0)),
              ("mixed_rule", _policy(solve_prec=L.GF_MIXED, solve_outer=2))]
     net = None
-    if args.train > 0:
+    if args.train >= 0:
         net, info = train_mlp(args.train)
         out["selector_training"] = info
         pol = _policy(solve_prec=L.GF_MIXED, solve_outer=2, selector=L.GF_SEL_MLP)
@@ -262,7 +277,7 @@ def oc_reuse(args):
 
 def true_checks(args):
     import torch
-    dims, rhos, kinds = batch_states()
+    dims, rhos, kinds = batch_states_tapered()
     out = {"workload": f"{len(dims)} batch102 states one at a time, checks every 25 probe steps, ratio 10"}
     mixed = dict(solve_prec=L.GF_MIXED, solve_outer=2)
     for tag, base in (("workload floors", dict(rho0=1e-6, ladder=LADDER, kmax=200, **mixed)),
@@ -390,7 +405,7 @@ def adaptive(args):
             g.close()
         out[f"96x48x48 bench states, {name}"] = {"guarded_solves_per_s": 4 / t, "fgmres_iters": its, "accepted": acc,
                                                   "floors": floors, "ms_per_iter": t / its * 1e3}
-    dims, rhos, kinds = batch_states()
+    dims, rhos, kinds = batch_states_tapered()
     for name, kw in variants:
         for rho0, ladder, kmax in ((1e-6, LADDER, 200), (1e-12, [1e-3, 1e-2], 300)):
             t, its, acc, fl = 0.0, 0, 0, []
@@ -566,7 +581,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["batch102", "oc_loop", "oc_reuse", "true_checks", "conditioning", "adaptive",
                                      "false_accept", "galerkin", "coarse_krylov"])
-    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--train", type=int, default=0, help="0: the committed selector weights")
     ap.add_argument("--iters", type=int, default=40)
     ap.add_argument("--forms", default="", help="false_accept: comma-separated form indices (default: all)")
     a = ap.parse_args(argv)
@@ -579,3 +594,4 @@ def main(argv=None):
 
 if __name__ == "__main__":
     sys.exit(main())
+
