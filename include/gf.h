@@ -247,6 +247,30 @@ int gf_set_coarse_operator(gf_grid* g, int kind);
  * the cantilever of Table geometries. */
 int gf_cantilever_load(gf_grid* g, double* f);
 
+/* Supports of the grid (Table geometries), used from the next gf_set_floor on:
+ * GF_GEOM_CANTILEVER (default): every DOF of the nodes on the face x = 0 fixed.
+ * GF_GEOM_BRIDGE: every DOF fixed at the nodes (0, 0, k) and y and z fixed (a roller, free
+ *   in x) at (nx, 0, k), for k in {0, nz/2, nz}: the bridge's supports at the two faces and
+ *   the mid-plane of the depth, y up. Needs even nz. Coarse levels take the supports by
+ *   injection: coarse node (I, J, K) fixes the components fine node (2^l I, 2^l J, 2^l K)
+ *   fixes, so a mid-depth support leaves the levels where nz / 2^l is odd. Every operator,
+ *   smoother, transfer and the coarsest inverse then read and write fixed components as 0
+ *   from a per-node bit mask held per level (n_nodes bytes each).
+ *   The bridge runs the default solver only: native FP64 Krylov (outer 0), node-block
+ *   Jacobi smoothing, rediscretised coarse levels, no adaptive components; other options,
+ *   gf_apply_K_split, gf_conditioning, Galerkin coarse operators and the batch return
+ *   GF_ERR_ARG. Switching clears the floor and the captured steps.
+ * Errors: GF_ERR_ARG for an unknown geometry or odd nz; GF_ERR_OOM. */
+#define GF_GEOM_CANTILEVER 0
+#define GF_GEOM_BRIDGE     1
+int gf_set_geometry(gf_grid* g, int geometry);
+
+/* f = the bridge's load (Table geometries): a unit pressure on the top face y = ny h,
+ * pointing down (-y), as consistent nodal forces, -h^2/4 from each top face around a node
+ * (the bilinear face integral of a uniform pressure; total -Lx Lz); 0 on the grid's fixed
+ * DOFs. n_dof doubles, device. */
+int gf_bridge_load(gf_grid* g, double* f);
+
 /* mask[d] = 1 if DOF d is free, 0 if fixed (n_dof bytes, device). */
 int gf_free_mask(gf_grid* g, uint8_t* mask);
 

@@ -24,6 +24,7 @@ MLP_PARAMS = 1412
 GF_MAX_LADDER = 8
 GF_MAX_TRUE_CHECKS = 16
 GF_COARSE_REDISCRETISED, GF_COARSE_GALERKIN = 0, 1
+GF_GEOM_CANTILEVER, GF_GEOM_BRIDGE = 0, 1
 
 ERRORS = {-1: "GF_ERR_ARG", -2: "GF_ERR_OOM", -3: "GF_ERR_CUDA", -4: "GF_ERR_NONFINITE",
           -5: "GF_ERR_TIMEOUT", -6: "GF_ERR_STATE"}
@@ -38,7 +39,7 @@ EXPORTED = [
     "gf_batch_solution", "gf_batch_autotune", "gf_batch_select_floor", "gf_batch_stats",
     "gf_mlp_create", "gf_mlp_destroy", "gf_mlp_set_norm", "gf_mlp_get_params", "gf_mlp_forward",
     "gf_mlp_loss_grad", "gf_mlp_train", "gf_mlp_predict", "gf_select_features", "gf_apply_K_split",
-    "gf_set_coarse_operator",
+    "gf_set_coarse_operator", "gf_set_geometry", "gf_bridge_load",
 ]
 
 
@@ -106,6 +107,8 @@ def lib():
         "gf_set_floor": [P, c_double],
         "gf_set_coarse_operator": [P, c_int],
         "gf_cantilever_load": [P, P],
+        "gf_set_geometry": [P, c_int],
+        "gf_bridge_load": [P, P],
         "gf_free_mask": [P, P],
         "gf_apply_K": [P, P, P],
         "gf_apply_K_f32": [P, P, P],
@@ -279,6 +282,17 @@ class Grid:
 
     def cantilever_load(self, f):
         _check(lib().gf_cantilever_load(self._h, _ptr(f, _torch().float64, self.n_dof, "f")))
+        return f
+
+    def set_geometry(self, kind):
+        """gf_set_geometry: GF_GEOM_CANTILEVER (clamped face x = 0) or GF_GEOM_BRIDGE (the
+        bridge's point supports and rollers), used from the next set_floor on."""
+        _check(lib().gf_set_geometry(self._h, int(kind)))
+        self.rho_min = None
+
+    def bridge_load(self, f):
+        """gf_bridge_load: the bridge's unit top-face pressure as consistent nodal forces."""
+        _check(lib().gf_bridge_load(self._h, _ptr(f, _torch().float64, self.n_dof, "f")))
         return f
 
     def free_mask(self, mask):

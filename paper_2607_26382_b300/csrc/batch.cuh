@@ -647,6 +647,8 @@ int gf_batch_select_floor(gf_batch* b, const gf_policy* pol, gf_select_info* inf
     o.history = nullptr;
     o.tol = pol->tau;
     o.kmax = pol->kmax;
+    for (gf_grid* gi : b->g)
+        if (gi->geom != GF_GEOM_CANTILEVER) return set_err(GF_ERR_ARG, "the batch serves the cantilever only");
     RET(validate_opts(&o));
     if ((pol->selector == GF_SEL_RULE || pol->selector == GF_SEL_MLP) && pol->probe_iters > pol->kmax)
         return set_err(GF_ERR_ARG, "batched policy needs probe_iters <= kmax");

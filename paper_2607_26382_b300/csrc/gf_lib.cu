@@ -72,7 +72,8 @@ struct Level {
     float* q32 = nullptr;
     double* Ke64 = nullptr;           // Galerkin levels (l >= 1): 24x24 element matrices, FP64 moduli
     float* Ke32 = nullptr;            //   and from the BF16-density moduli, rounded to FP32
-    gf::GridDims dims() const { return gf::GridDims{nx, ny, nz}; }
+    uint8_t* fix = nullptr;           // per-node fixed components (bridge supports); null: clamped face x = 0
+    gf::GridDims dims() const { return gf::GridDims{nx, ny, nz, fix}; }
 };
 
 // Element stiffness of the unit cube (E = 1 scaled by E0 by the caller) from the
@@ -135,6 +136,7 @@ struct gf_grid {
     int4* modal_items = nullptr;      // work items of the modal FP64 K*u (device; null: dense stencil)
     int modal_n = 0, modal_bx = 32;   // item count; CTA tile 32 x 16 or 16 x 32 element columns
     bool sym_gj = true;               // coarsest inverse by the blocked symmetric sweep (GF_SYM_GJ=0: two-pivot form)
+    int geom = GF_GEOM_CANTILEVER;    // supports: the clamped face x = 0, or the bridge's (gf_set_geometry)
     gf::K0Param<float> K0f;
     gf::K0Pair K0p;                   // K0f with rows 3a, 3a+1 paired (node_stencil_f32x2_kernel)
     bool f32x2 = true;                // FP32 node stencil with paired FMAs (GF_F32X2=0: scalar FMAs)
@@ -282,14 +284,22 @@ int tiled_f32(gf_grid* g, int l, const float* x, const BT* b, OT* out, const flo
     }
     if (g->tpb[1] > 0 && g->f32x2) {   // the same, with paired FMAs
         const int tpb = level_tpb(g, L.nodes, g->tpb[1]);
-        LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_f32x2_kernel<MODE, BT, OT>), x, b, out, E, L.dims(),
-               g->K0p, omega, halt);
+        if (L.fix)   // supports other than the clamped face (bridge): per-node fixed components
+            LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_f32x2_kernel<MODE, BT, OT, true>), x, b, out, E,
+                   L.dims(), g->K0p, omega, halt);
+        else
+            LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_f32x2_kernel<MODE, BT, OT>), x, b, out, E, L.dims(),
+                   g->K0p, omega, halt);
         return GF_OK;
     }
     if (g->tpb[1] > 0) {   // linear node-per-thread kernel with the autotuned block size
         const int tpb = level_tpb(g, L.nodes, g->tpb[1]);
-        LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_kernel<float, float, MODE, BT, OT>), x, b, out, E,
-               L.dims(), g->K0f, omega, halt);
+        if (L.fix)
+            LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_kernel<float, float, MODE, BT, OT, true>), x, b, out,
+                   E, L.dims(), g->K0f, omega, halt);
+        else
+            LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_kernel<float, float, MODE, BT, OT>), x, b, out, E,
+                   L.dims(), g->K0f, omega, halt);
         return GF_OK;
     }
     if (g->tpb[1] < 0) {   // 27-neighbour register-gather kernel
@@ -312,8 +322,12 @@ int stencil(gf_grid* g, int l, const T* x, const T* b, T* out, const ET* E, cons
     const Level& L = g->lv[l];
     if constexpr (sizeof(T) == sizeof(float)) return tiled_f32<MODE, float, float>(g, l, x, b, out, E, omega, halt);
     const int tpb = g->tpb[sizeof(T) == sizeof(double) ? 0 : 1];
-    LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_kernel<T, ET, MODE>), x, b, out, E, L.dims(), K0, omega,
-           halt);
+    if (L.fix)
+        LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_kernel<T, ET, MODE, T, T, true>), x, b, out, E, L.dims(),
+               K0, omega, halt);
+    else
+        LAUNCH(g, nblk(L.nodes, tpb), tpb, (gf::node_stencil_kernel<T, ET, MODE>), x, b, out, E, L.dims(), K0, omega,
+               halt);
     return GF_OK;
 }
 
@@ -382,7 +396,7 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
     g->stats.vcycles++;
     if (L == 1) {
         double* bm = g->lv[0].b64;
-        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, double>), v, bm, g->ndof, NX0, halt);
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, double>), v, bm, g->ndof, NX0, halt, (const uint8_t*)g->lv[0].fix);
         LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<double, double>), g->Ainv, (const double*)bm, z,
                g->nc, halt);
         return GF_OK;
@@ -393,7 +407,7 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
     if constexpr (sizeof(T) == sizeof(double)) {
         b0 = reinterpret_cast<const T*>(v);
     } else {
-        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, T>), v, B::b(g->lv[0]), g->ndof, NX0, halt);
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, T>), v, B::b(g->lv[0]), g->ndof, NX0, halt, (const uint8_t*)g->lv[0].fix);
         b0 = B::b(g->lv[0]);
     }
     for (int l = 0; l < L - 1; ++l) {
@@ -448,7 +462,7 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
         cur[l] = x;
     }
     if constexpr (sizeof(T) != sizeof(double))
-        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<T, double>), (const T*)cur[0], z, g->ndof, NX0, halt);
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<T, double>), (const T*)cur[0], z, g->ndof, NX0, halt, (const uint8_t*)g->lv[0].fix);
     return GF_OK;
 }
 
@@ -608,7 +622,7 @@ int vcycle_cheb(gf_grid* g, const double* v, double* z, int nu1, int nu2, const 
     if constexpr (sizeof(T) == sizeof(double)) {
         b0 = reinterpret_cast<const T*>(v);
     } else {
-        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, T>), v, B::b(g->lv[0]), g->ndof, NX0, halt);
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, T>), v, B::b(g->lv[0]), g->ndof, NX0, halt, (const uint8_t*)g->lv[0].fix);
         b0 = B::b(g->lv[0]);
     }
     auto smooth = [&](int l, const T* b, T*& x, T*& t, int degree, bool from_zero) -> int {
@@ -660,7 +674,7 @@ int vcycle_cheb(gf_grid* g, const double* v, double* z, int nu1, int nu2, const 
     if constexpr (sizeof(T) == sizeof(double))
         CK(cudaMemcpyAsync(z, cur[0], sizeof(double) * g->ndof, cudaMemcpyDeviceToDevice, g->cur_stream));
     else
-        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<T, double>), (const T*)cur[0], z, g->ndof, NX0, halt);
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<T, double>), (const T*)cur[0], z, g->ndof, NX0, halt, (const uint8_t*)g->lv[0].fix);
     return GF_OK;
 }
 
@@ -687,7 +701,7 @@ int vcycle_galerkin(gf_grid* g, const double* v, double* z, int nu1, int nu2, T 
     if constexpr (sizeof(T) == sizeof(double)) {
         b0 = reinterpret_cast<const T*>(v);
     } else {
-        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, T>), v, B::b(g->lv[0]), g->ndof, NX0, halt);
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, T>), v, B::b(g->lv[0]), g->ndof, NX0, halt, (const uint8_t*)g->lv[0].fix);
         b0 = B::b(g->lv[0]);
     }
     for (int l = 0; l < L - 1; ++l) {
@@ -746,7 +760,7 @@ int vcycle_galerkin(gf_grid* g, const double* v, double* z, int nu1, int nu2, T 
         cur[l] = x;
     }
     if constexpr (sizeof(T) != sizeof(double))
-        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<T, double>), (const T*)cur[0], z, g->ndof, NX0, halt);
+        LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<T, double>), (const T*)cur[0], z, g->ndof, NX0, halt, (const uint8_t*)g->lv[0].fix);
     return GF_OK;
 }
 
@@ -902,7 +916,7 @@ int fine_correct(gf_grid* g, const double* v, double* z, int steps, const int* h
     } else {
         float* zt = (float*)g->fcZT;
         LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, float>), (const double*)z, zt, n, g->nx + 1,
-               halt);
+               halt, (const uint8_t*)nullptr);
         RET((tiled_f32<gf::ST_RESID, double, float>(g, 0, zt, v, (float*)r, lev.E32, 0.0f, halt)));
     }
     RET(inner_fgmres<T>(g, 0, (const T*)r, d, steps, halt, nb));
@@ -955,9 +969,16 @@ int applyK64(gf_grid* g, const double* u, double* y, const int* halt)
 {
     g->stats.apply_K_fp64++;
     if (g->modal_items) {   // modal factorisation of K0 (default; GF_MODAL=0: dense node stencil)
-        if (g->modal_bx == 32)
+        const bool mk = g->lv[0].fix != nullptr;   // per-node fixed components (bridge supports)
+        if (g->modal_bx == 32 && mk)
+            LAUNCH(g, g->modal_n, dim3(32, 16), (gf::apply_modal_kernel<32, 16, true>), u, y,
+                   (const double*)g->lv[0].E64, g->lv[0].dims(), g->Kmodal, (const int4*)g->modal_items, halt);
+        else if (g->modal_bx == 32)
             LAUNCH(g, g->modal_n, dim3(32, 16), (gf::apply_modal_kernel<32, 16>), u, y, (const double*)g->lv[0].E64,
                    g->lv[0].dims(), g->Kmodal, (const int4*)g->modal_items, halt);
+        else if (mk)
+            LAUNCH(g, g->modal_n, dim3(16, 32), (gf::apply_modal_kernel<16, 32, true>), u, y,
+                   (const double*)g->lv[0].E64, g->lv[0].dims(), g->Kmodal, (const int4*)g->modal_items, halt);
         else
             LAUNCH(g, g->modal_n, dim3(16, 32), (gf::apply_modal_kernel<16, 32>), u, y, (const double*)g->lv[0].E64,
                    g->lv[0].dims(), g->Kmodal, (const int4*)g->modal_items, halt);
@@ -1320,7 +1341,7 @@ int cycle_start(gf_grid* g, const double* f, const double* x, bool x_zero, bool 
     const int* skip = &g->st->skip;
     if (!x_zero) RET(applyOuter(g, x, v0, skip, outer));
     LAUNCH(g, g->nbr, gf::RED_THREADS, gf::residual_norms_kernel, f, v0, v0, g->ndof, g->nx + 1, g->partial,
-           x_zero ? 1 : 0, skip);
+           x_zero ? 1 : 0, skip, (const uint8_t*)g->lv[0].fix);
     LAUNCH(g, 1, 64, gf::reduce_partials_kernel, g->partial, g->nbr, 2, 2, g->st, 0, 0);
     LAUNCH(g, 1, 32, gf::cycle_start_tail_kernel, g->st, g->hist, g->host_status_dev, first ? 1 : 0);
     if (outer == 2)
@@ -1423,7 +1444,7 @@ int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, g
     RET(set_coarse_steps(g, o));
     const int NX0 = g->nx + 1;
     // fixed entries of u are written as 0
-    LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, double>), u, u, g->ndof, NX0, nullptr);
+    LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, double>), u, u, g->ndof, NX0, nullptr, (const uint8_t*)g->lv[0].fix);
     LAUNCH(g, 1, 1, init_state_kernel, g->st, o->kmax, m, o->tol);
     *g->host_status = gf::KS_RUN;
     bool first = true, aborted = false;
@@ -1504,11 +1525,21 @@ int validate_opts(const gf_solve_opts* o)
     return GF_OK;
 }
 
+// The bridge geometry (per-node fixed components) runs the default solver: native FP64
+// Krylov, node-block Jacobi smoothing, rediscretised coarse levels, no adaptive components.
+int validate_geom(const gf_grid* g, const gf_solve_opts* o)
+{
+    if (g->geom == GF_GEOM_CANTILEVER) return GF_OK;
+    if (o->outer != 0 || o->smoother != 0 || o->ls_ratio > 0.0 || o->fine_steps != 0 || o->coarse_steps != 0)
+        return set_err(GF_ERR_ARG, "the bridge geometry takes outer 0, smoother 0 and no adaptive components");
+    return GF_OK;
+}
+
 int guard_impl(gf_grid* g, const double* f, const double* u, double* eta)
 {
     RET(applyK64(g, u, g->work, nullptr));
     LAUNCH(g, g->nbr, gf::RED_THREADS, gf::residual_norms_kernel, f, g->work, (double*)nullptr, g->ndof,
-           g->nx + 1, g->partial, 0, (const int*)nullptr);
+           g->nx + 1, g->partial, 0, (const int*)nullptr, (const uint8_t*)g->lv[0].fix);
     LAUNCH(g, 1, 64, gf::reduce_partials_kernel, g->partial, g->nbr, 2, 2, g->gst, 0, 0);
     double h[2];
     CK(cudaMemcpyAsync(h, g->gst->h1, sizeof(h), cudaMemcpyDeviceToHost, g->stream));
@@ -1978,6 +2009,7 @@ int gf_destroy_grid(gf_grid* g)
         cudaFree(L.b32); cudaFree(L.x32); cudaFree(L.t32); cudaFree(L.r32);
         cudaFree(L.q64); cudaFree(L.q32);
         cudaFree(L.Ke64); cudaFree(L.Ke32);
+        cudaFree(L.fix);
     }
     cudaFree(g->galG); cudaFree(g->gal_s[0]); cudaFree(g->gal_s[1]);
     cudaFree(g->ls_partial); cudaFree(g->ls_alpha);
@@ -2081,6 +2113,7 @@ int gf_set_coarse_operator(gf_grid* g, int kind)
     if (kind != GF_COARSE_REDISCRETISED && kind != GF_COARSE_GALERKIN)
         return set_err(GF_ERR_ARG, "kind must be GF_COARSE_REDISCRETISED or GF_COARSE_GALERKIN");
     if (kind == g->coarse_kind) return GF_OK;
+    if (g->geom != GF_GEOM_CANTILEVER) return set_err(GF_ERR_ARG, "the bridge geometry keeps rediscretised coarse levels");
     RET(set_device(g));
     drop_graphs(g);            // captured Arnoldi steps hold the other V-cycle
     g->coarse_kind = kind;
@@ -2094,6 +2127,46 @@ int gf_cantilever_load(gf_grid* g, double* f)
     if (!f) return set_err(GF_ERR_ARG, "null f");
     RET(set_device(g));
     LAUNCH(g, nblk(g->ndof), 256, gf::cantilever_load_kernel, f, g->lv[0].dims());
+    return GF_OK;
+}
+
+int gf_set_geometry(gf_grid* g, int geometry)
+{
+    RET(check_grid(g));
+    if (geometry != GF_GEOM_CANTILEVER && geometry != GF_GEOM_BRIDGE)
+        return set_err(GF_ERR_ARG, "geometry must be GF_GEOM_CANTILEVER or GF_GEOM_BRIDGE");
+    if (geometry == g->geom) return GF_OK;
+    RET(set_device(g));
+    if (geometry == GF_GEOM_BRIDGE) {
+        if (g->nz % 2) return set_err(GF_ERR_ARG, "the bridge's mid-depth supports need even nz");
+        if (g->coarse_kind != GF_COARSE_REDISCRETISED)
+            return set_err(GF_ERR_ARG, "the bridge geometry keeps rediscretised coarse levels");
+        for (int l = 0; l < g->L; ++l) {
+            Level& c = g->lv[l];
+            RET(allocT(&c.fix, (size_t)c.nodes));
+            LAUNCH(g, nblk(c.nodes), 256, gf::bridge_fix_kernel, c.fix, gf::GridDims{c.nx, c.ny, c.nz}, l, g->nx, g->nz);
+            g->stc_cz[l] = 0;   // the variants that read the clamped face from the index are off
+        }
+        g->vc_l0 = -1;
+        if (g->tpb[1] <= 0) g->tpb[1] = 256;
+    } else {
+        for (Level& c : g->lv) {
+            cudaFree(c.fix);
+            c.fix = nullptr;
+        }
+    }
+    drop_graphs(g);
+    g->geom = geometry;
+    g->has_floor = false;   // gf_set_floor again: the coarsest inverse carries the supports
+    return GF_OK;
+}
+
+int gf_bridge_load(gf_grid* g, double* f)
+{
+    RET(check_grid(g));
+    if (!f) return set_err(GF_ERR_ARG, "null f");
+    RET(set_device(g));
+    LAUNCH(g, nblk(g->ndof), 256, gf::bridge_load_kernel, f, g->lv[0].dims(), g->h * g->h);
     return GF_OK;
 }
 
@@ -2117,6 +2190,7 @@ int gf_apply_K(gf_grid* g, const double* u, double* y)
 
 int gf_apply_K_split(gf_grid* g, const double* u, double* y)
 {
+    if (g && g->geom != GF_GEOM_CANTILEVER) return set_err(GF_ERR_ARG, "the split operator serves the cantilever only");
     RET(check_grid(g));
     if (!u || !y || u == y) return set_err(GF_ERR_ARG, "u, y non-null and distinct");
     if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
@@ -2150,6 +2224,7 @@ int gf_vcycle_ex(gf_grid* g, const double* v, double* z, const gf_solve_opts* o)
 {
     RET(check_grid(g));
     RET(validate_opts(o));
+    RET(validate_geom(g, o));
     if (!v || !z || v == z) return set_err(GF_ERR_ARG, "v, z non-null and distinct");
     if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
     RET(set_device(g));
@@ -2179,6 +2254,7 @@ int gf_solve(gf_grid* g, const double* f, double* u, const gf_solve_opts* opts, 
 {
     RET(check_grid(g));
     RET(validate_opts(opts));
+    RET(validate_geom(g, opts));
     if (!f || !u || f == u) return set_err(GF_ERR_ARG, "f, u non-null and distinct");
     if (!g->has_floor) return set_err(GF_ERR_STATE, "set_floor first");
     RET(set_device(g));
@@ -2188,6 +2264,7 @@ int gf_solve(gf_grid* g, const double* f, double* u, const gf_solve_opts* opts, 
 int gf_conditioning(gf_grid* g, const double* f, int iters, double* lambda_min, double* lambda_max,
                     double* eta_direct)
 {
+    if (g && g->geom != GF_GEOM_CANTILEVER) return set_err(GF_ERR_ARG, "the conditioning diagnostic serves the cantilever only");
     RET(check_grid(g));
     if (!lambda_min || !lambda_max || (eta_direct && !f)) return set_err(GF_ERR_ARG, "null pointer");
     if (g->L != 1) return set_err(GF_ERR_STATE, "gf_conditioning needs a one-level grid (levels = 1)");
@@ -2317,6 +2394,7 @@ int select_floor_reuse(gf_grid* g, const double* f, double* u, const gf_policy* 
     o.tol = pol->tau;
     o.kmax = pol->kmax;
     RET(validate_opts(&o));
+    RET(validate_geom(g, &o));
     RET(set_device(g));
     const double rm = pol->first_index == 0 ? pol->rho0 : pol->ladder[pol->first_index - 1];
     if (!(g->has_floor && g->rho_min == rm)) RET(gf_set_floor(g, rm));
@@ -2371,6 +2449,7 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
     o.history = nullptr;
     o.tol = pol->tau;
     RET(validate_opts(&o));
+    RET(validate_geom(g, &o));
     RET(set_device(g));
     std::memset(info, 0, sizeof(*info));
     info->r50 = info->r100 = std::nan("");
@@ -2597,6 +2676,8 @@ int gf_select_features(const gf_grid* g, double r50, double r100, double* x)
 
 int gf_set_stencil_blocks(gf_grid* g, int tpb64, int tpb32)
 {
+    if (g && g->geom != GF_GEOM_CANTILEVER && tpb32 <= 0)
+        return set_err(GF_ERR_ARG, "the bridge geometry runs the node-per-thread FP32 stencils (tpb32 > 0)");
     RET(check_grid(g));
     const auto ok = [](int t, bool f32) {
         return t == 64 || t == 128 || t == 256 || (f32 && (t == 0 || t == -64 || t == -128 || t == -256));
@@ -2712,7 +2793,7 @@ extern "C" int gf_true_residual_noalloc(int nx, int ny, int nz, double h, double
     gf::node_stencil_kernel<double, double, gf::ST_APPLY, double, double><<<nblk(nodes), 256, 0, s>>>(
         u, (const double*)nullptr, Ku, E, d, K0, 0.0, (const int*)nullptr);
     CK(cudaGetLastError());
-    gf::residual_norms_kernel<<<nb, gf::RED_THREADS, 0, s>>>(f, Ku, nullptr, ndof, nx + 1, partial, 0, nullptr);
+    gf::residual_norms_kernel<<<nb, gf::RED_THREADS, 0, s>>>(f, Ku, nullptr, ndof, nx + 1, partial, 0, nullptr, nullptr);
     CK(cudaGetLastError());
     noalloc_eta_kernel<<<1, 32, 0, s>>>(partial, nb, eta);
     CK(cudaGetLastError());

@@ -9,6 +9,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 namespace gf {
 
@@ -377,14 +378,14 @@ __global__ void scale_kernel(double* __restrict__ v, long long n, const KState* 
 __global__ void __launch_bounds__(RED_THREADS)
 residual_norms_kernel(const double* __restrict__ f, const double* y, double* r,
                       long long n, int NX, double* __restrict__ partial, int y_is_zero,
-                      const int* __restrict__ halt)
+                      const int* __restrict__ halt, const uint8_t* __restrict__ fix = nullptr)
 {
     if (halt != nullptr && *halt != 0) return;
     double acc[2] = {0.0, 0.0};
     long long r0, r1;
     block_rows(n, r0, r1);
     for (long long q = r0 + threadIdx.x; q < r1; q += RED_THREADS) {
-        const bool fixed = ((q / 3) % NX) == 0;
+        const bool fixed = fix ? ((fix[q / 3] >> (int)(q % 3)) & 1) != 0 : ((q / 3) % NX) == 0;
         const double fv = fixed ? 0.0 : f[q];
         const double rv = y_is_zero ? fv : fv - y[q];
         if (r) r[q] = rv;
@@ -395,14 +396,17 @@ residual_norms_kernel(const double* __restrict__ f, const double* y, double* r,
 }
 
 // masked copy (fixed entries -> 0), optional type conversion
+// (fix: per-node fixed-component bits, or null for the clamped face x = 0)
 template <typename TI, typename TO>
 __global__ void masked_convert_kernel(const TI* a, TO* b, long long n, int NX,
-                                      const int* __restrict__ halt)
+                                      const int* __restrict__ halt, const uint8_t* __restrict__ fix)
 {
     if (halt != nullptr && *halt != 0) return;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-         q += (long long)gridDim.x * blockDim.x)
-        b[q] = (((q / 3) % NX) == 0) ? TO(0) : (TO)a[q];
+         q += (long long)gridDim.x * blockDim.x) {
+        const bool fixed = fix ? ((fix[q / 3] >> (int)(q % 3)) & 1) != 0 : ((q / 3) % NX) == 0;
+        b[q] = fixed ? TO(0) : (TO)a[q];
+    }
 }
 
 // Dense GEMV for the coarsest solve: x = A b, A row-major FP64 (n x n); one warp per row.

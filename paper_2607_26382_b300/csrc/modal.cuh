@@ -173,7 +173,8 @@ __device__ __forceinline__ void face_inv(const double f[4], double v[4])
 // One CTA per work item: node tile (x, y) of (BX-1) x (BY-1) nodes and node planes [z, w).
 // The host balances the items (modal_plan): tiles at the far edges of the grid hold fewer
 // element columns and take longer runs of planes, so that every CTA costs about the same.
-template <int BX, int BY>
+// MASK: fixed components from d.fix (any supports); otherwise the clamped face x = 0.
+template <int BX, int BY, bool MASK = false>
 __global__ void __launch_bounds__(MODAL_THREADS, 1)
 apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const double* __restrict__ E,
                    GridDims d, ModalCoef C, const int4* __restrict__ items, const int* __restrict__ halt)
@@ -197,10 +198,17 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int ni = ex + (q & 1), nj = ey + (q >> 1);
-            const bool ok = col && kz >= 0 && kz < NZ && ni >= 1;
             const long long n = ni + (long long)NX * nj + plane * kz;
+            if constexpr (MASK) {
+                const bool in = col && kz >= 0 && kz < NZ;
+                const unsigned mb = in ? (unsigned)__ldg(d.fix + n) : 7u;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v[c][q] = ok ? __ldg(u + 3 * n + c) : 0.0;
+                for (int c = 0; c < 3; ++c) v[c][q] = ((mb >> c) & 1u) ? 0.0 : __ldg(u + 3 * n + c);
+            } else {
+                const bool ok = col && kz >= 0 && kz < NZ && ni >= 1;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c][q] = ok ? __ldg(u + 3 * n + c) : 0.0;
+            }
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) face_fwd(v[c], f[c]);
@@ -284,6 +292,7 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
         const int ni = i0 + tx, nj = j0 + ty;
         if (ez >= k0 && tx < BX - 1 && ty < BY - 1 && ni < NX && nj < NY) {
             const long long n = ni + (long long)NX * nj + plane * ez;
+            const unsigned ob = MASK ? (unsigned)__ldg(d.fix + n) : (ni == 0 ? 7u : 0u);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 // node (ni, nj) is corner (1,1) of column (tx, ty), (0,1) of (tx+1, ty),
@@ -291,7 +300,7 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
                 double acc = part[3 * 3 + c][ty][tx] + part[2 * 3 + c][ty][tx + 1];
                 acc += part[1 * 3 + c][ty + 1][tx];
                 acc += part[0 * 3 + c][ty + 1][tx + 1];
-                y[3 * n + c] = (ni == 0) ? 0.0 : acc;
+                y[3 * n + c] = ((ob >> c) & 1u) ? 0.0 : acc;
             }
         }
 #pragma unroll

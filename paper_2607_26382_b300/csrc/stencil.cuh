@@ -30,8 +30,32 @@ __host__ __device__ constexpr int local_index(int x, int y, int z) {
 enum StencilMode { ST_APPLY = 0, ST_RESID = 1, ST_SWEEP = 2 };
 
 struct GridDims {
-    int nx, ny, nz;   // elements per axis
+    int nx, ny, nz;                 // elements per axis
+    const uint8_t* fix = nullptr;   // per node, bit c set: component c fixed (device); null: every
+                                    // DOF of the nodes on the clamped face x = 0 (the cantilever)
 };
+
+// Fixed components of node n (i: its x index) as bits 0..2.
+__device__ __forceinline__ unsigned fix_bits(const GridDims& d, long long n, int i)
+{
+    return d.fix ? (unsigned)__ldg(d.fix + n) : (i == 0 ? 7u : 0u);
+}
+
+// Is DOF q (= 3n + c) fixed?
+__device__ __forceinline__ bool fix_dof(const GridDims& d, long long q)
+{
+    const long long n = q / 3;
+    return d.fix ? ((__ldg(d.fix + n) >> (int)(q - 3 * n)) & 1) != 0 : (n % (d.nx + 1)) == 0;
+}
+
+// The node block of a partly fixed node: identity rows and columns on its fixed components.
+template <typename T>
+__device__ __forceinline__ void mask_block(unsigned fb, T& d00, T& d11, T& d22, T& d01, T& d02, T& d12)
+{
+    if (fb & 1u) { d00 = T(1); d01 = T(0); d02 = T(0); }
+    if (fb & 2u) { d11 = T(1); d01 = T(0); d12 = T(0); }
+    if (fb & 4u) { d22 = T(1); d02 = T(0); d12 = T(0); }
+}
 
 // (i, j, k) of node n = i + NX (j + NY k). Grids hold fewer than 2^31 nodes
 // (gf_create_grid checks), so 32-bit unsigned division suffices.
@@ -69,7 +93,9 @@ __device__ __forceinline__ void node_block_update(T d00, T d11, T d22, T d01, T 
 // MODE == ST_SWEEP: out = x + omega * D_n^{-1} (b - K x)     (D_n: 3x3 node block)
 // Fixed nodes (i == 0) read as 0 and are written as 0. Element moduli E are
 // already multiplied by the element edge h (K_e(h) = h K_e(1) in 3D).
-template <typename T, typename ET, int MODE, typename BT, typename OT>
+// MASK: fixed components from d.fix (any supports); otherwise the clamped face x = 0
+// by the node index (the cantilever code, unchanged).
+template <typename T, typename ET, int MODE, typename BT, typename OT, bool MASK = false>
 __device__ __forceinline__ void stencil_node(long long n, const T* __restrict__ x, const BT* __restrict__ b,
                                              OT* __restrict__ out, const ET* __restrict__ E, GridDims d,
                                              const K0Param<T>& K0, T omega)
@@ -77,7 +103,8 @@ __device__ __forceinline__ void stencil_node(long long n, const T* __restrict__ 
     const int NX = d.nx + 1, NY = d.ny + 1;
     int i, j, k;
     node_coords(n, NX, NY, i, j, k);
-    if (i == 0) {
+    const unsigned fb = MASK ? (unsigned)__ldg(d.fix + n) : (i == 0 ? 7u : 0u);
+    if (fb == 7u) {
         out[3 * n + 0] = OT(0);
         out[3 * n + 1] = OT(0);
         out[3 * n + 2] = OT(0);
@@ -100,10 +127,17 @@ __device__ __forceinline__ void stencil_node(long long n, const T* __restrict__ 
 #pragma unroll
                 for (int dx = 0; dx < 3; ++dx) {
                     const int ni = i - 1 + dx, nj = j - 1 + dy, nk = k - 1 + dz;
-                    const bool ok = ni >= 1 && ni < NX && nj >= 0 && nj < NY && nk >= 0 && nk < NZ;
                     const long long m = n + (dx - 1) + (long long)NX * ((dy - 1) + (long long)NY * (dz - 1));
+                    if constexpr (MASK) {
+                        const bool in = ni >= 0 && ni < NX && nj >= 0 && nj < NY && nk >= 0 && nk < NZ;
+                        const unsigned mb = in ? (unsigned)__ldg(d.fix + m) : 7u;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) nb[dz][dy][dx][c] = ok ? x[3 * m + c] : T(0);
+                        for (int c = 0; c < 3; ++c) nb[dz][dy][dx][c] = ((mb >> c) & 1u) ? T(0) : x[3 * m + c];
+                    } else {
+                        const bool ok = ni >= 1 && ni < NX && nj >= 0 && nj < NY && nk >= 0 && nk < NZ;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) nb[dz][dy][dx][c] = ok ? x[3 * m + c] : T(0);
+                    }
                 }
         }
     };
@@ -134,6 +168,12 @@ __device__ __forceinline__ void stencil_node(long long n, const T* __restrict__ 
                                 u0 = nb[oz + bz][oy + by][ox + bx][0];
                                 u1 = nb[oz + bz][oy + by][ox + bx][1];
                                 u2 = nb[oz + bz][oy + by][ox + bx][2];
+                            } else if constexpr (MASK) {
+                                const long long m = ni + (long long)NX * ((ey + by) + (long long)NY * (ez + bz));
+                                const unsigned mb = (unsigned)__ldg(d.fix + m);
+                                u0 = (mb & 1u) ? T(0) : x[3 * m + 0];
+                                u1 = (mb & 2u) ? T(0) : x[3 * m + 1];
+                                u2 = (mb & 4u) ? T(0) : x[3 * m + 2];
                             } else if (ni != 0) {
                                 const long long m = ni + (long long)NX * ((ey + by) + (long long)NY * (ez + bz));
                                 u0 = x[3 * m + 0];
@@ -163,20 +203,39 @@ __device__ __forceinline__ void stencil_node(long long n, const T* __restrict__ 
             }
         }
     }
+    if constexpr (MASK) {   // a partly fixed node: its fixed components stay 0
+        if (fb & 1u) a0 = T(0);
+        if (fb & 2u) a1 = T(0);
+        if (fb & 4u) a2 = T(0);
+    }
     if (MODE == ST_APPLY) {
         out[3 * n + 0] = OT(a0);
         out[3 * n + 1] = OT(a1);
         out[3 * n + 2] = OT(a2);
         return;
     }
-    const T r0 = T(b[3 * n + 0]) - a0;
-    const T r1 = T(b[3 * n + 1]) - a1;
-    const T r2 = T(b[3 * n + 2]) - a2;
+    T r0 = T(b[3 * n + 0]) - a0;
+    T r1 = T(b[3 * n + 1]) - a1;
+    T r2 = T(b[3 * n + 2]) - a2;
+    if constexpr (MASK) {
+        if (fb & 1u) r0 = T(0);
+        if (fb & 2u) r1 = T(0);
+        if (fb & 4u) r2 = T(0);
+    }
     if (MODE == ST_RESID) {
         out[3 * n + 0] = OT(r0);
         out[3 * n + 1] = OT(r1);
         out[3 * n + 2] = OT(r2);
         return;
+    }
+    if constexpr (MASK) {
+        if (fb) {   // identity rows and columns on the fixed components; their output stays 0
+            mask_block<T>(fb, d00, d11, d22, d01, d02, d12);
+            const T xm[3] = {(fb & 1u) ? T(0) : x[3 * n + 0], (fb & 2u) ? T(0) : x[3 * n + 1],
+                             (fb & 4u) ? T(0) : x[3 * n + 2]};
+            node_block_update<T, OT>(d00, d11, d22, d01, d02, d12, r0, r1, r2, xm, out + 3 * n, omega);
+            return;
+        }
     }
     node_block_update<T, OT>(d00, d11, d22, d01, d02, d12, r0, r1, r2, x + 3 * n, out + 3 * n, omega);
 }
@@ -184,7 +243,7 @@ __device__ __forceinline__ void stencil_node(long long n, const T* __restrict__ 
 // FP32: at most 80 registers (3 blocks of 256 per SM), which the plane-wise neighbour
 // loads allow with a few bytes of spill; measured 17.3 -> 14.7 us (96x48x48) and
 // 92.8 -> 74.5 us (192x96x96) against the unbounded 108-120-register build.
-template <typename T, typename ET, int MODE, typename BT = T, typename OT = T>
+template <typename T, typename ET, int MODE, typename BT = T, typename OT = T, bool MASK = false>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 node_stencil_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __restrict__ out,
                     const ET* __restrict__ E, GridDims d, const __grid_constant__ K0Param<T> K0,
@@ -194,7 +253,7 @@ node_stencil_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __res
     const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
-    stencil_node<T, ET, MODE, BT, OT>(n, x, b, out, E, d, K0, omega);
+    stencil_node<T, ET, MODE, BT, OT, MASK>(n, x, b, out, E, d, K0, omega);
 }
 
 // ---- FP32 node stencil with paired FMAs (fma.rn.f32x2) ------------------------------
@@ -214,7 +273,7 @@ __device__ __forceinline__ void fma_f32x2(float& d0, float& d1, float2 a, float 
         : "+f"(d0), "+f"(d1) : "f"(a.x), "f"(a.y), "f"(b));
 }
 
-template <int MODE, typename BT, typename OT>
+template <int MODE, typename BT, typename OT, bool MASK = false>
 __device__ __forceinline__ void stencil_node_f32x2(long long n, const float* __restrict__ x, const BT* __restrict__ b,
                                                    OT* __restrict__ out, const float* __restrict__ E, GridDims d,
                                                    const K0Pair& K0, float omega)
@@ -222,7 +281,8 @@ __device__ __forceinline__ void stencil_node_f32x2(long long n, const float* __r
     const int NX = d.nx + 1, NY = d.ny + 1;
     int i, j, k;
     node_coords(n, NX, NY, i, j, k);
-    if (i == 0) {
+    const unsigned fb = MASK ? (unsigned)__ldg(d.fix + n) : (i == 0 ? 7u : 0u);
+    if (fb == 7u) {
         out[3 * n + 0] = OT(0);
         out[3 * n + 1] = OT(0);
         out[3 * n + 2] = OT(0);
@@ -238,10 +298,17 @@ __device__ __forceinline__ void stencil_node_f32x2(long long n, const float* __r
 #pragma unroll
             for (int dx = 0; dx < 3; ++dx) {
                 const int ni = i - 1 + dx, nj = j - 1 + dy, nk = k - 1 + dz;
-                const bool ok = ni >= 1 && ni < NX && nj >= 0 && nj < NY && nk >= 0 && nk < NZ;
                 const long long m = n + (dx - 1) + (long long)NX * ((dy - 1) + (long long)NY * (dz - 1));
+                if constexpr (MASK) {
+                    const bool in = ni >= 0 && ni < NX && nj >= 0 && nj < NY && nk >= 0 && nk < NZ;
+                    const unsigned mb = in ? (unsigned)__ldg(d.fix + m) : 7u;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) nb[dz][dy][dx][c] = ok ? x[3 * m + c] : 0.f;
+                    for (int c = 0; c < 3; ++c) nb[dz][dy][dx][c] = ((mb >> c) & 1u) ? 0.f : x[3 * m + c];
+                } else {
+                    const bool ok = ni >= 1 && ni < NX && nj >= 0 && nj < NY && nk >= 0 && nk < NZ;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) nb[dz][dy][dx][c] = ok ? x[3 * m + c] : 0.f;
+                }
             }
     };
     load_plane(0);
@@ -289,25 +356,44 @@ __device__ __forceinline__ void stencil_node_f32x2(long long n, const float* __r
             }
         }
     }
+    if constexpr (MASK) {
+        if (fb & 1u) a0 = 0.f;
+        if (fb & 2u) a1 = 0.f;
+        if (fb & 4u) a2 = 0.f;
+    }
     if (MODE == ST_APPLY) {
         out[3 * n + 0] = OT(a0);
         out[3 * n + 1] = OT(a1);
         out[3 * n + 2] = OT(a2);
         return;
     }
-    const float r0 = float(b[3 * n + 0]) - a0;
-    const float r1 = float(b[3 * n + 1]) - a1;
-    const float r2 = float(b[3 * n + 2]) - a2;
+    float r0 = float(b[3 * n + 0]) - a0;
+    float r1 = float(b[3 * n + 1]) - a1;
+    float r2 = float(b[3 * n + 2]) - a2;
+    if constexpr (MASK) {
+        if (fb & 1u) r0 = 0.f;
+        if (fb & 2u) r1 = 0.f;
+        if (fb & 4u) r2 = 0.f;
+    }
     if (MODE == ST_RESID) {
         out[3 * n + 0] = OT(r0);
         out[3 * n + 1] = OT(r1);
         out[3 * n + 2] = OT(r2);
         return;
     }
+    if constexpr (MASK) {
+        if (fb) {
+            mask_block<float>(fb, d00, d11, d22, d01, d02, d12);
+            const float xm[3] = {(fb & 1u) ? 0.f : x[3 * n + 0], (fb & 2u) ? 0.f : x[3 * n + 1],
+                                 (fb & 4u) ? 0.f : x[3 * n + 2]};
+            node_block_update<float, OT>(d00, d11, d22, d01, d02, d12, r0, r1, r2, xm, out + 3 * n, omega);
+            return;
+        }
+    }
     node_block_update<float, OT>(d00, d11, d22, d01, d02, d12, r0, r1, r2, x + 3 * n, out + 3 * n, omega);
 }
 
-template <int MODE, typename BT, typename OT>
+template <int MODE, typename BT, typename OT, bool MASK = false>
 __global__ void __launch_bounds__(256, 3)
 node_stencil_f32x2_kernel(const float* __restrict__ x, const BT* __restrict__ b, OT* __restrict__ out,
                           const float* __restrict__ E, GridDims d, const __grid_constant__ K0Pair K0, float omega,
@@ -317,7 +403,7 @@ node_stencil_f32x2_kernel(const float* __restrict__ x, const BT* __restrict__ b,
     const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
-    stencil_node_f32x2<MODE, BT, OT>(n, x, b, out, E, d, K0, omega);
+    stencil_node_f32x2<MODE, BT, OT, MASK>(n, x, b, out, E, d, K0, omega);
 }
 
 // First smoothing sweep from x = 0: out = omega * D_n^{-1} b, b_n = (r0, r1, r2).
@@ -329,7 +415,8 @@ __device__ __forceinline__ void first_sweep_vals(long long n, T r0, T r1, T r2, 
     const int NX = d.nx + 1, NY = d.ny + 1;
     int i, j, k;
     node_coords(n, NX, NY, i, j, k);
-    if (i == 0) {
+    const unsigned fb = fix_bits(d, n, i);
+    if (fb == 7u) {
         out[3 * n + 0] = T(0);
         out[3 * n + 1] = T(0);
         out[3 * n + 2] = T(0);
@@ -353,6 +440,12 @@ __device__ __forceinline__ void first_sweep_vals(long long n, T r0, T r1, T r2, 
                 d02 = fma(Ee, K0.k[(3 * a + 0) * 24 + 3 * a + 2], d02);
                 d12 = fma(Ee, K0.k[(3 * a + 1) * 24 + 3 * a + 2], d12);
             }
+    if (fb) {   // a partly fixed node: identity rows and columns, zero right-hand side there
+        mask_block<T>(fb, d00, d11, d22, d01, d02, d12);
+        if (fb & 1u) r0 = T(0);
+        if (fb & 2u) r1 = T(0);
+        if (fb & 4u) r2 = T(0);
+    }
     const T c00 = d11 * d22 - d12 * d12;
     const T c01 = d02 * d12 - d01 * d22;
     const T c02 = d01 * d12 - d02 * d11;
@@ -398,7 +491,8 @@ __device__ __forceinline__ void restrict_vals(long long n, const T* __restrict__
     int I, J, K;
     node_coords(n, CX, CY, I, J, K);
     s0 = s1 = s2 = T(0);
-    if (I == 0) return;
+    const unsigned fb = fix_bits(cd, n, I);
+    if (fb == 7u) return;
     const int FX = 2 * cd.nx + 1, FY = 2 * cd.ny + 1, FZ = 2 * cd.nz + 1;
 #pragma unroll
     for (int dk = -1; dk <= 1; ++dk) {
@@ -411,7 +505,7 @@ __device__ __forceinline__ void restrict_vals(long long n, const T* __restrict__
 #pragma unroll
             for (int di = -1; di <= 1; ++di) {
                 const int fi = 2 * I + di;
-                if (fi >= FX) continue;
+                if (fi < 0 || fi >= FX) continue;   // (fi < 0 only on supports other than the clamped face)
                 const T w = T((di ? 0.5 : 1.0) * (dj ? 0.5 : 1.0) * (dk ? 0.5 : 1.0));
                 const long long m = fi + (long long)FX * (fj + (long long)FY * fk);
                 s0 = fma(w, r[3 * m + 0], s0);
@@ -420,6 +514,9 @@ __device__ __forceinline__ void restrict_vals(long long n, const T* __restrict__
             }
         }
     }
+    if (fb & 1u) s0 = T(0);
+    if (fb & 2u) s1 = T(0);
+    if (fb & 4u) s2 = T(0);
 }
 
 template <typename T>
@@ -472,7 +569,8 @@ __device__ __forceinline__ void prolong_node(long long n, T* __restrict__ x, con
     const int FX = fd.nx + 1, FY = fd.ny + 1;
     int i, j, k;
     node_coords(n, FX, FY, i, j, k);
-    if (i == 0) return;
+    const unsigned fb = fix_bits(fd, n, i);
+    if (fb == 7u) return;
     const int CX = fd.nx / 2 + 1, CY = fd.ny / 2 + 1;
     int Is[2], Js[2], Ks[2];
     T wi[2], wj[2], wk[2];
@@ -493,9 +591,9 @@ __device__ __forceinline__ void prolong_node(long long n, T* __restrict__ x, con
                 s1 = fma(w, (T)xc[3 * m + 1], s1);
                 s2 = fma(w, (T)xc[3 * m + 2], s2);
             }
-    x[3 * n + 0] += s0;
-    x[3 * n + 1] += s1;
-    x[3 * n + 2] += s2;
+    if (!(fb & 1u)) x[3 * n + 0] += s0;
+    if (!(fb & 2u)) x[3 * n + 1] += s1;
+    if (!(fb & 4u)) x[3 * n + 2] += s2;
 }
 
 template <typename T, typename CT>
@@ -643,7 +741,7 @@ __global__ void coarse_assemble_kernel(const double* __restrict__ E, double* __r
     A[t] = s;
 }
 
-// Fixed DOFs (nodes with i == 0): zero row and column, unit diagonal.
+// Fixed DOFs: zero row and column, unit diagonal.
 __global__ void coarse_fix_kernel(double* __restrict__ A, GridDims d)
 {
     const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
@@ -651,7 +749,7 @@ __global__ void coarse_fix_kernel(double* __restrict__ A, GridDims d)
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ndof * ndof) return;
     const long long r = t / ndof, c = t % ndof;
-    const bool fr = ((r / 3) % NX) == 0, fc = ((c / 3) % NX) == 0;
+    const bool fr = fix_dof(d, r), fc = fix_dof(d, c);
     if (fr || fc) A[t] = (r == c) ? 1.0 : 0.0;
 }
 
@@ -670,7 +768,49 @@ __global__ void free_mask_kernel(uint8_t* __restrict__ mask, GridDims d)
     const long long ndof = 3LL * (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ndof) return;
-    mask[t] = ((t / 3) % (d.nx + 1)) != 0;
+    mask[t] = !fix_dof(d, t);
+}
+
+// The bridge's load: a unit pressure on the top face y = ny h, pointing down (-y), as
+// consistent nodal forces -p h^2 / 4 from each of the (up to four) top faces around a
+// node (the bilinear face integral of a uniform pressure); 0 on fixed DOFs. h2 = h^2.
+__global__ void bridge_load_kernel(double* __restrict__ f, GridDims d, double h2)
+{
+    const int NX = d.nx + 1, NY = d.ny + 1;
+    const long long ndof = 3LL * NX * NY * (d.nz + 1);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ndof) return;
+    const long long n = t / 3;
+    const int c = (int)(t - 3 * n);
+    int i, j, k;
+    node_coords(n, NX, NY, i, j, k);
+    double v = 0.0;
+    if (c == 1 && j == d.ny && !fix_dof(d, t)) {
+        const int fx = (i > 0) + (i < d.nx), fz = (k > 0) + (k < d.nz);   // top faces touching the node
+        v = -0.25 * h2 * (double)(fx * fz);
+    }
+    f[t] = v;
+}
+
+// Per-node fixed components of the bridge's supports on level l of a hierarchy whose
+// fine grid has nz_f elements in z: fine node (i, j, k) is fixed in every component at
+// (0, 0, k) and in y and z at (nx_f, 0, k) for k in {0, nz_f/2, nz_f}; coarse node
+// (I, J, K) takes the components of fine node (2^l I, 2^l J, 2^l K) (injection).
+__global__ void bridge_fix_kernel(uint8_t* __restrict__ fix, GridDims d, int level, int nx_f, int nz_f)
+{
+    const int NX = d.nx + 1, NY = d.ny + 1;
+    const long long nn = (long long)NX * NY * (d.nz + 1);
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    int I, J, K;
+    node_coords(n, NX, NY, I, J, K);
+    const int i = I << level, j = J << level, k = K << level;
+    unsigned b = 0;
+    if (j == 0 && (k == 0 || 2 * k == nz_f || k == nz_f)) {
+        if (i == 0) b = 7u;
+        else if (i == nx_f) b = 6u;
+    }
+    fix[n] = (uint8_t)b;
 }
 
 // dc_e = -p (1 - rho_min) rho_e^(p-1) u_e^T K0 u_e * E0 h (scale folded in K0/caller).
@@ -692,8 +832,9 @@ sensitivity_kernel(const double* __restrict__ u, const double* __restrict__ rho,
         const int ox = (a == 1 || a == 2 || a == 5 || a == 6), oy = (a == 2 || a == 3 || a == 6 || a == 7), oz = a >= 4;
         const int ni = ex + ox;
         const long long m = ni + (long long)NX * ((ey + oy) + (long long)NY * (ez + oz));
+        const unsigned mb = fix_bits(d, m, ni);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) ue[3 * a + c] = (ni == 0) ? 0.0 : u[3 * m + c];
+        for (int c = 0; c < 3; ++c) ue[3 * a + c] = ((mb >> c) & 1u) ? 0.0 : u[3 * m + c];
     }
     double energy = 0.0;
 #pragma unroll
