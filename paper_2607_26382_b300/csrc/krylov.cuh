@@ -576,6 +576,25 @@ __device__ __forceinline__ void sym_gj_tile(const double* __restrict__ Min, doub
         Wp[i][r] = (i < bb) ? c : 0.0;
     }
     __syncthreads();
+    // the 4 x 4 dots of this thread's entries, register-blocked (each operand read once
+    // per pivot; the sum over pivots runs in the same order for every entry)
+    double dots[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) dots[a][b] = 0.0;
+#pragma unroll
+    for (int i = 0; i < SGJ_B; ++i) {
+        double vp[4], wq[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) vp[a] = Vp[i][threadIdx.y + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) wq[b] = Wq[i][threadIdx.x + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) dots[a][b] = fma(vp[a], wq[b], dots[a][b]);
+    }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int r = threadIdx.y + 16 * a, p = p0 + r;
@@ -593,11 +612,8 @@ __device__ __forceinline__ void sym_gj_tile(const double* __restrict__ Min, doub
             } else if (inq) {
                 out = -Wp[q - k][r];
             } else {
-                double dot = 0.0;
-#pragma unroll
-                for (int i = 0; i < SGJ_B; ++i) dot = fma(Vp[i][r], Wq[i][c], dot);
                 const double old = Min[(long long)p * n + q];
-                out = (q < k) ? old + dot : old - dot;
+                out = (q < k) ? old + dots[a][b] : old - dots[a][b];
             }
             Mout[(long long)p * n + q] = out;
             if (next_here && p >= kn && q < kn + bbn) {   // (p <= q, so p < kn + bbn too)
