@@ -414,6 +414,11 @@ int gf_batch_grid(gf_batch* b, int i, gf_grid** g);
 int gf_batch_set_state(gf_batch* b, int i, const double* rho_hat, double p, const double* f);
 /* Copy state i's current solution into u (n_dof doubles, device); blocks. */
 int gf_batch_solution(gf_batch* b, int i, double* u);
+/* Coarse-level operators of every state (as gf_set_coarse_operator for one grid):
+ * GF_COARSE_REDISCRETISED (default) or GF_COARSE_GALERKIN. The lockstep coarsest
+ * inverses then assemble each state's Galerkin coarsest operator, and every state's
+ * result stays bit-identical to its single grid's. Drops the captured steps. */
+int gf_batch_set_coarse_operator(gf_batch* b, int kind);
 /* Autotuner: time the node stencils at 64/128/256 threads per block once per
  * distinct grid shape and keep the fastest (results do not depend on the pick).
  * tpb_out (host, optional): 2*n_states ints, [FP64, FP32] block size per state. */

@@ -39,7 +39,7 @@ EXPORTED = [
     "gf_batch_solution", "gf_batch_autotune", "gf_batch_select_floor", "gf_batch_stats",
     "gf_mlp_create", "gf_mlp_destroy", "gf_mlp_set_norm", "gf_mlp_get_params", "gf_mlp_forward",
     "gf_mlp_loss_grad", "gf_mlp_train", "gf_mlp_predict", "gf_select_features", "gf_apply_K_split",
-    "gf_set_coarse_operator", "gf_set_geometry", "gf_bridge_load",
+    "gf_set_coarse_operator", "gf_set_geometry", "gf_bridge_load", "gf_batch_set_coarse_operator",
 ]
 
 
@@ -139,6 +139,7 @@ def lib():
         "gf_batch_set_state": [P, c_int, P, c_double, P],
         "gf_batch_solution": [P, c_int, P],
         "gf_batch_autotune": [P, POINTER(c_int)],
+        "gf_batch_set_coarse_operator": [P, c_int],
         "gf_batch_select_floor": [P, POINTER(Policy), POINTER(SelectInfo)],
         "gf_batch_stats": [P, POINTER(c_longlong)],
         "gf_mlp_create": [POINTER(ctypes.c_float), P, POINTER(P)],
@@ -510,6 +511,10 @@ class Batch:
     def solution(self, i, u):
         _check(lib().gf_batch_solution(self._h, int(i), _ptr(u, _torch().float64, self.n_dof[i], "u")))
         return u
+
+    def set_coarse_operator(self, kind):
+        """gf_batch_set_coarse_operator: GF_COARSE_REDISCRETISED or GF_COARSE_GALERKIN for every state."""
+        _check(lib().gf_batch_set_coarse_operator(self._h, int(kind)))
 
     def autotune(self):
         out = (c_int * (2 * len(self)))()

@@ -409,7 +409,10 @@ int batch_set_floor(gf_batch* b, const std::vector<int>& active, const std::vect
         const long long n = g->nc;
         const long long steps = g->sym_gj ? (n + gf::SGJ_B - 1) / gf::SGJ_B : (n + 1) / 2;
         double* start = (steps & 1) ? g->Agj : g->Ainv;   // see batch_gj_step_kernel / batch_sym_gj_kernel
-        LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, (const double*)c.E64, start, c.dims(), g->K0d);
+        if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1)   // as build_coarse_inverse of one grid
+            LAUNCH(g, nblk(n * n), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, start, c.dims());
+        else
+            LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, (const double*)c.E64, start, c.dims(), g->K0d);
         LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, start, c.dims());
     }
     CK(cudaMemcpyAsync(b->d_active, active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, b->stream));
@@ -593,6 +596,15 @@ int gf_batch_solution(gf_batch* b, int i, double* u)
     if (!b || i < 0 || i >= b->B || !u) return set_err(GF_ERR_ARG, "state index / null pointer");
     CK(cudaMemcpyAsync(u, b->u[i], sizeof(double) * b->g[i]->ndof, cudaMemcpyDeviceToDevice, b->stream));
     CK(cudaStreamSynchronize(b->stream));
+    return GF_OK;
+}
+
+int gf_batch_set_coarse_operator(gf_batch* b, int kind)
+{
+    if (!b) return set_err(GF_ERR_ARG, "null batch");
+    for (gf_grid* g : b->g) RET(gf_set_coarse_operator(g, kind));
+    batch_drop_graphs(b);   // the captured step graphs hold the other V-cycle
+    b->key_prec = -1;
     return GF_OK;
 }
 

@@ -95,3 +95,45 @@ def test_batch_rejects_single_grid_options(gf):
             batch.select_floor(gf.policy_defaults(**kw))
     assert batch.select_floor(gf.policy_defaults())[0]["status"] in (gf.GF_ACCEPTED, gf.GF_NO_ADMISSIBLE_FLOOR)
     batch.close()
+
+
+@pytest.mark.parametrize("prec,outer", [(0, 0), (1, 2), (1, 0)])
+def test_batch_galerkin_matches_single_state(gf, prec, outer):
+    """Galerkin coarse operators in the batch (gf_batch_set_coarse_operator): every state's
+    Algorithm-1 result and solution equal its single grid's with the same coarse operator,
+    bit for bit (the lockstep coarsest inverses assemble the Galerkin coarsest matrices)."""
+    L = 3
+    pol = gf.policy_defaults(rho0=1e-8, ladder=[1e-5, 1e-4, 1e-3], kmax=120, solve_prec=prec, solve_outer=outer)
+    batch = gf.Batch([s[0] for s in STATES], levels=L)
+    batch.set_coarse_operator(gf.GF_COARSE_GALERKIN)
+    rhos, fs = [], []
+    for i, (dims, kind, seed, q) in enumerate(STATES):
+        rho = dev(_rho(dims, kind, seed, q))
+        f = dev(O.cantilever_load(O.Mesh(*dims)))
+        rhos.append(rho)
+        fs.append(f)
+        batch.set_state(i, rho, f, 3.0)
+    tuned = batch.autotune()
+    res = batch.select_floor(pol)
+    for i, (dims, kind, seed, q) in enumerate(STATES):
+        g = gf.create_grid(*dims, levels=L)
+        g.set_coarse_operator(gf.GF_COARSE_GALERKIN)
+        g.set_stencil_blocks(*tuned[i])
+        g.set_density(rhos[i], 3.0)
+        u1 = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        ref = g.select_floor(fs[i], u1, pol)
+        got = res[i]
+        for key in ("status", "floor_index", "escalated", "eta", "r50", "r100"):
+            a, b = got[key], ref[key]
+            assert a == b or (isinstance(a, float) and np.isnan(a) and np.isnan(b)), (i, key, a, b)
+        assert got["attempts"] == ref["attempts"], i
+        u2 = torch.zeros_like(u1)
+        batch.solution(i, u2)
+        if got["status"] == gf.GF_ACCEPTED:
+            assert torch.equal(u1, u2), i
+            m = O.Mesh(*dims)
+            E = O.young_modulus(_rho(dims, kind, seed, q), got["rho_min"], 3.0)
+            eta = O.true_residual(m, E, O.element_stiffness(), O.cantilever_load(m), u2.cpu().numpy())
+            assert eta <= 1e-6 * (1 + 1e-9)
+        g.close()
+    batch.close()
