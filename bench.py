@@ -582,8 +582,10 @@ def run_b300(args):
               "launches_in_timed_region": st["apply_K_fp64"], "share_of_timed_region_est": share_fp64}
     stencil = {"bound": "alu", "achieved": flops / t_32 / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                "frac": flops / t_32 / 1e12 / fp32_peak,
-               "traffic": profiled_traffic("node_stencil_fp32_96x48x48.md", *FP32_ST_SPAN),
-               "kernel": "node_stencil_f32x2_kernel (FP32 V-cycle stencil, fine level)",
+               "traffic": None,
+               "kernel": ("modal_stencil_f32_kernel (the FP32 V-cycle's fine-level operator in the sum/difference "
+                          "basis; achieved and frac in dense-equivalent flops, 1152 per element, against the FP32 "
+                          "FMA peak: it executes ~171 FP32 instructions per element and is issue-bound)"),
                "peak_source": FP32_PEAK_NOTE, "gdofs": g.n_dof / t_32 / 1e9, "ms_per_launch": t_32 * 1e3}
     split = {"bound": "hbm", "achieved": 7.36e6 * (g.n_dof / 698691.0) / t_s / 1e9, "peak": hbm, "unit": "GB/s",
              "kernel": "apply_split_tc_kernel (split-integer FP64-class K*u, the outer-2 form)",

@@ -133,6 +133,8 @@ struct gf_grid {
     std::vector<Level> lv;
     gf::K0Param<double> K0d;
     gf::ModalCoef Kmodal;             // K0 in the sum/difference basis (apply_modal_kernel)
+    gf::ModalCoefF Kmodal32;          // the same in FP32 with K0's node blocks (modal_stencil_f32_kernel)
+    bool modal_f32 = true;            // level-0 FP32 stencils in the modal basis (GF_MODAL_F32=0: node stencils)
     int4* modal_items = nullptr;      // work items of the modal FP64 K*u (device; null: dense stencil)
     int modal_n = 0, modal_bx = 32;   // item count; CTA tile 32 x 16 or 16 x 32 element columns
     bool sym_gj = true;               // coarsest inverse by the blocked symmetric sweep (GF_SYM_GJ=0: two-pivot form)
@@ -280,6 +282,15 @@ int tiled_f32(gf_grid* g, int l, const float* x, const BT* b, OT* out, const flo
                         (L.nz + 1 + cz - 1) / cz);
         LAUNCH_SMEM(g, grid, gf::S3_THREADS, sizeof(gf::S3Smem), (gf::stencil_tc32_kernel<MODE, BT, OT>), x, b, out,
                     E, L.dims(), g->Msplit, (const gf::S3BFrag*)g->B3, (float)g->s_split, omega, cz, halt);
+        return GF_OK;
+    }
+    if (l == 0 && g->modal_f32 && g->modal_items && !L.fix && g->tpb[1] > 0) {   // the modal FP32 fine level
+        if (g->modal_bx == 32)
+            LAUNCH(g, g->modal_n, dim3(32, 16), (gf::modal_stencil_f32_kernel<MODE, BT, OT, 32, 16>), x, b, out, E,
+                   L.dims(), g->Kmodal32, omega, (const int4*)g->modal_items, halt);
+        else
+            LAUNCH(g, g->modal_n, dim3(16, 32), (gf::modal_stencil_f32_kernel<MODE, BT, OT, 16, 32>), x, b, out, E,
+                   L.dims(), g->Kmodal32, omega, (const int4*)g->modal_items, halt);
         return GF_OK;
     }
     if (g->tpb[1] > 0 && g->f32x2) {   // the same, with paired FMAs
@@ -1744,6 +1755,21 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         g->K0f.k[q] = (float)K[q];
     }
     g->Kmodal = gf::modal_coef(E0, nu);
+    for (int q = 0; q < 6; ++q) g->Kmodal32.diag[q] = (float)g->Kmodal.diag[q];
+    for (int q = 0; q < 4; ++q) g->Kmodal32.cross[q] = (float)g->Kmodal.cross[q];
+    for (int a = 0; a < 8; ++a) {
+        const int r0 = 3 * a;
+        g->Kmodal32.blk[a][0] = (float)K[(r0 + 0) * 24 + r0 + 0];
+        g->Kmodal32.blk[a][1] = (float)K[(r0 + 1) * 24 + r0 + 1];
+        g->Kmodal32.blk[a][2] = (float)K[(r0 + 2) * 24 + r0 + 2];
+        g->Kmodal32.blk[a][3] = (float)K[(r0 + 0) * 24 + r0 + 1];
+        g->Kmodal32.blk[a][4] = (float)K[(r0 + 0) * 24 + r0 + 2];
+        g->Kmodal32.blk[a][5] = (float)K[(r0 + 1) * 24 + r0 + 2];
+    }
+    {
+        const char* e = getenv("GF_MODAL_F32");
+        g->modal_f32 = !(e && e[0] == '0');
+    }
     {
         const char* e = getenv("GF_SYM_GJ");
         g->sym_gj = !(e && e[0] == '0');

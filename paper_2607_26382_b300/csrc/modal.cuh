@@ -149,10 +149,11 @@ inline std::vector<int4> modal_plan(int nx, int ny, int nz, int bx, int by, int 
 }
 
 // 2D sum/difference transform of a face: v[x + 2y] -> f[bx + 2by] = sum s_x^bx s_y^by v.
-__device__ __forceinline__ void face_fwd(const double v[4], double f[4])
+template <typename T>
+__device__ __forceinline__ void face_fwd(const T v[4], T f[4])
 {
-    const double sx0 = v[1] + v[0], dx0 = v[1] - v[0];
-    const double sx1 = v[3] + v[2], dx1 = v[3] - v[2];
+    const T sx0 = v[1] + v[0], dx0 = v[1] - v[0];
+    const T sx1 = v[3] + v[2], dx1 = v[3] - v[2];
     f[0] = sx0 + sx1;
     f[2] = sx1 - sx0;
     f[1] = dx0 + dx1;
@@ -160,10 +161,11 @@ __device__ __forceinline__ void face_fwd(const double v[4], double f[4])
 }
 
 // Its transpose: f[bx + 2by] -> v[x + 2y] = sum_beta s_x^bx s_y^by f[beta].
-__device__ __forceinline__ void face_inv(const double f[4], double v[4])
+template <typename T>
+__device__ __forceinline__ void face_inv(const T f[4], T v[4])
 {
-    const double lo0 = f[0] - f[2], hi0 = f[0] + f[2];   // bx = 0: y offset 0 / 1
-    const double lo1 = f[1] - f[3], hi1 = f[1] + f[3];   // bx = 1
+    const T lo0 = f[0] - f[2], hi0 = f[0] + f[2];   // bx = 0: y offset 0 / 1
+    const T lo1 = f[1] - f[3], hi1 = f[1] + f[3];   // bx = 1
     v[0] = lo0 - lo1;
     v[1] = lo0 + lo1;
     v[2] = hi0 - hi1;
@@ -211,7 +213,7 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
             }
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) face_fwd(v[c], f[c]);
+        for (int c = 0; c < 3; ++c) face_fwd<double>(v[c], f[c]);
     };
 
     double bot[3][4];     // modal face of the current element's bottom node plane
@@ -284,7 +286,7 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             double v[4];
-            face_inv(face[c], v);
+            face_inv<double>(face[c], v);
 #pragma unroll
             for (int q = 0; q < 4; ++q) part[q * 3 + c][ty][tx] = v[q];
         }
@@ -307,6 +309,204 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int q = 0; q < 4; ++q) bot[c][q] = top[c][q];
+    }
+}
+
+// ---- the FP32 V-cycle's fine-level operator in the same basis ------------------------
+// The level-0 smoothing sweeps and residual of the mixed V-cycle (and the FP32 K*u) with
+// the modal K0 in FP32: the column walk of apply_modal_kernel (same plan), with the next
+// node plane's values and element modulus loaded one step ahead, and at the gather each
+// node also sums its 3x3 diagonal block from the moduli of its eight elements (kept in
+// shared memory for the current and the previous element layer) for the damped
+// node-block Jacobi update:
+//   MODE ST_APPLY: out = K x;  ST_RESID: out = b - K x;  ST_SWEEP: out = x + omega D_n^-1 (b - K x).
+// Fixed nodes (the clamped face x = 0) read as 0 and are written as 0. FP32 arithmetic
+// (the V-cycle's precision); K*u rounds differently from the node stencil, within FP32.
+struct ModalCoefF {
+    float diag[6], cross[4];
+    float blk[8][6];   // the 3x3 diagonal block of K0 at local node a: d00 d11 d22 d01 d02 d12
+};
+
+template <int MODE, typename BT, typename OT, int BX, int BY>
+__global__ void __launch_bounds__(MODAL_THREADS, 1)
+modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, OT* __restrict__ out,
+                         const float* __restrict__ E, GridDims d, const __grid_constant__ ModalCoefF C,
+                         float omega, const int4* __restrict__ items, const int* __restrict__ halt)
+{
+    if (halt != nullptr && *halt != 0) return;
+    __shared__ float part[12][BY][BX];     // [corner * 3 + comp][column]
+    __shared__ float Es[2][BY][BX];        // element moduli of the column, by layer parity
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
+    const int4 it = items[blockIdx.x];
+    const int i0 = it.x * (BX - 1), j0 = it.y * (BY - 1);
+    const int k0 = it.z;
+    const int k1 = min(NZ, it.w);
+    const int ex = i0 - 1 + tx, ey = j0 - 1 + ty;
+    const bool col = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
+    const long long plane = (long long)NX * NY;
+    const int ni = i0 + tx, nj = j0 + ty;   // this thread's output node column
+    const bool outnode = tx < BX - 1 && ty < BY - 1 && ni < NX && nj < NY;
+
+    auto load_raw = [&](int kz, float v[3][4]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int qi = ex + (q & 1), qj = ey + (q >> 1);
+            const bool ok = col && kz >= 0 && kz < NZ && qi >= 1;
+            const long long n = qi + (long long)NX * qj + plane * kz;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[c][q] = ok ? __ldg(x + 3 * n + c) : 0.f;
+        }
+    };
+    auto load_E = [&](int kz) -> float {
+        return (col && kz >= 0 && kz < d.nz) ? __ldg(E + ex + (long long)d.nx * (ey + (long long)d.ny * kz)) : 0.f;
+    };
+
+    float bot[3][4], carry[3][4], raw[3][4];
+    load_raw(k0 - 1, raw);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) face_fwd<float>(raw[c], bot[c]);
+    load_raw(k0, raw);                      // the next top face, untransformed
+    float Ecur = load_E(k0 - 1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) carry[c][q] = 0.f;
+
+    for (int ez = k0 - 1; ez < k1; ++ez) {
+        // loads one step ahead: the plane after next, the next element's modulus, and this
+        // step's node values for the update
+        float rawn[3][4];
+        load_raw(ez + 2, rawn);
+        const float Enext = load_E(ez + 1);
+        float xn[3] = {0.f, 0.f, 0.f}, bn[3] = {0.f, 0.f, 0.f};
+        long long nn = 0;
+        if (ez >= k0 && outnode) {
+            nn = ni + (long long)NX * nj + plane * ez;
+            if (MODE != ST_APPLY) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) bn[c] = float(b[3 * nn + c]);
+            }
+            if (MODE == ST_SWEEP) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) xn[c] = x[3 * nn + c];
+            }
+        }
+        float top[3][4];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) face_fwd<float>(raw[c], top[c]);
+        float face[3][4];
+        if (col && ez >= 0 && ez < d.nz) {
+            float m[3][8];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    m[c][q] = top[c][q] + bot[c][q];
+                    m[c][q + 4] = top[c][q] - bot[c][q];
+                }
+            const float s = Ecur;
+            float sd[6], sc[4];
+#pragma unroll
+            for (int k = 1; k < 6; ++k) sd[k] = s * C.diag[k];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sc[k] = s * C.cross[k];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float G[8];
+#pragma unroll
+                for (int beta = 0; beta < 8; ++beta) {
+                    const int bc = (beta >> c) & 1;
+                    const int n = ((beta >> ((c + 1) % 3)) & 1) + ((beta >> ((c + 2) % 3)) & 1);
+                    float t = (bc == 0 && n == 0) ? 0.f : sd[bc * 3 + n] * m[c][beta];
+#pragma unroll
+                    for (int dd = 1; dd < 3; ++dd) {
+                        const int dc = (c + dd) % 3;
+                        const int o = 3 - c - dc;
+                        const int bdd = (beta >> dc) & 1;
+                        if (bc != bdd) {
+                            const int alpha = beta ^ (1 << c) ^ (1 << dc);
+                            const int k = (bc ? 0 : 2) + ((beta >> o) & 1);
+                            t = fmaf(sc[k], m[dc][alpha], t);
+                        }
+                    }
+                    G[beta] = t;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    face[c][q] = carry[c][q] + (G[q] - G[q + 4]);
+                    carry[c][q] = G[q] + G[q + 4];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    face[c][q] = carry[c][q];
+                    carry[c][q] = 0.f;
+                }
+        }
+        const int cur = ez & 1;
+        __syncthreads();   // the previous step's gather has read `part` and Es[cur]
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float v[4];
+            face_inv<float>(face[c], v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) part[q * 3 + c][ty][tx] = v[q];
+        }
+        Es[cur][ty][tx] = Ecur;
+        __syncthreads();
+        if (ez >= k0 && outnode) {
+            float a[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float acc = part[3 * 3 + c][ty][tx] + part[2 * 3 + c][ty][tx + 1];
+                acc += part[1 * 3 + c][ty + 1][tx];
+                acc += part[0 * 3 + c][ty + 1][tx + 1];
+                a[c] = acc;
+            }
+            if (ni == 0) {
+                out[3 * nn + 0] = OT(0);
+                out[3 * nn + 1] = OT(0);
+                out[3 * nn + 2] = OT(0);
+            } else if (MODE == ST_APPLY) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[3 * nn + c] = OT(a[c]);
+            } else if (MODE == ST_RESID) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[3 * nn + c] = OT(bn[c] - a[c]);
+            } else {
+                // the node's 3x3 diagonal block from its eight elements (previous layer: the
+                // node at local z offset 1; current layer: offset 0), in a fixed order
+                float db[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int lz = 0; lz < 2; ++lz) {
+                    const int layer = lz == 0 ? (cur ^ 1) : cur;   // ez - 1, then ez
+                    const int oz = lz == 0 ? 1 : 0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int cx = q & 1, cy = q >> 1;            // column (tx + cx, ty + cy)
+                        const float Ee = Es[layer][ty + cy][tx + cx];
+                        const int la = local_index(1 - cx, 1 - cy, oz);
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) db[k] = fmaf(Ee, C.blk[la][k], db[k]);
+                    }
+                }
+                const float r0 = bn[0] - a[0], r1 = bn[1] - a[1], r2 = bn[2] - a[2];
+                node_block_update<float, OT>(db[0], db[1], db[2], db[3], db[4], db[5], r0, r1, r2, xn, out + 3 * nn,
+                                             omega);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                bot[c][q] = top[c][q];
+                raw[c][q] = rawn[c][q];
+            }
+        Ecur = Enext;
     }
 }
 
