@@ -368,9 +368,17 @@ __global__ void scale_kernel(double* __restrict__ v, long long n, const KState* 
 {
     if (check_status && st->status != KS_RUN) return;
     const double s = st->inv;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n;
-         r += (long long)gridDim.x * blockDim.x)
-        v[r] *= s;
+    // four independent entries per thread and iteration (loads in flight together)
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; r + 3 * stride < n; r += 4 * stride) {
+        const double a0 = v[r], a1 = v[r + stride], a2 = v[r + 2 * stride], a3 = v[r + 3 * stride];
+        v[r] = a0 * s;
+        v[r + stride] = a1 * s;
+        v[r + 2 * stride] = a2 * s;
+        v[r + 3 * stride] = a3 * s;
+    }
+    for (; r < n; r += stride) v[r] *= s;
 }
 
 // r = M f - y (y = K x) into r; partial[b][0] = ||r||^2, partial[b][1] = ||M f||^2.
