@@ -26,7 +26,9 @@ batch102: 102 frozen states of uneven size (nx in {32,48,64,80}, ny = nz = nx/2,
               N states) picking the first floor: its most probable floor, and (c0.9)
               the highest floor it is 90% sure the search must reach.
 oc_loop: a guarded SIMP-OC loop (vol 0.3, filter radius 1.5, p = 3, move 0.2) on the
-  96x48x48 cantilever, Algorithm 1 at every iteration, compared across selectors.
+  96x48x48 cantilever, Algorithm 1 at every iteration, compared across selectors: the
+  plain FP64 full ladder, the mixed form with Eq. (trigger) and with the learned selector
+  (native FP64 Krylov), and the latter two with the FP64-class Krylov.
 oc_reuse: the in-loop settings of Section 4.1.2 (rho0 = 1e-12, ladder {1e-3, 1e-2},
   kmax = 300, tau = 1e-6) on the same loop with the p continuation 1.5 -> 3.5 after
   iteration 15 (no Heaviside projection), mixed solves. Three guarded selectors:
@@ -203,14 +205,17 @@ def oc_loop(args):
     nx, ny, nz = 96, 48, 48
     out = {"workload": f"guarded SIMP-OC {nx}x{ny}x{nz}, {args.iters} iterations, vol 0.3, r_min 1.5, p 3"}
     modes = [("plain_fp64_full", _policy(selector=L.GF_SEL_FULL, solve_prec=L.GF_FP64, solve_outer=0)),
-             ("mixed_rule", _policy(solve_prec=L.GF_MIXED, solve_outer=2))]
+             ("mixed_rule", _policy(solve_prec=L.GF_MIXED, solve_outer=0)),
+             ("mixed_rule_fp64class", _policy(solve_prec=L.GF_MIXED, solve_outer=2))]
     net = None
     if args.train >= 0:
         net, info = train_mlp(args.train)
-        out["selector_training"] = info
-        pol = _policy(solve_prec=L.GF_MIXED, solve_outer=2, selector=L.GF_SEL_MLP)
-        pol.mlp = net.handle
-        modes.append(("mixed_learned", pol))
+        out["selector_training"] = {k: v for k, v in info.items() if k in ("states", "train_states", "held_out_accuracy",
+                                                                            "label_counts", "label_form")}
+        for name, outer in (("mixed_learned", 0), ("mixed_learned_fp64class", 2)):
+            pol = _policy(solve_prec=L.GF_MIXED, solve_outer=outer, selector=L.GF_SEL_MLP)
+            pol.mlp = net.handle
+            modes.append((name, pol))
     for name, pol in modes:
         g = L.create_grid(nx, ny, nz, levels=5)
         f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
