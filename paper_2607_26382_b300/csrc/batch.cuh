@@ -19,6 +19,8 @@ struct BatchTables {
     double** A;        // coarsest dense matrices (the inverses, in the end)
     double** W;        // their second Gauss-Jordan buffers
     int* n;            // coarsest sizes
+    int* m;            // coarsest free-DOF counts (the symmetric sweep's size)
+    int** pos;         // coarsest free-DOF positions (gf_grid::cpos)
 };
 
 __global__ void batch_mark_kernel(KState** st, const int* __restrict__ active, int B)
@@ -76,22 +78,35 @@ batch_gj_step_kernel(BatchTables t, const int* __restrict__ active, int s)
     gj_tile(from_w ? t.W[i] : t.A[i], from_w ? t.A[i] : t.W[i], n, k, p0, q0);
 }
 
-// The blocked symmetric sweep (sym_gj_kernel) on every state's matrix at once: step s
-// takes pivots SGJ_B*s .. SGJ_B*s + SGJ_B - 1. State i runs ceil(n_i/SGJ_B) steps and
-// starts in W_i when that count is odd, so its last step writes the upper triangle of A_i.
-// The P buffers of state i sit past its second matrix buffer, W_i + n_i^2 (as for one grid).
+// The blocked symmetric sweep (sym_gj_kernel) on every state's free-DOF matrix at once:
+// step s takes pivots SGJ_B*s .. SGJ_B*s + SGJ_B - 1. State i runs ceil(m_i/SGJ_B) steps
+// and starts in A_i when that count is odd, so its last step writes the upper triangle
+// (m_i x m_i) into W_i, as for one grid. The P buffers of state i sit past its full
+// second matrix buffer, W_i + n_i^2. Grid: (1 + tiles (tiles + 1) / 2, 1, B) for the
+// largest state's tiles x tiles; block 0 forms the next P, the others one upper tile.
+__device__ __forceinline__ bool batch_sym_from_w(int m, int s)
+{
+    return (((m + SGJ_B - 1) / SGJ_B + s) & 1) == 0;
+}
+
 __global__ void __launch_bounds__(256)
-batch_sym_gj_kernel(BatchTables t, const int* __restrict__ active, int s)
+batch_sym_gj_kernel(BatchTables t, const int* __restrict__ active, int s, int tiles)
 {
     const int i = blockIdx.z;
-    if (!active[i] || blockIdx.y > blockIdx.x) return;
-    const int n = t.n[i], k = SGJ_B * s;
-    if (k >= n || (int)blockIdx.y * SGJ_T >= n || (int)blockIdx.x * SGJ_T >= n) return;   // uniform over the block
-    const int steps = (n + SGJ_B - 1) / SGJ_B;
-    const bool from_w = ((steps & 1) ^ (s & 1)) != 0;
-    double* Pb = t.W[i] + (long long)n * n;
-    sym_gj_tile(from_w ? t.W[i] : t.A[i], from_w ? t.A[i] : t.W[i], n, k, blockIdx.y, blockIdx.x,
-                Pb + SGJ_B * SGJ_B * (s & 1), Pb + SGJ_B * SGJ_B * ((s + 1) & 1));
+    if (!active[i]) return;
+    const int m = t.m[i], k = SGJ_B * s;
+    if (k >= m) return;
+    const bool from_w = batch_sym_from_w(m, s);
+    const double* Min = from_w ? t.W[i] : t.A[i];
+    double* Pb = t.W[i] + (long long)t.n[i] * t.n[i];
+    if (blockIdx.x == 0) {   // the next pivot block's P, as sym_gj_kernel
+        sym_gj_next_p(Min, m, k, Pb + SGJ_B * SGJ_B * (s & 1), Pb + SGJ_B * SGJ_B * ((s + 1) & 1));
+        return;
+    }
+    int tp, tq;   // upper tiles of the largest state's T x T, as sym_gj_kernel
+    sgj_upper_tile((int)blockIdx.x - 1, tiles, tp, tq);
+    if (tp * SGJ_T >= m || tq * SGJ_T >= m) return;   // uniform over the block
+    sym_gj_tile(Min, from_w ? t.A[i] : t.W[i], m, k, tp, tq, Pb + SGJ_B * SGJ_B * (s & 1));
 }
 
 // P of every active state's first pivot block (from the start buffer of its sweep).
@@ -99,30 +114,25 @@ __global__ void __launch_bounds__(256) batch_sym_gj_first_kernel(BatchTables t, 
 {
     const int i = blockIdx.x;
     if (!active[i]) return;
-    const int n = t.n[i];
-    const int steps = (n + SGJ_B - 1) / SGJ_B;
-    const double* M = (steps & 1) ? t.W[i] : t.A[i];
+    const int m = t.m[i];
+    if (m == 0) return;
+    const double* M = batch_sym_from_w(m, 0) ? t.W[i] : t.A[i];
     __shared__ double S[SGJ_B][SGJ_B];
-    const int tid = threadIdx.x, bb = min(SGJ_B, n);
+    const int tid = threadIdx.x, bb = min(SGJ_B, m);
     const int bi = tid / SGJ_B, bj = tid % SGJ_B;
-    if (tid < SGJ_B * SGJ_B && bi < bb && bj < bb) S[bi][bj] = M[(long long)min(bi, bj) * n + max(bi, bj)];
+    if (tid < SGJ_B * SGJ_B && bi < bb && bj < bb) S[bi][bj] = M[(long long)min(bi, bj) * m + max(bi, bj)];
     __syncthreads();
     sgj_invert_block(S, bb, tid);
-    if (tid < SGJ_B * SGJ_B) t.W[i][(long long)n * n + tid] = (bi < bb && bj < bb) ? S[bi][bj] : 0.0;
+    if (tid < SGJ_B * SGJ_B) t.W[i][(long long)t.n[i] * t.n[i] + tid] = (bi < bb && bj < bb) ? S[bi][bj] : 0.0;
 }
 
-// Lower triangles of the active states' A_i from their upper triangles (in place).
-__global__ void batch_sym_mirror_kernel(BatchTables t, const int* __restrict__ active)
+// The active states' full inverses A_i from their free-DOF sweeps in W_i (sym_expand).
+__global__ void batch_sym_expand_kernel(BatchTables t, const int* __restrict__ active)
 {
     const int i = blockIdx.y;
     if (!active[i]) return;
-    const int n = t.n[i];
-    double* A = t.A[i];
-    const long long nn = (long long)n * n;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
-        const int p = (int)(e / n), q = (int)(e % n);
-        if (p > q) A[e] = A[(long long)q * n + p];
-    }
+    sym_expand(t.W[i], t.m[i], t.pos[i], t.A[i], t.n[i], (long long)blockIdx.x * blockDim.x + threadIdx.x,
+               (long long)gridDim.x * blockDim.x);
 }
 
 }  // namespace gf
@@ -406,13 +416,26 @@ int batch_set_floor(gf_batch* b, const std::vector<int>& active, const std::vect
         g->skip_coarse_inverse = false;
         if (rc != GF_OK) return rc;
         Level& c = g->lv[g->L - 1];
+        const bool gal = g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1;   // as build_coarse_inverse of one grid
+        if (g->sym_gj) {   // the free-DOF matrix, in the buffer batch_sym_gj_kernel starts from
+            const long long m = g->ncf;
+            double* start = (((m + gf::SGJ_B - 1) / gf::SGJ_B) & 1) ? g->Ainv : g->Agj;
+            if (gal)
+                LAUNCH(g, nblk(m * m), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, start, c.dims(),
+                       (const int*)g->cidx, (int)m);
+            else
+                LAUNCH(g, nblk(m * m), 256, gf::coarse_assemble_kernel, (const double*)c.E64, start, c.dims(), g->K0d,
+                       (const int*)g->cidx, (int)m);
+            continue;
+        }
         const long long n = g->nc;
-        const long long steps = g->sym_gj ? (n + gf::SGJ_B - 1) / gf::SGJ_B : (n + 1) / 2;
-        double* start = (steps & 1) ? g->Agj : g->Ainv;   // see batch_gj_step_kernel / batch_sym_gj_kernel
-        if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1)   // as build_coarse_inverse of one grid
-            LAUNCH(g, nblk(n * n), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, start, c.dims());
+        double* start = (((n + 1) / 2) & 1) ? g->Agj : g->Ainv;   // see batch_gj_step_kernel
+        if (gal)
+            LAUNCH(g, nblk(n * n), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, start, c.dims(),
+                   (const int*)nullptr, 0);
         else
-            LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, (const double*)c.E64, start, c.dims(), g->K0d);
+            LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, (const double*)c.E64, start, c.dims(), g->K0d,
+                   (const int*)nullptr, 0);
         LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, start, c.dims());
     }
     CK(cudaMemcpyAsync(b->d_active, active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, b->stream));
@@ -420,16 +443,20 @@ int batch_set_floor(gf_batch* b, const std::vector<int>& active, const std::vect
     for (int i = 0; i < B; ++i)
         if (active[i]) nmax = std::max(nmax, b->g[i]->nc);
     if (b->g[0]->sym_gj) {   // the single grid's algorithm, so that states stay bit-identical to it
-        const unsigned st = (unsigned)((nmax + gf::SGJ_T - 1) / gf::SGJ_T);
+        int mmax = 0;
+        for (int i = 0; i < B; ++i)
+            if (active[i]) mmax = std::max(mmax, b->g[i]->ncf);
+        const unsigned st = (unsigned)std::max(1, (mmax + gf::SGJ_T - 1) / gf::SGJ_T);
         gf::batch_sym_gj_first_kernel<<<B, 256, 0, b->stream>>>(b->tab, b->d_active);
         b->launches += 1;
         CK(cudaGetLastError());
-        for (int s = 0; gf::SGJ_B * s < nmax; ++s) {
-            gf::batch_sym_gj_kernel<<<dim3(st, st, B), dim3(16, 16), 0, b->stream>>>(b->tab, b->d_active, s);
+        for (int s = 0; gf::SGJ_B * s < mmax; ++s) {
+            gf::batch_sym_gj_kernel<<<dim3(1 + st * (st + 1) / 2, 1, B), dim3(16, 16), 0, b->stream>>>(
+                b->tab, b->d_active, s, (int)st);
             b->launches += 1;
             CK(cudaGetLastError());
         }
-        gf::batch_sym_mirror_kernel<<<dim3((unsigned)std::max(1, b->sms), B), 256, 0, b->stream>>>(b->tab, b->d_active);
+        gf::batch_sym_expand_kernel<<<dim3((unsigned)std::max(1, b->sms), B), 256, 0, b->stream>>>(b->tab, b->d_active);
         b->launches += 1;
         CK(cudaGetLastError());
         return GF_OK;
@@ -531,6 +558,7 @@ int gf_create_batch(int n_states, const int* dims, int levels, double h, double 
     const size_t P = sizeof(void*) * n_states;
     if (cudaMalloc(&b->tab.st, P) != cudaSuccess || cudaMalloc(&b->tab.hist, P) != cudaSuccess ||
         cudaMalloc(&b->tab.A, P) != cudaSuccess || cudaMalloc(&b->tab.W, P) != cudaSuccess || cudaMalloc(&b->tab.n, sizeof(int) * n_states) != cudaSuccess ||
+        cudaMalloc(&b->tab.m, sizeof(int) * n_states) != cudaSuccess || cudaMalloc(&b->tab.pos, P) != cudaSuccess ||
         cudaMalloc(&b->d_active, sizeof(int) * n_states) != cudaSuccess ||
         cudaMalloc(&b->d_abort, sizeof(int) * n_states) != cudaSuccess)
         return fail(set_err(GF_ERR_OOM, "batch tables"));
@@ -538,15 +566,20 @@ int gf_create_batch(int n_states, const int* dims, int levels, double h, double 
         cudaHostGetDevicePointer((void**)&b->gather_dev, b->gather_host, 0) != cudaSuccess)
         return fail(set_err(GF_ERR_CUDA, "mapped gather"));
     std::vector<double*> A(n_states), W(n_states);
-    std::vector<int> n(n_states);
+    std::vector<int*> pos(n_states);
+    std::vector<int> n(n_states), m(n_states);
     for (int i = 0; i < n_states; ++i) {
         A[i] = b->g[i]->Ainv;
         W[i] = b->g[i]->Agj;
         n[i] = b->g[i]->nc;
+        m[i] = b->g[i]->ncf;
+        pos[i] = b->g[i]->cpos;
     }
     if (cudaMemcpy(b->tab.A, A.data(), P, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->tab.W, W.data(), P, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->tab.n, n.data(), sizeof(int) * n_states, cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(b->tab.n, n.data(), sizeof(int) * n_states, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->tab.m, m.data(), sizeof(int) * n_states, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->tab.pos, pos.data(), P, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(set_err(GF_ERR_CUDA, "tables"));
     *out = b;
     return GF_OK;
@@ -568,7 +601,7 @@ int gf_destroy_batch(gf_batch* b)
     if (b->evFork) cudaEventDestroy(b->evFork);
     if (b->capS) cudaStreamDestroy(b->capS);
     cudaFree(b->tab.st); cudaFree(b->tab.hist); cudaFree(b->tab.A); cudaFree(b->tab.W);
-    cudaFree(b->tab.n); cudaFree(b->d_active); cudaFree(b->d_abort);
+    cudaFree(b->tab.n); cudaFree(b->tab.m); cudaFree(b->tab.pos); cudaFree(b->d_active); cudaFree(b->d_abort);
     if (b->gather_host) cudaFreeHost(b->gather_host);
     delete b;
     return GF_OK;

@@ -239,15 +239,16 @@ gal_node_kernel(const T* __restrict__ x, const BT* __restrict__ b, OT* __restric
                              out + 3 * n, omega);
 }
 
-// Dense coarsest operator from element matrices (coarse_assemble_kernel's layout and
+// Dense coarsest operator from element matrices (coarse_assemble_kernel's layouts and
 // element order): A[r][c] = sum over the elements holding both nodes of K_e[3 a_r + c_r][3 a_c + c_c].
-__global__ void gal_assemble_kernel(const double* __restrict__ Ke, double* __restrict__ A, GridDims d)
+__global__ void gal_assemble_kernel(const double* __restrict__ Ke, double* __restrict__ A, GridDims d,
+                                    const int* __restrict__ idx = nullptr, int m = 0)
 {
     const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
     const long long ndof = 3LL * NX * NY * NZ;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ndof * ndof) return;
-    const long long r = t / ndof, c = t % ndof;
+    long long r, c;
+    if (!coarse_entry(t, ndof, idx, m, r, c)) return;
     const long long nr = r / 3, nc = c / 3;
     const int cr = (int)(r % 3), cc = (int)(c % 3);
     const int ir = (int)(nr % NX), jr = (int)((nr / NX) % NY), kr = (int)(nr / ((long long)NX * NY));

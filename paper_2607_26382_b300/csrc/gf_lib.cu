@@ -157,6 +157,9 @@ struct gf_grid {
     double* Ainv = nullptr;
     int nc = 0;
     double* Agj = nullptr;            // second buffer of the double-buffered Gauss-Jordan
+    int* cpos = nullptr;              // coarsest level: position of each DOF among the free ones (-1: fixed)
+    int* cidx = nullptr;              // coarsest level: the free DOFs in order; ncf of them (+1 word: the count)
+    int ncf = 0;
     int* dflag = nullptr;
     // Krylov workspace
     int m_alloc = 0;
@@ -1102,34 +1105,61 @@ int build_galerkin(gf_grid* g)
     return GF_OK;
 }
 
+// The coarsest level's free-DOF map (cpos, cidx, ncf) for the current supports.
+int build_coarse_map(gf_grid* g)
+{
+    const Level& c = g->lv[g->L - 1];
+    gf::coarse_map_kernel<<<1, 32, 0, g->stream>>>(c.dims(), g->cpos, g->cidx, g->cidx + g->nc);
+    CK(cudaGetLastError());
+    int m = 0;
+    CK(cudaMemcpyAsync(&m, g->cidx + g->nc, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    g->ncf = m;
+    return GF_OK;
+}
+
 int build_coarse_inverse(gf_grid* g)
 {
     Level& c = g->lv[g->L - 1];
     const long long n = g->nc;
     gf::K0Param<double> K = g->K0d;   // the level's E64 already carries h
-    // ceil(n/2) double-buffered steps; start in the buffer that makes the last one land in Ainv
-    const long long steps = (n + 1) / 2;
-    double* src = (steps & 1) ? g->Agj : g->Ainv;
-    if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1)
-        LAUNCH(g, nblk(n * n), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, src, c.dims());
-    else
-        LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, c.E64, src, c.dims(), K);
-    LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, src, c.dims());
-    if (g->sym_gj) {   // blocked symmetric sweep on the upper triangle, then the mirror into Ainv
-        const unsigned tiles = (unsigned)((n + gf::SGJ_T - 1) / gf::SGJ_T);
+    if (g->sym_gj) {
+        // blocked symmetric sweep on the upper triangle of the operator restricted to the
+        // free DOFs (m x m; the fixed ones only carry identity rows), ceil(m / SGJ_B)
+        // double-buffered steps ending in Agj, then the expansion into Ainv (n x n)
+        const long long m = g->ncf;
+        const long long steps = (m + gf::SGJ_B - 1) / gf::SGJ_B;
+        double* src = (steps & 1) ? g->Ainv : g->Agj;
+        if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1)
+            LAUNCH(g, nblk(m * m), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, src, c.dims(),
+                   (const int*)g->cidx, (int)m);
+        else
+            LAUNCH(g, nblk(m * m), 256, gf::coarse_assemble_kernel, c.E64, src, c.dims(), K, (const int*)g->cidx,
+                   (int)m);
+        const unsigned tiles = (unsigned)((m + gf::SGJ_T - 1) / gf::SGJ_T);
         double* Pb = g->Agj + n * n;   // two P buffers past the matrix
-        LAUNCH(g, 1, 256, gf::sym_gj_first_kernel, (const double*)src, (int)n, Pb);
-        for (long long k = 0; k < n; k += gf::SGJ_B) {
+        if (m > 0) LAUNCH(g, 1, 256, gf::sym_gj_first_kernel, (const double*)src, (int)m, Pb);
+        for (long long k = 0; k < m; k += gf::SGJ_B) {
             double* dst = (src == g->Ainv) ? g->Agj : g->Ainv;
             const int s = (int)(k / gf::SGJ_B);
-            LAUNCH(g, dim3(tiles, tiles), dim3(16, 16), gf::sym_gj_kernel, (const double*)src, dst, (int)n, (int)k,
+            LAUNCH(g, 1 + tiles * (tiles + 1) / 2, dim3(16, 16), gf::sym_gj_kernel, (const double*)src, dst, (int)m, (int)k,
                    (const double*)(Pb + gf::SGJ_B * gf::SGJ_B * (s & 1)), Pb + gf::SGJ_B * gf::SGJ_B * ((s + 1) & 1));
             src = dst;
         }
-        LAUNCH(g, std::min<long long>(nblk(n * n), 4LL * g->sms), 256, gf::sym_mirror_kernel, (const double*)src,
-               g->Ainv, (int)n);
+        LAUNCH(g, std::min<long long>(nblk(n * n), 4LL * g->sms), 256, gf::sym_expand_kernel, (const double*)g->Agj,
+               (int)m, (const int*)g->cpos, g->Ainv, (int)n);
         return GF_OK;
     }
+    // two-pivot Gauss-Jordan on all DOFs: ceil(n/2) double-buffered steps; start in the
+    // buffer that makes the last one land in Ainv
+    const long long steps = (n + 1) / 2;
+    double* src = (steps & 1) ? g->Agj : g->Ainv;
+    if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1)
+        LAUNCH(g, nblk(n * n), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, src, c.dims(), (const int*)nullptr,
+               0);
+    else
+        LAUNCH(g, nblk(n * n), 256, gf::coarse_assemble_kernel, c.E64, src, c.dims(), K, (const int*)nullptr, 0);
+    LAUNCH(g, nblk(n * n), 256, gf::coarse_fix_kernel, src, c.dims());
     const unsigned tiles = (unsigned)((n + gf::GJ_T - 1) / gf::GJ_T);
     for (int k = 0; k < n; k += 2) {
         double* dst = (src == g->Ainv) ? g->Agj : g->Ainv;
@@ -1909,6 +1939,7 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     int r = GF_OK;
     g->nbr = (int)std::min<long long>(2LL * g->sms, std::max<long long>(1, (g->ndof + 1023) / 1024));
     if ((r = allocT(&g->Ainv, (size_t)g->nc * g->nc)) || (r = allocT(&g->Agj, (size_t)g->nc * g->nc + 2 * gf::SGJ_B * gf::SGJ_B)) ||
+        (r = allocT(&g->cpos, (size_t)g->nc)) || (r = allocT(&g->cidx, (size_t)g->nc + 1)) ||
         (r = allocT(&g->dflag, 4)) || (r = allocT(&g->rho64, g->nel)) ||
         (r = allocT(&g->rho16, g->nel)) || (r = allocT(&g->work, g->ndof)) ||
         (r = allocT(&g->partial, (size_t)g->nbr * 40)) || (r = allocT(&g->st, 1)) || (r = allocT(&g->gst, 1)) ||
@@ -1928,6 +1959,7 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         const char* e = getenv("GF_GRAPHS");
         g->use_graphs = !(e && e[0] == '0');
     }
+    if ((r = build_coarse_map(g)) != GF_OK) return fail(r);
     if (g->modal_items && !getenv("GF_MODAL_CHUNK") && !getenv("GF_MODAL_BX"))
         if ((r = modal_autotune(g)) != GF_OK) return fail(r);
     *out = g;
@@ -2041,7 +2073,7 @@ int gf_destroy_grid(gf_grid* g)
     cudaFree(g->ls_partial); cudaFree(g->ls_alpha);
     cudaFree(g->fcV); cudaFree(g->fcZ); cudaFree(g->fcR); cudaFree(g->fcD); cudaFree(g->fcQ); cudaFree(g->fcZT);
     cudaFree(g->fc); cudaFree(g->fc_partial);
-    cudaFree(g->Ainv); cudaFree(g->Agj); cudaFree(g->dflag); cudaFree(g->cheb); cudaFree(g->cheb_ss);
+    cudaFree(g->Ainv); cudaFree(g->Agj); cudaFree(g->cpos); cudaFree(g->cidx); cudaFree(g->dflag); cudaFree(g->cheb); cudaFree(g->cheb_ss);
     cudaFree(g->rho64); cudaFree(g->rho16); cudaFree(g->work); cudaFree(g->partial);
     cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Vd); cudaFree(g->pdd); cudaFree(g->ddticket); cudaFree(g->Z); cudaFree(g->hist);
     cudaFree(g->ckx);
@@ -2181,6 +2213,7 @@ int gf_set_geometry(gf_grid* g, int geometry)
             c.fix = nullptr;
         }
     }
+    RET(build_coarse_map(g));
     drop_graphs(g);
     g->geom = geometry;
     g->has_floor = false;   // gf_set_floor again: the coarsest inverse carries the supports

@@ -512,9 +512,9 @@ gj_step_kernel(const double* __restrict__ Ain, double* __restrict__ Aout, int n,
 // Every entry costs SGJ_B FMAs per launch on n^2/2 entries: n^3/2 FMAs in all, half of
 // the full-matrix two-pivot form. A block owns a SGJ_T x SGJ_T upper tile and forms W
 // for its columns (and rows, when the tile holds the pivot columns). P of each step is
-// computed once: the block holding the next pivot block on its diagonal inverts that
-// block from its own outputs and leaves P for the next launch in a small buffer
-// (sym_gj_first_kernel makes the first one).
+// computed once: one extra block of the launch forms the next pivot block's entries
+// with the tile's operations and inverts it while the tiles run, leaving P for the next
+// launch in a small buffer (sym_gj_first_kernel makes the first one).
 constexpr int SGJ_B = 8, SGJ_T = 64;
 
 // In-place inverse of the bb x bb SPD block S by the sweep (threads 0 .. SGJ_B^2 - 1 own
@@ -525,10 +525,10 @@ __device__ __forceinline__ void sgj_invert_block(double (*S)[SGJ_B], int bb, int
     const bool own = tid < SGJ_B * SGJ_B && bi < bb && bj < bb;
     for (int j = 0; j < bb; ++j) {
         double nv = 0.0;
-        if (own) {
-            const double piv = S[j][j], rj = S[j][bj], ci = S[bi][j], old = S[bi][bj];
-            if (bi == j) nv = (bj == j) ? 1.0 / piv : rj / piv;
-            else nv = (bj == j) ? -ci / piv : old - ci * (rj / piv);
+        if (own) {   // one reciprocal per pivot, the same in every lane (no divergent divides)
+            const double ip = 1.0 / S[j][j], rj = S[j][bj] * ip, ci = S[bi][j], old = S[bi][bj];
+            if (bi == j) nv = (bj == j) ? ip : rj;
+            else nv = (bj == j) ? -ci * ip : old - ci * rj;
         }
         __syncthreads();
         if (own) S[bi][bj] = nv;
@@ -548,31 +548,43 @@ __global__ void __launch_bounds__(256) sym_gj_first_kernel(const double* __restr
     if (tid < SGJ_B * SGJ_B) Pout[tid] = (bi < bb && bj < bb) ? S[bi][bj] : 0.0;
 }
 
-__device__ __forceinline__ void sym_gj_tile(const double* __restrict__ Min, double* __restrict__ Mout, int n, int k,
-                                            int tp, int tq, const double* __restrict__ Pin, double* __restrict__ Pout)
+// V_p's entry i for the pivot block at k (bb pivots): 0 inside the block and past n.
+__device__ __forceinline__ double sgj_v(const double* __restrict__ Min, int n, int k, int bb, int p, int i)
 {
-    __shared__ double Pm[SGJ_B][SGJ_B], Pn[SGJ_B][SGJ_B];
+    if (p >= n || i >= bb) return 0.0;
+    if (p < k) return Min[(long long)p * n + k + i];
+    if (p >= k + bb) return Min[(long long)(k + i) * n + p];
+    return 0.0;
+}
+
+__device__ __forceinline__ void sym_gj_tile(const double* __restrict__ Min, double* __restrict__ Mout, int n, int k,
+                                            int tp, int tq, const double* __restrict__ Pin)
+{
+    __shared__ double Pm[SGJ_B][SGJ_B];
     __shared__ double Vp[SGJ_B][SGJ_T], Vq[SGJ_B][SGJ_T], Wq[SGJ_B][SGJ_T], Wp[SGJ_B][SGJ_T];
     const int tid = threadIdx.y * 16 + threadIdx.x;
     const int bb = min(SGJ_B, n - k);
     const int p0 = tp * SGJ_T, q0 = tq * SGJ_T;
-    const int kn = k + SGJ_B, bbn = min(SGJ_B, n - kn);        // next pivot block
-    const bool next_here = bbn > 0 && tp == tq && kn / SGJ_T == tp;
     if (tid < SGJ_B * SGJ_B) Pm[tid / SGJ_B][tid % SGJ_B] = Pin[tid];
-    // V for the tile's rows and columns (0 inside the pivot block and outside the matrix)
-    auto vrow = [&](int p, int i) -> double {
-        if (p >= n || i >= bb) return 0.0;
-        if (p < k) return Min[(long long)p * n + k + i];
-        if (p >= k + bb) return Min[(long long)(k + i) * n + p];
-        return 0.0;
-    };
     for (int e = tid; e < SGJ_B * SGJ_T; e += 256) {
         const int i = e / SGJ_T, r = e % SGJ_T;
-        Vp[i][r] = vrow(p0 + r, i);
-        Vq[i][r] = vrow(q0 + r, i);
+        Vp[i][r] = sgj_v(Min, n, k, bb, p0 + r, i);
+        Vq[i][r] = sgj_v(Min, n, k, bb, q0 + r, i);
     }
+    // this thread's old entries start its accumulators (loaded early, so that their
+    // latency hides behind the dots)
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int p = p0 + threadIdx.y + 16 * a, q = q0 + threadIdx.x + 16 * b;
+            acc[a][b] = (p < n && q < n && q >= p) ? Min[(long long)p * n + q] : 0.0;
+        }
     __syncthreads();
-    const bool need_wp = q0 < k + bb && q0 + SGJ_T > k;   // the tile holds pivot columns
+    // W for the tile's columns, stored as -s W_q (the sign of the update), and for its rows
+    // when the tile holds the pivot columns
+    const bool need_wp = q0 < k + bb && q0 + SGJ_T > k;
     for (int e = tid; e < SGJ_B * SGJ_T; e += 256) {
         const int i = e / SGJ_T, r = e % SGJ_T;
         double a = 0.0, c = 0.0;
@@ -580,17 +592,13 @@ __device__ __forceinline__ void sym_gj_tile(const double* __restrict__ Min, doub
             a = fma(Pm[i < bb ? i : 0][j], Vq[j][r], a);
             if (need_wp) c = fma(Pm[i < bb ? i : 0][j], Vp[j][r], c);
         }
-        Wq[i][r] = (i < bb) ? a : 0.0;
+        const double w = (i < bb) ? a : 0.0;
+        Wq[i][r] = (q0 + r < k) ? w : -w;
         Wp[i][r] = (i < bb) ? c : 0.0;
     }
     __syncthreads();
-    // the 4 x 4 dots of this thread's entries, register-blocked (each operand read once
-    // per pivot; the sum over pivots runs in the same order for every entry)
-    double dots[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) dots[a][b] = 0.0;
+    // acc_pq += V_p . (-s W_q), register-blocked 4 x 4 (each operand read once per pivot;
+    // the pivots run in the same order for every entry)
 #pragma unroll
     for (int i = 0; i < SGJ_B; ++i) {
         double vp[4], wq[4];
@@ -601,7 +609,7 @@ __device__ __forceinline__ void sym_gj_tile(const double* __restrict__ Min, doub
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) dots[a][b] = fma(vp[a], wq[b], dots[a][b]);
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(vp[a], wq[b], acc[a][b]);
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
@@ -613,51 +621,97 @@ __device__ __forceinline__ void sym_gj_tile(const double* __restrict__ Min, doub
             if (q >= n || q < p) continue;
             const bool inp = p >= k && p < k + bb, inq = q >= k && q < k + bb;
             double out;
-            if (inp && inq) {
-                out = Pm[p - k][q - k];
-            } else if (inp) {
-                out = Wq[p - k][c];
-            } else if (inq) {
-                out = -Wp[q - k][r];
-            } else {
-                const double old = Min[(long long)p * n + q];
-                out = (q < k) ? old + dots[a][b] : old - dots[a][b];
-            }
+            if (inp && inq) out = Pm[p - k][q - k];
+            else if (inp) out = -Wq[p - k][c];   // q > B, so stored as -W_q
+            else if (inq) out = -Wp[q - k][r];
+            else out = acc[a][b];
             Mout[(long long)p * n + q] = out;
-            if (next_here && p >= kn && q < kn + bbn) {   // (p <= q, so p < kn + bbn too)
-                Pn[p - kn][q - kn] = out;
-                Pn[q - kn][p - kn] = out;
-            }
-        }
-    }
-    if (next_here) {   // uniform over the block
-        __syncthreads();
-        sgj_invert_block(Pn, bbn, tid);
-        if (tid < SGJ_B * SGJ_B) {
-            const int bi = tid / SGJ_B, bj = tid % SGJ_B;
-            Pout[tid] = (bi < bbn && bj < bbn) ? Pn[bi][bj] : 0.0;
         }
     }
 }
 
-// Pivots k .. k+SGJ_B-1 from Min into Mout (upper triangles) with P = Pin, leaving the next
-// block's P in Pout; grid: SGJ_T tiles, lower ones idle.
+// The next pivot block's P (pivots kn = k + SGJ_B onwards) after this launch's step: its
+// entries formed with the tile's operations in the tile's order (so bit-identical to what
+// the tile writes), then inverted. Run by one extra block, the first one dispatched,
+// while the tiles run.
+__device__ __forceinline__ void sym_gj_next_p(const double* __restrict__ Min, int n, int k,
+                                              const double* __restrict__ Pin, double* __restrict__ Pout)
+{
+    __shared__ double Pm[SGJ_B][SGJ_B], Vn[SGJ_B][SGJ_B], Wn[SGJ_B][SGJ_B], Pn[SGJ_B][SGJ_B];
+    const int tid = threadIdx.y * 16 + threadIdx.x;
+    const int bb = min(SGJ_B, n - k), kn = k + SGJ_B, bbn = min(SGJ_B, n - kn);
+    if (bbn <= 0) return;   // uniform over the block
+    const int bi = tid / SGJ_B, bj = tid % SGJ_B;
+    const bool own = tid < SGJ_B * SGJ_B && bi < bbn && bj < bbn;
+    const int p = kn + min(bi, bj), q = kn + max(bi, bj);   // q > k: the update's sign is -
+    double acc = own ? Min[(long long)p * n + q] : 0.0;
+    if (tid < SGJ_B * SGJ_B) {
+        Pm[bi][bj] = Pin[tid];
+        Vn[bi][bj] = sgj_v(Min, n, k, bb, kn + bj, bi);   // V_{kn + bj}, entry bi
+    }
+    __syncthreads();
+    if (tid < SGJ_B * SGJ_B) {   // -W of the next block's columns, as the tile stores it
+        double w = 0.0;
+        for (int j = 0; j < bb; ++j) w = fma(Pm[bi < bb ? bi : 0][j], Vn[j][bj], w);
+        Wn[bi][bj] = -((bi < bb) ? w : 0.0);
+    }
+    __syncthreads();
+    if (own) {
+        for (int i = 0; i < SGJ_B; ++i) acc = fma(Vn[i][p - kn], Wn[i][q - kn], acc);
+        Pn[bi][bj] = acc;
+    }
+    __syncthreads();
+    sgj_invert_block(Pn, bbn, tid);
+    if (tid < SGJ_B * SGJ_B) Pout[tid] = (bi < bbn && bj < bbn) ? Pn[bi][bj] : 0.0;
+}
+
+// Upper tile b (row-major over the T x T tiles with tq >= tp) -> (tp, tq).
+__device__ __forceinline__ void sgj_upper_tile(int b, int T, int& tp, int& tq)
+{
+    int r = b, row = 0;
+    while (row < T && r >= T - row) {
+        r -= T - row;
+        ++row;
+    }
+    tp = row;
+    tq = row + r;
+}
+
+// Pivots k .. k+SGJ_B-1 from Min into Mout (upper triangles) with P = Pin. Grid: one block
+// per upper SGJ_T tile (T (T + 1) / 2 of them, T = ceil(n / SGJ_T)) after block 0, which
+// leaves the next block's P in Pout. Only working blocks are launched, so the block
+// scheduler's round-robin gives every SM at most ceil(tiles / SMs) tiles.
 __global__ void __launch_bounds__(256)
 sym_gj_kernel(const double* __restrict__ Min, double* __restrict__ Mout, int n, int k, const double* __restrict__ Pin,
               double* __restrict__ Pout)
 {
-    if (blockIdx.y > blockIdx.x) return;
-    sym_gj_tile(Min, Mout, n, k, blockIdx.y, blockIdx.x, Pin, Pout);
+    if (blockIdx.x == 0) {
+        sym_gj_next_p(Min, n, k, Pin, Pout);
+        return;
+    }
+    int tp, tq;
+    sgj_upper_tile((int)blockIdx.x - 1, (n + SGJ_T - 1) / SGJ_T, tp, tq);
+    sym_gj_tile(Min, Mout, n, k, tp, tq, Pin);
 }
 
-// Full symmetric matrix from the upper triangle of U into A (A may be U).
-__global__ void sym_mirror_kernel(const double* __restrict__ U, double* __restrict__ A, int n)
+// The full n x n inverse A from the inverse U over the free DOFs (upper triangle, m x m):
+// A[p][q] = U[min(a, b)][max(a, b)] with a = pos[p], b = pos[q]; a fixed DOF (pos -1) gets
+// an identity row and column. U and A do not overlap.
+__device__ __forceinline__ void sym_expand(const double* __restrict__ U, int m, const int* __restrict__ pos,
+                                           double* __restrict__ A, int n, long long e0, long long stride)
 {
     const long long nn = (long long)n * n;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
+    for (long long e = e0; e < nn; e += stride) {
         const int p = (int)(e / n), q = (int)(e % n);
-        A[e] = (p <= q) ? U[e] : U[(long long)q * n + p];
+        const int a = pos[p], b = pos[q];
+        A[e] = (a < 0 || b < 0) ? (p == q ? 1.0 : 0.0) : U[(long long)min(a, b) * m + max(a, b)];
     }
+}
+
+__global__ void sym_expand_kernel(const double* __restrict__ U, int m, const int* __restrict__ pos,
+                                  double* __restrict__ A, int n)
+{
+    sym_expand(U, m, pos, A, n, (long long)blockIdx.x * blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 }  // namespace gf

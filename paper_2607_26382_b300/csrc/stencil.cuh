@@ -708,18 +708,36 @@ density_stats_kernel(const double* __restrict__ rho, long long n, double* __rest
     }
 }
 
-// Dense coarsest operator (all DOFs of the coarsest level, row-major n x n), one
-// thread per entry: A[r][c] = sum over the elements e containing both nodes of
-// E_e h K0[3 a_r + c_r][3 a_c + c_c], summed in a fixed element order so that the
-// matrix (and its inverse) is bit-reproducible.
+// Entry t of a dense coarsest matrix: row r and column c among all ndof DOFs (idx null,
+// layout ndof x ndof), or among the free DOFs idx[0 .. m-1] (compact layout m x m).
+__device__ __forceinline__ bool coarse_entry(long long t, long long ndof, const int* __restrict__ idx, int m,
+                                             long long& r, long long& c)
+{
+    if (idx) {
+        if (t >= (long long)m * m) return false;
+        r = idx[t / m];
+        c = idx[t % m];
+        return true;
+    }
+    if (t >= ndof * ndof) return false;
+    r = t / ndof;
+    c = t % ndof;
+    return true;
+}
+
+// Dense coarsest operator (row-major, over all DOFs of the coarsest level or, with idx,
+// over its free DOFs only), one thread per entry: A[r][c] = sum over the elements e
+// containing both nodes of E_e h K0[3 a_r + c_r][3 a_c + c_c], summed in a fixed element
+// order so that the matrix (and its inverse) is bit-reproducible.
 __global__ void coarse_assemble_kernel(const double* __restrict__ E, double* __restrict__ A, GridDims d,
-                                       const __grid_constant__ K0Param<double> K0)
+                                       const __grid_constant__ K0Param<double> K0, const int* __restrict__ idx = nullptr,
+                                       int m = 0)
 {
     const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
     const long long ndof = 3LL * NX * NY * NZ;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ndof * ndof) return;
-    const long long r = t / ndof, c = t % ndof;
+    long long r, c;
+    if (!coarse_entry(t, ndof, idx, m, r, c)) return;
     const long long nr = r / 3, nc = c / 3;
     const int cr = (int)(r % 3), cc = (int)(c % 3);
     const int ir = (int)(nr % NX), jr = (int)((nr / NX) % NY), kr = (int)(nr / ((long long)NX * NY));
@@ -739,6 +757,25 @@ __global__ void coarse_assemble_kernel(const double* __restrict__ E, double* __r
                 }
     }
     A[t] = s;
+}
+
+// The free DOFs of a level in ascending order (idx[0 .. m-1]), each DOF's position among
+// them (pos[q], -1 for a fixed DOF), and m (*m_out). One warp.
+__global__ void coarse_map_kernel(GridDims d, int* __restrict__ pos, int* __restrict__ idx, int* __restrict__ m_out)
+{
+    const long long ndof = 3LL * (d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    const unsigned lane = threadIdx.x;
+    int base = 0;
+    for (long long q0 = 0; q0 < ndof; q0 += 32) {
+        const long long q = q0 + lane;
+        const bool fr = q < ndof && !fix_dof(d, q);
+        const unsigned bal = __ballot_sync(0xffffffffu, fr);
+        const int at = base + __popc(bal & ((1u << lane) - 1u));
+        if (q < ndof) pos[q] = fr ? at : -1;
+        if (fr) idx[at] = (int)q;
+        base += __popc(bal);
+    }
+    if (lane == 0) *m_out = base;
 }
 
 // Fixed DOFs: zero row and column, unit diagonal.
