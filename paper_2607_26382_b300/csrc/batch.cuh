@@ -255,7 +255,7 @@ int batch_graphs(gf_batch* b, const gf_solve_opts* o)
                           [&](int i) {
                               gf_grid* g = b->g[i];
                               LAUNCH(g, 1, 1, gf::backsolve_kernel, g->st);
-                              LAUNCH(g, 2 * g->sms, 256, gf::update_x_kernel, b->u[i], (const double*)g->Z, g->ndof,
+                              LAUNCH(g, 2 * g->sms, 256, gf::update_x_kernel, b->u[i], (const double*)g->Z, g->ldk,
                                      g->ndof, (const gf::KState*)g->st);
                               return GF_OK;
                           },

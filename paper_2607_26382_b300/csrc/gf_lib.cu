@@ -163,7 +163,9 @@ struct gf_grid {
     int* dflag = nullptr;
     // Krylov workspace
     int m_alloc = 0;
+    long long ldk = 0;                // leading dimension of V, Z, Vd: ndof rounded up to 32 (256-byte rows)
     double *V = nullptr, *Z = nullptr, *partial = nullptr, *work = nullptr;
+    int nbc[3][3] = {};               // grid of the FP64 Gram-Schmidt passes (dots, update+dots, update+norm) x NV 8/16/32
     double* ckx = nullptr;            // iterate of a probe true-residual check
     // fine-level adaptive correction: inner basis V (steps + 1), Z (steps), r, d, q, z in the
     // V-cycle's precision (fc_es bytes per entry), the inner solver's state and partial sums
@@ -251,6 +253,13 @@ namespace {
 // Block size for a launch over `nodes` nodes: levels with fewer than two 256-thread
 // blocks per SM take ctpb-thread blocks, so that every SM gets work (the results do not
 // depend on the block size: one node per thread).
+// Blocks of 256 threads for an elementwise pass over n entries: about four entries per
+// thread (their loads in flight together), at least two blocks per SM.
+int stream_blocks(const gf_grid* g, long long n)
+{
+    return (int)std::max<long long>(2LL * g->sms, (n + 1023) / 1024);
+}
+
 int level_tpb(const gf_grid* g, long long nodes, int base)
 {
     return (g->ctpb > 0 && nodes < 512LL * g->sms) ? g->ctpb : base;
@@ -1185,7 +1194,7 @@ int ensure_krylov(gf_grid* g, int m, int kmax, int outer)
         cudaFree(g->Vd);
         g->Vd = nullptr;
         g->md_alloc = 0;
-        RET(allocT(&g->Vd, (size_t)(m + 1) * g->ndof));
+        RET(allocT(&g->Vd, (size_t)(m + 1) * g->ldk));
         if (!g->pdd) {
             // each pass's grid is the blocks resident at once on this GPU (one round),
             // capped by the number of row tiles
@@ -1218,8 +1227,8 @@ int ensure_krylov(gf_grid* g, int m, int kmax, int outer)
         cudaFree(g->Z);
         g->V = g->Z = nullptr;
         g->m_alloc = 0;
-        RET(allocT(&g->V, (size_t)(m + 1) * g->ndof));
-        RET(allocT(&g->Z, (size_t)m * g->ndof));
+        RET(allocT(&g->V, (size_t)(m + 1) * g->ldk));
+        RET(allocT(&g->Z, (size_t)m * g->ldk));
         g->m_alloc = m;
     }
     if (kmax + 1 > g->hist_cap) {
@@ -1267,7 +1276,7 @@ int pick_nv(int nv)
 template <int NV>
 int cgs2_step(gf_grid* g, int j, double* w, int outer)
 {
-    const long long n = g->ndof, ld = g->ndof;
+    const long long n = g->ndof, ld = g->ldk;
     const int nv = j + 1;
     if (outer == 2) {   // double-float passes on the FP32 pipe; w arrives as wd
         float2* wd = g->Vd + (long long)(j + 1) * ld;
@@ -1281,12 +1290,14 @@ int cgs2_step(gf_grid* g, int j, double* w, int outer)
         LAUNCH(g, 1, 32, gf::arnoldi_tail_kernel, g->st, g->hist, j, NV, g->host_status_dev, 1e-14);
         return GF_OK;
     }
-    LAUNCH(g, g->nbr, gf::RED_THREADS, gf::cgs_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
-    LAUNCH(g, 1, 32 * 32, gf::reduce_partials_kernel, g->partial, g->nbr, NV + 1, NV + 1, g->st, 0, 1);
-    LAUNCH(g, g->nbr, gf::RED_THREADS, gf::cgs_update_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
-    LAUNCH(g, 1, 32 * 32, gf::reduce_partials_kernel, g->partial, g->nbr, NV, nv, g->st, 1, 1);
-    LAUNCH(g, g->nbr, gf::RED_THREADS, gf::cgs_update_norm_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
-    LAUNCH(g, 1, 32, gf::reduce_partials_kernel, g->partial, g->nbr, 1, 1, g->st, 2, 1);
+    const int q = NV == 8 ? 0 : (NV == 16 ? 1 : 2);
+    const int b0 = g->nbc[0][q], b1 = g->nbc[1][q], b2 = g->nbc[2][q];
+    LAUNCH(g, b0, gf::RED_THREADS, gf::cgs_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
+    LAUNCH(g, 1, 32 * 32, gf::reduce_partials_kernel, g->partial, b0, NV + 1, NV + 1, g->st, 0, 1);
+    LAUNCH(g, b1, gf::RED_THREADS, gf::cgs_update_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
+    LAUNCH(g, 1, 32 * 32, gf::reduce_partials_kernel, g->partial, b1, NV, nv, g->st, 1, 1);
+    LAUNCH(g, b2, gf::RED_THREADS, gf::cgs_update_norm_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
+    LAUNCH(g, 1, 32, gf::reduce_partials_kernel, g->partial, b2, 1, 1, g->st, 2, 1);
     LAUNCH(g, 1, 32, gf::arnoldi_tail_kernel, g->st, g->hist, j, NV, g->host_status_dev, 1e-14);
     return GF_OK;
 }
@@ -1299,7 +1310,7 @@ int cgs2_step(gf_grid* g, int j, double* w, int outer)
 int cgs2_step_long(gf_grid* g, int j, double* w, int outer)
 {
     constexpr int NS = gf::KRY_NV;
-    const long long n = g->ndof, ld = g->ndof;
+    const long long n = g->ndof, ld = g->ldk;
     const int nv = j + 1, slices = (nv + NS - 1) / NS;
     double* h1 = g->st->h1;   // device addresses of the state's slots
     double* h2 = g->st->h2;
@@ -1353,7 +1364,7 @@ int cgs2_step_long(gf_grid* g, int j, double* w, int outer)
 
 int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
 {
-    const long long ld = g->ndof;
+    const long long ld = g->ldk;
     double* vj = g->V + (long long)j * ld;
     double* zj = g->Z + (long long)j * ld;
     double* w = g->V + (long long)(j + 1) * ld;
@@ -1371,7 +1382,7 @@ int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
     if (o->outer == 2)
         LAUNCH(g, 2 * g->sms, 256, gf::ddgs_scale_kernel, g->Vd + (long long)(j + 1) * ld, w, g->ndof, g->st);
     else
-        LAUNCH(g, 2 * g->sms, 256, gf::scale_kernel, w, g->ndof, g->st, 1);
+        LAUNCH(g, stream_blocks(g, g->ndof), 256, gf::scale_kernel, w, g->ndof, g->st, 1);
     return GF_OK;
 }
 
@@ -1388,7 +1399,7 @@ int cycle_start(gf_grid* g, const double* f, const double* x, bool x_zero, bool 
     if (outer == 2)
         LAUNCH(g, 2 * g->sms, 256, gf::ddgs_scale_fp64_kernel, v0, g->Vd, g->ndof, g->st);
     else
-        LAUNCH(g, 2 * g->sms, 256, gf::scale_kernel, v0, g->ndof, g->st, 1);
+        LAUNCH(g, stream_blocks(g, g->ndof), 256, gf::scale_kernel, v0, g->ndof, g->st, 1);
     return GF_OK;
 }
 
@@ -1463,7 +1474,7 @@ int true_check(gf_grid* g, const double* f, const double* u, ProbeHook* hook, in
     if (!g->ckx) RET(allocT(&g->ckx, g->ndof));
     LAUNCH(g, 1, 1, gf::backsolve_kernel, g->st);   // y of the current J columns (recomputed at the cycle end)
     CK(cudaMemcpyAsync(g->ckx, u, sizeof(double) * g->ndof, cudaMemcpyDeviceToDevice, g->stream));
-    LAUNCH(g, 2 * g->sms, 256, gf::update_x_kernel, g->ckx, g->Z, g->ndof, g->ndof, g->st);
+    LAUNCH(g, 2 * g->sms, 256, gf::update_x_kernel, g->ckx, g->Z, g->ldk, g->ndof, g->st);
     double eta = 0.0, est = 0.0;
     RET(guard_impl(g, f, g->ckx, &eta));
     CK(cudaMemcpy(&est, g->hist + k, sizeof(double), cudaMemcpyDeviceToHost));
@@ -1531,7 +1542,7 @@ int solve_impl(gf_grid* g, const double* f, double* u, const gf_solve_opts* o, g
         }
         if (aborted) break;
         LAUNCH(g, 1, 1, gf::backsolve_kernel, g->st);
-        LAUNCH(g, 2 * g->sms, 256, gf::update_x_kernel, u, g->Z, g->ndof, g->ndof, g->st);
+        LAUNCH(g, 2 * g->sms, 256, gf::update_x_kernel, u, g->Z, g->ldk, g->ndof, g->st);
         RET(read_state(g, &hs));
         if (hs.status != gf::KS_RUN) break;
     }
@@ -1938,11 +1949,36 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     }
     int r = GF_OK;
     g->nbr = (int)std::min<long long>(2LL * g->sms, std::max<long long>(1, (g->ndof + 1023) / 1024));
+    g->ldk = (g->ndof + 31) / 32 * 32;
+    // the FP64 Gram-Schmidt passes run the blocks resident at once (one round), capped by
+    // 256-row tiles; their partial rows share g->partial with the other reductions
+    long long partial_rows = (long long)g->nbr * 40;
+    {
+        const void* kc[3][3] = {
+            {(const void*)gf::cgs_dots_kernel<8>, (const void*)gf::cgs_dots_kernel<16>,
+             (const void*)gf::cgs_dots_kernel<32>},
+            {(const void*)gf::cgs_update_dots_kernel<8>, (const void*)gf::cgs_update_dots_kernel<16>,
+             (const void*)gf::cgs_update_dots_kernel<32>},
+            {(const void*)gf::cgs_update_norm_kernel<8>, (const void*)gf::cgs_update_norm_kernel<16>,
+             (const void*)gf::cgs_update_norm_kernel<32>}};
+        const int nvq[3] = {8, 16, 32};
+        const long long tiles = std::max<long long>(1, (g->ndof + gf::RED_THREADS - 1) / gf::RED_THREADS);
+        for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) {
+                int nb = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kc[p][q], gf::RED_THREADS, 0) != cudaSuccess ||
+                    nb <= 0)
+                    nb = 2;
+                g->nbc[p][q] = (int)std::min<long long>((long long)nb * g->sms, tiles);
+                const int stride = p == 0 ? nvq[q] + 1 : (p == 1 ? nvq[q] : 1);
+                partial_rows = std::max(partial_rows, (long long)g->nbc[p][q] * stride);
+            }
+    }
     if ((r = allocT(&g->Ainv, (size_t)g->nc * g->nc)) || (r = allocT(&g->Agj, (size_t)g->nc * g->nc + 2 * gf::SGJ_B * gf::SGJ_B)) ||
         (r = allocT(&g->cpos, (size_t)g->nc)) || (r = allocT(&g->cidx, (size_t)g->nc + 1)) ||
         (r = allocT(&g->dflag, 4)) || (r = allocT(&g->rho64, g->nel)) ||
         (r = allocT(&g->rho16, g->nel)) || (r = allocT(&g->work, g->ndof)) ||
-        (r = allocT(&g->partial, (size_t)g->nbr * 40)) || (r = allocT(&g->st, 1)) || (r = allocT(&g->gst, 1)) ||
+        (r = allocT(&g->partial, (size_t)partial_rows)) || (r = allocT(&g->st, 1)) || (r = allocT(&g->gst, 1)) ||
         (r = allocT(&g->Edf, g->nel)))
         return fail(r);
     if (cudaHostAlloc((void**)&g->host_status, sizeof(int), cudaHostAllocMapped) != cudaSuccess)

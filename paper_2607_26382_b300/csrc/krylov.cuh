@@ -61,29 +61,67 @@ __device__ __forceinline__ void block_rows(long long n, long long& r0, long long
     r1 = r0 + chunk < n ? r0 + chunk : n;
 }
 
-// pass 1: partial[b][i] = sum_r V_i[r] w[r] (i < nv), partial[b][nv] = sum_r w[r]^2
+// The three FP64 passes of CGS2 over the rows of a block. Each thread takes rows
+// r, r + RED_THREADS, ... in order; CGS_ROWS<NV> of them per iteration have all their
+// loads (predicated) in flight together, then the FP64 multiply-adds run for the nv live
+// vectors only: the FP64 pipe, not memory, bounds these passes on B300 once nv is a few
+// vectors, and a multiply-add by a zero entry would cost as much as a real one. Below
+// that the rows in flight hide the HBM latency (two rows per iteration for NV = 8; the
+// results do not depend on it).
 template <int NV>
-__global__ void __launch_bounds__(RED_THREADS)
+struct CgsRows {
+    static constexpr int value = NV <= 8 ? 2 : 1;
+};
+
+// pass 1: partial[b][i] = sum_r V_i[r] w[r] (i < nv), partial[b][nv] = sum_r w[r]^2
+// (NV = 32: the row's vectors in two groups of 16, loaded together per group, so that
+// two blocks fit on an SM; the multiply-adds run in the same order)
+template <int NV>
+__global__ void __launch_bounds__(RED_THREADS, NV >= 16 ? 2 : 1)
 cgs_dots_kernel(const double* __restrict__ V, long long ld, int nv, const double* __restrict__ w,
                 long long n, double* __restrict__ partial, const KState* __restrict__ st)
 {
+    constexpr int ROWS = CgsRows<NV>::value;
+    constexpr int G = NV == 32 ? 16 : NV;   // vectors loaded together
     if (st->status != KS_RUN) return;
     double acc[NV + 1];
 #pragma unroll
     for (int q = 0; q <= NV; ++q) acc[q] = 0.0;
     long long r0, r1;
     block_rows(n, r0, r1);
-    for (long long r = r0 + threadIdx.x; r < r1; r += RED_THREADS) {
-        const double wr = w[r];
-        double v[NV];
+    for (long long r = r0 + threadIdx.x; r < r1; r += (long long)RED_THREADS * ROWS) {
+        double wr[ROWS];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) v[q] = q < nv ? V[q * ld + r] : 0.0;
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            if (q >= nv) break;
-            acc[q] = fma(v[q], wr, acc[q]);
+        for (int u = 0; u < ROWS; ++u) {
+            const long long rr = r + (long long)u * RED_THREADS;
+            wr[u] = (u == 0 || rr < r1) ? w[rr] : 0.0;
         }
-        acc[NV] = fma(wr, wr, acc[NV]);
+#pragma unroll
+        for (int g0 = 0; g0 < NV; g0 += G) {
+            if (g0 >= nv) break;
+            double v[ROWS][G];
+#pragma unroll
+            for (int u = 0; u < ROWS; ++u) {
+                const long long rr = r + (long long)u * RED_THREADS;
+                const bool ok = u == 0 || rr < r1;   // row r itself is inside the range
+#pragma unroll
+                for (int q = 0; q < G; ++q) v[u][q] = (ok && g0 + q < nv) ? V[(g0 + q) * ld + rr] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < ROWS; ++u) {
+                if (r + (long long)u * RED_THREADS >= r1) break;
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    if (g0 + q >= nv) break;
+                    acc[g0 + q] = fma(v[u][q], wr[u], acc[g0 + q]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+            if (r + (long long)u * RED_THREADS >= r1) break;
+            acc[NV] = fma(wr[u], wr[u], acc[NV]);
+        }
     }
     // row layout: dots in slots [0, nv), ||w||^2 in slot NV (row stride NV + 1)
     block_reduce_store<NV + 1>(acc, NV + 1, partial + (long long)blockIdx.x * (NV + 1));
@@ -95,6 +133,7 @@ __global__ void __launch_bounds__(RED_THREADS)
 cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
                        long long n, double* __restrict__ partial, const KState* __restrict__ st)
 {
+    constexpr int ROWS = CgsRows<NV>::value;
     if (st->status != KS_RUN) return;
     __shared__ double h[NV];
     double acc[NV];
@@ -104,36 +143,47 @@ cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, doubl
     __syncthreads();
     long long r0, r1;
     block_rows(n, r0, r1);
-    // all loads of a row first (predicated, so they are in flight together), then FP64
-    // multiply-adds for the nv live vectors only: the FP64 pipe, not memory, bounds this
-    // pass on B300, and a multiply-add by a zero entry would cost as much as a real one
-    for (long long r = r0 + threadIdx.x; r < r1; r += RED_THREADS) {
-        double v[NV];
+    for (long long r = r0 + threadIdx.x; r < r1; r += (long long)RED_THREADS * ROWS) {
+        double wr[ROWS], v[ROWS][NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) v[q] = q < nv ? V[q * ld + r] : 0.0;
-        double s = 0.0;
+        for (int u = 0; u < ROWS; ++u) {
+            const long long rr = r + (long long)u * RED_THREADS;
+            const bool ok = u == 0 || rr < r1;   // row r itself is inside the range
+            wr[u] = ok ? w[rr] : 0.0;
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            if (q >= nv) break;
-            s = fma(h[q], v[q], s);
+            for (int q = 0; q < NV; ++q) v[u][q] = (ok && q < nv) ? V[q * ld + rr] : 0.0;
         }
-        const double wn = w[r] - s;
-        w[r] = wn;
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            if (q >= nv) break;
-            acc[q] = fma(v[q], wn, acc[q]);
+        for (int u = 0; u < ROWS; ++u) {
+            const long long rr = r + (long long)u * RED_THREADS;
+            if (rr >= r1) break;
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                if (q >= nv) break;
+                s = fma(h[q], v[u][q], s);
+            }
+            const double wn = wr[u] - s;
+            w[rr] = wn;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                if (q >= nv) break;
+                acc[q] = fma(v[u][q], wn, acc[q]);
+            }
         }
     }
     block_reduce_store<NV>(acc, nv, partial + (long long)blockIdx.x * NV);
 }
 
 // pass 3: w -= sum_i h2_i V_i ; partial[b][0] = ||w_new||^2 (block part)
+// (NV = 32: two groups of 16 vectors, as in pass 1)
 template <int NV>
-__global__ void __launch_bounds__(RED_THREADS)
+__global__ void __launch_bounds__(RED_THREADS, NV >= 16 ? 2 : 1)
 cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
                        long long n, double* __restrict__ partial, const KState* __restrict__ st)
 {
+    constexpr int ROWS = CgsRows<NV>::value;
+    constexpr int G = NV == 32 ? 16 : NV;
     if (st->status != KS_RUN) return;
     __shared__ double h[NV];
     if (threadIdx.x < NV) h[threadIdx.x] = threadIdx.x < nv ? st->h2[threadIdx.x] : 0.0;
@@ -141,29 +191,46 @@ cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, doubl
     double acc[1] = {0.0};
     long long r0, r1;
     block_rows(n, r0, r1);
-    for (long long r = r0 + threadIdx.x; r < r1; r += RED_THREADS) {
-        double v[NV];
+    for (long long r = r0 + threadIdx.x; r < r1; r += (long long)RED_THREADS * ROWS) {
+        double s[ROWS], wr[ROWS];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) v[q] = q < nv ? V[q * ld + r] : 0.0;
-        double s = 0.0;
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            if (q >= nv) break;
-            s = fma(h[q], v[q], s);
+        for (int u = 0; u < ROWS; ++u) {
+            const long long rr = r + (long long)u * RED_THREADS;
+            wr[u] = (u == 0 || rr < r1) ? w[rr] : 0.0;
+            s[u] = 0.0;
         }
-        const double wn = w[r] - s;
-        w[r] = wn;
-        acc[0] = fma(wn, wn, acc[0]);
+#pragma unroll
+        for (int g0 = 0; g0 < NV; g0 += G) {
+            if (g0 >= nv) break;
+            double v[ROWS][G];
+#pragma unroll
+            for (int u = 0; u < ROWS; ++u) {
+                const long long rr = r + (long long)u * RED_THREADS;
+                const bool ok = u == 0 || rr < r1;   // row r itself is inside the range
+#pragma unroll
+                for (int q = 0; q < G; ++q) v[u][q] = (ok && g0 + q < nv) ? V[(g0 + q) * ld + rr] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < ROWS; ++u) {
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    if (g0 + q >= nv) break;
+                    s[u] = fma(h[g0 + q], v[u][q], s[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < ROWS; ++u) {
+            const long long rr = r + (long long)u * RED_THREADS;
+            if (rr >= r1) break;
+            const double wn = wr[u] - s[u];
+            w[rr] = wn;
+            acc[0] = fma(wn, wn, acc[0]);
+        }
     }
     block_reduce_store<1>(acc, 1, partial + blockIdx.x);
 }
 
-// ---- long restarts: the basis in slices of KRY_NV vectors -------------------------
-// Past KRY_NV basis vectors, each dot pass runs cgs_dots_kernel<KRY_NV> once per slice
-// of V against the same w (classical Gram-Schmidt: every dot of a pass sees the same w),
-// and the update w -= V h runs slice after slice with this kernel; hsl points at the
-// slice's coefficients in the state. With partial != nullptr (the last slice of the
-// second update) it also leaves the block parts of ||w_new||^2 in partial[b].
 template <int NV>
 __global__ void __launch_bounds__(RED_THREADS)
 cgs_slice_update_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
