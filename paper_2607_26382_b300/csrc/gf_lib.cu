@@ -260,6 +260,24 @@ int stream_blocks(const gf_grid* g, long long n)
     return (int)std::max<long long>(2LL * g->sms, (n + 1023) / 1024);
 }
 
+// Opt a kernel in to `bytes` of dynamic shared memory (above the default 48 KB), once.
+template <auto KERN>
+bool smem_opt_in(int bytes)
+{
+    static const bool ok =
+        cudaFuncSetAttribute((const void*)KERN, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+    return ok;
+}
+
+// A modal kernel (modal.cuh) over n_items work items, with its dynamic shared memory.
+template <typename T, int BX, int BY, auto KERN, typename... Args>
+int launch_modal(gf_grid* g, int n_items, Args... args)
+{
+    constexpr int bytes = gf::modal_smem_bytes<T, BX, BY>();
+    if (!smem_opt_in<KERN>(bytes)) return set_err(GF_ERR_CUDA, "shared memory of the modal kernel");
+    return launch_smem(g, dim3(n_items), dim3(BX, BY), bytes, KERN, args...);
+}
+
 int level_tpb(const gf_grid* g, long long nodes, int base)
 {
     return (g->ctpb > 0 && nodes < 512LL * g->sms) ? g->ctpb : base;
@@ -298,11 +316,11 @@ int tiled_f32(gf_grid* g, int l, const float* x, const BT* b, OT* out, const flo
     }
     if (l == 0 && g->modal_f32 && g->modal_items && !L.fix && g->tpb[1] > 0) {   // the modal FP32 fine level
         if (g->modal_bx == 32)
-            LAUNCH(g, g->modal_n, dim3(32, 16), (gf::modal_stencil_f32_kernel<MODE, BT, OT, 32, 16>), x, b, out, E,
-                   L.dims(), g->Kmodal32, omega, (const int4*)g->modal_items, halt);
+            RET((launch_modal<float, 32, 16, gf::modal_stencil_f32_kernel<MODE, BT, OT, 32, 16>>(
+                g, g->modal_n, x, b, out, E, L.dims(), g->Kmodal32, omega, (const int4*)g->modal_items, halt)));
         else
-            LAUNCH(g, g->modal_n, dim3(16, 32), (gf::modal_stencil_f32_kernel<MODE, BT, OT, 16, 32>), x, b, out, E,
-                   L.dims(), g->Kmodal32, omega, (const int4*)g->modal_items, halt);
+            RET((launch_modal<float, 16, 32, gf::modal_stencil_f32_kernel<MODE, BT, OT, 16, 32>>(
+                g, g->modal_n, x, b, out, E, L.dims(), g->Kmodal32, omega, (const int4*)g->modal_items, halt)));
         return GF_OK;
     }
     if (g->tpb[1] > 0 && g->f32x2) {   // the same, with paired FMAs
@@ -993,18 +1011,20 @@ int applyK64(gf_grid* g, const double* u, double* y, const int* halt)
     g->stats.apply_K_fp64++;
     if (g->modal_items) {   // modal factorisation of K0 (default; GF_MODAL=0: dense node stencil)
         const bool mk = g->lv[0].fix != nullptr;   // per-node fixed components (bridge supports)
+        const double* E = g->lv[0].E64;
+        const int4* it = g->modal_items;
         if (g->modal_bx == 32 && mk)
-            LAUNCH(g, g->modal_n, dim3(32, 16), (gf::apply_modal_kernel<32, 16, true>), u, y,
-                   (const double*)g->lv[0].E64, g->lv[0].dims(), g->Kmodal, (const int4*)g->modal_items, halt);
+            RET((launch_modal<double, 32, 16, gf::apply_modal_kernel<32, 16, true>>(g, g->modal_n, u, y, E,
+                                                                                   g->lv[0].dims(), g->Kmodal, it, halt)));
         else if (g->modal_bx == 32)
-            LAUNCH(g, g->modal_n, dim3(32, 16), (gf::apply_modal_kernel<32, 16>), u, y, (const double*)g->lv[0].E64,
-                   g->lv[0].dims(), g->Kmodal, (const int4*)g->modal_items, halt);
+            RET((launch_modal<double, 32, 16, gf::apply_modal_kernel<32, 16, false>>(g, g->modal_n, u, y, E,
+                                                                                    g->lv[0].dims(), g->Kmodal, it, halt)));
         else if (mk)
-            LAUNCH(g, g->modal_n, dim3(16, 32), (gf::apply_modal_kernel<16, 32, true>), u, y,
-                   (const double*)g->lv[0].E64, g->lv[0].dims(), g->Kmodal, (const int4*)g->modal_items, halt);
+            RET((launch_modal<double, 16, 32, gf::apply_modal_kernel<16, 32, true>>(g, g->modal_n, u, y, E,
+                                                                                   g->lv[0].dims(), g->Kmodal, it, halt)));
         else
-            LAUNCH(g, g->modal_n, dim3(16, 32), (gf::apply_modal_kernel<16, 32>), u, y, (const double*)g->lv[0].E64,
-                   g->lv[0].dims(), g->Kmodal, (const int4*)g->modal_items, halt);
+            RET((launch_modal<double, 16, 32, gf::apply_modal_kernel<16, 32, false>>(g, g->modal_n, u, y, E,
+                                                                                    g->lv[0].dims(), g->Kmodal, it, halt)));
         return GF_OK;
     }
     return stencil<double, double, gf::ST_APPLY>(g, 0, u, nullptr, y, g->lv[0].E64, g->K0d, 0.0, halt);
@@ -1820,8 +1840,9 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         const char* e = getenv("GF_MODAL");
         if (!(e && e[0] == '0')) {
             int per_sm = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gf::apply_modal_kernel<32, 16>,
-                                                              gf::MODAL_THREADS, 0) != cudaSuccess ||
+            if (!smem_opt_in<gf::apply_modal_kernel<32, 16, false>>(gf::modal_smem_bytes<double, 32, 16>()) ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gf::apply_modal_kernel<32, 16>, gf::MODAL_THREADS,
+                                                              gf::modal_smem_bytes<double, 32, 16>()) != cudaSuccess ||
                 per_sm < 1)
                 per_sm = 1;
             const char* ch = getenv("GF_MODAL_CHUNK");
@@ -2011,8 +2032,11 @@ namespace {
 int modal_autotune(gf_grid* g)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gf::apply_modal_kernel<32, 16>, gf::MODAL_THREADS, 0) !=
-            cudaSuccess ||
+    if (!smem_opt_in<gf::apply_modal_kernel<32, 16, false>>(gf::modal_smem_bytes<double, 32, 16>()) ||
+        !smem_opt_in<gf::apply_modal_kernel<16, 32, false>>(gf::modal_smem_bytes<double, 16, 32>()))
+        return set_err(GF_ERR_CUDA, "shared memory of the modal kernel");
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gf::apply_modal_kernel<32, 16>, gf::MODAL_THREADS,
+                                                      gf::modal_smem_bytes<double, 32, 16>()) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     struct Cand {
@@ -2042,10 +2066,12 @@ int modal_autotune(gf_grid* g)
     int best_i = -1;
     auto run = [&](const Cand& c) {
         if (c.bx == 32)
-            gf::apply_modal_kernel<32, 16><<<(unsigned)c.items.size(), dim3(32, 16), 0, g->stream>>>(
+            gf::apply_modal_kernel<32, 16><<<(unsigned)c.items.size(), dim3(32, 16),
+                                             gf::modal_smem_bytes<double, 32, 16>(), g->stream>>>(
                 f.x64, f.t64, f.E64, f.dims(), g->Kmodal, dev, nullptr);
         else
-            gf::apply_modal_kernel<16, 32><<<(unsigned)c.items.size(), dim3(16, 32), 0, g->stream>>>(
+            gf::apply_modal_kernel<16, 32><<<(unsigned)c.items.size(), dim3(16, 32),
+                                             gf::modal_smem_bytes<double, 16, 32>(), g->stream>>>(
                 f.x64, f.t64, f.E64, f.dims(), g->Kmodal, dev, nullptr);
     };
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||

@@ -66,6 +66,14 @@ __host__ inline ModalCoef modal_coef(double E0, double nu)
 
 constexpr int MODAL_THREADS = 512;   // element columns per CTA: 32 x 16 or 16 x 32
 
+// Dynamic shared memory of the modal kernels: two buffers of 12 corner forces per column
+// (and, for the FP32 kernel, three layers of element moduli).
+template <typename T, int BX, int BY>
+constexpr int modal_smem_bytes()
+{
+    return (int)(sizeof(T) * (2 * 12 + (sizeof(T) == 4 ? 3 : 0)) * BX * BY);
+}
+
 // Work items of apply_modal_kernel<BX, BY> for a grid of nx x ny x nz elements on `slots`
 // concurrent CTAs. A CTA step costs the busiest of the SM's four sub-partitions (warp w
 // runs on w mod 4), counting the warps that hold at least one element column inside
@@ -182,7 +190,10 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
                    GridDims d, ModalCoef C, const int4* __restrict__ items, const int* __restrict__ halt)
 {
     if (halt != nullptr && *halt != 0) return;
-    __shared__ double part[12][BY][BX];     // [corner * 3 + comp][column]
+    // two buffers of corner forces [corner * 3 + comp][column], by step parity (dynamic
+    // shared memory, modal_smem_bytes<double, BX, BY>): one barrier per step
+    extern __shared__ __align__(16) unsigned char modal_smem[];
+    double(*partb)[12][BY][BX] = reinterpret_cast<double(*)[12][BY][BX]>(modal_smem);
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
     const int4 it = items[blockIdx.x];
@@ -281,8 +292,10 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
                     carry[c][q] = 0.0;
                 }
         }
-        // node plane ez: this column's four corner forces, then the gather
-        __syncthreads();   // the previous step's gather has read `part`
+        // node plane ez: this column's four corner forces, then the gather (the buffer of
+        // this parity was last read by the gather two steps back, which every thread
+        // finished before the previous step's barrier)
+        double(*part)[BY][BX] = partb[(ez - k0 + 1) & 1];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             double v[4];
@@ -334,8 +347,13 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
                          float omega, const int4* __restrict__ items, const int* __restrict__ halt)
 {
     if (halt != nullptr && *halt != 0) return;
-    __shared__ float part[12][BY][BX];     // [corner * 3 + comp][column]
-    __shared__ float Es[2][BY][BX];        // element moduli of the column, by layer parity
+    // corner forces [corner * 3 + comp][column] in two buffers by step parity, and the
+    // column's element moduli in three by layer (the gather reads this layer's and the
+    // previous one's): dynamic shared memory, modal_smem_bytes<float, BX, BY>; one
+    // barrier per step
+    extern __shared__ __align__(16) unsigned char modal_smem[];
+    float(*partb)[12][BY][BX] = reinterpret_cast<float(*)[12][BY][BX]>(modal_smem);
+    float(*Es)[BY][BX] = reinterpret_cast<float(*)[BY][BX]>(modal_smem + sizeof(float) * 2 * 12 * BY * BX);
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
     const int4 it = items[blockIdx.x];
@@ -447,8 +465,11 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
                     carry[c][q] = 0.f;
                 }
         }
-        const int cur = ez & 1;
-        __syncthreads();   // the previous step's gather has read `part` and Es[cur]
+        // buffers of this step: part by parity, Es by step mod 3 (last read by the gathers
+        // three and two steps back, finished before the previous step's barrier)
+        const int step = ez - k0 + 1;
+        const int cur = step % 3, prv = (step + 2) % 3;
+        float(*part)[BY][BX] = partb[step & 1];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             float v[4];
@@ -483,7 +504,7 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
                 float db[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int lz = 0; lz < 2; ++lz) {
-                    const int layer = lz == 0 ? (cur ^ 1) : cur;   // ez - 1, then ez
+                    const int layer = lz == 0 ? prv : cur;   // ez - 1, then ez
                     const int oz = lz == 0 ? 1 : 0;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
