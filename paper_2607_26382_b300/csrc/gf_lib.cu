@@ -507,9 +507,11 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
     return GF_OK;
 }
 
-// The mixed V-cycle (FP32 stencils, linear or tiled per the grid's tuning): level 0 reads the FP64 input v
-// as its right-hand side and the last post-sweep writes the FP64 result z, so no
-// conversion passes are needed.
+// The mixed V-cycle (FP32 stencils, linear or tiled per the grid's tuning): level 0's first
+// sweep reads the FP64 input v and stores it rounded to FP32 (b32) for the level's other
+// sweeps and residual (a conversion per entry instead of one per read: the conversions
+// run on the FP64 pipe), and the last post-sweep writes the FP64 result z, so no
+// separate conversion passes are needed.
 int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2, float omega, const int* halt,
                        double ls = 0.0)
 {
@@ -523,13 +525,13 @@ int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2,
         float* x = lev.x32;
         float* t = lev.t32;
         if (l == 0) {
-            LAUNCH(g, nblk(lev.nodes), 256, (gf::first_sweep_kernel<float, float, double>), v, x,
+            LAUNCH(g, nblk(lev.nodes), 256, (gf::first_sweep_store_kernel<float, float, double>), v, lev.b32, x,
                    (const float*)lev.E32, lev.dims(), g->K0f, omega, halt);
             for (int s = 1; s < nu1; ++s) {
-                RET((tiled_f32<gf::ST_SWEEP, double, float>(g, l, x, v, t, lev.E32, omega, halt)));
+                RET((tiled_f32<gf::ST_SWEEP, float, float>(g, l, x, lev.b32, t, lev.E32, omega, halt)));
                 std::swap(x, t);
             }
-            RET((tiled_f32<gf::ST_RESID, double, float>(g, l, x, v, lev.r32, lev.E32, omega, halt)));
+            RET((tiled_f32<gf::ST_RESID, float, float>(g, l, x, lev.b32, lev.r32, lev.E32, omega, halt)));
         } else {   // first sweep done together with the restriction into this level
             for (int s = 1; s < nu1; ++s) {
                 RET((tiled_f32<gf::ST_SWEEP, float, float>(g, l, x, lev.b32, t, lev.E32, omega, halt)));
@@ -577,9 +579,9 @@ int vcycle_mixed_tiled(gf_grid* g, const double* v, double* z, int nu1, int nu2,
         for (int s = 0; s < nu2; ++s) {
             const bool last = (s == nu2 - 1);
             if (l == 0 && last) {
-                RET((tiled_f32<gf::ST_SWEEP, double, double>(g, 0, x, v, z, lev.E32, omega, halt)));
+                RET((tiled_f32<gf::ST_SWEEP, float, double>(g, 0, x, lev.b32, z, lev.E32, omega, halt)));
             } else if (l == 0) {
-                RET((tiled_f32<gf::ST_SWEEP, double, float>(g, 0, x, v, t, lev.E32, omega, halt)));
+                RET((tiled_f32<gf::ST_SWEEP, float, float>(g, 0, x, lev.b32, t, lev.E32, omega, halt)));
                 std::swap(x, t);
             } else {
                 RET((tiled_f32<gf::ST_SWEEP, float, float>(g, l, x, lev.b32, t, lev.E32, omega, halt)));
@@ -1727,7 +1729,8 @@ bool stc_smem_attrs()
 {
     return stc_smem_attr<gf::ST_APPLY, float, float>() && stc_smem_attr<gf::ST_RESID, float, float>() &&
            stc_smem_attr<gf::ST_SWEEP, float, float>() && stc_smem_attr<gf::ST_RESID, double, float>() &&
-           stc_smem_attr<gf::ST_SWEEP, double, float>() && stc_smem_attr<gf::ST_SWEEP, double, double>();
+           stc_smem_attr<gf::ST_SWEEP, double, float>() && stc_smem_attr<gf::ST_SWEEP, double, double>() &&
+           stc_smem_attr<gf::ST_SWEEP, float, double>();
 }
 
 // Node layers per CTA of stencil_tc32_kernel on a level: the fewest element layers per

@@ -481,6 +481,25 @@ first_sweep_kernel(const BT* __restrict__ b, T* __restrict__ out, const ET* __re
     first_sweep_node<T, ET, BT>(n, b, out, E, d, K0, omega);
 }
 
+// The same, storing the right-hand side converted to T once (bout) for the level's later
+// sweeps and residual: they then read T instead of converting BT at every read.
+template <typename T, typename ET, typename BT>
+__global__ void __launch_bounds__(256)
+first_sweep_store_kernel(const BT* __restrict__ b, T* __restrict__ bout, T* __restrict__ out,
+                         const ET* __restrict__ E, GridDims d, const __grid_constant__ K0Param<T> K0, T omega,
+                         const int* __restrict__ halt)
+{
+    if (halt != nullptr && *halt != 0) return;
+    const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    const T r0 = (T)b[3 * n + 0], r1 = (T)b[3 * n + 1], r2 = (T)b[3 * n + 2];
+    bout[3 * n + 0] = r0;
+    bout[3 * n + 1] = r1;
+    bout[3 * n + 2] = r2;
+    first_sweep_vals<T, ET>(n, r0, r1, r2, out, E, d, K0, omega);
+}
+
 // Restriction = transpose of trilinear prolongation, then mask: coarse node (I,J,K)
 // gathers the fine nodes (2I+di, 2J+dj, 2K+dk), di,dj,dk in {-1,0,1}, with weight
 // prod (1 if offset 0 else 1/2). `cd` are the coarse element counts.
