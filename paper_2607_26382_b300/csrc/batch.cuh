@@ -21,6 +21,7 @@ struct BatchTables {
     int* n;            // coarsest sizes
     int* m;            // coarsest free-DOF counts (the symmetric sweep's size)
     int** pos;         // coarsest free-DOF positions (gf_grid::cpos)
+    int* band;         // coarsest operator bands (gf_grid::cband)
 };
 
 __global__ void batch_mark_kernel(KState** st, const int* __restrict__ active, int B)
@@ -82,8 +83,9 @@ batch_gj_step_kernel(BatchTables t, const int* __restrict__ active, int s)
 // step s takes pivots SGJ_B*s .. SGJ_B*s + SGJ_B - 1. State i runs ceil(m_i/SGJ_B) steps
 // and starts in A_i when that count is odd, so its last step writes the upper triangle
 // (m_i x m_i) into W_i, as for one grid. The P buffers of state i sit past its full
-// second matrix buffer, W_i + n_i^2. Grid: (1 + tiles (tiles + 1) / 2, 1, B) for the
-// largest state's tiles x tiles; block 0 forms the next P, the others one upper tile.
+// second matrix buffer, W_i + n_i^2. Grid: (1 + tiles (tiles + 1) / 2, 1, B), tiles the
+// largest of the states' active tile counts at this step (sgj_active); block 0 forms the
+// next P, the others one upper tile (states skip the tiles past their own bound).
 __device__ __forceinline__ bool batch_sym_from_w(int m, int s)
 {
     return (((m + SGJ_B - 1) / SGJ_B + s) & 1) == 0;
@@ -103,9 +105,9 @@ batch_sym_gj_kernel(BatchTables t, const int* __restrict__ active, int s, int ti
         sym_gj_next_p(Min, m, k, Pb + SGJ_B * SGJ_B * (s & 1), Pb + SGJ_B * SGJ_B * ((s + 1) & 1));
         return;
     }
-    int tp, tq;   // upper tiles of the largest state's T x T, as sym_gj_kernel
+    int tp, tq;   // upper tiles of the leading tiles x tiles, as sym_gj_kernel
     sgj_upper_tile((int)blockIdx.x - 1, tiles, tp, tq);
-    if (tp * SGJ_T >= m || tq * SGJ_T >= m) return;   // uniform over the block
+    if (tq * SGJ_T >= sgj_active(m, k, t.band[i])) return;   // uniform over the block (tp <= tq)
     sym_gj_tile(Min, from_w ? t.A[i] : t.W[i], m, k, tp, tq, Pb + SGJ_B * SGJ_B * (s & 1));
 }
 
@@ -417,15 +419,16 @@ int batch_set_floor(gf_batch* b, const std::vector<int>& active, const std::vect
         if (rc != GF_OK) return rc;
         Level& c = g->lv[g->L - 1];
         const bool gal = g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1;   // as build_coarse_inverse of one grid
-        if (g->sym_gj) {   // the free-DOF matrix, in the buffer batch_sym_gj_kernel starts from
+        if (g->sym_gj) {   // the free-DOF matrix, in both buffers (as build_coarse_inverse of one grid)
             const long long m = g->ncf;
-            double* start = (((m + gf::SGJ_B - 1) / gf::SGJ_B) & 1) ? g->Ainv : g->Agj;
-            if (gal)
-                LAUNCH(g, nblk(m * m), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, start, c.dims(),
-                       (const int*)g->cidx, (int)m);
-            else
-                LAUNCH(g, nblk(m * m), 256, gf::coarse_assemble_kernel, (const double*)c.E64, start, c.dims(), g->K0d,
-                       (const int*)g->cidx, (int)m);
+            for (double* buf : {g->Ainv, g->Agj}) {
+                if (gal)
+                    LAUNCH(g, nblk(m * m), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, buf, c.dims(),
+                           (const int*)g->cidx, (int)m);
+                else
+                    LAUNCH(g, nblk(m * m), 256, gf::coarse_assemble_kernel, (const double*)c.E64, buf, c.dims(),
+                           g->K0d, (const int*)g->cidx, (int)m);
+            }
             continue;
         }
         const long long n = g->nc;
@@ -446,13 +449,17 @@ int batch_set_floor(gf_batch* b, const std::vector<int>& active, const std::vect
         int mmax = 0;
         for (int i = 0; i < B; ++i)
             if (active[i]) mmax = std::max(mmax, b->g[i]->ncf);
-        const unsigned st = (unsigned)std::max(1, (mmax + gf::SGJ_T - 1) / gf::SGJ_T);
         gf::batch_sym_gj_first_kernel<<<B, 256, 0, b->stream>>>(b->tab, b->d_active);
         b->launches += 1;
         CK(cudaGetLastError());
         for (int s = 0; gf::SGJ_B * s < mmax; ++s) {
-            gf::batch_sym_gj_kernel<<<dim3(1 + st * (st + 1) / 2, 1, B), dim3(16, 16), 0, b->stream>>>(
-                b->tab, b->d_active, s, (int)st);
+            int ts = 1;   // the largest active tile count of the states still sweeping
+            for (int i = 0; i < B; ++i)
+                if (active[i] && gf::SGJ_B * s < b->g[i]->ncf)
+                    ts = std::max(ts, (gf::sgj_active(b->g[i]->ncf, gf::SGJ_B * s, b->g[i]->cband) + gf::SGJ_T - 1) /
+                                          gf::SGJ_T);
+            gf::batch_sym_gj_kernel<<<dim3(1 + ts * (ts + 1) / 2, 1, B), dim3(16, 16), 0, b->stream>>>(
+                b->tab, b->d_active, s, ts);
             b->launches += 1;
             CK(cudaGetLastError());
         }
@@ -559,6 +566,7 @@ int gf_create_batch(int n_states, const int* dims, int levels, double h, double 
     if (cudaMalloc(&b->tab.st, P) != cudaSuccess || cudaMalloc(&b->tab.hist, P) != cudaSuccess ||
         cudaMalloc(&b->tab.A, P) != cudaSuccess || cudaMalloc(&b->tab.W, P) != cudaSuccess || cudaMalloc(&b->tab.n, sizeof(int) * n_states) != cudaSuccess ||
         cudaMalloc(&b->tab.m, sizeof(int) * n_states) != cudaSuccess || cudaMalloc(&b->tab.pos, P) != cudaSuccess ||
+        cudaMalloc(&b->tab.band, sizeof(int) * n_states) != cudaSuccess ||
         cudaMalloc(&b->d_active, sizeof(int) * n_states) != cudaSuccess ||
         cudaMalloc(&b->d_abort, sizeof(int) * n_states) != cudaSuccess)
         return fail(set_err(GF_ERR_OOM, "batch tables"));
@@ -567,19 +575,21 @@ int gf_create_batch(int n_states, const int* dims, int levels, double h, double 
         return fail(set_err(GF_ERR_CUDA, "mapped gather"));
     std::vector<double*> A(n_states), W(n_states);
     std::vector<int*> pos(n_states);
-    std::vector<int> n(n_states), m(n_states);
+    std::vector<int> n(n_states), m(n_states), band(n_states);
     for (int i = 0; i < n_states; ++i) {
         A[i] = b->g[i]->Ainv;
         W[i] = b->g[i]->Agj;
         n[i] = b->g[i]->nc;
         m[i] = b->g[i]->ncf;
+        band[i] = b->g[i]->cband;
         pos[i] = b->g[i]->cpos;
     }
     if (cudaMemcpy(b->tab.A, A.data(), P, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->tab.W, W.data(), P, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->tab.n, n.data(), sizeof(int) * n_states, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->tab.m, m.data(), sizeof(int) * n_states, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->tab.pos, pos.data(), P, cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(b->tab.pos, pos.data(), P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->tab.band, band.data(), sizeof(int) * n_states, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(set_err(GF_ERR_CUDA, "tables"));
     *out = b;
     return GF_OK;
@@ -601,7 +611,7 @@ int gf_destroy_batch(gf_batch* b)
     if (b->evFork) cudaEventDestroy(b->evFork);
     if (b->capS) cudaStreamDestroy(b->capS);
     cudaFree(b->tab.st); cudaFree(b->tab.hist); cudaFree(b->tab.A); cudaFree(b->tab.W);
-    cudaFree(b->tab.n); cudaFree(b->tab.m); cudaFree(b->tab.pos); cudaFree(b->d_active); cudaFree(b->d_abort);
+    cudaFree(b->tab.n); cudaFree(b->tab.m); cudaFree(b->tab.pos); cudaFree(b->tab.band); cudaFree(b->d_active); cudaFree(b->d_abort);
     if (b->gather_host) cudaFreeHost(b->gather_host);
     delete b;
     return GF_OK;

@@ -160,6 +160,7 @@ struct gf_grid {
     int* cpos = nullptr;              // coarsest level: position of each DOF among the free ones (-1: fixed)
     int* cidx = nullptr;              // coarsest level: the free DOFs in order; ncf of them (+1 word: the count)
     int ncf = 0;
+    int cband = 0;                    // coarsest level: bound on |p - q| over the operator's non-zeros (free DOFs)
     int* dflag = nullptr;
     // Krylov workspace
     int m_alloc = 0;
@@ -1146,6 +1147,11 @@ int build_coarse_map(gf_grid* g)
     CK(cudaMemcpyAsync(&m, g->cidx + g->nc, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     g->ncf = m;
+    // nodes couple to the 27 nodes around them: node indices differ by at most
+    // 1 + NX + NX NY (x fastest), DOF indices by 3 of that + 2; dropping the fixed DOFs
+    // only brings indices closer
+    const int NX = c.nx + 1, NY = c.ny + 1;
+    g->cband = 3 * (1 + NX + NX * NY) + 2;
     return GF_OK;
 }
 
@@ -1161,20 +1167,23 @@ int build_coarse_inverse(gf_grid* g)
         const long long m = g->ncf;
         const long long steps = (m + gf::SGJ_B - 1) / gf::SGJ_B;
         double* src = (steps & 1) ? g->Ainv : g->Agj;
-        if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1)
-            LAUNCH(g, nblk(m * m), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, src, c.dims(),
-                   (const int*)g->cidx, (int)m);
-        else
-            LAUNCH(g, nblk(m * m), 256, gf::coarse_assemble_kernel, c.E64, src, c.dims(), K, (const int*)g->cidx,
-                   (int)m);
-        const unsigned tiles = (unsigned)((m + gf::SGJ_T - 1) / gf::SGJ_T);
+        for (double* buf : {g->Ainv, g->Agj}) {   // both buffers start as A (the entries ahead of the band)
+            if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1)
+                LAUNCH(g, nblk(m * m), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, buf, c.dims(),
+                       (const int*)g->cidx, (int)m);
+            else
+                LAUNCH(g, nblk(m * m), 256, gf::coarse_assemble_kernel, c.E64, buf, c.dims(), K, (const int*)g->cidx,
+                       (int)m);
+        }
         double* Pb = g->Agj + n * n;   // two P buffers past the matrix
         if (m > 0) LAUNCH(g, 1, 256, gf::sym_gj_first_kernel, (const double*)src, (int)m, Pb);
         for (long long k = 0; k < m; k += gf::SGJ_B) {
             double* dst = (src == g->Ainv) ? g->Agj : g->Ainv;
             const int s = (int)(k / gf::SGJ_B);
-            LAUNCH(g, 1 + tiles * (tiles + 1) / 2, dim3(16, 16), gf::sym_gj_kernel, (const double*)src, dst, (int)m, (int)k,
-                   (const double*)(Pb + gf::SGJ_B * gf::SGJ_B * (s & 1)), Pb + gf::SGJ_B * gf::SGJ_B * ((s + 1) & 1));
+            const int tiles = (gf::sgj_active((int)m, (int)k, g->cband) + gf::SGJ_T - 1) / gf::SGJ_T;
+            LAUNCH(g, 1 + tiles * (tiles + 1) / 2, dim3(16, 16), gf::sym_gj_kernel, (const double*)src, dst, (int)m,
+                   (int)k, (const double*)(Pb + gf::SGJ_B * gf::SGJ_B * (s & 1)),
+                   Pb + gf::SGJ_B * gf::SGJ_B * ((s + 1) & 1), tiles);
             src = dst;
         }
         LAUNCH(g, std::min<long long>(nblk(n * n), 4LL * g->sms), 256, gf::sym_expand_kernel, (const double*)g->Agj,

@@ -744,20 +744,33 @@ __device__ __forceinline__ void sgj_upper_tile(int b, int T, int& tp, int& tq)
     tq = row + r;
 }
 
-// Pivots k .. k+SGJ_B-1 from Min into Mout (upper triangles) with P = Pin. Grid: one block
-// per upper SGJ_T tile (T (T + 1) / 2 of them, T = ceil(n / SGJ_T)) after block 0, which
-// leaves the next block's P in Pout. Only working blocks are launched, so the block
-// scheduler's round-robin gives every SM at most ceil(tiles / SMs) tiles.
+// The band: with A_pq = 0 for |p - q| > band, sweeping the pivots before k leaves
+// S = A_UU - A_UK A_KK^-1 A_KU banded too, so V_p = M_{p,B} = 0 (exactly: untouched zero
+// entries of A) for p >= k + SGJ_B + band, and W_q = P V_q = 0 there. Step k changes only
+// the entries with p, q below sgj_active(n, k, band); the rest still hold A's entries in
+// both buffers (both start as A), so only the tiles whose columns start below that bound
+// are launched. For the coarsest level's 27-point coupling this leaves about half of the
+// n^3/2 work (the swept part fills in; the part ahead stays banded).
+__host__ __device__ inline int sgj_active(int n, int k, int band)
+{
+    return min(n, k + SGJ_B + band);
+}
+
+// Pivots k .. k+SGJ_B-1 from Min into Mout (upper triangles) with P = Pin. Grid: block 0
+// leaves the next block's P in Pout; blocks 1 .. T (T + 1) / 2 take the upper SGJ_T tiles
+// of the leading T x T tiles, T = ceil(sgj_active(n, k, band) / SGJ_T). Only working
+// blocks are launched, so the block scheduler's round-robin gives every SM at most
+// ceil(tiles / SMs) tiles.
 __global__ void __launch_bounds__(256)
 sym_gj_kernel(const double* __restrict__ Min, double* __restrict__ Mout, int n, int k, const double* __restrict__ Pin,
-              double* __restrict__ Pout)
+              double* __restrict__ Pout, int tiles)
 {
     if (blockIdx.x == 0) {
         sym_gj_next_p(Min, n, k, Pin, Pout);
         return;
     }
     int tp, tq;
-    sgj_upper_tile((int)blockIdx.x - 1, (n + SGJ_T - 1) / SGJ_T, tp, tq);
+    sgj_upper_tile((int)blockIdx.x - 1, tiles, tp, tq);
     sym_gj_tile(Min, Mout, n, k, tp, tq, Pin);
 }
 
