@@ -1056,11 +1056,12 @@ def test_modal_apply_matches_oracle_and_dense(gf, dims, chunk, monkeypatch):
 @pytest.mark.parametrize("dims", [(16, 8, 8, 3), (24, 10, 6, 2), (2, 2, 2, 1), (8, 4, 4, 1), (12, 6, 6, 2)])
 def test_symmetric_blocked_inverse_matches_two_pivot_form(gf, dims, monkeypatch):
     """The coarsest level's dense FP64 inverse by the blocked symmetric sweep (8 pivots per
-    launch on the upper triangle; default) against the two-pivot full-matrix Gauss-Jordan
-    (GF_SYM_GJ=0): FP64 V-cycles agree to 1e-10 relative, on coarsest levels whose size is
-    not always a multiple of the pivot block (135 / 936 / 81 / 675 / 336 DOFs); on one-level
-    grids the inverse is the whole operator's, and its direct solution meets the oracle's
-    guard."""
+    launch on the upper triangle of the free-DOF matrix, each launch over the band ahead of
+    its pivots; default) against the two-pivot full-matrix Gauss-Jordan (GF_SYM_GJ=0): FP64
+    V-cycles agree to 1e-10 relative, on coarsest levels whose size is not always a multiple
+    of the pivot block (135 / 936 / 81 / 675 / 336 DOFs; at 936 and 675 the band, 278 and
+    167, leaves the early launches a leading block of the matrix); on one-level grids the
+    inverse is the whole operator's, and its direct solution meets the oracle's guard."""
     nx, ny, nz, L = dims
     outs = []
     for sym in ("1", "0"):
