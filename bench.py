@@ -604,7 +604,7 @@ def run_b300(args):
             "value": a2 / (ms2 / 1000.0), "unit": UNIT, "passes": args.states * 2, "accepted": a2,
             "fgmres_iters_per_pass": it2 / (args.states * 2), "records": rec2,
             "form": "outer 2: split-integer K*u (~2^-48 of |K||u|) and double-float CGS2 (~2^-47)",
-            "caution": ("at rho0 = 1e-12 this form stops on a projected estimate the FP64 guard rejects on 28 of "
+            "caution": ("at rho0 = 1e-12 this form stops on a projected estimate the FP64 guard rejects on 27-28 of "
                         "102 states (native FP64: 0); the guard keeps acceptance correct")}
     g.close()
     if not args.no_extras:
