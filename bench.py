@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["b300", "reference"], default="b300")
-    ap.add_argument("--states", type=int, default=2)
+    ap.add_argument("--states", type=int, default=4,
+                    help="192x96x96 states per step, solved together through the batch (gf_batch)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-class and 96x48x48 figures")
@@ -393,6 +394,37 @@ def timed_kernel(fn, reps=20):
     return k0.elapsed_time(k1) / reps / 1000.0
 
 
+def large_batch(gf, B):
+    """B 192x96x96 cantilever grids in one batch (gf_batch) and their tip loads."""
+    import torch
+    b = gf.Batch([LARGE] * B, levels=LEVELS)
+    fs = [b.cantilever_load(i, torch.zeros(b.n_dof[i], dtype=torch.float64, device="cuda")) for i in range(B)]
+    return b, fs
+
+
+def batched_passes(gf, b, rhos, fs, pol, steps):
+    """Algorithm-1 passes of all the batch's states together, `steps` times (each step sets
+    every state's density and load, then gf_batch_select_floor); (accepted, ms, records,
+    Arnoldi steps, FP64 K*u launches)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    acc, iters, recs, kus = 0, 0, [], 0
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        for i in range(len(b)):
+            b.set_state(i, rhos[i], fs[i], P_SIMP)
+        for out in b.select_floor(pol):
+            acc += int(out["status"] == gf.GF_ACCEPTED)
+            iters += sum(a["iters"] for a in out["attempts"]) + (out["probe_iters_run"] if out["escalated"] else 0)
+            kus += sum(a["iters"] + 1 for a in out["attempts"])   # Arnoldi K*z, then the guard
+            recs.append((out["floor_index"], out["escalated"], [a["iters"] for a in out["attempts"]],
+                         [a["accepted"] for a in out["attempts"]]))
+    e1.record()
+    torch.cuda.synchronize()
+    return acc, e0.elapsed_time(e1), recs, iters, kus
+
+
 def single_state_passes(gf, g, rhos, f, u, pol, steps):
     """Algorithm-1 passes over the states in turn; (accepted, ms, records, Arnoldi steps)."""
     import torch
@@ -518,13 +550,11 @@ def run_b300(args):
     rhos_h = W.large_states(state_seeds(rank, args.states))
     t_inputs = time.perf_counter() - t0
     rhos = [torch.as_tensor(r, device="cuda") for r in rhos_h]
-    g = gf.create_grid(*LARGE, levels=LEVELS)
-    f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
-    g.cantilever_load(f)
-    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    B = args.states
+    b, fs = large_batch(gf, B)
     pol = pol_of(gf, gf.GF_MIXED, 0)
 
-    single_state_passes(gf, g, rhos, f, u, pol, args.warmup)
+    batched_passes(gf, b, rhos, fs, pol, args.warmup)
 
     def barrier():
         if dist is not None:
@@ -533,15 +563,25 @@ def run_b300(args):
 
     clock = ClockSampler(local)
     barrier()
-    g.reset_stats()
+    launches0 = b.kernel_launches()
     clock.start()
-    accepted, ms, records, iters = single_state_passes(gf, g, rhos, f, u, pol, args.steps)
+    accepted, ms, records, iters, kus = batched_passes(gf, b, rhos, fs, pol, args.steps)
     barrier()
     clocks = clock.stop()
-    st = g.stats()
-    (ms,), (accepted, launches) = over_ranks(dist, "cuda", [ms], [accepted, st["kernel_launches"]])
+    (ms,), (accepted, launches) = over_ranks(dist, "cuda", [ms], [accepted, b.kernel_launches() - launches0])
     accepted, launches = int(accepted), int(launches)
     value = accepted / (ms / 1000.0)
+
+    # the same passes one state at a time through one grid (gf_select_floor)
+    g = gf.create_grid(*LARGE, levels=LEVELS)
+    f = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    g.cantilever_load(f)
+    u = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+    single_state_passes(gf, g, rhos, f, u, pol, 2)
+    a1, ms1, _, it1 = single_state_passes(gf, g, rhos, f, u, pol, args.steps)
+    single = {"value": a1 / (ms1 / 1000.0), "unit": UNIT, "passes": args.steps, "accepted": a1,
+              "ms_per_pass": ms1 / args.steps, "fgmres_iters_per_pass": it1 / args.steps,
+              "form": "one state at a time through one grid (gf_select_floor), same states and policy"}
 
     # ---- kernels timed alone on the grid's stream (CUDA events, after warm-up)
     g.set_density(rhos[0], P_SIMP)
@@ -565,7 +605,7 @@ def run_b300(args):
     modal_peak = 148 * 2 * sm_max * 1e6 * (MODAL_FLOPS / MODAL_INSTR) / 1e12
     # share of the timed region spent in the native FP64 operator (Arnoldi K*z, cycle-start
     # residuals, guards): its launches in the timed region x its duration timed alone
-    share_fp64 = st["apply_K_fp64"] * t_k / (ms / 1000.0) if ms > 0 else None
+    share_fp64 = kus * t_k / (ms / 1000.0) if ms > 0 else None
     native = {"bound": "alu", "achieved": modal_flops / t_k / 1e12, "peak": modal_peak, "unit": "TFLOP/s",
               "frac": modal_flops / t_k / 1e12 / modal_peak,
               "traffic": profiled_traffic("apply_modal_kernel_192x96x96.md", *MODAL_SPAN),
@@ -579,7 +619,7 @@ def run_b300(args):
                                    "ratio": flops / t_k / 1e12 / fp64_peak,
                                    "note": "1152 flop/element of the dense 24x24 product per launch time"},
               "gdofs": g.n_dof / t_k / 1e9, "ms_per_launch": t_k * 1e3,
-              "launches_in_timed_region": st["apply_K_fp64"], "share_of_timed_region_est": share_fp64}
+              "launches_in_timed_region": kus, "share_of_timed_region_est": share_fp64}
     stencil = {"bound": "alu", "achieved": flops / t_32 / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                "frac": flops / t_32 / 1e12 / fp32_peak,
                "traffic": None,
@@ -595,7 +635,7 @@ def run_b300(args):
     roofline = dict(native)
     roofline["other_kernels"] = {"vcycle_stencil_fp32": stencil, "split_operator": split}
 
-    extras = {}
+    extras = {"single_state_192x96x96": single}
     if not args.no_extras:
         # the FP64-class Krylov form on the same states (split-integer operator, double-float CGS2)
         single_state_passes(gf, g, rhos, f, u, pol_of(gf, gf.GF_MIXED, 2), 1)
@@ -603,7 +643,8 @@ def run_b300(args):
         extras["fp64class_krylov_192x96x96"] = {
             "value": a2 / (ms2 / 1000.0), "unit": UNIT, "passes": args.states * 2, "accepted": a2,
             "fgmres_iters_per_pass": it2 / (args.states * 2), "records": rec2,
-            "form": "outer 2: split-integer K*u (~2^-48 of |K||u|) and double-float CGS2 (~2^-47)",
+            "form": ("outer 2: split-integer K*u (~2^-48 of |K||u|) and double-float CGS2 (~2^-47); one state at a "
+                     "time"),
             "caution": ("at rho0 = 1e-12 this form stops on a projected estimate the FP64 guard rejects on 27-28 of "
                         "102 states (native FP64: 0); the guard keeps acceptance correct")}
     g.close()
@@ -632,61 +673,63 @@ def run_b300(args):
     if not args.no_batch:
         batch = comparison_102(gf, dist)
 
-    # ---- end to end through the public API with host buffers (pinned), 192x96x96
+    # ---- end to end through the public API with host buffers (pinned), 192x96x96: the
+    # batched passes, every state's density and load uploaded and its solution read back
     e2e = None
     if not args.no_e2e:
-        g = gf.create_grid(*LARGE, levels=LEVELS)
         rho_pin = [torch.as_tensor(r).pin_memory() for r in rhos_h]
-        f0 = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
-        g.cantilever_load(f0)
-        f_pin = f0.cpu().pin_memory()
-        # double-buffered device inputs and solutions: step i+1's inputs go up and step
-        # i's solution comes back on a copy stream while step i+1 solves
-        f_d = [torch.empty_like(f0) for _ in range(2)]
-        rho_d = [torch.empty(g.n_elem, dtype=torch.float64, device="cuda") for _ in range(2)]
-        u = [torch.zeros_like(f0) for _ in range(2)]
-        u_pin = [torch.empty(g.n_dof, dtype=torch.float64).pin_memory() for _ in range(2)]
+        f_pin = fs[0].cpu().pin_memory()
+        n_dof, n_elem = b.n_dof[0], b.n_elem[0]
+        # double-buffered device inputs and solutions: step s+1's inputs go up and step s's
+        # solutions come back on a copy stream while the neighbouring step solves
+        rho_d = [[torch.empty(n_elem, dtype=torch.float64, device="cuda") for _ in range(B)] for _ in range(2)]
+        f_d = [[torch.empty(n_dof, dtype=torch.float64, device="cuda") for _ in range(B)] for _ in range(2)]
+        u_d = [[torch.empty(n_dof, dtype=torch.float64, device="cuda") for _ in range(B)] for _ in range(2)]
+        u_pin = [[torch.empty(n_dof, dtype=torch.float64).pin_memory() for _ in range(B)] for _ in range(2)]
         copy_stream = torch.cuda.Stream()
-        for i in range(min(args.warmup, 1)):
-            g.set_density(rhos[0], P_SIMP)
-            g.select_floor(f0, u[0], pol)
         barrier()
         t0 = time.perf_counter()
         acc_e2e = 0
 
-        def upload(i):
+        def upload(s):
             with torch.cuda.stream(copy_stream):
-                rho_d[i % 2].copy_(rho_pin[i % len(rho_pin)], non_blocking=True)
-                f_d[i % 2].copy_(f_pin, non_blocking=True)
+                for i in range(B):
+                    rho_d[s % 2][i].copy_(rho_pin[i], non_blocking=True)
+                    f_d[s % 2][i].copy_(f_pin, non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(copy_stream)
             return ev
 
         ready = upload(0)
         fetched = [None, None]
-        for i in range(args.steps):
-            ready.synchronize()                      # step i's inputs are on the device
-            if fetched[i % 2] is not None:
-                fetched[i % 2].synchronize()         # step i-2's solution has left u[i % 2]
-            if i + 1 < args.steps:
-                ready = upload(i + 1)                # overlaps step i's solve
-            g.set_density(rho_d[i % 2], P_SIMP)
-            out = g.select_floor(f_d[i % 2], u[i % 2], pol)   # returns once the solve is done
-            with torch.cuda.stream(copy_stream):     # overlaps step i+1's solve
-                u_pin[i % 2].copy_(u[i % 2], non_blocking=True)
-                fetched[i % 2] = torch.cuda.Event()
-                fetched[i % 2].record(copy_stream)
-            acc_e2e += int(out["status"] == gf.GF_ACCEPTED)
+        for s in range(args.steps):
+            ready.synchronize()                      # step s's inputs are on the device
+            if fetched[s % 2] is not None:
+                fetched[s % 2].synchronize()         # step s-2's solutions have left u_d[s % 2]
+            if s + 1 < args.steps:
+                ready = upload(s + 1)                # overlaps step s's solve
+            for i in range(B):
+                b.set_state(i, rho_d[s % 2][i], f_d[s % 2][i], P_SIMP)
+            outs = b.select_floor(pol)               # returns once every state is done
+            for i in range(B):
+                b.solution(i, u_d[s % 2][i])
+            with torch.cuda.stream(copy_stream):     # overlaps step s+1's solve
+                for i in range(B):
+                    u_pin[s % 2][i].copy_(u_d[s % 2][i], non_blocking=True)
+                fetched[s % 2] = torch.cuda.Event()
+                fetched[s % 2].record(copy_stream)
+            acc_e2e += sum(int(o["status"] == gf.GF_ACCEPTED) for o in outs)
         copy_stream.synchronize()
         torch.cuda.synchronize()
         barrier()
         dt = time.perf_counter() - t0
         (dt,), (acc_e2e,) = over_ranks(dist, "cuda", [dt], [acc_e2e])
-        e2e = {"value": int(acc_e2e) / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * (g.n_elem + g.n_dof),
-               "d2h_bytes_per_step": 8 * g.n_dof,
-               "note": "pinned host buffers; step i+1's upload and step i's download run on a copy stream "
-                       "during the neighbouring solves (double-buffered device inputs and solutions)"}
-        g.close()
+        e2e = {"value": int(acc_e2e) / dt, "unit": UNIT, "h2d_bytes_per_step": 8 * B * (n_elem + n_dof),
+               "d2h_bytes_per_step": 8 * B * n_dof,
+               "note": ("pinned host buffers; every step uploads each state's density and load and reads back "
+                        "its solution; step s+1's uploads and step s's downloads run on a copy stream during "
+                        "the neighbouring solves (double-buffered device inputs and solutions)")}
+    b.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -697,6 +740,8 @@ def run_b300(args):
               "scaling": "weak", "vs_baseline": None, "dtype": "f64 (Krylov, guard, coarsest) / f32+bf16 (V-cycle)",
               "data": "synthetic",
               "config": {"workload": WORKLOAD, "n_dof": 3 * 193 * 97 * 97, "states": args.states,
+                         "step": (f"one Algorithm-1 pass of each of {args.states} states, solved together by "
+                                  "gf_batch_select_floor (lockstep FGMRES, one CUDA graph per step)"),
                          "parallelism": f"replicas x{world}", "seconds_inputs": t_inputs,
                          "l2": "inputs larger than L2 (Krylov bases V, Z = 2.66 GB per state solve)"},
               "accepted": accepted, "fgmres_iters_per_step": iters / args.steps, "records": records,

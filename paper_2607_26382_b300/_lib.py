@@ -512,6 +512,13 @@ class Batch:
         _check(lib().gf_batch_solution(self._h, int(i), _ptr(u, _torch().float64, self.n_dof[i], "u")))
         return u
 
+    def cantilever_load(self, i, f):
+        """The cantilever tip load of state i's grid into f (gf_cantilever_load)."""
+        gh = c_void_p()
+        _check(lib().gf_batch_grid(self._h, int(i), ctypes.byref(gh)))
+        _check(lib().gf_cantilever_load(gh, _ptr(f, _torch().float64, self.n_dof[i], "f")))
+        return f
+
     def set_coarse_operator(self, kind):
         """gf_batch_set_coarse_operator: GF_COARSE_REDISCRETISED or GF_COARSE_GALERKIN for every state."""
         _check(lib().gf_batch_set_coarse_operator(self._h, int(kind)))
