@@ -66,11 +66,11 @@ __device__ __forceinline__ void block_rows(long long n, long long& r0, long long
 // their loads (predicated) in flight together, then the FP64 multiply-adds run for the nv
 // live vectors only: the FP64 pipe, not memory, bounds these passes on B300 once nv is a
 // few vectors, and a multiply-add by a zero entry would cost as much as a real one. Below
-// that the rows in flight hide the HBM latency (two rows per iteration for NV = 8; the
+// that the rows in flight hide the HBM latency (four rows per iteration for NV = 8; the
 // results do not depend on it). The grid is the blocks resident at once (gf_grid::nbc).
 template <int NV>
 struct CgsRows {
-    static constexpr int value = NV <= 8 ? 2 : 1;
+    static constexpr int value = NV <= 8 ? 4 : 1;
 };
 
 // pass 1: partial[b][i] = sum_r V_i[r] w[r] (i < nv), partial[b][nv] = sum_r w[r]^2
