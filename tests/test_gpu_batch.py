@@ -137,3 +137,18 @@ def test_batch_galerkin_matches_single_state(gf, prec, outer):
             assert eta <= 1e-6 * (1 + 1e-9)
         g.close()
     batch.close()
+
+
+def test_batch_cantilever_load_matches_grid_and_oracle(gf):
+    # Batch.cantilever_load writes each state's tip load on its own grid: the same vector
+    # as a single grid of that size, and the oracle's load
+    dims = [(16, 8, 8), (20, 12, 8)]
+    b = gf.Batch(dims, levels=2)
+    for i, d in enumerate(dims):
+        fb = b.cantilever_load(i, torch.empty(b.n_dof[i], dtype=torch.float64, device="cuda"))
+        g = gf.create_grid(*d, levels=2)
+        fg = g.cantilever_load(torch.empty(g.n_dof, dtype=torch.float64, device="cuda"))
+        assert torch.equal(fb, fg)
+        assert np.array_equal(fb.cpu().numpy(), O.cantilever_load(O.Mesh(*d)))
+        g.close()
+    b.close()
