@@ -47,8 +47,10 @@ FP64_PEAK_NOTE = "derived: 148 SMs x 2 FP64 FMA/clk x 2 flop x sm_max_mhz"
 FP32_PEAK_NOTE = "derived: 148 SMs x 128 FP32 FMA/clk x 2 flop x sm_max_mhz"
 WORKLOAD = ("cantilever 192x96x96 (5,447,811 DOF), optimised-like density: 40 guarded SIMP-OC iterations "
             "(vol 0.3, linear-hat filter r=1.5, p=3, rho_min 1e-3) then a seeded 30% of voxels forced to "
-            "floor; probe at 1e-6, ladder {1e-5,1e-4,1e-3}; FGMRES(30), kmax 200, 5-level GMG, FP32/BF16 "
-            "V-cycle, native FP64 Krylov (K*u, CGS2, Givens), FP64 coarsest solve and guard, tau=1e-6")
+            "floor; probe at 1e-6, ladder {1e-5,1e-4,1e-3}; FGMRES(30), kmax 200, 5-level GMG (2+2 Jacobi "
+            "sweeps, omega 0.6), guard tau=1e-6 on the recomputed FP64 residual")
+# the GPU arm's arithmetic (the oracle is FP64 throughout)
+GPU_ARITHMETIC = ("FP32/BF16 V-cycle, native FP64 Krylov (K*u, CGS2, Givens), FP64 coarsest solve and guard")
 # the oracle's sample: the same recipe at 24x12x12 (3 levels), made by the oracle's own SIMP-OC
 CPU_DIMS, CPU_LEVELS = (24, 12, 12), 3
 CPU_WORKLOAD = ("cantilever 24x12x12 (12,675 DOF) made by the same recipe with the oracle's own SIMP-OC "
@@ -750,7 +752,7 @@ def run_b300(args):
               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
               "scaling": "weak", "vs_baseline": None, "dtype": "f64 (Krylov, guard, coarsest) / f32+bf16 (V-cycle)",
               "data": "synthetic",
-              "config": arm_config(args, world), "seconds_inputs": t_inputs,
+              "config": arm_config(args, world), "arithmetic": GPU_ARITHMETIC, "seconds_inputs": t_inputs,
               "accepted": accepted, "fgmres_iters_per_step": iters / args.steps, "records": records,
               "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
               "cpu_baseline": cpu, "apply_K_fp64_gdofs": native["gdofs"], "apply_K_split_gdofs": split["gdofs"],
