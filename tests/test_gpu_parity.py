@@ -1022,6 +1022,53 @@ def test_full_size_select_floor_matches_oracle_record(gf, prec, outer):
     assert out["eta"] <= w["tau"]
 
 
+def _check_against_record(out, rec):
+    w = rec["workload"]
+    assert out["status"] == rec["status"] and out["floor_index"] == rec["floor_index"]
+    assert out["escalated"] == rec["escalated"]
+    assert abs(out["r50"] - rec["r50"]) <= 1e-4 * rec["r50"]
+    assert abs(out["r100"] - rec["r100"]) <= 1e-4 * rec["r100"]
+    assert len(out["attempts"]) == len(rec["attempts"])
+    for a, b in zip(out["attempts"], rec["attempts"]):
+        assert a["rho_min"] == b["rho_min"] and abs(a["iters"] - b["iters"]) <= 2
+        assert a["accepted"] == b["accepted"]
+    assert out["eta"] <= w["tau"]
+
+
+@pytest.mark.parametrize("form", ["single", "batch"])
+def test_192x96x96_select_floor_matches_oracle_record(gf, form):
+    """Algorithm 1 at the large workload's size (192x96x96, 5 levels) on the
+    smoothed-Gaussian state of seed 0 against the oracle's record
+    (tests/golden/policy_c3_seed0.json, written by tests/golden/make_policy_records.py
+    --size c3 from oracle/ alone), in the form the benchmark times: mixed V-cycle, native
+    FP64 Krylov, one grid ("single") or two copies of the state solved together by the
+    batch ("batch"). The same checks as the 96x48x48 record."""
+    import json
+    import os
+    rec = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "policy_c3_seed0.json")))
+    w = rec["workload"]
+    dims = (w["nx"], w["ny"], w["nz"])
+    rho = dev(synth.smoothed_gaussian_density(*dims, rec["seed"], w["sigma"], w["floor_frac"]))
+    pol = gf.policy_defaults(rho0=w["rho0"], ladder=w["ladder"], tau=w["tau"], kmax=w["kmax"],
+                             probe_iters=w["probe_iters"], solve_restart=w["restart"], solve_prec=gf.GF_MIXED,
+                             solve_outer=0)
+    if form == "single":
+        g = gf.create_grid(*dims, levels=w["levels"])
+        g.set_density(rho, w["p"])
+        f = g.cantilever_load(torch.zeros(g.n_dof, dtype=torch.float64, device="cuda"))
+        outs = [g.select_floor(f, torch.zeros_like(f), pol)]
+        g.close()
+    else:
+        b = gf.Batch([dims] * 2, levels=w["levels"])
+        for i in range(2):
+            b.set_state(i, rho, b.cantilever_load(i, torch.zeros(b.n_dof[i], dtype=torch.float64, device="cuda")),
+                        w["p"])
+        outs = b.select_floor(pol)
+        b.close()
+    for out in outs:
+        _check_against_record(out, rec)
+
+
 # ------------------------------------------------------------- modal FP64 K*u -----
 @pytest.mark.parametrize("chunk", ["0", "1", "3", "7"])
 @pytest.mark.parametrize("dims", [(40, 20, 10, 2), (34, 18, 10, 2), (1, 2, 2, 1), (60, 28, 12, 3), (31, 14, 4, 1)])
