@@ -136,6 +136,7 @@ struct gf_grid {
     gf::ModalCoefF Kmodal32;          // the same in FP32 with K0's node blocks (modal_stencil_f32_kernel)
     bool modal_f32 = true;            // level-0 FP32 stencils in the modal basis (GF_MODAL_F32=0: node stencils)
     int4* modal_items = nullptr;      // work items of the modal FP64 K*u (device; null: dense stencil)
+    double* modal_es = nullptr;       // its elements' scaled coefficients E_e C, 9 x nel (modal_scale_kernel)
     int modal_n = 0, modal_bx = 32;   // item count; CTA tile 32 x 16 or 16 x 32 element columns
     bool sym_gj = true;               // coarsest inverse by the blocked symmetric sweep (GF_SYM_GJ=0: two-pivot form)
     int geom = GF_GEOM_CANTILEVER;    // supports: the clamped face x = 0, or the bridge's (gf_set_geometry)
@@ -1014,20 +1015,20 @@ int applyK64(gf_grid* g, const double* u, double* y, const int* halt)
     g->stats.apply_K_fp64++;
     if (g->modal_items) {   // modal factorisation of K0 (default; GF_MODAL=0: dense node stencil)
         const bool mk = g->lv[0].fix != nullptr;   // per-node fixed components (bridge supports)
-        const double* E = g->lv[0].E64;
+        const double* Es = g->modal_es;
         const int4* it = g->modal_items;
         if (g->modal_bx == 32 && mk)
-            RET((launch_modal<double, 32, 16, gf::apply_modal_kernel<32, 16, true>>(g, g->modal_n, u, y, E,
-                                                                                   g->lv[0].dims(), g->Kmodal, it, halt)));
+            RET((launch_modal<double, 32, 16, gf::apply_modal_kernel<32, 16, true>>(g, g->modal_n, u, y, Es,
+                                                                                   g->lv[0].dims(), it, halt)));
         else if (g->modal_bx == 32)
-            RET((launch_modal<double, 32, 16, gf::apply_modal_kernel<32, 16, false>>(g, g->modal_n, u, y, E,
-                                                                                    g->lv[0].dims(), g->Kmodal, it, halt)));
+            RET((launch_modal<double, 32, 16, gf::apply_modal_kernel<32, 16, false>>(g, g->modal_n, u, y, Es,
+                                                                                    g->lv[0].dims(), it, halt)));
         else if (mk)
-            RET((launch_modal<double, 16, 32, gf::apply_modal_kernel<16, 32, true>>(g, g->modal_n, u, y, E,
-                                                                                   g->lv[0].dims(), g->Kmodal, it, halt)));
+            RET((launch_modal<double, 16, 32, gf::apply_modal_kernel<16, 32, true>>(g, g->modal_n, u, y, Es,
+                                                                                   g->lv[0].dims(), it, halt)));
         else
-            RET((launch_modal<double, 16, 32, gf::apply_modal_kernel<16, 32, false>>(g, g->modal_n, u, y, E,
-                                                                                    g->lv[0].dims(), g->Kmodal, it, halt)));
+            RET((launch_modal<double, 16, 32, gf::apply_modal_kernel<16, 32, false>>(g, g->modal_n, u, y, Es,
+                                                                                    g->lv[0].dims(), it, halt)));
         return GF_OK;
     }
     return stencil<double, double, gf::ST_APPLY>(g, 0, u, nullptr, y, g->lv[0].E64, g->K0d, 0.0, halt);
@@ -1867,7 +1868,9 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
             const std::vector<int4>& items = use32 ? i32 : i16;
             g->modal_bx = use32 ? 32 : 16;
             g->modal_n = (int)items.size();
-            if (alloc((void**)&g->modal_items, sizeof(int4) * items.size()) != GF_OK) return fail(GF_ERR_OOM);
+            if (alloc((void**)&g->modal_items, sizeof(int4) * items.size()) != GF_OK ||
+                alloc((void**)&g->modal_es, sizeof(double) * 9 * (size_t)g->nel) != GF_OK)
+                return fail(GF_ERR_OOM);
             if (cudaMemcpy(g->modal_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) !=
                 cudaSuccess)
                 return fail(set_err(GF_ERR_CUDA, "modal work items"));
@@ -2080,14 +2083,14 @@ int modal_autotune(gf_grid* g)
         if (c.bx == 32)
             gf::apply_modal_kernel<32, 16><<<(unsigned)c.items.size(), dim3(32, 16),
                                              gf::modal_smem_bytes<double, 32, 16>(), g->stream>>>(
-                f.x64, f.t64, f.E64, f.dims(), g->Kmodal, dev, nullptr);
+                f.x64, f.t64, g->modal_es, f.dims(), dev, nullptr);
         else
             gf::apply_modal_kernel<16, 32><<<(unsigned)c.items.size(), dim3(16, 32),
                                              gf::modal_smem_bytes<double, 16, 32>(), g->stream>>>(
-                f.x64, f.t64, f.E64, f.dims(), g->Kmodal, dev, nullptr);
+                f.x64, f.t64, g->modal_es, f.dims(), dev, nullptr);
     };
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
-        cudaMemsetAsync(f.E64, 0, sizeof(double) * f.nel, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(g->modal_es, 0, sizeof(double) * 9 * f.nel, g->stream) != cudaSuccess ||
         cudaMemsetAsync(f.x64, 0, sizeof(double) * f.ndof, g->stream) != cudaSuccess)
         rc = set_err(GF_ERR_CUDA, "modal autotune set-up");
     for (size_t i = 0; rc == GF_OK && i < cand.size(); ++i) {
@@ -2155,6 +2158,7 @@ int gf_destroy_grid(gf_grid* g)
     cudaFree(g->lzv);
     cudaFree(g->Edf);
     cudaFree(g->modal_items);
+    cudaFree(g->modal_es);
     cudaFree(g->B3);
     cudaFree(g->Btc);
     cudaFree(g->oc_rho); cudaFree(g->oc_dc); cudaFree(g->oc_dcx); cudaFree(g->oc_dvx); cudaFree(g->oc_ones);
@@ -2223,6 +2227,9 @@ int gf_set_floor(gf_grid* g, double rho_min)
     const int p_int = (p == std::floor(p)) ? (int)p : 0;
     Level& f = g->lv[0];
     LAUNCH(g, nblk(g->nel), 256, gf::modulus_fp64_kernel, g->rho64, f.E64, g->nel, rho_min, p, p_int, f.h);
+    if (g->modal_es)
+        LAUNCH(g, nblk(g->nel), 256, gf::modal_scale_kernel, (const double*)f.E64, g->Kmodal, g->modal_es,
+               (long long)g->nel);
     LAUNCH(g, nblk(g->nel), 256, gf::modulus_fp32_kernel, g->rho16, f.E32, g->nel, (float)rho_min, (float)p,
            p_int, (float)f.h);
     if (g->has_split) LAUNCH(g, nblk(g->nel), 256, gf::edf_kernel, (const double*)f.E64, g->s_split, g->Edf, g->nel);

@@ -19,9 +19,10 @@
 //
 // Cost per element: the sum/difference network forward (48 FP64 adds, a face of
 // the column's next node plane transformed once and reused by the element above),
-// 9 scalings by E_e and 45 multiply-adds in modal space, the transposed network back
-// (60), and the 9 adds of the node gather -- about 170 FP64 instructions against the
-// 576 FMAs of the dense 24x24 product. B300 issues FP64 at 1/64 of the FP32 rate, so
+// 45 multiply-adds in modal space with the element's 9 coefficients E_e C (scaled once
+// per floor, modal_scale_kernel), the transposed network back (60), and the 9 adds of
+// the node gather -- 162 FP64 instructions against the 576 FMAs of the dense 24x24
+// product. B300 issues FP64 at 1/64 of the FP32 rate, so
 // this count, not memory, bounds the kernel.
 //
 // Layout of the work: a CTA owns BX x BY element columns (a tile plus a one-element
@@ -156,6 +157,20 @@ inline std::vector<int4> modal_plan(int nx, int ny, int nz, int bx, int by, int 
     return items;
 }
 
+// The 9 scaled modal coefficients of every element, E_e C.diag[1..5] then E_e C.cross[0..3],
+// as 9 arrays of nel (Es[k * nel + e]): the element's only coupling to its modulus in
+// apply_modal_kernel, formed once per floor (the same FP64 products the kernel would form).
+__global__ void modal_scale_kernel(const double* __restrict__ E, ModalCoef C, double* __restrict__ Es, long long nel)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nel) return;
+    const double s = E[e];
+#pragma unroll
+    for (int k = 1; k < 6; ++k) Es[(k - 1) * nel + e] = s * C.diag[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Es[(5 + k) * nel + e] = s * C.cross[k];
+}
+
 // 2D sum/difference transform of a face: v[x + 2y] -> f[bx + 2by] = sum s_x^bx s_y^by v.
 template <typename T>
 __device__ __forceinline__ void face_fwd(const T v[4], T f[4])
@@ -186,8 +201,8 @@ __device__ __forceinline__ void face_inv(const T f[4], T v[4])
 // MASK: fixed components from d.fix (any supports); otherwise the clamped face x = 0.
 template <int BX, int BY, bool MASK = false>
 __global__ void __launch_bounds__(MODAL_THREADS, 1)
-apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const double* __restrict__ E,
-                   GridDims d, ModalCoef C, const int4* __restrict__ items, const int* __restrict__ halt)
+apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const double* __restrict__ Es,
+                   GridDims d, const int4* __restrict__ items, const int* __restrict__ halt)
 {
     if (halt != nullptr && *halt != 0) return;
     // two buffers of corner forces [corner * 3 + comp][column], by step parity (dynamic
@@ -249,12 +264,14 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
                     m[c][q] = top[c][q] + bot[c][q];
                     m[c][q + 4] = top[c][q] - bot[c][q];
                 }
-            const double s = __ldg(E + ex + (long long)d.nx * (ey + (long long)d.ny * ez));
+            // the element's scaled modal coefficients E_e C (modal_scale_kernel, once per floor)
+            const long long e = ex + (long long)d.nx * (ey + (long long)d.ny * ez);
+            const long long nel = (long long)d.nx * d.ny * d.nz;
             double sd[6], sc[4];
 #pragma unroll
-            for (int k = 1; k < 6; ++k) sd[k] = s * C.diag[k];
+            for (int k = 1; k < 6; ++k) sd[k] = __ldg(Es + (k - 1) * nel + e);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) sc[k] = s * C.cross[k];
+            for (int k = 0; k < 4; ++k) sc[k] = __ldg(Es + (5 + k) * nel + e);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 double G[8];
