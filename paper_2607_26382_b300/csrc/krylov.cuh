@@ -128,6 +128,8 @@ cgs_dots_kernel(const double* __restrict__ V, long long ld, int nv, const double
 }
 
 // pass 2: w -= sum_i h1_i V_i ; partial[b][i] = sum_r V_i[r] w_new[r]
+// (the update runs as w_new = fma(-h_nv-1, V_nv-1, ... fma(-h_0, V_0, w)): nv FMAs, no
+// separate subtraction; the negated coefficients are formed once per block)
 template <int NV>
 __global__ void __launch_bounds__(RED_THREADS)
 cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
@@ -135,9 +137,9 @@ cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, doubl
 {
     constexpr int ROWS = CgsRows<NV>::value;
     if (st->status != KS_RUN) return;
-    __shared__ double h[NV];
+    __shared__ double h[NV];   // -h1
     double acc[NV];
-    if (threadIdx.x < NV) h[threadIdx.x] = threadIdx.x < nv ? st->h1[threadIdx.x] : 0.0;
+    if (threadIdx.x < NV) h[threadIdx.x] = threadIdx.x < nv ? -st->h1[threadIdx.x] : 0.0;
 #pragma unroll
     for (int q = 0; q < NV; ++q) acc[q] = 0.0;
     __syncthreads();
@@ -157,13 +159,13 @@ cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, doubl
         for (int u = 0; u < ROWS; ++u) {
             const long long rr = r + (long long)u * RED_THREADS;
             if (rr >= r1) break;
-            double s = 0.0;
+            double s = wr[u];
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
                 if (q >= nv) break;
                 s = fma(h[q], v[u][q], s);
             }
-            const double wn = wr[u] - s;
+            const double wn = s;
             w[rr] = wn;
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
@@ -176,7 +178,7 @@ cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, doubl
 }
 
 // pass 3: w -= sum_i h2_i V_i ; partial[b][0] = ||w_new||^2 (block part)
-// (NV = 32: two groups of 16 vectors, as in pass 1)
+// (NV = 32: two groups of 16 vectors, as in pass 1; the update as in pass 2, from -h2)
 template <int NV>
 __global__ void __launch_bounds__(RED_THREADS, NV >= 16 ? 2 : 1)
 cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
@@ -185,8 +187,8 @@ cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, doubl
     constexpr int ROWS = CgsRows<NV>::value;
     constexpr int G = NV == 32 ? 16 : NV;
     if (st->status != KS_RUN) return;
-    __shared__ double h[NV];
-    if (threadIdx.x < NV) h[threadIdx.x] = threadIdx.x < nv ? st->h2[threadIdx.x] : 0.0;
+    __shared__ double h[NV];   // -h2
+    if (threadIdx.x < NV) h[threadIdx.x] = threadIdx.x < nv ? -st->h2[threadIdx.x] : 0.0;
     __syncthreads();
     double acc[1] = {0.0};
     long long r0, r1;
@@ -197,7 +199,7 @@ cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, doubl
         for (int u = 0; u < ROWS; ++u) {
             const long long rr = r + (long long)u * RED_THREADS;
             wr[u] = (u == 0 || rr < r1) ? w[rr] : 0.0;
-            s[u] = 0.0;
+            s[u] = wr[u];
         }
 #pragma unroll
         for (int g0 = 0; g0 < NV; g0 += G) {
@@ -223,7 +225,7 @@ cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, doubl
         for (int u = 0; u < ROWS; ++u) {
             const long long rr = r + (long long)u * RED_THREADS;
             if (rr >= r1) break;
-            const double wn = wr[u] - s[u];
+            const double wn = s[u];
             w[rr] = wn;
             acc[0] = fma(wn, wn, acc[0]);
         }
