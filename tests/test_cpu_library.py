@@ -91,3 +91,24 @@ def test_conditioning_screen_matches_oracle(gflib):
     for bad in ((0.0, 1.0, 1e-6, 1e-6), (2.0, 1.0, 1e-6, 1e-6), (1e-3, 1.0, 0.0, 1e-6), (1e-3, 1.0, 1e-6, 0.0)):
         with pytest.raises(gflib.GFError):
             gflib.conditioning_screen(*bad)
+
+
+@pytest.mark.parametrize("dims,bridge", [((12, 6, 6), False), ((12, 5, 3), False), ((8, 4, 4), False),
+                                         ((12, 6, 6), True), ((16, 4, 8), True)])
+def test_coarsest_band_bound_holds_for_the_free_dof_matrix(dims, bridge):
+    """The coarsest inverse's sweep launches only the tiles inside the band ahead of its
+    pivots, assuming the free-DOF operator (free DOFs in ascending order) has no non-zero
+    with |p - q| > 3 (1 + NX + NX NY) + 2. The oracle's assembled operator, with random
+    moduli, stays inside that band for the cantilever and for the bridge's supports, and
+    reaches within one node layer of it (the bound is not loose by a layer)."""
+    nx, ny, nz = dims
+    mesh = O.BridgeMesh(nx, ny, nz) if bridge else O.Mesh(nx, ny, nz)
+    E = np.random.default_rng(nx * ny + nz).uniform(0.01, 1.0, mesh.n_elem)
+    K = O.assemble_sparse(mesh, E, O.element_stiffness(), constrained=False)
+    free = np.flatnonzero(mesh.free)
+    rows, cols = K[free][:, free].nonzero()
+    NX, NY = nx + 1, ny + 1
+    band = 3 * (1 + NX + NX * NY) + 2
+    width = int(np.max(np.abs(rows - cols)))
+    assert width <= band
+    assert width > band - 3 * NX * NY
