@@ -350,8 +350,8 @@ def oracle_full_c2():
 def arm_config(args, world):
     """The workload both arms report (the reference arm times a bounded sample of it)."""
     return {"workload": WORKLOAD, "n_dof": 3 * 193 * 97 * 97, "states": args.states,
-            "step": (f"one Algorithm-1 pass of each of {args.states} states, solved together by "
-                     "gf_batch_select_floor (lockstep FGMRES, one CUDA graph per step)"),
+            "step": (f"one Algorithm-1 pass of each of {args.states} states, solved concurrently by "
+                     "gf_select_floor_many (one grid per state, each on its own stream and host thread)"),
             "parallelism": f"replicas x{world}",
             "l2": "inputs larger than L2 (Krylov bases V, Z = 2.66 GB per state solve)"}
 
@@ -405,6 +405,46 @@ def timed_kernel(fn, reps=20):
     k1.record()
     torch.cuda.synchronize()
     return k0.elapsed_time(k1) / reps / 1000.0
+
+
+def large_grids(gf, B):
+    """B 192x96x96 grids, each on its own stream, their tip loads and solution vectors."""
+    import torch
+    streams = [torch.cuda.Stream() for _ in range(B)]
+    grids = [gf.create_grid(*LARGE, levels=LEVELS, stream=st) for st in streams]
+    fs = [g.cantilever_load(torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")) for g in grids]
+    return grids, fs, [torch.zeros_like(f) for f in fs], streams
+
+
+def concurrent_passes(gf, grids, streams, rhos, fs, us, pol, steps):
+    """Algorithm-1 passes of all the states at once, `steps` times: each step sets every
+    grid's density (on its own stream) and runs gf_select_floor_many, one host thread per
+    grid. CUDA events on the current stream bracket every grid stream's work. (accepted, ms,
+    records, Arnoldi steps, FP64 K*u launches)."""
+    import torch
+    cur = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    acc, iters, recs, kus = 0, 0, [], 0
+    torch.cuda.synchronize()
+    e0.record(cur)
+    for st in streams:
+        st.wait_event(e0)
+    for _ in range(steps):
+        for g, rho in zip(grids, rhos):
+            g.set_density(rho, P_SIMP)
+        for out in gf.select_floor_many(grids, fs, us, pol):
+            acc += int(out["status"] == gf.GF_ACCEPTED)
+            iters += sum(a["iters"] for a in out["attempts"]) + (out["probe_iters_run"] if out["escalated"] else 0)
+            kus += sum(a["iters"] + 1 for a in out["attempts"])   # Arnoldi K*z, then the guard
+            recs.append((out["floor_index"], out["escalated"], [a["iters"] for a in out["attempts"]],
+                         [a["accepted"] for a in out["attempts"]]))
+    for st in streams:
+        ev = torch.cuda.Event()
+        ev.record(st)
+        cur.wait_event(ev)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    return acc, e0.elapsed_time(e1), recs, iters, kus
 
 
 def large_batch(gf, B):
@@ -564,10 +604,10 @@ def run_b300(args):
     t_inputs = time.perf_counter() - t0
     rhos = [torch.as_tensor(r, device="cuda") for r in rhos_h]
     B = args.states
-    b, fs = large_batch(gf, B)
+    grids, fs, us, streams = large_grids(gf, B)
     pol = pol_of(gf, gf.GF_MIXED, 0)
 
-    batched_passes(gf, b, rhos, fs, pol, args.warmup)
+    concurrent_passes(gf, grids, streams, rhos, fs, us, pol, args.warmup)
 
     def barrier():
         if dist is not None:
@@ -576,14 +616,26 @@ def run_b300(args):
 
     clock = ClockSampler(local)
     barrier()
-    launches0 = b.kernel_launches()
+    for g in grids:
+        g.reset_stats()
     clock.start()
-    accepted, ms, records, iters, kus = batched_passes(gf, b, rhos, fs, pol, args.steps)
+    accepted, ms, records, iters, kus = concurrent_passes(gf, grids, streams, rhos, fs, us, pol, args.steps)
     barrier()
     clocks = clock.stop()
-    (ms,), (accepted, launches) = over_ranks(dist, "cuda", [ms], [accepted, b.kernel_launches() - launches0])
+    launches = sum(g.stats()["kernel_launches"] for g in grids)
+    (ms,), (accepted, launches) = over_ranks(dist, "cuda", [ms], [accepted, launches])
     accepted, launches = int(accepted), int(launches)
     value = accepted / (ms / 1000.0)
+
+    # the same states in lockstep through the batch (gf_batch_select_floor)
+    b, fs_b = large_batch(gf, B)
+    batched_passes(gf, b, rhos, fs_b, pol, 2)
+    ab, msb, _, itb, _ = batched_passes(gf, b, rhos, fs_b, pol, args.steps)
+    lockstep = {"value": ab / (msb / 1000.0), "unit": UNIT, "steps": args.steps, "accepted": ab,
+                "ms_per_step": msb / args.steps, "fgmres_iters_per_step": itb / args.steps,
+                "form": (f"the {B} states in lockstep through the batch (gf_batch_select_floor, one CUDA graph per "
+                         "FGMRES step)")}
+    b.close()
 
     # the same passes one state at a time through one grid (gf_select_floor)
     g = gf.create_grid(*LARGE, levels=LEVELS)
@@ -648,7 +700,7 @@ def run_b300(args):
     roofline = dict(native)
     roofline["other_kernels"] = {"vcycle_stencil_fp32": stencil, "split_operator": split}
 
-    extras = {"single_state_192x96x96": single}
+    extras = {"single_state_192x96x96": single, "batched_lockstep_192x96x96": lockstep}
     if not args.no_extras:
         # the FP64-class Krylov form on the same states (split-integer operator, double-float CGS2)
         single_state_passes(gf, g, rhos, f, u, pol_of(gf, gf.GF_MIXED, 2), 1)
@@ -687,12 +739,12 @@ def run_b300(args):
         batch = comparison_102(gf, dist)
 
     # ---- end to end through the public API with host buffers (pinned), 192x96x96: the
-    # batched passes, every state's density and load uploaded and its solution read back
+    # concurrent passes, every state's density and load uploaded and its solution read back
     e2e = None
     if not args.no_e2e:
         rho_pin = [torch.as_tensor(r).pin_memory() for r in rhos_h]
         f_pin = fs[0].cpu().pin_memory()
-        n_dof, n_elem = b.n_dof[0], b.n_elem[0]
+        n_dof, n_elem = grids[0].n_dof, grids[0].n_elem
         # double-buffered device inputs and solutions: step s+1's inputs go up and step s's
         # solutions come back on a copy stream while the neighbouring step solves
         rho_d = [[torch.empty(n_elem, dtype=torch.float64, device="cuda") for _ in range(B)] for _ in range(2)]
@@ -721,11 +773,10 @@ def run_b300(args):
                 fetched[s % 2].synchronize()         # step s-2's solutions have left u_d[s % 2]
             if s + 1 < args.steps:
                 ready = upload(s + 1)                # overlaps step s's solve
-            for i in range(B):
-                b.set_state(i, rho_d[s % 2][i], f_d[s % 2][i], P_SIMP)
-            outs = b.select_floor(pol)               # returns once every state is done
-            for i in range(B):
-                b.solution(i, u_d[s % 2][i])
+            for i, gr in enumerate(grids):
+                gr.set_density(rho_d[s % 2][i], P_SIMP)
+            # returns once every grid's pass is done (each grid synchronises its stream)
+            outs = gf.select_floor_many(grids, f_d[s % 2], u_d[s % 2], pol)
             with torch.cuda.stream(copy_stream):     # overlaps step s+1's solve
                 for i in range(B):
                     u_pin[s % 2][i].copy_(u_d[s % 2][i], non_blocking=True)
@@ -742,7 +793,8 @@ def run_b300(args):
                "note": ("pinned host buffers; every step uploads each state's density and load and reads back "
                         "its solution; step s+1's uploads and step s's downloads run on a copy stream during "
                         "the neighbouring solves (double-buffered device inputs and solutions)")}
-    b.close()
+    for gr in grids:
+        gr.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -330,6 +330,18 @@ int gf_true_residual(gf_grid* g, const double* f, const double* u, double* eta);
 int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol,
                     gf_select_info* info);
 
+/* Algorithm 1 on n frozen states at once, one grid each: one host thread per grid runs
+ * gf_select_floor(grids[i], f[i], u[i], pol, &info[i]) (host arrays of n device
+ * pointers; info a host array of n). Grids created on distinct streams run concurrently
+ * on the device, each state's work in order on its own stream, so one state's
+ * latency-bound phases (coarse V-cycle levels, small reductions, the early launches of
+ * the coarsest inverse) fill the SMs another state's leaves idle. The grids must be
+ * distinct (GF_ERR_ARG otherwise) and each must have its density set. Returns GF_OK, or
+ * the lowest-index failing grid's status with its message in gf_last_error; the other
+ * grids' results are still written. Blocks until every grid is done. */
+int gf_select_floor_many(int n, gf_grid* const* grids, const double* const* f, double* const* u,
+                         const gf_policy* pol, gf_select_info* info);
+
 /* ---- floor-conditioning diagnostic (Sec. 4.1.3) ------------------------------ */
 
 /* Extreme eigenvalues of the free-DOF operator K(rho_min) of Eq. (frozen_operator) on a

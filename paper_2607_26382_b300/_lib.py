@@ -32,7 +32,7 @@ ERRORS = {-1: "GF_ERR_ARG", -2: "GF_ERR_OOM", -3: "GF_ERR_CUDA", -4: "GF_ERR_NON
 EXPORTED = [
     "gf_create_grid", "gf_destroy_grid", "gf_grid_sizes", "gf_set_density", "gf_set_floor",
     "gf_cantilever_load", "gf_free_mask", "gf_apply_K", "gf_apply_K_f32", "gf_vcycle", "gf_vcycle_ex", "gf_chebyshev_lambda", "gf_conditioning", "gf_conditioning_screen", "gf_solve",
-    "gf_true_residual", "gf_select_floor", "gf_policy_defaults", "gf_trigger_rule",
+    "gf_true_residual", "gf_select_floor", "gf_select_floor_many", "gf_policy_defaults", "gf_trigger_rule",
     "gf_probe_features", "gf_sensitivity", "gf_get_stats", "gf_reset_stats", "gf_last_error",
     "gf_true_residual_noalloc", "gf_filter", "gf_filter_adjoint", "gf_oc_update", "gf_compliance",
     "gf_oc_iteration", "gf_create_batch", "gf_destroy_batch", "gf_batch_grid", "gf_batch_set_state",
@@ -120,6 +120,7 @@ def lib():
         "gf_solve": [P, P, P, POINTER(SolveOpts), POINTER(SolveInfo)],
         "gf_true_residual": [P, P, P, POINTER(c_double)],
         "gf_select_floor": [P, P, P, POINTER(Policy), POINTER(SelectInfo)],
+        "gf_select_floor_many": [c_int, POINTER(P), POINTER(P), POINTER(P), POINTER(Policy), POINTER(SelectInfo)],
         "gf_trigger_rule": [c_double, c_double, POINTER(Policy)],
         "gf_probe_features": [POINTER(c_double), c_int, POINTER(Policy), POINTER(c_double), POINTER(c_double)],
         "gf_sensitivity": [P, P, P],
@@ -643,6 +644,24 @@ def select_features(grid_handle, r50, r100):
     x = (c_double * 6)()
     _check(lib().gf_select_features(grid_handle, float(r50), float(r100), x))
     return [x[i] for i in range(6)]
+
+
+def select_floor_many(grids, fs, us, policy: Policy):
+    """gf_select_floor_many: Algorithm 1 on several grids at once, one host thread per grid
+    (grids created on distinct streams run concurrently); a list of result dicts."""
+    t = _torch().float64
+    n = len(grids)
+    if not (len(fs) == len(us) == n):
+        raise ValueError("one f and one u per grid")
+    hs = (c_void_p * n)(*[g._h for g in grids])
+    fp = (c_void_p * n)(*[_ptr(f, t, g.n_dof, "f") for g, f in zip(grids, fs)])
+    up = (c_void_p * n)(*[_ptr(u, t, g.n_dof, "u") for g, u in zip(grids, us)])
+    infos = (SelectInfo * n)()
+    _check(lib().gf_select_floor_many(n, hs, fp, up, ctypes.byref(policy), infos))
+    for g, inf in zip(grids, infos):
+        if inf.status == GF_ACCEPTED:
+            g.rho_min = inf.rho_min
+    return [_select_dict(infos[i]) for i in range(n)]
 
 
 def create_grid(nx, ny, nz, h=1.0, E0=1.0, nu=0.3, levels=3, stream=None) -> Grid:

@@ -33,6 +33,7 @@
 #include <utility>
 #include <mutex>
 #include <functional>
+#include <thread>
 
 namespace {
 
@@ -2725,6 +2726,30 @@ int gf_select_floor(gf_grid* g, const double* f, double* u, const gf_policy* pol
             break;
         }
     }
+    return GF_OK;
+}
+
+int gf_select_floor_many(int n, gf_grid* const* grids, const double* const* f, double* const* u,
+                         const gf_policy* pol, gf_select_info* info)
+{
+    if (n < 0 || (n > 0 && (!grids || !f || !u || !pol || !info))) return set_err(GF_ERR_ARG, "null pointer / n < 0");
+    for (int i = 0; i < n; ++i) {
+        RET(check_grid(grids[i]));
+        for (int k = 0; k < i; ++k)
+            if (grids[k] == grids[i]) return set_err(GF_ERR_ARG, "the same grid twice");
+    }
+    std::vector<int> rc(n, GF_OK);
+    std::vector<std::string> msg(n);
+    std::vector<std::thread> workers;
+    workers.reserve(n);
+    for (int i = 0; i < n; ++i)
+        workers.emplace_back([&, i] {
+            rc[i] = gf_select_floor(grids[i], f[i], u[i], pol, &info[i]);
+            if (rc[i] != GF_OK) msg[i] = g_err;   // the worker's thread-local message
+        });
+    for (std::thread& t : workers) t.join();
+    for (int i = 0; i < n; ++i)
+        if (rc[i] != GF_OK) return set_err(rc[i], "grid " + std::to_string(i) + ": " + msg[i]);
     return GF_OK;
 }
 

@@ -152,3 +152,37 @@ def test_batch_cantilever_load_matches_grid_and_oracle(gf):
         assert np.array_equal(fb.cpu().numpy(), O.cantilever_load(O.Mesh(*d)))
         g.close()
     b.close()
+
+
+def test_select_floor_many_matches_each_grid_alone(gf):
+    # gf_select_floor_many runs one host thread per grid; grids on distinct streams run
+    # concurrently, and every state's result is bit-identical to its grid run alone
+    pol = gf.policy_defaults(rho0=1e-6, ladder=[1e-5, 1e-4, 1e-3], tau=1e-6, kmax=200, probe_iters=100,
+                             solve_prec=gf.GF_MIXED, solve_outer=0)
+
+    def grids_for(streams):
+        gs, fs = [], []
+        for (dims, kind, seed, q), st in zip(STATES[:3], streams):
+            g = gf.create_grid(*dims, levels=3, stream=st)
+            g.set_density(dev(_rho(dims, kind, seed, q)), 3.0)
+            fs.append(g.cantilever_load(torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")))
+            gs.append(g)
+        return gs, fs
+
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    alone, u_alone = [], []
+    gs, fs = grids_for(streams)
+    for g, f in zip(gs, fs):
+        u = torch.zeros_like(f)
+        alone.append(g.select_floor(f, u, pol))
+        u_alone.append(u)
+    gs2, fs2 = grids_for(streams)
+    us2 = [torch.zeros_like(f) for f in fs2]
+    many = gf.select_floor_many(gs2, fs2, us2, pol)
+    torch.cuda.synchronize()
+    for a, b, ua, ub in zip(alone, many, u_alone, us2):
+        assert a == b and torch.equal(ua, ub) and b["status"] == gf.GF_ACCEPTED
+    with pytest.raises(gf.GFError):
+        gf.select_floor_many([gs2[0], gs2[0]], [fs2[0], fs2[0]], [us2[0], torch.zeros_like(us2[0])], pol)
+    for g in gs + gs2:
+        g.close()
