@@ -136,9 +136,12 @@ struct gf_grid {
     gf::ModalCoef Kmodal;             // K0 in the sum/difference basis (apply_modal_kernel)
     gf::ModalCoefF Kmodal32;          // the same in FP32 with K0's node blocks (modal_stencil_f32_kernel)
     bool modal_f32 = true;            // level-0 FP32 stencils in the modal basis (GF_MODAL_F32=0: node stencils)
-    int4* modal_items = nullptr;      // work items of the modal FP64 K*u (device; null: dense stencil)
-    double* modal_es = nullptr;       // its elements' scaled coefficients E_e C, 9 x nel (modal_scale_kernel)
+    int4* modal_items = nullptr;      // work items of the modal FP32 fine level (tiles overlapping by one column)
     int modal_n = 0, modal_bx = 32;   // item count; CTA tile 32 x 16 or 16 x 32 element columns
+    int4* modal64_items = nullptr;    // work items of the modal FP64 K*u (tiles apart; device; null: dense stencil)
+    int modal64_n = 0, modal64_bx = 32;
+    double* modal_side = nullptr;     // its side buffer: corner forces at the nodes on tile boundaries
+    double* modal_es = nullptr;       // its elements' scaled coefficients E_e C, 9 x nel (modal_scale_kernel)
     bool sym_gj = true;               // coarsest inverse by the blocked symmetric sweep (GF_SYM_GJ=0: two-pivot form)
     int geom = GF_GEOM_CANTILEVER;    // supports: the clamped face x = 0, or the bridge's (gf_set_geometry)
     gf::K0Param<float> K0f;
@@ -1014,22 +1017,33 @@ int coarse_correct(gf_grid* g, int l, T* x, const T* xc, T* c, const T* r, doubl
 int applyK64(gf_grid* g, const double* u, double* y, const int* halt)
 {
     g->stats.apply_K_fp64++;
-    if (g->modal_items) {   // modal factorisation of K0 (default; GF_MODAL=0: dense node stencil)
+    if (g->modal64_items) {   // modal factorisation of K0 (default; GF_MODAL=0: dense node stencil)
         const bool mk = g->lv[0].fix != nullptr;   // per-node fixed components (bridge supports)
         const double* Es = g->modal_es;
-        const int4* it = g->modal_items;
-        if (g->modal_bx == 32 && mk)
-            RET((launch_modal<double, 32, 16, gf::apply_modal_kernel<32, 16, true>>(g, g->modal_n, u, y, Es,
-                                                                                   g->lv[0].dims(), it, halt)));
-        else if (g->modal_bx == 32)
-            RET((launch_modal<double, 32, 16, gf::apply_modal_kernel<32, 16, false>>(g, g->modal_n, u, y, Es,
-                                                                                    g->lv[0].dims(), it, halt)));
+        const int4* it = g->modal64_items;
+        const gf::GridDims d = g->lv[0].dims();
+        const int bx = g->modal64_bx;
+        const gf::ModalSide sd = gf::modal_side(d, bx, gf::MODAL_THREADS / bx);
+        double* side = g->modal_side;
+        if (bx == 32 && mk)
+            RET((launch_modal<double, 32, 16, gf::apply_modal_kernel<32, 16, true>>(g, g->modal64_n, u, y, Es, d, it,
+                                                                                   side, sd, halt)));
+        else if (bx == 32)
+            RET((launch_modal<double, 32, 16, gf::apply_modal_kernel<32, 16, false>>(g, g->modal64_n, u, y, Es, d, it,
+                                                                                    side, sd, halt)));
         else if (mk)
-            RET((launch_modal<double, 16, 32, gf::apply_modal_kernel<16, 32, true>>(g, g->modal_n, u, y, Es,
-                                                                                   g->lv[0].dims(), it, halt)));
+            RET((launch_modal<double, 16, 32, gf::apply_modal_kernel<16, 32, true>>(g, g->modal64_n, u, y, Es, d, it,
+                                                                                   side, sd, halt)));
         else
-            RET((launch_modal<double, 16, 32, gf::apply_modal_kernel<16, 32, false>>(g, g->modal_n, u, y, Es,
-                                                                                    g->lv[0].dims(), it, halt)));
+            RET((launch_modal<double, 16, 32, gf::apply_modal_kernel<16, 32, false>>(g, g->modal64_n, u, y, Es, d, it,
+                                                                                    side, sd, halt)));
+        const long long ne = sd.entries(d);
+        if (mk)
+            LAUNCH(g, (unsigned)((ne + 255) / 256), 256, gf::modal_fixup_kernel<true>, (const double*)side, sd, y, d,
+                   halt);
+        else
+            LAUNCH(g, (unsigned)((ne + 255) / 256), 256, gf::modal_fixup_kernel<false>, (const double*)side, sd, y, d,
+                   halt);
         return GF_OK;
     }
     return stencil<double, double, gf::ST_APPLY>(g, 0, u, nullptr, y, g->lv[0].E64, g->K0d, 0.0, halt);
@@ -1862,19 +1876,26 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
             const char* ch = getenv("GF_MODAL_CHUNK");
             const char* bxs = getenv("GF_MODAL_BX");
             const int forced = ch ? std::max(0, atoi(ch)) : 0;
-            double c32 = 0, c16 = 0;
-            std::vector<int4> i32 = gf::modal_plan(nx, ny, nz, 32, 16, g->sms * per_sm, forced, &c32);
-            std::vector<int4> i16 = gf::modal_plan(nx, ny, nz, 16, 32, g->sms * per_sm, forced, &c16);
-            const bool use32 = bxs ? atoi(bxs) == 32 : c32 <= c16;
-            const std::vector<int4>& items = use32 ? i32 : i16;
-            g->modal_bx = use32 ? 32 : 16;
-            g->modal_n = (int)items.size();
-            if (alloc((void**)&g->modal_items, sizeof(int4) * items.size()) != GF_OK ||
-                alloc((void**)&g->modal_es, sizeof(double) * 9 * (size_t)g->nel) != GF_OK)
+            // the FP32 fine level's plan (tiles overlapping by one column) and the FP64 K*u's
+            // (tiles apart), each over both tile shapes by the cost model
+            for (int halo = 1; halo >= 0; --halo) {
+                double c32 = 0, c16 = 0;
+                std::vector<int4> i32 = gf::modal_plan(nx, ny, nz, 32, 16, g->sms * per_sm, forced, &c32, halo);
+                std::vector<int4> i16 = gf::modal_plan(nx, ny, nz, 16, 32, g->sms * per_sm, forced, &c16, halo);
+                const bool use32 = bxs ? atoi(bxs) == 32 : c32 <= c16;
+                const std::vector<int4>& items = use32 ? i32 : i16;
+                int4** dst = halo ? &g->modal_items : &g->modal64_items;
+                (halo ? g->modal_bx : g->modal64_bx) = use32 ? 32 : 16;
+                (halo ? g->modal_n : g->modal64_n) = (int)items.size();
+                if (alloc((void**)dst, sizeof(int4) * items.size()) != GF_OK) return fail(GF_ERR_OOM);
+                if (cudaMemcpy(*dst, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                    return fail(set_err(GF_ERR_CUDA, "modal work items"));
+            }
+            const gf::GridDims d0{nx, ny, nz, nullptr};   // the fine level (the levels come later)
+            const long long side = std::max(gf::modal_side(d0, 32, 16).entries(d0), gf::modal_side(d0, 16, 32).entries(d0));
+            if (alloc((void**)&g->modal_es, sizeof(double) * 9 * (size_t)g->nel) != GF_OK ||
+                alloc((void**)&g->modal_side, sizeof(double) * 12 * (size_t)side) != GF_OK)
                 return fail(GF_ERR_OOM);
-            if (cudaMemcpy(g->modal_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) !=
-                cudaSuccess)
-                return fail(set_err(GF_ERR_CUDA, "modal work items"));
         }
     }
     for (int a = 0; a < 8; ++a)
@@ -2033,7 +2054,7 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         g->use_graphs = !(e && e[0] == '0');
     }
     if ((r = build_coarse_map(g)) != GF_OK) return fail(r);
-    if (g->modal_items && !getenv("GF_MODAL_CHUNK") && !getenv("GF_MODAL_BX"))
+    if (g->modal64_items && !getenv("GF_MODAL_CHUNK") && !getenv("GF_MODAL_BX"))
         if ((r = modal_autotune(g)) != GF_OK) return fail(r);
     *out = g;
     return GF_OK;
@@ -2041,16 +2062,22 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
 
 }  // extern "C"
 namespace {
-// Time the modal FP64 K*u under a few launch plans -- the cheapest ones by modal_plan's
-// cost model over both tile shapes and several run lengths -- and keep the fastest. The
-// plan changes which CTA computes what, never the arithmetic of a node, so K*u does not
-// depend on it. Runs once per grid, on zeroed level-0 scratch, on the grid's stream.
+// Time the modal kernels under a few launch plans -- the cheapest ones by modal_plan's
+// cost model over both tile shapes and several run lengths -- and keep the fastest: the
+// FP64 K*u (tiles apart, with its boundary fix-up) and the FP32 fine-level operator
+// (tiles overlapping by one column). The plan changes which CTA computes what, never the
+// arithmetic of a node, so neither result depends on it. Runs once per grid, on zeroed
+// level-0 scratch, on the grid's stream.
 int modal_autotune(gf_grid* g)
 {
     int per_sm = 0;
     if (!smem_opt_in<gf::apply_modal_kernel<32, 16, false>>(gf::modal_smem_bytes<double, 32, 16>()) ||
-        !smem_opt_in<gf::apply_modal_kernel<16, 32, false>>(gf::modal_smem_bytes<double, 16, 32>()))
-        return set_err(GF_ERR_CUDA, "shared memory of the modal kernel");
+        !smem_opt_in<gf::apply_modal_kernel<16, 32, false>>(gf::modal_smem_bytes<double, 16, 32>()) ||
+        !smem_opt_in<gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 32, 16>>(
+            gf::modal_smem_bytes<float, 32, 16>()) ||
+        !smem_opt_in<gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 16, 32>>(
+            gf::modal_smem_bytes<float, 16, 32>()))
+        return set_err(GF_ERR_CUDA, "shared memory of the modal kernels");
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gf::apply_modal_kernel<32, 16>, gf::MODAL_THREADS,
                                                       gf::modal_smem_bytes<double, 32, 16>()) != cudaSuccess ||
         per_sm < 1)
@@ -2060,74 +2087,99 @@ int modal_autotune(gf_grid* g)
         double cost;
         std::vector<int4> items;
     };
-    std::vector<Cand> cand;
-    const int NZ = g->nz + 1;
-    for (int bx : {32, 16})
-        for (int L : {0, 2, 3, 4, 6, 8, 12, 16, 24, 33, 48, 64}) {
-            if (L > NZ) continue;
-            Cand c{bx, 0.0, {}};
-            c.items = gf::modal_plan(g->nx, g->ny, g->nz, bx, gf::MODAL_THREADS / bx, g->sms * per_sm, L, &c.cost);
-            cand.push_back(std::move(c));
-        }
-    std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.cost < b.cost; });
-    if (cand.size() > 6) cand.resize(6);
-    size_t maxn = 0;
-    for (const Cand& c : cand) maxn = std::max(maxn, c.items.size());
-    int4* dev = nullptr;
-    RET(alloc((void**)&dev, sizeof(int4) * maxn));
     Level& f = g->lv[0];
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    int rc = GF_OK;
-    float best = 1e30f;
-    int best_i = -1;
-    auto run = [&](const Cand& c) {
-        if (c.bx == 32)
-            gf::apply_modal_kernel<32, 16><<<(unsigned)c.items.size(), dim3(32, 16),
-                                             gf::modal_smem_bytes<double, 32, 16>(), g->stream>>>(
-                f.x64, f.t64, g->modal_es, f.dims(), dev, nullptr);
-        else
-            gf::apply_modal_kernel<16, 32><<<(unsigned)c.items.size(), dim3(16, 32),
-                                             gf::modal_smem_bytes<double, 16, 32>(), g->stream>>>(
-                f.x64, f.t64, g->modal_es, f.dims(), dev, nullptr);
-    };
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
-        cudaMemsetAsync(g->modal_es, 0, sizeof(double) * 9 * f.nel, g->stream) != cudaSuccess ||
-        cudaMemsetAsync(f.x64, 0, sizeof(double) * f.ndof, g->stream) != cudaSuccess)
-        rc = set_err(GF_ERR_CUDA, "modal autotune set-up");
-    for (size_t i = 0; rc == GF_OK && i < cand.size(); ++i) {
-        const Cand& c = cand[i];
-        if (cudaMemcpyAsync(dev, c.items.data(), sizeof(int4) * c.items.size(), cudaMemcpyHostToDevice, g->stream) !=
-            cudaSuccess) {
-            rc = set_err(GF_ERR_CUDA, "modal autotune items");
-            break;
+    const gf::GridDims d = f.dims();
+    const int NZ = g->nz + 1;
+    if (cudaMemsetAsync(g->modal_es, 0, sizeof(double) * 9 * f.nel, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(f.x64, 0, sizeof(double) * f.ndof, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(f.x32, 0, sizeof(float) * f.ndof, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(f.b32, 0, sizeof(float) * f.ndof, g->stream) != cudaSuccess ||
+        cudaMemsetAsync(f.E32, 0, sizeof(float) * f.nel, g->stream) != cudaSuccess)
+        return set_err(GF_ERR_CUDA, "modal autotune set-up");
+    for (int halo = 0; halo <= 1; ++halo) {
+        if (halo && !g->modal_f32) break;
+        std::vector<Cand> cand;
+        for (int bx : {32, 16})
+            for (int L : {0, 2, 3, 4, 6, 8, 12, 16, 24, 33, 48, 64}) {
+                if (L > NZ) continue;
+                Cand c{bx, 0.0, {}};
+                c.items = gf::modal_plan(g->nx, g->ny, g->nz, bx, gf::MODAL_THREADS / bx, g->sms * per_sm, L, &c.cost,
+                                         halo);
+                cand.push_back(std::move(c));
+            }
+        std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.cost < b.cost; });
+        if (cand.size() > 6) cand.resize(6);
+        size_t maxn = 0;
+        for (const Cand& c : cand) maxn = std::max(maxn, c.items.size());
+        int4* dev = nullptr;
+        RET(alloc((void**)&dev, sizeof(int4) * maxn));
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        int rc = GF_OK;
+        float best = 1e30f;
+        int best_i = -1;
+        auto run = [&](const Cand& c) {
+            const unsigned n = (unsigned)c.items.size();
+            if (!halo) {
+                const gf::ModalSide sd = gf::modal_side(d, c.bx, gf::MODAL_THREADS / c.bx);
+                if (c.bx == 32)
+                    gf::apply_modal_kernel<32, 16><<<n, dim3(32, 16), gf::modal_smem_bytes<double, 32, 16>(),
+                                                     g->stream>>>(f.x64, f.t64, g->modal_es, d, dev, g->modal_side,
+                                                                  sd, nullptr);
+                else
+                    gf::apply_modal_kernel<16, 32><<<n, dim3(16, 32), gf::modal_smem_bytes<double, 16, 32>(),
+                                                     g->stream>>>(f.x64, f.t64, g->modal_es, d, dev, g->modal_side,
+                                                                  sd, nullptr);
+                const long long ne = sd.entries(d);
+                gf::modal_fixup_kernel<false><<<(unsigned)((ne + 255) / 256), 256, 0, g->stream>>>(
+                    g->modal_side, sd, f.t64, d, nullptr);
+            } else if (c.bx == 32) {
+                gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 32, 16>
+                    <<<n, dim3(32, 16), gf::modal_smem_bytes<float, 32, 16>(), g->stream>>>(
+                        f.x32, (const float*)f.b32, f.t32, f.E32, d, g->Kmodal32, 0.6f, dev, nullptr);
+            } else {
+                gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 16, 32>
+                    <<<n, dim3(16, 32), gf::modal_smem_bytes<float, 16, 32>(), g->stream>>>(
+                        f.x32, (const float*)f.b32, f.t32, f.E32, d, g->Kmodal32, 0.6f, dev, nullptr);
+            }
+        };
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+            rc = set_err(GF_ERR_CUDA, "modal autotune events");
+        for (size_t i = 0; rc == GF_OK && i < cand.size(); ++i) {
+            const Cand& c = cand[i];
+            if (cudaMemcpyAsync(dev, c.items.data(), sizeof(int4) * c.items.size(), cudaMemcpyHostToDevice,
+                                g->stream) != cudaSuccess) {
+                rc = set_err(GF_ERR_CUDA, "modal autotune items");
+                break;
+            }
+            run(c);
+            cudaEventRecord(e0, g->stream);
+            for (int r = 0; r < 3; ++r) run(c);
+            cudaEventRecord(e1, g->stream);
+            float ms = 0.0f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+                cudaGetLastError() != cudaSuccess) {
+                rc = set_err(GF_ERR_CUDA, "modal autotune launch");
+                break;
+            }
+            if (ms < best) {
+                best = ms;
+                best_i = (int)i;
+            }
         }
-        run(c);
-        cudaEventRecord(e0, g->stream);
-        for (int r = 0; r < 3; ++r) run(c);
-        cudaEventRecord(e1, g->stream);
-        float ms = 0.0f;
-        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
-            cudaGetLastError() != cudaSuccess) {
-            rc = set_err(GF_ERR_CUDA, "modal autotune launch");
-            break;
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(dev);
+        RET(rc);
+        if (best_i >= 0) {
+            const Cand& c = cand[best_i];
+            int4** dst = halo ? &g->modal_items : &g->modal64_items;
+            cudaFree(*dst);
+            *dst = nullptr;
+            RET(alloc((void**)dst, sizeof(int4) * c.items.size()));
+            CK(cudaMemcpy(*dst, c.items.data(), sizeof(int4) * c.items.size(), cudaMemcpyHostToDevice));
+            (halo ? g->modal_n : g->modal64_n) = (int)c.items.size();
+            (halo ? g->modal_bx : g->modal64_bx) = c.bx;
         }
-        if (ms < best) {
-            best = ms;
-            best_i = (int)i;
-        }
-    }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    cudaFree(dev);
-    RET(rc);
-    if (best_i >= 0) {
-        const Cand& c = cand[best_i];
-        cudaFree(g->modal_items);
-        g->modal_items = nullptr;
-        RET(alloc((void**)&g->modal_items, sizeof(int4) * c.items.size()));
-        CK(cudaMemcpy(g->modal_items, c.items.data(), sizeof(int4) * c.items.size(), cudaMemcpyHostToDevice));
-        g->modal_n = (int)c.items.size();
-        g->modal_bx = c.bx;
     }
     return GF_OK;
 }
@@ -2159,6 +2211,8 @@ int gf_destroy_grid(gf_grid* g)
     cudaFree(g->lzv);
     cudaFree(g->Edf);
     cudaFree(g->modal_items);
+    cudaFree(g->modal64_items);
+    cudaFree(g->modal_side);
     cudaFree(g->modal_es);
     cudaFree(g->B3);
     cudaFree(g->Btc);

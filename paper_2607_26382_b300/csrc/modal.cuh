@@ -25,14 +25,18 @@
 // product. B300 issues FP64 at 1/64 of the FP32 rate, so
 // this count, not memory, bounds the kernel.
 //
-// Layout of the work: a CTA owns BX x BY element columns (a tile plus a one-element
-// halo on the low x and y sides; 32 x 16 or 16 x 32, whichever wastes fewer warps on
-// the grid) and walks them up a run of node planes. At each
-// step every thread forms its element's forces, sums its bottom face with the top
-// face of the element below (carried in registers, in modal form), transforms the
-// face back to its four nodes and stores them in shared memory; after a barrier each
-// node of the (BX-1) x (BY-1) output tile adds the four columns around it in a fixed
-// order. No atomics: the result does not depend on the launch shape.
+// Layout of the work: a CTA owns a tile of BX x BY element columns (32 x 16 or 16 x 32,
+// whichever wastes fewer warps on the grid; the tiles do not overlap) and walks them up
+// a run of node planes. At each step every thread forms its element's forces, sums its
+// bottom face with the top face of the element below (carried in registers, in modal
+// form), transforms the face back to its four nodes and stores them in shared memory;
+// after a barrier each of the (BX-1) x (BY-1) nodes inside the tile adds the four
+// columns around it in a fixed order. A node on a tile boundary has columns in two or
+// four tiles: each column writes its corner to that node's slot in a side buffer, and
+// modal_fixup_kernel adds the four slots in the same fixed order. No atomics: the result
+// does not depend on the launch shape. (The FP32 fine-level kernel below keeps tiles
+// that overlap by one element column on the low x and y sides and needs no side buffer:
+// its smoothing update of a node needs the node's complete residual.)
 #pragma once
 #include <cuda_runtime.h>
 #include <algorithm>
@@ -75,8 +79,11 @@ constexpr int modal_smem_bytes()
     return (int)(sizeof(T) * (2 * 12 + (sizeof(T) == 4 ? 3 : 0)) * BX * BY);
 }
 
-// Work items of apply_modal_kernel<BX, BY> for a grid of nx x ny x nz elements on `slots`
-// concurrent CTAs. A CTA step costs the busiest of the SM's four sub-partitions (warp w
+// Work items of the modal kernels for a grid of nx x ny x nz elements on `slots`
+// concurrent CTAs: x = tile column, y = tile row, [z, w) = node planes. halo = true:
+// tiles of (bx-1) x (by-1) output nodes whose bx x by element columns start one column
+// and one row below the tile (the FP32 kernel); halo = false: tiles of bx x by element
+// columns that do not overlap (apply_modal_kernel). A CTA step costs the busiest of the SM's four sub-partitions (warp w
 // runs on w mod 4), counting the warps that hold at least one element column inside
 // the grid (a warp issues its FP64 instructions for 32 lanes whatever its active mask):
 // far-edge tiles whose whole warps fall outside are cheaper and take longer runs of
@@ -85,10 +92,11 @@ constexpr int modal_smem_bytes()
 // waves x (largest item cost), with (planes + 1) steps per run. *cost receives that
 // product. Plain host arithmetic, deterministic.
 inline std::vector<int4> modal_plan(int nx, int ny, int nz, int bx, int by, int slots, int forced_planes,
-                                    double* cost)
+                                    double* cost, bool halo = true)
 {
     const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
-    const int tx = (NX + bx - 2) / (bx - 1), ty = (NY + by - 2) / (by - 1);
+    const int tx = halo ? (NX + bx - 2) / (bx - 1) : (nx + bx - 1) / bx;
+    const int ty = halo ? (NY + by - 2) / (by - 1) : (ny + by - 1) / by;
     std::vector<long long> v(tx * ty);
     for (int b = 0; b < ty; ++b)
         for (int a = 0; a < tx; ++a) {
@@ -96,7 +104,9 @@ inline std::vector<int4> modal_plan(int nx, int ny, int nz, int bx, int by, int 
             for (int w = 0; w < bx * by / 32; ++w) {
                 bool any = false;
                 for (int l = 0; l < 32 && !any; ++l) {
-                    const int t = 32 * w + l, ex = a * (bx - 1) - 1 + t % bx, ey = b * (by - 1) - 1 + t / bx;
+                    const int t = 32 * w + l;
+                    const int ex = halo ? a * (bx - 1) - 1 + t % bx : a * bx + t % bx;
+                    const int ey = halo ? b * (by - 1) - 1 + t / bx : b * by + t / bx;
                     any = ex >= 0 && ex < nx && ey >= 0 && ey < ny;
                 }
                 per_smsp[w % 4] += any;
@@ -195,14 +205,51 @@ __device__ __forceinline__ void face_inv(const T f[4], T v[4])
     v[3] = hi0 + hi1;
 }
 
-// One CTA per work item: node tile (x, y) of (BX-1) x (BY-1) nodes and node planes [z, w).
-// The host balances the items (modal_plan): tiles at the far edges of the grid hold fewer
-// element columns and take longer runs of planes, so that every CTA costs about the same.
+// Side buffer of apply_modal_kernel<BX, BY>: for every node on a tile boundary, the
+// corner forces of the four element columns around it, 12 doubles [slot q][component],
+// slot q = qx + 2 qy holding corner q of column (ni - qx, nj - qy). Nodes with ni a
+// multiple of BX come first ("x lines", (nz + 1) x (nx / BX + 1) x (ny + 1) of them),
+// then nodes with nj a multiple of BY ("y lines", (nz + 1) x (ny / BY + 1) x (nx + 1)
+// entries; those that also lie on an x line stay unused).
+struct ModalSide {
+    int bx, by, nxl, nyl;   // tile shape; x lines nx / bx + 1, y lines ny / by + 1
+    long long xn;           // entries of the x lines
+    __host__ __device__ long long entries(const GridDims& d) const
+    {
+        return xn + (long long)(d.nz + 1) * nyl * (d.nx + 1);
+    }
+    __host__ __device__ long long slot_x(const GridDims& d, int ix, int nj, int kz) const
+    {
+        return ((long long)kz * nxl + ix) * (d.ny + 1) + nj;
+    }
+    __host__ __device__ long long slot_y(const GridDims& d, int iy, int ni, int kz) const
+    {
+        return xn + ((long long)kz * nyl + iy) * (d.nx + 1) + ni;
+    }
+};
+
+__host__ inline ModalSide modal_side(const GridDims& d, int bx, int by)
+{
+    ModalSide m;
+    m.bx = bx;
+    m.by = by;
+    m.nxl = d.nx / bx + 1;
+    m.nyl = d.ny / by + 1;
+    m.xn = (long long)(d.nz + 1) * m.nxl * (d.ny + 1);
+    return m;
+}
+
+// One CTA per work item: element tile (x, y) of BX x BY columns and node planes [z, w).
+// The host balances the items (modal_plan, halo = false): tiles at the far edges of the
+// grid hold fewer element columns and take longer runs of planes, so that every CTA costs
+// about the same. Writes y at the nodes inside the tile and the side buffer for the
+// nodes on its boundary (modal_fixup_kernel completes those).
 // MASK: fixed components from d.fix (any supports); otherwise the clamped face x = 0.
 template <int BX, int BY, bool MASK = false>
 __global__ void __launch_bounds__(MODAL_THREADS, 1)
 apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const double* __restrict__ Es,
-                   GridDims d, const int4* __restrict__ items, const int* __restrict__ halt)
+                   GridDims d, const int4* __restrict__ items, double* __restrict__ side, ModalSide sd_,
+                   const int* __restrict__ halt)
 {
     if (halt != nullptr && *halt != 0) return;
     // two buffers of corner forces [corner * 3 + comp][column], by step parity (dynamic
@@ -212,12 +259,20 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
     const int4 it = items[blockIdx.x];
-    const int i0 = it.x * (BX - 1), j0 = it.y * (BY - 1);
+    const int i0 = it.x * BX, j0 = it.y * BY;
     const int k0 = it.z;
     const int k1 = min(NZ, it.w);
-    const int ex = i0 - 1 + tx, ey = j0 - 1 + ty;         // this thread's element column
-    const bool col = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
+    const int ex = i0 + tx, ey = j0 + ty;                 // this thread's element column
+    const bool col = ex < d.nx && ey < d.ny;
     const long long plane = (long long)NX * NY;
+    // corners of this column on the tile boundary (bit q: corner q = qx + 2 qy)
+    unsigned ring = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int lx = tx + (q & 1), ly = ty + (q >> 1);
+        if (lx == 0 || lx == BX || ly == 0 || ly == BY) ring |= 1u << q;
+    }
+    if (!col) ring = 0u;   // the fix-up reads a column outside the grid as zero
 
     // face transform of node plane kz for this column (zero outside the domain; the
     // clamped face x = 0 reads as 0)
@@ -276,7 +331,7 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
             for (int c = 0; c < 3; ++c) {
                 double G[8];
 #pragma unroll
-                for (int beta = 0; beta < 8; ++beta) {
+                for (int beta = 1; beta < 8; ++beta) {
                     const int bc = (beta >> c) & 1;
                     const int n = ((beta >> ((c + 1) % 3)) & 1) + ((beta >> ((c + 2) % 3)) & 1);
                     double t = (bc == 0 && n == 0) ? 0.0 : sd[bc * 3 + n] * m[c][beta];
@@ -294,8 +349,11 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
                     G[beta] = t;
                 }
                 // z stage of the transposed network: bottom face G0 - G1, top face G0 + G1
+                // (the constant mode beta = 0 carries no force: a rigid translation)
+                face[c][0] = carry[c][0] - G[4];
+                carry[c][0] = G[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 1; q < 4; ++q) {
                     face[c][q] = carry[c][q] + (G[q] - G[q + 4]);
                     carry[c][q] = G[q] + G[q + 4];
                 }
@@ -313,22 +371,34 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
         // this parity was last read by the gather two steps back, which every thread
         // finished before the previous step's barrier)
         double(*part)[BY][BX] = partb[(ez - k0 + 1) & 1];
+        const bool out = ez >= k0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             double v[4];
             face_inv<double>(face[c], v);
 #pragma unroll
             for (int q = 0; q < 4; ++q) part[q * 3 + c][ty][tx] = v[q];
+            if (out && ring) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (!((ring >> q) & 1u)) continue;
+                    const int lx = tx + (q & 1), ly = ty + (q >> 1);
+                    const long long sl = (lx == 0 || lx == BX)
+                                             ? sd_.slot_x(d, it.x + (lx == BX ? 1 : 0), ey + (q >> 1), ez)
+                                             : sd_.slot_y(d, it.y + (ly == BY ? 1 : 0), ex + (q & 1), ez);
+                    side[sl * 12 + q * 3 + c] = v[q];
+                }
+            }
         }
         __syncthreads();
-        const int ni = i0 + tx, nj = j0 + ty;
-        if (ez >= k0 && tx < BX - 1 && ty < BY - 1 && ni < NX && nj < NY) {
+        const int ni = i0 + tx + 1, nj = j0 + ty + 1;   // the node inside the tile at this column's corner 3
+        if (out && tx < BX - 1 && ty < BY - 1 && ni < NX && nj < NY) {
             const long long n = ni + (long long)NX * nj + plane * ez;
             const unsigned ob = MASK ? (unsigned)__ldg(d.fix + n) : (ni == 0 ? 7u : 0u);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                // node (ni, nj) is corner (1,1) of column (tx, ty), (0,1) of (tx+1, ty),
-                // (1,0) of (tx, ty+1) and (0,0) of (tx+1, ty+1)
+                // node (ni, nj) is corner 3 (1,1) of column (tx, ty), 2 (0,1) of (tx+1, ty),
+                // 1 (1,0) of (tx, ty+1) and 0 (0,0) of (tx+1, ty+1)
                 double acc = part[3 * 3 + c][ty][tx] + part[2 * 3 + c][ty][tx + 1];
                 acc += part[1 * 3 + c][ty + 1][tx];
                 acc += part[0 * 3 + c][ty + 1][tx + 1];
@@ -342,9 +412,57 @@ apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const d
     }
 }
 
+// The nodes on tile boundaries: the four corner forces from the side buffer, added in the
+// order of the gather inside a tile (columns outside the grid read as zero there too), so
+// every node of K*u has the same arithmetic wherever the tiles fall. One thread per
+// side-buffer entry.
+template <bool MASK = false>
+__global__ void modal_fixup_kernel(const double* __restrict__ side, ModalSide sd_, double* __restrict__ y,
+                                   GridDims d, const int* __restrict__ halt)
+{
+    if (halt != nullptr && *halt != 0) return;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int NX = d.nx + 1, NY = d.ny + 1;
+    if (t >= sd_.entries(d)) return;
+    int ni, nj, kz;
+    if (t < sd_.xn) {
+        nj = (int)(t % NY);
+        const long long r = t / NY;
+        ni = (int)(r % sd_.nxl) * sd_.bx;
+        kz = (int)(r / sd_.nxl);
+    } else {
+        const long long u = t - sd_.xn;
+        ni = (int)(u % NX);
+        const long long r = u / NX;
+        nj = (int)(r % sd_.nyl) * sd_.by;
+        kz = (int)(r / sd_.nyl);
+        if (ni % sd_.bx == 0) return;   // on an x line: its entry is there
+    }
+    if (ni >= NX || nj >= NY) return;
+    const long long n = ni + (long long)NX * nj + (long long)NX * NY * kz;
+    const unsigned ob = MASK ? (unsigned)__ldg(d.fix + n) : (ni == 0 ? 7u : 0u);
+    bool in[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int ex = ni - (q & 1), ey = nj - (q >> 1);
+        in[q] = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
+    }
+    const double* s = side + t * 12;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double p3 = in[3] ? s[9 + c] : 0.0, p2 = in[2] ? s[6 + c] : 0.0;
+        const double p1 = in[1] ? s[3 + c] : 0.0, p0 = in[0] ? s[c] : 0.0;
+        double acc = p3 + p2;
+        acc += p1;
+        acc += p0;
+        y[3 * n + c] = ((ob >> c) & 1u) ? 0.0 : acc;
+    }
+}
+
 // ---- the FP32 V-cycle's fine-level operator in the same basis ------------------------
 // The level-0 smoothing sweeps and residual of the mixed V-cycle (and the FP32 K*u) with
-// the modal K0 in FP32: the column walk of apply_modal_kernel (same plan), with the next
+// the modal K0 in FP32: the column walk of apply_modal_kernel (on tiles that overlap by one
+// element column, modal_plan with halo = true, so no side buffer), with the next
 // node plane's values and element modulus loaded one step ahead, and at the gather each
 // node also sums its 3x3 diagonal block from the moduli of its eight elements (kept in
 // shared memory for the current and the previous element layer) for the damped
