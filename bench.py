@@ -214,7 +214,7 @@ def profiled_traffic(profile, source, start, end):
 # kernel text spans hashed for the traffic figures
 FP64_KU_SPAN = ("stencil.cuh", "// (i, j, k) of node n", "// First smoothing sweep")
 MODAL_SPAN = ("modal.cuh", "// 2D sum/difference transform", "}  // namespace gf")
-MODAL_INSTR, MODAL_FLOPS = 162, 186     # FP64 instructions and flops per element of the modal K*u
+MODAL_INSTR, MODAL_FLOPS = 153, 177     # FP64 instructions and flops per element of the modal K*u
 FP32_ST_SPAN = FP64_KU_SPAN                # both node-stencil bodies and their shared block update
 SPLIT_KU_SPAN = ("split_tc.cuh", "template <bool DD>", "}  // namespace gf")
 
@@ -662,10 +662,11 @@ def run_b300(args):
     fp64_peak = 148 * 2 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FMAs only
     fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12
     hbm = measured_peaks().get("hbm_gbs", 6400.0)
-    # the modal K*u executes MODAL_INSTR FP64 instructions per element (48 adds forward,
-    # 21 multiplies + 24 FMAs in modal space with the element's scaled coefficients, 60 adds
-    # back, 9 adds of the node gather) = MODAL_FLOPS flops; its ceiling is the FP64 issue
-    # rate (2 FP64 instructions per clock and SM) times this mix's flops per instruction
+    # the modal K*u executes MODAL_INSTR FP64 instructions per element (45 adds forward,
+    # 21 multiplies + 24 FMAs in modal space with the element's scaled coefficients, 54 adds
+    # back, 9 adds of the node gather; the constant mode carries no force) = MODAL_FLOPS
+    # flops; its ceiling is the FP64 issue rate (2 FP64 instructions per clock and SM) times
+    # this mix's flops per instruction. Timed: the kernel and its tile-boundary fix-up.
     modal_flops = MODAL_FLOPS * g.n_elem
     modal_peak = 148 * 2 * sm_max * 1e6 * (MODAL_FLOPS / MODAL_INSTR) / 1e12
     # share of the timed region spent in the native FP64 operator (Arnoldi K*z, cycle-start

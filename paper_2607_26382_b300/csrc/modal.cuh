@@ -17,13 +17,14 @@
 // (Checked numerically against the Gauss-integrated K0 on the host: both are the
 // exact integral, and they agree to rounding.)
 //
-// Cost per element: the sum/difference network forward (48 FP64 adds, a face of
-// the column's next node plane transformed once and reused by the element above),
-// 45 multiply-adds in modal space with the element's 9 coefficients E_e C (scaled once
-// per floor, modal_scale_kernel), the transposed network back (60), and the 9 adds of
-// the node gather -- 162 FP64 instructions against the 576 FMAs of the dense 24x24
-// product. B300 issues FP64 at 1/64 of the FP32 rate, so
-// this count, not memory, bounds the kernel.
+// Cost per element: the sum/difference network forward (45 FP64 adds, a face of
+// the column's next node plane transformed once and reused by the element above; the
+// constant mode is never formed), 45 multiply-adds in modal space with the element's 9
+// coefficients E_e C (scaled once per floor, modal_scale_kernel), the transposed network
+// back (54: the constant mode, a rigid translation, carries no force), and the 9 adds of
+// the node gather -- 153 FP64 instructions against the 576 FMAs of the dense 24x24
+// product. B300 issues FP64 at 1/64 of the FP32 rate, so this count, not memory, bounds
+// the kernel.
 //
 // Layout of the work: a CTA owns a tile of BX x BY element columns (32 x 16 or 16 x 32,
 // whichever wastes fewer warps on the grid; the tiles do not overlap) and walks them up
