@@ -1101,10 +1101,11 @@ def test_modal_apply_matches_oracle_and_dense(gf, dims, chunk, monkeypatch):
 
 @pytest.mark.parametrize("dims", [(40, 20, 10, 2), (34, 18, 6, 2), (1, 2, 2, 1)])
 def test_modal_apply_is_independent_of_the_launch_plan(gf, dims, monkeypatch):
-    """Each node of the FP64 K*u sums the same four column corners in one order wherever the
+    """Each node of the modal K*u sums the same four column corners in one order wherever the
     tiles fall: inside a tile in the kernel, on a tile boundary in the fix-up from the side
-    buffer. Forced tile shapes (32 x 16, 16 x 32) and run lengths (1, 4 node planes, the
-    cost model's choice) give bit-identical results, on grids whose tiles are ragged."""
+    buffer (which for the FP32 fine level also forms the node's smoothing update). Forced
+    tile shapes (32 x 16, 16 x 32) and run lengths (1, 4 node planes, the cost model's
+    choice) give bit-identical FP64 K*u, FP32 K*u and mixed V-cycles, on ragged tiles."""
     nx, ny, nz, L = dims
     outs = []
     for bx in ("32", "16"):
@@ -1115,13 +1116,19 @@ def test_modal_apply_is_independent_of_the_launch_plan(gf, dims, monkeypatch):
             u = synth.random_vector(m.n_dof, 3)
             y = torch.full((g.n_dof,), np.nan, dtype=torch.float64, device="cuda")
             g.apply_K(dev(u), y)
-            outs.append(host(y))
+            y32 = torch.full((g.n_dof,), np.nan, dtype=torch.float32, device="cuda")
+            g.apply_K_f32(dev(u, torch.float32), y32)
+            z = torch.full((g.n_dof,), np.nan, dtype=torch.float64, device="cuda")
+            g.vcycle(dev(u * m.free), z, gf.GF_MIXED)
+            outs.append((host(y), host(y32), host(z)))
             g.close()
-    assert not np.isnan(outs[0]).any()
+    for a in outs[0]:
+        assert not np.isnan(a).any()
     for o in outs[1:]:
-        assert np.array_equal(o, outs[0])
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
     ref = O.apply_K(m, O.young_modulus(rho, 1e-6, 3.0), O.element_stiffness(), u)
-    assert relerr(outs[0], ref) <= 1e-10
+    assert relerr(outs[0][0], ref) <= 1e-10
 
 
 # ------------------------------------------------------------- coarsest inverse -----
