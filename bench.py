@@ -213,7 +213,7 @@ def profiled_traffic(profile, source, start, end):
 
 # kernel text spans hashed for the traffic figures
 FP64_KU_SPAN = ("stencil.cuh", "// (i, j, k) of node n", "// First smoothing sweep")
-MODAL_SPAN = ("modal.cuh", "// 2D sum/difference transform", "}  // namespace gf")
+MODAL_SPAN = ("modal.cuh", "// 2D sum/difference transform", "// ---- the FP32 V-cycle's fine-level operator")
 MODAL_INSTR, MODAL_FLOPS = 153, 177     # FP64 instructions and flops per element of the modal K*u
 FP32_ST_SPAN = FP64_KU_SPAN                # both node-stencil bodies and their shared block update
 SPLIT_KU_SPAN = ("split_tc.cuh", "template <bool DD>", "}  // namespace gf")

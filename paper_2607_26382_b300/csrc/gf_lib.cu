@@ -136,11 +136,11 @@ struct gf_grid {
     gf::ModalCoef Kmodal;             // K0 in the sum/difference basis (apply_modal_kernel)
     gf::ModalCoefF Kmodal32;          // the same in FP32 with K0's node blocks (modal_stencil_f32_kernel)
     bool modal_f32 = true;            // level-0 FP32 stencils in the modal basis (GF_MODAL_F32=0: node stencils)
-    int4* modal_items = nullptr;      // work items of the modal FP32 fine level
+    int4* modal_items = nullptr;      // work items of the modal FP32 fine level (tiles overlapping by one column)
     int modal_n = 0, modal_bx = 32;   // item count; CTA tile 32 x 16 or 16 x 32 element columns
     int4* modal64_items = nullptr;    // work items of the modal FP64 K*u (device; null: dense stencil)
     int modal64_n = 0, modal64_bx = 32;
-    double* modal_side = nullptr;     // side buffer of both: corner forces at the nodes on tile boundaries
+    double* modal_side = nullptr;     // its side buffer: corner forces at the nodes on tile boundaries
     double* modal_es = nullptr;       // its elements' scaled coefficients E_e C, 9 x nel (modal_scale_kernel)
     bool sym_gj = true;               // coarsest inverse by the blocked symmetric sweep (GF_SYM_GJ=0: two-pivot form)
     int geom = GF_GEOM_CANTILEVER;    // supports: the clamped face x = 0, or the bridge's (gf_set_geometry)
@@ -321,18 +321,12 @@ int tiled_f32(gf_grid* g, int l, const float* x, const BT* b, OT* out, const flo
         return GF_OK;
     }
     if (l == 0 && g->modal_f32 && g->modal_items && !L.fix && g->tpb[1] > 0) {   // the modal FP32 fine level
-        const gf::GridDims d = L.dims();
-        const gf::ModalSide sd = gf::modal_side(d, g->modal_bx, gf::MODAL_THREADS / g->modal_bx);
-        float* side = (float*)g->modal_side;   // shared with the FP64 K*u: both run on the grid's stream
         if (g->modal_bx == 32)
             RET((launch_modal<float, 32, 16, gf::modal_stencil_f32_kernel<MODE, BT, OT, 32, 16>>(
-                g, g->modal_n, x, b, out, E, d, g->Kmodal32, omega, (const int4*)g->modal_items, side, sd, halt)));
+                g, g->modal_n, x, b, out, E, L.dims(), g->Kmodal32, omega, (const int4*)g->modal_items, halt)));
         else
             RET((launch_modal<float, 16, 32, gf::modal_stencil_f32_kernel<MODE, BT, OT, 16, 32>>(
-                g, g->modal_n, x, b, out, E, d, g->Kmodal32, omega, (const int4*)g->modal_items, side, sd, halt)));
-        const long long ne = sd.entries(d);
-        LAUNCH(g, (unsigned)((ne + 255) / 256), 256, (gf::modal_fixup_f32_kernel<MODE, BT, OT>), (const float*)side,
-               sd, x, b, out, E, d, g->Kmodal32, omega, halt);
+                g, g->modal_n, x, b, out, E, L.dims(), g->Kmodal32, omega, (const int4*)g->modal_items, halt)));
         return GF_OK;
     }
     if (g->tpb[1] > 0 && g->f32x2) {   // the same, with paired FMAs
@@ -1882,12 +1876,12 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
             const char* ch = getenv("GF_MODAL_CHUNK");
             const char* bxs = getenv("GF_MODAL_BX");
             const int forced = ch ? std::max(0, atoi(ch)) : 0;
-            // the FP32 fine level's plan and the FP64 K*u's (tuned apart later), each over
-            // both tile shapes by the cost model
+            // the FP32 fine level's plan (tiles overlapping by one column) and the FP64 K*u's
+            // (tiles apart), each over both tile shapes by the cost model
             for (int f32 = 1; f32 >= 0; --f32) {
                 double c32 = 0, c16 = 0;
-                std::vector<int4> i32 = gf::modal_plan(nx, ny, nz, 32, 16, g->sms * per_sm, forced, &c32);
-                std::vector<int4> i16 = gf::modal_plan(nx, ny, nz, 16, 32, g->sms * per_sm, forced, &c16);
+                std::vector<int4> i32 = gf::modal_plan(nx, ny, nz, 32, 16, g->sms * per_sm, forced, &c32, f32);
+                std::vector<int4> i16 = gf::modal_plan(nx, ny, nz, 16, 32, g->sms * per_sm, forced, &c16, f32);
                 const bool use32 = bxs ? atoi(bxs) == 32 : c32 <= c16;
                 const std::vector<int4>& items = use32 ? i32 : i16;
                 int4** dst = f32 ? &g->modal_items : &g->modal64_items;
@@ -2070,7 +2064,8 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
 namespace {
 // Time the modal kernels under a few launch plans -- the cheapest ones by modal_plan's
 // cost model over both tile shapes and several run lengths -- and keep the fastest, for
-// the FP64 K*u and the FP32 fine-level sweep apart (each with its tile-boundary fix-up).
+// the FP64 K*u (tiles apart, with its tile-boundary fix-up) and the FP32 fine-level sweep
+// (tiles overlapping by one column) apart.
 // The plan changes which CTA computes what, never the arithmetic of a node, so neither
 // result depends on it. Runs once per grid, on zeroed
 // level-0 scratch, on the grid's stream.
@@ -2109,7 +2104,8 @@ int modal_autotune(gf_grid* g)
             for (int L : {0, 2, 3, 4, 6, 8, 12, 16, 24, 33, 48, 64}) {
                 if (L > NZ) continue;
                 Cand c{bx, 0.0, {}};
-                c.items = gf::modal_plan(g->nx, g->ny, g->nz, bx, gf::MODAL_THREADS / bx, g->sms * per_sm, L, &c.cost);
+                c.items = gf::modal_plan(g->nx, g->ny, g->nz, bx, gf::MODAL_THREADS / bx, g->sms * per_sm, L, &c.cost,
+                                         f32);
                 cand.push_back(std::move(c));
             }
         std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.cost < b.cost; });
@@ -2137,19 +2133,14 @@ int modal_autotune(gf_grid* g)
                                                                   sd, nullptr);
                 gf::modal_fixup_kernel<false><<<(unsigned)((ne + 255) / 256), 256, 0, g->stream>>>(
                     g->modal_side, sd, f.t64, d, nullptr);
+            } else if (c.bx == 32) {   // the FP32 sweep (tiles overlapping by one column; no fix-up)
+                gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 32, 16>
+                    <<<n, dim3(32, 16), gf::modal_smem_bytes<float, 32, 16>(), g->stream>>>(
+                        f.x32, (const float*)f.b32, f.t32, f.E32, d, g->Kmodal32, 0.6f, dev, nullptr);
             } else {
-                float* side = (float*)g->modal_side;
-                if (c.bx == 32)
-                    gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 32, 16>
-                        <<<n, dim3(32, 16), gf::modal_smem_bytes<float, 32, 16>(), g->stream>>>(
-                            f.x32, (const float*)f.b32, f.t32, f.E32, d, g->Kmodal32, 0.6f, dev, side, sd, nullptr);
-                else
-                    gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 16, 32>
-                        <<<n, dim3(16, 32), gf::modal_smem_bytes<float, 16, 32>(), g->stream>>>(
-                            f.x32, (const float*)f.b32, f.t32, f.E32, d, g->Kmodal32, 0.6f, dev, side, sd, nullptr);
-                gf::modal_fixup_f32_kernel<gf::ST_SWEEP, float, float><<<(unsigned)((ne + 255) / 256), 256, 0,
-                                                                         g->stream>>>(
-                    side, sd, f.x32, (const float*)f.b32, f.t32, f.E32, d, g->Kmodal32, 0.6f, nullptr);
+                gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 16, 32>
+                    <<<n, dim3(16, 32), gf::modal_smem_bytes<float, 16, 32>(), g->stream>>>(
+                        f.x32, (const float*)f.b32, f.t32, f.E32, d, g->Kmodal32, 0.6f, dev, nullptr);
             }
         };
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)

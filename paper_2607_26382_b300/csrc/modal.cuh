@@ -35,8 +35,10 @@
 // columns around it in a fixed order. A node on a tile boundary has columns in two or
 // four tiles: each column writes its corner to that node's slot in a side buffer, and
 // modal_fixup_kernel adds the four slots in the same fixed order. No atomics: the result
-// does not depend on the launch shape. The FP32 fine-level kernel below works the same
-// way; its fix-up also forms the boundary node's smoothing update.
+// does not depend on the launch shape. (The FP32 fine-level kernel below keeps tiles
+// that overlap by one element column on the low x and y sides and needs no side buffer:
+// its smoothing update of a node needs the node's complete residual, and a fix-up launch
+// per sweep costs more there than the overlap.)
 #pragma once
 #include <cuda_runtime.h>
 #include <algorithm>
@@ -80,8 +82,10 @@ constexpr int modal_smem_bytes()
 }
 
 // Work items of the modal kernels for a grid of nx x ny x nz elements on `slots`
-// concurrent CTAs: x = tile column, y = tile row (tiles of bx x by element columns that
-// do not overlap), [z, w) = node planes. A CTA step costs the busiest of the SM's four sub-partitions (warp w
+// concurrent CTAs: x = tile column, y = tile row, [z, w) = node planes. halo = true:
+// tiles of (bx-1) x (by-1) output nodes whose bx x by element columns start one column
+// and one row below the tile (the FP32 kernel); halo = false: tiles of bx x by element
+// columns that do not overlap (apply_modal_kernel). A CTA step costs the busiest of the SM's four sub-partitions (warp w
 // runs on w mod 4), counting the warps that hold at least one element column inside
 // the grid (a warp issues its FP64 instructions for 32 lanes whatever its active mask):
 // far-edge tiles whose whole warps fall outside are cheaper and take longer runs of
@@ -90,10 +94,11 @@ constexpr int modal_smem_bytes()
 // waves x (largest item cost), with (planes + 1) steps per run. *cost receives that
 // product. Plain host arithmetic, deterministic.
 inline std::vector<int4> modal_plan(int nx, int ny, int nz, int bx, int by, int slots, int forced_planes,
-                                    double* cost)
+                                    double* cost, bool halo = true)
 {
-    const int NZ = nz + 1;
-    const int tx = (nx + bx - 1) / bx, ty = (ny + by - 1) / by;
+    const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
+    const int tx = halo ? (NX + bx - 2) / (bx - 1) : (nx + bx - 1) / bx;
+    const int ty = halo ? (NY + by - 2) / (by - 1) : (ny + by - 1) / by;
     std::vector<long long> v(tx * ty);
     for (int b = 0; b < ty; ++b)
         for (int a = 0; a < tx; ++a) {
@@ -101,7 +106,9 @@ inline std::vector<int4> modal_plan(int nx, int ny, int nz, int bx, int by, int 
             for (int w = 0; w < bx * by / 32; ++w) {
                 bool any = false;
                 for (int l = 0; l < 32 && !any; ++l) {
-                    const int t = 32 * w + l, ex = a * bx + t % bx, ey = b * by + t / bx;
+                    const int t = 32 * w + l;
+                    const int ex = halo ? a * (bx - 1) - 1 + t % bx : a * bx + t % bx;
+                    const int ey = halo ? b * (by - 1) - 1 + t / bx : b * by + t / bx;
                     any = ex >= 0 && ex < nx && ey >= 0 && ey < ny;
                 }
                 per_smsp[w % 4] += any;
@@ -273,7 +280,7 @@ __device__ __forceinline__ void modal_ring_store(const T (*__restrict__ part)[BY
 }
 
 // One CTA per work item: element tile (x, y) of BX x BY columns and node planes [z, w).
-// The host balances the items (modal_plan): tiles at the far edges of the
+// The host balances the items (modal_plan, halo = false): tiles at the far edges of the
 // grid hold fewer element columns and take longer runs of planes, so that every CTA costs
 // about the same. Writes y at the nodes inside the tile and the side buffer for the
 // nodes on its boundary (modal_fixup_kernel completes those).
@@ -476,8 +483,8 @@ __global__ void modal_fixup_kernel(const double* __restrict__ side, ModalSide sd
 
 // ---- the FP32 V-cycle's fine-level operator in the same basis ------------------------
 // The level-0 smoothing sweeps and residual of the mixed V-cycle (and the FP32 K*u) with
-// the modal K0 in FP32: the column walk of apply_modal_kernel (its own plan; the corners
-// at tile-boundary nodes go to the side buffer, in FP32), with the next
+// the modal K0 in FP32: the column walk of apply_modal_kernel (on tiles that overlap by one
+// element column, modal_plan with halo = true, so no side buffer), with the next
 // node plane's values and element modulus loaded one step ahead, and at the gather each
 // node also sums its 3x3 diagonal block from the moduli of its eight elements (kept in
 // shared memory for the current and the previous element layer) for the damped
@@ -490,35 +497,11 @@ struct ModalCoefF {
     float blk[8][6];   // the 3x3 diagonal block of K0 at local node a: d00 d11 d22 d01 d02 d12
 };
 
-// The output of node (ni, nj, kz) from its gathered force a = (K x)_n: K x, b - K x, or the
-// damped node-block Jacobi update with the node's 3x3 diagonal block db (the clamped face
-// x = 0 is written as 0). Shared by the kernel and its tile-boundary fix-up.
-template <int MODE, typename OT>
-__device__ __forceinline__ void modal_f32_out(const float a[3], const float bn[3], const float xn[3], const float db[6],
-                                              int ni, OT* __restrict__ o, float omega)
-{
-    if (ni == 0) {
-        o[0] = OT(0);
-        o[1] = OT(0);
-        o[2] = OT(0);
-    } else if (MODE == ST_APPLY) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) o[c] = OT(a[c]);
-    } else if (MODE == ST_RESID) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) o[c] = OT(bn[c] - a[c]);
-    } else {
-        const float r0 = bn[0] - a[0], r1 = bn[1] - a[1], r2 = bn[2] - a[2];
-        node_block_update<float, OT>(db[0], db[1], db[2], db[3], db[4], db[5], r0, r1, r2, xn, o, omega);
-    }
-}
-
 template <int MODE, typename BT, typename OT, int BX, int BY>
 __global__ void __launch_bounds__(MODAL_THREADS, 1)
 modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, OT* __restrict__ out,
                          const float* __restrict__ E, GridDims d, const __grid_constant__ ModalCoefF C,
-                         float omega, const int4* __restrict__ items, float* __restrict__ side, ModalSide sd_,
-                         const int* __restrict__ halt)
+                         float omega, const int4* __restrict__ items, const int* __restrict__ halt)
 {
     if (halt != nullptr && *halt != 0) return;
     // corner forces [corner * 3 + comp][column] in two buffers by step parity, and the
@@ -531,13 +514,13 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
     const int4 it = items[blockIdx.x];
-    const int i0 = it.x * BX, j0 = it.y * BY;
+    const int i0 = it.x * (BX - 1), j0 = it.y * (BY - 1);
     const int k0 = it.z;
     const int k1 = min(NZ, it.w);
-    const int ex = i0 + tx, ey = j0 + ty;
-    const bool col = ex < d.nx && ey < d.ny;
+    const int ex = i0 - 1 + tx, ey = j0 - 1 + ty;
+    const bool col = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
     const long long plane = (long long)NX * NY;
-    const int ni = i0 + tx + 1, nj = j0 + ty + 1;   // this thread's output node column (inside the tile)
+    const int ni = i0 + tx, nj = j0 + ty;   // this thread's output node column
     const bool outnode = tx < BX - 1 && ty < BY - 1 && ni < NX && nj < NY;
 
     auto load_raw = [&](int kz, float v[3][4]) {
@@ -653,7 +636,6 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
         }
         Es[cur][ty][tx] = Ecur;
         __syncthreads();
-        if (ez >= k0) modal_ring_store<float, BX, BY>(part, side, sd_, d, it, ez, tx + BX * ty);   // for the fix-up
         if (ez >= k0 && outnode) {
             float a[3];
 #pragma unroll
@@ -663,10 +645,20 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
                 acc += part[0 * 3 + c][ty + 1][tx + 1];
                 a[c] = acc;
             }
-            // the node's 3x3 diagonal block from its eight elements (previous layer: the
-            // node at local z offset 1; current layer: offset 0), in a fixed order
-            float db[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (MODE == ST_SWEEP) {
+            if (ni == 0) {
+                out[3 * nn + 0] = OT(0);
+                out[3 * nn + 1] = OT(0);
+                out[3 * nn + 2] = OT(0);
+            } else if (MODE == ST_APPLY) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[3 * nn + c] = OT(a[c]);
+            } else if (MODE == ST_RESID) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[3 * nn + c] = OT(bn[c] - a[c]);
+            } else {
+                // the node's 3x3 diagonal block from its eight elements (previous layer: the
+                // node at local z offset 1; current layer: offset 0), in a fixed order
+                float db[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int lz = 0; lz < 2; ++lz) {
                     const int layer = lz == 0 ? prv : cur;   // ez - 1, then ez
@@ -680,8 +672,10 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
                         for (int k = 0; k < 6; ++k) db[k] = fmaf(Ee, C.blk[la][k], db[k]);
                     }
                 }
+                const float r0 = bn[0] - a[0], r1 = bn[1] - a[1], r2 = bn[2] - a[2];
+                node_block_update<float, OT>(db[0], db[1], db[2], db[3], db[4], db[5], r0, r1, r2, xn, out + 3 * nn,
+                                             omega);
             }
-            modal_f32_out<MODE, OT>(a, bn, xn, db, ni, out + 3 * nn, omega);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -692,80 +686,6 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
             }
         Ecur = Enext;
     }
-}
-
-// The FP32 kernel's tile-boundary nodes: the four corner forces from the side buffer (FP32
-// slots), the node's diagonal block from the moduli of its eight elements, and the output,
-// each in the order of modal_stencil_f32_kernel (out-of-grid columns and layers read as 0).
-template <int MODE, typename BT, typename OT>
-__global__ void modal_fixup_f32_kernel(const float* __restrict__ side, ModalSide sd_, const float* __restrict__ x,
-                                       const BT* __restrict__ b, OT* __restrict__ out, const float* __restrict__ E,
-                                       GridDims d, const __grid_constant__ ModalCoefF C, float omega,
-                                       const int* __restrict__ halt)
-{
-    if (halt != nullptr && *halt != 0) return;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int NX = d.nx + 1, NY = d.ny + 1;
-    if (t >= sd_.entries(d)) return;
-    int ni, nj, kz;
-    if (t < sd_.xn) {
-        nj = (int)(t % NY);
-        const long long r = t / NY;
-        ni = (int)(r % sd_.nxl) * sd_.bx;
-        kz = (int)(r / sd_.nxl);
-    } else {
-        const long long u = t - sd_.xn;
-        ni = (int)(u % NX);
-        const long long r = u / NX;
-        nj = (int)(r % sd_.nyl) * sd_.by;
-        kz = (int)(r / sd_.nyl);
-        if (ni % sd_.bx == 0) return;   // on an x line: its entry is there
-    }
-    if (ni >= NX || nj >= NY) return;
-    const long long n = ni + (long long)NX * nj + (long long)NX * NY * kz;
-    bool in[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int ex = ni - (q & 1), ey = nj - (q >> 1);
-        in[q] = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny;
-    }
-    const float* s = side + t * 12;
-    float a[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float p3 = in[3] ? s[9 + c] : 0.f, p2 = in[2] ? s[6 + c] : 0.f;
-        const float p1 = in[1] ? s[3 + c] : 0.f, p0 = in[0] ? s[c] : 0.f;
-        float acc = p3 + p2;
-        acc += p1;
-        acc += p0;
-        a[c] = acc;
-    }
-    float bn[3] = {0.f, 0.f, 0.f}, xn[3] = {0.f, 0.f, 0.f};
-    if (MODE != ST_APPLY) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) bn[c] = float(b[3 * n + c]);
-    }
-    float db[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (MODE == ST_SWEEP) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) xn[c] = x[3 * n + c];
-#pragma unroll
-        for (int lz = 0; lz < 2; ++lz) {
-            const int ez = kz - 1 + lz;   // the layer below the node plane, then the one above
-            const int oz = lz == 0 ? 1 : 0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int cx = q & 1, cy = q >> 1;   // column (ni - 1 + cx, nj - 1 + cy)
-                const int ex = ni - 1 + cx, ey = nj - 1 + cy;
-                const bool ok = ex >= 0 && ex < d.nx && ey >= 0 && ey < d.ny && ez >= 0 && ez < d.nz;
-                const float Ee = ok ? __ldg(E + ex + (long long)d.nx * (ey + (long long)d.ny * ez)) : 0.f;
-                const int la = local_index(1 - cx, 1 - cy, oz);
-#pragma unroll
-                for (int k = 0; k < 6; ++k) db[k] = fmaf(Ee, C.blk[la][k], db[k]);
-            }
-        }
-    }
-    modal_f32_out<MODE, OT>(a, bn, xn, db, ni, out + 3 * n, omega);
 }
 
 }  // namespace gf
