@@ -1163,11 +1163,10 @@ int build_coarse_map(gf_grid* g)
     CK(cudaMemcpyAsync(&m, g->cidx + g->nc, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     g->ncf = m;
-    // nodes couple to the 27 nodes around them: node indices differ by at most
-    // 1 + NX + NX NY (x fastest), DOF indices by 3 of that + 2; dropping the fixed DOFs
-    // only brings indices closer
-    const int NX = c.nx + 1, NY = c.ny + 1;
-    g->cband = 3 * (1 + NX + NX * NY) + 2;
+    // nodes couple to the 27 nodes around them: in the compact order (coarse_axes) their
+    // positions differ by at most 1 + N_a + N_a N_b, DOF positions by 3 of that + 2;
+    // dropping the fixed DOFs only brings positions closer
+    g->cband = gf::coarse_band(c.dims());
     return GF_OK;
 }
 

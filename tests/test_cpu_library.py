@@ -94,21 +94,38 @@ def test_conditioning_screen_matches_oracle(gflib):
 
 
 @pytest.mark.parametrize("dims,bridge", [((12, 6, 6), False), ((12, 5, 3), False), ((8, 4, 4), False),
-                                         ((12, 6, 6), True), ((16, 4, 8), True)])
+                                         ((12, 6, 6), True), ((16, 4, 8), True), ((4, 10, 6), False)])
 def test_coarsest_band_bound_holds_for_the_free_dof_matrix(dims, bridge):
     """The coarsest inverse's sweep launches only the tiles inside the band ahead of its
-    pivots, assuming the free-DOF operator (free DOFs in ascending order) has no non-zero
-    with |p - q| > 3 (1 + NX + NX NY) + 2. The oracle's assembled operator, with random
-    moduli, stays inside that band for the cantilever and for the bridge's supports, and
-    reaches within one node layer of it (the bound is not loose by a layer)."""
+    pivots. It orders the free DOFs with nodes running along the axis with the fewest nodes
+    first and the most nodes last (ties in x, y, z order), a node's three components
+    together, and assumes no non-zero with |p - q| > 3 (1 + N_a + N_a N_b) + 2 (N_a <= N_b
+    the two smallest node counts). The oracle's assembled operator, with random moduli and
+    permuted into that order here, stays inside that band for the cantilever and for the
+    bridge's supports, and reaches within one node layer of it (the bound is not loose by a
+    layer); in x-fastest order it would not fit when x is not the shortest axis."""
     nx, ny, nz = dims
     mesh = O.BridgeMesh(nx, ny, nz) if bridge else O.Mesh(nx, ny, nz)
     E = np.random.default_rng(nx * ny + nz).uniform(0.01, 1.0, mesh.n_elem)
-    K = O.assemble_sparse(mesh, E, O.element_stiffness(), constrained=False)
-    free = np.flatnonzero(mesh.free)
+    K = O.assemble_sparse(mesh, E, O.element_stiffness(), constrained=False).tocsr()
+    N = [nx + 1, ny + 1, nz + 1]
+    ax = sorted(range(3), key=lambda a: N[a])          # stable: ties keep x, y, z order
+    # DOF q = 3 (i + NX (j + NY k)) + c listed in the compact order
+    order = []
+    for u2 in range(N[ax[2]]):
+        for u1 in range(N[ax[1]]):
+            for u0 in range(N[ax[0]]):
+                v = [0, 0, 0]
+                v[ax[0]], v[ax[1]], v[ax[2]] = u0, u1, u2
+                node = v[0] + N[0] * (v[1] + N[1] * v[2])
+                order.extend(3 * node + c for c in range(3))
+    order = np.array(order)
+    assert np.array_equal(np.sort(order), np.arange(3 * N[0] * N[1] * N[2]))
+    free = order[mesh.free[order]]
     rows, cols = K[free][:, free].nonzero()
-    NX, NY = nx + 1, ny + 1
-    band = 3 * (1 + NX + NX * NY) + 2
+    band = 3 * (1 + N[ax[0]] + N[ax[0]] * N[ax[1]]) + 2
     width = int(np.max(np.abs(rows - cols)))
     assert width <= band
-    assert width > band - 3 * NX * NY
+    assert width > band - 3 * N[ax[0]] * N[ax[1]]
+    if ax[0] != 0:   # the x-fastest bound is wider than the permuted one
+        assert band < 3 * (1 + N[0] + N[0] * N[1]) + 2
