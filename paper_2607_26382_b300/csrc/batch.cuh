@@ -406,10 +406,16 @@ int batch_solve(gf_batch* b, const gf_solve_opts* o, const std::vector<int>& act
 }
 
 // Set the floor of the active states: moduli and hierarchy per state, then the
-// coarsest inverses with lockstep Gauss-Jordan pivots over the batch.
+// coarsest inverses: each state's banded LDL^T inverse (the default, as one grid's), or
+// the sweeps with lockstep pivots over the batch.
 int batch_set_floor(gf_batch* b, const std::vector<int>& active, const std::vector<double>& rho_min)
 {
     const int B = b->B;
+    if (b->g[0]->coarse_ldl) {   // the banded LDL^T inverse: each state's own set-up, as one grid's
+        for (int i = 0; i < B; ++i)
+            if (active[i]) RET(gf_set_floor(b->g[i], rho_min[i]));
+        return GF_OK;
+    }
     for (int i = 0; i < B; ++i) {
         if (!active[i]) continue;
         gf_grid* g = b->g[i];

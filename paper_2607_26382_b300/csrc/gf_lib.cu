@@ -19,6 +19,7 @@
 #include "galerkin.cuh"
 #include "coarse_krylov.cuh"
 #include "modal.cuh"
+#include "ldl.cuh"
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -142,7 +143,9 @@ struct gf_grid {
     int modal64_n = 0, modal64_bx = 32;
     double* modal_side = nullptr;     // its side buffer: corner forces at the nodes on tile boundaries
     double* modal_es = nullptr;       // its elements' scaled coefficients E_e C, 9 x nel (modal_scale_kernel)
-    bool sym_gj = true;               // coarsest inverse by the blocked symmetric sweep (GF_SYM_GJ=0: two-pivot form)
+    bool coarse_ldl = true;           // coarsest inverse from the banded LDL^T factorisation (GF_COARSE_LDL=0: a sweep)
+    bool sym_gj = true;               // else the blocked symmetric sweep (GF_SYM_GJ=0: the two-pivot form)
+    double* ldl_ws = nullptr;         // its workspace: 1 / d (nc), X of the band rows (nc x LDL_C), Q (LDL_C^2)
     int geom = GF_GEOM_CANTILEVER;    // supports: the clamped face x = 0, or the bridge's (gf_set_geometry)
     gf::K0Param<float> K0f;
     gf::K0Pair K0p;                   // K0f with rows 3a, 3a+1 paired (node_stencil_f32x2_kernel)
@@ -1170,11 +1173,65 @@ int build_coarse_map(gf_grid* g)
     return GF_OK;
 }
 
+// The coarsest inverse from the banded LDL^T factorisation (ldl.cuh): the free-DOF matrix
+// assembled into Ainv (m x m), factored in place by blocks of LDL_C pivots, the inverse
+// formed block by block from the last into Agj (m x m), then expanded into Ainv (n x n).
+int build_coarse_inverse_ldl(gf_grid* g)
+{
+    Level& c = g->lv[g->L - 1];
+    const int n = g->nc, m = g->ncf, b = g->cband;
+    double* M = g->Ainv;
+    double* Z = g->Agj;
+    double* dinv = g->ldl_ws;
+    double* Xs = dinv + n;
+    double* Qs = Xs + (long long)n * gf::LDL_C;
+    if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1)
+        LAUNCH(g, nblk((long long)m * m), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, M, c.dims(),
+               (const int*)g->cidx, m);
+    else
+        LAUNCH(g, nblk((long long)m * m), 256, gf::coarse_assemble_kernel, c.E64, M, c.dims(), g->K0d,
+               (const int*)g->cidx, m);
+    constexpr int C = gf::LDL_C, W = gf::LDL_WARPS;
+    for (int j0 = 0; j0 < m; j0 += C) {   // A = L D L^T
+        const int cb = std::min(C, m - j0), j1 = j0 + cb;
+        LAUNCH(g, 1, 512, gf::ldl_diag_kernel, M, m, j0, cb, dinv);
+        if (j1 >= m) break;
+        const int r1 = gf::ldl_band_end(m, j1, b);
+        LAUNCH(g, (r1 - j1 + W - 1) / W, W * 32, gf::ldl_panel_kernel, M, m, j0, cb, r1, (const double*)dinv);
+        const int T = (r1 - j1 + 15) / 16;
+        LAUNCH(g, T * (T + 1) / 2, 256, gf::ldl_update_kernel, M, m, j0, cb, r1);
+    }
+    static const bool smem_ok =   // the rows and Y kernels stage the band's rows: up to 227 KB
+        cudaFuncSetAttribute((const void*)gf::ldl_inv_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) == cudaSuccess &&
+        cudaFuncSetAttribute((const void*)gf::ldl_inv_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) == cudaSuccess;
+    if (!smem_ok) return set_err(GF_ERR_CUDA, "shared memory of ldl_inv_rows_kernel");
+    for (int j0 = (m - 1) / C * C; m > 0 && j0 >= 0; j0 -= C) {   // Z = A^-1, last block first
+        const int cb = std::min(C, m - j0), j1 = j0 + cb;
+        const int kend = gf::ldl_band_end(m, j1, b);
+        if (j1 < m) {
+            const size_t smem = sizeof(double) * ((size_t)C * (C + 1) + (size_t)(kend - j1) * (C + W));
+            if (smem > 200 * 1024) return set_err(GF_ERR_ARG, "coarsest band too wide for the LDL^T inverse");
+            LAUNCH_SMEM(g, (m - j1 + W - 1) / W, W * 32, smem, gf::ldl_inv_rows_kernel, (const double*)M, Z, m, j0, cb,
+                        kend, Xs);
+        }
+        LAUNCH_SMEM(g, cb, W * 32, sizeof(double) * (size_t)(kend - j1) * (C + 1), gf::ldl_inv_diag_kernel,
+                    (const double*)M, m, j0, cb, kend, (const double*)Xs, (const double*)dinv, Qs);
+        LAUNCH(g, (cb + W - 1) / W, W * 32, gf::ldl_inv_diag2_kernel, (const double*)M, Z, m, j0, cb,
+               (const double*)Qs);
+    }
+    LAUNCH(g, std::min<long long>(nblk((long long)n * n), 4LL * g->sms), 256, gf::sym_expand_kernel, (const double*)Z,
+           m, (const int*)g->cpos, g->Ainv, n);
+    return GF_OK;
+}
+
 int build_coarse_inverse(gf_grid* g)
 {
     Level& c = g->lv[g->L - 1];
     const long long n = g->nc;
     gf::K0Param<double> K = g->K0d;   // the level's E64 already carries h
+    if (g->coarse_ldl) return build_coarse_inverse_ldl(g);
     if (g->sym_gj) {
         // blocked symmetric sweep on the upper triangle of the operator restricted to the
         // free DOFs (m x m; the fixed ones only carry identity rows), ceil(m / SGJ_B)
@@ -1861,6 +1918,8 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     {
         const char* e = getenv("GF_SYM_GJ");
         g->sym_gj = !(e && e[0] == '0');
+        const char* l = getenv("GF_COARSE_LDL");
+        g->coarse_ldl = !(l && l[0] == '0') && g->sym_gj;
     }
     {   // modal FP64 K*u (GF_MODAL=0: the dense node stencil); GF_MODAL_CHUNK=<planes> forces
         // runs of that many node planes per CTA and GF_MODAL_BX=32/16 the tile shape (tests)
@@ -2032,6 +2091,7 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
             }
     }
     if ((r = allocT(&g->Ainv, (size_t)g->nc * g->nc)) || (r = allocT(&g->Agj, (size_t)g->nc * g->nc + 2 * gf::SGJ_B * gf::SGJ_B)) ||
+        (r = allocT(&g->ldl_ws, (size_t)g->nc * (1 + gf::LDL_C) + gf::LDL_C * gf::LDL_C)) ||
         (r = allocT(&g->cpos, (size_t)g->nc)) || (r = allocT(&g->cidx, (size_t)g->nc + 1)) ||
         (r = allocT(&g->dflag, 4)) || (r = allocT(&g->rho64, g->nel)) ||
         (r = allocT(&g->rho16, g->nel)) || (r = allocT(&g->work, g->ndof)) ||
@@ -2203,7 +2263,7 @@ int gf_destroy_grid(gf_grid* g)
     cudaFree(g->ls_partial); cudaFree(g->ls_alpha);
     cudaFree(g->fcV); cudaFree(g->fcZ); cudaFree(g->fcR); cudaFree(g->fcD); cudaFree(g->fcQ); cudaFree(g->fcZT);
     cudaFree(g->fc); cudaFree(g->fc_partial);
-    cudaFree(g->Ainv); cudaFree(g->Agj); cudaFree(g->cpos); cudaFree(g->cidx); cudaFree(g->dflag); cudaFree(g->cheb); cudaFree(g->cheb_ss);
+    cudaFree(g->Ainv); cudaFree(g->Agj); cudaFree(g->ldl_ws); cudaFree(g->cpos); cudaFree(g->cidx); cudaFree(g->dflag); cudaFree(g->cheb); cudaFree(g->cheb_ss);
     cudaFree(g->rho64); cudaFree(g->rho16); cudaFree(g->work); cudaFree(g->partial);
     cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Vd); cudaFree(g->pdd); cudaFree(g->ddticket); cudaFree(g->Z); cudaFree(g->hist);
     cudaFree(g->ckx);

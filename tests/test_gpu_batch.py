@@ -82,6 +82,35 @@ def test_batch_matches_single_state(gf, selector, prec, outer, smoother, restart
     batch.close()
 
 
+def test_batch_sweep_inverse_matches_single_state(gf, monkeypatch):
+    """With the coarsest inverse by the blocked symmetric sweep (GF_COARSE_LDL=0) the batch
+    runs the sweep in lockstep over its states: every state's result and solution still
+    equal its single grid's, bit for bit."""
+    monkeypatch.setenv("GF_COARSE_LDL", "0")
+    L = 3
+    pol = gf.policy_defaults(rho0=1e-8, ladder=[1e-5, 1e-4, 1e-3], kmax=120, solve_prec=1, solve_outer=0)
+    batch = gf.Batch([s[0] for s in STATES], levels=L)
+    tuned = batch.autotune()
+    rhos, fs = [], []
+    for i, (dims, kind, seed, q) in enumerate(STATES):
+        rhos.append(dev(_rho(dims, kind, seed, q)))
+        fs.append(dev(O.cantilever_load(O.Mesh(*dims))))
+        batch.set_state(i, rhos[i], fs[i], 3.0)
+    res = batch.select_floor(pol)
+    for i, (dims, kind, seed, q) in enumerate(STATES):
+        g = gf.create_grid(*dims, levels=L)
+        g.set_stencil_blocks(*tuned[i])
+        g.set_density(rhos[i], 3.0)
+        u1 = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        ref = g.select_floor(fs[i], u1, pol)
+        assert res[i]["attempts"] == ref["attempts"], i
+        u2 = torch.zeros_like(u1)
+        batch.solution(i, u2)
+        assert torch.equal(u1, u2), i
+        g.close()
+    batch.close()
+
+
 def test_batch_rejects_single_grid_options(gf):
     """The reuse selector, true-residual checks, the line-searched coarse correction, the
     fine-level correction and the coarse-level Krylov solve are single-grid options; the batch

@@ -1132,25 +1132,30 @@ def test_modal_apply_is_independent_of_the_launch_plan(gf, dims, monkeypatch):
 
 
 # ------------------------------------------------------------- coarsest inverse -----
-@pytest.mark.parametrize("dims", [(16, 8, 8, 3), (24, 10, 6, 2), (2, 2, 2, 1), (8, 4, 4, 1), (12, 6, 6, 2)])
-def test_symmetric_blocked_inverse_matches_two_pivot_form(gf, dims, monkeypatch):
-    """The coarsest level's dense FP64 inverse by the blocked symmetric sweep (8 pivots per
+@pytest.mark.parametrize("dims", [(16, 8, 8, 3), (24, 10, 6, 2), (2, 2, 2, 1), (8, 4, 4, 1), (12, 6, 6, 2),
+                                  (48, 24, 24, 3)])
+def test_coarsest_inverses_agree(gf, dims, monkeypatch):
+    """The coarsest level's dense FP64 inverse three ways: the banded LDL^T factorisation and
+    the block-by-block inverse from it (default), the blocked symmetric sweep (8 pivots per
     launch on the upper triangle of the free-DOF matrix, each launch over the band ahead of
-    its pivots; default) against the two-pivot full-matrix Gauss-Jordan (GF_SYM_GJ=0): FP64
-    V-cycles agree to 1e-10 relative, on coarsest levels whose size is not always a multiple
-    of the pivot block (135 / 936 / 81 / 675 / 336 DOFs; at 936 and 675 the band, 278 and
-    167, leaves the early launches a leading block of the matrix); on one-level grids the
-    inverse is the whole operator's, and its direct solution meets the oracle's guard."""
+    its pivots; GF_COARSE_LDL=0), and the two-pivot full-matrix Gauss-Jordan (GF_SYM_GJ=0).
+    FP64 V-cycles agree to 1e-10 relative, on coarsest levels whose size is not always a
+    multiple of the pivot blocks (135 / 936 / 81 / 675 / 336 / 1,911 DOFs; at 936 and 675
+    the band leaves the early sweeps a leading block of the matrix; at 1,911, the size of
+    the 192x96x96 hierarchy's coarsest level, 56 LDL^T blocks each have 173 band rows below
+    them); on one-level grids the inverse is the whole operator's, and its direct solution
+    meets the oracle's guard."""
     nx, ny, nz, L = dims
     outs = []
-    for sym in ("1", "0"):
+    for ldl, sym in (("1", "1"), ("0", "1"), ("1", "0")):
+        monkeypatch.setenv("GF_COARSE_LDL", ldl)
         monkeypatch.setenv("GF_SYM_GJ", sym)
         g, m, rho = make(gf, nx, ny, nz, L, seed=3, rho_min=1e-4, kind="bernoulli")
         v = synth.random_vector(m.n_dof, 9)
         z = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
         g.vcycle(dev(v), z, gf.GF_FP64)
         outs.append(host(z))
-        if L == 1 and sym == "1":
+        if L == 1 and ldl == "1" and sym == "1":
             f = O.cantilever_load(m)
             res = g.conditioning(dev(f), iters=20)
             E = O.young_modulus(rho, 1e-4, 3.0)
@@ -1158,4 +1163,6 @@ def test_symmetric_blocked_inverse_matches_two_pivot_form(gf, dims, monkeypatch)
             assert res["eta_direct"] <= 1e-9
             ref = O.vcycle(O.build_hierarchy(m, E, 1), v * m.free)
             assert relerr(outs[-1], ref) <= 1e-8
-    assert relerr(outs[0], outs[1]) <= 1e-10
+        g.close()
+    assert relerr(outs[0], outs[2]) <= 1e-10
+    assert relerr(outs[1], outs[2]) <= 1e-10
