@@ -222,8 +222,8 @@ int gf_set_density(gf_grid* g, const double* rho_hat, double p);
 
 /* Set the floor: E_e = rho_min + (1 - rho_min) rho_hat_e^p (Eq. floor_scaling, E0
  * scales it), coarse moduli = mean of the 8 children, and the FP64 inverse of the
- * coarsest operator (Gauss-Jordan without pivoting on the SPD operator restricted to
- * the free DOFs, in its symmetric "sweep" form; identity rows on fixed DOFs). 0 < rho_min <= 1. */
+ * coarsest operator (from the banded LDL^T factorisation of the SPD operator restricted
+ * to the free DOFs, block by block; identity rows on fixed DOFs). 0 < rho_min <= 1. */
 int gf_set_floor(gf_grid* g, double rho_min);
 
 /* Coarse-level operators of the V-cycle, used from the next gf_set_floor on:
@@ -346,7 +346,7 @@ int gf_select_floor_many(int n, gf_grid* const* grids, const double* const* f, d
 
 /* Extreme eigenvalues of the free-DOF operator K(rho_min) of Eq. (frozen_operator) on a
  * one-level grid (levels == 1, at most 8192 DOFs: gf_set_floor then holds K's dense
- * FP64 inverse, built by the Gauss-Jordan sweep). *lambda_max: `iters` Lanczos steps on K
+ * FP64 inverse, built from its LDL^T factorisation). *lambda_max: `iters` Lanczos steps on K
  * (matrix-free FP64 operator); *lambda_min: 1 / the largest eigenvalue after `iters`
  * Lanczos steps on the dense inverse. Both start from the all-ones vector on the free
  * DOFs, re-orthogonalise against the two previous vectors, and take the extreme

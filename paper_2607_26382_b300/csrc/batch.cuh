@@ -22,6 +22,7 @@ struct BatchTables {
     int* m;            // coarsest free-DOF counts (the symmetric sweep's size)
     int** pos;         // coarsest free-DOF positions (gf_grid::cpos)
     int* band;         // coarsest operator bands (gf_grid::cband)
+    LdlState* ldl;     // the states' LDL^T inverse buffers (ldl_state)
 };
 
 __global__ void batch_mark_kernel(KState** st, const int* __restrict__ active, int B)
@@ -411,9 +412,63 @@ int batch_solve(gf_batch* b, const gf_solve_opts* o, const std::vector<int>& act
 int batch_set_floor(gf_batch* b, const std::vector<int>& active, const std::vector<double>& rho_min)
 {
     const int B = b->B;
-    if (b->g[0]->coarse_ldl) {   // the banded LDL^T inverse: each state's own set-up, as one grid's
-        for (int i = 0; i < B; ++i)
-            if (active[i]) RET(gf_set_floor(b->g[i], rho_min[i]));
+    if (b->g[0]->coarse_ldl) {   // the banded LDL^T inverse, every state's steps in one launch
+        int steps = 0;
+        for (int i = 0; i < B; ++i) {
+            if (!active[i]) continue;
+            gf_grid* g = b->g[i];
+            g->skip_coarse_inverse = true;
+            const int rc = gf_set_floor(g, rho_min[i]);
+            g->skip_coarse_inverse = false;
+            if (rc != GF_OK) return rc;
+            RET(assemble_coarse_free(g, g->Ainv));
+            steps = std::max(steps, (g->ncf + gf::LDL_C - 1) / gf::LDL_C);
+        }
+        CK(cudaMemcpyAsync(b->d_active, active.data(), sizeof(int) * B, cudaMemcpyHostToDevice, b->stream));
+        if (!ldl_smem_opt_in()) return set_err(GF_ERR_CUDA, "shared memory of the LDL^T inverse kernels");
+        auto launch = [&](auto kern, int ctas, int threads, size_t smem, int s) -> int {
+            if (ctas <= 0) return GF_OK;
+            kern<<<dim3((unsigned)ctas, 1, (unsigned)B), threads, smem, b->stream>>>(
+                (const gf::LdlState*)b->tab.ldl, (const int*)b->d_active, s);
+            b->launches += 1;
+            CK(cudaGetLastError());
+            return GF_OK;
+        };
+        for (int s = 0; s < steps; ++s) {   // A = L D L^T, block s of every state
+            int panel = 0, upd = 0;
+            for (int i = 0; i < B; ++i) {
+                int j0, c, r1;
+                if (!active[i] || !gf::ldl_factor_step(b->g[i]->ncf, b->g[i]->cband, s, j0, c, r1)) continue;
+                if (j0 + c >= b->g[i]->ncf) continue;
+                panel = std::max(panel, gf::ldl_panel_ctas(j0 + c, r1));
+                upd = std::max(upd, gf::ldl_update_ctas(j0 + c, r1));
+            }
+            RET(launch(gf::ldl_diag_batch_kernel, 1, 512, 0, s));
+            RET(launch(gf::ldl_panel_batch_kernel, panel, gf::LDL_WARPS * 32, 0, s));
+            RET(launch(gf::ldl_update_batch_kernel, upd, 256, 0, s));
+        }
+        for (int s = 0; s < steps; ++s) {   // Z = A^-1, last blocks first
+            int rows = 0, cmax = 0;
+            size_t rsm = 0, dsm = 0;
+            for (int i = 0; i < B; ++i) {
+                int j0, c, kend;
+                const int m = b->g[i]->ncf;
+                if (!active[i] || !gf::ldl_inverse_step(m, b->g[i]->cband, s, j0, c, kend)) continue;
+                cmax = std::max(cmax, c);
+                dsm = std::max(dsm, gf::ldl_diag_smem(kend - j0 - c));
+                if (j0 + c < m) {
+                    rows = std::max(rows, gf::ldl_rows_ctas(m, j0 + c));
+                    rsm = std::max(rsm, gf::ldl_rows_smem(kend - j0 - c));
+                }
+            }
+            if (rsm > 200 * 1024) return set_err(GF_ERR_ARG, "coarsest band too wide for the LDL^T inverse");
+            RET(launch(gf::ldl_inv_rows_batch_kernel, rows, gf::LDL_WARPS * 32, rsm, s));
+            RET(launch(gf::ldl_inv_diag_batch_kernel, cmax, gf::LDL_WARPS * 32, dsm, s));
+            RET(launch(gf::ldl_inv_diag2_batch_kernel, gf::ldl_diag2_ctas(cmax), gf::LDL_WARPS * 32, 0, s));
+        }
+        gf::batch_sym_expand_kernel<<<dim3((unsigned)std::max(1, b->sms), B), 256, 0, b->stream>>>(b->tab, b->d_active);
+        b->launches += 1;
+        CK(cudaGetLastError());
         return GF_OK;
     }
     for (int i = 0; i < B; ++i) {
@@ -573,6 +628,7 @@ int gf_create_batch(int n_states, const int* dims, int levels, double h, double 
         cudaMalloc(&b->tab.A, P) != cudaSuccess || cudaMalloc(&b->tab.W, P) != cudaSuccess || cudaMalloc(&b->tab.n, sizeof(int) * n_states) != cudaSuccess ||
         cudaMalloc(&b->tab.m, sizeof(int) * n_states) != cudaSuccess || cudaMalloc(&b->tab.pos, P) != cudaSuccess ||
         cudaMalloc(&b->tab.band, sizeof(int) * n_states) != cudaSuccess ||
+        cudaMalloc(&b->tab.ldl, sizeof(gf::LdlState) * n_states) != cudaSuccess ||
         cudaMalloc(&b->d_active, sizeof(int) * n_states) != cudaSuccess ||
         cudaMalloc(&b->d_abort, sizeof(int) * n_states) != cudaSuccess)
         return fail(set_err(GF_ERR_OOM, "batch tables"));
@@ -582,7 +638,9 @@ int gf_create_batch(int n_states, const int* dims, int levels, double h, double 
     std::vector<double*> A(n_states), W(n_states);
     std::vector<int*> pos(n_states);
     std::vector<int> n(n_states), m(n_states), band(n_states);
+    std::vector<gf::LdlState> ldl(n_states);
     for (int i = 0; i < n_states; ++i) {
+        ldl[i] = ldl_state(b->g[i]);
         A[i] = b->g[i]->Ainv;
         W[i] = b->g[i]->Agj;
         n[i] = b->g[i]->nc;
@@ -595,7 +653,8 @@ int gf_create_batch(int n_states, const int* dims, int levels, double h, double 
         cudaMemcpy(b->tab.n, n.data(), sizeof(int) * n_states, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->tab.m, m.data(), sizeof(int) * n_states, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->tab.pos, pos.data(), P, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->tab.band, band.data(), sizeof(int) * n_states, cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(b->tab.band, band.data(), sizeof(int) * n_states, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->tab.ldl, ldl.data(), sizeof(gf::LdlState) * n_states, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(set_err(GF_ERR_CUDA, "tables"));
     *out = b;
     return GF_OK;
@@ -617,7 +676,8 @@ int gf_destroy_batch(gf_batch* b)
     if (b->evFork) cudaEventDestroy(b->evFork);
     if (b->capS) cudaStreamDestroy(b->capS);
     cudaFree(b->tab.st); cudaFree(b->tab.hist); cudaFree(b->tab.A); cudaFree(b->tab.W);
-    cudaFree(b->tab.n); cudaFree(b->tab.m); cudaFree(b->tab.pos); cudaFree(b->tab.band); cudaFree(b->d_active); cudaFree(b->d_abort);
+    cudaFree(b->tab.n); cudaFree(b->tab.m); cudaFree(b->tab.pos); cudaFree(b->tab.band); cudaFree(b->tab.ldl);
+    cudaFree(b->d_active); cudaFree(b->d_abort);
     if (b->gather_host) cudaFreeHost(b->gather_host);
     delete b;
     return GF_OK;

@@ -1176,53 +1176,74 @@ int build_coarse_map(gf_grid* g)
 // The coarsest inverse from the banded LDL^T factorisation (ldl.cuh): the free-DOF matrix
 // assembled into Ainv (m x m), factored in place by blocks of LDL_C pivots, the inverse
 // formed block by block from the last into Agj (m x m), then expanded into Ainv (n x n).
-int build_coarse_inverse_ldl(gf_grid* g)
+gf::LdlState ldl_state(gf_grid* g)
+{
+    gf::LdlState S;
+    S.M = g->Ainv;
+    S.Z = g->Agj;
+    S.dinv = g->ldl_ws;
+    S.Xs = S.dinv + g->nc;
+    S.Qs = S.Xs + (long long)g->nc * gf::LDL_C;
+    S.m = g->ncf;
+    S.b = g->cband;
+    return S;
+}
+
+// The free-DOF matrix of the coarsest level into M (the first step of either inverse).
+int assemble_coarse_free(gf_grid* g, double* M)
 {
     Level& c = g->lv[g->L - 1];
-    const int n = g->nc, m = g->ncf, b = g->cband;
-    double* M = g->Ainv;
-    double* Z = g->Agj;
-    double* dinv = g->ldl_ws;
-    double* Xs = dinv + n;
-    double* Qs = Xs + (long long)n * gf::LDL_C;
+    const long long m = g->ncf;
     if (g->coarse_kind == GF_COARSE_GALERKIN && g->L > 1)
-        LAUNCH(g, nblk((long long)m * m), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, M, c.dims(),
-               (const int*)g->cidx, m);
+        LAUNCH(g, nblk(m * m), 256, gf::gal_assemble_kernel, (const double*)c.Ke64, M, c.dims(), (const int*)g->cidx,
+               (int)m);
     else
-        LAUNCH(g, nblk((long long)m * m), 256, gf::coarse_assemble_kernel, c.E64, M, c.dims(), g->K0d,
-               (const int*)g->cidx, m);
-    constexpr int C = gf::LDL_C, W = gf::LDL_WARPS;
-    for (int j0 = 0; j0 < m; j0 += C) {   // A = L D L^T
-        const int cb = std::min(C, m - j0), j1 = j0 + cb;
-        LAUNCH(g, 1, 512, gf::ldl_diag_kernel, M, m, j0, cb, dinv);
-        if (j1 >= m) break;
-        const int r1 = gf::ldl_band_end(m, j1, b);
-        LAUNCH(g, (r1 - j1 + W - 1) / W, W * 32, gf::ldl_panel_kernel, M, m, j0, cb, r1, (const double*)dinv);
-        const int T = (r1 - j1 + 15) / 16;
-        LAUNCH(g, T * (T + 1) / 2, 256, gf::ldl_update_kernel, M, m, j0, cb, r1);
+        LAUNCH(g, nblk(m * m), 256, gf::coarse_assemble_kernel, c.E64, M, c.dims(), g->K0d, (const int*)g->cidx,
+               (int)m);
+    return GF_OK;
+}
+
+// Dynamic shared memory of the inverse's row and Y kernels (single and batched), once.
+bool ldl_smem_opt_in()
+{
+    static const bool ok = [] {
+        const int bytes = 200 * 1024;
+        bool r = true;
+        for (const void* k : {(const void*)gf::ldl_inv_rows_kernel, (const void*)gf::ldl_inv_diag_kernel,
+                              (const void*)gf::ldl_inv_rows_batch_kernel, (const void*)gf::ldl_inv_diag_batch_kernel})
+            r = r && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+        return r;
+    }();
+    return ok;
+}
+
+int build_coarse_inverse_ldl(gf_grid* g)
+{
+    const gf::LdlState S = ldl_state(g);
+    const int m = S.m;
+    RET(assemble_coarse_free(g, S.M));
+    if (!ldl_smem_opt_in()) return set_err(GF_ERR_CUDA, "shared memory of the LDL^T inverse kernels");
+    int j0, c, r1;
+    for (int s = 0; gf::ldl_factor_step(m, S.b, s, j0, c, r1); ++s) {   // A = L D L^T
+        LAUNCH(g, 1, 512, gf::ldl_diag_kernel, S, j0, c);
+        if (j0 + c >= m) break;
+        LAUNCH(g, gf::ldl_panel_ctas(j0 + c, r1), gf::LDL_WARPS * 32, gf::ldl_panel_kernel, S, j0, c, r1);
+        LAUNCH(g, gf::ldl_update_ctas(j0 + c, r1), 256, gf::ldl_update_kernel, S, j0, c, r1);
     }
-    static const bool smem_ok =   // the rows and Y kernels stage the band's rows: up to 227 KB
-        cudaFuncSetAttribute((const void*)gf::ldl_inv_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024) == cudaSuccess &&
-        cudaFuncSetAttribute((const void*)gf::ldl_inv_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024) == cudaSuccess;
-    if (!smem_ok) return set_err(GF_ERR_CUDA, "shared memory of ldl_inv_rows_kernel");
-    for (int j0 = (m - 1) / C * C; m > 0 && j0 >= 0; j0 -= C) {   // Z = A^-1, last block first
-        const int cb = std::min(C, m - j0), j1 = j0 + cb;
-        const int kend = gf::ldl_band_end(m, j1, b);
-        if (j1 < m) {
-            const size_t smem = sizeof(double) * ((size_t)C * (C + 1) + (size_t)(kend - j1) * (C + W));
-            if (smem > 200 * 1024) return set_err(GF_ERR_ARG, "coarsest band too wide for the LDL^T inverse");
-            LAUNCH_SMEM(g, (m - j1 + W - 1) / W, W * 32, smem, gf::ldl_inv_rows_kernel, (const double*)M, Z, m, j0, cb,
-                        kend, Xs);
-        }
-        LAUNCH_SMEM(g, cb, W * 32, sizeof(double) * (size_t)(kend - j1) * (C + 1), gf::ldl_inv_diag_kernel,
-                    (const double*)M, m, j0, cb, kend, (const double*)Xs, (const double*)dinv, Qs);
-        LAUNCH(g, (cb + W - 1) / W, W * 32, gf::ldl_inv_diag2_kernel, (const double*)M, Z, m, j0, cb,
-               (const double*)Qs);
+    int kend;
+    for (int s = 0; gf::ldl_inverse_step(m, S.b, s, j0, c, kend); ++s) {   // Z = A^-1, last block first
+        const int j1 = j0 + c;
+        if (gf::ldl_rows_smem(kend - j1) > 200 * 1024)
+            return set_err(GF_ERR_ARG, "coarsest band too wide for the LDL^T inverse");
+        if (j1 < m)
+            LAUNCH_SMEM(g, gf::ldl_rows_ctas(m, j1), gf::LDL_WARPS * 32, gf::ldl_rows_smem(kend - j1),
+                        gf::ldl_inv_rows_kernel, S, j0, c, kend);
+        LAUNCH_SMEM(g, c, gf::LDL_WARPS * 32, gf::ldl_diag_smem(kend - j1), gf::ldl_inv_diag_kernel, S, j0, c, kend);
+        LAUNCH(g, gf::ldl_diag2_ctas(c), gf::LDL_WARPS * 32, gf::ldl_inv_diag2_kernel, S, j0, c);
     }
-    LAUNCH(g, std::min<long long>(nblk((long long)n * n), 4LL * g->sms), 256, gf::sym_expand_kernel, (const double*)Z,
-           m, (const int*)g->cpos, g->Ainv, n);
+    const long long n = g->nc;
+    LAUNCH(g, std::min<long long>(nblk(n * n), 4LL * g->sms), 256, gf::sym_expand_kernel, (const double*)S.Z, m,
+           (const int*)g->cpos, g->Ainv, (int)n);
     return GF_OK;
 }
 

@@ -85,14 +85,46 @@ __host__ __device__ inline int ldl_band_end(int m, int j1, int b)
     return min(m, j1 + b);
 }
 
+// Step s of the factor: block J = [j0, j0 + c), band rows [j0 + c, r1); false past the
+// last block.
+__host__ __device__ inline bool ldl_factor_step(int m, int b, int s, int& j0, int& c, int& r1)
+{
+    j0 = LDL_C * s;
+    if (j0 >= m) return false;
+    c = min(LDL_C, m - j0);
+    r1 = ldl_band_end(m, j0 + c, b);
+    return true;
+}
+
+// Step s of the inverse: the blocks from the last one back; band rows [j0 + c, kend).
+__host__ __device__ inline bool ldl_inverse_step(int m, int b, int s, int& j0, int& c, int& kend)
+{
+    const int blk = (m + LDL_C - 1) / LDL_C - 1 - s;
+    if (blk < 0) return false;
+    j0 = LDL_C * blk;
+    c = min(LDL_C, m - j0);
+    kend = ldl_band_end(m, j0 + c, b);
+    return true;
+}
+
+// One coarsest matrix and its buffers: M (m x m: A, then its factor), Z (m x m: the
+// inverse), dinv (m), Xs (m x LDL_C), Qs (LDL_C x LDL_C); b the band.
+struct LdlState {
+    double* M;
+    double* Z;
+    double* dinv;
+    double* Xs;
+    double* Qs;
+    int m, b;
+};
+
 // 1a. Factor the diagonal block J = [j0, j0 + c) of M (its lower triangle already holds
 // A_JJ minus the earlier blocks' updates): afterwards M[j0+r][j0+t] = L_rt (r > t) and
 // M[j0+t][j0+t] = d_t; dinv[j0+t] = 1 / d_t. One CTA of 512 threads, one barrier per
 // pivot: the trailing entries are updated from pivot t's unscaled column (S keeps it; L is
 // scaled once at the end), and the thread that finishes the next pivot forms its
 // reciprocal.
-__global__ void __launch_bounds__(512) ldl_diag_kernel(double* __restrict__ M, int m, int j0, int c,
-                                                       double* __restrict__ dinv)
+__device__ __forceinline__ void ldl_diag_body(double* __restrict__ M, int m, int j0, int c, double* __restrict__ dinv)
 {
     __shared__ double S[LDL_C][LDL_C + 1];
     __shared__ double ip[LDL_C];
@@ -167,15 +199,15 @@ __device__ __forceinline__ void ldl_load_ljj(const double* __restrict__ M, int m
 
 // 1b. The band rows below block J: L_rJ from (L_rJ D_J) L_JJ^T = M_rJ by the forward
 // substitution, then the scaling by 1 / d. One warp per row r in [j1, band end).
-__global__ void __launch_bounds__(LDL_WARPS * 32) ldl_panel_kernel(double* __restrict__ M, int m, int j0, int c,
-                                                                    int r1, const double* __restrict__ dinv)
+__device__ __forceinline__ void ldl_panel_body(double* __restrict__ M, int m, int j0, int c, int r1,
+                                               const double* __restrict__ dinv, int bid)
 {
     __shared__ double Lj[LDL_C][LDL_C + 1];
     ldl_load_ljj(M, m, j0, c, Lj);
     ldl_cp_wait();
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int r = j0 + c + blockIdx.x * LDL_WARPS + (threadIdx.x >> 5);
+    const int r = j0 + c + bid * LDL_WARPS + (threadIdx.x >> 5);
     if (r >= r1) return;   // whole warps leave together
     double* row = M + (long long)r * m + j0;
     double acc = lane < c ? row[lane] : 0.0;
@@ -186,10 +218,10 @@ __global__ void __launch_bounds__(LDL_WARPS * 32) ldl_panel_kernel(double* __res
 // 1c. The band below block J loses L_rJ D_J L_qJ^T: entries (r, q), j1 <= q <= r < r1, as
 // 16 x 16 tiles of the lower triangle (tile b in row-major order over the tiles with
 // tq <= tp). The c products of an entry run in pivot order; d_t is read from the diagonal.
-__global__ void __launch_bounds__(256) ldl_update_kernel(double* __restrict__ M, int m, int j0, int c, int r1)
+__device__ __forceinline__ void ldl_update_body(double* __restrict__ M, int m, int j0, int c, int r1, int bid)
 {
     __shared__ double Lr[16][LDL_C + 1], Wq[16][LDL_C + 1];
-    int b = blockIdx.x, tp = 0;
+    int b = bid, tp = 0;
     while (b > tp) {   // lower tiles row by row: row tp holds tp + 1 tiles
         b -= tp + 1;
         ++tp;
@@ -217,9 +249,8 @@ __global__ void __launch_bounds__(256) ldl_update_kernel(double* __restrict__ M,
 // transpose, to Z[J][i]. One warp per row; lane t owns column j0 + t. The band rows
 // [j1, kend) also keep X in Xs (row-major, LDL_C wide) for ldl_inv_diag_kernel. The
 // CTA stages the band's L rows and each warp its row of Z in shared memory.
-__global__ void __launch_bounds__(LDL_WARPS * 32) ldl_inv_rows_kernel(const double* __restrict__ M, double* __restrict__ Z,
-                                                                       int m, int j0, int c, int kend,
-                                                                       double* __restrict__ Xs)
+__device__ __forceinline__ void ldl_inv_rows_body(const double* __restrict__ M, double* __restrict__ Z, int m, int j0,
+                                                  int c, int kend, double* __restrict__ Xs, int bid)
 {
     extern __shared__ __align__(16) double ldl_smem[];
     const int j1 = j0 + c, nk = kend - j1;
@@ -233,7 +264,7 @@ __global__ void __launch_bounds__(LDL_WARPS * 32) ldl_inv_rows_kernel(const doub
         else Lb[e] = 0.0;
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int i = j1 + blockIdx.x * LDL_WARPS + wid;
+    const int i = j1 + bid * LDL_WARPS + wid;
     double* zr = Zr + (long long)wid * nk;
     if (i < m)
         for (int k = lane; k < nk; k += 32) ldl_cp8(zr + k, Z + (long long)i * m + j1 + k);
@@ -253,15 +284,14 @@ __global__ void __launch_bounds__(LDL_WARPS * 32) ldl_inv_rows_kernel(const doub
 // over the band rows): the sum, split over the CTA's warps in k (each warp one stretch,
 // added in warp order), then the backward substitution by warp 0. One CTA per row s; Q to
 // Qs (LDL_C x LDL_C).
-__global__ void __launch_bounds__(LDL_WARPS * 32) ldl_inv_diag_kernel(const double* __restrict__ M, int m, int j0, int c,
-                                                                       int kend, const double* __restrict__ Xs,
-                                                                       const double* __restrict__ dinv,
-                                                                       double* __restrict__ Qs)
+__device__ __forceinline__ void ldl_inv_diag_body(const double* __restrict__ M, int m, int j0, int c, int kend,
+                                                  const double* __restrict__ Xs, const double* __restrict__ dinv,
+                                                  double* __restrict__ Qs, int s)
 {
     extern __shared__ __align__(16) double ldl_smem[];
     __shared__ double Lj[LDL_C][LDL_C + 1];
     __shared__ double part[LDL_WARPS][LDL_C];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, s = blockIdx.x, j1 = j0 + c;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, j1 = j0 + c;
     const int nk = kend - j1, per = (nk + LDL_WARPS - 1) / LDL_WARPS;
     double* Lc = ldl_smem;          // [nk]: L[j1 + k][j0 + s]
     double* Xk = ldl_smem + nk;     // [nk][LDL_C]: the band rows of X
@@ -286,15 +316,14 @@ __global__ void __launch_bounds__(LDL_WARPS * 32) ldl_inv_diag_kernel(const doub
 // substitution z_s = Q_sw - sum_{u>s} L_us z_u (lane s owns z_s). One warp per column w,
 // LDL_WARPS columns per CTA; the upper entries (s <= w) are kept and mirrored, so Z_JJ is
 // exactly symmetric.
-__global__ void __launch_bounds__(LDL_WARPS * 32) ldl_inv_diag2_kernel(const double* __restrict__ M,
-                                                                        double* __restrict__ Z, int m, int j0, int c,
-                                                                        const double* __restrict__ Qs)
+__device__ __forceinline__ void ldl_inv_diag2_body(const double* __restrict__ M, double* __restrict__ Z, int m, int j0,
+                                                   int c, const double* __restrict__ Qs, int bid)
 {
     __shared__ double Lj[LDL_C][LDL_C + 1];
     ldl_load_ljj(M, m, j0, c, Lj);
     ldl_cp_wait();
     __syncthreads();
-    const int lane = threadIdx.x & 31, w = blockIdx.x * LDL_WARPS + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, w = bid * LDL_WARPS + (threadIdx.x >> 5);
     if (w >= c) return;   // whole warps leave together
     double acc = lane < c ? Qs[lane * LDL_C + w] : 0.0;
     acc = ldl_bwd_row(acc, Lj, c, lane);
@@ -302,6 +331,107 @@ __global__ void __launch_bounds__(LDL_WARPS * 32) ldl_inv_diag2_kernel(const dou
         Z[(long long)(j0 + lane) * m + j0 + w] = acc;
         Z[(long long)(j0 + w) * m + j0 + lane] = acc;
     }
+}
+
+// ---- launches: one matrix (the step's block passed in), or a batch of them in lockstep
+// (state blockIdx.z, its block of step s derived from its own size and band; CTAs past a
+// state's work leave). Same bodies, so a batched state is bit-identical to one grid.
+__global__ void __launch_bounds__(512) ldl_diag_kernel(LdlState S, int j0, int c)
+{
+    ldl_diag_body(S.M, S.m, j0, c, S.dinv);
+}
+__global__ void __launch_bounds__(LDL_WARPS * 32) ldl_panel_kernel(LdlState S, int j0, int c, int r1)
+{
+    ldl_panel_body(S.M, S.m, j0, c, r1, S.dinv, blockIdx.x);
+}
+__global__ void __launch_bounds__(256) ldl_update_kernel(LdlState S, int j0, int c, int r1)
+{
+    ldl_update_body(S.M, S.m, j0, c, r1, blockIdx.x);
+}
+__global__ void __launch_bounds__(LDL_WARPS * 32) ldl_inv_rows_kernel(LdlState S, int j0, int c, int kend)
+{
+    ldl_inv_rows_body(S.M, S.Z, S.m, j0, c, kend, S.Xs, blockIdx.x);
+}
+__global__ void __launch_bounds__(LDL_WARPS * 32) ldl_inv_diag_kernel(LdlState S, int j0, int c, int kend)
+{
+    ldl_inv_diag_body(S.M, S.m, j0, c, kend, S.Xs, S.dinv, S.Qs, blockIdx.x);
+}
+__global__ void __launch_bounds__(LDL_WARPS * 32) ldl_inv_diag2_kernel(LdlState S, int j0, int c)
+{
+    ldl_inv_diag2_body(S.M, S.Z, S.m, j0, c, S.Qs, blockIdx.x);
+}
+
+// CTAs each launch needs for a block (the batched launches take the largest over states).
+__host__ __device__ inline int ldl_panel_ctas(int j1, int r1) { return (r1 - j1 + LDL_WARPS - 1) / LDL_WARPS; }
+__host__ __device__ inline int ldl_update_ctas(int j1, int r1)
+{
+    const int T = (r1 - j1 + 15) / 16;
+    return T * (T + 1) / 2;
+}
+__host__ __device__ inline int ldl_rows_ctas(int m, int j1) { return (m - j1 + LDL_WARPS - 1) / LDL_WARPS; }
+__host__ __device__ inline int ldl_diag2_ctas(int c) { return (c + LDL_WARPS - 1) / LDL_WARPS; }
+__host__ __device__ inline size_t ldl_rows_smem(int nk)
+{
+    return sizeof(double) * ((size_t)LDL_C * (LDL_C + 1) + (size_t)nk * (LDL_C + LDL_WARPS));
+}
+__host__ __device__ inline size_t ldl_diag_smem(int nk) { return sizeof(double) * (size_t)nk * (LDL_C + 1); }
+
+__global__ void __launch_bounds__(512) ldl_diag_batch_kernel(const LdlState* __restrict__ st,
+                                                             const int* __restrict__ active, int s)
+{
+    int j0, c, r1;
+    if (!active[blockIdx.z]) return;
+    const LdlState S = st[blockIdx.z];
+    if (!ldl_factor_step(S.m, S.b, s, j0, c, r1)) return;
+    ldl_diag_body(S.M, S.m, j0, c, S.dinv);
+}
+__global__ void __launch_bounds__(LDL_WARPS * 32) ldl_panel_batch_kernel(const LdlState* __restrict__ st,
+                                                                          const int* __restrict__ active, int s)
+{
+    int j0, c, r1;
+    if (!active[blockIdx.z]) return;
+    const LdlState S = st[blockIdx.z];
+    if (!ldl_factor_step(S.m, S.b, s, j0, c, r1) || j0 + c >= S.m) return;
+    if ((int)blockIdx.x >= ldl_panel_ctas(j0 + c, r1)) return;
+    ldl_panel_body(S.M, S.m, j0, c, r1, S.dinv, blockIdx.x);
+}
+__global__ void __launch_bounds__(256) ldl_update_batch_kernel(const LdlState* __restrict__ st,
+                                                               const int* __restrict__ active, int s)
+{
+    int j0, c, r1;
+    if (!active[blockIdx.z]) return;
+    const LdlState S = st[blockIdx.z];
+    if (!ldl_factor_step(S.m, S.b, s, j0, c, r1) || j0 + c >= S.m) return;
+    if ((int)blockIdx.x >= ldl_update_ctas(j0 + c, r1)) return;
+    ldl_update_body(S.M, S.m, j0, c, r1, blockIdx.x);
+}
+__global__ void __launch_bounds__(LDL_WARPS * 32) ldl_inv_rows_batch_kernel(const LdlState* __restrict__ st,
+                                                                             const int* __restrict__ active, int s)
+{
+    int j0, c, kend;
+    if (!active[blockIdx.z]) return;
+    const LdlState S = st[blockIdx.z];
+    if (!ldl_inverse_step(S.m, S.b, s, j0, c, kend) || j0 + c >= S.m) return;
+    if ((int)blockIdx.x >= ldl_rows_ctas(S.m, j0 + c)) return;
+    ldl_inv_rows_body(S.M, S.Z, S.m, j0, c, kend, S.Xs, blockIdx.x);
+}
+__global__ void __launch_bounds__(LDL_WARPS * 32) ldl_inv_diag_batch_kernel(const LdlState* __restrict__ st,
+                                                                             const int* __restrict__ active, int s)
+{
+    int j0, c, kend;
+    if (!active[blockIdx.z]) return;
+    const LdlState S = st[blockIdx.z];
+    if (!ldl_inverse_step(S.m, S.b, s, j0, c, kend) || (int)blockIdx.x >= c) return;
+    ldl_inv_diag_body(S.M, S.m, j0, c, kend, S.Xs, S.dinv, S.Qs, blockIdx.x);
+}
+__global__ void __launch_bounds__(LDL_WARPS * 32) ldl_inv_diag2_batch_kernel(const LdlState* __restrict__ st,
+                                                                              const int* __restrict__ active, int s)
+{
+    int j0, c, kend;
+    if (!active[blockIdx.z]) return;
+    const LdlState S = st[blockIdx.z];
+    if (!ldl_inverse_step(S.m, S.b, s, j0, c, kend) || (int)blockIdx.x >= ldl_diag2_ctas(c)) return;
+    ldl_inv_diag2_body(S.M, S.Z, S.m, j0, c, S.Qs, blockIdx.x);
 }
 
 }  // namespace gf
