@@ -434,6 +434,8 @@ int coarse_correct(gf_grid* g, int l, T* x, const T* xc, T* c, const T* r, doubl
 
 template <typename T>
 int coarsest_solve(gf_grid* g, const T* b, T* x, const int* halt);
+template <typename TB, typename TX>
+int free_gemv(gf_grid* g, const TB* b, TX* x, const int* halt);
 
 // One V-cycle z = B v in precision T (Table solver-config: 2:1 trilinear transfer,
 // damped node-block Jacobi smoothing, coarsest solve by the FP64 dense inverse).
@@ -447,6 +449,7 @@ int vcycle_impl(gf_grid* g, const double* v, double* z, int nu1, int nu2, T omeg
     if (L == 1) {
         double* bm = g->lv[0].b64;
         LAUNCH(g, 2 * g->sms, 256, (gf::masked_convert_kernel<double, double>), v, bm, g->ndof, NX0, halt, (const uint8_t*)g->lv[0].fix);
+        if (g->coarse_ldl) return free_gemv<double, double>(g, (const double*)bm, z, halt);
         LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<double, double>), g->Ainv, (const double*)bm, z,
                g->nc, halt);
         return GF_OK;
@@ -933,6 +936,21 @@ int inner_fgmres(gf_grid* g, int l, const T* r, T* d, int steps, const int* halt
 }
 
 // The coarsest level's solve x = A_c^{-1} b: the dense FP64 inverse, or (coarse_steps > 0)
+// x = A^-1 b on the coarsest level with the free-DOF inverse the LDL^T path leaves in Agj
+// (free_gemv_kernel; eight rows per CTA).
+template <typename TB, typename TX>
+int free_gemv(gf_grid* g, const TB* b, TX* x, const int* halt)
+{
+    const int m = g->ncf;
+    const size_t smem = sizeof(double) * (size_t)std::max(1, m);
+    static const bool ok = cudaFuncSetAttribute((const void*)gf::free_gemv_kernel<TB, TX>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024) == cudaSuccess;
+    if (!ok) return set_err(GF_ERR_CUDA, "shared memory of free_gemv_kernel");
+    LAUNCH_SMEM(g, std::max(1, (m + 7) / 8), 256, smem, (gf::free_gemv_kernel<TB, TX>), (const double*)g->Agj, m,
+                (const int*)g->cidx, b, x, g->nc, (const int*)g->cpos, halt);
+    return GF_OK;
+}
+
 // Table solver-config's inner Krylov solve on the coarse level, from x = 0.
 template <typename T>
 int coarsest_solve(gf_grid* g, const T* b, T* x, const int* halt)
@@ -950,6 +968,7 @@ int coarsest_solve(gf_grid* g, const T* b, T* x, const int* halt)
         const int nb = (int)std::min<long long>(g->fc_nb, std::max<long long>(1, (c.ndof + 1023) / 1024));
         return inner_fgmres<T>(g, g->L - 1, b, x, g->coarse_steps, halt, nb);
     }
+    if (g->coarse_ldl) return free_gemv<T, T>(g, b, x, halt);
     LAUNCH(g, nblk(32LL * g->nc), 256, (gf::dense_gemv_kernel<T, T>), (const double*)g->Ainv, b, x, g->nc, halt);
     return GF_OK;
 }

@@ -503,6 +503,86 @@ dense_gemv_kernel(const double* __restrict__ A, const TB* __restrict__ b, TX* __
     if (lane == 0) x[warp] = (TX)s;
 }
 
+// Coarsest solve with the inverse of the free-DOF operator (m x m row-major FP64, the
+// LDL^T path's Z): x[idx[r]] = sum_c Z[r][c] b[idx[c]], and x = 0 on the fixed DOFs
+// (pos < 0). Each CTA stages b's free entries in shared memory (as FP64), every thread's
+// index and value loads issued eight at a time; one warp per row. With m even the row is
+// read as 16-byte pairs, lane p taking pairs p, p + 32, ... into eight partial sums
+// (columns 2p and 2p + 1 of the four pairs in flight), added in a fixed tree; with m odd,
+// single columns into four partial sums. Then the warp's lanes in a fixed tree.
+template <typename TB, typename TX>
+__global__ void __launch_bounds__(256)
+free_gemv_kernel(const double* __restrict__ Z, int m, const int* __restrict__ idx, const TB* __restrict__ b,
+                 TX* __restrict__ x, int n, const int* __restrict__ pos, const int* __restrict__ halt)
+{
+    if (halt != nullptr && *halt != 0) return;
+    extern __shared__ double gemv_b[];
+    for (int c0 = threadIdx.x; c0 < m; c0 += 8 * blockDim.x) {
+        int ix[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = c0 + u * blockDim.x;
+            ix[u] = c < m ? idx[c] : 0;
+        }
+        double bv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) bv[u] = (double)b[ix[u]];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = c0 + u * blockDim.x;
+            if (c < m) gemv_b[c] = bv[u];
+        }
+    }
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+        if (pos[q] < 0) x[q] = TX(0);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= m) return;
+    const double* row = Z + (long long)r * m;
+    double s;
+    if ((m & 1) == 0) {   // rows start on 16-byte boundaries
+        const double2* row2 = reinterpret_cast<const double2*>(row);
+        const int m2 = m >> 1;
+        double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int p = lane;
+        for (; p + 96 < m2; p += 128) {
+            double2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = row2[p + 32 * u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[2 * u] = fma(v[u].x, gemv_b[2 * (p + 32 * u)], a[2 * u]);
+                a[2 * u + 1] = fma(v[u].y, gemv_b[2 * (p + 32 * u) + 1], a[2 * u + 1]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (p + 32 * u < m2) {
+                const double2 v = row2[p + 32 * u];
+                a[2 * u] = fma(v.x, gemv_b[2 * (p + 32 * u)], a[2 * u]);
+                a[2 * u + 1] = fma(v.y, gemv_b[2 * (p + 32 * u) + 1], a[2 * u + 1]);
+            }
+        s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    } else {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int c = lane;
+        for (; c + 96 < m; c += 128) {
+            s0 = fma(row[c], gemv_b[c], s0);
+            s1 = fma(row[c + 32], gemv_b[c + 32], s1);
+            s2 = fma(row[c + 64], gemv_b[c + 64], s2);
+            s3 = fma(row[c + 96], gemv_b[c + 96], s3);
+        }
+        if (c < m) s0 = fma(row[c], gemv_b[c], s0);
+        if (c + 32 < m) s1 = fma(row[c + 32], gemv_b[c + 32], s1);
+        if (c + 64 < m) s2 = fma(row[c + 64], gemv_b[c + 64], s2);
+        s = (s0 + s1) + (s2 + s3);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) x[idx[r]] = (TX)s;
+}
+
 // Gauss-Jordan inversion of an SPD matrix without pivoting, two pivots per launch on a
 // double-buffered matrix. The step on pivot k maps A to A' with
 //   row k:   A'_kq = A_kq / A_kk            (1 / A_kk at q = k)
