@@ -174,7 +174,7 @@ struct gf_grid {
     int m_alloc = 0;
     long long ldk = 0;                // leading dimension of V, Z, Vd: ndof rounded up to 32 (256-byte rows)
     double *V = nullptr, *Z = nullptr, *partial = nullptr, *work = nullptr;
-    int nbc[3][3] = {};               // grid of the FP64 Gram-Schmidt passes (dots, update+dots, update+norm) x NV 8/16/32
+    int nbc[3][4] = {};               // grid of the FP64 Gram-Schmidt passes (dots, update+dots, update+norm) x NV 8/16/24/32
     double* ckx = nullptr;            // iterate of a probe true-residual check
     // fine-level adaptive correction: inner basis V (steps + 1), Z (steps), r, d, q, z in the
     // V-cycle's precision (fc_es bytes per entry), the inner solver's state and partial sums
@@ -1411,9 +1411,12 @@ int read_state(gf_grid* g, HostState* hs)
     return GF_OK;
 }
 
-int pick_nv(int nv)
+// Register width of the Gram-Schmidt passes for nv basis vectors: the FP64 passes also
+// have a 24-wide form (17..24 vectors loaded in one group, against a second group of 1..8
+// in the 32-wide one); the double-float passes 8, 16 and 32.
+int pick_nv(int nv, bool dd)
 {
-    return nv <= 8 ? 8 : (nv <= 16 ? 16 : 32);
+    return nv <= 8 ? 8 : (nv <= 16 ? 16 : (nv <= 24 && !dd ? 24 : 32));
 }
 
 template <int NV>
@@ -1421,7 +1424,7 @@ int cgs2_step(gf_grid* g, int j, double* w, int outer)
 {
     const long long n = g->ndof, ld = g->ldk;
     const int nv = j + 1;
-    if (outer == 2) {   // double-float passes on the FP32 pipe; w arrives as wd
+    if constexpr (NV != 24) if (outer == 2) {   // double-float passes on the FP32 pipe; w arrives as wd
         float2* wd = g->Vd + (long long)(j + 1) * ld;
         const int q = NV == 8 ? 0 : (NV == 16 ? 1 : 2);
         LAUNCH(g, g->nbd_k[0][q], gf::DD_THREADS, gf::ddgs_dots_kernel<NV>, (const float2*)g->Vd, ld, nv,
@@ -1433,7 +1436,7 @@ int cgs2_step(gf_grid* g, int j, double* w, int outer)
         LAUNCH(g, 1, 32, gf::arnoldi_tail_kernel, g->st, g->hist, j, NV, g->host_status_dev, 1e-14);
         return GF_OK;
     }
-    const int q = NV == 8 ? 0 : (NV == 16 ? 1 : 2);
+    const int q = NV == 8 ? 0 : (NV == 16 ? 1 : (NV == 24 ? 2 : 3));
     const int b0 = g->nbc[0][q], b1 = g->nbc[1][q], b2 = g->nbc[2][q];
     LAUNCH(g, b0, gf::RED_THREADS, gf::cgs_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
     LAUNCH(g, 1, 32 * 32, gf::reduce_partials_kernel, g->partial, b0, NV + 1, NV + 1, g->st, 0, 1);
@@ -1517,9 +1520,10 @@ int arnoldi_step(gf_grid* g, int j, const gf_solve_opts* o)
     if (o->outer == 2) RET(applyKsplit_dd(g, zj, g->Vd + (long long)(j + 1) * ld, halt));
     else RET(applyOuter(g, zj, w, halt, o->outer));
     if (j + 1 > gf::KRY_NV) RET(cgs2_step_long(g, j, w, o->outer));
-    else switch (pick_nv(j + 1)) {
+    else switch (pick_nv(j + 1, o->outer == 2)) {
         case 8: RET(cgs2_step<8>(g, j, w, o->outer)); break;
         case 16: RET(cgs2_step<16>(g, j, w, o->outer)); break;
+        case 24: RET(cgs2_step<24>(g, j, w, o->outer)); break;
         default: RET(cgs2_step<32>(g, j, w, o->outer)); break;
     }
     if (o->outer == 2)
@@ -2110,17 +2114,17 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     // 256-row tiles; their partial rows share g->partial with the other reductions
     long long partial_rows = (long long)g->nbr * 40;
     {
-        const void* kc[3][3] = {
+        const void* kc[3][4] = {
             {(const void*)gf::cgs_dots_kernel<8>, (const void*)gf::cgs_dots_kernel<16>,
-             (const void*)gf::cgs_dots_kernel<32>},
+             (const void*)gf::cgs_dots_kernel<24>, (const void*)gf::cgs_dots_kernel<32>},
             {(const void*)gf::cgs_update_dots_kernel<8>, (const void*)gf::cgs_update_dots_kernel<16>,
-             (const void*)gf::cgs_update_dots_kernel<32>},
+             (const void*)gf::cgs_update_dots_kernel<24>, (const void*)gf::cgs_update_dots_kernel<32>},
             {(const void*)gf::cgs_update_norm_kernel<8>, (const void*)gf::cgs_update_norm_kernel<16>,
-             (const void*)gf::cgs_update_norm_kernel<32>}};
-        const int nvq[3] = {8, 16, 32};
+             (const void*)gf::cgs_update_norm_kernel<24>, (const void*)gf::cgs_update_norm_kernel<32>}};
+        const int nvq[4] = {8, 16, 24, 32};
         const long long tiles = std::max<long long>(1, (g->ndof + gf::RED_THREADS - 1) / gf::RED_THREADS);
         for (int p = 0; p < 3; ++p)
-            for (int q = 0; q < 3; ++q) {
+            for (int q = 0; q < 4; ++q) {
                 int nb = 0;
                 if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kc[p][q], gf::RED_THREADS, 0) != cudaSuccess ||
                     nb <= 0)
