@@ -590,7 +590,7 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
             for (int c = 0; c < 3; ++c) {
                 float G[8];
 #pragma unroll
-                for (int beta = 0; beta < 8; ++beta) {
+                for (int beta = 1; beta < 8; ++beta) {   // beta = 0 (a rigid translation) carries no force
                     const int bc = (beta >> c) & 1;
                     const int n = ((beta >> ((c + 1) % 3)) & 1) + ((beta >> ((c + 2) % 3)) & 1);
                     float t = (bc == 0 && n == 0) ? 0.f : sd[bc * 3 + n] * m[c][beta];
@@ -607,8 +607,10 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
                     }
                     G[beta] = t;
                 }
+                face[c][0] = carry[c][0] - G[4];
+                carry[c][0] = G[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 1; q < 4; ++q) {
                     face[c][q] = carry[c][q] + (G[q] - G[q + 4]);
                     carry[c][q] = G[q] + G[q + 4];
                 }
