@@ -213,5 +213,15 @@ def test_select_floor_many_matches_each_grid_alone(gf):
         assert a == b and torch.equal(ua, ub) and b["status"] == gf.GF_ACCEPTED
     with pytest.raises(gf.GFError):
         gf.select_floor_many([gs2[0], gs2[0]], [fs2[0], fs2[0]], [us2[0], torch.zeros_like(us2[0])], pol)
+    # a grid that cannot run (no density stored) fails the call with its own error, named by
+    # its position; the other grids still run to completion
+    dims = STATES[0][0]
+    bad = gf.create_grid(*dims, levels=3)
+    fb = bad.cantilever_load(torch.zeros(bad.n_dof, dtype=torch.float64, device="cuda"))
+    with pytest.raises(gf.GFError) as e:
+        gf.select_floor_many([gs2[0], bad], [fs2[0], fb], [us2[0], torch.zeros_like(fb)], pol)
+    assert "grid 1" in str(e.value) and "set_density" in str(e.value)
+    torch.cuda.synchronize()
+    bad.close()
     for g in gs + gs2:
         g.close()
