@@ -32,24 +32,64 @@ struct KState {
 };
 
 // ---------------------------------------------------------------- reductions --
+__host__ __device__ constexpr int pow2_at_least(int v)
+{
+    return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2);
+}
+
+// Sums P values (a power of two <= 32) over the 32 lanes of a warp by transposition: at the
+// level with lane offset o each lane keeps one half of its values (the upper half when its
+// bit o is set), sends the other half to lane ^ o and adds what it receives, so the P
+// values cost P - 1 shuffles and adds instead of 5 P; then the lanes that hold the same
+// value (those sharing their top log2 P bits) add theirs. Lane l returns the warp's sum
+// of value l / (32 / P).
+template <int P>
+__device__ __forceinline__ double warp_transpose_sum(double (&v)[P], int lane)
+{
+#pragma unroll
+    for (int h = P / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const double lo = v[i], hi = v[i + h];
+            v[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, o);
+        }
+    }
+    double s = v[0];
+#pragma unroll
+    for (int o = 16 / P; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// partial[b][q] = sum over the block's threads of acc[q], q < nv: each warp sums its values
+// by transposition (the first 32; an NV of 33 adds its last value by a shuffle tree), then
+// thread q adds the warps' sums in warp order.
 template <int NV>
 __device__ __forceinline__ void block_reduce_store(double (&acc)[NV], int nv, double* __restrict__ out_row)
 {
+    constexpr int NT = NV < 32 ? NV : 32;   // values summed by transposition
+    constexpr int P = pow2_at_least(NT);
+    constexpr int SPREAD = 32 / P;          // lanes that end up with one value
     __shared__ double red[RED_THREADS / 32][NV];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double v[P];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        double v = acc[q];
+    for (int q = 0; q < P; ++q) v[q] = q < NT ? acc[q] : 0.0;
+    const double s = warp_transpose_sum<P>(v, lane);
+    if (lane % SPREAD == 0 && lane / SPREAD < NT) red[warp][lane / SPREAD] = s;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][q] = v;
+    for (int q = NT; q < NV; ++q) {   // NV = 33: the norm slot
+        double t = acc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) red[warp][q] = t;
     }
     __syncthreads();
     if (threadIdx.x < nv) {
-        double s = 0.0;
+        double t = 0.0;
 #pragma unroll
-        for (int w = 0; w < RED_THREADS / 32; ++w) s += red[w][threadIdx.x];
-        out_row[threadIdx.x] = s;
+        for (int w = 0; w < RED_THREADS / 32; ++w) t += red[w][threadIdx.x];
+        out_row[threadIdx.x] = t;
     }
 }
 
