@@ -1131,6 +1131,32 @@ def test_modal_apply_is_independent_of_the_launch_plan(gf, dims, monkeypatch):
     assert relerr(outs[0][0], ref) <= 1e-10
 
 
+@pytest.mark.parametrize("maxn", ["10000", "2000"])
+def test_cluster_coarse_vcycle_matches_level_launches(gf, maxn, monkeypatch):
+    """GF_VC_CLUSTER=<max nodes> (opt-in): the mixed V-cycle's levels from the first one with
+    at most that many nodes run in one cluster launch (its own n x n coarsest GEMV; the sweep's
+    inverse, GF_COARSE_LDL=0, so that it exists). The V-cycle agrees with the per-level
+    launches to FP32 rounding, 1e-5 relative (not bit for bit: the per-level path's FP32
+    kernels and the cluster's scalar node loops round differently), on 64x32x32 with 4
+    levels, levels 1-3 or 2-3 in the cluster."""
+    nx, ny, nz, L = 64, 32, 32, 4
+    monkeypatch.setenv("GF_COARSE_LDL", "0")
+    outs = []
+    for env in (None, maxn):
+        if env is None:
+            monkeypatch.delenv("GF_VC_CLUSTER", raising=False)
+        else:
+            monkeypatch.setenv("GF_VC_CLUSTER", env)
+        g, m, rho = make(gf, nx, ny, nz, L, seed=21, rho_min=1e-4, kind="bernoulli")
+        v = synth.random_vector(m.n_dof, 4) * m.free
+        z = torch.full((g.n_dof,), np.nan, dtype=torch.float64, device="cuda")
+        g.vcycle(dev(v), z, gf.GF_MIXED)
+        outs.append(host(z))
+        g.close()
+    assert not np.isnan(outs[0]).any() and not np.isnan(outs[1]).any()
+    assert relerr(outs[1], outs[0]) <= 1e-5
+
+
 # ------------------------------------------------------------- coarsest inverse -----
 @pytest.mark.parametrize("dims", [(16, 8, 8, 3), (24, 10, 6, 2), (2, 2, 2, 1), (8, 4, 4, 1), (12, 6, 6, 2),
                                   (48, 24, 24, 3)])
