@@ -7,8 +7,8 @@ about a quarter of an hour of CPU).
 
 Calls only oracle/ (and the seeded generators in synth/). The record (probe
 features, candidate floors, per-attempt iterations, flags and recomputed eta) is
-a full-size decision fixture for the GPU path and gives the oracle's own step and
-set-up counts, from which the CPU baseline extrapolates a bounded timing sample.
+a full-size decision fixture for the GPU path (the tests compare the GPU's decision,
+floor, iteration counts and features against it).
 """
 import argparse
 import json
