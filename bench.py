@@ -351,7 +351,8 @@ def arm_config(args, world):
     """The workload both arms report (the reference arm times a bounded sample of it)."""
     return {"workload": WORKLOAD, "n_dof": 3 * 193 * 97 * 97, "states": args.states,
             "step": (f"one Algorithm-1 pass of each of {args.states} states, solved concurrently by "
-                     "gf_select_floor_many (one grid per state, each on its own stream and host thread)"),
+                     "gf_select_floor_many (one grid per state, each on its own stream and host thread, "
+                     "half-SM launch shapes: gf_set_sm_share)"),
             "parallelism": f"replicas x{world}",
             "l2": "inputs larger than L2 (Krylov bases V, Z = 2.66 GB per state solve)"}
 
@@ -408,10 +409,13 @@ def timed_kernel(fn, reps=20):
 
 
 def large_grids(gf, B):
-    """B 192x96x96 grids, each on its own stream, their tip loads and solution vectors."""
+    """B 192x96x96 grids, each on its own stream with the launch shapes that leave half of
+    each SM to the other grids' kernels (set_sm_share), their tip loads and solution vectors."""
     import torch
     streams = [torch.cuda.Stream() for _ in range(B)]
     grids = [gf.create_grid(*LARGE, levels=LEVELS, stream=st) for st in streams]
+    for g in grids:
+        g.set_sm_share(1)
     fs = [g.cantilever_load(torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")) for g in grids]
     return grids, fs, [torch.zeros_like(f) for f in fs], streams
 
@@ -451,6 +455,7 @@ def large_batch(gf, B):
     """B 192x96x96 cantilever grids in one batch (gf_batch) and their tip loads."""
     import torch
     b = gf.Batch([LARGE] * B, levels=LEVELS)
+    b.set_sm_share(1)
     fs = [b.cantilever_load(i, torch.zeros(b.n_dof[i], dtype=torch.float64, device="cuda")) for i in range(B)]
     return b, fs
 
@@ -557,6 +562,7 @@ def comparison_102(gf, dist):
     out["selector"] = {k: meta.get(k) for k in ("states", "train_states", "held_out_accuracy", "label_counts",
                                                 "label_form")}
     b = S._batch_for(dims, W.BATCH_LEVELS, rhos_h)
+    b.set_sm_share(1)
     b.autotune()
     forms = [("batched_mixed_rule", 0, gf.GF_SEL_RULE), ("batched_mixed_learned", 0, gf.GF_SEL_MLP),
              ("batched_mixed_rule_fp64class", 2, gf.GF_SEL_RULE),
@@ -654,9 +660,16 @@ def run_b300(args):
     x = torch.randn(g.n_dof, dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
     xf, yf = x.float(), torch.empty(g.n_dof, dtype=torch.float32, device="cuda")
-    t_k = timed_kernel(lambda: g.apply_K(x, y))
-    t_32 = timed_kernel(lambda: g.apply_K_f32(xf, yf))
+    t_kf = timed_kernel(lambda: g.apply_K(x, y))
+    t_32f = timed_kernel(lambda: g.apply_K_f32(xf, yf))
     t_s = timed_kernel(lambda: g.apply_K_split(x, y))
+    # the headline grids' forms (16x16-column tiles, one CTA per SM), timed alone on grid 0's stream
+    g0 = grids[0]
+    g0.set_density(rhos[0], P_SIMP)
+    g0.set_floor(RHO0)
+    with torch.cuda.stream(streams[0]):
+        t_k = timed_kernel(lambda: g0.apply_K(x, y))
+        t_32 = timed_kernel(lambda: g0.apply_K_f32(xf, yf))
     flops = 1152.0 * g.n_elem                  # 2*24*24 per element and application (dense product)
     sm_max = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2032.0)
     fp64_peak = 148 * 2 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FMAs only
@@ -675,8 +688,8 @@ def run_b300(args):
     native = {"bound": "alu", "achieved": modal_flops / t_k / 1e12, "peak": modal_peak, "unit": "TFLOP/s",
               "frac": modal_flops / t_k / 1e12 / modal_peak,
               "traffic": profiled_traffic("apply_modal_kernel_192x96x96.md", *MODAL_SPAN),
-              "kernel": ("apply_modal_kernel (native FP64 K*u in the sum/difference basis of K0: the Krylov "
-                         "operator and the guard)"),
+              "kernel": ("apply_modal_kernel<16,16> (native FP64 K*u in the sum/difference basis of K0: the "
+                         "Krylov operator and the guard; the headline grids' half-SM tiles, timed alone)"),
               "peak_source": ("derived: 148 SMs x 2 FP64 instructions/clk x sm_max_mhz x "
                               f"{MODAL_FLOPS}/{MODAL_INSTR} flop per instruction of this kernel's mix "
                               "(no measured FP64 peak on this pool)"),
@@ -689,7 +702,7 @@ def run_b300(args):
     stencil = {"bound": "alu", "achieved": flops / t_32 / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                "frac": flops / t_32 / 1e12 / fp32_peak,
                "traffic": None,
-               "kernel": ("modal_stencil_f32_kernel (the FP32 V-cycle's fine-level operator in the sum/difference "
+               "kernel": ("modal_stencil_f32_kernel<16,16> (the FP32 V-cycle's fine-level operator in the sum/difference "
                           "basis; achieved and frac in dense-equivalent flops, 1152 per element, against the FP32 "
                           "FMA peak: it executes ~171 FP32 instructions per element and is issue-bound)"),
                "peak_source": FP32_PEAK_NOTE, "gdofs": g.n_dof / t_32 / 1e9, "ms_per_launch": t_32 * 1e3}
@@ -698,8 +711,14 @@ def run_b300(args):
              "gdofs": g.n_dof / t_s / 1e9, "ms_per_launch": t_s * 1e3,
              "note": "against HBM: its bytes are u, y and the moduli (~10.5 B/DOF); it is issue-bound, far under"}
     split["frac"] = split["achieved"] / hbm
+    full_sm = {"ms_per_launch": t_kf * 1e3, "achieved": modal_flops / t_kf / 1e12, "unit": "TFLOP/s",
+               "frac": modal_flops / t_kf / 1e12 / modal_peak, "gdofs": g.n_dof / t_kf / 1e9,
+               "fp32_stencil_ms_per_launch": t_32f * 1e3,
+               "kernel": ("apply_modal_kernel with the full-SM tiles (32x16 or 16x32 columns, one CTA fills an SM): "
+                          "the single-state form, same peak")}
     roofline = dict(native)
-    roofline["other_kernels"] = {"vcycle_stencil_fp32": stencil, "split_operator": split}
+    roofline["other_kernels"] = {"vcycle_stencil_fp32": stencil, "split_operator": split,
+                                 "apply_modal_full_sm": full_sm}
 
     extras = {"single_state_192x96x96": single, "batched_lockstep_192x96x96": lockstep}
     if not args.no_extras:

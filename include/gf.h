@@ -244,6 +244,21 @@ int gf_set_floor(gf_grid* g, double rho_min);
 #define GF_COARSE_GALERKIN      1
 int gf_set_coarse_operator(gf_grid* g, int kind);
 
+/* Launch shapes for a grid whose solves share the GPU with other grids' solves (streams
+ * running at once, e.g. gf_select_floor_many). share = 0 (default): every kernel is sized
+ * to fill the SMs, the fastest shapes for one solve alone. share = 1: the FP64 modal K*u
+ * and the FP32 fine-level operator run 16x16-column tiles planned for one CTA per SM, and
+ * the FP64 Gram-Schmidt passes half of their resident blocks (the update-and-dots pass in
+ * 128-thread blocks), so each takes about half of an SM's registers and another grid's
+ * kernel can run beside it: on B300 the FP64 kernels issue from a small fraction of the
+ * SM's instruction slots and the FP32 V-cycle from the rest. Results do not depend on it
+ * (the operator is bit-identical under every launch plan; the Gram-Schmidt sums change
+ * their block partition, within rounding). Re-plans and re-times the modal kernels on the
+ * level-0 buffers, so switching clears the floor (gf_set_floor again before solving) and
+ * the captured steps; call it before gf_set_density's first solve, off any capture.
+ * Errors: GF_ERR_ARG for share outside {0, 1}. */
+int gf_set_sm_share(gf_grid* g, int share);
+
 /* f = unit point load in -z at the node (nx, ny/2, nz/2) (n_dof doubles, device);
  * the cantilever of Table geometries. */
 int gf_cantilever_load(gf_grid* g, double* f);
@@ -432,6 +447,11 @@ int gf_batch_solution(gf_batch* b, int i, double* u);
  * inverses then assemble each state's Galerkin coarsest operator, and every state's
  * result stays bit-identical to its single grid's. Drops the captured steps. */
 int gf_batch_set_coarse_operator(gf_batch* b, int kind);
+/* Launch shapes of every state's grid (as gf_set_sm_share for one grid): 1 = the half-SM
+ * shapes, so that the states' chains, which the step graphs run concurrently, share the
+ * SMs; 0 = full-SM shapes (default). Clears the floors and drops the captured steps.
+ * Errors: GF_ERR_ARG for share outside {0, 1}. */
+int gf_batch_set_sm_share(gf_batch* b, int share);
 /* Autotuner: time the node stencils at 64/128/256 threads per block once per
  * distinct grid shape and keep the fastest (results do not depend on the pick).
  * tpb_out (host, optional): 2*n_states ints, [FP64, FP32] block size per state. */

@@ -39,7 +39,7 @@ EXPORTED = [
     "gf_batch_solution", "gf_batch_autotune", "gf_batch_select_floor", "gf_batch_stats",
     "gf_mlp_create", "gf_mlp_destroy", "gf_mlp_set_norm", "gf_mlp_get_params", "gf_mlp_forward",
     "gf_mlp_loss_grad", "gf_mlp_train", "gf_mlp_predict", "gf_select_features", "gf_apply_K_split",
-    "gf_set_coarse_operator", "gf_set_geometry", "gf_bridge_load", "gf_batch_set_coarse_operator",
+    "gf_set_coarse_operator", "gf_set_sm_share", "gf_batch_set_sm_share", "gf_set_geometry", "gf_bridge_load", "gf_batch_set_coarse_operator",
 ]
 
 
@@ -106,6 +106,8 @@ def lib():
         "gf_set_density": [P, P, c_double],
         "gf_set_floor": [P, c_double],
         "gf_set_coarse_operator": [P, c_int],
+        "gf_set_sm_share": [P, c_int],
+        "gf_batch_set_sm_share": [P, c_int],
         "gf_cantilever_load": [P, P],
         "gf_set_geometry": [P, c_int],
         "gf_bridge_load": [P, P],
@@ -281,6 +283,12 @@ class Grid:
         """gf_set_coarse_operator: GF_COARSE_REDISCRETISED or GF_COARSE_GALERKIN, used from
         the next set_floor on (switching clears the floor)."""
         _check(lib().gf_set_coarse_operator(self._h, int(kind)))
+
+    def set_sm_share(self, share):
+        """gf_set_sm_share: 1 = launch shapes that leave half of each SM to other grids' solves
+        running at once (select_floor_many), 0 = shapes that fill the SMs (default).
+        Switching clears the floor."""
+        _check(lib().gf_set_sm_share(self._h, int(share)))
 
     def cantilever_load(self, f):
         _check(lib().gf_cantilever_load(self._h, _ptr(f, _torch().float64, self.n_dof, "f")))
@@ -523,6 +531,10 @@ class Batch:
     def set_coarse_operator(self, kind):
         """gf_batch_set_coarse_operator: GF_COARSE_REDISCRETISED or GF_COARSE_GALERKIN for every state."""
         _check(lib().gf_batch_set_coarse_operator(self._h, int(kind)))
+
+    def set_sm_share(self, share):
+        """gf_batch_set_sm_share: half-SM launch shapes (1) or full-SM ones (0) for every state."""
+        _check(lib().gf_batch_set_sm_share(self._h, int(share)))
 
     def autotune(self):
         out = (c_int * (2 * len(self)))()

@@ -717,6 +717,15 @@ int gf_batch_set_coarse_operator(gf_batch* b, int kind)
     return GF_OK;
 }
 
+int gf_batch_set_sm_share(gf_batch* b, int share)
+{
+    if (!b) return set_err(GF_ERR_ARG, "null batch");
+    for (gf_grid* g : b->g) RET(gf_set_sm_share(g, share));
+    batch_drop_graphs(b);   // the captured step graphs hold the other launch shapes
+    b->key_prec = -1;
+    return GF_OK;
+}
+
 int gf_batch_autotune(gf_batch* b, int* tpb_out)
 {
     if (!b) return set_err(GF_ERR_ARG, "null batch");

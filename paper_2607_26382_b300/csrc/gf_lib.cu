@@ -138,9 +138,10 @@ struct gf_grid {
     gf::ModalCoefF Kmodal32;          // the same in FP32 with K0's node blocks (modal_stencil_f32_kernel)
     bool modal_f32 = true;            // level-0 FP32 stencils in the modal basis (GF_MODAL_F32=0: node stencils)
     int4* modal_items = nullptr;      // work items of the modal FP32 fine level (tiles overlapping by one column)
-    int modal_n = 0, modal_bx = 32;   // item count; CTA tile 32 x 16 or 16 x 32 element columns
+    int modal_n = 0, modal_bx = 32, modal_by = 16;   // item count; CTA tile 32 x 16, 16 x 32 or 16 x 16 columns
     int4* modal64_items = nullptr;    // work items of the modal FP64 K*u (device; null: dense stencil)
-    int modal64_n = 0, modal64_bx = 32;
+    int modal64_n = 0, modal64_bx = 32, modal64_by = 16;
+    bool half_sm = false;             // gf_set_sm_share: launch shapes that leave half of each SM free
     double* modal_side = nullptr;     // its side buffer: corner forces at the nodes on tile boundaries
     double* modal_es = nullptr;       // its elements' scaled coefficients E_e C, 9 x nel (modal_scale_kernel)
     bool coarse_ldl = true;           // coarsest inverse from the banded LDL^T factorisation (GF_COARSE_LDL=0: a sweep)
@@ -327,8 +328,11 @@ int tiled_f32(gf_grid* g, int l, const float* x, const BT* b, OT* out, const flo
         if (g->modal_bx == 32)
             RET((launch_modal<float, 32, 16, gf::modal_stencil_f32_kernel<MODE, BT, OT, 32, 16>>(
                 g, g->modal_n, x, b, out, E, L.dims(), g->Kmodal32, omega, (const int4*)g->modal_items, halt)));
-        else
+        else if (g->modal_by == 32)
             RET((launch_modal<float, 16, 32, gf::modal_stencil_f32_kernel<MODE, BT, OT, 16, 32>>(
+                g, g->modal_n, x, b, out, E, L.dims(), g->Kmodal32, omega, (const int4*)g->modal_items, halt)));
+        else
+            RET((launch_modal<float, 16, 16, gf::modal_stencil_f32_kernel<MODE, BT, OT, 16, 16>>(
                 g, g->modal_n, x, b, out, E, L.dims(), g->Kmodal32, omega, (const int4*)g->modal_items, halt)));
         return GF_OK;
     }
@@ -1044,21 +1048,21 @@ int applyK64(gf_grid* g, const double* u, double* y, const int* halt)
         const double* Es = g->modal_es;
         const int4* it = g->modal64_items;
         const gf::GridDims d = g->lv[0].dims();
-        const int bx = g->modal64_bx;
-        const gf::ModalSide sd = gf::modal_side(d, bx, gf::MODAL_THREADS / bx);
+        const int bx = g->modal64_bx, by = g->modal64_by;
+        const gf::ModalSide sd = gf::modal_side(d, bx, by);
         double* side = g->modal_side;
-        if (bx == 32 && mk)
-            RET((launch_modal<double, 32, 16, gf::apply_modal_kernel<32, 16, true>>(g, g->modal64_n, u, y, Es, d, it,
-                                                                                   side, sd, halt)));
-        else if (bx == 32)
-            RET((launch_modal<double, 32, 16, gf::apply_modal_kernel<32, 16, false>>(g, g->modal64_n, u, y, Es, d, it,
-                                                                                    side, sd, halt)));
-        else if (mk)
-            RET((launch_modal<double, 16, 32, gf::apply_modal_kernel<16, 32, true>>(g, g->modal64_n, u, y, Es, d, it,
-                                                                                   side, sd, halt)));
+#define GF_MODAL64(BXV, BYV)                                                                                      \
+    (mk ? launch_modal<double, BXV, BYV, gf::apply_modal_kernel<BXV, BYV, true>>(g, g->modal64_n, u, y, Es, d, it, \
+                                                                                  side, sd, halt)                 \
+        : launch_modal<double, BXV, BYV, gf::apply_modal_kernel<BXV, BYV, false>>(g, g->modal64_n, u, y, Es, d, it, \
+                                                                                   side, sd, halt))
+        if (bx == 32)
+            RET(GF_MODAL64(32, 16));
+        else if (by == 32)
+            RET(GF_MODAL64(16, 32));
         else
-            RET((launch_modal<double, 16, 32, gf::apply_modal_kernel<16, 32, false>>(g, g->modal64_n, u, y, Es, d, it,
-                                                                                    side, sd, halt)));
+            RET(GF_MODAL64(16, 16));
+#undef GF_MODAL64
         const long long ne = sd.entries(d);
         if (mk)
             LAUNCH(g, (unsigned)((ne + 255) / 256), 256, gf::modal_fixup_kernel<true>, (const double*)side, sd, y, d,
@@ -1440,7 +1444,10 @@ int cgs2_step(gf_grid* g, int j, double* w, int outer)
     const int b0 = g->nbc[0][q], b1 = g->nbc[1][q], b2 = g->nbc[2][q];
     LAUNCH(g, b0, gf::RED_THREADS, gf::cgs_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
     LAUNCH(g, 1, 32 * 32, gf::reduce_partials_kernel, g->partial, b0, NV + 1, NV + 1, g->st, 0, 1);
-    LAUNCH(g, b1, gf::RED_THREADS, gf::cgs_update_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
+    if (g->half_sm)
+        LAUNCH(g, b1, 128, (gf::cgs_update_dots_kernel<NV, 128>), g->V, ld, nv, w, n, g->partial, g->st);
+    else
+        LAUNCH(g, b1, gf::RED_THREADS, gf::cgs_update_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
     LAUNCH(g, 1, 32 * 32, gf::reduce_partials_kernel, g->partial, b1, NV, nv, g->st, 1, 1);
     LAUNCH(g, b2, gf::RED_THREADS, gf::cgs_update_norm_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
     LAUNCH(g, 1, 32, gf::reduce_partials_kernel, g->partial, b2, 1, 1, g->st, 2, 1);
@@ -1910,6 +1917,8 @@ const char* gf_last_error(void) { return g_err.c_str(); }
 }  // extern "C"
 namespace {
 int modal_autotune(gf_grid* g);
+int modal_default_plan(gf_grid* g);
+int cgs_grids(gf_grid* g, long long* partial_rows);
 }
 extern "C" {
 int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int levels, void* stream,
@@ -1965,36 +1974,15 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         const char* l = getenv("GF_COARSE_LDL");
         g->coarse_ldl = !(l && l[0] == '0') && g->sym_gj;
     }
-    {   // modal FP64 K*u (GF_MODAL=0: the dense node stencil); GF_MODAL_CHUNK=<planes> forces
-        // runs of that many node planes per CTA and GF_MODAL_BX=32/16 the tile shape (tests)
+    {   // modal FP64 K*u (GF_MODAL=0: the dense node stencil)
         const char* e = getenv("GF_MODAL");
         if (!(e && e[0] == '0')) {
-            int per_sm = 0;
-            if (!smem_opt_in<gf::apply_modal_kernel<32, 16, false>>(gf::modal_smem_bytes<double, 32, 16>()) ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gf::apply_modal_kernel<32, 16>, gf::MODAL_THREADS,
-                                                              gf::modal_smem_bytes<double, 32, 16>()) != cudaSuccess ||
-                per_sm < 1)
-                per_sm = 1;
-            const char* ch = getenv("GF_MODAL_CHUNK");
-            const char* bxs = getenv("GF_MODAL_BX");
-            const int forced = ch ? std::max(0, atoi(ch)) : 0;
-            // the FP32 fine level's plan (tiles overlapping by one column) and the FP64 K*u's
-            // (tiles apart), each over both tile shapes by the cost model
-            for (int f32 = 1; f32 >= 0; --f32) {
-                double c32 = 0, c16 = 0;
-                std::vector<int4> i32 = gf::modal_plan(nx, ny, nz, 32, 16, g->sms * per_sm, forced, &c32, f32);
-                std::vector<int4> i16 = gf::modal_plan(nx, ny, nz, 16, 32, g->sms * per_sm, forced, &c16, f32);
-                const bool use32 = bxs ? atoi(bxs) == 32 : c32 <= c16;
-                const std::vector<int4>& items = use32 ? i32 : i16;
-                int4** dst = f32 ? &g->modal_items : &g->modal64_items;
-                (f32 ? g->modal_bx : g->modal64_bx) = use32 ? 32 : 16;
-                (f32 ? g->modal_n : g->modal64_n) = (int)items.size();
-                if (alloc((void**)dst, sizeof(int4) * items.size()) != GF_OK) return fail(GF_ERR_OOM);
-                if (cudaMemcpy(*dst, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-                    return fail(set_err(GF_ERR_CUDA, "modal work items"));
-            }
+            const int rp = modal_default_plan(g);
+            if (rp != GF_OK) return fail(rp);
             const gf::GridDims d0{nx, ny, nz, nullptr};   // the fine level (the levels come later)
-            const long long side = std::max(gf::modal_side(d0, 32, 16).entries(d0), gf::modal_side(d0, 16, 32).entries(d0));
+            const long long side = std::max(std::max(gf::modal_side(d0, 32, 16).entries(d0),
+                                                     gf::modal_side(d0, 16, 32).entries(d0)),
+                                            gf::modal_side(d0, 16, 16).entries(d0));
             if (alloc((void**)&g->modal_es, sizeof(double) * 9 * (size_t)g->nel) != GF_OK ||
                 alloc((void**)&g->modal_side, sizeof(double) * 12 * (size_t)side) != GF_OK)
                 return fail(GF_ERR_OOM);
@@ -2110,29 +2098,14 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
     int r = GF_OK;
     g->nbr = (int)std::min<long long>(2LL * g->sms, std::max<long long>(1, (g->ndof + 1023) / 1024));
     g->ldk = (g->ndof + 31) / 32 * 32;
-    // the FP64 Gram-Schmidt passes run the blocks resident at once (one round), capped by
-    // 256-row tiles; their partial rows share g->partial with the other reductions
+    // the FP64 Gram-Schmidt passes' partial rows (both launch shapes: gf_set_sm_share) share
+    // g->partial with the other reductions
     long long partial_rows = (long long)g->nbr * 40;
-    {
-        const void* kc[3][4] = {
-            {(const void*)gf::cgs_dots_kernel<8>, (const void*)gf::cgs_dots_kernel<16>,
-             (const void*)gf::cgs_dots_kernel<24>, (const void*)gf::cgs_dots_kernel<32>},
-            {(const void*)gf::cgs_update_dots_kernel<8>, (const void*)gf::cgs_update_dots_kernel<16>,
-             (const void*)gf::cgs_update_dots_kernel<24>, (const void*)gf::cgs_update_dots_kernel<32>},
-            {(const void*)gf::cgs_update_norm_kernel<8>, (const void*)gf::cgs_update_norm_kernel<16>,
-             (const void*)gf::cgs_update_norm_kernel<24>, (const void*)gf::cgs_update_norm_kernel<32>}};
-        const int nvq[4] = {8, 16, 24, 32};
-        const long long tiles = std::max<long long>(1, (g->ndof + gf::RED_THREADS - 1) / gf::RED_THREADS);
-        for (int p = 0; p < 3; ++p)
-            for (int q = 0; q < 4; ++q) {
-                int nb = 0;
-                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kc[p][q], gf::RED_THREADS, 0) != cudaSuccess ||
-                    nb <= 0)
-                    nb = 2;
-                g->nbc[p][q] = (int)std::min<long long>((long long)nb * g->sms, tiles);
-                const int stride = p == 0 ? nvq[q] + 1 : (p == 1 ? nvq[q] : 1);
-                partial_rows = std::max(partial_rows, (long long)g->nbc[p][q] * stride);
-            }
+    for (int h = 1; h >= 0; --h) {
+        long long rows = 0;
+        g->half_sm = h != 0;
+        cgs_grids(g, &rows);
+        partial_rows = std::max(partial_rows, rows);
     }
     if ((r = allocT(&g->Ainv, (size_t)g->nc * g->nc)) || (r = allocT(&g->Agj, (size_t)g->nc * g->nc + 2 * gf::SGJ_B * gf::SGJ_B)) ||
         (r = allocT(&g->ldl_ws, (size_t)g->nc * (1 + gf::LDL_C) + gf::LDL_C * gf::LDL_C)) ||
@@ -2165,6 +2138,76 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
 
 }  // extern "C"
 namespace {
+// Launch plans of the modal kernels by modal_plan's cost model alone: the FP32 fine level's
+// (tiles overlapping by one column) and the FP64 K*u's (tiles apart), each the cheaper of
+// the two full-SM tile shapes, or the 16 x 16 shape when the grid shares its SMs
+// (half_sm). GF_MODAL_CHUNK=<planes> forces runs of that many node planes per CTA and
+// GF_MODAL_BX=32/16 the tile shape (tests). Replaces the items held before.
+int modal_default_plan(gf_grid* g)
+{
+    int per_sm = 0;
+    if (!smem_opt_in<gf::apply_modal_kernel<32, 16, false>>(gf::modal_smem_bytes<double, 32, 16>()) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gf::apply_modal_kernel<32, 16>, gf::MODAL_THREADS,
+                                                      gf::modal_smem_bytes<double, 32, 16>()) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const char* ch = getenv("GF_MODAL_CHUNK");
+    const char* bxs = getenv("GF_MODAL_BX");
+    const int forced = ch ? std::max(0, atoi(ch)) : 0;
+    for (int f32 = 1; f32 >= 0; --f32) {
+        double c32 = 0, c16 = 0;
+        std::vector<int4> i32 = gf::modal_plan(g->nx, g->ny, g->nz, 32, 16, g->sms * per_sm, forced, &c32, f32);
+        std::vector<int4> i16 =
+            gf::modal_plan(g->nx, g->ny, g->nz, 16, g->half_sm ? 16 : 32, g->sms * per_sm, forced, &c16, f32);
+        const bool use32 = !g->half_sm && (bxs ? atoi(bxs) == 32 : c32 <= c16);
+        const std::vector<int4>& items = use32 ? i32 : i16;
+        int4** dst = f32 ? &g->modal_items : &g->modal64_items;
+        cudaFree(*dst);
+        *dst = nullptr;
+        (f32 ? g->modal_bx : g->modal64_bx) = use32 ? 32 : 16;
+        (f32 ? g->modal_by : g->modal64_by) = use32 ? 16 : (g->half_sm ? 16 : 32);
+        (f32 ? g->modal_n : g->modal64_n) = (int)items.size();
+        RET(alloc((void**)dst, sizeof(int4) * items.size()));
+        CK(cudaMemcpy(*dst, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    }
+    return GF_OK;
+}
+
+// Grids of the FP64 Gram-Schmidt passes: the blocks resident at once (one round), capped
+// by 256-row tiles; half_sm: half of them, and the update-and-dots pass in 128-thread
+// blocks, so that each leaves about half of an SM's registers to other streams.
+// *partial_rows: the partial-sum rows the passes need.
+int cgs_grids(gf_grid* g, long long* partial_rows)
+{
+    const void* kc[3][4] = {
+        {(const void*)gf::cgs_dots_kernel<8>, (const void*)gf::cgs_dots_kernel<16>,
+         (const void*)gf::cgs_dots_kernel<24>, (const void*)gf::cgs_dots_kernel<32>},
+        {(const void*)gf::cgs_update_dots_kernel<8>, (const void*)gf::cgs_update_dots_kernel<16>,
+         (const void*)gf::cgs_update_dots_kernel<24>, (const void*)gf::cgs_update_dots_kernel<32>},
+        {(const void*)gf::cgs_update_norm_kernel<8>, (const void*)gf::cgs_update_norm_kernel<16>,
+         (const void*)gf::cgs_update_norm_kernel<24>, (const void*)gf::cgs_update_norm_kernel<32>}};
+    const void* kh[4] = {(const void*)gf::cgs_update_dots_kernel<8, 128>, (const void*)gf::cgs_update_dots_kernel<16, 128>,
+                         (const void*)gf::cgs_update_dots_kernel<24, 128>, (const void*)gf::cgs_update_dots_kernel<32, 128>};
+    const int nvq[4] = {8, 16, 24, 32};
+    const long long tiles = std::max<long long>(1, (g->ndof + gf::RED_THREADS - 1) / gf::RED_THREADS);
+    long long rows = 0;
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 4; ++q) {
+            const bool h128 = g->half_sm && p == 1;
+            int nb = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, h128 ? kh[q] : kc[p][q], h128 ? 128 : gf::RED_THREADS,
+                                                              0) != cudaSuccess ||
+                nb <= 0)
+                nb = 2;
+            if (g->half_sm) nb = std::max(1, nb / 2);
+            g->nbc[p][q] = (int)std::min<long long>((long long)nb * g->sms, tiles);
+            const int stride = p == 0 ? nvq[q] + 1 : (p == 1 ? nvq[q] : 1);
+            rows = std::max(rows, (long long)g->nbc[p][q] * stride);
+        }
+    *partial_rows = rows;
+    return GF_OK;
+}
+
 // Time the modal kernels under a few launch plans -- the cheapest ones by modal_plan's
 // cost model over both tile shapes and several run lengths -- and keep the fastest, for
 // the FP64 K*u (tiles apart, with its tile-boundary fix-up) and the FP32 fine-level sweep
@@ -2180,14 +2223,17 @@ int modal_autotune(gf_grid* g)
         !smem_opt_in<gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 32, 16>>(
             gf::modal_smem_bytes<float, 32, 16>()) ||
         !smem_opt_in<gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 16, 32>>(
-            gf::modal_smem_bytes<float, 16, 32>()))
+            gf::modal_smem_bytes<float, 16, 32>()) ||
+        !smem_opt_in<gf::apply_modal_kernel<16, 16, false>>(gf::modal_smem_bytes<double, 16, 16>()) ||
+        !smem_opt_in<gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 16, 16>>(
+            gf::modal_smem_bytes<float, 16, 16>()))
         return set_err(GF_ERR_CUDA, "shared memory of the modal kernels");
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gf::apply_modal_kernel<32, 16>, gf::MODAL_THREADS,
                                                       gf::modal_smem_bytes<double, 32, 16>()) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     struct Cand {
-        int bx;
+        int bx, by;
         double cost;
         std::vector<int4> items;
     };
@@ -2205,10 +2251,10 @@ int modal_autotune(gf_grid* g)
         std::vector<Cand> cand;
         for (int bx : {32, 16})
             for (int L : {0, 2, 3, 4, 6, 8, 12, 16, 24, 33, 48, 64}) {
-                if (L > NZ) continue;
-                Cand c{bx, 0.0, {}};
-                c.items = gf::modal_plan(g->nx, g->ny, g->nz, bx, gf::MODAL_THREADS / bx, g->sms * per_sm, L, &c.cost,
-                                         f32);
+                if (L > NZ || (g->half_sm && bx == 32)) continue;
+                const int by = g->half_sm ? 16 : gf::MODAL_THREADS / bx;
+                Cand c{bx, by, 0.0, {}};
+                c.items = gf::modal_plan(g->nx, g->ny, g->nz, bx, by, g->sms * per_sm, L, &c.cost, f32);
                 cand.push_back(std::move(c));
             }
         std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.cost < b.cost; });
@@ -2223,15 +2269,19 @@ int modal_autotune(gf_grid* g)
         int best_i = -1;
         auto run = [&](const Cand& c) {
             const unsigned n = (unsigned)c.items.size();
-            const gf::ModalSide sd = gf::modal_side(d, c.bx, gf::MODAL_THREADS / c.bx);
+            const gf::ModalSide sd = gf::modal_side(d, c.bx, c.by);
             const long long ne = sd.entries(d);
             if (!f32) {
                 if (c.bx == 32)
                     gf::apply_modal_kernel<32, 16><<<n, dim3(32, 16), gf::modal_smem_bytes<double, 32, 16>(),
                                                      g->stream>>>(f.x64, f.t64, g->modal_es, d, dev, g->modal_side,
                                                                   sd, nullptr);
-                else
+                else if (c.by == 32)
                     gf::apply_modal_kernel<16, 32><<<n, dim3(16, 32), gf::modal_smem_bytes<double, 16, 32>(),
+                                                     g->stream>>>(f.x64, f.t64, g->modal_es, d, dev, g->modal_side,
+                                                                  sd, nullptr);
+                else
+                    gf::apply_modal_kernel<16, 16><<<n, dim3(16, 16), gf::modal_smem_bytes<double, 16, 16>(),
                                                      g->stream>>>(f.x64, f.t64, g->modal_es, d, dev, g->modal_side,
                                                                   sd, nullptr);
                 gf::modal_fixup_kernel<false><<<(unsigned)((ne + 255) / 256), 256, 0, g->stream>>>(
@@ -2240,9 +2290,13 @@ int modal_autotune(gf_grid* g)
                 gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 32, 16>
                     <<<n, dim3(32, 16), gf::modal_smem_bytes<float, 32, 16>(), g->stream>>>(
                         f.x32, (const float*)f.b32, f.t32, f.E32, d, g->Kmodal32, 0.6f, dev, nullptr);
-            } else {
+            } else if (c.by == 32) {
                 gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 16, 32>
                     <<<n, dim3(16, 32), gf::modal_smem_bytes<float, 16, 32>(), g->stream>>>(
+                        f.x32, (const float*)f.b32, f.t32, f.E32, d, g->Kmodal32, 0.6f, dev, nullptr);
+            } else {
+                gf::modal_stencil_f32_kernel<gf::ST_SWEEP, float, float, 16, 16>
+                    <<<n, dim3(16, 16), gf::modal_smem_bytes<float, 16, 16>(), g->stream>>>(
                         f.x32, (const float*)f.b32, f.t32, f.E32, d, g->Kmodal32, 0.6f, dev, nullptr);
             }
         };
@@ -2283,6 +2337,7 @@ int modal_autotune(gf_grid* g)
             CK(cudaMemcpy(*dst, c.items.data(), sizeof(int4) * c.items.size(), cudaMemcpyHostToDevice));
             (f32 ? g->modal_n : g->modal64_n) = (int)c.items.size();
             (f32 ? g->modal_bx : g->modal64_bx) = c.bx;
+            (f32 ? g->modal_by : g->modal64_by) = c.by;
         }
     }
     return GF_OK;
@@ -2416,6 +2471,25 @@ int gf_set_coarse_operator(gf_grid* g, int kind)
     drop_graphs(g);            // captured Arnoldi steps hold the other V-cycle
     g->coarse_kind = kind;
     g->has_floor = false;      // the next gf_set_floor builds the hierarchy
+    return GF_OK;
+}
+
+int gf_set_sm_share(gf_grid* g, int share)
+{
+    RET(check_grid(g));
+    if (share != 0 && share != 1) return set_err(GF_ERR_ARG, "share must be 0 or 1");
+    if ((share != 0) == g->half_sm) return GF_OK;
+    RET(set_device(g));
+    drop_graphs(g);            // captured Arnoldi steps hold the other launch shapes
+    g->has_floor = false;      // the modal autotune below runs on the level-0 buffers
+    g->half_sm = share != 0;
+    long long rows = 0;
+    RET(cgs_grids(g, &rows));
+    if (g->modal64_items) {
+        RET(modal_default_plan(g));
+        if (!getenv("GF_MODAL_CHUNK") && !getenv("GF_MODAL_BX")) RET(modal_autotune(g));
+    }
+    CK(cudaStreamSynchronize(g->stream));
     return GF_OK;
 }
 

@@ -61,16 +61,16 @@ __device__ __forceinline__ double warp_transpose_sum(double (&v)[P], int lane)
     return s;
 }
 
-// partial[b][q] = sum over the block's threads of acc[q], q < nv: each warp sums its values
-// by transposition (the first 32; an NV of 33 adds its last value by a shuffle tree), then
-// thread q adds the warps' sums in warp order.
-template <int NV>
+// partial[b][q] = sum over the block's T threads of acc[q], q < nv: each warp sums its
+// values by transposition (the first 32; an NV of 33 adds its last value by a shuffle
+// tree), then thread q adds the warps' sums in warp order.
+template <int NV, int T = RED_THREADS>
 __device__ __forceinline__ void block_reduce_store(double (&acc)[NV], int nv, double* __restrict__ out_row)
 {
     constexpr int NT = NV < 32 ? NV : 32;   // values summed by transposition
     constexpr int P = pow2_at_least(NT);
     constexpr int SPREAD = 32 / P;          // lanes that end up with one value
-    __shared__ double red[RED_THREADS / 32][NV];
+    __shared__ double red[T / 32][NV];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double v[P];
 #pragma unroll
@@ -88,7 +88,7 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NV], int nv, do
     if (threadIdx.x < nv) {
         double t = 0.0;
 #pragma unroll
-        for (int w = 0; w < RED_THREADS / 32; ++w) t += red[w][threadIdx.x];
+        for (int w = 0; w < T / 32; ++w) t += red[w][threadIdx.x];
         out_row[threadIdx.x] = t;
     }
 }
@@ -169,9 +169,11 @@ cgs_dots_kernel(const double* __restrict__ V, long long ld, int nv, const double
 
 // pass 2: w -= sum_i h1_i V_i ; partial[b][i] = sum_r V_i[r] w_new[r]
 // (the update runs as w_new = fma(-h_nv-1, V_nv-1, ... fma(-h_0, V_0, w)): nv FMAs, no
-// separate subtraction; the negated coefficients are formed once per block)
-template <int NV>
-__global__ void __launch_bounds__(RED_THREADS)
+// separate subtraction; the negated coefficients are formed once per block). T threads
+// per block: 128 when the grid leaves half of each SM to other streams (its NV = 32 form
+// holds up to 255 registers per thread).
+template <int NV, int T = RED_THREADS>
+__global__ void __launch_bounds__(T)
 cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
                        long long n, double* __restrict__ partial, const KState* __restrict__ st)
 {
@@ -185,11 +187,11 @@ cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, doubl
     __syncthreads();
     long long r0, r1;
     block_rows(n, r0, r1);
-    for (long long r = r0 + threadIdx.x; r < r1; r += (long long)RED_THREADS * ROWS) {
+    for (long long r = r0 + threadIdx.x; r < r1; r += (long long)T * ROWS) {
         double wr[ROWS], v[ROWS][NV];
 #pragma unroll
         for (int u = 0; u < ROWS; ++u) {
-            const long long rr = r + (long long)u * RED_THREADS;
+            const long long rr = r + (long long)u * T;
             const bool ok = u == 0 || rr < r1;   // row r itself is inside the range
             wr[u] = ok ? w[rr] : 0.0;
 #pragma unroll
@@ -197,7 +199,7 @@ cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, doubl
         }
 #pragma unroll
         for (int u = 0; u < ROWS; ++u) {
-            const long long rr = r + (long long)u * RED_THREADS;
+            const long long rr = r + (long long)u * T;
             if (rr >= r1) break;
             double s = wr[u];
 #pragma unroll
@@ -214,7 +216,7 @@ cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, doubl
             }
         }
     }
-    block_reduce_store<NV>(acc, nv, partial + (long long)blockIdx.x * NV);
+    block_reduce_store<NV, T>(acc, nv, partial + (long long)blockIdx.x * NV);
 }
 
 // pass 3: w -= sum_i h2_i V_i ; partial[b][0] = ||w_new||^2 (block part)

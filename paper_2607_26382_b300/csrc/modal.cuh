@@ -71,7 +71,10 @@ __host__ inline ModalCoef modal_coef(double E0, double nu)
     return c;
 }
 
-constexpr int MODAL_THREADS = 512;   // element columns per CTA: 32 x 16 or 16 x 32
+// Element columns per CTA of the full-SM tile shapes, 32 x 16 or 16 x 32 (one CTA fills
+// an SM's registers); the 16 x 16 shape takes half of them, so that kernels of other
+// streams (the FP32 V-cycle of a concurrent solve) can share the SM.
+constexpr int MODAL_THREADS = 512;
 
 // Dynamic shared memory of the modal kernels: two buffers of 12 corner forces per column
 // (and, for the FP32 kernel, three layers of element moduli).
@@ -286,7 +289,7 @@ __device__ __forceinline__ void modal_ring_store(const T (*__restrict__ part)[BY
 // nodes on its boundary (modal_fixup_kernel completes those).
 // MASK: fixed components from d.fix (any supports); otherwise the clamped face x = 0.
 template <int BX, int BY, bool MASK = false>
-__global__ void __launch_bounds__(MODAL_THREADS, 1)
+__global__ void __launch_bounds__(BX * BY, MODAL_THREADS / (BX * BY))
 apply_modal_kernel(const double* __restrict__ u, double* __restrict__ y, const double* __restrict__ Es,
                    GridDims d, const int4* __restrict__ items, double* __restrict__ side, ModalSide sd_,
                    const int* __restrict__ halt)
@@ -482,6 +485,29 @@ __global__ void modal_fixup_kernel(const double* __restrict__ side, ModalSide sd
 }
 
 // ---- the FP32 V-cycle's fine-level operator in the same basis ------------------------
+// A pair of FP32 values, the x and y components of one quantity, added and subtracted by
+// the packed f32x2 instructions: each lane rounds to nearest like the scalar instruction,
+// so the pair gives bit for bit the scalar results at half the instructions.
+struct f32x2 {
+    float x, y;
+};
+__device__ __forceinline__ f32x2 operator+(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("{\n .reg .b64 ra, rb, rc;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " add.rn.f32x2 rc, ra, rb;\n mov.b64 {%0, %1}, rc;\n}\n"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ f32x2 operator-(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("{\n .reg .b64 ra, rb, rc;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rc, ra, rb;\n mov.b64 {%0, %1}, rc;\n}\n"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 // The level-0 smoothing sweeps and residual of the mixed V-cycle (and the FP32 K*u) with
 // the modal K0 in FP32: the column walk of apply_modal_kernel (on tiles that overlap by one
 // element column, modal_plan with halo = true, so no side buffer), with the next
@@ -498,18 +524,21 @@ struct ModalCoefF {
 };
 
 template <int MODE, typename BT, typename OT, int BX, int BY>
-__global__ void __launch_bounds__(MODAL_THREADS, 1)
+__global__ void __launch_bounds__(BX * BY, MODAL_THREADS / (BX * BY))
 modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, OT* __restrict__ out,
                          const float* __restrict__ E, GridDims d, const __grid_constant__ ModalCoefF C,
                          float omega, const int4* __restrict__ items, const int* __restrict__ halt)
 {
     if (halt != nullptr && *halt != 0) return;
-    // corner forces [corner * 3 + comp][column] in two buffers by step parity, and the
-    // column's element moduli in three by layer (the gather reads this layer's and the
-    // previous one's): dynamic shared memory, modal_smem_bytes<float, BX, BY>; one
-    // barrier per step
+    // corner forces [corner][column] in two buffers by step parity, the x and y components
+    // as pairs (partb) and z apart (partz), and the column's element moduli in three by
+    // layer (the gather reads this layer's and the previous one's): dynamic shared memory,
+    // modal_smem_bytes<float, BX, BY>; one barrier per step. The x and y components run
+    // through the transforms, the face recurrence and the gather as f32x2 pairs; the
+    // modal-space products, whose index pattern differs by component, stay scalar.
     extern __shared__ __align__(16) unsigned char modal_smem[];
-    float(*partb)[12][BY][BX] = reinterpret_cast<float(*)[12][BY][BX]>(modal_smem);
+    f32x2(*partb)[4][BY][BX] = reinterpret_cast<f32x2(*)[4][BY][BX]>(modal_smem);
+    float(*partz)[4][BY][BX] = reinterpret_cast<float(*)[4][BY][BX]>(modal_smem + sizeof(float) * 2 * 8 * BY * BX);
     float(*Es)[BY][BX] = reinterpret_cast<float(*)[BY][BX]>(modal_smem + sizeof(float) * 2 * 12 * BY * BX);
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int NX = d.nx + 1, NY = d.ny + 1, NZ = d.nz + 1;
@@ -523,36 +552,40 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
     const int ni = i0 + tx, nj = j0 + ty;   // this thread's output node column
     const bool outnode = tx < BX - 1 && ty < BY - 1 && ni < NX && nj < NY;
 
-    auto load_raw = [&](int kz, float v[3][4]) {
+    auto load_raw = [&](int kz, f32x2 v[4], float vz[4]) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int qi = ex + (q & 1), qj = ey + (q >> 1);
             const bool ok = col && kz >= 0 && kz < NZ && qi >= 1;
             const long long n = qi + (long long)NX * qj + plane * kz;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) v[c][q] = ok ? __ldg(x + 3 * n + c) : 0.f;
+            v[q].x = ok ? __ldg(x + 3 * n + 0) : 0.f;
+            v[q].y = ok ? __ldg(x + 3 * n + 1) : 0.f;
+            vz[q] = ok ? __ldg(x + 3 * n + 2) : 0.f;
         }
     };
     auto load_E = [&](int kz) -> float {
         return (col && kz >= 0 && kz < d.nz) ? __ldg(E + ex + (long long)d.nx * (ey + (long long)d.ny * kz)) : 0.f;
     };
 
-    float bot[3][4], carry[3][4], raw[3][4];
-    load_raw(k0 - 1, raw);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) face_fwd<float>(raw[c], bot[c]);
-    load_raw(k0, raw);                      // the next top face, untransformed
+    f32x2 bot[4], carry[4], raw[4];         // x and y components
+    float botz[4], carryz[4], rawz[4];      // z
+    load_raw(k0 - 1, raw, rawz);
+    face_fwd<f32x2>(raw, bot);
+    face_fwd<float>(rawz, botz);
+    load_raw(k0, raw, rawz);                // the next top face, untransformed
     float Ecur = load_E(k0 - 1);
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) carry[c][q] = 0.f;
+    for (int q = 0; q < 4; ++q) {
+        carry[q] = f32x2{0.f, 0.f};
+        carryz[q] = 0.f;
+    }
 
     for (int ez = k0 - 1; ez < k1; ++ez) {
         // loads one step ahead: the plane after next, the next element's modulus, and this
         // step's node values for the update
-        float rawn[3][4];
-        load_raw(ez + 2, rawn);
+        f32x2 rawn[4];
+        float rawnz[4];
+        load_raw(ez + 2, rawn, rawnz);
         const float Enext = load_E(ez + 1);
         float xn[3] = {0.f, 0.f, 0.f}, bn[3] = {0.f, 0.f, 0.f};
         long long nn = 0;
@@ -567,33 +600,39 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
                 for (int c = 0; c < 3; ++c) xn[c] = x[3 * nn + c];
             }
         }
-        float top[3][4];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) face_fwd<float>(raw[c], top[c]);
-        float face[3][4];
+        f32x2 top[4];
+        float topz[4];
+        face_fwd<f32x2>(raw, top);
+        face_fwd<float>(rawz, topz);
+        f32x2 face[4];
+        float facez[4];
         if (col && ez >= 0 && ez < d.nz) {
-            float m[3][8];
+            f32x2 m[8];   // modes of the x and y components
+            float mz[8];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    m[c][q] = top[c][q] + bot[c][q];
-                    m[c][q + 4] = top[c][q] - bot[c][q];
-                }
+            for (int q = 0; q < 4; ++q) {
+                m[q] = top[q] + bot[q];
+                m[q + 4] = top[q] - bot[q];
+                mz[q] = topz[q] + botz[q];
+                mz[q + 4] = topz[q] - botz[q];
+            }
+            // component dc's mode beta
+            auto mode = [&](int dc, int beta) -> float { return dc == 0 ? m[beta].x : dc == 1 ? m[beta].y : mz[beta]; };
             const float s = Ecur;
             float sd[6], sc[4];
 #pragma unroll
             for (int k = 1; k < 6; ++k) sd[k] = s * C.diag[k];
 #pragma unroll
             for (int k = 0; k < 4; ++k) sc[k] = s * C.cross[k];
+            f32x2 G[8];
+            float Gz[8];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                float G[8];
 #pragma unroll
                 for (int beta = 1; beta < 8; ++beta) {   // beta = 0 (a rigid translation) carries no force
                     const int bc = (beta >> c) & 1;
                     const int n = ((beta >> ((c + 1) % 3)) & 1) + ((beta >> ((c + 2) % 3)) & 1);
-                    float t = (bc == 0 && n == 0) ? 0.f : sd[bc * 3 + n] * m[c][beta];
+                    float t = (bc == 0 && n == 0) ? 0.f : sd[bc * 3 + n] * mode(c, beta);
 #pragma unroll
                     for (int dd = 1; dd < 3; ++dd) {
                         const int dc = (c + dd) % 3;
@@ -602,51 +641,61 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
                         if (bc != bdd) {
                             const int alpha = beta ^ (1 << c) ^ (1 << dc);
                             const int k = (bc ? 0 : 2) + ((beta >> o) & 1);
-                            t = fmaf(sc[k], m[dc][alpha], t);
+                            t = fmaf(sc[k], mode(dc, alpha), t);
                         }
                     }
-                    G[beta] = t;
+                    if (c == 0) G[beta].x = t;
+                    else if (c == 1) G[beta].y = t;
+                    else Gz[beta] = t;
                 }
-                face[c][0] = carry[c][0] - G[4];
-                carry[c][0] = G[4];
+            }
+            face[0] = carry[0] - G[4];
+            carry[0] = G[4];
+            facez[0] = carryz[0] - Gz[4];
+            carryz[0] = Gz[4];
 #pragma unroll
-                for (int q = 1; q < 4; ++q) {
-                    face[c][q] = carry[c][q] + (G[q] - G[q + 4]);
-                    carry[c][q] = G[q] + G[q + 4];
-                }
+            for (int q = 1; q < 4; ++q) {
+                face[q] = carry[q] + (G[q] - G[q + 4]);
+                carry[q] = G[q] + G[q + 4];
+                facez[q] = carryz[q] + (Gz[q] - Gz[q + 4]);
+                carryz[q] = Gz[q] + Gz[q + 4];
             }
         } else {
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    face[c][q] = carry[c][q];
-                    carry[c][q] = 0.f;
-                }
+            for (int q = 0; q < 4; ++q) {
+                face[q] = carry[q];
+                carry[q] = f32x2{0.f, 0.f};
+                facez[q] = carryz[q];
+                carryz[q] = 0.f;
+            }
         }
         // buffers of this step: part by parity, Es by step mod 3 (last read by the gathers
         // three and two steps back, finished before the previous step's barrier)
         const int step = ez - k0 + 1;
         const int cur = step % 3, prv = (step + 2) % 3;
-        float(*part)[BY][BX] = partb[step & 1];
+        f32x2(*part)[BY][BX] = partb[step & 1];
+        float(*pz)[BY][BX] = partz[step & 1];
+        {
+            f32x2 v[4];
+            float vz[4];
+            face_inv<f32x2>(face, v);
+            face_inv<float>(facez, vz);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            float v[4];
-            face_inv<float>(face[c], v);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) part[q * 3 + c][ty][tx] = v[q];
+            for (int q = 0; q < 4; ++q) {
+                part[q][ty][tx] = v[q];
+                pz[q][ty][tx] = vz[q];
+            }
         }
         Es[cur][ty][tx] = Ecur;
         __syncthreads();
         if (ez >= k0 && outnode) {
-            float a[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float acc = part[3 * 3 + c][ty][tx] + part[2 * 3 + c][ty][tx + 1];
-                acc += part[1 * 3 + c][ty + 1][tx];
-                acc += part[0 * 3 + c][ty + 1][tx + 1];
-                a[c] = acc;
-            }
+            f32x2 axy = part[3][ty][tx] + part[2][ty][tx + 1];
+            axy = axy + part[1][ty + 1][tx];
+            axy = axy + part[0][ty + 1][tx + 1];
+            float az = pz[3][ty][tx] + pz[2][ty][tx + 1];
+            az += pz[1][ty + 1][tx];
+            az += pz[0][ty + 1][tx + 1];
+            const float a[3] = {axy.x, axy.y, az};
             if (ni == 0) {
                 out[3 * nn + 0] = OT(0);
                 out[3 * nn + 1] = OT(0);
@@ -680,12 +729,12 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
             }
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                bot[c][q] = top[c][q];
-                raw[c][q] = rawn[c][q];
-            }
+        for (int q = 0; q < 4; ++q) {
+            bot[q] = top[q];
+            raw[q] = rawn[q];
+            botz[q] = topz[q];
+            rawz[q] = rawnz[q];
+        }
         Ecur = Enext;
     }
 }

@@ -29,6 +29,7 @@ def main(argv=None):
     ap.add_argument("--kmax", type=int, default=200, help="iteration budget of solve_mixed")
     ap.add_argument("--fine", type=int, default=0, help="fine-level adaptive correction steps (solve_mixed)")
     ap.add_argument("--galerkin", action="store_true", help="Galerkin coarse operators (gf_set_coarse_operator)")
+    ap.add_argument("--sm-share", type=int, default=0, help="gf_set_sm_share: 1 = half-SM launch shapes")
     a = ap.parse_args(argv)
 
     import torch
@@ -38,6 +39,7 @@ def main(argv=None):
 
     nx, ny, nz = a.grid
     g = gf.create_grid(nx, ny, nz, levels=a.levels)
+    g.set_sm_share(a.sm_share)
     g.set_density(torch.as_tensor(synth.smoothed_gaussian_density(nx, ny, nz, a.seed), device="cuda"), 3.0)
     if a.galerkin:
         g.set_coarse_operator(gf.GF_COARSE_GALERKIN)

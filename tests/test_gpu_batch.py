@@ -211,6 +211,24 @@ def test_select_floor_many_matches_each_grid_alone(gf):
     torch.cuda.synchronize()
     for a, b, ua, ub in zip(alone, many, u_alone, us2):
         assert a == b and torch.equal(ua, ub) and b["status"] == gf.GF_ACCEPTED
+    # the half-SM launch shapes (gf_set_sm_share): the same operator bit for bit and the
+    # Gram-Schmidt sums over another block partition, so the same decisions and FGMRES
+    # iterations; the sums' rounding, amplified by the operator's conditioning over the
+    # iterations, moves the solutions apart by ~5e-9 here, inside the solve tolerance tau
+    gs3, fs3 = grids_for(streams)
+    for g in gs3:
+        g.set_sm_share(1)
+    with pytest.raises(gf.GFError):
+        gs3[0].set_sm_share(2)
+    us3 = [torch.zeros_like(f) for f in fs3]
+    shared = gf.select_floor_many(gs3, fs3, us3, pol)
+    torch.cuda.synchronize()
+    for a, c, ua, uc in zip(alone, shared, u_alone, us3):
+        assert c["status"] == gf.GF_ACCEPTED and c["floor_index"] == a["floor_index"]
+        assert [t["iters"] for t in c["attempts"]] == [t["iters"] for t in a["attempts"]]
+        assert float((uc - ua).norm() / ua.norm()) <= 1e-6
+    for g in gs3:
+        g.close()
     with pytest.raises(gf.GFError):
         gf.select_floor_many([gs2[0], gs2[0]], [fs2[0], fs2[0]], [us2[0], torch.zeros_like(us2[0])], pol)
     # a grid that cannot run (no density stored) fails the call with its own error, named by

@@ -1104,15 +1104,19 @@ def test_modal_apply_is_independent_of_the_launch_plan(gf, dims, monkeypatch):
     """Each node of the modal K*u sums the same four column corners in one order wherever the
     tiles fall: inside a tile in the kernel, on a tile boundary in the fix-up from the side
     buffer (which for the FP32 fine level also forms the node's smoothing update). Forced
-    tile shapes (32 x 16, 16 x 32) and run lengths (1, 4 node planes, the cost model's
-    choice) give bit-identical FP64 K*u, FP32 K*u and mixed V-cycles, on ragged tiles."""
+    tile shapes (32 x 16, 16 x 32, and the half-SM 16 x 16 of gf_set_sm_share) and run
+    lengths (1, 4 node planes, the cost model's choice) give bit-identical FP64 K*u, FP32
+    K*u and mixed V-cycles, on ragged tiles."""
     nx, ny, nz, L = dims
     outs = []
-    for bx in ("32", "16"):
+    for share, bx in ((0, "32"), (0, "16"), (1, "16")):
         for chunk in ("1", "4", "0"):
             monkeypatch.setenv("GF_MODAL_BX", bx)
             monkeypatch.setenv("GF_MODAL_CHUNK", chunk)
             g, m, rho = make(gf, nx, ny, nz, L, seed=11, rho_min=1e-6, kind="uniform")
+            if share:
+                g.set_sm_share(1)   # clears the floor
+                g.set_floor(1e-6)
             u = synth.random_vector(m.n_dof, 3)
             y = torch.full((g.n_dof,), np.nan, dtype=torch.float64, device="cuda")
             g.apply_K(dev(u), y)
