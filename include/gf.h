@@ -259,6 +259,18 @@ int gf_set_coarse_operator(gf_grid* g, int kind);
  * Errors: GF_ERR_ARG for share outside {0, 1}. */
 int gf_set_sm_share(gf_grid* g, int share);
 
+/* out[q] = in[q] rounded to binary32 (round to nearest, ties to even; subnormal results,
+ * overflow to infinity, NaN kept quiet), and out[q] = in[q] widened exactly to binary64,
+ * for q < n: the conversions the mixed V-cycle applies to its FP64 input and its FP32
+ * result (Sec. 3.3, the mixed-precision preconditioner), computed in integer arithmetic
+ * so that they stay off the FP64 pipe, bit for bit the IEEE 754 conversions. `in` and
+ * `out` are device arrays of n elements that do not overlap; enqueued on `stream` (a
+ * cudaStream_t, NULL = legacy default) of the current device, no synchronisation.
+ * n = 0 does nothing. Errors: GF_ERR_ARG for n < 0 or a null pointer with n > 0,
+ * GF_ERR_CUDA if the launch fails. */
+int gf_round_to_f32(const double* in, float* out, long long n, void* stream);
+int gf_widen_to_f64(const float* in, double* out, long long n, void* stream);
+
 /* f = unit point load in -z at the node (nx, ny/2, nz/2) (n_dof doubles, device);
  * the cantilever of Table geometries. */
 int gf_cantilever_load(gf_grid* g, double* f);

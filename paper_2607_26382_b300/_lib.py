@@ -39,7 +39,7 @@ EXPORTED = [
     "gf_batch_solution", "gf_batch_autotune", "gf_batch_select_floor", "gf_batch_stats",
     "gf_mlp_create", "gf_mlp_destroy", "gf_mlp_set_norm", "gf_mlp_get_params", "gf_mlp_forward",
     "gf_mlp_loss_grad", "gf_mlp_train", "gf_mlp_predict", "gf_select_features", "gf_apply_K_split",
-    "gf_set_coarse_operator", "gf_set_sm_share", "gf_batch_set_sm_share", "gf_set_geometry", "gf_bridge_load", "gf_batch_set_coarse_operator",
+    "gf_set_coarse_operator", "gf_set_sm_share", "gf_batch_set_sm_share", "gf_round_to_f32", "gf_widen_to_f64", "gf_set_geometry", "gf_bridge_load", "gf_batch_set_coarse_operator",
 ]
 
 
@@ -108,6 +108,8 @@ def lib():
         "gf_set_coarse_operator": [P, c_int],
         "gf_set_sm_share": [P, c_int],
         "gf_batch_set_sm_share": [P, c_int],
+        "gf_round_to_f32": [P, P, c_longlong, P],
+        "gf_widen_to_f64": [P, P, c_longlong, P],
         "gf_cantilever_load": [P, P],
         "gf_set_geometry": [P, c_int],
         "gf_bridge_load": [P, P],
@@ -468,6 +470,28 @@ def true_residual_noalloc(nx, ny, nz, rho_hat, p, rho_min, f, u, eta, h=1.0, E0=
         _ptr(f, t, 3 * n_nodes, "f"), _ptr(u, t, 3 * n_nodes, "u"), _ptr(eta, t, 1, "eta"),
         c_void_p(stream.cuda_stream)))
     return eta
+
+
+def round_to_f32(x, out=None, stream=None):
+    """gf_round_to_f32: x (CUDA float64) rounded to float32 by the library's integer routine."""
+    torch = _torch()
+    n = x.numel()
+    out = torch.empty(n, dtype=torch.float32, device=x.device) if out is None else out
+    stream = torch.cuda.current_stream() if stream is None else stream
+    _check(lib().gf_round_to_f32(_ptr(x, torch.float64, n, "x"), _ptr(out, torch.float32, n, "out"), int(n),
+                                 c_void_p(stream.cuda_stream)))
+    return out
+
+
+def widen_to_f64(x, out=None, stream=None):
+    """gf_widen_to_f64: x (CUDA float32) widened to float64 by the library's integer routine."""
+    torch = _torch()
+    n = x.numel()
+    out = torch.empty(n, dtype=torch.float64, device=x.device) if out is None else out
+    stream = torch.cuda.current_stream() if stream is None else stream
+    _check(lib().gf_widen_to_f64(_ptr(x, torch.float32, n, "x"), _ptr(out, torch.float64, n, "out"), int(n),
+                                 c_void_p(stream.cuda_stream)))
+    return out
 
 
 def _select_dict(info):

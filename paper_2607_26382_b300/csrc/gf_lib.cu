@@ -3157,6 +3157,33 @@ __global__ void noalloc_eta_kernel(const double* __restrict__ partial, int nbloc
 
 }  // namespace
 
+namespace {
+template <typename To, typename From>
+int convert_array(const From* in, To* out, long long n, void* stream)
+{
+    if (n < 0) return set_err(GF_ERR_ARG, "n < 0");
+    if (n == 0) return GF_OK;
+    if (!in || !out) return set_err(GF_ERR_ARG, "null pointer");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long blocks = std::min<long long>((n + 255) / 256, 8LL * sms);
+    gf::convert_kernel<To, From><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(in, out, n);
+    CK(cudaGetLastError());
+    return GF_OK;
+}
+}  // namespace
+
+extern "C" int gf_round_to_f32(const double* in, float* out, long long n, void* stream)
+{
+    return convert_array<float, double>(in, out, n, stream);
+}
+
+extern "C" int gf_widen_to_f64(const float* in, double* out, long long n, void* stream)
+{
+    return convert_array<double, float>(in, out, n, stream);
+}
+
 extern "C" int gf_true_residual_noalloc(int nx, int ny, int nz, double h, double E0, double nu,
                                         const double* rho_hat, double p, double rho_min, const double* f,
                                         const double* u, double* eta, void* stream)

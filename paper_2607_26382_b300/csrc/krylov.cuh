@@ -524,7 +524,7 @@ __global__ void masked_convert_kernel(const TI* a, TO* b, long long n, int NX,
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
          q += (long long)gridDim.x * blockDim.x) {
         const bool fixed = fix ? ((fix[q / 3] >> (int)(q % 3)) & 1) != 0 : ((q / 3) % NX) == 0;
-        b[q] = fixed ? TO(0) : (TO)a[q];
+        b[q] = fixed ? TO(0) : convert<TO>(a[q]);
     }
 }
 

@@ -593,7 +593,7 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
             nn = ni + (long long)NX * nj + plane * ez;
             if (MODE != ST_APPLY) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) bn[c] = float(b[3 * nn + c]);
+                for (int c = 0; c < 3; ++c) bn[c] = convert<float>(b[3 * nn + c]);
             }
             if (MODE == ST_SWEEP) {
 #pragma unroll
@@ -702,10 +702,10 @@ modal_stencil_f32_kernel(const float* __restrict__ x, const BT* __restrict__ b, 
                 out[3 * nn + 2] = OT(0);
             } else if (MODE == ST_APPLY) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) out[3 * nn + c] = OT(a[c]);
+                for (int c = 0; c < 3; ++c) out[3 * nn + c] = convert<OT>(a[c]);
             } else if (MODE == ST_RESID) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) out[3 * nn + c] = OT(bn[c] - a[c]);
+                for (int c = 0; c < 3; ++c) out[3 * nn + c] = convert<OT>(bn[c] - a[c]);
             } else {
                 // the node's 3x3 diagonal block from its eight elements (previous layer: the
                 // node at local z offset 1; current layer: offset 0), in a fixed order

@@ -14,6 +14,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "cvt.cuh"
+
 namespace gf {
 
 template <typename T>
@@ -83,9 +85,9 @@ __device__ __forceinline__ void node_block_update(T d00, T d11, T d22, T d01, T 
     const T c22 = fma(d00, d11, -(d01 * d01));
     const T det = fma(d00, c00, fma(d01, c01, d02 * c02));
     const T s = omega / det;
-    out[0] = OT(fma(s, fma(c00, r0, fma(c01, r1, c02 * r2)), x[0]));
-    out[1] = OT(fma(s, fma(c01, r0, fma(c11, r1, c12 * r2)), x[1]));
-    out[2] = OT(fma(s, fma(c02, r0, fma(c12, r1, c22 * r2)), x[2]));
+    out[0] = convert<OT>(fma(s, fma(c00, r0, fma(c01, r1, c02 * r2)), x[0]));
+    out[1] = convert<OT>(fma(s, fma(c01, r0, fma(c11, r1, c12 * r2)), x[1]));
+    out[2] = convert<OT>(fma(s, fma(c02, r0, fma(c12, r1, c22 * r2)), x[2]));
 }
 
 // MODE == ST_APPLY: out = K x
@@ -493,7 +495,7 @@ first_sweep_store_kernel(const BT* __restrict__ b, T* __restrict__ bout, T* __re
     const long long nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
-    const T r0 = (T)b[3 * n + 0], r1 = (T)b[3 * n + 1], r2 = (T)b[3 * n + 2];
+    const T r0 = convert<T>(b[3 * n + 0]), r1 = convert<T>(b[3 * n + 1]), r2 = convert<T>(b[3 * n + 2]);
     bout[3 * n + 0] = r0;
     bout[3 * n + 1] = r1;
     bout[3 * n + 2] = r2;
