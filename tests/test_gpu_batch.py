@@ -82,6 +82,45 @@ def test_batch_matches_single_state(gf, selector, prec, outer, smoother, restart
     batch.close()
 
 
+def test_batch_half_sm_matches_single_state(gf):
+    """gf_batch_set_sm_share(1), called after the states are set: every state's result and
+    solution equal those of its single grid with the same half-SM launch shapes, bit for bit
+    (the same kernels and Gram-Schmidt block partition), and the accepted solutions pass
+    the oracle's guard."""
+    L = 3
+    pol = gf.policy_defaults(rho0=1e-8, ladder=[1e-5, 1e-4, 1e-3], kmax=120, solve_prec=1, solve_outer=0)
+    batch = gf.Batch([s[0] for s in STATES], levels=L)
+    tuned = batch.autotune()
+    rhos, fs = [], []
+    for i, (dims, kind, seed, q) in enumerate(STATES):
+        rhos.append(dev(_rho(dims, kind, seed, q)))
+        fs.append(dev(O.cantilever_load(O.Mesh(*dims))))
+        batch.set_state(i, rhos[i], fs[i], 3.0)
+    batch.set_sm_share(1)
+    with pytest.raises(gf.GFError):
+        batch.set_sm_share(-1)
+    res = batch.select_floor(pol)
+    for i, (dims, kind, seed, q) in enumerate(STATES):
+        g = gf.create_grid(*dims, levels=L)
+        g.set_stencil_blocks(*tuned[i])
+        g.set_sm_share(1)
+        g.set_density(rhos[i], 3.0)
+        u1 = torch.zeros(g.n_dof, dtype=torch.float64, device="cuda")
+        ref = g.select_floor(fs[i], u1, pol)
+        assert res[i]["attempts"] == ref["attempts"], i
+        assert res[i]["status"] == ref["status"] and res[i]["floor_index"] == ref["floor_index"], i
+        u2 = torch.zeros_like(u1)
+        batch.solution(i, u2)
+        assert torch.equal(u1, u2), i
+        if res[i]["status"] == gf.GF_ACCEPTED:
+            m = O.Mesh(*dims)
+            E = O.young_modulus(_rho(dims, kind, seed, q), res[i]["rho_min"], 3.0)
+            eta = O.true_residual(m, E, O.element_stiffness(), O.cantilever_load(m), u2.cpu().numpy())
+            assert eta <= 1e-6 * (1 + 1e-9)
+        g.close()
+    batch.close()
+
+
 def test_batch_sweep_inverse_matches_single_state(gf, monkeypatch):
     """With the coarsest inverse by the blocked symmetric sweep (GF_COARSE_LDL=0) the batch
     runs the sweep in lockstep over its states: every state's result and solution still
