@@ -195,6 +195,7 @@ struct gf_grid {
     float2* Vd = nullptr;             // double-float copy of the basis (outer == 2)
     float2* pdd = nullptr;            // per-block partial pairs of the double-float passes
     unsigned int* ddticket = nullptr; // arrival counter of their last-block finish
+    unsigned int* cgsticket = nullptr;   // the same for the FP64 Gram-Schmidt passes
     int md_alloc = 0, nbd = 0;        // nbd: largest grid of the double-float passes (partials rows)
     int nbd_k[3][3] = {};             // grid per pass (dots, update+dots, update+norm) and NV (8, 16, 32)
     gf::KState* st = nullptr;
@@ -1442,15 +1443,17 @@ int cgs2_step(gf_grid* g, int j, double* w, int outer)
     }
     const int q = NV == 8 ? 0 : (NV == 16 ? 1 : (NV == 24 ? 2 : 3));
     const int b0 = g->nbc[0][q], b1 = g->nbc[1][q], b2 = g->nbc[2][q];
-    LAUNCH(g, b0, gf::RED_THREADS, gf::cgs_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
-    LAUNCH(g, 1, 32 * 32, gf::reduce_partials_kernel, g->partial, b0, NV + 1, NV + 1, g->st, 0, 1);
+    // each pass sums its block rows in its last block to arrive (fp64_finish): h1, h2, ||w||^2
+    LAUNCH(g, b0, gf::RED_THREADS, gf::cgs_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st, g->st,
+           g->cgsticket);
     if (g->half_sm)
-        LAUNCH(g, b1, 128, (gf::cgs_update_dots_kernel<NV, 128>), g->V, ld, nv, w, n, g->partial, g->st);
+        LAUNCH(g, b1, 128, (gf::cgs_update_dots_kernel<NV, 128>), g->V, ld, nv, w, n, g->partial, g->st, g->st,
+               g->cgsticket);
     else
-        LAUNCH(g, b1, gf::RED_THREADS, gf::cgs_update_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
-    LAUNCH(g, 1, 32 * 32, gf::reduce_partials_kernel, g->partial, b1, NV, nv, g->st, 1, 1);
-    LAUNCH(g, b2, gf::RED_THREADS, gf::cgs_update_norm_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st);
-    LAUNCH(g, 1, 32, gf::reduce_partials_kernel, g->partial, b2, 1, 1, g->st, 2, 1);
+        LAUNCH(g, b1, gf::RED_THREADS, gf::cgs_update_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st, g->st,
+               g->cgsticket);
+    LAUNCH(g, b2, gf::RED_THREADS, gf::cgs_update_norm_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st, g->st,
+           g->cgsticket);
     LAUNCH(g, 1, 32, gf::arnoldi_tail_kernel, g->st, g->hist, j, NV, g->host_status_dev, 1e-14);
     return GF_OK;
 }
@@ -1495,7 +1498,8 @@ int cgs2_step_long(gf_grid* g, int j, double* w, int outer)
         for (int c = 0; c < slices; ++c) {
             const int off = c * NS, cnt = std::min(NS, nv - off);
             LAUNCH(g, g->nbr, gf::RED_THREADS, gf::cgs_dots_kernel<NS>, (const double*)(g->V + off * ld), ld, cnt,
-                   (const double*)w, n, g->partial, (const gf::KState*)g->st);
+                   (const double*)w, n, g->partial, (const gf::KState*)g->st, (gf::KState*)nullptr,
+                   (unsigned int*)nullptr);
             LAUNCH(g, 1, 32 * 32, gf::reduce_slice_kernel, (const double*)g->partial, g->nbr, NS + 1, 0, cnt, h + off,
                    (const gf::KState*)g->st);
             if (pass == 0 && c == 0)
@@ -2112,9 +2116,11 @@ int gf_create_grid(int nx, int ny, int nz, double h, double E0, double nu, int l
         (r = allocT(&g->cpos, (size_t)g->nc)) || (r = allocT(&g->cidx, (size_t)g->nc + 1)) ||
         (r = allocT(&g->dflag, 4)) || (r = allocT(&g->rho64, g->nel)) ||
         (r = allocT(&g->rho16, g->nel)) || (r = allocT(&g->work, g->ndof)) ||
-        (r = allocT(&g->partial, (size_t)partial_rows)) || (r = allocT(&g->st, 1)) || (r = allocT(&g->gst, 1)) ||
+        (r = allocT(&g->partial, (size_t)partial_rows)) || (r = allocT(&g->st, 1)) || (r = allocT(&g->cgsticket, 1)) || (r = allocT(&g->gst, 1)) ||
         (r = allocT(&g->Edf, g->nel)))
         return fail(r);
+    if (cudaMemset(g->cgsticket, 0, sizeof(unsigned int)) != cudaSuccess)
+        return fail(set_err(GF_ERR_CUDA, "Gram-Schmidt ticket"));
     if (cudaHostAlloc((void**)&g->host_status, sizeof(int), cudaHostAllocMapped) != cudaSuccess)
         return fail(set_err(GF_ERR_CUDA, "cudaHostAlloc"));
     if (cudaHostGetDevicePointer((void**)&g->host_status_dev, g->host_status, 0) != cudaSuccess)
@@ -2364,7 +2370,7 @@ int gf_destroy_grid(gf_grid* g)
     cudaFree(g->fc); cudaFree(g->fc_partial);
     cudaFree(g->Ainv); cudaFree(g->Agj); cudaFree(g->ldl_ws); cudaFree(g->cpos); cudaFree(g->cidx); cudaFree(g->dflag); cudaFree(g->cheb); cudaFree(g->cheb_ss);
     cudaFree(g->rho64); cudaFree(g->rho16); cudaFree(g->work); cudaFree(g->partial);
-    cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Vd); cudaFree(g->pdd); cudaFree(g->ddticket); cudaFree(g->Z); cudaFree(g->hist);
+    cudaFree(g->st); cudaFree(g->gst); cudaFree(g->V); cudaFree(g->Vd); cudaFree(g->pdd); cudaFree(g->ddticket); cudaFree(g->cgsticket); cudaFree(g->Z); cudaFree(g->hist);
     cudaFree(g->ckx);
     cudaFree(g->lz);
     cudaFree(g->lzv);

@@ -93,6 +93,34 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NV], int nv, do
     }
 }
 
+// Cross-block finish of the FP64 passes: every block has stored its partial row; the last
+// block to arrive (atomic ticket after a fence) sums column q < cnt over the blocks in
+// reduce_partials_kernel's order (lane l takes blocks l, l + 32, ... in turn, then a
+// shuffle tree), writes dst[q] and re-arms the ticket. No block waits on another, and the
+// sums do not depend on the order of arrival.
+__device__ __forceinline__ void fp64_finish(const double* partial, int stride, int cnt, double* dst,
+                                            unsigned int* ticket)
+{
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int nb = gridDim.x;
+    for (int q = threadIdx.x >> 5; q < cnt; q += nw) {
+        double s = 0.0;
+#pragma unroll 8
+        for (int b = lane; b < nb; b += 32) s += __ldcg(partial + (long long)b * stride + q);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) dst[q] = s;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
 // rows of block b: [b*chunk, min(n, (b+1)*chunk))
 __device__ __forceinline__ void block_rows(long long n, long long& r0, long long& r1)
 {
@@ -119,7 +147,8 @@ struct CgsRows {
 template <int NV>
 __global__ void __launch_bounds__(RED_THREADS, NV >= 16 ? 2 : 1)
 cgs_dots_kernel(const double* __restrict__ V, long long ld, int nv, const double* __restrict__ w,
-                long long n, double* __restrict__ partial, const KState* __restrict__ st)
+                long long n, double* __restrict__ partial, const KState* st, KState* fin = nullptr,
+                unsigned int* ticket = nullptr)
 {
     constexpr int ROWS = CgsRows<NV>::value;
     constexpr int G = NV == 32 ? 16 : NV;   // vectors loaded together
@@ -165,6 +194,7 @@ cgs_dots_kernel(const double* __restrict__ V, long long ld, int nv, const double
     }
     // row layout: dots in slots [0, nv), ||w||^2 in slot NV (row stride NV + 1)
     block_reduce_store<NV + 1>(acc, NV + 1, partial + (long long)blockIdx.x * (NV + 1));
+    if (ticket != nullptr) fp64_finish(partial, NV + 1, NV + 1, fin->h1, ticket);   // h1, ||w||^2 in h1[NV]
 }
 
 // pass 2: w -= sum_i h1_i V_i ; partial[b][i] = sum_r V_i[r] w_new[r]
@@ -175,7 +205,8 @@ cgs_dots_kernel(const double* __restrict__ V, long long ld, int nv, const double
 template <int NV, int T = RED_THREADS>
 __global__ void __launch_bounds__(T)
 cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
-                       long long n, double* __restrict__ partial, const KState* __restrict__ st)
+                       long long n, double* __restrict__ partial, const KState* st, KState* fin = nullptr,
+                       unsigned int* ticket = nullptr)
 {
     constexpr int ROWS = CgsRows<NV>::value;
     if (st->status != KS_RUN) return;
@@ -217,6 +248,7 @@ cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, doubl
         }
     }
     block_reduce_store<NV, T>(acc, nv, partial + (long long)blockIdx.x * NV);
+    if (ticket != nullptr) fp64_finish(partial, NV, nv, fin->h2, ticket);
 }
 
 // pass 3: w -= sum_i h2_i V_i ; partial[b][0] = ||w_new||^2 (block part)
@@ -224,7 +256,8 @@ cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, doubl
 template <int NV>
 __global__ void __launch_bounds__(RED_THREADS, NV >= 16 ? 2 : 1)
 cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
-                       long long n, double* __restrict__ partial, const KState* __restrict__ st)
+                       long long n, double* __restrict__ partial, const KState* st, KState* fin = nullptr,
+                       unsigned int* ticket = nullptr)
 {
     constexpr int ROWS = CgsRows<NV>::value;
     constexpr int G = NV == 32 ? 16 : NV;
@@ -273,6 +306,7 @@ cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, doubl
         }
     }
     block_reduce_store<1>(acc, 1, partial + blockIdx.x);
+    if (ticket != nullptr) fp64_finish(partial, 1, 1, &fin->ww, ticket);
 }
 
 template <int NV>
