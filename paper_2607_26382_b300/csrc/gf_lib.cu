@@ -1443,7 +1443,8 @@ int cgs2_step(gf_grid* g, int j, double* w, int outer)
     }
     const int q = NV == 8 ? 0 : (NV == 16 ? 1 : (NV == 24 ? 2 : 3));
     const int b0 = g->nbc[0][q], b1 = g->nbc[1][q], b2 = g->nbc[2][q];
-    // each pass sums its block rows in its last block to arrive (fp64_finish): h1, h2, ||w||^2
+    // each pass sums its block rows in its last block to arrive (fp64_finish): h1, h2, ||w||^2;
+    // the last pass's last block then runs the Arnoldi tail
     LAUNCH(g, b0, gf::RED_THREADS, gf::cgs_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st, g->st,
            g->cgsticket);
     if (g->half_sm)
@@ -1453,8 +1454,7 @@ int cgs2_step(gf_grid* g, int j, double* w, int outer)
         LAUNCH(g, b1, gf::RED_THREADS, gf::cgs_update_dots_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st, g->st,
                g->cgsticket);
     LAUNCH(g, b2, gf::RED_THREADS, gf::cgs_update_norm_kernel<NV>, g->V, ld, nv, w, n, g->partial, g->st, g->st,
-           g->cgsticket);
-    LAUNCH(g, 1, 32, gf::arnoldi_tail_kernel, g->st, g->hist, j, NV, g->host_status_dev, 1e-14);
+           g->cgsticket, g->hist, j, NV, (volatile int*)g->host_status_dev, 1e-14);   // + the Arnoldi tail
     return GF_OK;
 }
 

@@ -98,7 +98,7 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NV], int nv, do
 // reduce_partials_kernel's order (lane l takes blocks l, l + 32, ... in turn, then a
 // shuffle tree), writes dst[q] and re-arms the ticket. No block waits on another, and the
 // sums do not depend on the order of arrival.
-__device__ __forceinline__ void fp64_finish(const double* partial, int stride, int cnt, double* dst,
+__device__ __forceinline__ bool fp64_finish(const double* partial, int stride, int cnt, double* dst,
                                             unsigned int* ticket)
 {
     __shared__ bool last;
@@ -106,7 +106,7 @@ __device__ __forceinline__ void fp64_finish(const double* partial, int stride, i
     __syncthreads();
     if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     __syncthreads();
-    if (!last) return;
+    if (!last) return false;
     __threadfence();
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int nb = gridDim.x;
@@ -119,7 +119,13 @@ __device__ __forceinline__ void fp64_finish(const double* partial, int stride, i
         if (lane == 0) dst[q] = s;
     }
     if (threadIdx.x == 0) *ticket = 0u;
+    return true;
 }
+
+// Step j's Arnoldi tail, one warp (defined with arnoldi_tail_kernel below).
+__device__ __forceinline__ void arnoldi_tail_warp(KState* st, double* hist, int j, int ww0_slot,
+                                                  volatile int* host_status, double breakdown_rtol, double* col,
+                                                  double* cs, double* sn, int lane);
 
 // rows of block b: [b*chunk, min(n, (b+1)*chunk))
 __device__ __forceinline__ void block_rows(long long n, long long& r0, long long& r1)
@@ -256,8 +262,8 @@ cgs_update_dots_kernel(const double* __restrict__ V, long long ld, int nv, doubl
 template <int NV>
 __global__ void __launch_bounds__(RED_THREADS, NV >= 16 ? 2 : 1)
 cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, double* __restrict__ w,
-                       long long n, double* __restrict__ partial, const KState* st, KState* fin = nullptr,
-                       unsigned int* ticket = nullptr)
+                       long long n, double* __restrict__ partial, const KState* st, KState* fin, unsigned int* ticket,
+                       double* tail_hist, int j, int ww0_slot, volatile int* host_status, double breakdown_rtol)
 {
     constexpr int ROWS = CgsRows<NV>::value;
     constexpr int G = NV == 32 ? 16 : NV;
@@ -306,7 +312,13 @@ cgs_update_norm_kernel(const double* __restrict__ V, long long ld, int nv, doubl
         }
     }
     block_reduce_store<1>(acc, 1, partial + blockIdx.x);
-    if (ticket != nullptr) fp64_finish(partial, 1, 1, &fin->ww, ticket);
+    if (ticket != nullptr && fp64_finish(partial, 1, 1, &fin->ww, ticket) && tail_hist != nullptr) {
+        // the last block also runs step j's Arnoldi tail (arnoldi_tail_kernel's warp)
+        __shared__ double col[KRY_MMAX + 1], cs[KRY_MMAX], sn[KRY_MMAX];
+        __syncthreads();   // ||w||^2 stored before warp 0 reads it
+        if (threadIdx.x < 32)
+            arnoldi_tail_warp(fin, tail_hist, j, ww0_slot, host_status, breakdown_rtol, col, cs, sn, (int)threadIdx.x);
+    }
 }
 
 template <int NV>
@@ -385,12 +397,11 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n
 // updates g, records the history and decides whether to stop. The serial recurrence
 // reads only shared memory: from global memory, each step's loads would wait behind
 // the previous step's store to the same struct.
-__global__ void arnoldi_tail_kernel(KState* __restrict__ st, double* __restrict__ hist, int j,
-                                    int ww0_slot, volatile int* host_status, double breakdown_rtol)
+__device__ __forceinline__ void arnoldi_tail_warp(KState* st, double* hist, int j, int ww0_slot,
+                                                  volatile int* host_status, double breakdown_rtol, double* col,
+                                                  double* cs, double* sn, int lane)
 {
-    __shared__ double col[KRY_MMAX + 1], cs[KRY_MMAX], sn[KRY_MMAX];
     if (st->status != KS_RUN) return;   // uniform over the warp
-    const int lane = threadIdx.x;
     for (int i = lane; i <= j; i += 32) col[i] = st->h1[i] + st->h2[i];
     for (int i = lane; i < j; i += 32) {
         cs[i] = st->cs[i];
@@ -449,6 +460,13 @@ __global__ void arnoldi_tail_kernel(KState* __restrict__ st, double* __restrict_
         st->inv = 1.0 / hnext;
     }
     if (st->status == KS_STOP) *host_status = KS_STOP;
+}
+
+__global__ void arnoldi_tail_kernel(KState* __restrict__ st, double* __restrict__ hist, int j,
+                                    int ww0_slot, volatile int* host_status, double breakdown_rtol)
+{
+    __shared__ double col[KRY_MMAX + 1], cs[KRY_MMAX], sn[KRY_MMAX];
+    arnoldi_tail_warp(st, hist, j, ww0_slot, host_status, breakdown_rtol, col, cs, sn, (int)threadIdx.x);
 }
 
 // Cycle start: beta = ||r||, history[k] = beta/||f|| (a true residual), g = beta e1.
