@@ -214,3 +214,33 @@ def test_bridge_modal_operator_forced_run_lengths(gf, monkeypatch):
             y = torch.full((g.n_dof,), np.nan, dtype=torch.float64, device="cuda")
             g.apply_K(dev(u), y)
             assert relerr(host(y), ref) <= 1e-10, (bx, chunk)
+
+
+def test_bridge_half_sm_shapes_are_bit_identical(gf):
+    """gf_set_sm_share(1) on the bridge (the masked modal kernels on 16 x 16 tiles, the
+    fix-up with per-node supports): FP64 K*u, FP32 K*u and the mixed V-cycle equal those of
+    the full-SM shapes bit for bit, and K*u matches the oracle."""
+    nx, ny, nz, L = 48, 24, 12, 2
+    m = O.BridgeMesh(nx, ny, nz)
+    rho = synth.smoothed_gaussian_density(nx, ny, nz, 4, 2.0, 0.4)
+    u = synth.random_vector(m.n_dof, 9)
+    outs = []
+    for share in (0, 1):
+        g = gf.create_grid(nx, ny, nz, levels=L)
+        g.set_sm_share(share)
+        g.set_geometry(gf.GF_GEOM_BRIDGE)
+        g.set_density(dev(rho), 3.0)
+        g.set_floor(1e-4)
+        y = torch.full((g.n_dof,), np.nan, dtype=torch.float64, device="cuda")
+        g.apply_K(dev(u), y)
+        y32 = torch.full((g.n_dof,), np.nan, dtype=torch.float32, device="cuda")
+        g.apply_K_f32(dev(u).float(), y32)
+        z = torch.full((g.n_dof,), np.nan, dtype=torch.float64, device="cuda")
+        g.vcycle(dev(u * m.free), z, gf.GF_MIXED)
+        outs.append((host(y), host(y32), host(z)))
+        g.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert not np.isnan(a).any()
+        assert np.array_equal(a, b)
+    ref = O.apply_K(m, O.young_modulus(rho, 1e-4, 3.0), O.element_stiffness(), u)
+    assert relerr(outs[1][0], ref) <= 1e-10
